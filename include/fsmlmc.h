@@ -1,0 +1,193 @@
+/*
+ * fsmlmc.h - C ABI of the GB300 (sm_103a) Frequency-Splitting MLMC trace library.
+ *
+ * Computes the stochastic traces of arXiv:2212.04430 (Whyte, Stathopoulos,
+ * Romero, Orginos, "Optimizing Shift Selection in Multilevel Monte Carlo for
+ * Disconnected Diagrams in Lattice QCD"): the shifted Wilson-Dirac solves
+ * (D + sigma I) x = z of Eq. (shifted_linear_systems) for Z4 noise z, the
+ * Gamma Omega_p insertion of Sec. 1, the level traces of Eq. (fs_trace_est) with
+ * the practical variance of Eq. (practical_variance), and the variance sampling
+ * algorithm of Sec. 3.1.
+ *
+ * Conventions
+ *   Lattice   dims = {Lx, Ly, Lz, Lt}, all even, >= 2; V = Lx Ly Lz Lt.
+ *             site = x + Lx (y + Ly (z + Lz t)).
+ *   Operator  Wilson, r = 1, DeGrand-Rossi gamma basis (gamma_5 = diag(1,1,-1,-1)):
+ *             (D psi)(x) = (4 + m) psi(x) - 1/2 sum_mu [(1 - g_mu) U_mu(x) psi(x + mu)
+ *                                         + (1 + g_mu) U_mu(x - mu)^dag psi(x - mu)],
+ *             mu = 0..3 is x, y, z, t; the t-hop across the boundary is multiplied by bc_t.
+ *   Omega_p   (Omega_p psi)(x) = U_z(x) U_z(x + z) ... U_z(x + (p-1) z) psi(x + p z)   (Sec. 1)
+ *   Noise     z(x, s, c) = i^k, k = (Philox4x32-10(ctr = {x, sample, level, job},
+ *             key = {seed mod 2^32, seed >> 32}).word0 >> 2(3 s + c)) & 3.
+ *   Host layouts (double, interleaved re/im):
+ *             spinor  [V][4 spin][3 colour][2]      gauge  [4 mu][V][3][3][2], U_mu(x): x -> x + mu
+ *             Gamma   [4][4][2] (row major, complex)
+ *
+ * Ownership and threading
+ *   The caller owns every pointer it passes; the library copies what it needs and
+ *   never keeps a caller pointer past the call. Device state (gauge copies, solver
+ *   workspaces) belongs to the fs_ctx and is freed by fs_ctx_destroy. A context is
+ *   used by one host thread at a time. Work is issued on the context's stream
+ *   (fs_set_stream, default: a stream the context creates); calls return after the
+ *   results they write are complete.
+ *
+ * Errors
+ *   Every int-returning call returns FS_OK (0) or one of the FS_ERR_* codes below;
+ *   fs_last_error(ctx) gives a message for the last failure on that context.
+ */
+#ifndef FSMLMC_H
+#define FSMLMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum fs_status {
+  FS_OK = 0,
+  FS_ERR_ARG = 1,      /* invalid argument (null pointer, bad size, odd dimension, ...)   */
+  FS_ERR_INPUT = 2,    /* non-finite value in an input array                              */
+  FS_ERR_OOM = 3,      /* device allocation failed                                        */
+  FS_ERR_BUDGET = 4,   /* request exceeds the memory budget                               */
+  FS_ERR_NOCONV = 5,   /* a system hit max_iter; outputs are written, see fs_sys_stats     */
+  FS_ERR_TIMEOUT = 6,  /* a bounded wait expired                                          */
+  FS_ERR_CUDA = 7,     /* CUDA runtime error                                              */
+  FS_ERR_STATE = 8     /* call not valid in the context's state (e.g. no gauge field yet) */
+};
+
+/* Storage precision of the Krylov vectors. F64: FP64 storage and arithmetic.
+ * F32 / F16 / BF16: that storage with FP32 arithmetic, FP64 reductions and FP64
+ * reliable updates (true residual recomputed in FP64). */
+enum fs_prec { FS_PREC_F64 = 0, FS_PREC_F32 = 1, FS_PREC_F16 = 2, FS_PREC_BF16 = 3 };
+
+/* Level estimators (all unbiased for the same level trace):
+ *   FS_EST_DIFF        z^dag Gamma Omega_p [(D+s_l)^-1 - (D+s_{l+1})^-1] z, Eq. (tele_sum)
+ *   FS_EST_SPLIT_EVEN  (s_{l+1}-s_l) [(D+s_l)^-dag z]^dag Gamma Omega_p (D+s_{l+1})^-1 z,
+ *                      Eq. (fs_trace_est); the adjoint solve uses gamma_5 z
+ *   FS_EST_PRODUCT     (s_{l+1}-s_l) z^dag Gamma Omega_p (D+s_l)^-1 (D+s_{l+1})^-1 z,
+ *                      Eq. (tele_sum_prod_disp0), two nested solves
+ * The last level is z^dag Gamma Omega_p (D+s_L)^-1 z for all three. */
+enum fs_estimator { FS_EST_DIFF = 0, FS_EST_SPLIT_EVEN = 1, FS_EST_PRODUCT = 2 };
+
+/* Per-system solver status (fs_sys_stats.status). */
+enum fs_sys_status { FS_SYS_CONVERGED = 2, FS_SYS_NOCONV = 3 };
+
+typedef struct fs_ctx fs_ctx;
+
+typedef struct fs_solve_params {
+  double tol;          /* stop when ||z - (D+sigma) x|| <= tol ||z||  (FP64 true residual)   */
+  int max_iter;        /* BiCGStab iterations per system before FS_SYS_NOCONV                */
+  int prec;            /* enum fs_prec                                                       */
+  int rhs_tile;        /* systems solved together in one batch (1..64); 0 = library choice  */
+  int link_compress;   /* 18: full links; 12: two rows stored, third reconstructed          */
+  double delta;        /* reliable update when the sloppy residual drops by this factor;
+                          0 = library choice                                                 */
+  int verify;          /* 1: recompute the full-lattice FP64 residual of every solution      */
+  int pad;
+} fs_solve_params;
+
+typedef struct fs_sys_stats {
+  int iters;           /* BiCGStab iterations                                                */
+  int status;          /* enum fs_sys_status                                                 */
+  int reliable_updates;
+  int restarts;
+  double true_resid;   /* ||z - (D+sigma) x|| / ||z|| in FP64                                 */
+} fs_sys_stats;
+
+typedef struct fs_mlmc_params {
+  double m;                 /* bare mass                                                   */
+  int nlev;                 /* number of shifts = L + 1                                    */
+  int p;                    /* z-displacement of Omega_p, 0 <= p < Lz                      */
+  const double* sigma;      /* [nlev] shifts, sigma_0 < ... < sigma_L, Eq. (tele_sum)       */
+  const int* n_samples;     /* [nlev] N_l noise vectors per level                           */
+  const double* gamma;      /* Gamma, 4x4 complex [4][4][2]                                 */
+  uint64_t seed;            /* Philox key                                                   */
+  uint32_t job;             /* Philox counter word 3                                        */
+  int estimator;            /* enum fs_estimator                                            */
+  fs_solve_params solve;
+} fs_mlmc_params;
+
+/* ---- context ------------------------------------------------------------------ */
+
+/* Create a context for a lattice on CUDA device `device`. bc_t = -1 (antiperiodic in t)
+ * or +1 (periodic). FS_ERR_ARG for odd or non-positive dims or V >= 2^31 / 24. */
+int fs_ctx_create(fs_ctx** ctx, const int dims[4], int bc_t, int device);
+void fs_ctx_destroy(fs_ctx* ctx);
+/* Message of the last error on ctx ("" if none); valid until the next call on ctx. */
+const char* fs_last_error(const fs_ctx* ctx);
+/* Issue all work of ctx on `stream` (a cudaStream_t; NULL restores the context's own). */
+int fs_set_stream(fs_ctx* ctx, void* stream);
+/* Device memory currently held by ctx, in bytes. */
+size_t fs_ctx_device_bytes(const fs_ctx* ctx);
+
+/* Upload the gauge field U (host, [4][V][3][3][2] doubles). Builds the FP64 copy used
+ * for true residuals and contractions and the lower-precision copies on demand.
+ * FS_ERR_INPUT if U holds a non-finite value. */
+int fs_set_gauge(fs_ctx* ctx, const double* U);
+
+/* ---- the operations of the paper -------------------------------------------------- */
+
+/* out_k = (D + sigma I) in_k for k < nrhs, full lattice (the operator of
+ * Eq. (shifted_linear_systems)). in/out: host [nrhs][V][4][3][2]. prec selects the
+ * storage precision of the device vectors (F64 computes in FP64, others in FP32). */
+int wilson_dslash(fs_ctx* ctx, double m, double sigma, const double* in, double* out, int nrhs,
+                  int prec, int link_compress);
+
+/* Solve (D + sigma_j I) x_{j,k} = b_k, Eq. (shifted_linear_systems), for every shift j < nshift
+ * and right-hand side k < nrhs, with even-odd preconditioned BiCGStab batched over systems.
+ * b: host [nrhs][V][24]; x: host [nshift][nrhs][V][24]; stats (optional): [nshift][nrhs].
+ * Returns FS_ERR_NOCONV if any system stopped at max_iter (x and stats still written). */
+int shifted_solve(fs_ctx* ctx, double m, const double* sigma, int nshift, const double* b, int nrhs,
+                  double* x, const fs_solve_params* params, fs_sys_stats* stats);
+
+/* FS-MLMC trace estimate, Eq. (fs_trace_est): for every level l < nlev, N_l Z4 noise
+ * vectors z_{s,l} (Philox counter {site, s, l, job}) give samples c_{s,l} of the chosen
+ * estimator. Outputs (host, caller-owned):
+ *   trace   [nlev][2]   T_l = (1/N_l) sum_s c_{s,l}
+ *   var     [nlev]      V_l = (1/N_l) sum_s |c_{s,l}|^2 - |T_l|^2   (Eq. (practical_variance))
+ *   samples [sum N_l][2] (optional) every c_{s,l}, level-major
+ *   stats   [number of solves] (optional), in the order the solves are listed in
+ *           fs_mlmc_num_solves' documentation.
+ * The total trace is sum_l T_l and V_FS = sum_l V_l / N_l (Eq. (total_var)). */
+int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* params, double* trace, double* var,
+                     double* samples, fs_sys_stats* stats);
+
+/* Number of shifted solves mlmc_level_trace performs: per level l < L two solves per
+ * sample (DIFF: z at s_l then z at s_{l+1}; SPLIT_EVEN: gamma_5 z at s_l then z at s_{l+1};
+ * PRODUCT: z at s_{l+1} then its solution at s_l), one per sample at level L. */
+int fs_mlmc_num_solves(const fs_mlmc_params* params);
+
+/* Variance sampling, Sec. 3.1 algorithm, for the m_shifts sampling shifts s_hat
+ * (s_hat_0 < ... ) and every displacement p[k], k < np, with Ns Z4 noise vectors
+ * (Philox counter {site, k, 0x80000000, job}). For each noise z_k and shift s_i it solves
+ * x^(i) = (D+s_i)^-1 z_k and y^(i) = (D+s_i)^-dag z_k = gamma_5 (D+s_i)^-1 gamma_5 z_k, then
+ *   a_i  = z_k^dag Gamma Omega_p x^(i)         -> VL[k_p][i]      (Eq. (sampled_single))
+ *   b_ij = y^(i)^dag Gamma Omega_p x^(j), j>=i -> Vbar[k_p][i][j] (Eq. (bar_vl))
+ * with the practical variance of Eq. (practical_variance). Outputs (host):
+ *   VL [np][m_shifts], Vbar [np][m_shifts][m_shifts] (entries j < i set to 0),
+ *   a (optional) [Ns][np][m_shifts][2], b (optional) [Ns][np][m_shifts][m_shifts][2],
+ *   iters (optional) [m_shifts] mean BiCGStab iterations of the solves at each shift. */
+int variance_sample(fs_ctx* ctx, double m, const double* s_hat, int m_shifts, const double* gamma,
+                    const int* p, int np, int Ns, uint64_t seed, uint32_t job,
+                    const fs_solve_params* params, double* VL, double* Vbar, double* a, double* b,
+                    double* iters);
+
+/* The Z4 noise vector (seed, job, level, sample) as integer codes k (z = i^k),
+ * host [V][4][3] bytes, generated on the device (bit-exact RNG checks). */
+int fs_noise_codes(fs_ctx* ctx, uint64_t seed, uint32_t job, uint32_t level, uint32_t sample,
+                   uint8_t* codes);
+
+/* Sum over all calls since the last reset of the device time of the hopping (dslash)
+ * kernel launches of ctx: number of launches, total milliseconds, and the algorithmic
+ * bytes they moved. Timing is recorded only while enabled (CUDA events around each
+ * launch on the context's stream). */
+int fs_profile_enable(fs_ctx* ctx, int enable);
+int fs_profile_read(fs_ctx* ctx, long long* launches, double* total_ms, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSMLMC_H */

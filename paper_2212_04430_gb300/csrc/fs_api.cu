@@ -1,0 +1,668 @@
+// C ABI of the FS-MLMC library (declared in include/fsmlmc.h).
+#include "fsmlmc.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fs_engine.h"
+
+struct fs_ctx {
+  fs::Ctx c;
+};
+
+namespace {
+
+using fs::Ctx;
+
+bool finite_array(const double* a, size_t n) {
+  for (size_t i = 0; i < n; i++)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+int set_device(Ctx& c) {
+  cudaError_t e = cudaSetDevice(c.device);
+  return e ? c.cuda_fail(e, "cudaSetDevice") : 0;
+}
+
+fs::NoiseSpec noise_id(uint64_t seed, uint32_t job, uint32_t level, uint32_t sample, bool g5) {
+  fs::NoiseSpec n{};
+  n.key0 = (uint32_t)(seed & 0xFFFFFFFFull);
+  n.key1 = (uint32_t)(seed >> 32);
+  n.job = job;
+  n.level = level;
+  n.sample = sample;
+  n.flags = fs::NOISE_VALID | (g5 ? fs::NOISE_G5 : 0);
+  return n;
+}
+
+struct Opts {
+  fs::SolveOpts so;
+  int tile;
+};
+
+int resolve_params(Ctx& c, const fs_solve_params* p, int nsys, double m, Opts& o) {
+  fs_solve_params d{};
+  if (p) d = *p;
+  o.so.m = m;
+  o.so.prec = d.prec;
+  if (o.so.prec < FS_PREC_F64 || o.so.prec > FS_PREC_BF16) return c.fail(FS_ERR_ARG, "prec must be 0..3");
+  o.so.tol = d.tol > 0 ? d.tol : (o.so.prec == FS_PREC_F64 ? 1e-10 : 1e-8);
+  if (o.so.tol < 1e-14) return c.fail(FS_ERR_ARG, "tol below 1e-14 is not reachable in FP64");
+  o.so.max_iter = d.max_iter > 0 ? d.max_iter : 20000;
+  o.so.nr = d.link_compress == 0 ? 18 : d.link_compress;
+  if (o.so.nr != 18 && o.so.nr != 12) return c.fail(FS_ERR_ARG, "link_compress must be 18 or 12");
+  if (o.so.prec == FS_PREC_F64) o.so.nr = 18;  // FP64 path keeps full links
+  if (d.delta > 0) o.so.delta = d.delta;
+  else o.so.delta = o.so.prec == FS_PREC_F64 ? 0.0 : (o.so.prec == FS_PREC_F32 ? 1e-3 : 0.1);
+  if (o.so.delta >= 1.0) return c.fail(FS_ERR_ARG, "delta must be < 1");
+  o.so.verify = d.verify;
+  o.so.check_every = 4;
+  int tile = d.rhs_tile;
+  if (tile < 0 || tile > fs::MAX_TILE) return c.fail(FS_ERR_ARG, "rhs_tile must be in [0, 64]");
+  if (tile == 0) tile = std::min(32, std::max(1, nsys));
+  o.tile = tile;
+  return 0;
+}
+
+void fill_stats(const fs::SysState& s, fs_sys_stats* out, bool verify) {
+  out->iters = s.iters;
+  out->status = s.status == fs::SYS_CONVERGED ? FS_SYS_CONVERGED : FS_SYS_NOCONV;
+  out->reliable_updates = s.updates;
+  out->restarts = s.restarts;
+  const double r2 = verify ? s.r2_full : s.r2_true;
+  out->true_resid = s.b2 > 0 ? std::sqrt(r2 / s.b2) : 0.0;
+}
+
+// A group of systems that must share a tile, with the contractions over their solutions.
+struct Group {
+  std::vector<fs::SysSpec> sys;
+  std::vector<fs::ContractPair> pairs;  // right / left are group-local; out is a global row
+  std::vector<int> stat_index;          // global stats index per system (-1: none)
+};
+
+// Solve groups tile by tile (whole groups per tile) and run their contractions.
+int run_groups(Ctx& c, const std::vector<Group>& groups, const Opts& o, const double* gamma,
+               const std::vector<int>& plist, int rows, std::vector<double>& result,
+               std::vector<fs::SysState>* states, int* noconv) {
+  int gmax = 1;
+  for (auto& g : groups) gmax = std::max(gmax, (int)g.sys.size());
+  const int N = std::max(o.tile, gmax);
+  if (N > fs::MAX_TILE) return c.fail(FS_ERR_ARG, "a group of systems does not fit in one tile");
+  fs::TileBase* T = c.tile(o.so.prec, N, o.so.nr);
+  if (!T) return c.fail(FS_ERR_OOM, "device allocation of the solver tile failed");
+  const int np = (int)plist.size();
+  result.assign((size_t)rows * np * 2, 0.0);
+  size_t gi = 0;
+  while (gi < groups.size()) {
+    std::vector<fs::SysSpec> specs;
+    std::vector<fs::ContractPair> pairs;
+    std::vector<int> stat_idx;
+    while (gi < groups.size() && specs.size() + groups[gi].sys.size() <= (size_t)N) {
+      const int base = (int)specs.size();
+      for (auto& s : groups[gi].sys) specs.push_back(s);
+      for (int k : groups[gi].stat_index) stat_idx.push_back(k);
+      for (auto p : groups[gi].pairs) {
+        p.right += base;
+        p.left += base;
+        pairs.push_back(p);
+      }
+      gi++;
+    }
+    int rc = fs::solve_tile(&c, T, specs.data(), (int)specs.size(), o.so);
+    if (rc) return rc;
+    for (size_t j = 0; j < specs.size(); j++) {
+      if (T->st_h[j].status != fs::SYS_CONVERGED) *noconv = 1;
+      if (states && stat_idx[j] >= 0) (*states)[stat_idx[j]] = T->st_h[j];
+    }
+    if (!pairs.empty()) {
+      std::vector<double> part;
+      rc = fs::contract_tile(&c, T, pairs, gamma, plist, part, rows);
+      if (rc) return rc;
+      for (auto& p : pairs)
+        for (int q = 0; q < np * 2; q++) result[(size_t)p.out * np * 2 + q] = part[(size_t)p.out * np * 2 + q];
+    }
+  }
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fs_ctx_create(fs_ctx** out, const int dims[4], int bc_t, int device) {
+  if (!out || !dims) return FS_ERR_ARG;
+  *out = nullptr;
+  long long V = 1;
+  for (int mu = 0; mu < 4; mu++) {
+    if (dims[mu] < 2 || dims[mu] % 2) return FS_ERR_ARG;
+    V *= dims[mu];
+  }
+  if (V >= (1LL << 27)) return FS_ERR_ARG;
+  if (bc_t != 1 && bc_t != -1) return FS_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return FS_ERR_CUDA; }
+  fs_ctx* ctx = new fs_ctx();
+  Ctx& c = ctx->c;
+  c.device = device;
+  for (int mu = 0; mu < 4; mu++) c.g.L[mu] = dims[mu];
+  c.g.Lh0 = dims[0] / 2;
+  c.g.V = (int)V;
+  c.g.Vh = (int)(V / 2);
+  c.g.bc_t = bc_t;
+  if (cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c.own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return FS_ERR_CUDA;
+  }
+  c.stream = c.own_stream;
+  *out = ctx;
+  return FS_OK;
+}
+
+void fs_ctx_destroy(fs_ctx* ctx) {
+  if (!ctx) return;
+  Ctx& c = ctx->c;
+  cudaSetDevice(c.device);
+  cudaStreamSynchronize(c.stream);
+  c.tiles.clear();
+  if (c.gauge64) cudaFree(c.gauge64);
+  for (auto& kv : c.gauge_lo) cudaFree(kv.second);
+  if (c.canon_d) cudaFree(c.canon_d);
+  if (c.canon_h) cudaFreeHost(c.canon_h);
+  for (auto& ev : c.prof.pending) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+  for (auto& ev : c.prof.pool) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+  if (c.prof.work_d) cudaFree(c.prof.work_d);
+  if (c.own_stream) cudaStreamDestroy(c.own_stream);
+  delete ctx;
+}
+
+const char* fs_last_error(const fs_ctx* ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
+
+int fs_set_stream(fs_ctx* ctx, void* stream) {
+  if (!ctx) return FS_ERR_ARG;
+  ctx->c.stream = stream ? (cudaStream_t)stream : ctx->c.own_stream;
+  return FS_OK;
+}
+
+size_t fs_ctx_device_bytes(const fs_ctx* ctx) { return ctx ? ctx->c.device_bytes() : 0; }
+
+int fs_set_gauge(fs_ctx* ctx, const double* U) {
+  if (!ctx) return FS_ERR_ARG;
+  Ctx& c = ctx->c;
+  if (!U) return c.fail(FS_ERR_ARG, "null gauge field");
+  if (int rc = set_device(c)) return rc;
+  const size_t n = (size_t)4 * c.g.V * 18;
+  if (!finite_array(U, n)) return c.fail(FS_ERR_INPUT, "gauge field holds a non-finite value");
+  double* stage = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&stage, n * sizeof(double), c.stream);
+  if (e) return c.cuda_fail(e, "gauge staging allocation");
+  e = cudaMemcpyAsync(stage, U, n * sizeof(double), cudaMemcpyHostToDevice, c.stream);
+  auto need = [&](void*& p, size_t bytes) -> cudaError_t {
+    if (p) return cudaSuccess;
+    cudaError_t r = cudaMalloc(&p, bytes);
+    if (r == cudaSuccess) c.extra_bytes += bytes;
+    return r;
+  };
+  const size_t nl = (size_t)8 * c.g.Vh;
+  if (!e) e = need(c.gauge64, nl * 18 * sizeof(double));
+  if (!e) e = fs::launch_gauge_pack<double>(c.gauge64, stage, c.g, 18, c.stream);
+  struct LoCopy { int prec, nr; size_t bytes; };
+  const LoCopy lo[] = {
+      {FS_PREC_F32, 18, nl * fs::link_pad<float>(18) * sizeof(float)},
+      {FS_PREC_F32, 12, nl * fs::link_pad<float>(12) * sizeof(float)},
+      {FS_PREC_F16, 18, nl * fs::link_pad<__half>(18) * sizeof(__half)},
+      {FS_PREC_F16, 12, nl * fs::link_pad<__half>(12) * sizeof(__half)},
+  };
+  for (const LoCopy& l : lo) {
+    if (e) break;
+    void*& p = c.gauge_lo[l.prec * 100 + l.nr];
+    e = need(p, l.bytes);
+    if (!e) {
+      if (l.prec == FS_PREC_F32) e = fs::launch_gauge_pack<float>(p, stage, c.g, l.nr, c.stream);
+      else e = fs::launch_gauge_pack<__half>(p, stage, c.g, l.nr, c.stream);
+    }
+  }
+  cudaFreeAsync(stage, c.stream);
+  if (!e) e = cudaStreamSynchronize(c.stream);
+  if (e) return c.cuda_fail(e, "fs_set_gauge");
+  c.have_gauge = true;
+  return FS_OK;
+}
+
+int wilson_dslash(fs_ctx* ctx, double m, double sigma, const double* in, double* out, int nrhs, int prec,
+                  int link_compress) {
+  if (!ctx) return FS_ERR_ARG;
+  Ctx& c = ctx->c;
+  if (nrhs < 0) return c.fail(FS_ERR_ARG, "nrhs must be >= 0");
+  if (nrhs == 0) return FS_OK;
+  if (!in || !out) return c.fail(FS_ERR_ARG, "null vector");
+  if (prec < FS_PREC_F64 || prec > FS_PREC_BF16) return c.fail(FS_ERR_ARG, "prec must be 0..3");
+  const int nr = link_compress == 0 ? 18 : link_compress;
+  if (nr != 18 && nr != 12) return c.fail(FS_ERR_ARG, "link_compress must be 18 or 12");
+  if (prec == FS_PREC_F64 && nr != 18) return c.fail(FS_ERR_ARG, "FP64 uses uncompressed links");
+  if (!c.have_gauge) return c.fail(FS_ERR_STATE, "no gauge field set");
+  if (!std::isfinite(m) || !std::isfinite(sigma)) return c.fail(FS_ERR_INPUT, "non-finite mass or shift");
+  const size_t vlen = (size_t)c.g.V * 24;
+  if (!finite_array(in, vlen * nrhs)) return c.fail(FS_ERR_INPUT, "input holds a non-finite value");
+  if (int rc = set_device(c)) return rc;
+  const int N = std::min(nrhs, fs::MAX_TILE);
+  if (int rc = c.ensure_canon(N)) return rc;
+  fs::TileBase* T = c.tile(prec, N, nr);
+  if (!T) return c.fail(FS_ERR_OOM, "device allocation of the tile failed");
+  cudaError_t e = cudaSuccess;
+  for (int k0 = 0; k0 < nrhs && !e; k0 += N) {
+    const int nb = std::min(N, nrhs - k0);
+    for (int j = 0; j < N; j++) {
+      fs::SysState& s = T->st_h[j];
+      memset(&s, 0, sizeof(s));
+      T->vec_h[j] = j < nb ? j : -1;
+      if (j >= nb) continue;
+      const double A = 4.0 + m + sigma;
+      s.A = A;
+      s.cd[fs::C_A] = A;
+      s.cf[fs::C_A] = (float)A;
+      s.flags = fs::FLAG_INIT;
+    }
+    e = cudaMemcpyAsync(T->st_d, T->st_h, sizeof(fs::SysState) * N, cudaMemcpyHostToDevice, c.stream);
+    if (!e) e = cudaMemcpyAsync(T->vec_d, T->vec_h, sizeof(int) * N, cudaMemcpyHostToDevice, c.stream);
+    if (!e) e = cudaMemcpyAsync(c.canon_d, in + k0 * vlen, nb * vlen * sizeof(double), cudaMemcpyHostToDevice,
+                                c.stream);
+    if (!e) e = T->enqueue_dslash(c.canon_d);
+    if (!e) e = cudaMemcpyAsync(out + k0 * vlen, c.canon_d, nb * vlen * sizeof(double), cudaMemcpyDeviceToHost,
+                                c.stream);
+    if (!e) e = cudaStreamSynchronize(c.stream);
+  }
+  if (e) return c.cuda_fail(e, "wilson_dslash");
+  return FS_OK;
+}
+
+int shifted_solve(fs_ctx* ctx, double m, const double* sigma, int nshift, const double* b, int nrhs, double* x,
+                  const fs_solve_params* params, fs_sys_stats* stats) {
+  if (!ctx) return FS_ERR_ARG;
+  Ctx& c = ctx->c;
+  if (nshift < 0 || nrhs < 0) return c.fail(FS_ERR_ARG, "negative count");
+  if (nshift == 0 || nrhs == 0) return FS_OK;
+  if (!sigma || !b || !x) return c.fail(FS_ERR_ARG, "null pointer");
+  if (!c.have_gauge) return c.fail(FS_ERR_STATE, "no gauge field set");
+  if (!std::isfinite(m) || !finite_array(sigma, nshift)) return c.fail(FS_ERR_INPUT, "non-finite mass or shift");
+  const size_t vlen = (size_t)c.g.V * 24;
+  if (!finite_array(b, vlen * nrhs)) return c.fail(FS_ERR_INPUT, "right-hand side holds a non-finite value");
+  for (int j = 0; j < nshift; j++)
+    if (std::fabs(4.0 + m + sigma[j]) < 1e-12) return c.fail(FS_ERR_ARG, "4 + m + sigma must be nonzero");
+  Opts o;
+  const int S = nshift * nrhs;
+  if (int rc = resolve_params(c, params, S, m, o)) return rc;
+  if (int rc = set_device(c)) return rc;
+  const int N = o.tile;
+  if (int rc = c.ensure_canon((size_t)nrhs + N)) return rc;
+  fs::TileBase* T = c.tile(o.so.prec, N, o.so.nr);
+  if (!T) return c.fail(FS_ERR_OOM, "device allocation of the solver tile failed");
+  cudaError_t e = cudaMemcpyAsync(c.canon_d, b, nrhs * vlen * sizeof(double), cudaMemcpyHostToDevice, c.stream);
+  if (e) return c.cuda_fail(e, "upload right-hand sides");
+  int noconv = 0;
+  std::vector<fs::SysSpec> specs(N);
+  for (int i0 = 0; i0 < S; i0 += N) {
+    const int nb = std::min(N, S - i0);
+    for (int i = 0; i < nb; i++) {
+      const int j = (i0 + i) / nrhs, k = (i0 + i) % nrhs;
+      specs[i].sigma = sigma[j];
+      specs[i].rhs_kind = 1;
+      specs[i].vec = k;
+      specs[i].noise = fs::NoiseSpec{};
+    }
+    int rc = fs::solve_tile(&c, T, specs.data(), nb, o.so);
+    if (rc) return rc;
+    for (int i = 0; i < N; i++) T->vec_h[i] = i < nb ? nrhs + i : -1;
+    e = cudaMemcpyAsync(T->vec_d, T->vec_h, sizeof(int) * N, cudaMemcpyHostToDevice, c.stream);
+    if (!e) e = T->enqueue_solution_to_canon(c.canon_d);
+    if (!e) e = cudaMemcpyAsync(x + (size_t)i0 * vlen, c.canon_d + (size_t)nrhs * vlen, nb * vlen * sizeof(double),
+                                cudaMemcpyDeviceToHost, c.stream);
+    if (!e) e = cudaStreamSynchronize(c.stream);
+    if (e) return c.cuda_fail(e, "download solutions");
+    for (int i = 0; i < nb; i++) {
+      if (T->st_h[i].status != fs::SYS_CONVERGED) noconv = 1;
+      if (stats) fill_stats(T->st_h[i], &stats[i0 + i], o.so.verify != 0);
+    }
+  }
+  return noconv ? c.fail(FS_ERR_NOCONV, "some systems reached max_iter") : FS_OK;
+}
+
+int fs_mlmc_num_solves(const fs_mlmc_params* p) {
+  if (!p || p->nlev < 1 || !p->n_samples) return -1;
+  long long n = 0;
+  for (int l = 0; l < p->nlev; l++) n += (long long)p->n_samples[l] * (l + 1 < p->nlev ? 2 : 1);
+  return n > 0x7FFFFFFF ? -1 : (int)n;
+}
+
+int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double* var, double* samples,
+                     fs_sys_stats* stats) {
+  if (!ctx) return FS_ERR_ARG;
+  Ctx& c = ctx->c;
+  if (!P || !trace || !var) return c.fail(FS_ERR_ARG, "null pointer");
+  if (P->nlev < 1 || !P->sigma || !P->n_samples || !P->gamma) return c.fail(FS_ERR_ARG, "bad level parameters");
+  if (!c.have_gauge) return c.fail(FS_ERR_STATE, "no gauge field set");
+  if (P->p < 0 || P->p > 30) return c.fail(FS_ERR_ARG, "p must be in [0, 30]");
+  if (P->estimator < FS_EST_DIFF || P->estimator > FS_EST_PRODUCT) return c.fail(FS_ERR_ARG, "bad estimator");
+  if (!std::isfinite(P->m) || !finite_array(P->sigma, P->nlev) || !finite_array(P->gamma, 32))
+    return c.fail(FS_ERR_INPUT, "non-finite mass, shift or Gamma");
+  const int L = P->nlev - 1;
+  long long total = 0;
+  for (int l = 0; l <= L; l++) {
+    if (P->n_samples[l] < 1) return c.fail(FS_ERR_ARG, "every level needs at least one sample");
+    total += P->n_samples[l];
+    if (l < L && !(P->sigma[l + 1] > P->sigma[l])) return c.fail(FS_ERR_ARG, "shifts must increase");
+    if (std::fabs(4.0 + P->m + P->sigma[l]) < 1e-12) return c.fail(FS_ERR_ARG, "4 + m + sigma must be nonzero");
+  }
+  const int nsolve = fs_mlmc_num_solves(P);
+  if (nsolve < 0) return c.fail(FS_ERR_ARG, "too many solves");
+  Opts o;
+  if (int rc = resolve_params(c, &P->solve, nsolve, P->m, o)) return rc;
+  if (int rc = set_device(c)) return rc;
+  const std::vector<int> plist = {P->p};
+  std::vector<double> csum(total * 2, 0.0);  // per-sample values, level-major
+  std::vector<long long> off(L + 2, 0);
+  for (int l = 0; l <= L; l++) off[l + 1] = off[l] + P->n_samples[l];
+  std::vector<fs::SysState> st(nsolve);
+  std::vector<int> solve_off(L + 2, 0);
+  for (int l = 0; l <= L; l++) solve_off[l + 1] = solve_off[l] + P->n_samples[l] * (l < L ? 2 : 1);
+  int noconv = 0;
+
+  if (P->estimator != FS_EST_PRODUCT) {
+    // rows: DIFF -> one per solve (c_a, c_b), SPLIT_EVEN -> one per level-l sample
+    std::vector<Group> groups;
+    for (int l = 0; l <= L; l++) {
+      for (int s = 0; s < P->n_samples[l]; s++) {
+        Group g;
+        const int si = solve_off[l] + s * (l < L ? 2 : 1);
+        if (l == L) {
+          fs::SysSpec a{P->sigma[L], 0, -1, noise_id(P->seed, P->job, l, s, false)};
+          g.sys = {a};
+          g.stat_index = {si};
+          g.pairs = {{0, 0, 0, si}};
+        } else if (P->estimator == FS_EST_DIFF) {
+          fs::SysSpec a{P->sigma[l], 0, -1, noise_id(P->seed, P->job, l, s, false)};
+          fs::SysSpec b{P->sigma[l + 1], 0, -1, noise_id(P->seed, P->job, l, s, false)};
+          // two independent systems on the same noise: separate groups pack tiles better
+          Group g2;
+          g.sys = {a}; g.stat_index = {si}; g.pairs = {{0, 0, 0, si}};
+          g2.sys = {b}; g2.stat_index = {si + 1}; g2.pairs = {{0, 0, 0, si + 1}};
+          groups.push_back(g);
+          groups.push_back(g2);
+          continue;
+        } else {
+          fs::SysSpec a{P->sigma[l], 0, -1, noise_id(P->seed, P->job, l, s, true)};
+          fs::SysSpec b{P->sigma[l + 1], 0, -1, noise_id(P->seed, P->job, l, s, false)};
+          g.sys = {a, b};
+          g.stat_index = {si, si + 1};
+          g.pairs = {{1, 0, 1, si}};  // y_a^dag Gamma Omega_p x_b, y_a = gamma_5 x_a
+        }
+        groups.push_back(g);
+      }
+    }
+    std::vector<double> res;
+    int rc = run_groups(c, groups, o, P->gamma, plist, nsolve, res, &st, &noconv);
+    if (rc) return rc;
+    for (int l = 0; l <= L; l++) {
+      for (int s = 0; s < P->n_samples[l]; s++) {
+        const int si = solve_off[l] + s * (l < L ? 2 : 1);
+        double re, im;
+        if (l == L) {
+          re = res[(size_t)si * 2]; im = res[(size_t)si * 2 + 1];
+        } else if (P->estimator == FS_EST_DIFF) {
+          re = res[(size_t)si * 2] - res[(size_t)(si + 1) * 2];
+          im = res[(size_t)si * 2 + 1] - res[(size_t)(si + 1) * 2 + 1];
+        } else {
+          const double ds = P->sigma[l + 1] - P->sigma[l];
+          re = ds * res[(size_t)si * 2]; im = ds * res[(size_t)si * 2 + 1];
+        }
+        csum[(off[l] + s) * 2] = re;
+        csum[(off[l] + s) * 2 + 1] = im;
+      }
+    }
+  } else {
+    // PRODUCT: x1 = (D + s_{l+1})^-1 z, then x01 = (D + s_l)^-1 x1, c = (s_{l+1} - s_l) z^dag Gamma Omega_p x01
+    const int N = o.tile;
+    fs::TileBase* T = c.tile(o.so.prec, N, o.so.nr);
+    if (!T) return c.fail(FS_ERR_OOM, "device allocation of the solver tile failed");
+    if (int rc = c.ensure_canon(N)) return rc;
+    for (int l = 0; l < L; l++) {
+      for (int s0 = 0; s0 < P->n_samples[l]; s0 += N) {
+        const int nb = std::min(N, P->n_samples[l] - s0);
+        std::vector<fs::SysSpec> sp(nb);
+        for (int i = 0; i < nb; i++)
+          sp[i] = fs::SysSpec{P->sigma[l + 1], 0, -1, noise_id(P->seed, P->job, l, s0 + i, false)};
+        int rc = fs::solve_tile(&c, T, sp.data(), nb, o.so);
+        if (rc) return rc;
+        for (int i = 0; i < nb; i++) {
+          st[solve_off[l] + (s0 + i) * 2] = T->st_h[i];
+          if (T->st_h[i].status != fs::SYS_CONVERGED) noconv = 1;
+        }
+        for (int i = 0; i < N; i++) T->vec_h[i] = i < nb ? i : -1;
+        cudaError_t e = cudaMemcpyAsync(T->vec_d, T->vec_h, sizeof(int) * N, cudaMemcpyHostToDevice, c.stream);
+        if (!e) e = T->enqueue_solution_to_canon(c.canon_d);
+        if (e) return c.cuda_fail(e, "stage nested right-hand sides");
+        for (int i = 0; i < nb; i++) {
+          sp[i].sigma = P->sigma[l];
+          sp[i].rhs_kind = 1;
+          sp[i].vec = i;
+        }
+        rc = fs::solve_tile(&c, T, sp.data(), nb, o.so);
+        if (rc) return rc;
+        std::vector<fs::ContractPair> pairs(nb);
+        for (int i = 0; i < nb; i++) {
+          pairs[i] = fs::ContractPair{i, i, 0, i};
+          st[solve_off[l] + (s0 + i) * 2 + 1] = T->st_h[i];
+          if (T->st_h[i].status != fs::SYS_CONVERGED) noconv = 1;
+        }
+        std::vector<double> part;
+        rc = fs::contract_tile(&c, T, pairs, P->gamma, plist, part, nb);
+        if (rc) return rc;
+        const double ds = P->sigma[l + 1] - P->sigma[l];
+        for (int i = 0; i < nb; i++) {
+          csum[(off[l] + s0 + i) * 2] = ds * part[(size_t)i * 2];
+          csum[(off[l] + s0 + i) * 2 + 1] = ds * part[(size_t)i * 2 + 1];
+        }
+      }
+    }
+    std::vector<Group> groups;
+    for (int s = 0; s < P->n_samples[L]; s++) {
+      Group g;
+      const int si = solve_off[L] + s;
+      g.sys = {fs::SysSpec{P->sigma[L], 0, -1, noise_id(P->seed, P->job, L, s, false)}};
+      g.stat_index = {si};
+      g.pairs = {{0, 0, 0, s}};
+      groups.push_back(g);
+    }
+    std::vector<double> res;
+    int rc = run_groups(c, groups, o, P->gamma, plist, P->n_samples[L], res, &st, &noconv);
+    if (rc) return rc;
+    for (int s = 0; s < P->n_samples[L]; s++) {
+      csum[(off[L] + s) * 2] = res[(size_t)s * 2];
+      csum[(off[L] + s) * 2 + 1] = res[(size_t)s * 2 + 1];
+    }
+  }
+  // per-level mean and practical variance, Eq. (practical_variance)
+  for (int l = 0; l <= L; l++) {
+    const int n = P->n_samples[l];
+    double sr = 0, si = 0, s2 = 0;
+    for (int s = 0; s < n; s++) {
+      const double re = csum[(off[l] + s) * 2], im = csum[(off[l] + s) * 2 + 1];
+      sr += re; si += im; s2 += re * re + im * im;
+    }
+    const double tr = sr / n, ti = si / n;
+    trace[2 * l] = tr;
+    trace[2 * l + 1] = ti;
+    var[l] = s2 / n - (tr * tr + ti * ti);
+  }
+  if (samples) memcpy(samples, csum.data(), csum.size() * sizeof(double));
+  if (stats)
+    for (int k = 0; k < nsolve; k++) fill_stats(st[k], &stats[k], o.so.verify != 0);
+  return noconv ? c.fail(FS_ERR_NOCONV, "some systems reached max_iter") : FS_OK;
+}
+
+int variance_sample(fs_ctx* ctx, double m, const double* s_hat, int ms, const double* gamma, const int* p, int np,
+                    int Ns, uint64_t seed, uint32_t job, const fs_solve_params* params, double* VL, double* Vbar,
+                    double* a_out, double* b_out, double* iters) {
+  if (!ctx) return FS_ERR_ARG;
+  Ctx& c = ctx->c;
+  if (!s_hat || !gamma || !p || !VL || !Vbar) return c.fail(FS_ERR_ARG, "null pointer");
+  if (ms < 1 || 2 * ms > fs::MAX_TILE) return c.fail(FS_ERR_ARG, "m_shifts must be in [1, 32]");
+  if (np < 1 || np > fs::CONTRACT_MAXP) return c.fail(FS_ERR_ARG, "np must be in [1, 16]");
+  if (Ns < 1) return c.fail(FS_ERR_ARG, "Ns must be >= 1");
+  if (!c.have_gauge) return c.fail(FS_ERR_STATE, "no gauge field set");
+  if (!std::isfinite(m) || !finite_array(s_hat, ms) || !finite_array(gamma, 32))
+    return c.fail(FS_ERR_INPUT, "non-finite mass, shift or Gamma");
+  for (int i = 0; i < ms; i++) {
+    if (i > 0 && !(s_hat[i] > s_hat[i - 1])) return c.fail(FS_ERR_ARG, "sampling shifts must increase");
+    if (std::fabs(4.0 + m + s_hat[i]) < 1e-12) return c.fail(FS_ERR_ARG, "4 + m + sigma must be nonzero");
+  }
+  // displacements are contracted in increasing order; map back to the caller's order
+  std::vector<int> order(np);
+  for (int k = 0; k < np; k++) order[k] = k;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return p[a] < p[b]; });
+  std::vector<int> plist(np);
+  for (int k = 0; k < np; k++) plist[k] = p[order[k]];
+  Opts o;
+  if (int rc = resolve_params(c, params, 2 * ms * Ns, m, o)) return rc;
+  if (int rc = set_device(c)) return rc;
+  o.tile = std::max(2 * ms, (o.tile / (2 * ms)) * (2 * ms));
+  const int per = ms + ms * (ms + 1) / 2;  // contraction rows per noise vector
+  std::vector<Group> groups(Ns);
+  for (int k = 0; k < Ns; k++) {
+    Group& g = groups[k];
+    for (int i = 0; i < ms; i++)
+      g.sys.push_back(fs::SysSpec{s_hat[i], 0, -1, noise_id(seed, job, 0x80000000u, k, false)});
+    for (int i = 0; i < ms; i++)
+      g.sys.push_back(fs::SysSpec{s_hat[i], 0, -1, noise_id(seed, job, 0x80000000u, k, true)});
+    for (int i = 0; i < 2 * ms; i++) g.stat_index.push_back(k * 2 * ms + i);
+    int row = k * per;
+    for (int i = 0; i < ms; i++) g.pairs.push_back({i, i, 0, row++});               // a_i
+    for (int i = 0; i < ms; i++)
+      for (int j = i; j < ms; j++) g.pairs.push_back({j, ms + i, 1, row++});        // b_ij
+  }
+  std::vector<double> res;
+  std::vector<fs::SysState> st((size_t)Ns * 2 * ms);
+  int noconv = 0;
+  int rc = run_groups(c, groups, o, gamma, plist, Ns * per, res, &st, &noconv);
+  if (rc) return rc;
+  auto val = [&](int k, int r, int q, int ri) { return res[(((size_t)k * per + r) * np + q) * 2 + ri]; };
+  for (int qs = 0; qs < np; qs++) {
+    const int q = order[qs];  // caller's index of the qs-th smallest displacement
+    for (int i = 0; i < ms; i++) {
+      double sr = 0, si = 0, s2 = 0;
+      for (int k = 0; k < Ns; k++) {
+        const double re = val(k, i, qs, 0), im = val(k, i, qs, 1);
+        sr += re; si += im; s2 += re * re + im * im;
+        if (a_out) {
+          a_out[(((size_t)k * np + q) * ms + i) * 2] = re;
+          a_out[(((size_t)k * np + q) * ms + i) * 2 + 1] = im;
+        }
+      }
+      sr /= Ns; si /= Ns;
+      VL[(size_t)q * ms + i] = s2 / Ns - (sr * sr + si * si);
+    }
+    int r = ms;
+    for (int i = 0; i < ms; i++) {
+      for (int j = 0; j < ms; j++) {
+        if (j < i) {
+          Vbar[((size_t)q * ms + i) * ms + j] = 0.0;
+          if (b_out)
+            for (int k = 0; k < Ns; k++) {
+              b_out[((((size_t)k * np + q) * ms + i) * ms + j) * 2] = 0.0;
+              b_out[((((size_t)k * np + q) * ms + i) * ms + j) * 2 + 1] = 0.0;
+            }
+          continue;
+        }
+        double sr = 0, si = 0, s2 = 0;
+        for (int k = 0; k < Ns; k++) {
+          const double re = val(k, r, qs, 0), im = val(k, r, qs, 1);
+          sr += re; si += im; s2 += re * re + im * im;
+          if (b_out) {
+            b_out[((((size_t)k * np + q) * ms + i) * ms + j) * 2] = re;
+            b_out[((((size_t)k * np + q) * ms + i) * ms + j) * 2 + 1] = im;
+          }
+        }
+        sr /= Ns; si /= Ns;
+        Vbar[((size_t)q * ms + i) * ms + j] = s2 / Ns - (sr * sr + si * si);
+        r++;
+      }
+    }
+  }
+  if (iters) {
+    for (int i = 0; i < ms; i++) {
+      double sum = 0;
+      for (int k = 0; k < Ns; k++) sum += st[(size_t)k * 2 * ms + i].iters + st[(size_t)k * 2 * ms + ms + i].iters;
+      iters[i] = sum / (2.0 * Ns);
+    }
+  }
+  return noconv ? c.fail(FS_ERR_NOCONV, "some systems reached max_iter") : FS_OK;
+}
+
+int fs_noise_codes(fs_ctx* ctx, uint64_t seed, uint32_t job, uint32_t level, uint32_t sample, uint8_t* codes) {
+  if (!ctx) return FS_ERR_ARG;
+  Ctx& c = ctx->c;
+  if (!codes) return c.fail(FS_ERR_ARG, "null output");
+  if (int rc = set_device(c)) return rc;
+  const size_t n = (size_t)c.g.V * 12;
+  uint8_t* d = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&d, n, c.stream);
+  if (!e) e = fs::launch_noise_codes(d, noise_id(seed, job, level, sample, false), c.g.V, c.stream);
+  if (!e) e = cudaMemcpyAsync(codes, d, n, cudaMemcpyDeviceToHost, c.stream);
+  if (d) cudaFreeAsync(d, c.stream);
+  if (!e) e = cudaStreamSynchronize(c.stream);
+  return e ? c.cuda_fail(e, "fs_noise_codes") : FS_OK;
+}
+
+int fs_profile_enable(fs_ctx* ctx, int enable) {
+  if (!ctx) return FS_ERR_ARG;
+  Ctx& c = ctx->c;
+  if (int rc = set_device(c)) return rc;
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e) return c.cuda_fail(e, "fs_profile_enable");
+  for (auto& ev : c.prof.pending) c.prof.pool.push_back(ev);
+  c.prof.pending.clear();
+  c.prof.launches = 0;
+  c.prof.ms = 0;
+  c.prof.bytes = 0;
+  c.prof.pending_bytes = 0;
+  if (!c.prof.work_d) {
+    e = cudaMalloc(&c.prof.work_d, 12 * sizeof(unsigned long long));
+    if (e) return c.cuda_fail(e, "profile counters");
+  }
+  e = cudaMemset(c.prof.work_d, 0, 12 * sizeof(unsigned long long));
+  if (e) return c.cuda_fail(e, "profile counters");
+  c.prof.enabled = enable != 0;
+  return FS_OK;
+}
+
+int fs_profile_read(fs_ctx* ctx, long long* launches, double* total_ms, double* bytes) {
+  if (!ctx) return FS_ERR_ARG;
+  Ctx& c = ctx->c;
+  if (int rc = set_device(c)) return rc;
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e) return c.cuda_fail(e, "fs_profile_read");
+  for (auto& ev : c.prof.pending) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) c.prof.ms += ms;
+    c.prof.pool.push_back(ev);
+  }
+  c.prof.pending.clear();
+  unsigned long long w[12] = {0};
+  if (c.prof.work_d) {
+    e = cudaMemcpy(w, c.prof.work_d, sizeof(w), cudaMemcpyDeviceToHost);
+    if (e) return c.cuda_fail(e, "profile counters");
+  }
+  const double real_bytes[4] = {8.0, 4.0, 2.0, 2.0};
+  double b = c.prof.pending_bytes;
+  for (int pr = 0; pr < 4; pr++)
+    for (int k = 0; k < 3; k++) b += (double)w[pr * 3 + k] * (48.0 + 24.0 * k) * real_bytes[pr];
+  if (launches) *launches = c.prof.launches;
+  if (total_ms) *total_ms = c.prof.ms;
+  if (bytes) *bytes = b;
+  return FS_OK;
+}
+
+}  // extern "C"

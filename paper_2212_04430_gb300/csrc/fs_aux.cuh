@@ -1,0 +1,287 @@
+// Z4 noise on the device, canonical <-> even-odd layout conversion, gauge packing,
+// and the Gamma Omega_p contraction kernels.
+#pragma once
+
+#include "fs_hop.cuh"
+
+namespace fs {
+
+// ---- Philox4x32-10 (Salmon et al., SC'11), written from its definition ----
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    if (r > 0) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// Noise source of one tile slot: z(x, s, c) = i^k, k = (Philox(x, sample, level, job; seed).x >> 2(3s+c)) & 3.
+struct NoiseSpec {
+  uint32_t key0, key1, job, level, sample;
+  uint32_t flags;  // NOISE_* bits
+};
+enum { NOISE_G5 = 1, NOISE_VALID = 2, NOISE_RHS = 4 };  // gamma_5 z ; has a noise identity ; z is the rhs
+
+__device__ __forceinline__ void z4_site(const NoiseSpec& n, int lex, double (&z)[24]) {
+  const uint4 o = philox4x32_10(make_uint4((uint32_t)lex, n.sample, n.level, n.job), make_uint2(n.key0, n.key1));
+#pragma unroll
+  for (int j = 0; j < 12; j++) {
+    const uint32_t k = (o.x >> (2 * j)) & 3u;
+    // i^k: 0 -> 1, 1 -> i, 2 -> -1, 3 -> -i
+    double re = (k == 0) ? 1.0 : ((k == 2) ? -1.0 : 0.0);
+    double im = (k == 1) ? 1.0 : ((k == 3) ? -1.0 : 0.0);
+    if ((n.flags & NOISE_G5) && j >= 6) { re = -re; im = -im; }
+    z[2 * j] = re;
+    z[2 * j + 1] = im;
+  }
+}
+
+#ifdef FS_ENGINE_KERNELS
+// z for slots flagged INIT with a noise source, both parities (FP64 e/o tile fields).
+__global__ void __launch_bounds__(256) noise_kernel(double* z_e, double* z_o, const NoiseSpec* spec,
+                                                    const SysState* st, Geom g, Shape sh) {
+  const int lsys = threadIdx.x % sh.NB, lsite = threadIdx.x / sh.NB;
+  const int sys = blockIdx.y * sh.NB + lsys;
+  if (sys >= sh.N || !(st[sys].flags & FLAG_INIT) || !(spec[sys].flags & NOISE_RHS)) return;
+  const NoiseSpec n = spec[sys];
+  for (int chunk = blockIdx.x; chunk < 2 * sh.nchunk; chunk += gridDim.x) {
+    const int par = chunk >= sh.nchunk ? 1 : 0;
+    const int site = (chunk - par * sh.nchunk) * sh.SB + lsite;
+    if (site >= g.Vh) continue;
+    int x[4];
+    cb_coords(g, par, site, x);
+    double z[24];
+    z4_site(n, lex_index(g, x), z);
+    make_field<double>(par ? z_o : z_e, g.Vh, sh.N).store(site, sys, z);
+  }
+}
+
+// Integer Z4 codes of one noise vector in canonical order (bit-exact RNG check).
+__global__ void noise_codes_kernel(uint8_t* codes, NoiseSpec n, int V) {
+  const int lex = blockIdx.x * blockDim.x + threadIdx.x;
+  if (lex >= V) return;
+  const uint4 o = philox4x32_10(make_uint4((uint32_t)lex, n.sample, n.level, n.job), make_uint2(n.key0, n.key1));
+#pragma unroll
+  for (int j = 0; j < 12; j++) codes[(size_t)lex * 12 + j] = (uint8_t)((o.x >> (2 * j)) & 3u);
+}
+#endif  // FS_ENGINE_KERNELS
+
+// canonical FP64 [nvec][V][24]  ->  e/o tile fields of type Ts (slot j <- vector vec[j], -1 skips)
+template <typename Ts>
+__global__ void __launch_bounds__(256) pack_kernel(void* f_e, void* f_o, const double* canon, const int* vec,
+                                                  Geom g, Shape sh) {
+  const int lsys = threadIdx.x % sh.NB, lsite = threadIdx.x / sh.NB;
+  const int sys = blockIdx.y * sh.NB + lsys;
+  if (sys >= sh.N) return;
+  const int vi = vec[sys];
+  if (vi < 0) return;
+  for (int chunk = blockIdx.x; chunk < 2 * sh.nchunk; chunk += gridDim.x) {
+    const int par = chunk >= sh.nchunk ? 1 : 0;
+    const int site = (chunk - par * sh.nchunk) * sh.SB + lsite;
+    if (site >= g.Vh) continue;
+    int x[4];
+    cb_coords(g, par, site, x);
+    const double* src = canon + ((size_t)vi * g.V + lex_index(g, x)) * 24;
+    double v[24];
+#pragma unroll
+    for (int k = 0; k < 24; k += 2) {
+      const double2 w = *reinterpret_cast<const double2*>(src + k);
+      v[k] = w.x; v[k + 1] = w.y;
+    }
+    make_field<Ts>(par ? f_o : f_e, g.Vh, sh.N).store(site, sys, v);
+  }
+}
+
+template <typename Ts>
+__global__ void __launch_bounds__(256) unpack_kernel(double* canon, const void* f_e, const void* f_o,
+                                                    const int* vec, Geom g, Shape sh) {
+  const int lsys = threadIdx.x % sh.NB, lsite = threadIdx.x / sh.NB;
+  const int sys = blockIdx.y * sh.NB + lsys;
+  if (sys >= sh.N) return;
+  const int vi = vec[sys];
+  if (vi < 0) return;
+  for (int chunk = blockIdx.x; chunk < 2 * sh.nchunk; chunk += gridDim.x) {
+    const int par = chunk >= sh.nchunk ? 1 : 0;
+    const int site = (chunk - par * sh.nchunk) * sh.SB + lsite;
+    if (site >= g.Vh) continue;
+    int x[4];
+    cb_coords(g, par, site, x);
+    double v[24];
+    make_field<Ts>(const_cast<void*>(par ? f_o : f_e), g.Vh, sh.N).load(site, sys, v);
+    double* dst = canon + ((size_t)vi * g.V + lex_index(g, x)) * 24;
+#pragma unroll
+    for (int k = 0; k < 24; k += 2) *reinterpret_cast<double2*>(dst + k) = make_double2(v[k], v[k + 1]);
+  }
+}
+
+// canonical FP64 links [4][V][18] -> [parity][mu][Vh][RP] of type Tg, NR = 18 or 12 stored reals
+template <typename Tg, int NR>
+__global__ void gauge_pack_kernel(void* out, const double* canon, Geom g) {
+  constexpr int RP = link_pad<Tg>(NR);
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 8 * g.Vh) return;
+  const int site = idx % g.Vh;
+  const int pm = idx / g.Vh;  // parity * 4 + mu
+  const int par = pm / 4, mu = pm % 4;
+  int x[4];
+  cb_coords(g, par, site, x);
+  const double* src = canon + ((size_t)mu * g.V + lex_index(g, x)) * 18;
+  Tg* dst = reinterpret_cast<Tg*>(out) + ((size_t)pm * g.Vh + site) * RP;
+  constexpr int VW = Store<Tg>::VW;
+  double tmp[RP];
+#pragma unroll
+  for (int k = 0; k < RP; k++) tmp[k] = k < NR ? src[k] : 0.0;
+#pragma unroll
+  for (int c = 0; c < RP / VW; c++) store_vec<Tg, double>(dst + c * VW, tmp + c * VW);
+}
+
+// ---- contraction: c_p = sum_x L(x)^dag Gamma W(x, x + p z) R(x + p z) ----------
+// Walked from the right vector's site x': psi_0 = R(x'), psi_{q+1} = U_z(x' - (q+1) z) psi_q,
+// so psi_q = W(x' - q z, x') R(x') and c_q += L(x' - q z)^dag Gamma psi_q.
+struct ContractPair {
+  int right;      // slot holding the right vector (solution)
+  int left;       // slot of the left vector
+  int left_kind;  // 0: noise of slot `left` ; 1: gamma_5 * solution of slot `left`
+  int out;        // output row
+};
+
+struct ContractArgs {
+  const double* x_e;
+  const double* x_o;
+  const double* gauge64;  // FP64 links, 18 reals per link
+  const NoiseSpec* spec;
+  const ContractPair* pairs;
+  double* partial;        // [npairs][np][2][nblk]
+  double gamma[32];       // Gamma, 4x4 complex, row major
+  Geom g;
+  int N;
+  int pmask;              // bit q set: displacement q requested
+  int pmax;
+  int np;
+  int nblk;
+};
+
+constexpr int CONTRACT_MAXP = 16;
+
+#ifdef FS_ENGINE_KERNELS
+__global__ void __launch_bounds__(256) contract_kernel(ContractArgs a) {
+  __shared__ double sm[256 * 2];
+  const ContractPair pr = a.pairs[blockIdx.y];
+  const Geom g = a.g;
+  const int fs = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[CONTRACT_MAXP][2];
+#pragma unroll
+  for (int q = 0; q < CONTRACT_MAXP; q++) { acc[q][0] = 0; acc[q][1] = 0; }
+  if (fs < 2 * g.Vh) {
+    const int par = fs >= g.Vh ? 1 : 0;
+    const int site = fs - par * g.Vh;
+    int x[4];
+    cb_coords(g, par, site, x);
+    double psi[24];
+    make_field<double>(const_cast<double*>(par ? a.x_o : a.x_e), g.Vh, a.N).load(site, pr.right, psi);
+    int qi = 0;
+    for (int q = 0; q <= a.pmax; q++) {
+      int y[4] = {x[0], x[1], x[2], x[3]};
+      y[2] = ((x[2] - q) % g.L[2] + g.L[2]) % g.L[2];
+      if ((a.pmask >> q) & 1) {
+        double lv[24];
+        const int ypar = (y[0] + y[1] + y[2] + y[3]) & 1;
+        if (pr.left_kind == 0) {
+          z4_site(a.spec[pr.left], lex_index(g, y), lv);
+        } else {
+          make_field<double>(const_cast<double*>(ypar ? a.x_o : a.x_e), g.Vh, a.N)
+              .load(cb_index(g, y), pr.left, lv);
+#pragma unroll
+          for (int k = 12; k < 24; k++) lv[k] = -lv[k];
+        }
+        // L^dag Gamma psi
+        double cr = 0, ci = 0;
+#pragma unroll
+        for (int s = 0; s < 4; s++) {
+#pragma unroll
+          for (int c = 0; c < 3; c++) {
+            double gr = 0, gi = 0;
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+              const double Gr = a.gamma[(s * 4 + t) * 2], Gi = a.gamma[(s * 4 + t) * 2 + 1];
+              const double pr_ = psi[t * 6 + c * 2], pi_ = psi[t * 6 + c * 2 + 1];
+              gr += Gr * pr_ - Gi * pi_;
+              gi += Gr * pi_ + Gi * pr_;
+            }
+            const double lr = lv[s * 6 + c * 2], li = lv[s * 6 + c * 2 + 1];
+            cr += lr * gr + li * gi;
+            ci += lr * gi - li * gr;
+          }
+        }
+        acc[qi][0] = cr;
+        acc[qi][1] = ci;
+        qi++;
+      }
+      if (q < a.pmax) {
+        // psi <- U_z(x - (q+1) z) psi
+        int w[4] = {x[0], x[1], x[2], x[3]};
+        w[2] = ((x[2] - q - 1) % g.L[2] + g.L[2]) % g.L[2];
+        const int wpar = (w[0] + w[1] + w[2] + w[3]) & 1;
+        const double* lk = a.gauge64 + ((size_t)(wpar * 4 + 2) * g.Vh + cb_index(g, w)) * 18;
+        double u[18];
+#pragma unroll
+        for (int k = 0; k < 18; k++) u[k] = lk[k];
+        double np_[24];
+#pragma unroll
+        for (int s = 0; s < 4; s++) su3_mul<false, double>(u, psi + s * 6, np_ + s * 6);
+#pragma unroll
+        for (int k = 0; k < 24; k++) psi[k] = np_[k];
+      }
+    }
+  }
+  // fixed-shape block reduction per requested displacement
+  for (int qi = 0; qi < a.np; qi++) {
+    sm[threadIdx.x * 2] = acc[qi][0];
+    sm[threadIdx.x * 2 + 1] = acc[qi][1];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) {
+        sm[threadIdx.x * 2] += sm[(threadIdx.x + w) * 2];
+        sm[threadIdx.x * 2 + 1] += sm[(threadIdx.x + w) * 2 + 1];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const size_t base = (((size_t)blockIdx.y * a.np + qi) * 2) * a.nblk + blockIdx.x;
+      a.partial[base] = sm[0];
+      a.partial[base + a.nblk] = sm[1];
+    }
+    __syncthreads();
+  }
+}
+
+// result[pair.out][qi] = sum over blocks, fixed order
+__global__ void __launch_bounds__(256) contract_finalize(const double* partial, const ContractPair* pairs,
+                                                         double* result, int np, int nblk) {
+  __shared__ double sm[256 * 2];
+  const int pi = blockIdx.x / np, qi = blockIdx.x % np;
+  const size_t base = (((size_t)pi * np + qi) * 2) * nblk;
+  double r = 0, im = 0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) { r += partial[base + b]; im += partial[base + nblk + b]; }
+  sm[threadIdx.x * 2] = r;
+  sm[threadIdx.x * 2 + 1] = im;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sm[threadIdx.x * 2] += sm[(threadIdx.x + w) * 2];
+      sm[threadIdx.x * 2 + 1] += sm[(threadIdx.x + w) * 2 + 1];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int row = pairs[pi].out;
+    result[((size_t)row * np + qi) * 2] = sm[0];
+    result[((size_t)row * np + qi) * 2 + 1] = sm[1];
+  }
+}
+#endif  // FS_ENGINE_KERNELS
+
+}  // namespace fs

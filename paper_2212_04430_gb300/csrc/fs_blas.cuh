@@ -1,0 +1,379 @@
+// Per-site BiCGStab vector updates over a tile of systems, the per-system
+// finalize kernels that turn group partials into the BiCGStab scalars, and the
+// reliable-update and initialisation steps.
+//
+// Mixed precision: vectors r, rhat, p, v, s, t live in the storage type Ts and
+// are combined in Tm (FP32 for FP32/FP16/BF16 storage); the iterate x is split
+// into x_hi (FP64) + x_lo / scale (Tx). A reliable update folds x_lo into x_hi,
+// recomputes r_hi = bhat - M x_hi entirely in FP64 and restarts the sloppy
+// residual from it (the search direction p is kept).
+#pragma once
+
+#include "fs_hop.cuh"
+
+namespace fs {
+
+enum BlasOp {
+  OP_P = 0,       // p = r + beta (p - omega v)
+  OP_S = 1,       // s = r - alpha v
+  OP_XR = 2,      // x_lo += alpha p + omega s ; r = s - omega t ; <rhat, r>, ||r||^2
+  OP_ACCX = 3,    // x_hi += x_lo / scale ; x_lo = 0
+  OP_ZEROX = 4,   // x_hi = 0 ; x_lo = 0
+  OP_SETR = 5,    // r = scale * src ; on restart/init rhat = r, p = v = 0 ; <rhat, r>, ||r||^2
+  OP_NORM64 = 6,  // ||src||^2 of an FP64 field
+};
+
+struct BlasArgs {
+  void* x_lo;
+  void* r;
+  void* rhat;
+  void* p;
+  void* v;
+  void* s;
+  void* t;
+  double* x_hi;
+  const double* src;
+  const SysState* st;
+  double* partial;
+  const int* gate;
+  int Vh;
+  Shape sh;
+  int mask;
+};
+
+template <typename Tm>
+__device__ __forceinline__ void cmul_acc(Tm (&o)[24], const Tm (&a)[24], Tm cr, Tm ci) {
+  // o += (cr + i ci) * a
+#pragma unroll
+  for (int k = 0; k < 24; k += 2) {
+    o[k] += cr * a[k] - ci * a[k + 1];
+    o[k + 1] += cr * a[k + 1] + ci * a[k];
+  }
+}
+
+template <typename Ts, typename Tx, typename Tm, int OP>
+__global__ void __launch_bounds__(256) blas_kernel(BlasArgs a) {
+  if (a.gate != nullptr && *a.gate == 0) return;
+  constexpr int K = (OP == OP_XR || OP == OP_SETR) ? 3 : (OP == OP_NORM64 ? 1 : 0);
+  __shared__ double smem[256 * (K > 0 ? K : 1)];
+  const Shape sh = a.sh;
+  const int Vh = a.Vh;
+  const int lsys = threadIdx.x % sh.NB;
+  const int lsite = threadIdx.x / sh.NB;
+  const int sys = blockIdx.y * sh.NB + lsys;
+  const bool sel = sys < sh.N && selected(a.st, sys, a.mask);
+  Tm c0r = 0, c0i = 0, c1r = 0, c1i = 0;
+  bool reset = false;
+  if (sel) {
+    const SysState& s = a.st[sys];
+    if (OP == OP_P) { c0r = coef<Tm>(s, C_BETA); c0i = coef<Tm>(s, C_BETA + 1);
+                      c1r = coef<Tm>(s, C_OMEGA); c1i = coef<Tm>(s, C_OMEGA + 1); }
+    if (OP == OP_S) { c0r = coef<Tm>(s, C_ALPHA); c0i = coef<Tm>(s, C_ALPHA + 1); }
+    if (OP == OP_XR) { c0r = coef<Tm>(s, C_ALPHA); c0i = coef<Tm>(s, C_ALPHA + 1);
+                       c1r = coef<Tm>(s, C_OMEGA); c1i = coef<Tm>(s, C_OMEGA + 1); }
+    if (OP == OP_SETR) reset = (s.flags & (FLAG_RESTART | FLAG_INIT)) != 0;
+  }
+  const Field<Ts> r = make_field<Ts>(a.r, Vh, sh.N);
+  const Field<Ts> rh = make_field<Ts>(a.rhat, Vh, sh.N);
+  const Field<Ts> p = make_field<Ts>(a.p, Vh, sh.N);
+  const Field<Ts> v = make_field<Ts>(a.v, Vh, sh.N);
+  const Field<Ts> s = make_field<Ts>(a.s, Vh, sh.N);
+  const Field<Ts> t = make_field<Ts>(a.t, Vh, sh.N);
+  const Field<Tx> xl = make_field<Tx>(a.x_lo, Vh, sh.N);
+  const Field<double> xh = make_field<double>(a.x_hi, Vh, sh.N);
+  const Field<double> src = make_field<double>(const_cast<double*>(a.src), Vh, sh.N);
+
+  for (int chunk = blockIdx.x; chunk < sh.nchunk; chunk += gridDim.x) {
+    const int site = chunk * sh.SB + lsite;
+    const bool act = sel && site < Vh;
+    double dv[K > 0 ? K : 1];
+#pragma unroll
+    for (int k = 0; k < (K > 0 ? K : 1); k++) dv[k] = 0.0;
+    if (act) {
+      if constexpr (OP == OP_P) {
+        Tm rv[24], pv[24], vv[24];
+        r.load(site, sys, rv); p.load(site, sys, pv); v.load(site, sys, vv);
+        Tm w[24];
+#pragma unroll
+        for (int k = 0; k < 24; k++) w[k] = pv[k];
+        cmul_acc(w, vv, -c1r, -c1i);  // p - omega v
+        Tm o[24];
+#pragma unroll
+        for (int k = 0; k < 24; k++) o[k] = rv[k];
+        cmul_acc(o, w, c0r, c0i);
+        p.store(site, sys, o);
+      } else if constexpr (OP == OP_S) {
+        Tm rv[24], vv[24];
+        r.load(site, sys, rv); v.load(site, sys, vv);
+        cmul_acc(rv, vv, -c0r, -c0i);
+        s.store(site, sys, rv);
+      } else if constexpr (OP == OP_XR) {
+        Tm xv[24], pv[24], sv[24], tv[24], hv[24];
+        xl.load(site, sys, xv); p.load(site, sys, pv); s.load(site, sys, sv);
+        t.load(site, sys, tv); rh.load(site, sys, hv);
+        cmul_acc(xv, pv, c0r, c0i);
+        cmul_acc(xv, sv, c1r, c1i);
+        xl.store(site, sys, xv);
+        cmul_acc(sv, tv, -c1r, -c1i);  // r = s - omega t
+        r.store(site, sys, sv);
+        Tm dr = 0, di = 0, nn = 0;
+#pragma unroll
+        for (int k = 0; k < 24; k += 2) {
+          dr += hv[k] * sv[k] + hv[k + 1] * sv[k + 1];
+          di += hv[k] * sv[k + 1] - hv[k + 1] * sv[k];
+          nn += sv[k] * sv[k] + sv[k + 1] * sv[k + 1];
+        }
+        dv[0] = (double)dr; dv[1] = (double)di; dv[2] = (double)nn;
+      } else if constexpr (OP == OP_ACCX) {
+        // on a breakdown the sloppy correction is discarded, never folded into x_hi
+        const bool keep = !(a.st[sys].flags & FLAG_RESTART);
+        const double isc = a.st[sys].cd[C_INVSCALE];
+        double hv[24], lv[24];
+        xh.load(site, sys, hv); xl.load(site, sys, lv);
+#pragma unroll
+        for (int k = 0; k < 24; k++) { if (keep) hv[k] += isc * lv[k]; lv[k] = 0.0; }
+        xh.store(site, sys, hv); xl.store(site, sys, lv);
+      } else if constexpr (OP == OP_ZEROX) {
+        double z[24];
+#pragma unroll
+        for (int k = 0; k < 24; k++) z[k] = 0.0;
+        xh.store(site, sys, z); xl.store(site, sys, z);
+      } else if constexpr (OP == OP_SETR) {
+        const double sc = a.st[sys].cd[C_SCALE];
+        double sv[24];
+        src.load(site, sys, sv);
+        Tm o[24];
+#pragma unroll
+        for (int k = 0; k < 24; k++) o[k] = (Tm)(sc * sv[k]);
+        r.store(site, sys, o);
+        // re-read what was stored so the dots see the rounded vector
+        Tm ov[24];
+        r.load(site, sys, ov);
+        Tm hv[24];
+        if (reset) {
+          rh.store(site, sys, o);
+#pragma unroll
+          for (int k = 0; k < 24; k++) hv[k] = ov[k];
+          Tm z[24];
+#pragma unroll
+          for (int k = 0; k < 24; k++) z[k] = 0;
+          p.store(site, sys, z);
+          v.store(site, sys, z);
+        } else {
+          rh.load(site, sys, hv);
+        }
+        Tm dr = 0, di = 0, nn = 0;
+#pragma unroll
+        for (int k = 0; k < 24; k += 2) {
+          dr += hv[k] * ov[k] + hv[k + 1] * ov[k + 1];
+          di += hv[k] * ov[k + 1] - hv[k + 1] * ov[k];
+          nn += ov[k] * ov[k] + ov[k + 1] * ov[k + 1];
+        }
+        dv[0] = (double)dr; dv[1] = (double)di; dv[2] = (double)nn;
+      } else if constexpr (OP == OP_NORM64) {
+        double sv[24];
+        src.load(site, sys, sv);
+        double nn = 0;
+#pragma unroll
+        for (int k = 0; k < 24; k++) nn += sv[k] * sv[k];
+        dv[0] = nn;
+      }
+    }
+    if constexpr (K > 0) {
+      group_partials<K>(dv, lsite, lsys, blockIdx.y * sh.NB, sh, Vh, chunk, smem, a.partial);
+    }
+  }
+}
+
+// ---- finalize: one block per system sums its group partials in fixed order ----
+enum FinOp { FIN_ALPHA = 0, FIN_OMEGA = 1, FIN_RHO = 2, FIN_TRUE = 3, FIN_UPDATE = 4, FIN_INIT = 5,
+             FIN_NORM = 6, FIN_VERIFY = 7 };
+
+struct FinArgs {
+  SysState* st;
+  const double* pa;  // partials [N][K][ngroups]
+  const double* pb;
+  const double* pc;
+  int* gate;
+  int N;
+  int ngroups;
+  int mask;
+  double target;     // rms target of the scaled residual entries
+  double nreal;      // 24 * Vh
+  int max_restarts;
+};
+
+template <int K>
+__device__ __forceinline__ void fin_sum(const double* part, int ngroups, int sys, double (&out)[K],
+                                        double* sm) {
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; k++) acc[k] = 0.0;
+  for (int gidx = threadIdx.x; gidx < ngroups; gidx += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < K; k++) acc[k] += part[((size_t)sys * K + k) * ngroups + gidx];
+  }
+#pragma unroll
+  for (int k = 0; k < K; k++) sm[threadIdx.x * K + k] = acc[k];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+#pragma unroll
+      for (int k = 0; k < K; k++) sm[threadIdx.x * K + k] += sm[(threadIdx.x + w) * K + k];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < K; k++) out[k] = sm[k];
+  __syncthreads();
+}
+
+__device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi, double& cr, double& ci) {
+  const double d = br * br + bi * bi;
+  cr = (ar * br + ai * bi) / d;
+  ci = (ai * br - ar * bi) / d;
+}
+
+__device__ __forceinline__ void set_coef(SysState& s, int k, double val) {
+  s.cd[k] = val;
+  s.cf[k] = (float)val;
+}
+
+__device__ __forceinline__ void set_beta(SysState& s) {
+  // beta = (rho / rho_old) (alpha / omega)
+  double q1r, q1i, q2r, q2i;
+  if (s.omega[0] == 0.0 && s.omega[1] == 0.0) {
+    set_coef(s, C_BETA, 0.0); set_coef(s, C_BETA + 1, 0.0);
+    return;
+  }
+  cdiv(s.rho[0], s.rho[1], s.rho_old[0], s.rho_old[1], q1r, q1i);
+  cdiv(s.alpha[0], s.alpha[1], s.omega[0], s.omega[1], q2r, q2i);
+  set_coef(s, C_BETA, q1r * q2r - q1i * q2i);
+  set_coef(s, C_BETA + 1, q1r * q2i + q1i * q2r);
+}
+
+#ifdef FS_ENGINE_KERNELS
+__global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
+  __shared__ double sm[256 * 3];
+  const int sys = blockIdx.x;
+  if (op == FIN_UPDATE && sys == 0 && threadIdx.x == 0 && a.gate) {
+    // every gated update kernel of this iteration has run (stream order); re-arm
+    *a.gate = 0;
+  }
+  if (sys >= a.N || !selected(a.st, sys, a.mask)) return;
+  SysState& s = a.st[sys];
+  if (op == FIN_ALPHA) {
+    double rv[2];
+    fin_sum<2>(a.pa, a.ngroups, sys, rv, sm);
+    if (threadIdx.x == 0) {
+      double ar = 0, ai = 0;
+      if (rv[0] == 0.0 && rv[1] == 0.0) {
+        s.flags |= FLAG_UPDATE | FLAG_RESTART;
+      } else {
+        cdiv(s.rho[0], s.rho[1], rv[0], rv[1], ar, ai);
+        if (!isfinite(ar) || !isfinite(ai)) { ar = ai = 0; s.flags |= FLAG_UPDATE | FLAG_RESTART; }
+      }
+      if ((s.flags & FLAG_RESTART) && a.gate) atomicExch(a.gate, 1);
+      s.alpha[0] = ar; s.alpha[1] = ai;
+      set_coef(s, C_ALPHA, ar); set_coef(s, C_ALPHA + 1, ai);
+    }
+  } else if (op == FIN_OMEGA) {
+    double v[3];
+    fin_sum<3>(a.pa, a.ngroups, sys, v, sm);
+    if (threadIdx.x == 0) {
+      double wr = 0, wi = 0;
+      if (v[2] > 0.0 && isfinite(v[2])) { wr = v[0] / v[2]; wi = v[1] / v[2]; }
+      else s.flags |= FLAG_UPDATE | FLAG_RESTART;
+      if ((s.flags & FLAG_RESTART) && a.gate) atomicExch(a.gate, 1);
+      s.omega[0] = wr; s.omega[1] = wi;
+      set_coef(s, C_OMEGA, wr); set_coef(s, C_OMEGA + 1, wi);
+    }
+  } else if (op == FIN_RHO) {
+    double v[3];
+    fin_sum<3>(a.pa, a.ngroups, sys, v, sm);
+    if (threadIdx.x == 0) {
+      s.iters += 1;
+      s.rho_old[0] = s.rho[0]; s.rho_old[1] = s.rho[1];
+      s.rho[0] = v[0]; s.rho[1] = v[1];
+      s.r2 = v[2];
+      set_beta(s);
+      const double isc = s.cd[C_INVSCALE];
+      const double r2hi = v[2] * isc * isc;
+      if (!isfinite(v[2]) || !isfinite(v[0]) || !isfinite(v[1])) s.flags |= FLAG_UPDATE | FLAG_RESTART;
+      if (r2hi <= s.tol2) s.flags |= FLAG_UPDATE;
+      if (v[2] < s.delta2 * s.r2_max) s.flags |= FLAG_UPDATE;
+      if (s.iters >= s.max_iter) s.flags |= FLAG_UPDATE | FLAG_FINAL;
+      if (v[2] > s.r2_max) s.r2_max = v[2];
+      if ((s.flags & FLAG_UPDATE) && a.gate) atomicExch(a.gate, 1);
+    }
+  } else if (op == FIN_TRUE) {
+    double v[1];
+    fin_sum<1>(a.pa, a.ngroups, sys, v, sm);
+    if (threadIdx.x == 0) {
+      s.r2_true = v[0];
+      s.updates += 1;
+      if (v[0] <= s.tol2) {
+        s.status = SYS_CONVERGED;
+        s.flags = 0;
+      } else if ((s.flags & FLAG_FINAL) || !isfinite(v[0]) ||
+                 ((s.flags & FLAG_RESTART) && s.restarts >= a.max_restarts)) {
+        s.status = SYS_NOCONV;
+        s.flags = 0;
+      } else {
+        const double sc = a.target * sqrt(a.nreal / v[0]);
+        set_coef(s, C_SCALE, sc);
+        set_coef(s, C_INVSCALE, 1.0 / sc);
+      }
+    }
+  } else if (op == FIN_UPDATE || op == FIN_INIT) {
+    double v[3];
+    fin_sum<3>(a.pa, a.ngroups, sys, v, sm);
+    if (threadIdx.x == 0) {
+      s.rho[0] = v[0]; s.rho[1] = v[1];
+      s.r2 = v[2];
+      s.r2_max = v[2];
+      if (s.flags & (FLAG_RESTART | FLAG_INIT)) {
+        if (s.flags & FLAG_RESTART) s.restarts += 1;
+        s.rho_old[0] = 1.0; s.rho_old[1] = 0.0;
+        s.alpha[0] = 1.0; s.alpha[1] = 0.0;
+        s.omega[0] = 1.0; s.omega[1] = 0.0;
+        set_coef(s, C_BETA, 0.0); set_coef(s, C_BETA + 1, 0.0);
+        set_coef(s, C_OMEGA, 1.0); set_coef(s, C_OMEGA + 1, 0.0);
+      } else {
+        set_beta(s);
+      }
+      s.flags = 0;
+    }
+  } else if (op == FIN_NORM) {
+    // initial norms: pa = ||bhat||^2, pb = ||z_e||^2, pc = ||z_o||^2
+    double bh[1], ze[1], zo[1];
+    fin_sum<1>(a.pa, a.ngroups, sys, bh, sm);
+    fin_sum<1>(a.pb, a.ngroups, sys, ze, sm);
+    fin_sum<1>(a.pc, a.ngroups, sys, zo, sm);
+    if (threadIdx.x == 0) {
+      s.b2 = ze[0] + zo[0];
+      s.r2_true = bh[0];
+      s.iters = 0; s.updates = 0; s.restarts = 0;
+      if (s.b2 == 0.0 || bh[0] <= s.tol2 * s.b2) {
+        // zero right-hand side (or already solved by x = 0)
+        s.tol2 = s.tol2 * s.b2;
+        s.status = SYS_CONVERGED;
+        s.flags = 0;
+      } else {
+        s.tol2 = s.tol2 * s.b2;  // host stored tol^2; make it absolute
+        s.status = SYS_ACTIVE;
+        const double sc = a.target * sqrt(a.nreal / bh[0]);
+        set_coef(s, C_SCALE, sc);
+        set_coef(s, C_INVSCALE, 1.0 / sc);
+      }
+    }
+  } else if (op == FIN_VERIFY) {
+    double e[1], o[1];
+    fin_sum<1>(a.pa, a.ngroups, sys, e, sm);
+    fin_sum<1>(a.pb, a.ngroups, sys, o, sm);
+    if (threadIdx.x == 0) s.r2_full = e[0] + o[0];
+  }
+}
+#endif  // FS_ENGINE_KERNELS
+
+}  // namespace fs

@@ -1,0 +1,455 @@
+// Engine: context services, the Tile kernel sequences and the batched solve loop.
+#define FS_ENGINE_KERNELS 1
+#include "fs_engine.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace fs {
+
+Shape make_shape(int N, int Vh) {
+  Shape s;
+  s.N = N;
+  int NB = N;
+  if (N > 32) {
+    NB = 1;
+    for (int d = 32; d >= 1; d--)
+      if (N % d == 0) { NB = d; break; }
+  }
+  s.NB = NB;
+  int SB = (256 / NB) / 8 * 8;
+  if (SB < 8) SB = 8;
+  s.SB = SB;
+  s.nchunk = (Vh + SB - 1) / SB;
+  return s;
+}
+
+double* pinned_alloc(size_t bytes) {
+  void* p = nullptr;
+  if (cudaMallocHost(&p, bytes) != cudaSuccess) return nullptr;
+  return (double*)p;
+}
+
+int Ctx::cuda_fail(cudaError_t e, const char* where) {
+  err = std::string(where) + ": " + cudaGetErrorString(e);
+  return 7;  // FS_ERR_CUDA
+}
+
+Launch Ctx::launch_for(const Shape& sh) const {
+  Launch l;
+  l.grid_y = (sh.N + sh.NB - 1) / sh.NB;
+  l.block = sh.SB * sh.NB;
+  const int target = std::max(1, (nsm * 8) / l.grid_y);
+  l.grid_x = std::min(sh.nchunk, target);
+  l.stream = stream;
+  return l;
+}
+
+void* Ctx::gauge_for(int prec, int nr) {
+  if (prec == PREC_F64) return gauge64;
+  const int key = (prec == PREC_BF16 ? PREC_F16 : prec) * 100 + nr;
+  auto it = gauge_lo.find(key);
+  return it == gauge_lo.end() ? nullptr : it->second;
+}
+
+int Ctx::ensure_canon(size_t nvec) {
+  if (nvec <= canon_cap) return 0;
+  if (canon_d) cudaFree(canon_d);
+  canon_d = nullptr;
+  canon_cap = 0;
+  if (cudaMalloc(&canon_d, nvec * (size_t)g.V * 24 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(3, "device allocation of the vector staging buffer failed");
+  }
+  canon_cap = nvec;
+  return 0;
+}
+
+int Ctx::ensure_canon_host(size_t nvec) {
+  if (nvec <= canon_h_cap) return 0;
+  if (canon_h) cudaFreeHost(canon_h);
+  canon_h = pinned_alloc(nvec * (size_t)g.V * 24 * sizeof(double));
+  canon_h_cap = canon_h ? nvec : 0;
+  return canon_h ? 0 : fail(3, "pinned host allocation failed");
+}
+
+size_t Ctx::device_bytes() const {
+  size_t b = extra_bytes + canon_cap * (size_t)g.V * 24 * sizeof(double);
+  for (auto& kv : tiles) b += kv.second->bytes;
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+template <typename Ts>
+class Tile : public TileBase {
+ public:
+  using Tx = typename XOf<Ts>::T;
+  Ctx* c = nullptr;
+  Shape sh{};
+  Launch L{};
+  int ngroups = 0;
+  double *bhat = nullptr, *r_hi = nullptr, *tmp64 = nullptr;
+  void *x_lo = nullptr, *r = nullptr, *rhat = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr,
+       *tmp = nullptr;
+  double *pa = nullptr, *pb = nullptr, *pc = nullptr;
+  int* gate = nullptr;
+  std::vector<void*> owned;
+
+  ~Tile() override {
+    for (void* q : owned) cudaFree(q);
+    if (st_h) cudaFreeHost(st_h);
+    if (spec_h) cudaFreeHost(spec_h);
+    if (vec_h) cudaFreeHost(vec_h);
+  }
+
+  void* dalloc(size_t n) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, n) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    owned.push_back(q);
+    bytes += n;
+    return q;
+  }
+
+  int alloc(Ctx* ctx, int n, int nr_) override {
+    c = ctx;
+    N = n;
+    nr = nr_;
+    sh = make_shape(N, c->g.Vh);
+    L = c->launch_for(sh);
+    ngroups = c->g.Vh / 8;
+    const size_t f64 = (size_t)24 * c->g.Vh * N * sizeof(double);
+    const size_t fts = (size_t)24 * c->g.Vh * N * sizeof(Ts);
+    const size_t ftx = (size_t)24 * c->g.Vh * N * sizeof(Tx);
+    z_e = (double*)dalloc(f64); z_o = (double*)dalloc(f64); bhat = (double*)dalloc(f64);
+    x_hi = (double*)dalloc(f64); x_o = (double*)dalloc(f64); r_hi = (double*)dalloc(f64);
+    x_lo = dalloc(ftx);
+    r = dalloc(fts); rhat = dalloc(fts); p = dalloc(fts); v = dalloc(fts); s = dalloc(fts); t = dalloc(fts);
+    tmp = dalloc(fts);
+    tmp64 = std::is_same<Ts, double>::value ? (double*)tmp : (double*)dalloc(f64);
+    const size_t pbytes = (size_t)N * 3 * ngroups * sizeof(double);
+    pa = (double*)dalloc(pbytes); pb = (double*)dalloc(pbytes); pc = (double*)dalloc(pbytes);
+    gate = (int*)dalloc(sizeof(int));
+    st_d = (SysState*)dalloc(sizeof(SysState) * MAX_TILE);
+    spec_d = (NoiseSpec*)dalloc(sizeof(NoiseSpec) * MAX_TILE);
+    vec_d = (int*)dalloc(sizeof(int) * MAX_TILE);
+    const void* req[] = {z_e, z_o, bhat, x_hi, x_o, r_hi, x_lo, r, rhat, p, v, s, t, tmp, tmp64,
+                         pa, pb, pc, gate, st_d, spec_d, vec_d};
+    for (const void* q : req)
+      if (!q) return 3;
+    if (cudaMallocHost(&st_h, sizeof(SysState) * MAX_TILE) != cudaSuccess) return 3;
+    if (cudaMallocHost(&spec_h, sizeof(NoiseSpec) * MAX_TILE) != cudaSuccess) return 3;
+    if (cudaMallocHost(&vec_h, sizeof(int) * MAX_TILE) != cudaSuccess) return 3;
+    memset(st_h, 0, sizeof(SysState) * MAX_TILE);
+    cudaMemsetAsync(gate, 0, sizeof(int), c->stream);
+    return 0;
+  }
+
+  HopArgs hop(void* out, const void* in, const void* X, const void* Y, const void* R, double* part, int p_out,
+              int mask, bool gated, bool hi) {
+    HopArgs a{};
+    a.out = out; a.in = in; a.X = X; a.Y = Y; a.R = R;
+    a.gauge = hi ? c->gauge64 : c->gauge_for(prec, nr);
+    a.st = st_d; a.partial = part; a.gate = gated ? gate : nullptr; a.work = nullptr;
+    a.g = c->g; a.sh = sh; a.p_out = p_out; a.mask = mask;
+    return a;
+  }
+  BlasArgs blas(int mask, const double* src, double* part, bool gated) {
+    BlasArgs b{};
+    b.x_lo = x_lo; b.r = r; b.rhat = rhat; b.p = p; b.v = v; b.s = s; b.t = t;
+    b.x_hi = x_hi; b.src = src; b.st = st_d; b.partial = part; b.gate = gated ? gate : nullptr;
+    b.Vh = c->g.Vh; b.sh = sh; b.mask = mask;
+    return b;
+  }
+  cudaError_t fin(int op, int mask, const double* a_, const double* b_ = nullptr, const double* c_ = nullptr) {
+    FinArgs f{};
+    f.st = st_d; f.pa = a_; f.pb = b_; f.pc = c_; f.gate = gate;
+    f.N = N; f.ngroups = ngroups; f.mask = mask;
+    f.target = 0.25;  // rms of a scaled residual entry (keeps FP16 away from both range limits)
+    f.nreal = 24.0 * c->g.Vh;
+    f.max_restarts = 8;
+    fin_kernel<<<N, 256, 0, c->stream>>>(f, op);
+    return cudaGetLastError();
+  }
+
+  // Timed hop launch in the inner precision (the kernel the roofline is about).
+  cudaError_t hop_lo(int coef, int dot, const HopArgs& a, int nextra) {
+    HopProfile& pf = c->prof;
+    if (!pf.enabled) return launch_hop<Ts>(coef, dot, nr, a, L);
+    cudaEvent_t e0, e1;
+    if (!pf.pool.empty()) {
+      e0 = pf.pool.back().first; e1 = pf.pool.back().second; pf.pool.pop_back();
+    } else {
+      cudaEventCreate(&e0); cudaEventCreate(&e1);
+    }
+    HopArgs b = a;
+    b.work = pf.work_d + prec * 3 + nextra;
+    cudaEventRecord(e0, c->stream);
+    cudaError_t e = launch_hop<Ts>(coef, dot, nr, b, L);
+    cudaEventRecord(e1, c->stream);
+    pf.pending.push_back({e0, e1});
+    pf.launches += 1;
+    // links: every link once per launch (algorithmic), nr reals each
+    pf.pending_bytes += (double)c->g.Vh * 8.0 * nr * sizeof(typename GaugeOf<Ts>::T);
+    return e;
+  }
+
+  cudaError_t enqueue_rhs_from_canon(const double* canon) override {
+    L.stream = c->stream;
+    return launch_pack<double>(z_e, z_o, canon, vec_d, c->g, sh, L);
+  }
+
+  cudaError_t enqueue_init() override {
+    L.stream = c->stream;
+    cudaError_t e;
+    // bhat_e = z_e - D_eo A^-1 z_o, ||bhat||^2
+    if ((e = launch_hop<double>(COEF_PREP, DOT_NORM, 18, hop(bhat, z_o, z_e, nullptr, nullptr, pa, 0, MASK_INIT,
+                                                              false, true), L))) return e;
+    if ((e = launch_blas<Ts>(OP_NORM64, blas(MASK_INIT, z_e, pb, false), L))) return e;
+    if ((e = launch_blas<Ts>(OP_NORM64, blas(MASK_INIT, z_o, pc, false), L))) return e;
+    if ((e = launch_blas<Ts>(OP_ZEROX, blas(MASK_INIT, nullptr, nullptr, false), L))) return e;
+    if ((e = fin(FIN_NORM, MASK_INIT, pa, pb, pc))) return e;
+    if ((e = launch_blas<Ts>(OP_SETR, blas(MASK_INIT, bhat, pa, false), L))) return e;
+    return fin(FIN_INIT, MASK_INIT, pa);
+  }
+
+  cudaError_t enqueue_iter() override {
+    L.stream = c->stream;
+    cudaError_t e;
+    if ((e = launch_blas<Ts>(OP_P, blas(MASK_ACTIVE, nullptr, nullptr, false), L))) return e;
+    if ((e = hop_lo(COEF_PLAIN, DOT_NONE, hop(tmp, p, nullptr, nullptr, nullptr, nullptr, 1, MASK_ACTIVE, false,
+                                              false), 0))) return e;
+    if ((e = hop_lo(COEF_MHAT, DOT_R, hop(v, tmp, p, nullptr, rhat, pa, 0, MASK_ACTIVE, false, false), 2)))
+      return e;
+    if ((e = fin(FIN_ALPHA, MASK_ACTIVE, pa))) return e;
+    if ((e = launch_blas<Ts>(OP_S, blas(MASK_ACTIVE, nullptr, nullptr, false), L))) return e;
+    if ((e = hop_lo(COEF_PLAIN, DOT_NONE, hop(tmp, s, nullptr, nullptr, nullptr, nullptr, 1, MASK_ACTIVE, false,
+                                              false), 0))) return e;
+    if ((e = hop_lo(COEF_MHAT, DOT_TS, hop(t, tmp, s, nullptr, nullptr, pa, 0, MASK_ACTIVE, false, false), 1)))
+      return e;
+    if ((e = fin(FIN_OMEGA, MASK_ACTIVE, pa))) return e;
+    if ((e = launch_blas<Ts>(OP_XR, blas(MASK_ACTIVE, nullptr, pa, false), L))) return e;
+    if ((e = fin(FIN_RHO, MASK_ACTIVE, pa))) return e;
+    // reliable update (only systems flagged by FIN_RHO; the gated kernels return at once otherwise)
+    if ((e = launch_blas<Ts>(OP_ACCX, blas(MASK_UPDATE, nullptr, nullptr, true), L))) return e;
+    if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
+                                hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, MASK_UPDATE, true, true), L)))
+      return e;
+    if ((e = launch_hop<double>(COEF_TRUERES, DOT_NORM, 18,
+                                hop(r_hi, tmp64, x_hi, bhat, nullptr, pa, 0, MASK_UPDATE, true, true), L)))
+      return e;
+    if ((e = fin(FIN_TRUE, MASK_UPDATE, pa))) return e;
+    if ((e = launch_blas<Ts>(OP_SETR, blas(MASK_UPDATE, r_hi, pa, true), L))) return e;
+    return fin(FIN_UPDATE, MASK_UPDATE, pa);
+  }
+
+  cudaError_t enqueue_recon() override {
+    L.stream = c->stream;
+    // x_o = A^-1 (z_o - D_oe x_e)
+    return launch_hop<double>(COEF_RECON, DOT_NONE, 18,
+                              hop(x_o, x_hi, z_o, nullptr, nullptr, nullptr, 1, MASK_HARVEST, false, true), L);
+  }
+
+  cudaError_t enqueue_verify() override {
+    L.stream = c->stream;
+    cudaError_t e;
+    if ((e = launch_hop<double>(COEF_FULLRES, DOT_NORM, 18,
+                                hop(r_hi, x_o, x_hi, z_e, nullptr, pa, 0, MASK_HARVEST, false, true), L)))
+      return e;
+    if ((e = launch_hop<double>(COEF_FULLRES, DOT_NORM, 18,
+                                hop(tmp64, x_hi, x_o, z_o, nullptr, pb, 1, MASK_HARVEST, false, true), L)))
+      return e;
+    return fin(FIN_VERIFY, MASK_HARVEST, pa, pb);
+  }
+
+  cudaError_t enqueue_dslash(double* canon) override {
+    L.stream = c->stream;
+    // in: canon[vec[j]] -> (p, tmp) ; out = (D + sigma) in -> (v, s) -> canon[vec[j]]
+    cudaError_t e;
+    if ((e = launch_pack<Ts>(p, tmp, canon, vec_d, c->g, sh, L))) return e;
+    const bool f64 = std::is_same<Ts, double>::value;
+    HopArgs he = hop(v, tmp, p, nullptr, nullptr, nullptr, 0, MASK_INIT, false, f64);
+    HopArgs ho = hop(s, p, tmp, nullptr, nullptr, nullptr, 1, MASK_INIT, false, f64);
+    if ((e = hop_lo(COEF_DSLASH, DOT_NONE, he, 1))) return e;
+    if ((e = hop_lo(COEF_DSLASH, DOT_NONE, ho, 1))) return e;
+    return launch_unpack<Ts>(canon, v, s, vec_d, c->g, sh, L);
+  }
+
+  cudaError_t enqueue_solution_to_canon(double* canon) override {
+    L.stream = c->stream;
+    return launch_unpack<double>(canon, x_hi, x_o, vec_d, c->g, sh, L);
+  }
+};
+
+TileBase* Ctx::tile(int prec, int N, int nr) {
+  const long long key = ((long long)prec * 1000 + N) * 100 + nr;
+  auto it = tiles.find(key);
+  if (it != tiles.end()) return it->second.get();
+  std::unique_ptr<TileBase> t;
+  switch (prec) {
+    case PREC_F64: t.reset(new Tile<double>()); break;
+    case PREC_F32: t.reset(new Tile<float>()); break;
+    case PREC_F16: t.reset(new Tile<__half>()); break;
+    case PREC_BF16: t.reset(new Tile<__nv_bfloat16>()); break;
+    default: return nullptr;
+  }
+  t->prec = prec;
+  if (t->alloc(this, N, nr) != 0) {
+    // release other cached tiles and retry once
+    tiles.clear();
+    switch (prec) {
+      case PREC_F64: t.reset(new Tile<double>()); break;
+      case PREC_F32: t.reset(new Tile<float>()); break;
+      case PREC_F16: t.reset(new Tile<__half>()); break;
+      default: t.reset(new Tile<__nv_bfloat16>()); break;
+    }
+    t->prec = prec;
+    if (t->alloc(this, N, nr) != 0) return nullptr;
+  }
+  TileBase* raw = t.get();
+  tiles[key] = std::move(t);
+  return raw;
+}
+
+static void set_coef_h(SysState& s, int k, double v) {
+  s.cd[k] = v;
+  s.cf[k] = (float)v;
+}
+
+int solve_tile(Ctx* c, TileBase* T, const SysSpec* specs, int n, const SolveOpts& o) {
+  if (n > T->N) return c->fail(1, "internal: batch larger than tile");
+  bool any_vec = false, any_noise = false;
+  for (int j = 0; j < T->N; j++) {
+    SysState& s = T->st_h[j];
+    memset(&s, 0, sizeof(SysState));
+    NoiseSpec& ns = T->spec_h[j];
+    memset(&ns, 0, sizeof(NoiseSpec));
+    T->vec_h[j] = -1;
+    if (j >= n) continue;
+    const double A = 4.0 + o.m + specs[j].sigma;
+    s.sigma = specs[j].sigma;
+    s.A = A;
+    s.inv4A = 1.0 / (4.0 * A);
+    set_coef_h(s, C_A, A);
+    set_coef_h(s, C_MINV4A, -1.0 / (4.0 * A));
+    set_coef_h(s, C_INV2A, 1.0 / (2.0 * A));
+    set_coef_h(s, C_INVA, 1.0 / A);
+    set_coef_h(s, C_INV4A, 1.0 / (4.0 * A));
+    set_coef_h(s, C_MINVA, -A);
+    set_coef_h(s, C_SCALE, 1.0);
+    set_coef_h(s, C_INVSCALE, 1.0);
+    s.tol2 = o.tol * o.tol;  // made absolute (x ||z||^2) on the device
+    s.delta2 = o.delta * o.delta;
+    s.max_iter = o.max_iter;
+    s.status = SYS_IDLE;
+    s.flags = FLAG_INIT;
+    ns = specs[j].noise;
+    if (specs[j].rhs_kind == 0) {
+      ns.flags |= NOISE_RHS;
+      any_noise = true;
+    } else {
+      T->vec_h[j] = specs[j].vec;
+      any_vec = true;
+    }
+  }
+  cudaStream_t st = c->stream;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(T->st_d, T->st_h, sizeof(SysState) * T->N, cudaMemcpyHostToDevice, st)))
+    return c->cuda_fail(e, "upload system state");
+  if ((e = cudaMemcpyAsync(T->spec_d, T->spec_h, sizeof(NoiseSpec) * T->N, cudaMemcpyHostToDevice, st)))
+    return c->cuda_fail(e, "upload noise specs");
+  if ((e = cudaMemcpyAsync(T->vec_d, T->vec_h, sizeof(int) * T->N, cudaMemcpyHostToDevice, st)))
+    return c->cuda_fail(e, "upload vector map");
+  const Shape sh = make_shape(T->N, c->g.Vh);
+  Launch L = c->launch_for(sh);
+  if (any_vec && (e = T->enqueue_rhs_from_canon(c->canon_d))) return c->cuda_fail(e, "pack right-hand sides");
+  if (any_noise) {
+    noise_kernel<<<dim3(std::min(2 * sh.nchunk, L.grid_x * 2), L.grid_y), L.block, 0, st>>>(
+        T->z_e, T->z_o, T->spec_d, T->st_d, c->g, sh);
+    if ((e = cudaGetLastError())) return c->cuda_fail(e, "noise kernel");
+  }
+  if ((e = T->enqueue_init())) return c->cuda_fail(e, "solver initialisation");
+
+  const int every = std::max(1, o.check_every);
+  long long guard = 0;
+  const long long guard_max = (long long)o.max_iter * 4 + 64;  // every system stops at max_iter (FLAG_FINAL)
+  while (true) {
+    for (int k = 0; k < every; k++)
+      if ((e = T->enqueue_iter())) return c->cuda_fail(e, "solver iteration");
+    guard += every;
+    if ((e = cudaMemcpyAsync(T->st_h, T->st_d, sizeof(SysState) * T->N, cudaMemcpyDeviceToHost, st)))
+      return c->cuda_fail(e, "download system state");
+    if ((e = cudaStreamSynchronize(st))) return c->cuda_fail(e, "solver iteration");
+    int busy = 0;
+    for (int j = 0; j < n; j++) busy += (T->st_h[j].status == SYS_ACTIVE || (T->st_h[j].flags & FLAG_INIT));
+    if (!busy) break;
+    if (guard > guard_max) return c->fail(6, "solver did not terminate within its iteration bound");
+  }
+  for (int j = 0; j < n; j++) T->st_h[j].flags |= FLAG_HARVEST;
+  if ((e = cudaMemcpyAsync(T->st_d, T->st_h, sizeof(SysState) * T->N, cudaMemcpyHostToDevice, st)))
+    return c->cuda_fail(e, "upload harvest flags");
+  if ((e = T->enqueue_recon())) return c->cuda_fail(e, "reconstruct odd sites");
+  if (o.verify && (e = T->enqueue_verify())) return c->cuda_fail(e, "verify residual");
+  if ((e = cudaMemcpyAsync(T->st_h, T->st_d, sizeof(SysState) * T->N, cudaMemcpyDeviceToHost, st)))
+    return c->cuda_fail(e, "download system state");
+  if ((e = cudaStreamSynchronize(st))) return c->cuda_fail(e, "harvest");
+  return 0;
+}
+
+int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, const double* gamma,
+                  const std::vector<int>& plist, std::vector<double>& result, int rows) {
+  const int np = (int)plist.size();
+  const int npairs = (int)pairs.size();
+  if (npairs == 0) return 0;
+  if (np <= 0 || np > CONTRACT_MAXP) return c->fail(1, "between 1 and 16 displacements are supported");
+  ContractArgs a{};
+  int pmask = 0, pmax = 0;
+  for (int q : plist) {
+    if (q < 0 || q > 30) return c->fail(1, "displacement p must be in [0, 30]");
+    if (pmask & (1 << q)) return c->fail(1, "displacements must be distinct");
+    pmask |= 1 << q;
+    pmax = std::max(pmax, q);
+  }
+  // results come back in increasing p; callers pass plist sorted
+  for (int k = 1; k < np; k++)
+    if (plist[k] <= plist[k - 1]) return c->fail(1, "displacements must be increasing");
+  a.x_e = T->x_hi; a.x_o = T->x_o; a.gauge64 = (const double*)c->gauge64; a.spec = T->spec_d;
+  for (int k = 0; k < 32; k++) a.gamma[k] = gamma[k];
+  a.g = c->g; a.N = T->N; a.pmask = pmask; a.pmax = pmax; a.np = np;
+  a.nblk = (2 * c->g.Vh + 255) / 256;
+  const size_t part_n = (size_t)npairs * np * 2 * a.nblk;
+  const size_t res_n = (size_t)rows * np * 2;
+  const size_t need = part_n * sizeof(double) + res_n * sizeof(double) + npairs * sizeof(ContractPair) + 256;
+  char* buf = nullptr;
+  cudaError_t e;
+  if ((e = cudaMallocAsync((void**)&buf, need, c->stream))) return c->cuda_fail(e, "contraction buffers");
+  double* part = (double*)buf;
+  double* res = part + part_n;
+  ContractPair* pr = (ContractPair*)(res + res_n);
+  a.partial = part;
+  a.pairs = pr;
+  e = cudaMemcpyAsync(pr, pairs.data(), npairs * sizeof(ContractPair), cudaMemcpyHostToDevice, c->stream);
+  if (!e) e = cudaMemsetAsync(res, 0, res_n * sizeof(double), c->stream);
+  if (!e) {
+    contract_kernel<<<dim3(a.nblk, npairs), 256, 0, c->stream>>>(a);
+    e = cudaGetLastError();
+  }
+  if (!e) {
+    contract_finalize<<<npairs * np, 256, 0, c->stream>>>(part, pr, res, np, a.nblk);
+    e = cudaGetLastError();
+  }
+  result.assign(res_n, 0.0);
+  if (!e) e = cudaMemcpyAsync(result.data(), res, res_n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  cudaFreeAsync(buf, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return c->cuda_fail(e, "contraction");
+  return 0;
+}
+
+// entry points used by the API translation unit
+cudaError_t launch_noise_codes(uint8_t* codes, NoiseSpec n, int V, cudaStream_t s) {
+  noise_codes_kernel<<<(V + 255) / 256, 256, 0, s>>>(codes, n, V);
+  return cudaGetLastError();
+}
+
+}  // namespace fs

@@ -1,0 +1,146 @@
+// Host-side engine: the context (device, geometry, gauge copies, stream, buffers)
+// and the Tile, a batch of up to 64 shifted systems solved together by
+// even-odd preconditioned BiCGStab with per-system convergence masks and
+// mixed-precision reliable updates.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "fs_aux.cuh"
+#include "fs_blas.cuh"
+#include "fs_hop.cuh"
+
+namespace fs {
+
+constexpr int MAX_TILE = 64;
+
+// ---- kernel launchers (one translation unit per storage precision) ----
+template <typename Ts> struct GaugeOf { using T = Ts; };
+template <> struct GaugeOf<__nv_bfloat16> { using T = __half; };
+template <typename Ts> struct XOf { using T = float; };
+template <> struct XOf<double> { using T = double; };
+
+struct Launch {
+  int grid_x;
+  int grid_y;
+  int block;
+  cudaStream_t stream;
+};
+
+template <typename Ts> cudaError_t launch_hop(int coef, int dot, int nr, const HopArgs& a, const Launch& l);
+template <typename Ts> cudaError_t launch_blas(int op, const BlasArgs& a, const Launch& l);
+template <typename Ts> cudaError_t launch_pack(void* fe, void* fo, const double* canon, const int* vec,
+                                               const Geom& g, const Shape& sh, const Launch& l);
+template <typename Ts> cudaError_t launch_unpack(double* canon, const void* fe, const void* fo, const int* vec,
+                                                 const Geom& g, const Shape& sh, const Launch& l);
+template <typename Tg> cudaError_t launch_gauge_pack(void* out, const double* canon, const Geom& g, int nr,
+                                                     cudaStream_t s);
+
+Shape make_shape(int N, int Vh);
+
+struct Ctx;
+
+// Profiling of the hopping kernel launches (CUDA events on the context stream).
+struct HopProfile {
+  bool enabled = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
+  long long launches = 0;
+  double ms = 0.0;
+  double bytes = 0.0;
+  double pending_bytes = 0.0;
+  unsigned long long* work_d = nullptr;  // (site, system) pairs per [precision][extra fields read]
+};
+
+class TileBase {
+ public:
+  virtual ~TileBase() {}
+  int N = 0;
+  int nr = 18;
+  int prec = 0;
+  size_t bytes = 0;
+  SysState* st_d = nullptr;
+  SysState* st_h = nullptr;  // pinned mirror
+  NoiseSpec* spec_d = nullptr;
+  NoiseSpec* spec_h = nullptr;
+  int* vec_d = nullptr;      // slot -> canonical vector index (pack / unpack)
+  int* vec_h = nullptr;
+  double* z_e = nullptr;     // full right-hand side (FP64)
+  double* z_o = nullptr;
+  double* x_hi = nullptr;    // solution, even sites (FP64)
+  double* x_o = nullptr;     // solution, odd sites (FP64, after reconstruction)
+  virtual int alloc(Ctx* c, int N, int nr) = 0;
+  virtual cudaError_t enqueue_rhs_from_canon(const double* canon) = 0;  // z <- canon[vec[j]] for INIT slots
+  virtual cudaError_t enqueue_init() = 0;
+  virtual cudaError_t enqueue_iter() = 0;
+  virtual cudaError_t enqueue_recon() = 0;
+  virtual cudaError_t enqueue_verify() = 0;
+  virtual cudaError_t enqueue_solution_to_canon(double* canon) = 0;  // canon[vec[j]] <- x for all j with vec >= 0
+  virtual cudaError_t enqueue_dslash(double* canon) = 0;  // canon[vec[j]] <- (D + sigma_j) canon[vec[j]], INIT slots
+};
+
+struct Ctx {
+  int device = 0;
+  int nsm = 0;
+  Geom g{};
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  bool have_gauge = false;
+  void* gauge64 = nullptr;              // [2][4][Vh][18] doubles
+  std::map<int, void*> gauge_lo;        // key: prec * 100 + nr
+  std::map<long long, std::unique_ptr<TileBase>> tiles;
+  double* canon_d = nullptr;            // staging for canonical vectors
+  size_t canon_cap = 0;                 // in vectors
+  double* canon_h = nullptr;            // pinned host staging
+  size_t canon_h_cap = 0;
+  HopProfile prof;
+  size_t extra_bytes = 0;
+
+  int fail(int code, const std::string& msg) {
+    err = msg;
+    return code;
+  }
+  int cuda_fail(cudaError_t e, const char* where);
+  Launch launch_for(const Shape& sh) const;
+  void* gauge_for(int prec, int nr);    // builds the copy on demand; nullptr on failure
+  TileBase* tile(int prec, int N, int nr);
+  int ensure_canon(size_t nvec);
+  int ensure_canon_host(size_t nvec);
+  size_t device_bytes() const;
+};
+
+// Solve a list of systems in one tile (tile-synchronous: returns when all are done).
+struct SysSpec {
+  double sigma;
+  int rhs_kind;        // 0: Z4 noise, 1: canonical vector vec (device staging)
+  int vec;             // canonical vector index for rhs_kind 1 (also output index)
+  NoiseSpec noise;     // noise identity (used for the right-hand side and contractions)
+};
+
+struct SolveOpts {
+  double m;
+  double tol;
+  int max_iter;
+  int prec;
+  int nr;
+  double delta;
+  int verify;
+  int check_every;
+};
+
+int solve_tile(Ctx* c, TileBase* T, const SysSpec* specs, int n, const SolveOpts& o);
+
+// Contractions over the solutions held in a tile.
+int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, const double* gamma,
+                  const std::vector<int>& plist, std::vector<double>& result /* [rows][np][2] */, int rows);
+
+double* pinned_alloc(size_t bytes);
+cudaError_t launch_noise_codes(uint8_t* codes, NoiseSpec n, int V, cudaStream_t s);
+
+}  // namespace fs

@@ -1,0 +1,323 @@
+// Even-odd Wilson hopping kernel over a tile of N systems, with a fused axpy
+// epilogue and fused dot-product partials.
+//
+// Wilson operator (r = 1, DeGrand-Rossi basis, gamma_mu = [[0, G_mu], [G_mu^dag, 0]]):
+//   D = (4 + m) - 1/2 H,
+//   (H psi)(x) = sum_mu (1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu),
+// with the t-hop that wraps multiplied by bc_t. The 4x4 projectors have rank 2:
+//   (1 + S g_mu) psi = [h; S G^dag h],  h = psi_up + S G psi_dn,
+// so each hop is one SU(3) product on a 2-spin half spinor (1320 flop per site).
+// The kernel computes, for output parity p and systems selected by `mask`:
+//   out = a X + b (H in) + c Y
+// with per-system (a, b, c) chosen by COEF from the system's shift, and
+// optionally per-system dot partials over fixed 8-site groups (deterministic,
+// independent of N and of the other systems in the tile).
+#pragma once
+
+#include "fs_common.cuh"
+
+namespace fs {
+
+enum Coef {
+  COEF_PLAIN = 0,    // out = H in
+  COEF_MHAT = 1,     // out = A X - H in / (4A)            Schur operator M = A - H_eo H_oe / (4A)
+  COEF_DSLASH = 2,   // out = A X - H in / 2              (D + sigma) on one parity
+  COEF_PREP = 3,     // out = X + H in / (2A)             bhat_e = z_e - D_eo A^-1 z_o
+  COEF_RECON = 4,    // out = X / A + H in / (2A)         x_o = A^-1 (z_o - D_oe x_e)
+  COEF_TRUERES = 5,  // out = Y - A X + H in / (4A)       r = bhat - M x
+  COEF_FULLRES = 6,  // out = Y - A X + H in / 2          r = z - (D + sigma) x on one parity
+};
+
+enum Dot { DOT_NONE = 0, DOT_R = 1, DOT_TS = 2, DOT_NORM = 3 };
+template <int DOT> struct DotK { static constexpr int K = 0; };
+template <> struct DotK<DOT_R> { static constexpr int K = 2; };
+template <> struct DotK<DOT_TS> { static constexpr int K = 3; };
+template <> struct DotK<DOT_NORM> { static constexpr int K = 1; };
+
+enum Mask { MASK_ALL = 0, MASK_ACTIVE = 1, MASK_UPDATE = 2, MASK_INIT = 3, MASK_HARVEST = 4 };
+
+__device__ __forceinline__ bool selected(const SysState* st, int sys, int mask) {
+  if (mask == MASK_ALL) return true;
+  const int s = st[sys].status, f = st[sys].flags;
+  // a system that broke down earlier in this iteration sits out until its restart
+  if (mask == MASK_ACTIVE) return s == SYS_ACTIVE && !(f & FLAG_RESTART);
+  if (mask == MASK_UPDATE) return s == SYS_ACTIVE && (f & FLAG_UPDATE);
+  if (mask == MASK_INIT) return (f & FLAG_INIT) != 0;
+  return (f & FLAG_HARVEST) != 0;
+}
+
+// Thread/block shape shared by all tile kernels: a block covers SB sites x NB
+// systems (sys fastest); grid.y splits the tile's N systems into chunks of NB.
+struct Shape {
+  int N, NB, SB, nchunk;  // nchunk = ceil(Vh / SB)
+};
+
+struct HopArgs {
+  void* out;
+  const void* in;
+  const void* X;
+  const void* Y;
+  const void* R;
+  const void* gauge;
+  const SysState* st;
+  double* partial;  // [N][K][Vh/8]
+  const int* gate;  // kernel returns at once if *gate == 0 (nullptr: always run)
+  unsigned long long* work;  // optional: += number of (site, system) pairs computed
+  Geom g;
+  Shape sh;
+  int p_out;
+  int mask;
+};
+
+// ---- links -----------------------------------------------------------------
+template <typename Tg, typename Tm, int NR>
+__device__ __forceinline__ void load_link(const Tg* __restrict__ gauge, int Vh, int parity, int mu,
+                                          int site, Tm (&u)[18]) {
+  constexpr int RP = link_pad<Tg>(NR);
+  constexpr int VW = Store<Tg>::VW;
+  const Tg* b = gauge + ((size_t)(parity * 4 + mu) * Vh + site) * RP;
+  Tm tmp[RP];
+#pragma unroll
+  for (int c = 0; c < RP / VW; c++) load_vec<Tg, Tm>(b + c * VW, tmp + c * VW);
+#pragma unroll
+  for (int k = 0; k < NR; k++) u[k] = tmp[k];
+  if constexpr (NR == 12) {
+    // third row = conj(row0 x row1) for a special unitary matrix
+    const Tm a0r = u[0], a0i = u[1], a1r = u[2], a1i = u[3], a2r = u[4], a2i = u[5];
+    const Tm b0r = u[6], b0i = u[7], b1r = u[8], b1i = u[9], b2r = u[10], b2i = u[11];
+    // c = a x b
+    Tm c0r = (a1r * b2r - a1i * b2i) - (a2r * b1r - a2i * b1i);
+    Tm c0i = (a1r * b2i + a1i * b2r) - (a2r * b1i + a2i * b1r);
+    Tm c1r = (a2r * b0r - a2i * b0i) - (a0r * b2r - a0i * b2i);
+    Tm c1i = (a2r * b0i + a2i * b0r) - (a0r * b2i + a0i * b2r);
+    Tm c2r = (a0r * b1r - a0i * b1i) - (a1r * b0r - a1i * b0i);
+    Tm c2i = (a0r * b1i + a0i * b1r) - (a1r * b0i + a1i * b0r);
+    u[12] = c0r; u[13] = -c0i; u[14] = c1r; u[15] = -c1i; u[16] = c2r; u[17] = -c2i;
+  }
+}
+
+// chi = U h  or  U^dag h  for one colour vector (3 complex)
+template <bool DAG, typename Tm>
+__device__ __forceinline__ void su3_mul(const Tm (&u)[18], const Tm* h, Tm* chi) {
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    Tm re = 0, im = 0;
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      const int k = DAG ? (b * 3 + a) * 2 : (a * 3 + b) * 2;
+      const Tm ur = u[k];
+      const Tm ui = DAG ? -u[k + 1] : u[k + 1];
+      re += ur * h[2 * b] - ui * h[2 * b + 1];
+      im += ur * h[2 * b + 1] + ui * h[2 * b];
+    }
+    chi[2 * a] = re;
+    chi[2 * a + 1] = im;
+  }
+}
+
+// One hop in direction MU with projector (1 + S gamma_mu), S = -1 forward, +1 backward.
+// psi indices: spin s, colour c -> psi[6 s + 2 c + {0 re, 1 im}].
+template <int MU, int S, bool DAG, typename Tm>
+__device__ __forceinline__ void hop_dir(Tm (&acc)[24], const Tm (&psi)[24], const Tm (&u)[18], Tm ph) {
+  Tm h0[6], h1[6];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const Tm p0r = psi[2 * c], p0i = psi[2 * c + 1];
+    const Tm p1r = psi[6 + 2 * c], p1i = psi[6 + 2 * c + 1];
+    const Tm p2r = psi[12 + 2 * c], p2i = psi[12 + 2 * c + 1];
+    const Tm p3r = psi[18 + 2 * c], p3i = psi[18 + 2 * c + 1];
+    Tm g0r, g0i, g1r, g1i;  // G psi_dn
+    if (MU == 0) {          // G1 = [[0, i], [i, 0]]
+      g0r = -p3i; g0i = p3r; g1r = -p2i; g1i = p2r;
+    } else if (MU == 1) {   // G2 = [[0, -1], [1, 0]]
+      g0r = -p3r; g0i = -p3i; g1r = p2r; g1i = p2i;
+    } else if (MU == 2) {   // G3 = diag(i, -i)
+      g0r = -p2i; g0i = p2r; g1r = p3i; g1i = -p3r;
+    } else {                // G4 = 1
+      g0r = p2r; g0i = p2i; g1r = p3r; g1i = p3i;
+    }
+    h0[2 * c] = p0r + S * g0r; h0[2 * c + 1] = p0i + S * g0i;
+    h1[2 * c] = p1r + S * g1r; h1[2 * c + 1] = p1i + S * g1i;
+  }
+  if (MU == 3) {
+#pragma unroll
+    for (int k = 0; k < 6; k++) { h0[k] *= ph; h1[k] *= ph; }
+  }
+  Tm x0[6], x1[6];
+  su3_mul<DAG>(u, h0, x0);
+  su3_mul<DAG>(u, h1, x1);
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const Tm x0r = x0[2 * c], x0i = x0[2 * c + 1], x1r = x1[2 * c], x1i = x1[2 * c + 1];
+    acc[2 * c] += x0r; acc[2 * c + 1] += x0i;
+    acc[6 + 2 * c] += x1r; acc[6 + 2 * c + 1] += x1i;
+    Tm d0r, d0i, d1r, d1i;  // G^dag chi
+    if (MU == 0) {          // G1^dag = [[0, -i], [-i, 0]]
+      d0r = x1i; d0i = -x1r; d1r = x0i; d1i = -x0r;
+    } else if (MU == 1) {   // G2^dag = [[0, 1], [-1, 0]]
+      d0r = x1r; d0i = x1i; d1r = -x0r; d1i = -x0i;
+    } else if (MU == 2) {   // G3^dag = diag(-i, i)
+      d0r = x0i; d0i = -x0r; d1r = -x1i; d1i = x1r;
+    } else {
+      d0r = x0r; d0i = x0i; d1r = x1r; d1i = x1i;
+    }
+    acc[12 + 2 * c] += S * d0r; acc[12 + 2 * c + 1] += S * d0i;
+    acc[18 + 2 * c] += S * d1r; acc[18 + 2 * c + 1] += S * d1i;
+  }
+}
+
+template <typename Ts, typename Tg, typename Tm, int NR, int MU>
+__device__ __forceinline__ void hop_mu(Tm (&acc)[24], const Field<Ts>& in, const Tg* gauge, const Geom& g,
+                                       int p_out, int site, int sys, const int (&x)[4]) {
+  // forward: (1 - g_mu) U_mu(x) psi(x + mu)
+  {
+    int y[4] = {x[0], x[1], x[2], x[3]};
+    y[MU] += 1;
+    Tm ph = 1;
+    if (y[MU] == g.L[MU]) { y[MU] = 0; if (MU == 3) ph = (Tm)g.bc_t; }
+    Tm psi[24], u[18];
+    in.load(cb_index(g, y), sys, psi);
+    load_link<Tg, Tm, NR>((const Tg*)gauge, g.Vh, p_out, MU, site, u);
+    hop_dir<MU, -1, false>(acc, psi, u, ph);
+  }
+  // backward: (1 + g_mu) U_mu(x - mu)^dag psi(x - mu)
+  {
+    int y[4] = {x[0], x[1], x[2], x[3]};
+    y[MU] -= 1;
+    Tm ph = 1;
+    if (y[MU] < 0) { y[MU] = g.L[MU] - 1; if (MU == 3) ph = (Tm)g.bc_t; }
+    const int nb = cb_index(g, y);
+    Tm psi[24], u[18];
+    in.load(nb, sys, psi);
+    load_link<Tg, Tm, NR>((const Tg*)gauge, g.Vh, 1 - p_out, MU, nb, u);
+    hop_dir<MU, +1, true>(acc, psi, u, ph);
+  }
+}
+
+// Write per-thread values into per-(8-site group, system) partial sums, in fixed order.
+template <int K>
+__device__ __forceinline__ void group_partials(const double (&vals)[K], int lsite, int lsys, int sys_base,
+                                               const Shape& sh, int Vh, int chunk, double* smem,
+                                               double* partial) {
+  const int NB = sh.NB;
+#pragma unroll
+  for (int k = 0; k < K; k++) smem[(lsite * NB + lsys) * K + k] = vals[k];
+  __syncthreads();
+  const int ngb = sh.SB / 8;
+  const int ngroups = Vh / 8;
+  if (lsite < ngb) {
+    const int grp = chunk * ngb + lsite;
+    const int sys = sys_base + lsys;
+    if (grp < ngroups && sys < sh.N) {
+      double s[K];
+#pragma unroll
+      for (int k = 0; k < K; k++) s[k] = 0.0;
+      for (int j = 0; j < 8; j++) {
+#pragma unroll
+        for (int k = 0; k < K; k++) s[k] += smem[((lsite * 8 + j) * NB + lsys) * K + k];
+      }
+#pragma unroll
+      for (int k = 0; k < K; k++) partial[((size_t)sys * K + k) * ngroups + grp] = s[k];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename Ts, typename Tg, typename Tm, int NR, int COEF, int DOT>
+__global__ void __launch_bounds__(256) hop_kernel(HopArgs a) {
+  if (a.gate != nullptr && *a.gate == 0) return;
+  constexpr int K = DotK<DOT>::K;
+  __shared__ double smem[256 * (K > 0 ? K : 1)];
+  const Shape sh = a.sh;
+  const Geom g = a.g;
+  const int lsys = threadIdx.x % sh.NB;
+  const int lsite = threadIdx.x / sh.NB;
+  const int sys = blockIdx.y * sh.NB + lsys;
+  const Field<Ts> in = make_field<Ts>(const_cast<void*>(a.in), g.Vh, sh.N);
+  const Field<Ts> out = make_field<Ts>(a.out, g.Vh, sh.N);
+  const bool sel = sys < sh.N && selected(a.st, sys, a.mask);
+
+  Tm ca = 0, cb = 1, cc = 0;
+  if (sel) {
+    const SysState& s = a.st[sys];
+    if (COEF == COEF_MHAT) { ca = coef<Tm>(s, C_A); cb = coef<Tm>(s, C_MINV4A); }
+    else if (COEF == COEF_DSLASH) { ca = coef<Tm>(s, C_A); cb = (Tm)-0.5; }
+    else if (COEF == COEF_PREP) { ca = 1; cb = coef<Tm>(s, C_INV2A); }
+    else if (COEF == COEF_RECON) { ca = coef<Tm>(s, C_INVA); cb = coef<Tm>(s, C_INV2A); }
+    else if (COEF == COEF_TRUERES) { ca = coef<Tm>(s, C_MINVA); cb = coef<Tm>(s, C_INV4A); cc = 1; }
+    else if (COEF == COEF_FULLRES) { ca = coef<Tm>(s, C_MINVA); cb = (Tm)0.5; cc = 1; }
+  }
+
+  for (int chunk = blockIdx.x; chunk < sh.nchunk; chunk += gridDim.x) {
+    const int site = chunk * sh.SB + lsite;
+    const bool act = sel && site < g.Vh;
+    if (a.work != nullptr) {
+      const int cnt = __syncthreads_count(act);
+      if (threadIdx.x == 0 && cnt) atomicAdd(a.work, (unsigned long long)cnt);
+    }
+    double dv[K > 0 ? K : 1];
+#pragma unroll
+    for (int k = 0; k < (K > 0 ? K : 1); k++) dv[k] = 0.0;
+    if (act) {
+      int x[4];
+      cb_coords(g, a.p_out, site, x);
+      Tm acc[24];
+#pragma unroll
+      for (int k = 0; k < 24; k++) acc[k] = 0;
+      hop_mu<Ts, Tg, Tm, NR, 0>(acc, in, (const Tg*)a.gauge, g, a.p_out, site, sys, x);
+      hop_mu<Ts, Tg, Tm, NR, 1>(acc, in, (const Tg*)a.gauge, g, a.p_out, site, sys, x);
+      hop_mu<Ts, Tg, Tm, NR, 2>(acc, in, (const Tg*)a.gauge, g, a.p_out, site, sys, x);
+      hop_mu<Ts, Tg, Tm, NR, 3>(acc, in, (const Tg*)a.gauge, g, a.p_out, site, sys, x);
+      Tm o[24];
+      if (COEF == COEF_PLAIN) {
+#pragma unroll
+        for (int k = 0; k < 24; k++) o[k] = acc[k];
+      } else {
+        Tm xv[24];
+        make_field<Ts>(const_cast<void*>(a.X), g.Vh, sh.N).load(site, sys, xv);
+#pragma unroll
+        for (int k = 0; k < 24; k++) o[k] = ca * xv[k] + cb * acc[k];
+        if (COEF == COEF_TRUERES || COEF == COEF_FULLRES) {
+          Tm yv[24];
+          make_field<Ts>(const_cast<void*>(a.Y), g.Vh, sh.N).load(site, sys, yv);
+#pragma unroll
+          for (int k = 0; k < 24; k++) o[k] += cc * yv[k];
+        }
+        if (DOT == DOT_TS) {
+          // <out, X> and <out, out>, out = t, X = s
+          Tm sr = 0, si = 0, tt = 0;
+#pragma unroll
+          for (int k = 0; k < 24; k += 2) {
+            sr += o[k] * xv[k] + o[k + 1] * xv[k + 1];
+            si += o[k] * xv[k + 1] - o[k + 1] * xv[k];
+            tt += o[k] * o[k] + o[k + 1] * o[k + 1];
+          }
+          dv[0] = (double)sr; dv[1] = (double)si; dv[2] = (double)tt;
+        }
+      }
+      if (DOT == DOT_R) {
+        Tm rv[24];
+        make_field<Ts>(const_cast<void*>(a.R), g.Vh, sh.N).load(site, sys, rv);
+        Tm sr = 0, si = 0;
+#pragma unroll
+        for (int k = 0; k < 24; k += 2) {
+          sr += rv[k] * o[k] + rv[k + 1] * o[k + 1];
+          si += rv[k] * o[k + 1] - rv[k + 1] * o[k];
+        }
+        dv[0] = (double)sr; dv[1] = (double)si;
+      }
+      if (DOT == DOT_NORM) {
+        Tm nn = 0;
+#pragma unroll
+        for (int k = 0; k < 24; k++) nn += o[k] * o[k];
+        dv[0] = (double)nn;
+      }
+      out.store(site, sys, o);
+    }
+    if constexpr (K > 0) {
+      group_partials<K>(dv, lsite, lsys, blockIdx.y * sh.NB, sh, g.Vh, chunk, smem, a.partial);
+    }
+  }
+}
+
+}  // namespace fs

@@ -1,0 +1,94 @@
+// Kernel launchers, instantiated once per storage precision (fs_kern_*.cu).
+#pragma once
+
+#include "fs_engine.h"
+
+namespace fs {
+
+template <typename Ts>
+using MathOf = typename std::conditional<std::is_same<Ts, double>::value, double, float>::type;
+
+template <typename Ts>
+cudaError_t launch_hop(int coef, int dot, int nr, const HopArgs& a, const Launch& l) {
+  using Tg = typename GaugeOf<Ts>::T;
+  using Tm = MathOf<Ts>;
+  const dim3 grid(l.grid_x, l.grid_y), block(l.block);
+#define FS_HOP(C, D, R)                                                  \
+  if (coef == C && dot == D && nr == R) {                                \
+    hop_kernel<Ts, Tg, Tm, R, C, D><<<grid, block, 0, l.stream>>>(a);    \
+    return cudaGetLastError();                                           \
+  }
+  if constexpr (std::is_same<Ts, double>::value) {
+    FS_HOP(COEF_PLAIN, DOT_NONE, 18)
+    FS_HOP(COEF_DSLASH, DOT_NONE, 18)
+    FS_HOP(COEF_MHAT, DOT_R, 18)
+    FS_HOP(COEF_MHAT, DOT_TS, 18)
+    FS_HOP(COEF_PREP, DOT_NORM, 18)
+    FS_HOP(COEF_RECON, DOT_NONE, 18)
+    FS_HOP(COEF_TRUERES, DOT_NORM, 18)
+    FS_HOP(COEF_FULLRES, DOT_NORM, 18)
+  } else {
+    FS_HOP(COEF_PLAIN, DOT_NONE, 18)
+    FS_HOP(COEF_DSLASH, DOT_NONE, 18)
+    FS_HOP(COEF_MHAT, DOT_R, 18)
+    FS_HOP(COEF_MHAT, DOT_TS, 18)
+    FS_HOP(COEF_PLAIN, DOT_NONE, 12)
+    FS_HOP(COEF_DSLASH, DOT_NONE, 12)
+    FS_HOP(COEF_MHAT, DOT_R, 12)
+    FS_HOP(COEF_MHAT, DOT_TS, 12)
+  }
+#undef FS_HOP
+  return cudaErrorInvalidValue;
+}
+
+template <typename Ts>
+cudaError_t launch_blas(int op, const BlasArgs& a, const Launch& l) {
+  using Tx = typename XOf<Ts>::T;
+  using Tm = MathOf<Ts>;
+  const dim3 grid(l.grid_x, l.grid_y), block(l.block);
+  switch (op) {
+    case OP_P: blas_kernel<Ts, Tx, Tm, OP_P><<<grid, block, 0, l.stream>>>(a); break;
+    case OP_S: blas_kernel<Ts, Tx, Tm, OP_S><<<grid, block, 0, l.stream>>>(a); break;
+    case OP_XR: blas_kernel<Ts, Tx, Tm, OP_XR><<<grid, block, 0, l.stream>>>(a); break;
+    case OP_ACCX: blas_kernel<Ts, Tx, Tm, OP_ACCX><<<grid, block, 0, l.stream>>>(a); break;
+    case OP_ZEROX: blas_kernel<Ts, Tx, Tm, OP_ZEROX><<<grid, block, 0, l.stream>>>(a); break;
+    case OP_SETR: blas_kernel<Ts, Tx, Tm, OP_SETR><<<grid, block, 0, l.stream>>>(a); break;
+    case OP_NORM64: blas_kernel<Ts, Tx, Tm, OP_NORM64><<<grid, block, 0, l.stream>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename Ts>
+cudaError_t launch_pack(void* fe, void* fo, const double* canon, const int* vec, const Geom& g, const Shape& sh,
+                        const Launch& l) {
+  pack_kernel<Ts><<<dim3(l.grid_x, l.grid_y), l.block, 0, l.stream>>>(fe, fo, canon, vec, g, sh);
+  return cudaGetLastError();
+}
+
+template <typename Ts>
+cudaError_t launch_unpack(double* canon, const void* fe, const void* fo, const int* vec, const Geom& g,
+                          const Shape& sh, const Launch& l) {
+  unpack_kernel<Ts><<<dim3(l.grid_x, l.grid_y), l.block, 0, l.stream>>>(canon, fe, fo, vec, g, sh);
+  return cudaGetLastError();
+}
+
+template <typename Tg>
+cudaError_t launch_gauge_pack(void* out, const double* canon, const Geom& g, int nr, cudaStream_t s) {
+  const int n = 8 * g.Vh;
+  const int blocks = (n + 255) / 256;
+  if (nr == 18) gauge_pack_kernel<Tg, 18><<<blocks, 256, 0, s>>>(out, canon, g);
+  else if (nr == 12) gauge_pack_kernel<Tg, 12><<<blocks, 256, 0, s>>>(out, canon, g);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+#define FS_INSTANTIATE(TS)                                                                                   \
+  template cudaError_t launch_hop<TS>(int, int, int, const HopArgs&, const Launch&);                        \
+  template cudaError_t launch_blas<TS>(int, const BlasArgs&, const Launch&);                                \
+  template cudaError_t launch_pack<TS>(void*, void*, const double*, const int*, const Geom&, const Shape&,   \
+                                       const Launch&);                                                      \
+  template cudaError_t launch_unpack<TS>(double*, const void*, const void*, const int*, const Geom&,         \
+                                         const Shape&, const Launch&);
+
+}  // namespace fs

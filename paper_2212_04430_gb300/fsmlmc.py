@@ -1,0 +1,289 @@
+"""Python binding of libfsmlmc.so (the C ABI in include/fsmlmc.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library. If the compiled library is missing this module raises at load time;
+there is no CPU fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import gamma as _gamma
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfsmlmc.so")
+
+FS_OK, FS_ERR_ARG, FS_ERR_INPUT, FS_ERR_OOM, FS_ERR_BUDGET, FS_ERR_NOCONV, FS_ERR_TIMEOUT, FS_ERR_CUDA, \
+    FS_ERR_STATE = range(9)
+PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+ESTIMATOR = {"diff": 0, "split_even": 1, "product": 2}
+SYS_CONVERGED, SYS_NOCONV = 2, 3
+
+EXPORTS = ["fs_ctx_create", "fs_ctx_destroy", "fs_last_error", "fs_set_stream", "fs_ctx_device_bytes",
+           "fs_set_gauge", "wilson_dslash", "shifted_solve", "mlmc_level_trace", "fs_mlmc_num_solves",
+           "variance_sample", "fs_noise_codes", "fs_profile_enable", "fs_profile_read"]
+
+
+class FsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("fsmlmc error %d: %s" % (code, msg))
+        self.code = code
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("prec", ctypes.c_int),
+                ("rhs_tile", ctypes.c_int), ("link_compress", ctypes.c_int), ("delta", ctypes.c_double),
+                ("verify", ctypes.c_int), ("pad", ctypes.c_int)]
+
+
+class SysStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("restarts", ctypes.c_int), ("true_resid", ctypes.c_double)]
+
+
+class MlmcParams(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_double), ("nlev", ctypes.c_int), ("p", ctypes.c_int),
+                ("sigma", ctypes.POINTER(ctypes.c_double)), ("n_samples", ctypes.POINTER(ctypes.c_int)),
+                ("gamma", ctypes.POINTER(ctypes.c_double)), ("seed", ctypes.c_uint64),
+                ("job", ctypes.c_uint32), ("estimator", ctypes.c_int), ("solve", SolveParams)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libfsmlmc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libfsmlmc.so not found at %s: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+    L = ctypes.CDLL(path)
+    P, I, D, U64, U32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "fs_ctx_create": (I, [ctypes.POINTER(P), ip, I, I]),
+        "fs_ctx_destroy": (None, [P]),
+        "fs_last_error": (ctypes.c_char_p, [P]),
+        "fs_set_stream": (I, [P, P]),
+        "fs_ctx_device_bytes": (ctypes.c_size_t, [P]),
+        "fs_set_gauge": (I, [P, dp]),
+        "wilson_dslash": (I, [P, D, D, dp, dp, I, I, I]),
+        "shifted_solve": (I, [P, D, dp, I, dp, I, dp, ctypes.POINTER(SolveParams), ctypes.POINTER(SysStats)]),
+        "mlmc_level_trace": (I, [P, ctypes.POINTER(MlmcParams), dp, dp, dp, ctypes.POINTER(SysStats)]),
+        "fs_mlmc_num_solves": (I, [ctypes.POINTER(MlmcParams)]),
+        "variance_sample": (I, [P, D, dp, I, dp, ip, I, I, U64, U32, ctypes.POINTER(SolveParams), dp, dp, dp,
+                                dp, dp]),
+        "fs_noise_codes": (I, [P, U64, U32, U32, U32, ctypes.POINTER(ctypes.c_uint8)]),
+        "fs_profile_enable": (I, [P, I]),
+        "fs_profile_read": (I, [P, ctypes.POINTER(ctypes.c_longlong), dp, dp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _real(a, shape=None):
+    """complex array -> contiguous float64 view with a trailing (re, im) axis."""
+    a = np.ascontiguousarray(a)
+    if np.iscomplexobj(a):
+        a = np.ascontiguousarray(a, dtype=np.complex128).view(np.float64)
+    else:
+        a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def _params(prec="f64", tol=0.0, max_iter=0, rhs_tile=0, link_compress=18, delta=0.0, verify=0):
+    p = SolveParams()
+    p.tol = tol
+    p.max_iter = max_iter
+    p.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    p.rhs_tile = rhs_tile
+    p.link_compress = link_compress
+    p.delta = delta
+    p.verify = int(verify)
+    return p
+
+
+class Context:
+    """A lattice on one CUDA device (fs_ctx)."""
+
+    def __init__(self, dims, bc_t=-1, device=0):
+        self.lib = load_library()
+        self.dims = tuple(int(d) for d in dims)
+        self.V = int(np.prod(self.dims))
+        self.h = ctypes.c_void_p()
+        arr = (ctypes.c_int * 4)(*self.dims)
+        rc = self.lib.fs_ctx_create(ctypes.byref(self.h), arr, int(bc_t), int(device))
+        if rc != FS_OK:
+            raise FsError(rc, "fs_ctx_create failed (dims %s, bc_t %d)" % (self.dims, bc_t))
+
+    def close(self):
+        if self.h:
+            self.lib.fs_ctx_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow_noconv=False):
+        if rc == FS_OK or (allow_noconv and rc == FS_ERR_NOCONV):
+            return rc
+        raise FsError(rc, self.lib.fs_last_error(self.h).decode())
+
+    def last_error(self):
+        return self.lib.fs_last_error(self.h).decode()
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+        handle = getattr(stream, "cuda_stream", stream)
+        self._check(self.lib.fs_set_stream(self.h, ctypes.c_void_p(handle or 0)))
+
+    def device_bytes(self):
+        return int(self.lib.fs_ctx_device_bytes(self.h))
+
+    def fs_set_gauge(self, U):
+        u = _real(U)
+        if u.size != 4 * self.V * 18:
+            raise ValueError("gauge field must have 4*V*3*3 complex entries")
+        self._check(self.lib.fs_set_gauge(self.h, _dptr(u)))
+
+    set_gauge = fs_set_gauge
+
+    def wilson_dslash(self, m, sigma, psi, prec="f64", link_compress=18):
+        """(D + sigma) psi for psi complex [V][4][3] or [nrhs][V][4][3]."""
+        x = _real(psi)
+        nrhs = x.size // (self.V * 24)
+        if nrhs * self.V * 24 != x.size:
+            raise ValueError("spinor size mismatch")
+        out = np.empty_like(x)
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        self._check(self.lib.wilson_dslash(self.h, m, sigma, _dptr(x), _dptr(out), nrhs, p, link_compress))
+        return out.view(np.complex128).reshape(np.shape(psi))
+
+    def shifted_solve(self, m, sigmas, b, **kw):
+        """x[j, k] = (D + sigma_j)^-1 b_k. Returns (x complex [nshift][nrhs][V][4][3], stats list, rc)."""
+        sig = np.ascontiguousarray(np.atleast_1d(sigmas), dtype=np.float64)
+        bb = _real(b)
+        nrhs = bb.size // (self.V * 24)
+        x = np.empty((len(sig), nrhs, self.V, 4, 3, 2), dtype=np.float64)
+        st = (SysStats * (len(sig) * nrhs))()
+        p = _params(**kw)
+        rc = self._check(self.lib.shifted_solve(self.h, m, _dptr(sig), len(sig), _dptr(bb), nrhs, _dptr(x),
+                                                ctypes.byref(p), st), allow_noconv=True)
+        return x.view(np.complex128)[..., 0], [_stats(s) for s in st], rc
+
+    def mlmc_level_trace(self, m, sigmas, gamma, p, n_samples, seed, job=0, estimator="diff", **kw):
+        sig = np.ascontiguousarray(sigmas, dtype=np.float64)
+        ns = np.ascontiguousarray(n_samples, dtype=np.int32)
+        if ns.size == 1 and sig.size > 1:
+            ns = np.full(sig.size, int(ns.ravel()[0]), dtype=np.int32)
+        g = _gamma.to_abi(gamma)
+        P = MlmcParams()
+        P.m = m
+        P.nlev = sig.size
+        P.p = int(p)
+        P.sigma = _dptr(sig)
+        P.n_samples = ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        P.gamma = _dptr(g)
+        P.seed = int(seed)
+        P.job = int(job)
+        P.estimator = ESTIMATOR[estimator] if isinstance(estimator, str) else int(estimator)
+        P.solve = _params(**kw)
+        nsolve = self.lib.fs_mlmc_num_solves(ctypes.byref(P))
+        trace = np.zeros((sig.size, 2))
+        var = np.zeros(sig.size)
+        samples = np.zeros((int(ns.sum()), 2))
+        st = (SysStats * max(nsolve, 1))()
+        rc = self._check(self.lib.mlmc_level_trace(self.h, ctypes.byref(P), _dptr(trace), _dptr(var),
+                                                   _dptr(samples), st), allow_noconv=True)
+        tr = trace[:, 0] + 1j * trace[:, 1]
+        smp = samples[:, 0] + 1j * samples[:, 1]
+        offs = np.concatenate([[0], np.cumsum(ns)])
+        return {"trace": tr, "var": var, "samples": [smp[offs[l]:offs[l + 1]] for l in range(sig.size)],
+                "total": complex(tr.sum()), "v_fs": float((var / ns).sum()),
+                "stats": [_stats(s) for s in st[:nsolve]], "rc": rc}
+
+    def variance_sample(self, m, s_hat, gamma, p_list, n_s, seed, job=0, **kw):
+        sh = np.ascontiguousarray(s_hat, dtype=np.float64)
+        pl = np.ascontiguousarray(p_list, dtype=np.int32)
+        ms, npl = sh.size, pl.size
+        g = _gamma.to_abi(gamma)
+        VL = np.zeros((npl, ms))
+        Vbar = np.zeros((npl, ms, ms))
+        a = np.zeros((n_s, npl, ms, 2))
+        b = np.zeros((n_s, npl, ms, ms, 2))
+        iters = np.zeros(ms)
+        prm = _params(**kw)
+        rc = self._check(self.lib.variance_sample(self.h, m, _dptr(sh), ms, _dptr(g),
+                                                  pl.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), npl, n_s,
+                                                  int(seed), int(job), ctypes.byref(prm), _dptr(VL), _dptr(Vbar),
+                                                  _dptr(a), _dptr(b), _dptr(iters)), allow_noconv=True)
+        return {"VL": VL, "Vbar": Vbar, "a": a[..., 0] + 1j * a[..., 1], "b": b[..., 0] + 1j * b[..., 1],
+                "Vl": (sh[None, None, :] - sh[None, :, None]) ** 2 * Vbar, "iters": iters, "rc": rc}
+
+    def fs_noise_codes(self, seed, job, level, sample):
+        codes = np.empty((self.V, 4, 3), dtype=np.uint8)
+        self._check(self.lib.fs_noise_codes(self.h, int(seed), int(job), int(level), int(sample),
+                                            codes.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+        return codes
+
+    noise_codes = fs_noise_codes
+
+    def profile_enable(self, enable=True):
+        self._check(self.lib.fs_profile_enable(self.h, int(enable)))
+
+    def profile_read(self):
+        n = ctypes.c_longlong()
+        ms = ctypes.c_double()
+        by = ctypes.c_double()
+        self._check(self.lib.fs_profile_read(self.h, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
+        return {"launches": n.value, "ms": ms.value, "bytes": by.value}
+
+
+def _stats(s):
+    return {"iters": s.iters, "status": s.status, "reliable_updates": s.reliable_updates,
+            "restarts": s.restarts, "true_resid": s.true_resid}
+
+
+# Module-level functions with the C ABI's names.
+def fs_ctx_create(dims, bc_t=-1, device=0):
+    return Context(dims, bc_t, device)
+
+
+def fs_set_gauge(ctx, U):
+    return ctx.fs_set_gauge(U)
+
+
+def wilson_dslash(ctx, m, sigma, psi, prec="f64", link_compress=18):
+    return ctx.wilson_dslash(m, sigma, psi, prec, link_compress)
+
+
+def shifted_solve(ctx, m, sigmas, b, **kw):
+    return ctx.shifted_solve(m, sigmas, b, **kw)
+
+
+def mlmc_level_trace(ctx, m, sigmas, gamma, p, n_samples, seed, job=0, estimator="diff", **kw):
+    return ctx.mlmc_level_trace(m, sigmas, gamma, p, n_samples, seed, job, estimator, **kw)
+
+
+def variance_sample(ctx, m, s_hat, gamma, p_list, n_s, seed, job=0, **kw):
+    return ctx.variance_sample(m, s_hat, gamma, p_list, n_s, seed, job, **kw)
+
+
+def fs_noise_codes(ctx, seed, job, level, sample):
+    return ctx.fs_noise_codes(seed, job, level, sample)

@@ -1,0 +1,247 @@
+"""CUDA path against the FP64 oracle, element by element on identical seeded inputs.
+
+Tolerances (from the arithmetic):
+  * Z4 noise codes: bit-exact (integer work).
+  * wilson_dslash: FP64 1e-13 (rounding order of 1320 flops); FP32 2e-6
+    (~10 ulp of FP32); FP16 storage 4e-3 (half ulp 4.9e-4 on inputs and output,
+    links in FP16); BF16 storage 3e-2 (bf16 ulp 3.9e-3).
+  * solutions: oracle-computed true relative residual <= tol (1e-10 FP64,
+    1e-8 mixed), as the solver's stopping rule.
+  * level / variance samples: relative 1e-9 (FP64 solves at 1e-12), 1e-6 (mixed
+    solves at 1e-8 ... 1e-10), normalised per level by max(|T|, mean |c|).
+"""
+
+import numpy as np
+import pytest
+
+import inputs
+from oracle import dirac as odirac
+from oracle import estimators as oest
+from oracle import philox as ophilox
+from helpers import oracle_D, rel_err, rel_resid, sample_err
+
+pkg = pytest.importorskip("paper_2212_04430_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def make_ctx(dims, u, bc_t=-1):
+    ctx = pkg.Context(dims, bc_t=bc_t, device=0)
+    ctx.fs_set_gauge(u)
+    return ctx
+
+
+# ---------------------------------------------------------------- noise
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 4, 4, 4), (6, 4, 2, 8), (8, 8, 8, 8)])
+def test_noise_codes_bit_exact(dims):
+    v = int(np.prod(dims))
+    ctx = pkg.Context(dims)
+    for (seed, job, level, sample) in [(0, 0, 0, 0), (2002, 3, 1, 17), (2**40 + 5, 7, 0x80000000, 3),
+                                       (2**64 - 1, 2**32 - 1, 2**32 - 1, 2**32 - 1)]:
+        got = ctx.fs_noise_codes(seed, job, level, sample)
+        ref = ophilox.z4_codes(v, seed, job, level, sample)
+        assert np.array_equal(got, ref)
+    ctx.close()
+
+
+# ---------------------------------------------------------------- dslash
+DSLASH_TOL = {"f64": 1e-13, "f32": 2e-6, "f16": 4e-3, "bf16": 3e-2}
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("dims,bc_t,nrhs", [((2, 2, 2, 2), -1, 1), ((4, 4, 4, 4), -1, 3),
+                                            ((4, 6, 2, 8), 1, 2), ((8, 8, 8, 8), -1, 17)])
+def test_dslash_parity(prec, dims, bc_t, nrhs):
+    u = inputs.gauge_field(dims, "haar", seed=1001)
+    psi = inputs.random_spinor(dims, 7, nvec=nrhs)
+    ctx = make_ctx(dims, u, bc_t)
+    for nr in ((18,) if prec == "f64" else (18, 12)):
+        got = ctx.wilson_dslash(-0.4, 0.15, psi, prec=prec, link_compress=nr)
+        ref = oracle_D(u, psi, -0.4, 0.15, dims, bc_t)
+        assert rel_err(got, ref) < DSLASH_TOL[prec], (prec, nr, rel_err(got, ref))
+    ctx.close()
+
+
+def test_dslash_ragged_tiles_and_empty():
+    """nrhs above the 64-system tile (two chunks, ragged tail) and nrhs = 0."""
+    dims = (4, 4, 2, 2)
+    u = inputs.gauge_field(dims, "smooth", seed=5, eps=0.3)
+    psi = inputs.random_spinor(dims, 8, nvec=70)
+    ctx = make_ctx(dims, u)
+    got = ctx.wilson_dslash(-0.2, 0.0, psi, prec="f64")
+    assert rel_err(got, oracle_D(u, psi, -0.2, 0.0, dims)) < 1e-13
+    empty = np.zeros((0, int(np.prod(dims)), 4, 3), dtype=complex)
+    assert ctx.wilson_dslash(-0.2, 0.0, empty).shape == empty.shape
+    ctx.close()
+
+
+def test_dslash_free_field_plane_wave_16x32():
+    """At 16^3x32 (no oracle needed): a plane wave is an eigenvector of the free
+    operator in spin space, (D + s) e^{ikx} u = [M(k) + i gamma.sin k] e^{ikx} u."""
+    dims = (16, 16, 16, 32)
+    u = inputs.unit_gauge(dims)
+    ctx = make_ctx(dims, u)
+    lx, ly, lz, lt = dims
+    n = np.array([3, 1, 5, 2])
+    k = 2 * np.pi * n / np.array(dims, dtype=float)
+    k[3] = (2 * n[3] + 1) * np.pi / lt  # antiperiodic in t
+    s = np.arange(int(np.prod(dims)))
+    x = np.stack([s % lx, (s // lx) % ly, (s // (lx * ly)) % lz, s // (lx * ly * lz)])
+    phase = np.exp(1j * (k[:, None] * x).sum(0))
+    spin = np.array([1.0, 0.5j, -0.25, 0.75 - 0.1j])
+    col = np.array([1.0, -1j, 0.3])
+    psi = phase[:, None, None] * spin[None, :, None] * col[None, None, :]
+    m, sigma = -0.35, 0.03
+    dk = (m + sigma + np.sum(1 - np.cos(k))) * np.eye(4) + 1j * sum(
+        odirac.GAMMA[mu] * np.sin(k[mu]) for mu in range(4))
+    ref = phase[:, None, None] * (dk @ spin)[None, :, None] * col[None, None, :]
+    for prec, tol in (("f64", 1e-12), ("f32", 2e-6)):
+        got = ctx.wilson_dslash(m, sigma, psi, prec=prec)
+        assert rel_err(got, ref) < tol
+    ctx.close()
+
+
+# ---------------------------------------------------------------- solves
+@pytest.mark.parametrize("prec,tol,nr", [("f64", 1e-10, 18), ("f32", 1e-8, 18), ("f16", 1e-8, 12),
+                                         ("bf16", 1e-8, 18)])
+def test_shifted_solve_residual_4444(prec, tol, nr):
+    dims = (4, 4, 4, 4)
+    u = inputs.gauge_field(dims, "haar", seed=1000)
+    b = inputs.random_spinor(dims, 9, nvec=3)
+    sig = [0.0, 0.4]
+    ctx = make_ctx(dims, u)
+    x, st, rc = ctx.shifted_solve(-0.4, sig, b, prec=prec, tol=tol, rhs_tile=4, link_compress=nr, verify=1)
+    assert rc == 0
+    for j, s in enumerate(sig):
+        for k in range(3):
+            r = rel_resid(u, x[j, k], b[k], -0.4, s, dims)
+            assert r <= tol * 1.05, (prec, j, k, r)
+            stt = st[j * 3 + k]
+            assert stt["status"] == 2 and stt["true_resid"] <= tol * 1.05
+            assert abs(stt["true_resid"] - r) <= 0.05 * r + 1e-15
+    ctx.close()
+
+
+def test_shifted_solve_matches_dense_2222():
+    """Smallest lattice (every direction wraps onto the same neighbour)."""
+    from oracle import solve as osolve
+    dims = (2, 2, 2, 2)
+    u = inputs.gauge_field(dims, "haar", seed=3)
+    b = inputs.random_spinor(dims, 4, nvec=2)
+    ctx = make_ctx(dims, u)
+    x, st, rc = ctx.shifted_solve(-0.3, [0.1], b, prec="f64", tol=1e-12, rhs_tile=1)
+    dense = osolve.dense_operator(u, -0.3, 0.1, dims)
+    for k in range(2):
+        ref = np.linalg.solve(dense, b[k].ravel()).reshape(b[k].shape)
+        assert rel_err(x[0, k], ref) < 1e-10
+    ctx.close()
+
+
+def test_shifted_solve_edge_cases():
+    dims = (4, 4, 2, 2)
+    u = inputs.gauge_field(dims, "smooth", seed=6, eps=0.3)
+    ctx = make_ctx(dims, u)
+    b = inputs.random_spinor(dims, 10, nvec=2)
+    b[1] = 0.0  # zero right-hand side: x = 0, converged at once
+    x, st, rc = ctx.shifted_solve(-0.2, [0.05], b, prec="f32")
+    assert rc == 0 and np.all(x[0, 1] == 0) and st[1]["status"] == 2
+    x, st, rc = ctx.shifted_solve(-0.2, [0.05], b[:1], prec="f64", max_iter=1, tol=1e-12)
+    assert rc == pkg.fsmlmc.FS_ERR_NOCONV and st[0]["status"] == 3
+    bad = b[:1].copy()
+    bad[0, 3, 1, 2] = np.nan
+    with pytest.raises(pkg.FsError) as e:
+        ctx.shifted_solve(-0.2, [0.05], bad)
+    assert e.value.code == pkg.fsmlmc.FS_ERR_INPUT
+    ctx.close()
+    with pytest.raises(pkg.FsError):
+        pkg.Context((4, 3, 4, 4))
+
+
+# ---------------------------------------------------------------- level traces
+def _oracle_levels(u, m, sig, gam, p, n, seed, job, dims, est):
+    solver = oest.make_dense_solver(u, m, dims)
+    return oest.level_samples(u, m, sig, gam, p, n, seed, job, dims, -1, est, solver)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f16", 1e-6)])
+def test_mlmc_config1_samples(prec, tol):
+    """4^4 Haar links, m = -0.4, shifts {0, 0.4}, Gamma = I, p = 0, 64 Z4 vectors per level."""
+    dims = (4, 4, 4, 4)
+    u = inputs.gauge_field(dims, "haar", seed=1001)
+    sig = [0.0, 0.4]
+    n = [64, 64]
+    ctx = make_ctx(dims, u)
+    solve_tol = 1e-12 if prec == "f64" else 1e-10
+    out = ctx.mlmc_level_trace(-0.4, sig, np.eye(4), 0, n, seed=2001, job=0, estimator="diff", prec=prec,
+                               tol=solve_tol, rhs_tile=32)
+    assert out["rc"] == 0
+    ref = _oracle_levels(u, -0.4, sig, odirac.IDENT4, 0, n, 2001, 0, dims, oest.DIFF)
+    for lev in range(2):
+        assert sample_err(out["samples"][lev], ref[lev]) < tol, lev
+        m2 = np.mean(np.abs(ref[lev]) ** 2)
+        assert abs(out["var"][lev] - oest.practical_variance(ref[lev])) <= 10 * tol * m2
+    ctx.close()
+
+
+@pytest.mark.parametrize("est", ["split_even", "product"])
+def test_mlmc_estimators_samples(est):
+    dims = (4, 4, 2, 4)
+    u = inputs.gauge_field(dims, "smooth", seed=11, eps=0.5)
+    sig = [0.0, 0.1, 0.5]
+    gam = pkg.gamma_matrix("g5g3")
+    n = [5, 4, 3]
+    ctx = make_ctx(dims, u)
+    out = ctx.mlmc_level_trace(-0.2, sig, gam, 2, n, seed=77, job=5, estimator=est, prec="f64", tol=1e-12,
+                               rhs_tile=8)
+    ref = _oracle_levels(u, -0.2, sig, odirac.gamma_product(["g5", "g3"]), 2, n, 77, 5, dims,
+                         oest.ESTIMATORS[est])
+    for lev in range(3):
+        assert sample_err(out["samples"][lev], ref[lev]) < 1e-9, (est, lev)
+    ctx.close()
+
+
+def test_mlmc_dense_expectation_config1():
+    """Mean of the GPU level samples against the exact dense level traces (5 sigma)."""
+    dims = (4, 4, 4, 4)
+    u = inputs.gauge_field(dims, "haar", seed=1001)
+    sig = [0.0, 0.4]
+    n = [256, 256]
+    ctx = make_ctx(dims, u)
+    out = ctx.mlmc_level_trace(-0.4, sig, np.eye(4), 0, n, seed=2001, job=1, prec="f32", tol=1e-10)
+    mats = oest.exact_level_matrices(u, -0.4, sig, odirac.IDENT4, 0, dims, -1, oest.DIFF)
+    for lev in range(2):
+        exact = np.trace(mats[lev])
+        se = np.sqrt(oest.exact_z4_variance(mats[lev]) / n[lev])
+        assert abs(out["trace"][lev] - exact) < 5 * se
+    ctx.close()
+
+
+# ---------------------------------------------------------------- variance sampling
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f32", 1e-6)])
+def test_variance_sample_parity(prec, tol):
+    dims = (4, 4, 4, 4)
+    u = inputs.gauge_field(dims, "smooth", seed=1005, eps=0.5)
+    s_hat = [0.0, 0.05, 0.25, 0.5, 1.0]
+    plist = [2, 0, 1]
+    ns = 3
+    ctx = make_ctx(dims, u)
+    out = ctx.variance_sample(-0.38, s_hat, pkg.gamma_matrix("g3"), plist, ns, seed=2005, job=0, prec=prec,
+                              tol=1e-12 if prec == "f64" else 1e-10)
+    solver = oest.make_dense_solver(u, -0.38, dims)
+    ref = oest.variance_sample(u, -0.38, s_hat, odirac.GAMMA[2], plist, ns, 2005, 0, dims, -1, solver)
+    for pi in range(len(plist)):
+        for i in range(5):
+            assert sample_err(out["a"][:, pi, i], ref["a"][:, pi, i]) < tol
+            for j in range(i, 5):
+                assert sample_err(out["b"][:, pi, i, j], ref["b"][:, pi, i, j]) < tol
+    m2a = np.mean(np.abs(ref["a"]) ** 2, axis=0)
+    m2b = np.mean(np.abs(ref["b"]) ** 2, axis=0)
+    assert np.all(np.abs(out["VL"] - ref["VL"]) <= 10 * tol * m2a)
+    assert np.all(np.abs(out["Vbar"] - ref["Vbar"]) <= 10 * tol * m2b + 1e-300)
+    ctx.close()
