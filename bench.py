@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Benchmark: Frequency-Splitting MLMC shifted Wilson solves per second on GB300.
+
+One step = one mlmc_level_trace call (the whole hot path: Z4 noise on the
+device, even-odd shifted solves at every level, Gamma Omega_p contraction,
+per-level trace and practical variance) over `--vectors` noise vectors per
+level. Default workload: 16^3x32 lattice, smoothed links U = exp(i 0.4 H),
+m = -0.35, 4-level FS shifts {0.005, 0.03, 0.15, 0.6}, Gamma = gamma_3, p = 4,
+32-system tiles, FP16 spinor storage with FP32 arithmetic, 12-real links, FP64
+reliable updates, solves to FP64 relative residual 1e-8.
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "shifted Wilson solves/s at 1e-8 resid; dslash HBM GB/s vs peak; p50/p99 latency"
+
+WORKLOADS = {
+    # the 16^3x32 FS-MLMC job (4 levels, 512 Z4 vectors per level in 32-system tiles)
+    "16x32": dict(dims=(16, 16, 16, 32), eps=0.4, gauge_seed=1003, noise_seed=2003, m=-0.35,
+                  sigmas=[0.005, 0.03, 0.15, 0.6], gamma="g3", p=4, vectors=32, tile=32, prec="f16",
+                  link=12, tol=1e-8, estimator="diff",
+                  name="16^3x32 Wilson FS-MLMC, 4 levels {0.005,0.03,0.15,0.6}, m=-0.35, eps=0.4, gamma3, p=4"),
+    # the 8^4 FS-MLMC job (3 levels, 256 Z4 vectors per level in 16-system tiles)
+    "8x8": dict(dims=(8, 8, 8, 8), eps=0.3, gauge_seed=1002, noise_seed=2002, m=-0.2,
+                sigmas=[0.02, 0.1, 0.5], gamma="g5g3", p=2, vectors=256, tile=16, prec="f32", link=18,
+                tol=1e-8, estimator="diff",
+                name="8^4 Wilson FS-MLMC, 3 levels {0.02,0.1,0.5}, m=-0.2, eps=0.3, gamma5 gamma3, p=2"),
+}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def hop_traffic_per_launch(workload):
+    """dram bytes per hop launch from the committed ncu summary, if it matches the kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "hop_kernel_%s.md" % workload)
+    if not os.path.exists(path):
+        return None
+    src = b""
+    for f in ("fs_hop.cuh", "fs_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2212_04430_gb300", "csrc", f), "rb") as fh:
+            src += fh.read()
+    digest = hashlib.sha256(src).hexdigest()[:16]
+    traffic, tag = None, None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("traffic_bytes_per_launch:"):
+                traffic = float(line.split(":")[1])
+            if line.startswith("kernel_source_sha256_16:"):
+                tag = line.split(":")[1].strip()
+    return traffic if (tag == digest and traffic) else None
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def oracle_rate(w, budget_s, seed_level=0):
+    """Oracle solves/s: a bounded number of oracle BiCGStab iterations on one system of the
+    workload, converted with the oracle's own iterations per solve (oracle/baseline_iters.json)."""
+    from oracle import dirac, philox, solve
+    import inputs
+    dims = w["dims"]
+    u = inputs.gauge_field(dims, "smooth", seed=w["gauge_seed"], eps=w["eps"])
+    shp = dirac.lattice_shape(dims)
+    ul = u.reshape((4,) + shp + (3, 3))
+    v = int(np.prod(dims))
+    lev = seed_level % len(w["sigmas"])
+    sigma = w["sigmas"][lev]
+    z = philox.z4_noise(v, w["noise_seed"], 0, lev, 0).ravel()
+
+    def apply_A(vec):
+        return dirac.apply_D(ul, vec.reshape(shp + (4, 3)), w["m"], sigma, -1).ravel()
+
+    t = time.time()
+    apply_A(z)
+    t_apply = time.time() - t
+    iters = max(1, int(budget_s / (2.0 * t_apply)))
+    t = time.time()
+    solve.bicgstab(apply_A, z, tol=1e-30, max_iter=iters)
+    dt = time.time() - t - t_apply  # bicgstab also applies A once for the final true residual
+    per_iter = dt / iters
+    with open(os.path.join(ROOT, "oracle", "baseline_iters.json")) as f:
+        cal = json.load(f)
+    sig = w["sigmas"]
+    it = [cal["iters"][repr(s)] for s in sig]
+    L = len(sig) - 1
+    mix = [it[l] + it[l + 1] for l in range(L)] + [it[L]]  # DIFF: two solves per sample below L
+    nsolve = 2 * L + 1
+    mean_iters = sum(mix) / nsolve
+    rate = 1.0 / (per_iter * mean_iters)
+    sample = ("%d oracle BiCGStab iterations (%.1f s) on one %s system at sigma=%g; "
+              "solves/s = 1 / (s per iteration x %.1f oracle iterations per solve, the workload's "
+              "shift mix from oracle/baseline_iters.json)" % (iters, dt, "x".join(map(str, dims)), sigma,
+                                                             mean_iters))
+    return rate, sample, dt
+
+
+def run_reference(args, w):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if int(os.environ.get("RANK", "0")) != 0:
+        return  # the CPU oracle runs once, on rank 0
+    budget = args.ref_budget
+    for k in range(args.warmup):
+        oracle_rate(w, min(budget, 3.0), k)
+    rates = []
+    t0 = time.time()
+    for k in range(args.steps):
+        r, sample, dt = oracle_rate(w, budget, k)
+        rates.append(r)
+    wall = time.time() - t0
+    value = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(args, w),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args, w):
+    return {"workload": w["name"], "lattice": "x".join(map(str, w["dims"])), "levels": len(w["sigmas"]),
+            "vectors_per_level_per_step": args.vectors or w["vectors"], "estimator": w["estimator"],
+            "rhs_tile": args.tile or w["tile"], "storage": w["prec"], "links": "%d-real" % w["link"],
+            "tol": w["tol"], "l2": "working set above L2 (no flush needed)"}
+
+
+# --------------------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="16x32", choices=sorted(WORKLOADS))
+    ap.add_argument("--vectors", type=int, default=0, help="Z4 vectors per level per step")
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-budget", type=float, default=8.0, help="seconds of oracle work per reference step")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+    if args.warmup < 1:
+        ap.error("--warmup must be >= 1")
+
+    ws, rank, local = dist_setup()
+    import torch
+
+    import inputs
+    import paper_2212_04430_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    dims = w["dims"]
+    nvec = args.vectors or w["vectors"]
+    tile = args.tile or w["tile"]
+    u = inputs.gauge_field(dims, "smooth", seed=w["gauge_seed"], eps=w["eps"])
+    ctx = pkg.Context(dims, bc_t=-1, device=local)
+    ctx.set_stream(stream.cuda_stream)
+    ctx.fs_set_gauge(u)
+    gam = pkg.gamma_matrix(w["gamma"])
+    kw = dict(prec=w["prec"], tol=w["tol"], rhs_tile=tile, link_compress=w["link"])
+    n = [nvec] * len(w["sigmas"])
+
+    def step(job):
+        out = ctx.mlmc_level_trace(w["m"], w["sigmas"], gam, w["p"], n, seed=w["noise_seed"],
+                                   job=job, estimator=w["estimator"], **kw)
+        if out["rc"] != 0:
+            raise RuntimeError("solver did not converge: %s" % ctx.last_error())
+        return out
+
+    solves_per_step = 2 * nvec * (len(w["sigmas"]) - 1) + nvec
+    job0 = 100000 * rank
+    for k in range(args.warmup):
+        step(job0 + k)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    ctx.profile_enable(True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    l0 = pkg.fsmlmc.fs_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters = []
+    for k in range(args.steps):
+        out = step(job0 + 1000 + k)
+        iters.extend(s["iters"] for s in out["stats"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    launches = pkg.fsmlmc.fs_kernel_launches() - l0
+    clk = clocks.stop()
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    ms_max = max_over_ranks(ms, ws)
+    total_solves = sum_over_ranks(solves_per_step * args.steps, ws)
+    value = total_solves / (ms_max / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        upin = torch.empty(u.size * 2, dtype=torch.float64, pin_memory=True)
+        upin.numpy()[:] = u.view(np.float64).ravel()
+        h2d = upin.numel() * 8
+        d2h = (len(n) * 2 + len(n) + sum(n) * 2) * 8
+        barrier(ws)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for k in range(args.steps):
+            ctx.fs_set_gauge(upin.numpy())
+            step(job0 + 2000 + k)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(f0.elapsed_time(f1), ws)
+        e2e = {"value": total_solves / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    peaks, peak_kind = load_peaks()
+    roof = None
+    if prof["launches"] > 0 and prof["ms"] > 0:
+        per_launch_s = prof["ms"] / prof["launches"] / 1e3
+        bytes_per_launch = prof["bytes"] / prof["launches"]
+        achieved = bytes_per_launch / per_launch_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": hop_traffic_per_launch(args.workload),
+                "kernel": "hop_kernel (even-odd Wilson hopping term, inner precision)",
+                "launches": prof["launches"], "avg_launch_us": per_launch_s * 1e6,
+                "algorithmic_bytes_per_launch": bytes_per_launch, "peak_source": peak_kind}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        try:
+            rate, sample, _ = oracle_rate(w, args.cpu_budget)
+            cpu = {"value": rate, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample}
+        except Exception as ex:  # the baseline never blocks the GPU line
+            cpu = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": "failed: %s" % ex}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_of(args, w), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk,
+                "solver": {"mean_iters": float(np.mean(iters)) if iters else None,
+                           "max_iters": int(max(iters)) if iters else None,
+                           "solves_per_step": solves_per_step}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -186,6 +186,9 @@ int fs_noise_codes(fs_ctx* ctx, uint64_t seed, uint32_t job, uint32_t level, uin
 int fs_profile_enable(fs_ctx* ctx, int enable);
 int fs_profile_read(fs_ctx* ctx, long long* launches, double* total_ms, double* bytes);
 
+/* Number of CUDA kernels this library has launched in the process (all contexts). */
+long long fs_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

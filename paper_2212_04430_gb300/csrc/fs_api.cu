@@ -56,7 +56,9 @@ int resolve_params(Ctx& c, const fs_solve_params* p, int nsys, double m, Opts& o
   if (o.so.nr != 18 && o.so.nr != 12) return c.fail(FS_ERR_ARG, "link_compress must be 18 or 12");
   if (o.so.prec == FS_PREC_F64) o.so.nr = 18;  // FP64 path keeps full links
   if (d.delta > 0) o.so.delta = d.delta;
-  else o.so.delta = o.so.prec == FS_PREC_F64 ? 0.0 : (o.so.prec == FS_PREC_F32 ? 1e-3 : 0.1);
+  // default reliable-update trigger: as deep as the storage precision lets the sloppy
+  // residual fall before rounding stalls it (each update costs two FP64 hops per system)
+  else o.so.delta = o.so.prec == FS_PREC_F64 ? 0.0 : (o.so.prec == FS_PREC_F32 ? 1e-4 : (o.so.prec == FS_PREC_F16 ? 1e-2 : 3e-2));
   if (o.so.delta >= 1.0) return c.fail(FS_ERR_ARG, "delta must be < 1");
   o.so.verify = d.verify;
   o.so.check_every = 4;
@@ -76,56 +78,13 @@ void fill_stats(const fs::SysState& s, fs_sys_stats* out, bool verify) {
   out->true_resid = s.b2 > 0 ? std::sqrt(r2 / s.b2) : 0.0;
 }
 
-// A group of systems that must share a tile, with the contractions over their solutions.
-struct Group {
-  std::vector<fs::SysSpec> sys;
-  std::vector<fs::ContractPair> pairs;  // right / left are group-local; out is a global row
-  std::vector<int> stat_index;          // global stats index per system (-1: none)
-};
-
-// Solve groups tile by tile (whole groups per tile) and run their contractions.
-int run_groups(Ctx& c, const std::vector<Group>& groups, const Opts& o, const double* gamma,
-               const std::vector<int>& plist, int rows, std::vector<double>& result,
-               std::vector<fs::SysState>* states, int* noconv) {
+// Tile for a job list: at least the largest group, at most 64 systems.
+fs::TileBase* tile_for(Ctx& c, const std::vector<fs::QJob>& jobs, const Opts& o) {
   int gmax = 1;
-  for (auto& g : groups) gmax = std::max(gmax, (int)g.sys.size());
+  for (auto& q : jobs) gmax = std::max(gmax, (int)q.sys.size());
   const int N = std::max(o.tile, gmax);
-  if (N > fs::MAX_TILE) return c.fail(FS_ERR_ARG, "a group of systems does not fit in one tile");
-  fs::TileBase* T = c.tile(o.so.prec, N, o.so.nr);
-  if (!T) return c.fail(FS_ERR_OOM, "device allocation of the solver tile failed");
-  const int np = (int)plist.size();
-  result.assign((size_t)rows * np * 2, 0.0);
-  size_t gi = 0;
-  while (gi < groups.size()) {
-    std::vector<fs::SysSpec> specs;
-    std::vector<fs::ContractPair> pairs;
-    std::vector<int> stat_idx;
-    while (gi < groups.size() && specs.size() + groups[gi].sys.size() <= (size_t)N) {
-      const int base = (int)specs.size();
-      for (auto& s : groups[gi].sys) specs.push_back(s);
-      for (int k : groups[gi].stat_index) stat_idx.push_back(k);
-      for (auto p : groups[gi].pairs) {
-        p.right += base;
-        p.left += base;
-        pairs.push_back(p);
-      }
-      gi++;
-    }
-    int rc = fs::solve_tile(&c, T, specs.data(), (int)specs.size(), o.so);
-    if (rc) return rc;
-    for (size_t j = 0; j < specs.size(); j++) {
-      if (T->st_h[j].status != fs::SYS_CONVERGED) *noconv = 1;
-      if (states && stat_idx[j] >= 0) (*states)[stat_idx[j]] = T->st_h[j];
-    }
-    if (!pairs.empty()) {
-      std::vector<double> part;
-      rc = fs::contract_tile(&c, T, pairs, gamma, plist, part, rows);
-      if (rc) return rc;
-      for (auto& p : pairs)
-        for (int q = 0; q < np * 2; q++) result[(size_t)p.out * np * 2 + q] = part[(size_t)p.out * np * 2 + q];
-    }
-  }
-  return 0;
+  if (N > fs::MAX_TILE) return nullptr;
+  return c.tile(o.so.prec, N, o.so.nr);
 }
 
 }  // namespace
@@ -296,37 +255,29 @@ int shifted_solve(fs_ctx* ctx, double m, const double* sigma, int nshift, const 
   const int S = nshift * nrhs;
   if (int rc = resolve_params(c, params, S, m, o)) return rc;
   if (int rc = set_device(c)) return rc;
-  const int N = o.tile;
-  if (int rc = c.ensure_canon((size_t)nrhs + N)) return rc;
-  fs::TileBase* T = c.tile(o.so.prec, N, o.so.nr);
+  std::vector<fs::QJob> jobs(S);
+  for (int i = 0; i < S; i++) {
+    const int j = i / nrhs, k = i % nrhs;
+    jobs[i].sys = {fs::SysSpec{sigma[j], 1, k, fs::NoiseSpec{}}};
+    jobs[i].stat_index = {i};
+    jobs[i].out_index = {i};
+  }
+  fs::TileBase* T = tile_for(c, jobs, o);
   if (!T) return c.fail(FS_ERR_OOM, "device allocation of the solver tile failed");
+  const int N = T->N;
+  if (int rc = c.ensure_canon((size_t)nrhs + N)) return rc;
   cudaError_t e = cudaMemcpyAsync(c.canon_d, b, nrhs * vlen * sizeof(double), cudaMemcpyHostToDevice, c.stream);
   if (e) return c.cuda_fail(e, "upload right-hand sides");
   int noconv = 0;
-  std::vector<fs::SysSpec> specs(N);
-  for (int i0 = 0; i0 < S; i0 += N) {
-    const int nb = std::min(N, S - i0);
-    for (int i = 0; i < nb; i++) {
-      const int j = (i0 + i) / nrhs, k = (i0 + i) % nrhs;
-      specs[i].sigma = sigma[j];
-      specs[i].rhs_kind = 1;
-      specs[i].vec = k;
-      specs[i].noise = fs::NoiseSpec{};
-    }
-    int rc = fs::solve_tile(&c, T, specs.data(), nb, o.so);
-    if (rc) return rc;
-    for (int i = 0; i < N; i++) T->vec_h[i] = i < nb ? nrhs + i : -1;
-    e = cudaMemcpyAsync(T->vec_d, T->vec_h, sizeof(int) * N, cudaMemcpyHostToDevice, c.stream);
-    if (!e) e = T->enqueue_solution_to_canon(c.canon_d);
-    if (!e) e = cudaMemcpyAsync(x + (size_t)i0 * vlen, c.canon_d + (size_t)nrhs * vlen, nb * vlen * sizeof(double),
-                                cudaMemcpyDeviceToHost, c.stream);
-    if (!e) e = cudaStreamSynchronize(c.stream);
-    if (e) return c.cuda_fail(e, "download solutions");
-    for (int i = 0; i < nb; i++) {
-      if (T->st_h[i].status != fs::SYS_CONVERGED) noconv = 1;
-      if (stats) fill_stats(T->st_h[i], &stats[i0 + i], o.so.verify != 0);
-    }
-  }
+  std::vector<fs::SysState> st(S);
+  fs::QOut out;
+  out.states = &st;
+  out.noconv = &noconv;
+  out.x_host = x;
+  out.canon_out_base = nrhs;
+  if (int rc = fs::run_queue(&c, T, jobs, o.so, out)) return rc;
+  if (stats)
+    for (int i = 0; i < S; i++) fill_stats(st[i], &stats[i], o.so.verify != 0);
   return noconv ? c.fail(FS_ERR_NOCONV, "some systems reached max_iter") : FS_OK;
 }
 
@@ -369,119 +320,77 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double
   std::vector<int> solve_off(L + 2, 0);
   for (int l = 0; l <= L; l++) solve_off[l + 1] = solve_off[l] + P->n_samples[l] * (l < L ? 2 : 1);
   int noconv = 0;
-
-  if (P->estimator != FS_EST_PRODUCT) {
-    // rows: DIFF -> one per solve (c_a, c_b), SPLIT_EVEN -> one per level-l sample
-    std::vector<Group> groups;
-    for (int l = 0; l <= L; l++) {
-      for (int s = 0; s < P->n_samples[l]; s++) {
-        Group g;
-        const int si = solve_off[l] + s * (l < L ? 2 : 1);
-        if (l == L) {
-          fs::SysSpec a{P->sigma[L], 0, -1, noise_id(P->seed, P->job, l, s, false)};
-          g.sys = {a};
-          g.stat_index = {si};
-          g.pairs = {{0, 0, 0, si}};
-        } else if (P->estimator == FS_EST_DIFF) {
-          fs::SysSpec a{P->sigma[l], 0, -1, noise_id(P->seed, P->job, l, s, false)};
-          fs::SysSpec b{P->sigma[l + 1], 0, -1, noise_id(P->seed, P->job, l, s, false)};
-          // two independent systems on the same noise: separate groups pack tiles better
-          Group g2;
-          g.sys = {a}; g.stat_index = {si}; g.pairs = {{0, 0, 0, si}};
-          g2.sys = {b}; g2.stat_index = {si + 1}; g2.pairs = {{0, 0, 0, si + 1}};
-          groups.push_back(g);
-          groups.push_back(g2);
-          continue;
-        } else {
-          fs::SysSpec a{P->sigma[l], 0, -1, noise_id(P->seed, P->job, l, s, true)};
-          fs::SysSpec b{P->sigma[l + 1], 0, -1, noise_id(P->seed, P->job, l, s, false)};
-          g.sys = {a, b};
-          g.stat_index = {si, si + 1};
-          g.pairs = {{1, 0, 1, si}};  // y_a^dag Gamma Omega_p x_b, y_a = gamma_5 x_a
-        }
-        groups.push_back(g);
+  // one result row per solve; the level sample is combined from the rows below
+  std::vector<fs::QJob> jobs;
+  const double nan = std::nan("");
+  for (int l = 0; l <= L; l++) {
+    for (int s = 0; s < P->n_samples[l]; s++) {
+      const int si = solve_off[l] + s * (l < L ? 2 : 1);
+      fs::QJob q;
+      if (l == L) {
+        q.sys = {fs::SysSpec{P->sigma[L], 0, -1, noise_id(P->seed, P->job, l, s, false)}};
+        q.stat_index = {si};
+        q.pairs = {{0, 0, 0, si}};
+        jobs.push_back(q);
+      } else if (P->estimator == FS_EST_DIFF) {
+        // the two solves of a DIFF sample are independent: one group each packs slots best
+        fs::QJob q2;
+        q.sys = {fs::SysSpec{P->sigma[l], 0, -1, noise_id(P->seed, P->job, l, s, false)}};
+        q.stat_index = {si};
+        q.pairs = {{0, 0, 0, si}};
+        q2.sys = {fs::SysSpec{P->sigma[l + 1], 0, -1, noise_id(P->seed, P->job, l, s, false)}};
+        q2.stat_index = {si + 1};
+        q2.pairs = {{0, 0, 0, si + 1}};
+        jobs.push_back(q);
+        jobs.push_back(q2);
+      } else if (P->estimator == FS_EST_SPLIT_EVEN) {
+        q.sys = {fs::SysSpec{P->sigma[l], 0, -1, noise_id(P->seed, P->job, l, s, true)},
+                 fs::SysSpec{P->sigma[l + 1], 0, -1, noise_id(P->seed, P->job, l, s, false)}};
+        q.stat_index = {si, si + 1};
+        q.pairs = {{1, 0, 1, si}};  // y^dag Gamma Omega_p x_{l+1}, y = gamma_5 x~_l
+        jobs.push_back(q);
+      } else {
+        // PRODUCT: x1 = (D + s_{l+1})^-1 z, then (D + s_l)^-1 x1 in the same slot
+        q.sys = {fs::SysSpec{P->sigma[l + 1], 0, -1, noise_id(P->seed, P->job, l, s, false)}};
+        q.chain = {P->sigma[l]};
+        q.stat_index = {si};
+        q.stat_index2 = {si + 1};
+        q.pairs = {{0, 0, 0, si}};
+        jobs.push_back(q);
       }
+      (void)nan;
     }
-    std::vector<double> res;
-    int rc = run_groups(c, groups, o, P->gamma, plist, nsolve, res, &st, &noconv);
-    if (rc) return rc;
-    for (int l = 0; l <= L; l++) {
-      for (int s = 0; s < P->n_samples[l]; s++) {
-        const int si = solve_off[l] + s * (l < L ? 2 : 1);
-        double re, im;
-        if (l == L) {
-          re = res[(size_t)si * 2]; im = res[(size_t)si * 2 + 1];
-        } else if (P->estimator == FS_EST_DIFF) {
-          re = res[(size_t)si * 2] - res[(size_t)(si + 1) * 2];
-          im = res[(size_t)si * 2 + 1] - res[(size_t)(si + 1) * 2 + 1];
-        } else {
-          const double ds = P->sigma[l + 1] - P->sigma[l];
-          re = ds * res[(size_t)si * 2]; im = ds * res[(size_t)si * 2 + 1];
-        }
-        csum[(off[l] + s) * 2] = re;
-        csum[(off[l] + s) * 2 + 1] = im;
-      }
-    }
-  } else {
-    // PRODUCT: x1 = (D + s_{l+1})^-1 z, then x01 = (D + s_l)^-1 x1, c = (s_{l+1} - s_l) z^dag Gamma Omega_p x01
-    const int N = o.tile;
-    fs::TileBase* T = c.tile(o.so.prec, N, o.so.nr);
-    if (!T) return c.fail(FS_ERR_OOM, "device allocation of the solver tile failed");
-    if (int rc = c.ensure_canon(N)) return rc;
-    for (int l = 0; l < L; l++) {
-      for (int s0 = 0; s0 < P->n_samples[l]; s0 += N) {
-        const int nb = std::min(N, P->n_samples[l] - s0);
-        std::vector<fs::SysSpec> sp(nb);
-        for (int i = 0; i < nb; i++)
-          sp[i] = fs::SysSpec{P->sigma[l + 1], 0, -1, noise_id(P->seed, P->job, l, s0 + i, false)};
-        int rc = fs::solve_tile(&c, T, sp.data(), nb, o.so);
-        if (rc) return rc;
-        for (int i = 0; i < nb; i++) {
-          st[solve_off[l] + (s0 + i) * 2] = T->st_h[i];
-          if (T->st_h[i].status != fs::SYS_CONVERGED) noconv = 1;
-        }
-        for (int i = 0; i < N; i++) T->vec_h[i] = i < nb ? i : -1;
-        cudaError_t e = cudaMemcpyAsync(T->vec_d, T->vec_h, sizeof(int) * N, cudaMemcpyHostToDevice, c.stream);
-        if (!e) e = T->enqueue_solution_to_canon(c.canon_d);
-        if (e) return c.cuda_fail(e, "stage nested right-hand sides");
-        for (int i = 0; i < nb; i++) {
-          sp[i].sigma = P->sigma[l];
-          sp[i].rhs_kind = 1;
-          sp[i].vec = i;
-        }
-        rc = fs::solve_tile(&c, T, sp.data(), nb, o.so);
-        if (rc) return rc;
-        std::vector<fs::ContractPair> pairs(nb);
-        for (int i = 0; i < nb; i++) {
-          pairs[i] = fs::ContractPair{i, i, 0, i};
-          st[solve_off[l] + (s0 + i) * 2 + 1] = T->st_h[i];
-          if (T->st_h[i].status != fs::SYS_CONVERGED) noconv = 1;
-        }
-        std::vector<double> part;
-        rc = fs::contract_tile(&c, T, pairs, P->gamma, plist, part, nb);
-        if (rc) return rc;
+  }
+  fs::TileBase* T = tile_for(c, jobs, o);
+  if (!T) return c.fail(FS_ERR_OOM, "device allocation of the solver tile failed");
+  if (P->estimator == FS_EST_PRODUCT)
+    if (int rc = c.ensure_canon(T->N)) return rc;
+  std::vector<double> res;
+  res.assign((size_t)nsolve * 2, 0.0);
+  fs::QOut out;
+  out.gamma = P->gamma;
+  out.plist = &plist;
+  out.rows = nsolve;
+  out.result = &res;
+  out.states = &st;
+  out.noconv = &noconv;
+  out.canon_chain_base = 0;
+  if (int rc = fs::run_queue(&c, T, jobs, o.so, out)) return rc;
+  for (int l = 0; l <= L; l++) {
+    for (int s = 0; s < P->n_samples[l]; s++) {
+      const int si = solve_off[l] + s * (l < L ? 2 : 1);
+      double re, im;
+      if (l == L) {
+        re = res[(size_t)si * 2]; im = res[(size_t)si * 2 + 1];
+      } else if (P->estimator == FS_EST_DIFF) {
+        re = res[(size_t)si * 2] - res[(size_t)(si + 1) * 2];
+        im = res[(size_t)si * 2 + 1] - res[(size_t)(si + 1) * 2 + 1];
+      } else {
         const double ds = P->sigma[l + 1] - P->sigma[l];
-        for (int i = 0; i < nb; i++) {
-          csum[(off[l] + s0 + i) * 2] = ds * part[(size_t)i * 2];
-          csum[(off[l] + s0 + i) * 2 + 1] = ds * part[(size_t)i * 2 + 1];
-        }
+        re = ds * res[(size_t)si * 2]; im = ds * res[(size_t)si * 2 + 1];
       }
-    }
-    std::vector<Group> groups;
-    for (int s = 0; s < P->n_samples[L]; s++) {
-      Group g;
-      const int si = solve_off[L] + s;
-      g.sys = {fs::SysSpec{P->sigma[L], 0, -1, noise_id(P->seed, P->job, L, s, false)}};
-      g.stat_index = {si};
-      g.pairs = {{0, 0, 0, s}};
-      groups.push_back(g);
-    }
-    std::vector<double> res;
-    int rc = run_groups(c, groups, o, P->gamma, plist, P->n_samples[L], res, &st, &noconv);
-    if (rc) return rc;
-    for (int s = 0; s < P->n_samples[L]; s++) {
-      csum[(off[L] + s) * 2] = res[(size_t)s * 2];
-      csum[(off[L] + s) * 2 + 1] = res[(size_t)s * 2 + 1];
+      csum[(off[l] + s) * 2] = re;
+      csum[(off[l] + s) * 2 + 1] = im;
     }
   }
   // per-level mean and practical variance, Eq. (practical_variance)
@@ -530,9 +439,9 @@ int variance_sample(fs_ctx* ctx, double m, const double* s_hat, int ms, const do
   if (int rc = set_device(c)) return rc;
   o.tile = std::max(2 * ms, (o.tile / (2 * ms)) * (2 * ms));
   const int per = ms + ms * (ms + 1) / 2;  // contraction rows per noise vector
-  std::vector<Group> groups(Ns);
+  std::vector<fs::QJob> groups(Ns);
   for (int k = 0; k < Ns; k++) {
-    Group& g = groups[k];
+    fs::QJob& g = groups[k];
     for (int i = 0; i < ms; i++)
       g.sys.push_back(fs::SysSpec{s_hat[i], 0, -1, noise_id(seed, job, 0x80000000u, k, false)});
     for (int i = 0; i < ms; i++)
@@ -543,11 +452,19 @@ int variance_sample(fs_ctx* ctx, double m, const double* s_hat, int ms, const do
     for (int i = 0; i < ms; i++)
       for (int j = i; j < ms; j++) g.pairs.push_back({j, ms + i, 1, row++});        // b_ij
   }
-  std::vector<double> res;
+  std::vector<double> res((size_t)Ns * per * np * 2, 0.0);
   std::vector<fs::SysState> st((size_t)Ns * 2 * ms);
   int noconv = 0;
-  int rc = run_groups(c, groups, o, gamma, plist, Ns * per, res, &st, &noconv);
-  if (rc) return rc;
+  fs::TileBase* T = tile_for(c, groups, o);
+  if (!T) return c.fail(FS_ERR_OOM, "device allocation of the solver tile failed");
+  fs::QOut out;
+  out.gamma = gamma;
+  out.plist = &plist;
+  out.rows = Ns * per;
+  out.result = &res;
+  out.states = &st;
+  out.noconv = &noconv;
+  if (int rc = fs::run_queue(&c, T, groups, o.so, out)) return rc;
   auto val = [&](int k, int r, int q, int ri) { return res[(((size_t)k * per + r) * np + q) * 2 + ri]; };
   for (int qs = 0; qs < np; qs++) {
     const int q = order[qs];  // caller's index of the qs-th smallest displacement
@@ -664,5 +581,7 @@ int fs_profile_read(fs_ctx* ctx, long long* launches, double* total_ms, double* 
   if (bytes) *bytes = b;
   return FS_OK;
 }
+
+long long fs_kernel_launches(void) { return fs::launch_count(); }
 
 }  // extern "C"

@@ -1,0 +1,284 @@
+// Continuous batching of shifted solves over the slots of one tile.
+//
+// Systems arrive as groups (systems whose solutions are contracted together).
+// A group is admitted when enough slots are free; its slots are initialised
+// (noise or caller right-hand side, even-odd preparation) while the other slots
+// keep iterating, since every kernel masks by slot state. When all systems of a
+// group have converged, the group is harvested (odd-site reconstruction, optional
+// FP64 verification, contractions, outputs) and its slots are reused at once. A
+// system with a follow-up shift (the nested solve of the product estimator) is
+// re-initialised in place with its own solution as the next right-hand side.
+#include "fs_engine.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace fs {
+
+namespace {
+
+void set_coef_h(SysState& s, int k, double v) {
+  s.cd[k] = v;
+  s.cf[k] = (float)v;
+}
+
+void init_state(SysState& s, double sigma, const SolveOpts& o) {
+  memset(&s, 0, sizeof(SysState));
+  const double A = 4.0 + o.m + sigma;
+  s.sigma = sigma;
+  s.A = A;
+  s.inv4A = 1.0 / (4.0 * A);
+  set_coef_h(s, C_A, A);
+  set_coef_h(s, C_MINV4A, -1.0 / (4.0 * A));
+  set_coef_h(s, C_INV2A, 1.0 / (2.0 * A));
+  set_coef_h(s, C_INVA, 1.0 / A);
+  set_coef_h(s, C_INV4A, 1.0 / (4.0 * A));
+  set_coef_h(s, C_MINVA, -A);
+  set_coef_h(s, C_SCALE, 1.0);
+  set_coef_h(s, C_INVSCALE, 1.0);
+  s.tol2 = o.tol * o.tol;  // made absolute (x ||z||^2) on the device
+  s.delta2 = o.delta * o.delta;
+  s.max_iter = o.max_iter;
+  s.status = SYS_IDLE;
+  s.flags = FLAG_INIT;
+}
+
+cudaError_t upload_slots(Ctx* c, TileBase* T, const std::vector<int>& slots) {
+  for (int j : slots) {
+    cudaError_t e = cudaMemcpyAsync(T->st_d + j, T->st_h + j, sizeof(SysState), cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaMemcpyAsync(T->spec_d + j, T->spec_h + j, sizeof(NoiseSpec), cudaMemcpyHostToDevice, c->stream);
+    if (e) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t upload_vec(Ctx* c, TileBase* T) {
+  return cudaMemcpyAsync(T->vec_d, T->vec_h, sizeof(int) * T->N, cudaMemcpyHostToDevice, c->stream);
+}
+
+}  // namespace
+
+int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpts& o, const QOut& out) {
+  const int N = T->N;
+  for (const QJob& q : jobs)
+    if ((int)q.sys.size() > N) return c->fail(1, "a group of systems does not fit in one tile");
+  const int np = out.plist ? (int)out.plist->size() : 0;
+  const size_t vlen = (size_t)c->g.V * 24;
+
+  struct Slot {
+    int job = -1, member = -1, phase = 0;
+    bool done = false;
+  };
+  std::vector<Slot> slot(N);
+  std::vector<int> free_slots;
+  for (int j = N - 1; j >= 0; j--) free_slots.push_back(j);
+  std::vector<int> remaining(jobs.size(), 0);  // members not yet in their final state
+  size_t next = 0, finished = 0;
+  cudaError_t e;
+  const int every = std::max(1, o.check_every);
+  long long iters_run = 0;
+  // every system stops at max_iter (FLAG_FINAL); a follow-up solve doubles that
+  const long long bound = ((long long)o.max_iter * 2 + 64) * (long long)(jobs.size() + 1);
+
+  // The host mirrors st_h / spec_h / vec_h are pinned and uploaded asynchronously: the host
+  // must not write them again until the copies that read them have executed. Every batch
+  // of uploads records `fence`; every host write waits on it first.
+  cudaEvent_t fence;
+  if ((e = cudaEventCreateWithFlags(&fence, cudaEventDisableTiming))) return c->cuda_fail(e, "event");
+  struct FenceGuard {
+    cudaEvent_t ev;
+    ~FenceGuard() { cudaEventDestroy(ev); }
+  } fence_guard{fence};
+  bool fence_pending = false;
+  auto mark = [&]() -> cudaError_t {
+    fence_pending = true;
+    return cudaEventRecord(fence, c->stream);
+  };
+  auto wait_fence = [&]() -> cudaError_t {
+    if (!fence_pending) return cudaSuccess;
+    fence_pending = false;
+    return cudaEventSynchronize(fence);
+  };
+
+  auto admit_rhs = [&](const std::vector<int>& adm, bool any_vec, bool any_noise) -> int {
+    if ((e = upload_slots(c, T, adm))) return c->cuda_fail(e, "upload slot state");
+    if (any_vec && (e = upload_vec(c, T))) return c->cuda_fail(e, "upload vector map");
+    if ((e = mark())) return c->cuda_fail(e, "upload fence");
+    if (any_vec && (e = T->enqueue_rhs_from_canon(c->canon_d))) return c->cuda_fail(e, "pack right-hand sides");
+    if (any_noise && (e = T->enqueue_noise())) return c->cuda_fail(e, "noise");
+    if ((e = T->enqueue_init())) return c->cuda_fail(e, "solver initialisation");
+    return 0;
+  };
+
+  while (finished < jobs.size()) {
+    if ((e = wait_fence())) return c->cuda_fail(e, "upload fence");
+    // ---- admit whole groups into free slots
+    std::vector<int> adm;
+    bool any_vec = false, any_noise = false;
+    for (int j = 0; j < N; j++) T->vec_h[j] = -1;
+    while (next < jobs.size() && free_slots.size() >= jobs[next].sys.size()) {
+      const QJob& q = jobs[next];
+      remaining[next] = (int)q.sys.size();
+      for (size_t k = 0; k < q.sys.size(); k++) {
+        const int j = free_slots.back();
+        free_slots.pop_back();
+        slot[j] = Slot{(int)next, (int)k, 0, false};
+        const SysSpec& sp = q.sys[k];
+        init_state(T->st_h[j], sp.sigma, o);
+        T->spec_h[j] = sp.noise;
+        if (sp.rhs_kind == 0) {
+          T->spec_h[j].flags |= NOISE_RHS;
+          any_noise = true;
+        } else {
+          T->vec_h[j] = sp.vec;
+          any_vec = true;
+        }
+        adm.push_back(j);
+      }
+      next++;
+    }
+    if (!adm.empty())
+      if (int rc = admit_rhs(adm, any_vec, any_noise)) return rc;
+
+    // ---- iterate
+    for (int k = 0; k < every; k++)
+      if ((e = T->enqueue_iter())) return c->cuda_fail(e, "solver iteration");
+    iters_run += every;
+    if ((e = cudaMemcpyAsync(T->st_h, T->st_d, sizeof(SysState) * N, cudaMemcpyDeviceToHost, c->stream)))
+      return c->cuda_fail(e, "download system state");
+    if ((e = cudaStreamSynchronize(c->stream))) return c->cuda_fail(e, "solver iteration");
+    if (iters_run > bound) return c->fail(6, "solver did not terminate within its iteration bound");
+
+    // ---- find finished systems
+    std::vector<int> chain_slots;
+    std::vector<int> done_jobs;
+    for (int j = 0; j < N; j++) {
+      Slot& sl = slot[j];
+      if (sl.job < 0 || sl.done) continue;
+      const SysState& s = T->st_h[j];
+      if (s.status != SYS_CONVERGED && s.status != SYS_NOCONV) continue;
+      const QJob& q = jobs[sl.job];
+      const bool has_chain = !q.chain.empty() && !std::isnan(q.chain[sl.member]);
+      if (s.status != SYS_CONVERGED && out.noconv) *out.noconv = 1;
+      if (sl.phase == 0 && has_chain) {
+        chain_slots.push_back(j);
+        continue;
+      }
+      sl.done = true;
+      if (--remaining[sl.job] == 0) done_jobs.push_back(sl.job);
+    }
+    if (chain_slots.empty() && done_jobs.empty()) continue;
+
+    // ---- harvest: reconstruct the odd sites (and verify) of every slot leaving its phase
+    std::vector<int> harvest = chain_slots;
+    for (int j = 0; j < N; j++)
+      if (slot[j].job >= 0 && slot[j].done &&
+          std::find(done_jobs.begin(), done_jobs.end(), slot[j].job) != done_jobs.end())
+        harvest.push_back(j);
+    for (int j : harvest) T->st_h[j].flags |= FLAG_HARVEST;
+    if ((e = upload_slots(c, T, harvest))) return c->cuda_fail(e, "upload harvest flags");
+    if ((e = T->enqueue_recon())) return c->cuda_fail(e, "reconstruct odd sites");
+    if (o.verify && (e = T->enqueue_verify())) return c->cuda_fail(e, "verify residual");
+    if ((e = cudaMemcpyAsync(T->st_h, T->st_d, sizeof(SysState) * N, cudaMemcpyDeviceToHost, c->stream)))
+      return c->cuda_fail(e, "download system state");
+    if ((e = cudaStreamSynchronize(c->stream))) return c->cuda_fail(e, "harvest");
+
+    // statistics of every harvested phase
+    for (int j : harvest) {
+      const QJob& q = jobs[slot[j].job];
+      const std::vector<int>& si = slot[j].phase == 0 ? q.stat_index : q.stat_index2;
+      if (out.states && !si.empty() && si[slot[j].member] >= 0) (*out.states)[si[slot[j].member]] = T->st_h[j];
+    }
+
+    // contractions of the completed groups
+    if (out.result && np > 0 && !done_jobs.empty()) {
+      std::vector<ContractPair> pairs;
+      for (int g : done_jobs) {
+        std::vector<int> member_slot(jobs[g].sys.size(), -1);
+        for (int j = 0; j < N; j++)
+          if (slot[j].job == g) member_slot[slot[j].member] = j;
+        for (ContractPair p : jobs[g].pairs) {
+          p.right = member_slot[p.right];
+          p.left = member_slot[p.left];
+          pairs.push_back(p);
+        }
+      }
+      if (!pairs.empty()) {
+        std::vector<double> part;
+        if (int rc = contract_tile(c, T, pairs, out.gamma, *out.plist, part, out.rows)) return rc;
+        for (const ContractPair& p : pairs)
+          for (int q2 = 0; q2 < np * 2; q2++)
+            (*out.result)[(size_t)p.out * np * 2 + q2] = part[(size_t)p.out * np * 2 + q2];
+      }
+    }
+
+    // solution vectors requested by the caller
+    if (out.x_host) {
+      std::vector<std::pair<int, int>> copies;  // slot, output index
+      for (int j = 0; j < N; j++) T->vec_h[j] = -1;
+      int used = 0;
+      for (int j : harvest) {
+        if (slot[j].phase != 0 || std::find(chain_slots.begin(), chain_slots.end(), j) != chain_slots.end())
+          continue;
+        const QJob& q = jobs[slot[j].job];
+        if (q.out_index.empty() || q.out_index[slot[j].member] < 0) continue;
+        T->vec_h[j] = out.canon_out_base + used;
+        copies.push_back({used, q.out_index[slot[j].member]});
+        used++;
+      }
+      if (used) {
+        if ((e = upload_vec(c, T))) return c->cuda_fail(e, "upload vector map");
+        if ((e = T->enqueue_solution_to_canon(c->canon_d))) return c->cuda_fail(e, "unpack solutions");
+        for (auto& cp : copies) {
+          e = cudaMemcpyAsync(out.x_host + (size_t)cp.second * vlen,
+                              c->canon_d + (size_t)(out.canon_out_base + cp.first) * vlen, vlen * sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream);
+          if (e) return c->cuda_fail(e, "download solutions");
+        }
+        if ((e = cudaStreamSynchronize(c->stream))) return c->cuda_fail(e, "download solutions");
+      }
+    }
+
+    // release the slots of completed groups
+    std::vector<int> released;
+    for (int g : done_jobs) {
+      for (int j = 0; j < N; j++) {
+        if (slot[j].job != g) continue;
+        memset(&T->st_h[j], 0, sizeof(SysState));
+        memset(&T->spec_h[j], 0, sizeof(NoiseSpec));
+        slot[j] = Slot{};
+        free_slots.push_back(j);
+        released.push_back(j);
+      }
+      finished++;
+    }
+    if (!released.empty()) {
+      if ((e = upload_slots(c, T, released))) return c->cuda_fail(e, "release slots");
+      if ((e = mark())) return c->cuda_fail(e, "upload fence");
+    }
+
+    // follow-up solves: the phase-0 solution becomes the right-hand side of the same slot
+    if (!chain_slots.empty()) {
+      if ((e = wait_fence())) return c->cuda_fail(e, "upload fence");
+      for (int j = 0; j < N; j++) T->vec_h[j] = -1;
+      for (int j : chain_slots) T->vec_h[j] = out.canon_chain_base + j;
+      if ((e = upload_vec(c, T))) return c->cuda_fail(e, "upload vector map");
+      if ((e = T->enqueue_solution_to_canon(c->canon_d))) return c->cuda_fail(e, "stage follow-up rhs");
+      // the map upload above must land before the host reuses vec_h (same map, re-sent below)
+      if ((e = cudaStreamSynchronize(c->stream))) return c->cuda_fail(e, "stage follow-up rhs");
+      for (int j : chain_slots) {
+        const QJob& q = jobs[slot[j].job];
+        const NoiseSpec keep = T->spec_h[j];
+        init_state(T->st_h[j], q.chain[slot[j].member], o);
+        T->spec_h[j] = keep;
+        T->spec_h[j].flags &= ~(uint32_t)NOISE_RHS;  // the noise stays the contraction's left vector
+        slot[j].phase = 1;
+      }
+      if (int rc = admit_rhs(chain_slots, true, false)) return rc;
+    }
+  }
+  return 0;
+}
+
+}  // namespace fs

@@ -3,10 +3,15 @@
 #include "fs_engine.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
 namespace fs {
+
+static std::atomic<long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 Shape make_shape(int N, int Vh) {
   Shape s;
@@ -88,6 +93,10 @@ class Tile : public TileBase {
   Ctx* c = nullptr;
   Shape sh{};
   Launch L{};
+  Shape sh1{};   // system-major: a block covers 256 sites of ONE system (uniform per-block masks)
+  Launch L1{};
+  Launch LH{};   // hopping kernels: one site chunk per block, so resident blocks sweep the
+                 // lattice in order and neighbour spinors are re-read from L2, not DRAM
   int ngroups = 0;
   double *bhat = nullptr, *r_hi = nullptr, *tmp64 = nullptr;
   void *x_lo = nullptr, *r = nullptr, *rhat = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr,
@@ -117,6 +126,16 @@ class Tile : public TileBase {
     nr = nr_;
     sh = make_shape(N, c->g.Vh);
     L = c->launch_for(sh);
+    sh1 = sh;
+    sh1.NB = 1;
+    sh1.SB = 256;
+    sh1.nchunk = (c->g.Vh + 255) / 256;
+    L1.grid_y = N;
+    L1.block = 256;
+    L1.grid_x = std::min(sh1.nchunk, std::max(1, 4 * c->nsm));
+    L1.stream = c->stream;
+    LH = L;
+    LH.grid_x = sh.nchunk;
     ngroups = c->g.Vh / 8;
     const size_t f64 = (size_t)24 * c->g.Vh * N * sizeof(double);
     const size_t fts = (size_t)24 * c->g.Vh * N * sizeof(Ts);
@@ -146,19 +165,19 @@ class Tile : public TileBase {
   }
 
   HopArgs hop(void* out, const void* in, const void* X, const void* Y, const void* R, double* part, int p_out,
-              int mask, bool gated, bool hi) {
+              int mask, bool gated, bool hi, bool sysmajor = false) {
     HopArgs a{};
     a.out = out; a.in = in; a.X = X; a.Y = Y; a.R = R;
     a.gauge = hi ? c->gauge64 : c->gauge_for(prec, nr);
     a.st = st_d; a.partial = part; a.gate = gated ? gate : nullptr; a.work = nullptr;
-    a.g = c->g; a.sh = sh; a.p_out = p_out; a.mask = mask;
+    a.g = c->g; a.sh = sysmajor ? sh1 : sh; a.p_out = p_out; a.mask = mask;
     return a;
   }
-  BlasArgs blas(int mask, const double* src, double* part, bool gated) {
+  BlasArgs blas(int mask, const double* src, double* part, bool gated, bool sysmajor = false) {
     BlasArgs b{};
     b.x_lo = x_lo; b.r = r; b.rhat = rhat; b.p = p; b.v = v; b.s = s; b.t = t;
     b.x_hi = x_hi; b.src = src; b.st = st_d; b.partial = part; b.gate = gated ? gate : nullptr;
-    b.Vh = c->g.Vh; b.sh = sh; b.mask = mask;
+    b.Vh = c->g.Vh; b.sh = sysmajor ? sh1 : sh; b.mask = mask;
     return b;
   }
   cudaError_t fin(int op, int mask, const double* a_, const double* b_ = nullptr, const double* c_ = nullptr) {
@@ -169,13 +188,15 @@ class Tile : public TileBase {
     f.nreal = 24.0 * c->g.Vh;
     f.max_restarts = 8;
     fin_kernel<<<N, 256, 0, c->stream>>>(f, op);
+    note_launch();
     return cudaGetLastError();
   }
 
   // Timed hop launch in the inner precision (the kernel the roofline is about).
   cudaError_t hop_lo(int coef, int dot, const HopArgs& a, int nextra) {
     HopProfile& pf = c->prof;
-    if (!pf.enabled) return launch_hop<Ts>(coef, dot, nr, a, L);
+    LH.stream = c->stream;
+    if (!pf.enabled) return launch_hop<Ts>(coef, dot, nr, a, LH);
     cudaEvent_t e0, e1;
     if (!pf.pool.empty()) {
       e0 = pf.pool.back().first; e1 = pf.pool.back().second; pf.pool.pop_back();
@@ -185,7 +206,7 @@ class Tile : public TileBase {
     HopArgs b = a;
     b.work = pf.work_d + prec * 3 + nextra;
     cudaEventRecord(e0, c->stream);
-    cudaError_t e = launch_hop<Ts>(coef, dot, nr, b, L);
+    cudaError_t e = launch_hop<Ts>(coef, dot, nr, b, LH);
     cudaEventRecord(e1, c->stream);
     pf.pending.push_back({e0, e1});
     pf.launches += 1;
@@ -199,17 +220,27 @@ class Tile : public TileBase {
     return launch_pack<double>(z_e, z_o, canon, vec_d, c->g, sh, L);
   }
 
+  cudaError_t enqueue_noise() override {
+    L1.stream = c->stream;
+    noise_kernel<<<dim3(std::min(2 * sh1.nchunk, 2 * L1.grid_x), N), 256, 0, c->stream>>>(z_e, z_o, spec_d, st_d,
+                                                                                      c->g, sh1);
+    note_launch();
+    return cudaGetLastError();
+  }
+
+  // Initialisation of the INIT slots; FP64 work on the system-major shape so that
+  // refilling a few slots costs only their own systems.
   cudaError_t enqueue_init() override {
-    L.stream = c->stream;
+    L1.stream = c->stream;
     cudaError_t e;
     // bhat_e = z_e - D_eo A^-1 z_o, ||bhat||^2
     if ((e = launch_hop<double>(COEF_PREP, DOT_NORM, 18, hop(bhat, z_o, z_e, nullptr, nullptr, pa, 0, MASK_INIT,
-                                                              false, true), L))) return e;
-    if ((e = launch_blas<Ts>(OP_NORM64, blas(MASK_INIT, z_e, pb, false), L))) return e;
-    if ((e = launch_blas<Ts>(OP_NORM64, blas(MASK_INIT, z_o, pc, false), L))) return e;
-    if ((e = launch_blas<Ts>(OP_ZEROX, blas(MASK_INIT, nullptr, nullptr, false), L))) return e;
+                                                              false, true, true), L1))) return e;
+    if ((e = launch_blas<Ts>(OP_NORM64, blas(MASK_INIT, z_e, pb, false, true), L1))) return e;
+    if ((e = launch_blas<Ts>(OP_NORM64, blas(MASK_INIT, z_o, pc, false, true), L1))) return e;
+    if ((e = launch_blas<Ts>(OP_ZEROX, blas(MASK_INIT, nullptr, nullptr, false, true), L1))) return e;
     if ((e = fin(FIN_NORM, MASK_INIT, pa, pb, pc))) return e;
-    if ((e = launch_blas<Ts>(OP_SETR, blas(MASK_INIT, bhat, pa, false), L))) return e;
+    if ((e = launch_blas<Ts>(OP_SETR, blas(MASK_INIT, bhat, pa, false, true), L1))) return e;
     return fin(FIN_INIT, MASK_INIT, pa);
   }
 
@@ -230,34 +261,38 @@ class Tile : public TileBase {
     if ((e = fin(FIN_OMEGA, MASK_ACTIVE, pa))) return e;
     if ((e = launch_blas<Ts>(OP_XR, blas(MASK_ACTIVE, nullptr, pa, false), L))) return e;
     if ((e = fin(FIN_RHO, MASK_ACTIVE, pa))) return e;
-    // reliable update (only systems flagged by FIN_RHO; the gated kernels return at once otherwise)
-    if ((e = launch_blas<Ts>(OP_ACCX, blas(MASK_UPDATE, nullptr, nullptr, true), L))) return e;
+    // Reliable update of the systems flagged by FIN_RHO, in FP64. These kernels use the
+    // system-major shape: a block serves one system, so unflagged systems cost one flag
+    // read per block instead of occupying FP64 issue slots inside mixed warps.
+    L1.stream = c->stream;
+    if ((e = launch_blas<Ts>(OP_ACCX, blas(MASK_UPDATE, nullptr, nullptr, true, true), L1))) return e;
     if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
-                                hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, MASK_UPDATE, true, true), L)))
+                                hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, MASK_UPDATE, true, true,
+                                    true), L1)))
       return e;
     if ((e = launch_hop<double>(COEF_TRUERES, DOT_NORM, 18,
-                                hop(r_hi, tmp64, x_hi, bhat, nullptr, pa, 0, MASK_UPDATE, true, true), L)))
+                                hop(r_hi, tmp64, x_hi, bhat, nullptr, pa, 0, MASK_UPDATE, true, true, true), L1)))
       return e;
     if ((e = fin(FIN_TRUE, MASK_UPDATE, pa))) return e;
-    if ((e = launch_blas<Ts>(OP_SETR, blas(MASK_UPDATE, r_hi, pa, true), L))) return e;
+    if ((e = launch_blas<Ts>(OP_SETR, blas(MASK_UPDATE, r_hi, pa, true, true), L1))) return e;
     return fin(FIN_UPDATE, MASK_UPDATE, pa);
   }
 
   cudaError_t enqueue_recon() override {
-    L.stream = c->stream;
+    L1.stream = c->stream;
     // x_o = A^-1 (z_o - D_oe x_e)
     return launch_hop<double>(COEF_RECON, DOT_NONE, 18,
-                              hop(x_o, x_hi, z_o, nullptr, nullptr, nullptr, 1, MASK_HARVEST, false, true), L);
+                              hop(x_o, x_hi, z_o, nullptr, nullptr, nullptr, 1, MASK_HARVEST, false, true, true), L1);
   }
 
   cudaError_t enqueue_verify() override {
-    L.stream = c->stream;
+    L1.stream = c->stream;
     cudaError_t e;
     if ((e = launch_hop<double>(COEF_FULLRES, DOT_NORM, 18,
-                                hop(r_hi, x_o, x_hi, z_e, nullptr, pa, 0, MASK_HARVEST, false, true), L)))
+                                hop(r_hi, x_o, x_hi, z_e, nullptr, pa, 0, MASK_HARVEST, false, true, true), L1)))
       return e;
     if ((e = launch_hop<double>(COEF_FULLRES, DOT_NORM, 18,
-                                hop(tmp64, x_hi, x_o, z_o, nullptr, pb, 1, MASK_HARVEST, false, true), L)))
+                                hop(tmp64, x_hi, x_o, z_o, nullptr, pb, 1, MASK_HARVEST, false, true, true), L1)))
       return e;
     return fin(FIN_VERIFY, MASK_HARVEST, pa, pb);
   }
@@ -311,91 +346,6 @@ TileBase* Ctx::tile(int prec, int N, int nr) {
   return raw;
 }
 
-static void set_coef_h(SysState& s, int k, double v) {
-  s.cd[k] = v;
-  s.cf[k] = (float)v;
-}
-
-int solve_tile(Ctx* c, TileBase* T, const SysSpec* specs, int n, const SolveOpts& o) {
-  if (n > T->N) return c->fail(1, "internal: batch larger than tile");
-  bool any_vec = false, any_noise = false;
-  for (int j = 0; j < T->N; j++) {
-    SysState& s = T->st_h[j];
-    memset(&s, 0, sizeof(SysState));
-    NoiseSpec& ns = T->spec_h[j];
-    memset(&ns, 0, sizeof(NoiseSpec));
-    T->vec_h[j] = -1;
-    if (j >= n) continue;
-    const double A = 4.0 + o.m + specs[j].sigma;
-    s.sigma = specs[j].sigma;
-    s.A = A;
-    s.inv4A = 1.0 / (4.0 * A);
-    set_coef_h(s, C_A, A);
-    set_coef_h(s, C_MINV4A, -1.0 / (4.0 * A));
-    set_coef_h(s, C_INV2A, 1.0 / (2.0 * A));
-    set_coef_h(s, C_INVA, 1.0 / A);
-    set_coef_h(s, C_INV4A, 1.0 / (4.0 * A));
-    set_coef_h(s, C_MINVA, -A);
-    set_coef_h(s, C_SCALE, 1.0);
-    set_coef_h(s, C_INVSCALE, 1.0);
-    s.tol2 = o.tol * o.tol;  // made absolute (x ||z||^2) on the device
-    s.delta2 = o.delta * o.delta;
-    s.max_iter = o.max_iter;
-    s.status = SYS_IDLE;
-    s.flags = FLAG_INIT;
-    ns = specs[j].noise;
-    if (specs[j].rhs_kind == 0) {
-      ns.flags |= NOISE_RHS;
-      any_noise = true;
-    } else {
-      T->vec_h[j] = specs[j].vec;
-      any_vec = true;
-    }
-  }
-  cudaStream_t st = c->stream;
-  cudaError_t e;
-  if ((e = cudaMemcpyAsync(T->st_d, T->st_h, sizeof(SysState) * T->N, cudaMemcpyHostToDevice, st)))
-    return c->cuda_fail(e, "upload system state");
-  if ((e = cudaMemcpyAsync(T->spec_d, T->spec_h, sizeof(NoiseSpec) * T->N, cudaMemcpyHostToDevice, st)))
-    return c->cuda_fail(e, "upload noise specs");
-  if ((e = cudaMemcpyAsync(T->vec_d, T->vec_h, sizeof(int) * T->N, cudaMemcpyHostToDevice, st)))
-    return c->cuda_fail(e, "upload vector map");
-  const Shape sh = make_shape(T->N, c->g.Vh);
-  Launch L = c->launch_for(sh);
-  if (any_vec && (e = T->enqueue_rhs_from_canon(c->canon_d))) return c->cuda_fail(e, "pack right-hand sides");
-  if (any_noise) {
-    noise_kernel<<<dim3(std::min(2 * sh.nchunk, L.grid_x * 2), L.grid_y), L.block, 0, st>>>(
-        T->z_e, T->z_o, T->spec_d, T->st_d, c->g, sh);
-    if ((e = cudaGetLastError())) return c->cuda_fail(e, "noise kernel");
-  }
-  if ((e = T->enqueue_init())) return c->cuda_fail(e, "solver initialisation");
-
-  const int every = std::max(1, o.check_every);
-  long long guard = 0;
-  const long long guard_max = (long long)o.max_iter * 4 + 64;  // every system stops at max_iter (FLAG_FINAL)
-  while (true) {
-    for (int k = 0; k < every; k++)
-      if ((e = T->enqueue_iter())) return c->cuda_fail(e, "solver iteration");
-    guard += every;
-    if ((e = cudaMemcpyAsync(T->st_h, T->st_d, sizeof(SysState) * T->N, cudaMemcpyDeviceToHost, st)))
-      return c->cuda_fail(e, "download system state");
-    if ((e = cudaStreamSynchronize(st))) return c->cuda_fail(e, "solver iteration");
-    int busy = 0;
-    for (int j = 0; j < n; j++) busy += (T->st_h[j].status == SYS_ACTIVE || (T->st_h[j].flags & FLAG_INIT));
-    if (!busy) break;
-    if (guard > guard_max) return c->fail(6, "solver did not terminate within its iteration bound");
-  }
-  for (int j = 0; j < n; j++) T->st_h[j].flags |= FLAG_HARVEST;
-  if ((e = cudaMemcpyAsync(T->st_d, T->st_h, sizeof(SysState) * T->N, cudaMemcpyHostToDevice, st)))
-    return c->cuda_fail(e, "upload harvest flags");
-  if ((e = T->enqueue_recon())) return c->cuda_fail(e, "reconstruct odd sites");
-  if (o.verify && (e = T->enqueue_verify())) return c->cuda_fail(e, "verify residual");
-  if ((e = cudaMemcpyAsync(T->st_h, T->st_d, sizeof(SysState) * T->N, cudaMemcpyDeviceToHost, st)))
-    return c->cuda_fail(e, "download system state");
-  if ((e = cudaStreamSynchronize(st))) return c->cuda_fail(e, "harvest");
-  return 0;
-}
-
 int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, const double* gamma,
                   const std::vector<int>& plist, std::vector<double>& result, int rows) {
   const int np = (int)plist.size();
@@ -432,10 +382,12 @@ int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, c
   if (!e) e = cudaMemsetAsync(res, 0, res_n * sizeof(double), c->stream);
   if (!e) {
     contract_kernel<<<dim3(a.nblk, npairs), 256, 0, c->stream>>>(a);
+    note_launch();
     e = cudaGetLastError();
   }
   if (!e) {
     contract_finalize<<<npairs * np, 256, 0, c->stream>>>(part, pr, res, np, a.nblk);
+    note_launch();
     e = cudaGetLastError();
   }
   result.assign(res_n, 0.0);
@@ -449,6 +401,7 @@ int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, c
 // entry points used by the API translation unit
 cudaError_t launch_noise_codes(uint8_t* codes, NoiseSpec n, int V, cudaStream_t s) {
   noise_codes_kernel<<<(V + 255) / 256, 256, 0, s>>>(codes, n, V);
+  note_launch();
   return cudaGetLastError();
 }
 

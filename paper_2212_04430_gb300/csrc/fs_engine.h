@@ -76,6 +76,7 @@ class TileBase {
   double* x_o = nullptr;     // solution, odd sites (FP64, after reconstruction)
   virtual int alloc(Ctx* c, int N, int nr) = 0;
   virtual cudaError_t enqueue_rhs_from_canon(const double* canon) = 0;  // z <- canon[vec[j]] for INIT slots
+  virtual cudaError_t enqueue_noise() = 0;  // z <- Z4 noise for INIT slots with a noise rhs
   virtual cudaError_t enqueue_init() = 0;
   virtual cudaError_t enqueue_iter() = 0;
   virtual cudaError_t enqueue_recon() = 0;
@@ -115,12 +116,12 @@ struct Ctx {
   size_t device_bytes() const;
 };
 
-// Solve a list of systems in one tile (tile-synchronous: returns when all are done).
+// One system to solve.
 struct SysSpec {
   double sigma;
-  int rhs_kind;        // 0: Z4 noise, 1: canonical vector vec (device staging)
-  int vec;             // canonical vector index for rhs_kind 1 (also output index)
-  NoiseSpec noise;     // noise identity (used for the right-hand side and contractions)
+  int rhs_kind;        // 0: Z4 noise, 1: canonical vector `vec` (device staging)
+  int vec;             // canonical vector index for rhs_kind 1
+  NoiseSpec noise;     // noise identity (the right-hand side and/or the contraction's left vector)
 };
 
 struct SolveOpts {
@@ -134,13 +135,39 @@ struct SolveOpts {
   int check_every;
 };
 
-int solve_tile(Ctx* c, TileBase* T, const SysSpec* specs, int n, const SolveOpts& o);
+// A group of systems whose solutions are contracted together (they share the tile
+// until all of them have converged).
+struct QJob {
+  std::vector<SysSpec> sys;
+  std::vector<double> chain;           // per system: NaN = none, else the follow-up shift
+  std::vector<ContractPair> pairs;     // right / left are group-local; out is a global result row
+  std::vector<int> stat_index;         // per system: stats row of its (first) solve, -1 none
+  std::vector<int> stat_index2;        // per system: stats row of the follow-up solve
+  std::vector<int> out_index;          // per system: host output vector index (-1 none)
+};
+
+struct QOut {
+  const double* gamma = nullptr;
+  const std::vector<int>* plist = nullptr;
+  int rows = 0;
+  std::vector<double>* result = nullptr;    // [rows][np][2]
+  std::vector<SysState>* states = nullptr;
+  int* noconv = nullptr;
+  double* x_host = nullptr;                 // solutions, [out_index][V][24]
+  int canon_out_base = 0;                   // staging vectors [base, base + N) for outputs
+  int canon_chain_base = 0;                 // staging vectors [base, base + N) for follow-up rhs
+};
+
+// Continuous batching of the jobs over the slots of tile T (fs_driver.cu).
+int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpts& o, const QOut& out);
 
 // Contractions over the solutions held in a tile.
 int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, const double* gamma,
                   const std::vector<int>& plist, std::vector<double>& result /* [rows][np][2] */, int rows);
 
 double* pinned_alloc(size_t bytes);
+void note_launch(int n = 1);          // library-wide count of kernel launches
+long long launch_count();
 cudaError_t launch_noise_codes(uint8_t* codes, NoiseSpec n, int V, cudaStream_t s);
 
 }  // namespace fs

@@ -16,6 +16,7 @@ cudaError_t launch_hop(int coef, int dot, int nr, const HopArgs& a, const Launch
 #define FS_HOP(C, D, R)                                                  \
   if (coef == C && dot == D && nr == R) {                                \
     hop_kernel<Ts, Tg, Tm, R, C, D><<<grid, block, 0, l.stream>>>(a);    \
+    note_launch();                                                       \
     return cudaGetLastError();                                           \
   }
   if constexpr (std::is_same<Ts, double>::value) {
@@ -56,6 +57,7 @@ cudaError_t launch_blas(int op, const BlasArgs& a, const Launch& l) {
     case OP_NORM64: blas_kernel<Ts, Tx, Tm, OP_NORM64><<<grid, block, 0, l.stream>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -63,6 +65,7 @@ template <typename Ts>
 cudaError_t launch_pack(void* fe, void* fo, const double* canon, const int* vec, const Geom& g, const Shape& sh,
                         const Launch& l) {
   pack_kernel<Ts><<<dim3(l.grid_x, l.grid_y), l.block, 0, l.stream>>>(fe, fo, canon, vec, g, sh);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -70,6 +73,7 @@ template <typename Ts>
 cudaError_t launch_unpack(double* canon, const void* fe, const void* fo, const int* vec, const Geom& g,
                           const Shape& sh, const Launch& l) {
   unpack_kernel<Ts><<<dim3(l.grid_x, l.grid_y), l.block, 0, l.stream>>>(canon, fe, fo, vec, g, sh);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -80,6 +84,7 @@ cudaError_t launch_gauge_pack(void* out, const double* canon, const Geom& g, int
   if (nr == 18) gauge_pack_kernel<Tg, 18><<<blocks, 256, 0, s>>>(out, canon, g);
   else if (nr == 12) gauge_pack_kernel<Tg, 12><<<blocks, 256, 0, s>>>(out, canon, g);
   else return cudaErrorInvalidValue;
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -23,7 +23,7 @@ SYS_CONVERGED, SYS_NOCONV = 2, 3
 
 EXPORTS = ["fs_ctx_create", "fs_ctx_destroy", "fs_last_error", "fs_set_stream", "fs_ctx_device_bytes",
            "fs_set_gauge", "wilson_dslash", "shifted_solve", "mlmc_level_trace", "fs_mlmc_num_solves",
-           "variance_sample", "fs_noise_codes", "fs_profile_enable", "fs_profile_read"]
+           "variance_sample", "fs_noise_codes", "fs_profile_enable", "fs_profile_read", "fs_kernel_launches"]
 
 
 class FsError(RuntimeError):
@@ -81,6 +81,7 @@ def load_library(path=LIB_PATH):
         "fs_noise_codes": (I, [P, U64, U32, U32, U32, ctypes.POINTER(ctypes.c_uint8)]),
         "fs_profile_enable": (I, [P, I]),
         "fs_profile_read": (I, [P, ctypes.POINTER(ctypes.c_longlong), dp, dp]),
+        "fs_kernel_launches": (ctypes.c_longlong, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -253,6 +254,11 @@ class Context:
         by = ctypes.c_double()
         self._check(self.lib.fs_profile_read(self.h, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
         return {"launches": n.value, "ms": ms.value, "bytes": by.value}
+
+
+def fs_kernel_launches():
+    """Kernels launched by the library in this process so far."""
+    return int(load_library().fs_kernel_launches())
 
 
 def _stats(s):

@@ -13,10 +13,16 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "fsmlmc.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"^\s*#.*$", "", src, flags=re.M)
+    src = re.sub(r"\{[^{}]*\}", ";", src)  # drop struct / enum bodies
     names = set()
-    for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**([A-Za-z_][A-Za-z0-9_]*)\s*\(",
-                         src, flags=re.M):
-        names.add(m.group(1))
+    for stmt in src.split(";"):
+        stmt = " ".join(stmt.split())
+        if "(" not in stmt or stmt.startswith(("typedef", "enum", "struct", "extern")):
+            continue
+        m = re.match(r"^[A-Za-z_][A-Za-z0-9_ ]*?[\s*]+([A-Za-z_][A-Za-z0-9_]*)\s*\(", stmt)
+        if m:
+            names.add(m.group(1))
     return sorted(names)
 
 

@@ -245,3 +245,39 @@ def test_variance_sample_parity(prec, tol):
     assert np.all(np.abs(out["VL"] - ref["VL"]) <= 10 * tol * m2a)
     assert np.all(np.abs(out["Vbar"] - ref["Vbar"]) <= 10 * tol * m2b + 1e-300)
     ctx.close()
+
+
+# ---------------------------------------------------------------- batching invariance
+@pytest.mark.parametrize("prec", ["f64", "f16"])
+def test_results_identical_alone_and_in_a_mix(prec):
+    """A level sample solved alone (1-system tile) equals the same sample solved inside a
+    32-system tile with continuous slot refill: per-system kernels and fixed-order
+    reductions make every system independent of its neighbours and its slot."""
+    dims = (4, 4, 4, 8)
+    u = inputs.gauge_field(dims, "smooth", seed=21, eps=0.4)
+    sig = [0.01, 0.1, 0.6]
+    g = pkg.gamma_matrix("g3")
+    ctx = make_ctx(dims, u)
+    kw = dict(prec=prec, tol=1e-10 if prec == "f64" else 1e-8)
+    mix = ctx.mlmc_level_trace(-0.3, sig, g, 1, [20, 20, 20], seed=5, job=9, rhs_tile=32, **kw)
+    alone = ctx.mlmc_level_trace(-0.3, sig, g, 1, [1, 1, 1], seed=5, job=9, rhs_tile=1, **kw)
+    for lev in range(3):
+        assert mix["samples"][lev][0] == alone["samples"][lev][0], (lev, mix["samples"][lev][0],
+                                                                  alone["samples"][lev][0])
+    ctx.close()
+
+
+def test_product_chain_and_split_even_in_mixed_tiles():
+    """Nested (product) and paired (split-even) systems with refill in a small tile."""
+    dims = (4, 4, 2, 4)
+    u = inputs.gauge_field(dims, "smooth", seed=13, eps=0.5)
+    sig = [0.0, 0.05, 0.3]
+    n = [9, 7, 5]
+    ctx = make_ctx(dims, u)
+    for est in ("product", "split_even"):
+        out = ctx.mlmc_level_trace(-0.25, sig, pkg.gamma_matrix("g4"), 1, n, seed=8, job=2, estimator=est,
+                                   prec="f64", tol=1e-12, rhs_tile=3)
+        ref = _oracle_levels(u, -0.25, sig, odirac.GAMMA[3], 1, n, 8, 2, dims, oest.ESTIMATORS[est])
+        for lev in range(3):
+            assert sample_err(out["samples"][lev], ref[lev]) < 1e-9, (est, lev)
+    ctx.close()
