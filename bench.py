@@ -32,12 +32,12 @@ METRIC = "shifted Wilson solves/s at 1e-8 resid; dslash HBM GB/s vs peak; p50/p9
 
 WORKLOADS = {
     # the 16^3x32 FS-MLMC job (4 levels, 512 Z4 vectors per level in 32-system tiles)
-    "16x32": dict(dims=(16, 16, 16, 32), eps=0.4, gauge_seed=1003, noise_seed=2003, m=-0.35,
+    "16x32": dict(key="16x32", dims=(16, 16, 16, 32), eps=0.4, gauge_seed=1003, noise_seed=2003, m=-0.35,
                   sigmas=[0.005, 0.03, 0.15, 0.6], gamma="g3", p=4, vectors=32, tile=32, prec="f16",
                   link=12, tol=1e-8, estimator="diff",
                   name="16^3x32 Wilson FS-MLMC, 4 levels {0.005,0.03,0.15,0.6}, m=-0.35, eps=0.4, gamma3, p=4"),
     # the 8^4 FS-MLMC job (3 levels, 256 Z4 vectors per level in 16-system tiles)
-    "8x8": dict(dims=(8, 8, 8, 8), eps=0.3, gauge_seed=1002, noise_seed=2002, m=-0.2,
+    "8x8": dict(key="8x8", dims=(8, 8, 8, 8), eps=0.3, gauge_seed=1002, noise_seed=2002, m=-0.2,
                 sigmas=[0.02, 0.1, 0.5], gamma="g5g3", p=2, vectors=256, tile=16, prec="f32", link=18,
                 tol=1e-8, estimator="diff",
                 name="8^4 Wilson FS-MLMC, 3 levels {0.02,0.1,0.5}, m=-0.2, eps=0.3, gamma5 gamma3, p=2"),
@@ -188,7 +188,7 @@ def oracle_rate(w, budget_s, seed_level=0):
     dt = time.time() - t - t_apply  # bicgstab also applies A once for the final true residual
     per_iter = dt / iters
     with open(os.path.join(ROOT, "oracle", "baseline_iters.json")) as f:
-        cal = json.load(f)
+        cal = json.load(f)[w["key"]]
     sig = w["sigmas"]
     it = [cal["iters"][repr(s)] for s in sig]
     L = len(sig) - 1

@@ -6,9 +6,13 @@ iterations the oracle itself needs per solve of the same systems. This script
 computes those counts with the oracle only (full unpreconditioned BiCGStab to
 relative residual 1e-8) and stores them next to it.
 
-Workload: 16^3x32 lattice, smoothed links U = exp(i 0.4 H) (gauge seed 1003),
-m = -0.35, shifts {0.005, 0.03, 0.15, 0.6}, Z4 noise (seed 2003, job 0,
-level l, sample 0).
+Workloads (keys of the JSON file):
+  16x32  16^3x32, smoothed links U = exp(i 0.4 H) (gauge seed 1003), m = -0.35,
+         shifts {0.005, 0.03, 0.15, 0.6}, Z4 noise seed 2003
+  8x8    8^4, U = exp(i 0.3 H) (gauge seed 1002), m = -0.2, shifts {0.02, 0.1, 0.5},
+         Z4 noise seed 2002
+each solved for the noise vector (job 0, level l, sample 0).
+Usage: python oracle/baseline_iters.py [workload ...]
 """
 
 import json
@@ -24,25 +28,42 @@ sys.path.insert(0, os.path.dirname(HERE))
 import inputs  # noqa: E402
 from oracle import philox, solve  # noqa: E402
 
-DIMS = (16, 16, 16, 32)
-M = -0.35
-SIGMAS = [0.005, 0.03, 0.15, 0.6]
+WORKLOADS = {
+    "16x32": dict(dims=(16, 16, 16, 32), eps=0.4, gauge_seed=1003, noise_seed=2003, m=-0.35,
+                  sigmas=[0.005, 0.03, 0.15, 0.6]),
+    "8x8": dict(dims=(8, 8, 8, 8), eps=0.3, gauge_seed=1002, noise_seed=2002, m=-0.2, sigmas=[0.02, 0.1, 0.5]),
+}
+PATH = os.path.join(HERE, "baseline_iters.json")
 
 
-def main():
-    u = inputs.gauge_field(DIMS, "smooth", seed=1003, eps=0.4)
-    v = int(np.prod(DIMS))
-    out = {"workload": "16^3x32 eps=0.4 gauge_seed=1003 m=-0.35", "tol": 1e-8, "iters": {}, "seconds": {}}
-    for lev, s in enumerate(SIGMAS):
-        z = philox.z4_noise(v, 2003, 0, lev, 0)
+def calibrate(name):
+    w = WORKLOADS[name]
+    dims = w["dims"]
+    u = inputs.gauge_field(dims, "smooth", seed=w["gauge_seed"], eps=w["eps"])
+    v = int(np.prod(dims))
+    out = {"tol": 1e-8, "iters": {}, "seconds": {}}
+    for lev, s in enumerate(w["sigmas"]):
+        z = philox.z4_noise(v, w["noise_seed"], 0, lev, 0)
         t = time.time()
-        r = solve.shifted_solve(u, z, M, s, DIMS, -1, tol=1e-8, max_iter=20000)
+        r = solve.shifted_solve(u, z, w["m"], s, dims, -1, tol=1e-8, max_iter=20000)
         out["iters"][repr(s)] = int(r.iters)
         out["seconds"][repr(s)] = time.time() - t
-        print(s, r.iters, r.rel_resid, time.time() - t, flush=True)
-    with open(os.path.join(HERE, "baseline_iters.json"), "w") as f:
-        json.dump(out, f, indent=1)
+        print(name, s, r.iters, r.rel_resid, time.time() - t, flush=True)
+    return out
+
+
+def main(names):
+    data = {}
+    if os.path.exists(PATH):
+        with open(PATH) as f:
+            data = json.load(f)
+        if "iters" in data:  # single-workload layout of an earlier run
+            data = {"16x32": data}
+    for n in names:
+        data[n] = calibrate(n)
+    with open(PATH, "w") as f:
+        json.dump(data, f, indent=1)
 
 
 if __name__ == "__main__":
-    main()
+    main(sys.argv[1:] or sorted(WORKLOADS))

@@ -324,3 +324,222 @@ __global__ void __launch_bounds__(256, sizeof(Tm) == 8 ? 1 : (sizeof(Ts) == 2 ? 
 }
 
 }  // namespace fs
+
+namespace fs {
+
+// ---- prefetching variant --------------------------------------------------------
+// The eight neighbour spinors of a (site, system) are fetched with per-thread
+// asynchronous copies (cp.async.cg, 16 B each, L2 only) into a ring of PF shared
+// memory slots, PF directions ahead of the arithmetic; the epilogue operands X
+// and R follow the directions through the same ring. This keeps ~PF x 24 reals
+// of every thread in flight without holding them in registers. Each thread reads
+// back only what it copied, so the ring needs no block barrier.
+// Ring layout: [slot][16-byte chunk][thread] (conflict-free 128-bit LDS/STS).
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename Ts>
+__host__ __device__ constexpr int chunks16() { return 24 * (int)sizeof(Ts) / 16; }
+
+template <typename Ts, int PF>
+__host__ __device__ constexpr size_t hop_pf_smem(int block) {
+  return (size_t)PF * chunks16<Ts>() * block * 16;
+}
+
+// Links of a block's sites staged in shared memory as FP32 (reconstructed once per
+// link instead of once per thread) when a block covers few sites, i.e. many systems
+// per site: [site][direction][20 floats] (18 used, padded to 16-byte multiples).
+constexpr int LINK_STAGE_MAX_SITES = 32;
+constexpr int LINK_F32 = 20;
+
+template <typename Ts, typename Tg, typename Tm, int NR, int COEF, int DOT, int PF>
+__global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
+  constexpr int K = DotK<DOT>::K;
+  constexpr int CV = chunks16<Ts>();
+  constexpr int VW = Store<Ts>::VW;
+  // items: 0..7 neighbour spinors, 8 = X (epilogue axpy operand), 9 = R (dot partner)
+  constexpr bool HAS_X = COEF != COEF_PLAIN;
+  constexpr bool HAS_R = DOT == DOT_R;
+  constexpr int NITEM = 8 + (HAS_X ? 1 : 0) + (HAS_R ? 1 : 0);
+  extern __shared__ uint4 ring[];
+  __shared__ double smem[256 * (K > 0 ? K : 1)];
+  __shared__ __align__(16) float lsm[LINK_STAGE_MAX_SITES * 8 * LINK_F32];
+  if (a.gate != nullptr && *a.gate == 0) return;
+  const Shape sh = a.sh;
+  const Geom g = a.g;
+  const int T = blockDim.x;
+  const bool stage = sh.SB <= LINK_STAGE_MAX_SITES;  // uniform per launch
+  const int lsys = threadIdx.x % sh.NB;
+  const int lsite = threadIdx.x / sh.NB;
+  const int sys = blockIdx.y * sh.NB + lsys;
+  const bool sel = sys < sh.N && selected(a.st, sys, a.mask);
+
+  Tm ca = 0, cb = 1;
+  if (sel) {
+    const SysState& s = a.st[sys];
+    if (COEF == COEF_MHAT) { ca = coef<Tm>(s, C_A); cb = coef<Tm>(s, C_MINV4A); }
+    else if (COEF == COEF_DSLASH) { ca = coef<Tm>(s, C_A); cb = (Tm)-0.5; }
+  }
+  const size_t cstride = (size_t)g.Vh * sh.N * VW;  // elements between 16-byte chunks c and c+1
+
+  for (int chunk = blockIdx.x; chunk < sh.nchunk; chunk += gridDim.x) {
+    const int site = chunk * sh.SB + lsite;
+    const bool act = sel && site < g.Vh;
+    if (a.work != nullptr) {
+      const int cnt = __syncthreads_count(act);
+      if (threadIdx.x == 0 && cnt) atomicAdd(a.work, (unsigned long long)cnt);
+    }
+    int nb[8];
+    Tm ph[2] = {1, 1};  // t forward / backward boundary phase
+    if (act) {
+      int x[4];
+      cb_coords(g, a.p_out, site, x);
+#pragma unroll
+      for (int mu = 0; mu < 4; mu++) {
+        int y[4] = {x[0], x[1], x[2], x[3]};
+        y[mu] = x[mu] + 1;
+        if (y[mu] == g.L[mu]) { y[mu] = 0; if (mu == 3) ph[0] = (Tm)g.bc_t; }
+        nb[2 * mu] = cb_index(g, y);
+        y[mu] = x[mu] - 1;
+        if (y[mu] < 0) { y[mu] = g.L[mu] - 1; if (mu == 3) ph[1] = (Tm)g.bc_t; }
+        nb[2 * mu + 1] = cb_index(g, y);
+      }
+    }
+    if (stage) {
+      // thread k < 8 SB stages link k: site chunk*SB + k/8, direction k%8 (reconstructed to 18 floats)
+      __syncthreads();  // the previous chunk's readers are done with lsm
+      for (int k = threadIdx.x; k < 8 * sh.SB; k += T) {
+        const int ls = k >> 3, d = k & 7, mu = d >> 1;
+        const int s2 = chunk * sh.SB + ls;
+        if (s2 < g.Vh) {
+          Tm u[18];
+          if ((d & 1) == 0) {
+            load_link<Tg, Tm, NR>((const Tg*)a.gauge, g.Vh, a.p_out, mu, s2, u);
+          } else {
+            int x[4];
+            cb_coords(g, a.p_out, s2, x);
+            x[mu] = x[mu] == 0 ? g.L[mu] - 1 : x[mu] - 1;
+            load_link<Tg, Tm, NR>((const Tg*)a.gauge, g.Vh, 1 - a.p_out, mu, cb_index(g, x), u);
+          }
+          float* dst = lsm + (ls * 8 + d) * LINK_F32;
+#pragma unroll
+          for (int q = 0; q < 18; q++) dst[q] = (float)u[q];
+        }
+      }
+      __syncthreads();
+    }
+    const size_t myoff = ((size_t)site * sh.N + sys) * VW;
+    auto issue = [&](int item) {
+      if (act && item < NITEM) {
+        const Ts* src;
+        if (item < 8) src = (const Ts*)a.in + ((size_t)nb[item] * sh.N + sys) * VW;
+        else if (HAS_X && item == 8) src = (const Ts*)a.X + myoff;
+        else src = (const Ts*)a.R + myoff;
+        uint4* dst = ring + (size_t)(item % PF) * CV * T + threadIdx.x;
+#pragma unroll
+        for (int c = 0; c < CV; c++) cp_async16(dst + c * T, src + c * cstride);
+      }
+      cp_async_commit();  // one group per item (empty when idle) keeps the wait counts uniform
+    };
+    auto fetch = [&](int item, Tm (&v)[24]) {
+      const uint4* srcv = ring + (size_t)(item % PF) * CV * T + threadIdx.x;
+#pragma unroll
+      for (int c = 0; c < CV; c++) {
+        const uint4 w = srcv[c * T];
+        load_vec<Ts, Tm>(reinterpret_cast<const Ts*>(&w), v + c * VW);
+      }
+    };
+#pragma unroll
+    for (int i = 0; i < PF; i++) issue(i);
+    Tm acc[24];
+#pragma unroll
+    for (int k = 0; k < 24; k++) acc[k] = 0;
+#pragma unroll
+    for (int d = 0; d < 8; d++) {
+      cp_async_wait<PF - 1>();
+      Tm psi[24], u[18];
+      if (act) {
+        fetch(d, psi);
+        const int mu = d >> 1;
+        if (stage) {
+          const float4* src4 = reinterpret_cast<const float4*>(lsm + (lsite * 8 + d) * LINK_F32);
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            const float4 w = src4[q];
+            u[4 * q] = (Tm)w.x; u[4 * q + 1] = (Tm)w.y; u[4 * q + 2] = (Tm)w.z; u[4 * q + 3] = (Tm)w.w;
+          }
+          const float2 w2 = *reinterpret_cast<const float2*>(lsm + (lsite * 8 + d) * LINK_F32 + 16);
+          u[16] = (Tm)w2.x; u[17] = (Tm)w2.y;
+        } else if ((d & 1) == 0) {
+          load_link<Tg, Tm, NR>((const Tg*)a.gauge, g.Vh, a.p_out, mu, site, u);
+        } else {
+          load_link<Tg, Tm, NR>((const Tg*)a.gauge, g.Vh, 1 - a.p_out, mu, nb[d], u);
+        }
+      }
+      issue(d + PF);  // the slot just read is refilled
+      if (act) {
+        switch (d) {
+          case 0: hop_dir<0, -1, false>(acc, psi, u, (Tm)1); break;
+          case 1: hop_dir<0, +1, true>(acc, psi, u, (Tm)1); break;
+          case 2: hop_dir<1, -1, false>(acc, psi, u, (Tm)1); break;
+          case 3: hop_dir<1, +1, true>(acc, psi, u, (Tm)1); break;
+          case 4: hop_dir<2, -1, false>(acc, psi, u, (Tm)1); break;
+          case 5: hop_dir<2, +1, true>(acc, psi, u, (Tm)1); break;
+          case 6: hop_dir<3, -1, false>(acc, psi, u, ph[0]); break;
+          default: hop_dir<3, +1, true>(acc, psi, u, ph[1]); break;
+        }
+      }
+    }
+    // remaining items (X, R) were issued in the last steps; wait for all
+    for (int i = 8 + PF; i < NITEM; i++) issue(i);
+    cp_async_wait<0>();
+    double dv[K > 0 ? K : 1];
+#pragma unroll
+    for (int k = 0; k < (K > 0 ? K : 1); k++) dv[k] = 0.0;
+    if (act) {
+      Tm o[24];
+      if constexpr (!HAS_X) {
+#pragma unroll
+        for (int k = 0; k < 24; k++) o[k] = acc[k];
+      } else {
+        Tm xv[24];
+        fetch(8, xv);
+#pragma unroll
+        for (int k = 0; k < 24; k++) o[k] = ca * xv[k] + cb * acc[k];
+        if (DOT == DOT_TS) {
+          Tm sr = 0, si = 0, tt = 0;
+#pragma unroll
+          for (int k = 0; k < 24; k += 2) {
+            sr += o[k] * xv[k] + o[k + 1] * xv[k + 1];
+            si += o[k] * xv[k + 1] - o[k + 1] * xv[k];
+            tt += o[k] * o[k] + o[k + 1] * o[k + 1];
+          }
+          dv[0] = (double)sr; dv[1] = (double)si; dv[2] = (double)tt;
+        }
+      }
+      if constexpr (HAS_R) {
+        Tm rv[24];
+        fetch(8 + (HAS_X ? 1 : 0), rv);
+        Tm sr = 0, si = 0;
+#pragma unroll
+        for (int k = 0; k < 24; k += 2) {
+          sr += rv[k] * o[k] + rv[k + 1] * o[k + 1];
+          si += rv[k] * o[k + 1] - rv[k + 1] * o[k];
+        }
+        dv[0] = (double)sr; dv[1] = (double)si;
+      }
+      make_field<Ts>(a.out, g.Vh, sh.N).store(site, sys, o);
+    }
+    if constexpr (K > 0) {
+      group_partials<K>(dv, lsite, lsys, blockIdx.y * sh.NB, sh, g.Vh, chunk, smem, a.partial);
+    }
+  }
+}
+
+}  // namespace fs

@@ -8,6 +8,25 @@ namespace fs {
 template <typename Ts>
 using MathOf = typename std::conditional<std::is_same<Ts, double>::value, double, float>::type;
 
+// Directions kept in flight by the prefetching hop kernel (shared-memory ring slots).
+template <typename Ts> constexpr int hop_pf() { return sizeof(Ts) == 2 ? 4 : 3; }
+
+template <typename Ts, typename Tg, typename Tm, int R, int C, int D>
+cudaError_t launch_hop_pf(const HopArgs& a, const Launch& l) {
+  constexpr int PF = hop_pf<Ts>();
+  const size_t smem = hop_pf_smem<Ts, PF>(l.block);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(hop_kernel_pf<Ts, Tg, Tm, R, C, D, PF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hop_pf_smem<Ts, PF>(256));
+    if (e) return e;
+    configured = true;
+  }
+  hop_kernel_pf<Ts, Tg, Tm, R, C, D, PF><<<dim3(l.grid_x, l.grid_y), l.block, smem, l.stream>>>(a);
+  note_launch();
+  return cudaGetLastError();
+}
+
 template <typename Ts>
 cudaError_t launch_hop(int coef, int dot, int nr, const HopArgs& a, const Launch& l) {
   using Tg = typename GaugeOf<Ts>::T;
@@ -19,6 +38,8 @@ cudaError_t launch_hop(int coef, int dot, int nr, const HopArgs& a, const Launch
     note_launch();                                                       \
     return cudaGetLastError();                                           \
   }
+#define FS_HOP_PF(C, D, R) \
+  if (coef == C && dot == D && nr == R) return launch_hop_pf<Ts, Tg, Tm, R, C, D>(a, l);
   if constexpr (std::is_same<Ts, double>::value) {
     FS_HOP(COEF_PLAIN, DOT_NONE, 18)
     FS_HOP(COEF_DSLASH, DOT_NONE, 18)
@@ -29,16 +50,17 @@ cudaError_t launch_hop(int coef, int dot, int nr, const HopArgs& a, const Launch
     FS_HOP(COEF_TRUERES, DOT_NORM, 18)
     FS_HOP(COEF_FULLRES, DOT_NORM, 18)
   } else {
-    FS_HOP(COEF_PLAIN, DOT_NONE, 18)
-    FS_HOP(COEF_DSLASH, DOT_NONE, 18)
-    FS_HOP(COEF_MHAT, DOT_R, 18)
-    FS_HOP(COEF_MHAT, DOT_TS, 18)
-    FS_HOP(COEF_PLAIN, DOT_NONE, 12)
-    FS_HOP(COEF_DSLASH, DOT_NONE, 12)
-    FS_HOP(COEF_MHAT, DOT_R, 12)
-    FS_HOP(COEF_MHAT, DOT_TS, 12)
+    FS_HOP_PF(COEF_PLAIN, DOT_NONE, 18)
+    FS_HOP_PF(COEF_DSLASH, DOT_NONE, 18)
+    FS_HOP_PF(COEF_MHAT, DOT_R, 18)
+    FS_HOP_PF(COEF_MHAT, DOT_TS, 18)
+    FS_HOP_PF(COEF_PLAIN, DOT_NONE, 12)
+    FS_HOP_PF(COEF_DSLASH, DOT_NONE, 12)
+    FS_HOP_PF(COEF_MHAT, DOT_R, 12)
+    FS_HOP_PF(COEF_MHAT, DOT_TS, 12)
   }
 #undef FS_HOP
+#undef FS_HOP_PF
   return cudaErrorInvalidValue;
 }
 
