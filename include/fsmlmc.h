@@ -189,6 +189,27 @@ int fs_profile_read(fs_ctx* ctx, long long* launches, double* total_ms, double* 
 /* Number of CUDA kernels this library has launched in the process (all contexts). */
 long long fs_kernel_launches(void);
 
+/* ---- allocation-free variant ------------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that may not
+ * allocate device memory while they run: work recorded into a CUDA stream capture,
+ * processes that hand out a fixed device-memory budget up front, latency-critical loops
+ * that cannot take an allocation's implicit synchronisation. It computes what
+ * wilson_dslash computes in FP64, out_k = (D + sigma I) in_k for k < nrhs, on DEVICE
+ * buffers in the canonical layouts (U [4][V][3][3][2], in/out [nrhs][V][4][3][2]),
+ * without a context and without allocating: its scratch (the even-odd packed gauge
+ * field, packed spinors and per-system coefficients) is one fixed 32 MiB static device
+ * array that every GPU loading the library holds until process exit.
+ * Limits: nrhs <= 64 and 576 V + 384 V nrhs bytes (plus alignment) <= 32 MiB, else
+ * FS_ERR_BUDGET; FS_ERR_ARG for bad dims / bc_t / null pointers.
+ * The first call on a device looks up the array's device address (that device must be
+ * current) and should come before any stream capture. The call is stream ordered on
+ * `stream` (a cudaStream_t, NULL = legacy default stream): it returns once its kernels
+ * are queued. All calls on a device share the array, so calls whose work overlaps on
+ * the GPU (unordered streams) race and corrupt each other; each call rewrites every
+ * scratch field it reads, so the contents left by the previous call do not matter. */
+int wilson_dslash_noalloc(const int dims[4], int bc_t, double m, double sigma, const double* U,
+                          const double* in, double* out, int nrhs, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,8 @@ SYS_CONVERGED, SYS_NOCONV = 2, 3
 
 EXPORTS = ["fs_ctx_create", "fs_ctx_destroy", "fs_last_error", "fs_set_stream", "fs_ctx_device_bytes",
            "fs_set_gauge", "wilson_dslash", "shifted_solve", "mlmc_level_trace", "fs_mlmc_num_solves",
-           "variance_sample", "fs_noise_codes", "fs_profile_enable", "fs_profile_read", "fs_kernel_launches"]
+           "variance_sample", "fs_noise_codes", "fs_profile_enable", "fs_profile_read", "fs_kernel_launches",
+           "wilson_dslash_noalloc"]
 
 
 class FsError(RuntimeError):
@@ -82,6 +83,7 @@ def load_library(path=LIB_PATH):
         "fs_profile_enable": (I, [P, I]),
         "fs_profile_read": (I, [P, ctypes.POINTER(ctypes.c_longlong), dp, dp]),
         "fs_kernel_launches": (ctypes.c_longlong, []),
+        "wilson_dslash_noalloc": (I, [ip, I, D, D, P, P, P, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -259,6 +261,17 @@ class Context:
 def fs_kernel_launches():
     """Kernels launched by the library in this process so far."""
     return int(load_library().fs_kernel_launches())
+
+
+def wilson_dslash_noalloc(dims, bc_t, m, sigma, U_ptr, in_ptr, out_ptr, nrhs, stream=0):
+    """Allocation-free FP64 (D + sigma) on device buffers given as raw device pointers
+    (e.g. torch tensor .data_ptr()); stream-ordered on `stream` (raw cudaStream_t).
+    Returns the status code (0 = queued)."""
+    L = load_library()
+    arr = (ctypes.c_int * 4)(*[int(d) for d in dims])
+    return int(L.wilson_dslash_noalloc(arr, int(bc_t), float(m), float(sigma), ctypes.c_void_p(U_ptr),
+                                       ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), int(nrhs),
+                                       ctypes.c_void_p(stream or 0)))
 
 
 def _stats(s):
