@@ -254,9 +254,9 @@ __global__ void __launch_bounds__(256, sizeof(Tm) == 8 ? 1 : (sizeof(Ts) == 2 ? 
   for (int chunk = blockIdx.x; chunk < sh.nchunk; chunk += gridDim.x) {
     const int site = chunk * sh.SB + lsite;
     const bool act = sel && site < g.Vh;
-    if (a.work != nullptr) {
-      const int cnt = __syncthreads_count(act);
-      if (threadIdx.x == 0 && cnt) atomicAdd(a.work, (unsigned long long)cnt);
+    if (a.work != nullptr) {  // profiling: (site, system) pairs computed, one atomic per warp
+      const unsigned m = __ballot_sync(__activemask(), act);  // blocks may end in a partial warp
+      if ((threadIdx.x & 31) == 0 && m) atomicAdd(a.work, (unsigned long long)__popc(m));
     }
     double dv[K > 0 ? K : 1];
 #pragma unroll
@@ -391,9 +391,9 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
   for (int chunk = blockIdx.x; chunk < sh.nchunk; chunk += gridDim.x) {
     const int site = chunk * sh.SB + lsite;
     const bool act = sel && site < g.Vh;
-    if (a.work != nullptr) {
-      const int cnt = __syncthreads_count(act);
-      if (threadIdx.x == 0 && cnt) atomicAdd(a.work, (unsigned long long)cnt);
+    if (a.work != nullptr) {  // profiling: (site, system) pairs computed, one atomic per warp
+      const unsigned m = __ballot_sync(__activemask(), act);  // blocks may end in a partial warp
+      if ((threadIdx.x & 31) == 0 && m) atomicAdd(a.work, (unsigned long long)__popc(m));
     }
     int nb[8];
     Tm ph[2] = {1, 1};  // t forward / backward boundary phase
@@ -410,29 +410,6 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
         if (y[mu] < 0) { y[mu] = g.L[mu] - 1; if (mu == 3) ph[1] = (Tm)g.bc_t; }
         nb[2 * mu + 1] = cb_index(g, y);
       }
-    }
-    if (stage) {
-      // thread k < 8 SB stages link k: site chunk*SB + k/8, direction k%8 (reconstructed to 18 floats)
-      __syncthreads();  // the previous chunk's readers are done with lsm
-      for (int k = threadIdx.x; k < 8 * sh.SB; k += T) {
-        const int ls = k >> 3, d = k & 7, mu = d >> 1;
-        const int s2 = chunk * sh.SB + ls;
-        if (s2 < g.Vh) {
-          Tm u[18];
-          if ((d & 1) == 0) {
-            load_link<Tg, Tm, NR>((const Tg*)a.gauge, g.Vh, a.p_out, mu, s2, u);
-          } else {
-            int x[4];
-            cb_coords(g, a.p_out, s2, x);
-            x[mu] = x[mu] == 0 ? g.L[mu] - 1 : x[mu] - 1;
-            load_link<Tg, Tm, NR>((const Tg*)a.gauge, g.Vh, 1 - a.p_out, mu, cb_index(g, x), u);
-          }
-          float* dst = lsm + (ls * 8 + d) * LINK_F32;
-#pragma unroll
-          for (int q = 0; q < 18; q++) dst[q] = (float)u[q];
-        }
-      }
-      __syncthreads();
     }
     const size_t myoff = ((size_t)site * sh.N + sys) * VW;
     auto issue = [&](int item) {
@@ -457,6 +434,29 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
     };
 #pragma unroll
     for (int i = 0; i < PF; i++) issue(i);
+    if (stage) {  // overlaps the spinor copies just issued
+      // thread k < 8 SB stages link k: site chunk*SB + k/8, direction k%8 (reconstructed to 18 floats)
+      __syncthreads();  // the previous chunk's readers are done with lsm
+      for (int k = threadIdx.x; k < 8 * sh.SB; k += T) {
+        const int ls = k >> 3, d = k & 7, mu = d >> 1;
+        const int s2 = chunk * sh.SB + ls;
+        if (s2 < g.Vh) {
+          Tm u[18];
+          if ((d & 1) == 0) {
+            load_link<Tg, Tm, NR>((const Tg*)a.gauge, g.Vh, a.p_out, mu, s2, u);
+          } else {
+            int x[4];
+            cb_coords(g, a.p_out, s2, x);
+            x[mu] = x[mu] == 0 ? g.L[mu] - 1 : x[mu] - 1;
+            load_link<Tg, Tm, NR>((const Tg*)a.gauge, g.Vh, 1 - a.p_out, mu, cb_index(g, x), u);
+          }
+          float* dst = lsm + (ls * 8 + d) * LINK_F32;
+#pragma unroll
+          for (int q = 0; q < 18; q++) dst[q] = (float)u[q];
+        }
+      }
+      __syncthreads();
+    }
     Tm acc[24];
 #pragma unroll
     for (int k = 0; k < 24; k++) acc[k] = 0;
