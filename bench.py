@@ -233,6 +233,48 @@ def config_of(args, w):
             "tol": w["tol"], "l2": "working set above L2 (no flush needed)"}
 
 
+# --------------------------------------------------------------------------- serving
+SERVE_LATTICES = [(8, 8, 8, 8), (12, 12, 12, 24), (16, 16, 16, 32)]
+CLIFFORD = ["1", "g1", "g2", "g3", "g4", "g5", "g1g2", "g1g3", "g1g4", "g2g3", "g2g4", "g3g4", "g5g1", "g5g2",
+            "g5g3", "g5g4"]
+
+
+def run_serving(pkg, inputs, device, n_jobs, rate=20.0, budget_gb=60, max_active=4, seed=4004):
+    """Poisson arrivals (mean `rate` jobs/s) of trace jobs: lattice uniform over 8^4, 12^3x24,
+    16^3x32; 2..6 log-uniform shifts in [0.005, 1]; 32..256 Z4 vectors per level; p in 0..4;
+    Gamma uniform over the 16 Clifford products; FP16 or BF16 inner solves; m = -0.2, eps = 0.3."""
+    rng = np.random.default_rng(seed)
+    gauges = {d: inputs.gauge_field(d, "smooth", seed=4100 + i, eps=0.3) for i, d in enumerate(SERVE_LATTICES)}
+    jobs = []
+    for k in range(n_jobs):
+        dims = SERVE_LATTICES[int(rng.integers(len(SERVE_LATTICES)))]
+        nlev = int(rng.integers(2, 7))
+        sig = np.sort(np.exp(rng.uniform(np.log(0.005), 0.0, size=nlev)))
+        jobs.append(dict(dims=dims, sig=sig, n=[int(rng.integers(32, 257))] * nlev, p=int(rng.integers(0, 5)),
+                         gamma=pkg.gamma_matrix(CLIFFORD[int(rng.integers(16))]),
+                         prec=["f16", "bf16"][int(rng.integers(2))], gap=float(rng.exponential(1.0 / rate))))
+    srv = pkg.Server(device=device, hbm_budget_bytes=int(budget_gb) << 30, max_active=max_active)
+    t0 = time.time()
+    tickets = []
+    t_next = t0
+    for k, j in enumerate(jobs):
+        t_next += j["gap"]
+        dt = t_next - time.time()
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(srv.submit(j["dims"], gauges[j["dims"]], -0.2, j["sig"], j["gamma"], j["p"], j["n"],
+                                  seed=7000 + k, job=k, prec=j["prec"], tol=1e-8, rhs_tile=32))
+    res = [srv.poll(t) for t in tickets]
+    wall = time.time() - t0
+    st = srv.stats()
+    srv.close()
+    bad = [r["status"] for r in res if r["status"] != 0]
+    return {"jobs": n_jobs, "arrival_rate_per_s": rate, "budget_gb": budget_gb, "max_active": max_active,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "mean_ms": st["mean_ms"],
+            "solves": int(st["solves"]), "solves_per_s": st["solves"] / wall, "wall_s": wall,
+            "failed_jobs": len(bad)}
+
+
 # --------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -247,6 +289,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=8.0, help="seconds of oracle work per reference step")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--serve-jobs", type=int, default=12, help="jobs in the serving run (0: skip)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -345,6 +388,10 @@ def main():
                 "launches": prof["launches"], "avg_launch_us": per_launch_s * 1e6,
                 "algorithmic_bytes_per_launch": bytes_per_launch, "peak_source": peak_kind}
 
+    serving = None
+    if args.serve_jobs > 0:
+        serving = run_serving(pkg, inputs, local, args.serve_jobs)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:
@@ -358,7 +405,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_of(args, w), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk,
+                "gpu_launches": launches, "clocks": clk, "serving": serving,
                 "solver": {"mean_iters": float(np.mean(iters)) if iters else None,
                            "max_iters": int(max(iters)) if iters else None,
                            "solves_per_step": solves_per_step}}

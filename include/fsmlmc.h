@@ -186,6 +186,54 @@ int fs_noise_codes(fs_ctx* ctx, uint64_t seed, uint32_t job, uint32_t level, uin
 int fs_profile_enable(fs_ctx* ctx, int enable);
 int fs_profile_read(fs_ctx* ctx, long long* launches, double* total_ms, double* bytes);
 
+/* ---- serving ---------------------------------------------------------------------
+ * A server on one GPU runs FS-MLMC trace jobs (one mlmc_level_trace each) as they arrive.
+ * Jobs are admitted first in first out when one of `max_active` slots is free and the
+ * job's device-memory estimate fits `hbm_budget_bytes` next to the running jobs; every
+ * running job has its own worker thread, context and CUDA stream, so their work overlaps
+ * on the device, and inside a job the solves are continuously batched. A job's results
+ * depend only on its own inputs and are identical alone or in a mix. */
+#define FS_JOB_MAX_LEVELS 16
+
+typedef struct fs_server fs_server;
+
+typedef struct fs_job {
+  int dims[4];
+  int bc_t;
+  const double* U;          /* host gauge field [4][V][3][3][2]; copied by fs_server_submit   */
+  fs_mlmc_params params;    /* as for mlmc_level_trace; its arrays are copied at submit       */
+} fs_job;
+
+typedef struct fs_job_result {
+  int status;               /* return code of the job's mlmc_level_trace                     */
+  int nlev;
+  double trace[FS_JOB_MAX_LEVELS][2];
+  double var[FS_JOB_MAX_LEVELS];
+  long long solves;
+  double mean_iters;
+  double latency_ms;        /* completion - submission                                       */
+  double queue_ms;          /* admission - submission                                        */
+} fs_job_result;
+
+typedef struct fs_server_report {
+  long long completed, queued, active, solves;
+  size_t reserved_bytes;    /* device-memory estimates of the running jobs                   */
+  double p50_ms, p99_ms, max_ms, mean_ms;  /* latency over completed jobs                   */
+  double solves_per_s;      /* solves of completed jobs / (last completion - first submission) */
+} fs_server_report;
+
+/* FS_ERR_ARG for max_active outside [1, 64] or a zero budget. */
+int fs_server_create(fs_server** server, int device, size_t hbm_budget_bytes, int max_active);
+/* Queue a job; FS_ERR_BUDGET if its estimate alone exceeds the budget, FS_ERR_ARG for bad
+ * dims or more than FS_JOB_MAX_LEVELS levels. */
+int fs_server_submit(fs_server* server, const fs_job* job, uint64_t* ticket);
+/* Wait up to timeout_ms (< 0: forever) for a job; FS_ERR_TIMEOUT if it is not done yet.
+ * A result is returned once, then the ticket is forgotten. */
+int fs_server_poll(fs_server* server, uint64_t ticket, fs_job_result* result, int timeout_ms);
+int fs_server_stats(fs_server* server, fs_server_report* stats);
+/* Finishes queued and running jobs, then stops the workers. */
+void fs_server_destroy(fs_server* server);
+
 /* Number of CUDA kernels this library has launched in the process (all contexts). */
 long long fs_kernel_launches(void);
 

@@ -7,6 +7,7 @@ point names, and the Dirac matrix table used to build Gamma insertions.
 
 from .fsmlmc import (  # noqa: F401
     Context,
+    Server,
     FsError,
     PREC,
     ESTIMATOR,

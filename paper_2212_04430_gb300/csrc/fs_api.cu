@@ -8,10 +8,6 @@
 
 #include "fs_engine.h"
 
-struct fs_ctx {
-  fs::Ctx c;
-};
-
 namespace {
 
 using fs::Ctx;

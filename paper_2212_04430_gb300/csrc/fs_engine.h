@@ -171,3 +171,8 @@ long long launch_count();
 cudaError_t launch_noise_codes(uint8_t* codes, NoiseSpec n, int V, cudaStream_t s);
 
 }  // namespace fs
+
+// The opaque context handle of the C ABI.
+struct fs_ctx {
+  fs::Ctx c;
+};

@@ -15,13 +15,11 @@ template <typename Ts, typename Tg, typename Tm, int R, int C, int D>
 cudaError_t launch_hop_pf(const HopArgs& a, const Launch& l) {
   constexpr int PF = hop_pf<Ts>();
   const size_t smem = hop_pf_smem<Ts, PF>(l.block);
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(hop_kernel_pf<Ts, Tg, Tm, R, C, D, PF>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hop_pf_smem<Ts, PF>(256));
-    if (e) return e;
-    configured = true;
-  }
+  // thread-safe one-time set-up (several server workers may launch concurrently)
+  static const cudaError_t configured = cudaFuncSetAttribute(
+      hop_kernel_pf<Ts, Tg, Tm, R, C, D, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)hop_pf_smem<Ts, PF>(256));
+  if (configured) return configured;
   hop_kernel_pf<Ts, Tg, Tm, R, C, D, PF><<<dim3(l.grid_x, l.grid_y), l.block, smem, l.stream>>>(a);
   note_launch();
   return cudaGetLastError();

@@ -1,0 +1,264 @@
+// Serving loop: continuous batching of FS-MLMC trace jobs on one GPU.
+//
+// Jobs (a gauge field and the parameters of one mlmc_level_trace call) are queued
+// as they arrive. A job is admitted, first in first out, when an active slot is
+// free and its device-memory estimate fits the budget next to the jobs already
+// running. Every active job runs on its own worker thread with its own context and
+// CUDA stream, so the work of concurrent jobs overlaps on the device; inside a
+// job the solves are continuously batched over the slots of its tile. A job's
+// results depend only on its own inputs (per-system kernels, fixed-order
+// reductions), so they are identical whether it runs alone or in a mix.
+// Latency = completion - submission; the server reports p50 / p99 over the
+// completed jobs.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "fs_engine.h"
+#include "fsmlmc.h"
+
+namespace {
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct SJob {
+  uint64_t ticket = 0;
+  int dims[4] = {0, 0, 0, 0};
+  int bc_t = -1;
+  std::vector<double> U, sigma, gamma;
+  std::vector<int> nsamp;
+  fs_mlmc_params P{};
+  size_t est = 0;
+  double t_submit = 0, t_start = 0, t_end = 0;
+  bool done = false;
+  fs_job_result res{};
+};
+
+size_t real_bytes(int prec) { return prec == FS_PREC_F64 ? 8 : (prec == FS_PREC_F32 ? 4 : 2); }
+
+// Device memory a job needs: gauge copies, its solver tile, staging and contraction buffers.
+size_t estimate(const SJob& j) {
+  const size_t V = (size_t)j.dims[0] * j.dims[1] * j.dims[2] * j.dims[3];
+  const size_t Vh = V / 2;
+  const int prec = j.P.solve.prec;
+  int tile = j.P.solve.rhs_tile > 0 ? j.P.solve.rhs_tile : 32;
+  tile = std::max(tile, j.P.estimator == FS_EST_SPLIT_EVEN ? 2 : 1);
+  const size_t f64 = 24 * Vh * tile * 8;
+  const size_t fts = 24 * Vh * tile * real_bytes(prec);
+  const size_t ftx = 24 * Vh * tile * (prec == FS_PREC_F64 ? 8 : 4);
+  const size_t tile_bytes = 6 * f64 + (prec == FS_PREC_F64 ? 0 : f64) + ftx + 7 * fts + 3 * (size_t)tile * 3 * (Vh / 8) * 8;
+  const size_t gauge = 8 * Vh * (18 * 8 + 20 * 4 + 12 * 4 + 24 * 2 + 16 * 2);
+  const size_t stage = j.P.estimator == FS_EST_PRODUCT ? (size_t)tile * V * 24 * 8 : 0;
+  const size_t contract = (size_t)tile * ((2 * Vh + 255) / 256) * 2 * 8 + (64u << 10);
+  return tile_bytes + gauge + stage + contract + (32u << 20);
+}
+
+}  // namespace
+
+struct fs_server {
+  int device = 0;
+  size_t budget = 0;
+  int max_active = 1;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<SJob*> queue;
+  std::map<uint64_t, std::unique_ptr<SJob>> jobs;
+  uint64_t next_ticket = 1;
+  size_t reserved = 0;
+  int active = 0;
+  bool stop = false;
+  std::vector<std::thread> workers;
+  std::vector<double> latencies;
+  long long completed = 0, solves = 0;
+  double t_first = -1, t_last = 0;
+
+  void worker() {
+    fs_ctx* ctx = nullptr;
+    int cdims[4] = {0, 0, 0, 0}, cbc = 0;
+    cudaSetDevice(device);
+    while (true) {
+      SJob* j = nullptr;
+      {
+        std::unique_lock<std::mutex> lock(mu);
+        cv_work.wait(lock, [&] {
+          return (stop && queue.empty()) || (!queue.empty() && reserved + queue.front()->est <= budget);
+        });
+        if (queue.empty()) break;  // stopping and drained
+        j = queue.front();
+        queue.pop_front();
+        reserved += j->est;
+        active += 1;
+        j->t_start = now_ms();
+      }
+      // a context per worker, rebuilt when the lattice changes; tiles are released per job
+      const bool same = ctx && cbc == j->bc_t && std::equal(cdims, cdims + 4, j->dims);
+      int rc = FS_OK;
+      if (!same) {
+        if (ctx) fs_ctx_destroy(ctx);
+        ctx = nullptr;
+        rc = fs_ctx_create(&ctx, j->dims, j->bc_t, device);
+        if (rc == FS_OK) {
+          std::copy(j->dims, j->dims + 4, cdims);
+          cbc = j->bc_t;
+        }
+      }
+      if (rc == FS_OK) rc = fs_set_gauge(ctx, j->U.data());
+      fs_job_result r{};
+      if (rc == FS_OK) {
+        const int nsolve = fs_mlmc_num_solves(&j->P);
+        std::vector<fs_sys_stats> st(std::max(nsolve, 1));
+        double trace[FS_JOB_MAX_LEVELS * 2], var[FS_JOB_MAX_LEVELS];
+        rc = mlmc_level_trace(ctx, &j->P, trace, var, nullptr, st.data());
+        long long it = 0;
+        for (int k = 0; k < nsolve; k++) it += st[k].iters;
+        for (int l = 0; l < j->P.nlev; l++) {
+          r.trace[l][0] = trace[2 * l];
+          r.trace[l][1] = trace[2 * l + 1];
+          r.var[l] = var[l];
+        }
+        r.solves = nsolve;
+        r.mean_iters = nsolve > 0 ? (double)it / nsolve : 0.0;
+      }
+      r.status = rc;
+      r.nlev = j->P.nlev;
+      if (ctx) ctx->c.tiles.clear();  // the tile memory goes back before the next admission
+      {
+        std::lock_guard<std::mutex> lock(mu);
+        j->t_end = now_ms();
+        r.latency_ms = j->t_end - j->t_submit;
+        r.queue_ms = j->t_start - j->t_submit;
+        j->res = r;
+        j->done = true;
+        reserved -= j->est;
+        active -= 1;
+        completed += 1;
+        solves += r.solves;
+        latencies.push_back(r.latency_ms);
+        if (t_first < 0) t_first = j->t_submit;
+        t_last = j->t_end;
+      }
+      cv_done.notify_all();
+      cv_work.notify_all();
+    }
+    if (ctx) fs_ctx_destroy(ctx);
+  }
+};
+
+extern "C" {
+
+int fs_server_create(fs_server** out, int device, size_t hbm_budget_bytes, int max_active) {
+  if (!out) return FS_ERR_ARG;
+  *out = nullptr;
+  if (max_active < 1 || max_active > 64 || hbm_budget_bytes == 0) return FS_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return FS_ERR_CUDA;
+  }
+  fs_server* s = new fs_server();
+  s->device = device;
+  s->budget = hbm_budget_bytes;
+  s->max_active = max_active;
+  for (int w = 0; w < max_active; w++) s->workers.emplace_back([s] { s->worker(); });
+  *out = s;
+  return FS_OK;
+}
+
+int fs_server_submit(fs_server* s, const fs_job* job, uint64_t* ticket) {
+  if (!s || !job || !ticket) return FS_ERR_ARG;
+  const fs_mlmc_params& P = job->params;
+  if (P.nlev < 1 || P.nlev > FS_JOB_MAX_LEVELS || !P.sigma || !P.n_samples || !P.gamma || !job->U)
+    return FS_ERR_ARG;
+  long long V = 1;
+  for (int mu = 0; mu < 4; mu++) {
+    if (job->dims[mu] < 2 || job->dims[mu] % 2) return FS_ERR_ARG;
+    V *= job->dims[mu];
+  }
+  if (V >= (1LL << 27)) return FS_ERR_ARG;
+  std::unique_ptr<SJob> j(new SJob());
+  std::copy(job->dims, job->dims + 4, j->dims);
+  j->bc_t = job->bc_t;
+  j->U.assign(job->U, job->U + (size_t)4 * V * 18);
+  j->sigma.assign(P.sigma, P.sigma + P.nlev);
+  j->nsamp.assign(P.n_samples, P.n_samples + P.nlev);
+  j->gamma.assign(P.gamma, P.gamma + 32);
+  j->P = P;
+  j->P.sigma = j->sigma.data();
+  j->P.n_samples = j->nsamp.data();
+  j->P.gamma = j->gamma.data();
+  j->est = estimate(*j);
+  if (j->est > s->budget) return FS_ERR_BUDGET;
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (s->stop) return FS_ERR_STATE;
+  j->ticket = s->next_ticket++;
+  j->t_submit = now_ms();
+  *ticket = j->ticket;
+  s->queue.push_back(j.get());
+  s->jobs[j->ticket] = std::move(j);
+  s->cv_work.notify_all();
+  return FS_OK;
+}
+
+int fs_server_poll(fs_server* s, uint64_t ticket, fs_job_result* out, int timeout_ms) {
+  if (!s || !out) return FS_ERR_ARG;
+  std::unique_lock<std::mutex> lock(s->mu);
+  auto it = s->jobs.find(ticket);
+  if (it == s->jobs.end()) return FS_ERR_ARG;
+  SJob* j = it->second.get();
+  const auto pred = [&] { return j->done; };
+  if (timeout_ms < 0) s->cv_done.wait(lock, pred);
+  else if (!s->cv_done.wait_for(lock, std::chrono::milliseconds(timeout_ms), pred)) return FS_ERR_TIMEOUT;
+  *out = j->res;
+  s->jobs.erase(it);  // a result is handed out once
+  return FS_OK;
+}
+
+int fs_server_stats(fs_server* s, fs_server_report* out) {
+  if (!s || !out) return FS_ERR_ARG;
+  std::lock_guard<std::mutex> lock(s->mu);
+  memset(out, 0, sizeof(*out));
+  out->completed = s->completed;
+  out->queued = (long long)s->queue.size();
+  out->active = s->active;
+  out->solves = s->solves;
+  out->reserved_bytes = s->reserved;
+  std::vector<double> l = s->latencies;
+  std::sort(l.begin(), l.end());
+  if (!l.empty()) {
+    auto pct = [&](double q) {
+      const size_t k = std::min(l.size() - 1, (size_t)(q * (double)(l.size() - 1) + 0.5));
+      return l[k];
+    };
+    out->p50_ms = pct(0.50);
+    out->p99_ms = pct(0.99);
+    out->max_ms = l.back();
+    double sum = 0;
+    for (double v : l) sum += v;
+    out->mean_ms = sum / (double)l.size();
+  }
+  const double span = s->t_last - s->t_first;
+  out->solves_per_s = span > 0 ? (double)s->solves / (span / 1e3) : 0.0;
+  return FS_OK;
+}
+
+void fs_server_destroy(fs_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  for (auto& t : s->workers) t.join();
+  delete s;
+}
+
+}  // extern "C"

@@ -24,7 +24,9 @@ SYS_CONVERGED, SYS_NOCONV = 2, 3
 EXPORTS = ["fs_ctx_create", "fs_ctx_destroy", "fs_last_error", "fs_set_stream", "fs_ctx_device_bytes",
            "fs_set_gauge", "wilson_dslash", "shifted_solve", "mlmc_level_trace", "fs_mlmc_num_solves",
            "variance_sample", "fs_noise_codes", "fs_profile_enable", "fs_profile_read", "fs_kernel_launches",
-           "wilson_dslash_noalloc"]
+           "wilson_dslash_noalloc", "fs_server_create", "fs_server_submit", "fs_server_poll",
+           "fs_server_stats", "fs_server_destroy"]
+JOB_MAX_LEVELS = 16
 
 
 class FsError(RuntimeError):
@@ -49,6 +51,24 @@ class MlmcParams(ctypes.Structure):
                 ("sigma", ctypes.POINTER(ctypes.c_double)), ("n_samples", ctypes.POINTER(ctypes.c_int)),
                 ("gamma", ctypes.POINTER(ctypes.c_double)), ("seed", ctypes.c_uint64),
                 ("job", ctypes.c_uint32), ("estimator", ctypes.c_int), ("solve", SolveParams)]
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 4), ("bc_t", ctypes.c_int), ("U", ctypes.POINTER(ctypes.c_double)),
+                ("params", MlmcParams)]
+
+
+class JobResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("nlev", ctypes.c_int), ("trace", (ctypes.c_double * 2) * 16),
+                ("var", ctypes.c_double * 16), ("solves", ctypes.c_longlong), ("mean_iters", ctypes.c_double),
+                ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double)]
+
+
+class ServerReport(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_longlong), ("queued", ctypes.c_longlong), ("active", ctypes.c_longlong),
+                ("solves", ctypes.c_longlong), ("reserved_bytes", ctypes.c_size_t), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("solves_per_s", ctypes.c_double)]
 
 
 _lib = None
@@ -84,6 +104,11 @@ def load_library(path=LIB_PATH):
         "fs_profile_read": (I, [P, ctypes.POINTER(ctypes.c_longlong), dp, dp]),
         "fs_kernel_launches": (ctypes.c_longlong, []),
         "wilson_dslash_noalloc": (I, [ip, I, D, D, P, P, P, I, P]),
+        "fs_server_create": (I, [ctypes.POINTER(P), I, ctypes.c_size_t, I]),
+        "fs_server_submit": (I, [P, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_uint64)]),
+        "fs_server_poll": (I, [P, ctypes.c_uint64, ctypes.POINTER(JobResult), I]),
+        "fs_server_stats": (I, [P, ctypes.POINTER(ServerReport)]),
+        "fs_server_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -272,6 +297,76 @@ def wilson_dslash_noalloc(dims, bc_t, m, sigma, U_ptr, in_ptr, out_ptr, nrhs, st
     return int(L.wilson_dslash_noalloc(arr, int(bc_t), float(m), float(sigma), ctypes.c_void_p(U_ptr),
                                        ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), int(nrhs),
                                        ctypes.c_void_p(stream or 0)))
+
+
+class Server:
+    """fs_server: FIFO admission by device-memory budget, one worker (context + stream) per
+    active job, continuous batching inside each job."""
+
+    def __init__(self, device=0, hbm_budget_bytes=60 << 30, max_active=4):
+        self.lib = load_library()
+        self.h = ctypes.c_void_p()
+        rc = self.lib.fs_server_create(ctypes.byref(self.h), int(device), int(hbm_budget_bytes), int(max_active))
+        if rc != FS_OK:
+            raise FsError(rc, "fs_server_create failed")
+
+    def submit(self, dims, U, m, sigmas, gamma, p, n_samples, seed, job=0, estimator="diff", bc_t=-1, **kw):
+        """Queue one trace job (arrays are copied); returns the ticket."""
+        u = _real(U)
+        sig = np.ascontiguousarray(sigmas, dtype=np.float64)
+        ns = np.ascontiguousarray(n_samples, dtype=np.int32)
+        g = _gamma.to_abi(gamma)
+        J = Job()
+        for k in range(4):
+            J.dims[k] = int(dims[k])
+        J.bc_t = int(bc_t)
+        J.U = _dptr(u)
+        P = J.params
+        P.m = m
+        P.nlev = sig.size
+        P.p = int(p)
+        P.sigma = _dptr(sig)
+        P.n_samples = ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        P.gamma = _dptr(g)
+        P.seed = int(seed)
+        P.job = int(job)
+        P.estimator = ESTIMATOR[estimator] if isinstance(estimator, str) else int(estimator)
+        P.solve = _params(**kw)
+        t = ctypes.c_uint64()
+        rc = self.lib.fs_server_submit(self.h, ctypes.byref(J), ctypes.byref(t))
+        if rc != FS_OK:
+            raise FsError(rc, "fs_server_submit failed")
+        return t.value
+
+    def poll(self, ticket, timeout_ms=-1):
+        """Result dict of a finished job, or None on timeout."""
+        r = JobResult()
+        rc = self.lib.fs_server_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(r), int(timeout_ms))
+        if rc == FS_ERR_TIMEOUT:
+            return None
+        if rc != FS_OK:
+            raise FsError(rc, "fs_server_poll failed")
+        n = r.nlev
+        return {"status": r.status, "trace": np.array([r.trace[l][0] + 1j * r.trace[l][1] for l in range(n)]),
+                "var": np.array([r.var[l] for l in range(n)]), "solves": r.solves, "mean_iters": r.mean_iters,
+                "latency_ms": r.latency_ms, "queue_ms": r.queue_ms}
+
+    def stats(self):
+        r = ServerReport()
+        if self.lib.fs_server_stats(self.h, ctypes.byref(r)) != FS_OK:
+            raise FsError(FS_ERR_ARG, "fs_server_stats failed")
+        return {k: getattr(r, k) for k, _ in ServerReport._fields_}
+
+    def close(self):
+        if self.h:
+            self.lib.fs_server_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _stats(s):

@@ -1,0 +1,87 @@
+"""Serving loop: continuous batching of trace jobs, HBM-budget admission, p50/p99.
+
+Each job's result must be the same alone (a plain mlmc_level_trace call) and in
+a mix of concurrently running jobs on different lattices; the kernels are
+per-system and the reductions fixed-order, so equality is exact.
+"""
+
+import numpy as np
+import pytest
+
+import inputs
+
+pkg = pytest.importorskip("paper_2212_04430_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _jobs():
+    rng = np.random.default_rng(404)
+    specs = []
+    lattices = [(4, 4, 4, 4), (4, 4, 2, 8), (6, 4, 4, 4)]
+    for k in range(7):
+        dims = lattices[k % 3]
+        nlev = 2 + k % 3
+        sig = np.sort(np.exp(rng.uniform(np.log(0.005), 0.0, size=nlev)))
+        specs.append(dict(dims=dims, gseed=5000 + k, m=-0.3, sigmas=sig, gamma=pkg.gamma_matrix(["g3", "g5g4", "1"][k % 3]),
+                          p=k % 3, n=[int(rng.integers(4, 12))] * nlev, seed=6000 + k,
+                          est=["diff", "split_even", "product"][k % 3], prec=["f16", "f32", "bf16"][k % 3]))
+    return specs
+
+
+def _run_alone(s, u):
+    ctx = pkg.Context(s["dims"])
+    ctx.fs_set_gauge(u)
+    out = ctx.mlmc_level_trace(s["m"], s["sigmas"], s["gamma"], s["p"], s["n"], seed=s["seed"], job=1,
+                               estimator=s["est"], prec=s["prec"], rhs_tile=8)
+    ctx.close()
+    return out
+
+
+def test_jobs_identical_alone_and_in_a_concurrent_mix():
+    specs = _jobs()
+    gauges = [inputs.gauge_field(s["dims"], "smooth", seed=s["gseed"], eps=0.4) for s in specs]
+    alone = [_run_alone(s, u) for s, u in zip(specs, gauges)]
+    srv = pkg.Server(device=0, hbm_budget_bytes=8 << 30, max_active=3)
+    tickets = [srv.submit(s["dims"], u, s["m"], s["sigmas"], s["gamma"], s["p"], s["n"], s["seed"], job=1,
+                          estimator=s["est"], prec=s["prec"], rhs_tile=8) for s, u in zip(specs, gauges)]
+    results = [srv.poll(t) for t in tickets]
+    for a, r in zip(alone, results):
+        assert r["status"] == 0
+        assert np.array_equal(r["trace"], a["trace"])
+        assert np.array_equal(r["var"], a["var"])
+    st = srv.stats()
+    assert st["completed"] == len(specs) and st["queued"] == 0 and st["active"] == 0
+    assert 0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
+    assert st["reserved_bytes"] == 0
+    srv.close()
+
+
+def test_budget_admission_and_poll_timeout():
+    dims = (8, 8, 8, 8)
+    u = inputs.gauge_field(dims, "smooth", seed=77, eps=0.3)
+    g = pkg.gamma_matrix("g5g3")
+    # a budget that fits one such job at a time: jobs run one after another and all finish
+    srv = pkg.Server(device=0, hbm_budget_bytes=150 << 20, max_active=4)
+    tickets = [srv.submit(dims, u, -0.2, [0.02, 0.1, 0.5], g, 2, [16, 16, 16], seed=9 + k, prec="f32",
+                          rhs_tile=16) for k in range(3)]
+    first = srv.poll(tickets[-1], timeout_ms=0)  # the last job cannot be done yet
+    assert first is None
+    res = [srv.poll(t) for t in tickets]
+    assert all(r["status"] == 0 for r in res)
+    # FIFO under a one-job budget: each job waited for the previous ones
+    assert res[2]["queue_ms"] >= res[1]["queue_ms"] >= res[0]["queue_ms"]
+    # a job larger than the whole budget is refused at submission
+    with pytest.raises(pkg.FsError) as e:
+        srv.submit((16, 16, 16, 32), inputs.unit_gauge((16, 16, 16, 32)), -0.2, [0.1, 0.5], g, 1, [8, 8], seed=1,
+                   prec="f32", rhs_tile=32)
+    assert e.value.code == pkg.fsmlmc.FS_ERR_BUDGET
+    with pytest.raises(pkg.FsError):
+        srv.poll(123456789, timeout_ms=0)  # unknown ticket
+    srv.close()
