@@ -304,7 +304,8 @@ def main():
     import paper_2212_04430_gb300 as pkg
 
     torch.cuda.set_device(local)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()  # a dedicated stream: the library launches on it, the events time it
+    torch.cuda.set_stream(stream)
     dims = w["dims"]
     nvec = args.vectors or w["vectors"]
     tile = args.tile or w["tile"]

@@ -54,7 +54,7 @@ int resolve_params(Ctx& c, const fs_solve_params* p, int nsys, double m, Opts& o
   if (d.delta > 0) o.so.delta = d.delta;
   // default reliable-update trigger: as deep as the storage precision lets the sloppy
   // residual fall before rounding stalls it (each update costs two FP64 hops per system)
-  else o.so.delta = o.so.prec == FS_PREC_F64 ? 0.0 : (o.so.prec == FS_PREC_F32 ? 1e-4 : (o.so.prec == FS_PREC_F16 ? 1e-2 : 3e-2));
+  else o.so.delta = o.so.prec == FS_PREC_F64 ? 0.0 : (o.so.prec == FS_PREC_F32 ? 1e-5 : (o.so.prec == FS_PREC_F16 ? 3e-3 : 2e-2));
   if (o.so.delta >= 1.0) return c.fail(FS_ERR_ARG, "delta must be < 1");
   o.so.verify = d.verify;
   o.so.check_every = 4;
@@ -106,6 +106,7 @@ int fs_ctx_create(fs_ctx** out, const int dims[4], int bc_t, int device) {
   c.g.V = (int)V;
   c.g.Vh = (int)(V / 2);
   c.g.bc_t = bc_t;
+  fs::geom_init_div(c.g);
   if (cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c.own_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();

@@ -24,22 +24,54 @@ namespace fs {
 
 enum Prec { PREC_F64 = 0, PREC_F32 = 1, PREC_F16 = 2, PREC_BF16 = 3 };
 
+// Unsigned division by a runtime constant d >= 1 through a multiply-high and a shift
+// (Granlund & Montgomery, PLDI'94): q = (hi32(n * mul) + n) >> shift with
+// shift = ceil(log2 d) and mul = floor(2^32 (2^shift - d) / d) + 1, exact for n < 2^31.
+struct FastDiv {
+  uint32_t d, mul, shift;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  uint32_t s = 0;
+  while ((1ull << s) < d) s++;
+  f.shift = s;
+  f.mul = (uint32_t)(((1ull << 32) * ((1ull << s) - d)) / d + 1);
+  return f;
+}
+__host__ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+#ifdef __CUDA_ARCH__
+  const uint32_t hi = __umulhi(n, f.mul);
+#else
+  const uint32_t hi = (uint32_t)(((uint64_t)n * f.mul) >> 32);
+#endif
+  return (uint32_t)(((uint64_t)hi + n) >> f.shift);
+}
+
 struct Geom {
   int L[4];  // Lx, Ly, Lz, Lt
   int Lh0;   // Lx / 2
   int Vh;    // sites per parity
   int V;     // all sites
   int bc_t;  // +1 periodic, -1 antiperiodic in t
+  FastDiv dLh0, dL1, dL2;  // reciprocals of Lx/2, Ly, Lz for the checkerboard coordinates
 };
+
+inline void geom_init_div(Geom& g) {
+  g.dLh0 = make_fastdiv((uint32_t)g.Lh0);
+  g.dL1 = make_fastdiv((uint32_t)g.L[1]);
+  g.dL2 = make_fastdiv((uint32_t)g.L[2]);
+}
 
 // Coordinates of checkerboard site i of parity p (parity = (x+y+z+t) & 1).
 __device__ __forceinline__ void cb_coords(const Geom& g, int p, int i, int x[4]) {
-  int xh = i % g.Lh0;
-  int r = i / g.Lh0;
-  x[1] = r % g.L[1];
-  r /= g.L[1];
-  x[2] = r % g.L[2];
-  x[3] = r / g.L[2];
+  const uint32_t r0 = fdiv((uint32_t)i, g.dLh0);
+  const int xh = i - (int)r0 * g.Lh0;
+  const uint32_t r1 = fdiv(r0, g.dL1);
+  x[1] = (int)r0 - (int)r1 * g.L[1];
+  const uint32_t r2 = fdiv(r1, g.dL2);
+  x[2] = (int)r1 - (int)r2 * g.L[2];
+  x[3] = (int)r2;
   x[0] = 2 * xh + ((x[1] + x[2] + x[3] + p) & 1);
 }
 

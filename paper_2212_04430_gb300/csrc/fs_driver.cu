@@ -142,8 +142,7 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
       if (int rc = admit_rhs(adm, any_vec, any_noise)) return rc;
 
     // ---- iterate
-    for (int k = 0; k < every; k++)
-      if ((e = T->enqueue_iter())) return c->cuda_fail(e, "solver iteration");
+    if ((e = T->enqueue_iters(every))) return c->cuda_fail(e, "solver iteration");
     iters_run += every;
     if ((e = cudaMemcpyAsync(T->st_h, T->st_d, sizeof(SysState) * N, cudaMemcpyDeviceToHost, c->stream)))
       return c->cuda_fail(e, "download system state");

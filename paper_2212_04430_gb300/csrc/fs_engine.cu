@@ -10,7 +10,10 @@
 namespace fs {
 
 static std::atomic<long long> g_launches{0};
-void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static thread_local bool t_capturing = false;  // launches recorded into a graph are counted per replay
+void note_launch(int n) {
+  if (!t_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
+}
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 Shape make_shape(int N, int Vh) {
@@ -104,8 +107,13 @@ class Tile : public TileBase {
   double *pa = nullptr, *pb = nullptr, *pc = nullptr;
   int* gate = nullptr;
   std::vector<void*> owned;
+  // K BiCGStab iterations captured once and replayed (launch overhead dominates small lattices)
+  cudaGraphExec_t gexec = nullptr;
+  int gk = 0;
+  size_t gnodes = 0;
 
   ~Tile() override {
+    if (gexec) cudaGraphExecDestroy(gexec);
     for (void* q : owned) cudaFree(q);
     if (st_h) cudaFreeHost(st_h);
     if (spec_h) cudaFreeHost(spec_h);
@@ -277,6 +285,37 @@ class Tile : public TileBase {
     if ((e = launch_blas<Ts>(OP_SETR, blas(MASK_UPDATE, r_hi, pa, true, true), L1))) return e;
     return fin(FIN_UPDATE, MASK_UPDATE, pa);
   }
+
+  cudaError_t enqueue_iters(int k) override {
+    const bool graphs = !c->prof.enabled && c->stream != nullptr && c->stream != cudaStreamLegacy &&
+                        c->stream != cudaStreamPerThread;
+    cudaError_t e = cudaSuccess;
+    if (!graphs || iters_eager < 1) {
+      // eager launches (always the first time, so every one-time kernel set-up is done)
+      for (int i = 0; i < k && !e; i++) e = enqueue_iter();
+      iters_eager++;
+      return e;
+    }
+    if (!gexec || gk != k) {
+      if (gexec) cudaGraphExecDestroy(gexec);
+      gexec = nullptr;
+      cudaGraph_t graph = nullptr;
+      t_capturing = true;
+      e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+      for (int i = 0; i < k && !e; i++) e = enqueue_iter();
+      cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+      t_capturing = false;
+      if (!e) e = e2;
+      if (!e) e = cudaGraphGetNodes(graph, nullptr, &gnodes);
+      if (!e) e = cudaGraphInstantiate(&gexec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e) return e;
+      gk = k;
+    }
+    note_launch((int)gnodes);
+    return cudaGraphLaunch(gexec, c->stream);
+  }
+  int iters_eager = 0;
 
   cudaError_t enqueue_recon() override {
     L1.stream = c->stream;

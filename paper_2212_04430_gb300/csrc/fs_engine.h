@@ -79,6 +79,7 @@ class TileBase {
   virtual cudaError_t enqueue_noise() = 0;  // z <- Z4 noise for INIT slots with a noise rhs
   virtual cudaError_t enqueue_init() = 0;
   virtual cudaError_t enqueue_iter() = 0;
+  virtual cudaError_t enqueue_iters(int k) = 0;  // k iterations, from a captured CUDA graph when possible
   virtual cudaError_t enqueue_recon() = 0;
   virtual cudaError_t enqueue_verify() = 0;
   virtual cudaError_t enqueue_solution_to_canon(double* canon) = 0;  // canon[vec[j]] <- x for all j with vec >= 0

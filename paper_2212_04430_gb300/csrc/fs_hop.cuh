@@ -227,7 +227,7 @@ __device__ __forceinline__ void group_partials(const double (&vals)[K], int lsit
 // with 18-real links) for latency hiding; FP32 storage needs ~128 registers for its
 // float4 spinors and keeps 2 blocks; FP64 is ALU bound.
 template <typename Ts, typename Tg, typename Tm, int NR, int COEF, int DOT>
-__global__ void __launch_bounds__(256, sizeof(Tm) == 8 ? 1 : (sizeof(Ts) == 2 ? 3 : 2)) hop_kernel(HopArgs a) {
+__global__ void __launch_bounds__(256, sizeof(Tm) == 8 ? 2 : (sizeof(Ts) == 2 ? 3 : 2)) hop_kernel(HopArgs a) {
   if (a.gate != nullptr && *a.gate == 0) return;
   constexpr int K = DotK<DOT>::K;
   __shared__ double smem[256 * (K > 0 ? K : 1)];

@@ -112,6 +112,7 @@ extern "C" int wilson_dslash_noalloc(const int dims[4], int bc_t, double m, doub
   g.V = (int)V;
   g.Vh = (int)Vh;
   g.bc_t = bc_t;
+  fs::geom_init_div(g);
   cudaStream_t s = (cudaStream_t)stream;
   const fs::Shape sh = fs::make_shape(nrhs, g.Vh);
   const int gy = (nrhs + sh.NB - 1) / sh.NB;

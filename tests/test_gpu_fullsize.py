@@ -1,0 +1,87 @@
+"""Parity at the benchmark sizes: 16^3x32 (the FS-MLMC job of the benchmark) and
+24^3x64 (variance sampling over p = 0..8).
+
+The oracle cannot solve these systems within a test, so it checks what it can
+compute one by one: the Z4 noise (bit-exact), the FP64 true residual of GPU
+solutions with its own operator, and the Gamma Omega_p contractions of those
+solutions against the GPU's level samples and variance samples. The GPU
+solution of a system is bit-identical whichever entry point solved it (kernels
+are per-system and reductions fixed-order), so shifted_solve exposes the very
+vectors that mlmc_level_trace and variance_sample contracted.
+"""
+
+import numpy as np
+import pytest
+
+import inputs
+from oracle import dirac as odirac
+from oracle import estimators as oest
+from oracle import philox as ophilox
+from helpers import rel_resid
+
+pkg = pytest.importorskip("paper_2212_04430_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def test_config3_16x32_level_samples_and_residuals():
+    dims = (16, 16, 16, 32)
+    v = int(np.prod(dims))
+    u = inputs.gauge_field(dims, "smooth", seed=1003, eps=0.4)
+    ctx = pkg.Context(dims)
+    ctx.fs_set_gauge(u)
+    sig = [0.005, 0.03, 0.15, 0.6]
+    m, p, seed, job = -0.35, 4, 2003, 77
+    kw = dict(prec="f16", tol=1e-8, rhs_tile=32, link_compress=12)
+    out = ctx.mlmc_level_trace(m, sig, pkg.gamma_matrix("g3"), p, [2, 2, 2, 2], seed=seed, job=job, **kw)
+    assert out["rc"] == 0
+    # sampled noise of the job, bit-exact at full size
+    for lev in (0, 3):
+        assert np.array_equal(ctx.fs_noise_codes(seed, job, lev, 1), ophilox.z4_codes(v, seed, job, lev, 1))
+    # level 0, sample 0 (DIFF): c(s0) - c(s1) on z_{0,0}; level 3, sample 1: c(s3) on z_{1,3}
+    cases = [(0, 0, [0.005, 0.03]), (3, 1, [0.6])]
+    for lev, s, shifts in cases:
+        z = ophilox.z4_noise(v, seed, job, lev, s)
+        x, st, rc = ctx.shifted_solve(m, shifts, z, **kw)
+        assert rc == 0
+        c = []
+        for j, sh in enumerate(shifts):
+            r = rel_resid(u, x[j, 0], z, m, sh, dims)
+            assert r <= 1.05e-8, (lev, sh, r)
+            c.append(oest.contract(u, z, x[j, 0], odirac.GAMMA[2], p, dims))
+        ref = c[0] - c[1] if len(c) == 2 else c[0]
+        got = out["samples"][lev][s]
+        assert abs(got - ref) <= 1e-9 * max(abs(ref), 1.0), (lev, got, ref)
+    ctx.close()
+
+
+def test_config5_24x64_variance_samples():
+    dims = (24, 24, 24, 64)
+    v = int(np.prod(dims))
+    u = inputs.gauge_field(dims, "smooth", seed=1005, eps=0.5)
+    ctx = pkg.Context(dims)
+    ctx.fs_set_gauge(u)
+    s_hat = [0.0, 0.05, 0.25, 0.5, 1.0]
+    m, seed, job = -0.38, 2005, 3
+    plist = list(range(9))
+    kw = dict(prec="f16", tol=1e-8, rhs_tile=10, link_compress=12)
+    out = ctx.variance_sample(m, s_hat, pkg.gamma_matrix("g3"), plist, 1, seed=seed, job=job, **kw)
+    assert out["rc"] == 0
+    assert np.array_equal(ctx.fs_noise_codes(seed, job, ophilox.VARIANCE_SAMPLE_LEVEL, 0),
+                          ophilox.z4_codes(v, seed, job, ophilox.VARIANCE_SAMPLE_LEVEL, 0))
+    # a_i(p) = z^dag gamma3 Omega_p x^(i) for the largest shift, recomputed by the oracle
+    z = ophilox.z4_noise(v, seed, job, ophilox.VARIANCE_SAMPLE_LEVEL, 0)
+    x, st, rc = ctx.shifted_solve(m, [1.0], z, **kw)
+    assert rc == 0
+    assert rel_resid(u, x[0, 0], z, m, 1.0, dims) <= 1.05e-8
+    for p in (0, 1, 5, 8):
+        ref = oest.contract(u, z, x[0, 0], odirac.GAMMA[2], p, dims)
+        got = out["a"][0, p, 4]
+        assert abs(got - ref) <= 1e-9 * max(abs(ref), 1.0), (p, got, ref)
+    ctx.close()
