@@ -52,8 +52,9 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def hop_traffic_per_launch(workload):
-    """dram bytes per hop launch from the committed ncu summary, if it matches the kernel source."""
+def hop_traffic_ratio(workload):
+    """DRAM traffic / algorithmic bytes of the hop mix, from the committed ncu summary, if that
+    summary was taken on the current kernel source (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "hop_kernel_%s.md" % workload)
     if not os.path.exists(path):
@@ -63,14 +64,14 @@ def hop_traffic_per_launch(workload):
         with open(os.path.join(ROOT, "paper_2212_04430_gb300", "csrc", f), "rb") as fh:
             src += fh.read()
     digest = hashlib.sha256(src).hexdigest()[:16]
-    traffic, tag = None, None
+    ratio, tag = None, None
     with open(path) as f:
         for line in f:
-            if line.startswith("traffic_bytes_per_launch:"):
-                traffic = float(line.split(":")[1])
+            if line.startswith("traffic_to_algorithmic_ratio:"):
+                ratio = float(line.split(":")[1])
             if line.startswith("kernel_source_sha256_16:"):
                 tag = line.split(":")[1].strip()
-    return traffic if (tag == digest and traffic) else None
+    return ratio if (tag == digest and ratio) else None
 
 
 class ClockSampler:
@@ -384,10 +385,13 @@ def main():
         bytes_per_launch = prof["bytes"] / prof["launches"]
         achieved = bytes_per_launch / per_launch_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": hop_traffic_per_launch(args.workload),
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                 "kernel": "hop_kernel (even-odd Wilson hopping term, inner precision)",
                 "launches": prof["launches"], "avg_launch_us": per_launch_s * 1e6,
                 "algorithmic_bytes_per_launch": bytes_per_launch, "peak_source": peak_kind}
+        ratio = hop_traffic_ratio(args.workload)
+        if ratio is not None:
+            roof["traffic"] = ratio * bytes_per_launch
 
     serving = None
     if args.serve_jobs > 0:

@@ -156,6 +156,9 @@ struct ContractArgs {
   const ContractPair* pairs;
   double* partial;        // [npairs][np][2][nblk]
   double gamma[32];       // Gamma, 4x4 complex, row major
+  int gmono;              // 1: Gamma is a monomial matrix with entries in {+-1, +-i}
+  int gperm[4];           // (Gamma psi)_s = i^gphase[s] psi_{gperm[s]} when gmono
+  int gphase[4];
   Geom g;
   int N;
   int pmask;              // bit q set: displacement q requested
@@ -199,21 +202,38 @@ __global__ void __launch_bounds__(256) contract_kernel(ContractArgs a) {
         }
         // L^dag Gamma psi
         double cr = 0, ci = 0;
+        if (a.gmono) {
+          // every Clifford product is a signed / phased permutation in this basis
 #pragma unroll
-        for (int s = 0; s < 4; s++) {
+          for (int s = 0; s < 4; s++) {
+            const int t = a.gperm[s], k = a.gphase[s];
 #pragma unroll
-          for (int c = 0; c < 3; c++) {
-            double gr = 0, gi = 0;
-#pragma unroll
-            for (int t = 0; t < 4; t++) {
-              const double Gr = a.gamma[(s * 4 + t) * 2], Gi = a.gamma[(s * 4 + t) * 2 + 1];
+            for (int c = 0; c < 3; c++) {
               const double pr_ = psi[t * 6 + c * 2], pi_ = psi[t * 6 + c * 2 + 1];
-              gr += Gr * pr_ - Gi * pi_;
-              gi += Gr * pi_ + Gi * pr_;
+              const double gr = k == 0 ? pr_ : (k == 1 ? -pi_ : (k == 2 ? -pr_ : pi_));
+              const double gi = k == 0 ? pi_ : (k == 1 ? pr_ : (k == 2 ? -pi_ : -pr_));
+              const double lr = lv[s * 6 + c * 2], li = lv[s * 6 + c * 2 + 1];
+              cr += lr * gr + li * gi;
+              ci += lr * gi - li * gr;
             }
-            const double lr = lv[s * 6 + c * 2], li = lv[s * 6 + c * 2 + 1];
-            cr += lr * gr + li * gi;
-            ci += lr * gi - li * gr;
+          }
+        } else {
+#pragma unroll
+          for (int s = 0; s < 4; s++) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+              double gr = 0, gi = 0;
+#pragma unroll
+              for (int t = 0; t < 4; t++) {
+                const double Gr = a.gamma[(s * 4 + t) * 2], Gi = a.gamma[(s * 4 + t) * 2 + 1];
+                const double pr_ = psi[t * 6 + c * 2], pi_ = psi[t * 6 + c * 2 + 1];
+                gr += Gr * pr_ - Gi * pi_;
+                gi += Gr * pi_ + Gi * pr_;
+              }
+              const double lr = lv[s * 6 + c * 2], li = lv[s * 6 + c * 2 + 1];
+              cr += lr * gr + li * gi;
+              ci += lr * gi - li * gr;
+            }
           }
         }
         acc[qi][0] = cr;

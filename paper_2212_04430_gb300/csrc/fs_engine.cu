@@ -404,6 +404,24 @@ int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, c
     if (plist[k] <= plist[k - 1]) return c->fail(1, "displacements must be increasing");
   a.x_e = T->x_hi; a.x_o = T->x_o; a.gauge64 = (const double*)c->gauge64; a.spec = T->spec_d;
   for (int k = 0; k < 32; k++) a.gamma[k] = gamma[k];
+  // detect a monomial Gamma (one entry per row, each +-1 or +-i): applied as a permutation
+  a.gmono = 1;
+  for (int r = 0; r < 4 && a.gmono; r++) {
+    int found = -1;
+    for (int t = 0; t < 4; t++) {
+      const double re = gamma[(r * 4 + t) * 2], im = gamma[(r * 4 + t) * 2 + 1];
+      if (re == 0.0 && im == 0.0) continue;
+      if (found >= 0) { a.gmono = 0; break; }
+      found = t;
+      if (re == 1.0 && im == 0.0) a.gphase[r] = 0;
+      else if (re == 0.0 && im == 1.0) a.gphase[r] = 1;
+      else if (re == -1.0 && im == 0.0) a.gphase[r] = 2;
+      else if (re == 0.0 && im == -1.0) a.gphase[r] = 3;
+      else a.gmono = 0;
+    }
+    if (found < 0) a.gmono = 0;
+    a.gperm[r] = found;
+  }
   a.g = c->g; a.N = T->N; a.pmask = pmask; a.pmax = pmax; a.np = np;
   a.nblk = (2 * c->g.Vh + 255) / 256;
   const size_t part_n = (size_t)npairs * np * 2 * a.nblk;

@@ -370,15 +370,24 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
   extern __shared__ uint4 ring[];
   __shared__ double smem[256 * (K > 0 ? K : 1)];
   __shared__ __align__(16) float lsm[LINK_STAGE_MAX_SITES * 8 * LINK_F32];
+  __shared__ unsigned grp_arrivals;
   if (a.gate != nullptr && *a.gate == 0) return;
   const Shape sh = a.sh;
   const Geom g = a.g;
   const int T = blockDim.x;
-  const bool stage = sh.SB <= LINK_STAGE_MAX_SITES;  // uniform per launch
+  // With 32 systems per warp a warp is one site: links are staged per warp and the
+  // 8-site dot partials are combined by the last warp to arrive (no block barrier).
+  const bool warp_mode = sh.NB == 32 && gridDim.x >= sh.nchunk;  // uniform per launch
+  const bool stage = !warp_mode && sh.SB <= LINK_STAGE_MAX_SITES;  // block-cooperative staging
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lsys = threadIdx.x % sh.NB;
   const int lsite = threadIdx.x / sh.NB;
   const int sys = blockIdx.y * sh.NB + lsys;
   const bool sel = sys < sh.N && selected(a.st, sys, a.mask);
+  if (warp_mode && K > 0) {
+    if (threadIdx.x == 0) grp_arrivals = 0;
+    __syncthreads();
+  }
 
   Tm ca = 0, cb = 1;
   if (sel) {
@@ -387,17 +396,19 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
     else if (COEF == COEF_DSLASH) { ca = coef<Tm>(s, C_A); cb = (Tm)-0.5; }
   }
   const size_t cstride = (size_t)g.Vh * sh.N * VW;  // elements between 16-byte chunks c and c+1
+  const size_t rowstride = (size_t)sh.N * VW;        // elements between consecutive sites
 
   for (int chunk = blockIdx.x; chunk < sh.nchunk; chunk += gridDim.x) {
     const int site = chunk * sh.SB + lsite;
-    const bool act = sel && site < g.Vh;
+    const bool live = site < g.Vh;
+    const bool act = sel && live;
     if (a.work != nullptr) {  // profiling: (site, system) pairs computed, one atomic per warp
       const unsigned m = __ballot_sync(__activemask(), act);  // blocks may end in a partial warp
       if ((threadIdx.x & 31) == 0 && m) atomicAdd(a.work, (unsigned long long)__popc(m));
     }
     int nb[8];
     Tm ph[2] = {1, 1};  // t forward / backward boundary phase
-    if (act) {
+    if (live) {
       int x[4];
       cb_coords(g, a.p_out, site, x);
 #pragma unroll
@@ -411,11 +422,12 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
         nb[2 * mu + 1] = cb_index(g, y);
       }
     }
-    const size_t myoff = ((size_t)site * sh.N + sys) * VW;
+    const Ts* in_base = (const Ts*)a.in + (size_t)sys * VW;
+    const size_t myoff = (size_t)site * rowstride + (size_t)sys * VW;
     auto issue = [&](int item) {
       if (act && item < NITEM) {
         const Ts* src;
-        if (item < 8) src = (const Ts*)a.in + ((size_t)nb[item] * sh.N + sys) * VW;
+        if (item < 8) src = in_base + (size_t)nb[item] * rowstride;
         else if (HAS_X && item == 8) src = (const Ts*)a.X + myoff;
         else src = (const Ts*)a.R + myoff;
         uint4* dst = ring + (size_t)(item % PF) * CV * T + threadIdx.x;
@@ -434,8 +446,25 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
     };
 #pragma unroll
     for (int i = 0; i < PF; i++) issue(i);
-    if (stage) {  // overlaps the spinor copies just issued
-      // thread k < 8 SB stages link k: site chunk*SB + k/8, direction k%8 (reconstructed to 18 floats)
+    // links of this chunk's sites, reconstructed once, while the first spinors are in flight
+    float* my_links = lsm + (warp_mode ? warp : lsite) * 8 * LINK_F32;
+    if (warp_mode) {
+      if (lane < 8 && live) {
+        const int d = lane, mu = d >> 1;
+        int nbd = nb[1];
+#pragma unroll
+        for (int k = 3; k < 8; k += 2)
+          if (d == k) nbd = nb[k];
+        Tm u[18];
+        if ((d & 1) == 0) load_link<Tg, Tm, NR>((const Tg*)a.gauge, g.Vh, a.p_out, mu, site, u);
+        else load_link<Tg, Tm, NR>((const Tg*)a.gauge, g.Vh, 1 - a.p_out, mu, nbd, u);
+        float* dst = my_links + d * LINK_F32;
+#pragma unroll
+        for (int q = 0; q < 18; q++) dst[q] = (float)u[q];
+      }
+      __syncwarp();
+    } else if (stage) {
+      // thread k < 8 SB stages link k: site chunk*SB + k/8, direction k%8
       __syncthreads();  // the previous chunk's readers are done with lsm
       for (int k = threadIdx.x; k < 8 * sh.SB; k += T) {
         const int ls = k >> 3, d = k & 7, mu = d >> 1;
@@ -457,6 +486,7 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
       }
       __syncthreads();
     }
+    const bool staged = warp_mode || stage;
     Tm acc[24];
 #pragma unroll
     for (int k = 0; k < 24; k++) acc[k] = 0;
@@ -467,14 +497,14 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
       if (act) {
         fetch(d, psi);
         const int mu = d >> 1;
-        if (stage) {
-          const float4* src4 = reinterpret_cast<const float4*>(lsm + (lsite * 8 + d) * LINK_F32);
+        if (staged) {
+          const float4* src4 = reinterpret_cast<const float4*>(my_links + d * LINK_F32);
 #pragma unroll
           for (int q = 0; q < 4; q++) {
             const float4 w = src4[q];
             u[4 * q] = (Tm)w.x; u[4 * q + 1] = (Tm)w.y; u[4 * q + 2] = (Tm)w.z; u[4 * q + 3] = (Tm)w.w;
           }
-          const float2 w2 = *reinterpret_cast<const float2*>(lsm + (lsite * 8 + d) * LINK_F32 + 16);
+          const float2 w2 = *reinterpret_cast<const float2*>(my_links + d * LINK_F32 + 16);
           u[16] = (Tm)w2.x; u[17] = (Tm)w2.y;
         } else if ((d & 1) == 0) {
           load_link<Tg, Tm, NR>((const Tg*)a.gauge, g.Vh, a.p_out, mu, site, u);
@@ -537,7 +567,35 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
       make_field<Ts>(a.out, g.Vh, sh.N).store(site, sys, o);
     }
     if constexpr (K > 0) {
-      group_partials<K>(dv, lsite, lsys, blockIdx.y * sh.NB, sh, g.Vh, chunk, smem, a.partial);
+      if (warp_mode) {
+        // warp = site `warp` of the chunk's single 8-site group; lane = system
+#pragma unroll
+        for (int k = 0; k < K; k++) smem[(warp * 32 + lane) * K + k] = dv[k];
+        __syncwarp();
+        __threadfence_block();
+        unsigned ticket = 0;
+        if (lane == 0) ticket = atomicAdd(&grp_arrivals, 1u);
+        ticket = __shfl_sync(0xffffffffu, ticket, 0);
+        if ((ticket & 7u) == 7u) {  // the last of the 8 warps sums the group in site order
+          __threadfence_block();
+          const int ngroups = g.Vh / 8;
+          const int grp = chunk;
+          const int sysg = blockIdx.y * 32 + lane;
+          if (grp < ngroups && sysg < sh.N) {
+            double sacc[K > 0 ? K : 1];
+#pragma unroll
+            for (int k = 0; k < K; k++) sacc[k] = 0.0;
+            for (int j = 0; j < 8; j++) {
+#pragma unroll
+              for (int k = 0; k < K; k++) sacc[k] += smem[(j * 32 + lane) * K + k];
+            }
+#pragma unroll
+            for (int k = 0; k < K; k++) a.partial[((size_t)sysg * K + k) * ngroups + grp] = sacc[k];
+          }
+        }
+      } else {
+        group_partials<K>(dv, lsite, lsys, blockIdx.y * sh.NB, sh, g.Vh, chunk, smem, a.partial);
+      }
     }
   }
 }

@@ -281,3 +281,20 @@ def test_product_chain_and_split_even_in_mixed_tiles():
         for lev in range(3):
             assert sample_err(out["samples"][lev], ref[lev]) < 1e-9, (est, lev)
     ctx.close()
+
+
+def test_contraction_with_a_dense_gamma():
+    """A Gamma that is not a Clifford product (dense complex 4x4) takes the general path of
+    the contraction; Clifford products take the permutation path (the tests above)."""
+    dims = (4, 4, 2, 4)
+    u = inputs.gauge_field(dims, "haar", seed=31)
+    rng = np.random.default_rng(8)
+    gam = rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))
+    sig = [0.05, 0.4]
+    ctx = make_ctx(dims, u)
+    out = ctx.mlmc_level_trace(-0.3, sig, gam, 1, [4, 3], seed=12, job=4, estimator="split_even", prec="f64",
+                               tol=1e-12, rhs_tile=4)
+    ref = _oracle_levels(u, -0.3, sig, gam, 1, [4, 3], 12, 4, dims, oest.SPLIT_EVEN)
+    for lev in range(2):
+        assert sample_err(out["samples"][lev], ref[lev]) < 1e-9, lev
+    ctx.close()
