@@ -269,11 +269,14 @@ def run_serving(pkg, inputs, device, n_jobs, rate=20.0, budget_gb=60, max_active
     wall = time.time() - t0
     st = srv.stats()
     srv.close()
-    bad = [r["status"] for r in res if r["status"] != 0]
+    bad = [dict(status=r["status"], prec=j["prec"], lattice="x".join(map(str, j["dims"])),
+                sigma_min=float(j["sig"][0]), noconv=r["noconv"], restarts=r["restarts"], max_iters=r["max_iters"])
+           for r, j in zip(res, jobs) if r["status"] != 0]
     return {"jobs": n_jobs, "arrival_rate_per_s": rate, "budget_gb": budget_gb, "max_active": max_active,
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "mean_ms": st["mean_ms"],
             "solves": int(st["solves"]), "solves_per_s": st["solves"] / wall, "wall_s": wall,
-            "failed_jobs": len(bad)}
+            "failed_jobs": len(bad), "failures": bad,
+            "restarts": int(sum(r["restarts"] for r in res)), "max_iters": int(max(r["max_iters"] for r in res))}
 
 
 # --------------------------------------------------------------------------- GPU arm

@@ -211,6 +211,9 @@ typedef struct fs_job_result {
   double var[FS_JOB_MAX_LEVELS];
   long long solves;
   double mean_iters;
+  int max_iters;            /* most BiCGStab iterations of one solve                          */
+  int noconv;               /* solves that ended FS_SYS_NOCONV                                */
+  long long restarts;       /* breakdown restarts summed over the solves                      */
   double latency_ms;        /* completion - submission                                       */
   double queue_ms;          /* admission - submission                                        */
 } fs_job_result;

@@ -69,7 +69,54 @@ struct HopArgs {
   int mask;
 };
 
+// ---- fixed-order arithmetic ------------------------------------------------------
+// Multiply-adds with a fixed rounding sequence (no compiler contraction choices):
+// every hop kernel variant forms its products, epilogues and dot products through
+// these, so a system's iterates are bit-identical whichever variant (tile shape)
+// computed them.
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// (re, im) += conj(a) b for one complex entry a = a0 + i a1, b = b0 + i b1
+template <typename Tm>
+__device__ __forceinline__ void dot_acc(Tm& re, Tm& im, Tm a0, Tm a1, Tm b0, Tm b1) {
+  re = fmadd(a0, b0, re);
+  re = fmadd(a1, b1, re);
+  im = fmadd(a0, b1, im);
+  im = fmadd(-a1, b0, im);
+}
+template <typename Tm>
+__device__ __forceinline__ void norm_acc(Tm& n, Tm a0, Tm a1) {
+  n = fmadd(a0, a0, n);
+  n = fmadd(a1, a1, n);
+}
+// a x + b y
+template <typename Tm>
+__device__ __forceinline__ Tm axpby(Tm a, Tm x, Tm b, Tm y) { return fmadd(b, y, a * x); }
+
 // ---- links -----------------------------------------------------------------
+// Third row of a special unitary matrix from its first two: u2 = conj(u0 x u1),
+// in one fixed multiply-add order.
+template <typename Tm>
+__device__ __forceinline__ void link_row3(Tm (&u)[18]) {
+  auto cross = [&](int i, int j, Tm& re, Tm& im) {  // component of u0 x u1: a_i b_j - a_j b_i
+    const Tm air = u[2 * i], aii = u[2 * i + 1], ajr = u[2 * j], aji = u[2 * j + 1];
+    const Tm bir = u[6 + 2 * i], bii = u[6 + 2 * i + 1], bjr = u[6 + 2 * j], bji = u[6 + 2 * j + 1];
+    re = air * bjr;
+    re = fmadd(-aii, bji, re);
+    re = fmadd(-ajr, bir, re);
+    re = fmadd(aji, bii, re);
+    im = air * bji;
+    im = fmadd(aii, bjr, im);
+    im = fmadd(-ajr, bii, im);
+    im = fmadd(-aji, bir, im);
+  };
+  Tm re, im;
+  cross(1, 2, re, im); u[12] = re; u[13] = -im;
+  cross(2, 0, re, im); u[14] = re; u[15] = -im;
+  cross(0, 1, re, im); u[16] = re; u[17] = -im;
+}
+
 template <typename Tg, typename Tm, int NR>
 __device__ __forceinline__ void load_link(const Tg* __restrict__ gauge, int Vh, int parity, int mu,
                                           int site, Tm (&u)[18]) {
@@ -81,34 +128,30 @@ __device__ __forceinline__ void load_link(const Tg* __restrict__ gauge, int Vh, 
   for (int c = 0; c < RP / VW; c++) load_vec<Tg, Tm>(b + c * VW, tmp + c * VW);
 #pragma unroll
   for (int k = 0; k < NR; k++) u[k] = tmp[k];
-  if constexpr (NR == 12) {
-    // third row = conj(row0 x row1) for a special unitary matrix
-    const Tm a0r = u[0], a0i = u[1], a1r = u[2], a1i = u[3], a2r = u[4], a2i = u[5];
-    const Tm b0r = u[6], b0i = u[7], b1r = u[8], b1i = u[9], b2r = u[10], b2i = u[11];
-    // c = a x b
-    Tm c0r = (a1r * b2r - a1i * b2i) - (a2r * b1r - a2i * b1i);
-    Tm c0i = (a1r * b2i + a1i * b2r) - (a2r * b1i + a2i * b1r);
-    Tm c1r = (a2r * b0r - a2i * b0i) - (a0r * b2r - a0i * b2i);
-    Tm c1i = (a2r * b0i + a2i * b0r) - (a0r * b2i + a0i * b2r);
-    Tm c2r = (a0r * b1r - a0i * b1i) - (a1r * b0r - a1i * b0i);
-    Tm c2i = (a0r * b1i + a0i * b1r) - (a1r * b0i + a1i * b0r);
-    u[12] = c0r; u[13] = -c0i; u[14] = c1r; u[15] = -c1i; u[16] = c2r; u[17] = -c2i;
-  }
+  if constexpr (NR == 12) link_row3(u);
 }
 
-// chi = U h  or  U^dag h  for one colour vector (3 complex)
+// chi = U h  or  U^dag h  for one colour vector (3 complex). Each real output is
+// one multiply-add chain (one product, five fused multiply-adds).
 template <bool DAG, typename Tm>
 __device__ __forceinline__ void su3_mul(const Tm (&u)[18], const Tm* h, Tm* chi) {
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    Tm re = 0, im = 0;
+    Tm re, im;
 #pragma unroll
     for (int b = 0; b < 3; b++) {
       const int k = DAG ? (b * 3 + a) * 2 : (a * 3 + b) * 2;
       const Tm ur = u[k];
       const Tm ui = DAG ? -u[k + 1] : u[k + 1];
-      re += ur * h[2 * b] - ui * h[2 * b + 1];
-      im += ur * h[2 * b + 1] + ui * h[2 * b];
+      if (b == 0) {
+        re = ur * h[0];
+        im = ur * h[1];
+      } else {
+        re = fmadd(ur, h[2 * b], re);
+        im = fmadd(ur, h[2 * b + 1], im);
+      }
+      re = fmadd(-ui, h[2 * b + 1], re);
+      im = fmadd(ui, h[2 * b], im);
     }
     chi[2 * a] = re;
     chi[2 * a + 1] = im;
@@ -279,21 +322,20 @@ __global__ void __launch_bounds__(256, sizeof(Tm) == 8 ? 2 : (sizeof(Ts) == 2 ? 
         Tm xv[24];
         make_field<Ts>(const_cast<void*>(a.X), g.Vh, sh.N).load(site, sys, xv);
 #pragma unroll
-        for (int k = 0; k < 24; k++) o[k] = ca * xv[k] + cb * acc[k];
+        for (int k = 0; k < 24; k++) o[k] = axpby(ca, xv[k], cb, acc[k]);
         if (COEF == COEF_TRUERES || COEF == COEF_FULLRES) {
           Tm yv[24];
           make_field<Ts>(const_cast<void*>(a.Y), g.Vh, sh.N).load(site, sys, yv);
 #pragma unroll
-          for (int k = 0; k < 24; k++) o[k] += cc * yv[k];
+          for (int k = 0; k < 24; k++) o[k] = fmadd(cc, yv[k], o[k]);
         }
         if (DOT == DOT_TS) {
           // <out, X> and <out, out>, out = t, X = s
           Tm sr = 0, si = 0, tt = 0;
 #pragma unroll
           for (int k = 0; k < 24; k += 2) {
-            sr += o[k] * xv[k] + o[k + 1] * xv[k + 1];
-            si += o[k] * xv[k + 1] - o[k + 1] * xv[k];
-            tt += o[k] * o[k] + o[k + 1] * o[k + 1];
+            dot_acc(sr, si, o[k], o[k + 1], xv[k], xv[k + 1]);
+            norm_acc(tt, o[k], o[k + 1]);
           }
           dv[0] = (double)sr; dv[1] = (double)si; dv[2] = (double)tt;
         }
@@ -303,16 +345,13 @@ __global__ void __launch_bounds__(256, sizeof(Tm) == 8 ? 2 : (sizeof(Ts) == 2 ? 
         make_field<Ts>(const_cast<void*>(a.R), g.Vh, sh.N).load(site, sys, rv);
         Tm sr = 0, si = 0;
 #pragma unroll
-        for (int k = 0; k < 24; k += 2) {
-          sr += rv[k] * o[k] + rv[k + 1] * o[k + 1];
-          si += rv[k] * o[k + 1] - rv[k + 1] * o[k];
-        }
+        for (int k = 0; k < 24; k += 2) dot_acc(sr, si, rv[k], rv[k + 1], o[k], o[k + 1]);
         dv[0] = (double)sr; dv[1] = (double)si;
       }
       if (DOT == DOT_NORM) {
         Tm nn = 0;
 #pragma unroll
-        for (int k = 0; k < 24; k++) nn += o[k] * o[k];
+        for (int k = 0; k < 24; k += 2) norm_acc(nn, o[k], o[k + 1]);
         dv[0] = (double)nn;
       }
       out.store(site, sys, o);
@@ -541,14 +580,13 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
         Tm xv[24];
         fetch(8, xv);
 #pragma unroll
-        for (int k = 0; k < 24; k++) o[k] = ca * xv[k] + cb * acc[k];
+        for (int k = 0; k < 24; k++) o[k] = axpby(ca, xv[k], cb, acc[k]);
         if (DOT == DOT_TS) {
           Tm sr = 0, si = 0, tt = 0;
 #pragma unroll
           for (int k = 0; k < 24; k += 2) {
-            sr += o[k] * xv[k] + o[k + 1] * xv[k + 1];
-            si += o[k] * xv[k + 1] - o[k + 1] * xv[k];
-            tt += o[k] * o[k] + o[k + 1] * o[k + 1];
+            dot_acc(sr, si, o[k], o[k + 1], xv[k], xv[k + 1]);
+            norm_acc(tt, o[k], o[k + 1]);
           }
           dv[0] = (double)sr; dv[1] = (double)si; dv[2] = (double)tt;
         }
@@ -558,10 +596,7 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
         fetch(8 + (HAS_X ? 1 : 0), rv);
         Tm sr = 0, si = 0;
 #pragma unroll
-        for (int k = 0; k < 24; k += 2) {
-          sr += rv[k] * o[k] + rv[k + 1] * o[k + 1];
-          si += rv[k] * o[k + 1] - rv[k + 1] * o[k];
-        }
+        for (int k = 0; k < 24; k += 2) dot_acc(sr, si, rv[k], rv[k + 1], o[k], o[k + 1]);
         dv[0] = (double)sr; dv[1] = (double)si;
       }
       make_field<Ts>(a.out, g.Vh, sh.N).store(site, sys, o);
@@ -598,6 +633,292 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
       }
     }
   }
+}
+
+}  // namespace fs
+
+namespace fs {
+
+// ---- persistent, cross-chunk pipelined variant (32 systems per warp) -------------
+// A warp holds one site and the 32 systems of a system chunk (lane = system); a
+// block holds the 8 sites of one site chunk, i.e. one 8-site dot group. The grid
+// is persistent (resident blocks x SMs) and each block sweeps the site chunks
+// blockIdx.x, blockIdx.x + gridDim.x, ... Every thread streams its operands,
+// item n = j NITEM + i (chunk j, operand i: the 8 neighbour spinors, then X and R),
+// through a ring of PF shared-memory slots, PF items ahead of the arithmetic and
+// across chunk boundaries, so the copies of the next site overlap the arithmetic
+// of the current one. The raw links of a chunk travel with its item 0 (lanes 0-7,
+// one direction each); lane d then reconstructs link d once for the warp, folding
+// in the antiperiodic t phase, and the 32 lanes read it from shared memory.
+// Neighbour indices are computed lane-parallel (lane d: direction d & 7) and
+// broadcast with a shuffle when an item is issued.
+template <typename Tg>
+__host__ __device__ constexpr int link_chunks16(int nr) {
+  return link_pad<Tg>(nr) * (int)sizeof(Tg) / 16;
+}
+
+template <bool COND> struct BoolC { static constexpr bool value = COND; };
+template <int I> struct IntC { static constexpr int value = I; };
+
+template <typename Ts, typename Tg, typename Tm, int NR, int COEF, int DOT, int PF>
+__global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
+  static_assert(!std::is_same<Tm, double>::value, "the pipelined hop kernel computes in FP32");
+  constexpr int K = DotK<DOT>::K;
+  constexpr int KK = K > 0 ? K : 1;
+  constexpr int CV = chunks16<Ts>();
+  constexpr int VW = Store<Ts>::VW;
+  constexpr bool HAS_X = COEF != COEF_PLAIN;
+  constexpr bool HAS_R = DOT == DOT_R;
+  constexpr int NITEM = 8 + (HAS_X ? 1 : 0) + (HAS_R ? 1 : 0);
+  static_assert(PF >= 1 && PF < NITEM, "ring depth");
+  constexpr int RPC = link_chunks16<Tg>(NR);  // 16-byte chunks per stored link
+  constexpr int RP = link_pad<Tg>(NR);
+  constexpr int GVW = Store<Tg>::VW;
+  extern __shared__ uint4 ring[];             // [PF][CV][256 threads]
+  __shared__ double dsm[2][8][32][KK];        // dot values of chunk parity j & 1: [site][system]
+  __shared__ __align__(16) float lsm[8 * 8 * LINK_F32];  // [warp][direction][20]
+  __shared__ uint4 lraw[2 * 8 * 8 * RPC];     // raw links, double buffered by chunk parity
+  if (a.gate != nullptr && *a.gate == 0) return;
+  const Shape sh = a.sh;
+  const Geom g = a.g;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int sys = blockIdx.y * 32 + lane;
+  const bool sel = sys < sh.N && selected(a.st, sys, a.mask);
+  Tm ca = 0, cb = 1;
+  if (sel) {
+    const SysState& s = a.st[sys];
+    if (COEF == COEF_MHAT) { ca = coef<Tm>(s, C_A); cb = coef<Tm>(s, C_MINV4A); }
+    else if (COEF == COEF_DSLASH) { ca = coef<Tm>(s, C_A); cb = (Tm)-0.5; }
+  }
+  const size_t cstride = (size_t)g.Vh * sh.N * VW;  // elements between 16-byte chunks c and c+1
+  const size_t rowstride = (size_t)sh.N * VW;        // elements between consecutive sites
+  const Ts* in_base = (const Ts*)a.in + (size_t)sys * VW;
+  const int G = gridDim.x;
+  const int nmine = (sh.nchunk - (int)blockIdx.x + G - 1) / G;  // chunks of this block (uniform)
+  if (a.work != nullptr) {  // profiling: (site, system) pairs computed, one atomic per warp
+    const unsigned m = __ballot_sync(0xffffffffu, sel);
+    if (lane == 0 && m && nmine > 0) atomicAdd(a.work, (unsigned long long)__popc(m) * (unsigned long long)nmine);
+  }
+  const int dl = lane & 7, mul = dl >> 1;  // the direction this lane computes neighbours for
+  auto site_of = [&](int j) { return ((int)blockIdx.x + j * G) * 8 + warp; };
+  // neighbour of site in direction dl, and the boundary phase of that hop
+  // (unrolled over mu with selects: a lane-dependent array index would put the
+  // geometry in local memory)
+  auto neighbour = [&](int site, int& nb, float& ph) {
+    int x[4];
+    cb_coords(g, a.p_out, site, x);
+    ph = 1.f;
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+      if (m == mul) {
+        int y = x[m];
+        if ((dl & 1) == 0) {
+          y += 1;
+          if (y == g.L[m]) { y = 0; if (m == 3) ph = (float)g.bc_t; }
+        } else {
+          y -= 1;
+          if (y < 0) { y = g.L[m] - 1; if (m == 3) ph = (float)g.bc_t; }
+        }
+        x[m] = y;
+      }
+    }
+    nb = cb_index(g, x);
+  };
+  int nbc = 0, nbn = 0;
+  float phc = 1.f, phn = 1.f;
+  if (nmine > 0) neighbour(site_of(0), nbc, phc);
+  if (nmine > 1) neighbour(site_of(1), nbn, phn);
+
+  auto slot_of = [&](int j, int i) { return (NITEM % PF == 0) ? (i % PF) : ((j * NITEM + i) % PF); };
+  // issue operand I of chunk j (NEXT: j is the chunk after the current one)
+  auto issue = [&](auto Ic, auto NEXTc, int j) {
+    constexpr int I = decltype(Ic)::value;
+    constexpr bool NEXT = decltype(NEXTc)::value;
+    if (j < nmine) {
+      const int nbl = NEXT ? nbn : nbc;
+      const int site = site_of(j);
+      if (I == 0 && lane < 8) {
+        // raw link of direction d = lane: U_mu(x) forward, U_mu(x - mu) backward
+        const int ls = (dl & 1) ? nbl : site;
+        const int par = (dl & 1) ? 1 - a.p_out : a.p_out;
+        const Tg* src = (const Tg*)a.gauge + ((size_t)(par * 4 + mul) * g.Vh + ls) * RP;
+        uint4* dst = lraw + (((j & 1) * 8 + warp) * 8 + dl) * RPC;
+#pragma unroll
+        for (int c = 0; c < RPC; c++) cp_async16(dst + c, src + c * (16 / sizeof(Tg)));
+      }
+      const Ts* src;
+      if constexpr (I < 8) {
+        const int nbi = __shfl_sync(0xffffffffu, nbl, I);
+        src = in_base + (size_t)nbi * rowstride;
+      } else {
+        const Ts* base = (HAS_X && I == 8) ? (const Ts*)a.X : (const Ts*)a.R;
+        src = base + (size_t)site * rowstride + (size_t)sys * VW;
+      }
+      if (sel) {
+        uint4* dst = ring + (size_t)slot_of(j, I) * CV * 256 + threadIdx.x;
+#pragma unroll
+        for (int c = 0; c < CV; c++) cp_async16(dst + c * 256, src + c * cstride);
+      }
+    }
+    cp_async_commit();  // one group per item (empty when idle) keeps the wait counts uniform
+  };
+  // item I of chunk j, PF items ahead of item D being consumed
+  auto issue_ahead = [&](auto Dc, int j) {
+    constexpr int N2 = decltype(Dc)::value + PF;
+    if constexpr (N2 < NITEM) issue(IntC<N2>{}, BoolC<false>{}, j);
+    else issue(IntC<N2 - NITEM>{}, BoolC<true>{}, j + 1);
+  };
+  auto fetch_chunk = [&](int slot, int c, Tm* v) {
+    const uint4 w = ring[((size_t)slot * CV + c) * 256 + threadIdx.x];
+    load_vec<Ts, Tm>(reinterpret_cast<const Ts*>(&w), v);
+  };
+
+  // prologue: the first PF operands of chunk 0
+  issue(IntC<0>{}, BoolC<false>{}, 0);
+  if constexpr (PF > 1) issue(IntC<1>{}, BoolC<false>{}, 0);
+  if constexpr (PF > 2) issue(IntC<2>{}, BoolC<false>{}, 0);
+  if constexpr (PF > 3) issue(IntC<3>{}, BoolC<false>{}, 0);
+  if constexpr (PF > 4) issue(IntC<4>{}, BoolC<false>{}, 0);
+  if constexpr (PF > 5) issue(IntC<5>{}, BoolC<false>{}, 0);
+  static_assert(PF <= 6, "prologue covers at most 6 ring slots");
+
+  for (int j = 0; j < nmine; j++) {
+    const int site = site_of(j);
+    Tm acc[24];
+#pragma unroll
+    for (int k = 0; k < 24; k++) acc[k] = 0;
+    const float* wl = lsm + warp * 8 * LINK_F32;
+#pragma unroll
+    for (int d = 0; d < 8; d++) {
+      cp_async_wait<PF - 1>();
+      if (d == 0) {
+        // this chunk's raw links arrived with its item 0: lane d reconstructs link d
+        __syncwarp();  // every lane is done with the previous chunk's links
+        if (lane < 8) {
+          const Tg* rawp = reinterpret_cast<const Tg*>(lraw + (((j & 1) * 8 + warp) * 8 + lane) * RPC);
+          Tm tmp[RP];
+#pragma unroll
+          for (int c = 0; c < RP / GVW; c++) load_vec<Tg, Tm>(rawp + c * GVW, tmp + c * GVW);
+          Tm u[18];
+#pragma unroll
+          for (int k = 0; k < NR; k++) u[k] = tmp[k];
+          if constexpr (NR == 12) link_row3(u);
+          float* dst = lsm + (warp * 8 + lane) * LINK_F32;
+#pragma unroll
+          for (int q = 0; q < 18; q++) dst[q] = (float)u[q] * phc;  // t phase folded in (lanes 6, 7)
+        }
+        __syncwarp();
+      }
+      Tm psi[24], u[18];
+      if (sel) {
+        const int slot = slot_of(j, d);
+#pragma unroll
+        for (int c = 0; c < CV; c++) fetch_chunk(slot, c, psi + c * VW);
+        const float4* src4 = reinterpret_cast<const float4*>(wl + d * LINK_F32);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const float4 w = src4[q];
+          u[4 * q] = w.x; u[4 * q + 1] = w.y; u[4 * q + 2] = w.z; u[4 * q + 3] = w.w;
+        }
+        const float2 w2 = *reinterpret_cast<const float2*>(wl + d * LINK_F32 + 16);
+        u[16] = w2.x; u[17] = w2.y;
+      }
+      switch (d) {  // the slot just read is refilled (d is a constant after unrolling)
+        case 0: issue_ahead(IntC<0>{}, j); break;
+        case 1: issue_ahead(IntC<1>{}, j); break;
+        case 2: issue_ahead(IntC<2>{}, j); break;
+        case 3: issue_ahead(IntC<3>{}, j); break;
+        case 4: issue_ahead(IntC<4>{}, j); break;
+        case 5: issue_ahead(IntC<5>{}, j); break;
+        case 6: issue_ahead(IntC<6>{}, j); break;
+        default: issue_ahead(IntC<7>{}, j); break;
+      }
+      if (sel) {
+        switch (d) {
+          case 0: hop_dir<0, -1, false>(acc, psi, u, (Tm)1); break;
+          case 1: hop_dir<0, +1, true>(acc, psi, u, (Tm)1); break;
+          case 2: hop_dir<1, -1, false>(acc, psi, u, (Tm)1); break;
+          case 3: hop_dir<1, +1, true>(acc, psi, u, (Tm)1); break;
+          case 4: hop_dir<2, -1, false>(acc, psi, u, (Tm)1); break;
+          case 5: hop_dir<2, +1, true>(acc, psi, u, (Tm)1); break;
+          case 6: hop_dir<3, -1, false>(acc, psi, u, (Tm)1); break;
+          default: hop_dir<3, +1, true>(acc, psi, u, (Tm)1); break;
+        }
+      }
+    }
+    double dv[KK];
+#pragma unroll
+    for (int k = 0; k < KK; k++) dv[k] = 0.0;
+    if constexpr (HAS_X) {
+      // out = ca X + cb (H in), in place of acc, one 16-byte chunk of X at a time
+      cp_async_wait<PF - 1>();
+      Tm sr = 0, si = 0, tt = 0;
+      if (sel) {
+        const int slot = slot_of(j, 8);
+#pragma unroll
+        for (int c = 0; c < CV; c++) {
+          Tm xv[VW];
+          fetch_chunk(slot, c, xv);
+#pragma unroll
+          for (int k = 0; k < VW; k++) acc[c * VW + k] = axpby(ca, xv[k], cb, acc[c * VW + k]);
+          if constexpr (DOT == DOT_TS) {  // <out, X> and <out, out>, out = t, X = s
+#pragma unroll
+            for (int k = 0; k < VW; k += 2) {
+              dot_acc(sr, si, acc[c * VW + k], acc[c * VW + k + 1], xv[k], xv[k + 1]);
+              norm_acc(tt, acc[c * VW + k], acc[c * VW + k + 1]);
+            }
+          }
+        }
+      }
+      issue_ahead(IntC<8>{}, j);
+      if constexpr (DOT == DOT_TS) { dv[0] = (double)sr; dv[1] = (double)si; dv[2] = (double)tt; }
+    }
+    if constexpr (HAS_R) {
+      cp_async_wait<PF - 1>();
+      Tm sr = 0, si = 0;
+      if (sel) {
+        const int slot = slot_of(j, NITEM - 1);
+#pragma unroll
+        for (int c = 0; c < CV; c++) {
+          Tm rv[VW];
+          fetch_chunk(slot, c, rv);
+#pragma unroll
+          for (int k = 0; k < VW; k += 2) dot_acc(sr, si, rv[k], rv[k + 1], acc[c * VW + k], acc[c * VW + k + 1]);
+        }
+      }
+      issue_ahead(IntC<NITEM - 1>{}, j);
+      dv[0] = (double)sr; dv[1] = (double)si;
+    }
+    if (sel) make_field<Ts>(a.out, g.Vh, sh.N).store(site, sys, acc);
+    if constexpr (K > 0) {
+      // the block's 8 sites form the 8-site group `chunk`; summed in site order by one warp
+      const int par = j & 1;
+#pragma unroll
+      for (int k = 0; k < K; k++) dsm[par][warp][lane][k] = dv[k];
+      __syncthreads();
+      if (warp == (j & 7)) {
+        const int chunk = (int)blockIdx.x + j * G;
+        const int ngroups = g.Vh / 8;
+        if (sys < sh.N) {
+          double s[KK];
+#pragma unroll
+          for (int k = 0; k < K; k++) s[k] = 0.0;
+          for (int w = 0; w < 8; w++) {
+#pragma unroll
+            for (int k = 0; k < K; k++) s[k] += dsm[par][w][lane][k];
+          }
+#pragma unroll
+          for (int k = 0; k < K; k++) a.partial[((size_t)sys * K + k) * ngroups + chunk] = s[k];
+        }
+      }
+      // dsm[par] is rewritten two chunks later, after the next barrier: no second barrier
+    }
+    // the next chunk becomes current
+    nbc = nbn;
+    phc = phn;
+    if (j + 2 < nmine) neighbour(site_of(j + 2), nbn, phn);
+  }
+  cp_async_wait<0>();
 }
 
 }  // namespace fs

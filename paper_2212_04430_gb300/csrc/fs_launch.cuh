@@ -1,6 +1,8 @@
 // Kernel launchers, instantiated once per storage precision (fs_kern_*.cu).
 #pragma once
 
+#include <algorithm>
+
 #include "fs_engine.h"
 
 namespace fs {
@@ -11,8 +13,48 @@ using MathOf = typename std::conditional<std::is_same<Ts, double>::value, double
 // Directions kept in flight by the prefetching hop kernel (shared-memory ring slots).
 template <typename Ts> constexpr int hop_pf() { return sizeof(Ts) == 2 ? 4 : 3; }
 
+// Ring depth of the persistent kernel: a divisor of the items per site where the
+// shared memory allows (static ring slots), two resident blocks per SM.
+template <typename Ts, int C, int D>
+constexpr int hop_pp_depth() {
+  constexpr int nitem = 8 + (C != COEF_PLAIN ? 1 : 0) + (D == DOT_R ? 1 : 0);
+  if constexpr (sizeof(Ts) == 2) return nitem == 8 ? 4 : (nitem == 9 ? 3 : 5);
+  return 3;
+}
+
+struct PersistentGrid {
+  cudaError_t err = cudaSuccess;
+  int blocks_per_sm = 0, nsm = 0;
+};
+
+template <typename Ts, typename Tg, typename Tm, int R, int C, int D>
+cudaError_t launch_hop_pp(const HopArgs& a, const Launch& l) {
+  constexpr int PF = hop_pp_depth<Ts, C, D>();
+  auto kern = hop_kernel_pp<Ts, Tg, Tm, R, C, D, PF>;
+  const size_t smem = hop_pf_smem<Ts, PF>(256);
+  // thread-safe one-time set-up: shared-memory opt-in and the resident grid
+  static const PersistentGrid pg = [&] {
+    PersistentGrid p;
+    int dev = 0;
+    if ((p.err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return p;
+    if ((p.err = cudaGetDevice(&dev))) return p;
+    if ((p.err = cudaDeviceGetAttribute(&p.nsm, cudaDevAttrMultiProcessorCount, dev))) return p;
+    p.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p.blocks_per_sm, kern, 256, smem);
+    if (!p.err && p.blocks_per_sm < 1) p.err = cudaErrorInvalidConfiguration;
+    return p;
+  }();
+  if (pg.err) return pg.err;
+  const int gy = l.grid_y;
+  const int gx = std::max(1, std::min(a.sh.nchunk, pg.blocks_per_sm * pg.nsm / std::max(gy, 1)));
+  kern<<<dim3(gx, gy), 256, smem, l.stream>>>(a);
+  note_launch();
+  return cudaGetLastError();
+}
+
 template <typename Ts, typename Tg, typename Tm, int R, int C, int D>
 cudaError_t launch_hop_pf(const HopArgs& a, const Launch& l) {
+  // 32 systems per warp, 8 sites per block: the persistent pipelined kernel
+  if (a.sh.NB == 32 && a.sh.SB == 8 && l.block == 256) return launch_hop_pp<Ts, Tg, Tm, R, C, D>(a, l);
   constexpr int PF = hop_pf<Ts>();
   const size_t smem = hop_pf_smem<Ts, PF>(l.block);
   // thread-safe one-time set-up (several server workers may launch concurrently)

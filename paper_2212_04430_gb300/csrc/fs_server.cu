@@ -120,7 +120,12 @@ struct fs_server {
         double trace[FS_JOB_MAX_LEVELS * 2], var[FS_JOB_MAX_LEVELS];
         rc = mlmc_level_trace(ctx, &j->P, trace, var, nullptr, st.data());
         long long it = 0;
-        for (int k = 0; k < nsolve; k++) it += st[k].iters;
+        for (int k = 0; k < nsolve; k++) {
+          it += st[k].iters;
+          r.max_iters = std::max(r.max_iters, st[k].iters);
+          r.noconv += st[k].status != FS_SYS_CONVERGED;
+          r.restarts += st[k].restarts;
+        }
         for (int l = 0; l < j->P.nlev; l++) {
           r.trace[l][0] = trace[2 * l];
           r.trace[l][1] = trace[2 * l + 1];

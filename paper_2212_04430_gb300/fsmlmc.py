@@ -61,6 +61,7 @@ class Job(ctypes.Structure):
 class JobResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("nlev", ctypes.c_int), ("trace", (ctypes.c_double * 2) * 16),
                 ("var", ctypes.c_double * 16), ("solves", ctypes.c_longlong), ("mean_iters", ctypes.c_double),
+                ("max_iters", ctypes.c_int), ("noconv", ctypes.c_int), ("restarts", ctypes.c_longlong),
                 ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double)]
 
 
@@ -349,6 +350,7 @@ class Server:
         n = r.nlev
         return {"status": r.status, "trace": np.array([r.trace[l][0] + 1j * r.trace[l][1] for l in range(n)]),
                 "var": np.array([r.var[l] for l in range(n)]), "solves": r.solves, "mean_iters": r.mean_iters,
+                "max_iters": r.max_iters, "noconv": r.noconv, "restarts": r.restarts,
                 "latency_ms": r.latency_ms, "queue_ms": r.queue_ms}
 
     def stats(self):
