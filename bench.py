@@ -60,7 +60,7 @@ def hop_traffic_ratio(workload):
     if not os.path.exists(path):
         return None
     src = b""
-    for f in ("fs_hop.cuh", "fs_common.cuh"):
+    for f in ("fs_hop.cuh", "fs_common.cuh", "fs_launch.cuh"):
         with open(os.path.join(ROOT, "paper_2212_04430_gb300", "csrc", f), "rb") as fh:
             src += fh.read()
     digest = hashlib.sha256(src).hexdigest()[:16]
