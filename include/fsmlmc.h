@@ -85,7 +85,10 @@ typedef struct fs_solve_params {
   double delta;        /* reliable update when the sloppy residual drops by this factor;
                           0 = library choice                                                 */
   int verify;          /* 1: recompute the full-lattice FP64 residual of every solution      */
-  int pad;
+  int fallback_iter;   /* a system BiCGStab leaves unconverged (breakdowns past the restart
+                          limit, or max_iter) is re-solved by FP64 CGNR on the normal equations
+                          M^dag M x = M^dag b, M^dag = gamma5 M gamma5, for at most this many
+                          iterations; 0 = 4 * max_iter, < 0 = no fallback                     */
 } fs_solve_params;
 
 typedef struct fs_sys_stats {
@@ -94,6 +97,8 @@ typedef struct fs_sys_stats {
   int reliable_updates;
   int restarts;
   double true_resid;   /* ||z - (D+sigma) x|| / ||z|| in FP64                                 */
+  int fallback_iters;  /* CGNR fallback iterations (0: BiCGStab alone)                        */
+  int pad;
 } fs_sys_stats;
 
 typedef struct fs_mlmc_params {

@@ -58,6 +58,9 @@ int resolve_params(Ctx& c, const fs_solve_params* p, int nsys, double m, Opts& o
   if (o.so.delta >= 1.0) return c.fail(FS_ERR_ARG, "delta must be < 1");
   o.so.verify = d.verify;
   o.so.check_every = 4;
+  if (d.fallback_iter < 0) o.so.cg_max_iter = 0;
+  else if (d.fallback_iter > 0) o.so.cg_max_iter = d.fallback_iter;
+  else o.so.cg_max_iter = (int)std::min<long long>(4LL * o.so.max_iter, 1 << 30);
   int tile = d.rhs_tile;
   if (tile < 0 || tile > fs::MAX_TILE) return c.fail(FS_ERR_ARG, "rhs_tile must be in [0, 64]");
   if (tile == 0) tile = std::min(32, std::max(1, nsys));
@@ -72,6 +75,8 @@ void fill_stats(const fs::SysState& s, fs_sys_stats* out, bool verify) {
   out->restarts = s.restarts;
   const double r2 = verify ? s.r2_full : s.r2_true;
   out->true_resid = s.b2 > 0 ? std::sqrt(r2 / s.b2) : 0.0;
+  out->fallback_iters = s.cg_iters;
+  out->pad = 0;
 }
 
 // Tile for a job list: at least the largest group, at most 64 systems.

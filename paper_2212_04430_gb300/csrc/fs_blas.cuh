@@ -185,9 +185,92 @@ __global__ void __launch_bounds__(256) blas_kernel(BlasArgs a) {
   }
 }
 
+// ---- CGNR fallback (FP64) ------------------------------------------------------
+// A system BiCGStab could not solve (breakdowns past the restart limit, or
+// max_iter) is re-solved by conjugate gradients on the normal equations
+// M^dag M x = M^dag bhat, with M^dag = gamma5 M gamma5 (gamma5-hermiticity of the
+// Wilson operator carries over to the even-odd Schur complement). CG on a
+// Hermitian positive definite operator cannot break down. The residual of the
+// original system, s = bhat - M x, is carried along (s -= alpha q) to decide
+// convergence, and replaced by the true FP64 residual every 64 iterations and at
+// apparent convergence.
+enum CgOp {
+  CG_XS = 0,  // x += alpha p ; s -= alpha q ; ||s||^2
+  CG_G5 = 1,  // g = gamma5 s
+  CG_R = 2,   // r = gamma5 w ; ||r||^2
+  CG_P = 3,   // p = r + beta p
+  CG_P0 = 4,  // p = r
+};
+
+struct CgArgs {
+  double *x, *s, *p, *q, *g, *w, *r;
+  const SysState* st;
+  double* partial;
+  int Vh;
+  Shape sh;
+  int mask;
+};
+
+template <int OP>
+__global__ void __launch_bounds__(256) cg_kernel(CgArgs a) {
+  constexpr int K = (OP == CG_XS || OP == CG_R) ? 1 : 0;
+  __shared__ double smem[256];
+  const Shape sh = a.sh;
+  const int lsys = threadIdx.x % sh.NB;
+  const int lsite = threadIdx.x / sh.NB;
+  const int sys = blockIdx.y * sh.NB + lsys;
+  const bool sel = sys < sh.N && selected(a.st, sys, a.mask);
+  const double alpha = sel ? a.st[sys].cd[C_ALPHA] : 0.0;
+  const double beta = sel ? a.st[sys].cd[C_BETA] : 0.0;
+  const Field<double> fx = make_field<double>(a.x, a.Vh, sh.N), fs = make_field<double>(a.s, a.Vh, sh.N);
+  const Field<double> fp = make_field<double>(a.p, a.Vh, sh.N), fq = make_field<double>(a.q, a.Vh, sh.N);
+  const Field<double> fg = make_field<double>(a.g, a.Vh, sh.N), fw = make_field<double>(a.w, a.Vh, sh.N);
+  const Field<double> fr = make_field<double>(a.r, a.Vh, sh.N);
+  for (int chunk = blockIdx.x; chunk < sh.nchunk; chunk += gridDim.x) {
+    const int site = chunk * sh.SB + lsite;
+    const bool act = sel && site < a.Vh;
+    double dv[1] = {0.0};
+    if (act) {
+      double u[24], v[24];
+      if constexpr (OP == CG_XS) {
+        fx.load(site, sys, u); fp.load(site, sys, v);
+#pragma unroll
+        for (int k = 0; k < 24; k++) u[k] = fma(alpha, v[k], u[k]);
+        fx.store(site, sys, u);
+        fs.load(site, sys, u); fq.load(site, sys, v);
+#pragma unroll
+        for (int k = 0; k < 24; k++) u[k] = fma(-alpha, v[k], u[k]);
+        fs.store(site, sys, u);
+#pragma unroll
+        for (int k = 0; k < 24; k++) dv[0] = fma(u[k], u[k], dv[0]);
+      } else if constexpr (OP == CG_G5 || OP == CG_R) {
+        // gamma5 = diag(1, 1, -1, -1) in spin (DeGrand-Rossi): negate spin components 2, 3
+        (OP == CG_G5 ? fs : fw).load(site, sys, u);
+#pragma unroll
+        for (int k = 12; k < 24; k++) u[k] = -u[k];
+        (OP == CG_G5 ? fg : fr).store(site, sys, u);
+        if constexpr (OP == CG_R) {
+#pragma unroll
+          for (int k = 0; k < 24; k++) dv[0] = fma(u[k], u[k], dv[0]);
+        }
+      } else if constexpr (OP == CG_P) {
+        fr.load(site, sys, u); fp.load(site, sys, v);
+#pragma unroll
+        for (int k = 0; k < 24; k++) u[k] = fma(beta, v[k], u[k]);
+        fp.store(site, sys, u);
+      } else {
+        fr.load(site, sys, u);
+        fp.store(site, sys, u);
+      }
+    }
+    if constexpr (K > 0) group_partials<K>(dv, lsite, lsys, blockIdx.y * sh.NB, sh, a.Vh, chunk, smem, a.partial);
+  }
+}
+
 // ---- finalize: one block per system sums its group partials in fixed order ----
 enum FinOp { FIN_ALPHA = 0, FIN_OMEGA = 1, FIN_RHO = 2, FIN_TRUE = 3, FIN_UPDATE = 4, FIN_INIT = 5,
-             FIN_NORM = 6, FIN_VERIFY = 7 };
+             FIN_NORM = 6, FIN_VERIFY = 7, FIN_CG_INIT = 8, FIN_CG_ALPHA = 9, FIN_CG_BETA = 10,
+             FIN_CG_TRUE = 11 };
 
 struct FinArgs {
   SysState* st;
@@ -372,6 +455,58 @@ __global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
     fin_sum<1>(a.pa, a.ngroups, sys, e, sm);
     fin_sum<1>(a.pb, a.ngroups, sys, o, sm);
     if (threadIdx.x == 0) s.r2_full = e[0] + o[0];
+  } else if (op == FIN_CG_INIT) {
+    // pa = ||s||^2 (s = bhat - M x), pb = ||r||^2 (r = M^dag s)
+    double sv[1], rv[1];
+    fin_sum<1>(a.pa, a.ngroups, sys, sv, sm);
+    fin_sum<1>(a.pb, a.ngroups, sys, rv, sm);
+    if (threadIdx.x == 0) {
+      s.r2_true = sv[0];
+      s.r2 = sv[0];
+      s.rho[0] = rv[0]; s.rho[1] = 0.0;
+      s.cg_iters = 0;
+      if (sv[0] <= s.tol2) { s.status = SYS_CONVERGED; s.flags = 0; }
+      else if (!(rv[0] > 0.0) || !isfinite(rv[0]) || !isfinite(sv[0])) { s.status = SYS_NOCONV; s.flags = 0; }
+      else s.flags = FLAG_CG;
+    }
+  } else if (op == FIN_CG_ALPHA) {
+    double qv[1];
+    fin_sum<1>(a.pa, a.ngroups, sys, qv, sm);  // ||M p||^2
+    if (threadIdx.x == 0) {
+      const double al = s.rho[0] / qv[0];
+      if (!(qv[0] > 0.0) || !isfinite(al)) { s.status = SYS_NOCONV; s.flags = 0; }
+      s.alpha[0] = al; s.alpha[1] = 0.0;
+      set_coef(s, C_ALPHA, al); set_coef(s, C_ALPHA + 1, 0.0);
+    }
+  } else if (op == FIN_CG_BETA) {
+    // pa = ||s||^2 after the step, pb = ||r||^2 of the new normal residual
+    double sv[1], rv[1];
+    fin_sum<1>(a.pa, a.ngroups, sys, sv, sm);
+    fin_sum<1>(a.pb, a.ngroups, sys, rv, sm);
+    if (threadIdx.x == 0) {
+      s.cg_iters += 1;
+      s.r2 = sv[0];
+      const double be = rv[0] / s.rho[0];
+      s.rho_old[0] = s.rho[0];
+      s.rho[0] = rv[0];
+      set_coef(s, C_BETA, be); set_coef(s, C_BETA + 1, 0.0);
+      if (!isfinite(be) || !isfinite(sv[0])) { s.status = SYS_NOCONV; s.flags = 0; }
+      else {
+        if (sv[0] <= s.tol2 || (s.cg_iters & 63) == 0 || s.cg_iters >= s.cg_max_iter) s.flags |= FLAG_UPDATE;
+        if (s.cg_iters >= s.cg_max_iter) s.flags |= FLAG_FINAL;
+      }
+    }
+  } else if (op == FIN_CG_TRUE) {
+    double tv[1];
+    fin_sum<1>(a.pa, a.ngroups, sys, tv, sm);  // ||bhat - M x||^2 in FP64; s now holds that residual
+    if (threadIdx.x == 0) {
+      s.r2_true = tv[0];
+      s.r2 = tv[0];
+      s.updates += 1;
+      if (tv[0] <= s.tol2) { s.status = SYS_CONVERGED; s.flags = 0; }
+      else if ((s.flags & FLAG_FINAL) || !isfinite(tv[0])) { s.status = SYS_NOCONV; s.flags = 0; }
+      else s.flags &= ~FLAG_UPDATE;
+    }
   }
 }
 #endif  // FS_ENGINE_KERNELS

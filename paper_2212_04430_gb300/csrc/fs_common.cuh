@@ -189,7 +189,8 @@ template <typename Tg> __host__ __device__ constexpr int link_pad(int nr) {
 
 // ---- per-system solver state (device resident, one entry per tile slot) ----
 enum SysStatus { SYS_IDLE = 0, SYS_ACTIVE = 1, SYS_CONVERGED = 2, SYS_NOCONV = 3 };
-enum SysFlags { FLAG_UPDATE = 1, FLAG_RESTART = 2, FLAG_FINAL = 4, FLAG_INIT = 8, FLAG_HARVEST = 16 };
+enum SysFlags { FLAG_UPDATE = 1, FLAG_RESTART = 2, FLAG_FINAL = 4, FLAG_INIT = 8, FLAG_HARVEST = 16,
+                FLAG_CG = 32 };  // FLAG_CG: the system is in the CGNR fallback
 
 // Indices into SysState::cd / cf.
 enum CoefIdx {
@@ -229,7 +230,8 @@ struct SysState {
   int updates;
   int restarts;
   int max_iter;
-  int pad[2];
+  int cg_iters;               // CGNR fallback iterations
+  int cg_max_iter;
 };
 
 template <typename Tm>

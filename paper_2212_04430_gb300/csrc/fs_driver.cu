@@ -57,6 +57,34 @@ cudaError_t upload_vec(Ctx* c, TileBase* T) {
   return cudaMemcpyAsync(T->vec_d, T->vec_h, sizeof(int) * T->N, cudaMemcpyHostToDevice, c->stream);
 }
 
+// CGNR fallback for the slots BiCGStab left unconverged: bounded host loop of
+// device iterations; returns with the stream idle and st_h current.
+int run_cg(Ctx* c, TileBase* T, const std::vector<int>& slots, const SolveOpts& o) {
+  if (T->cg_alloc()) return c->fail(3, "device allocation of the CGNR fallback vectors failed");
+  for (int j : slots) {
+    SysState& s = T->st_h[j];
+    s.status = SYS_ACTIVE;
+    s.flags = FLAG_CG;
+    s.cg_iters = 0;
+    s.cg_max_iter = o.cg_max_iter;
+  }
+  cudaError_t e = upload_slots(c, T, slots);
+  if (!e) e = T->enqueue_cg_init();
+  if (e) return c->cuda_fail(e, "CGNR fallback initialisation");
+  const int every = 16;
+  const long long bound = (long long)o.cg_max_iter + 2 * every;
+  for (long long it = 0;; it += every) {
+    for (int k = 0; k < every && !e; k++) e = T->enqueue_cg_iter();
+    if (!e) e = cudaMemcpyAsync(T->st_h, T->st_d, sizeof(SysState) * T->N, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return c->cuda_fail(e, "CGNR fallback iteration");
+    bool active = false;
+    for (int j : slots) active |= T->st_h[j].status == SYS_ACTIVE;
+    if (!active) return 0;
+    if (it > bound) return c->fail(6, "CGNR fallback did not terminate within its iteration bound");
+  }
+}
+
 }  // namespace
 
 int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpts& o, const QOut& out) {
@@ -69,6 +97,7 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
   struct Slot {
     int job = -1, member = -1, phase = 0;
     bool done = false;
+    bool cg_tried = false;  // the CGNR fallback ran on this phase
   };
   std::vector<Slot> slot(N);
   std::vector<int> free_slots;
@@ -152,11 +181,16 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
     // ---- find finished systems
     std::vector<int> chain_slots;
     std::vector<int> done_jobs;
+    std::vector<int> cg_slots;
     for (int j = 0; j < N; j++) {
       Slot& sl = slot[j];
       if (sl.job < 0 || sl.done) continue;
       const SysState& s = T->st_h[j];
       if (s.status != SYS_CONVERGED && s.status != SYS_NOCONV) continue;
+      if (s.status == SYS_NOCONV && o.cg_max_iter > 0 && !sl.cg_tried) {
+        cg_slots.push_back(j);
+        continue;
+      }
       const QJob& q = jobs[sl.job];
       const bool has_chain = !q.chain.empty() && !std::isnan(q.chain[sl.member]);
       if (s.status != SYS_CONVERGED && out.noconv) *out.noconv = 1;
@@ -166,6 +200,13 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
       }
       sl.done = true;
       if (--remaining[sl.job] == 0) done_jobs.push_back(sl.job);
+    }
+    if (!cg_slots.empty()) {
+      // BiCGStab failed on these systems: CGNR from their last reliable iterate; the next
+      // pass through the loop harvests them with the fallback's verdict
+      if (int rc = run_cg(c, T, cg_slots, o)) return rc;
+      for (int j : cg_slots) slot[j].cg_tried = true;
+      continue;
     }
     if (chain_slots.empty() && done_jobs.empty()) continue;
 
@@ -273,6 +314,7 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
         T->spec_h[j] = keep;
         T->spec_h[j].flags &= ~(uint32_t)NOISE_RHS;  // the noise stays the contraction's left vector
         slot[j].phase = 1;
+        slot[j].cg_tried = false;
       }
       if (int rc = admit_rhs(chain_slots, true, false)) return rc;
     }

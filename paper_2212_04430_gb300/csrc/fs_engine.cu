@@ -106,6 +106,7 @@ class Tile : public TileBase {
        *tmp = nullptr;
   double *pa = nullptr, *pb = nullptr, *pc = nullptr;
   int* gate = nullptr;
+  double *cg_p = nullptr, *cg_q = nullptr, *cg_g = nullptr, *cg_w = nullptr, *cg_r = nullptr;  // CGNR fallback
   std::vector<void*> owned;
   // K BiCGStab iterations captured once and replayed (launch overhead dominates small lattices)
   cudaGraphExec_t gexec = nullptr;
@@ -347,6 +348,75 @@ class Tile : public TileBase {
     if ((e = hop_lo(COEF_DSLASH, DOT_NONE, he, 1))) return e;
     if ((e = hop_lo(COEF_DSLASH, DOT_NONE, ho, 1))) return e;
     return launch_unpack<Ts>(canon, v, s, vec_d, c->g, sh, L);
+  }
+
+  // ---- CGNR fallback on M^dag M, FP64, system-major (only the FLAG_CG slots work) ----
+  int cg_alloc() override {
+    if (cg_p) return 0;
+    const size_t f64 = (size_t)24 * c->g.Vh * N * sizeof(double);
+    cg_p = (double*)dalloc(f64); cg_q = (double*)dalloc(f64); cg_g = (double*)dalloc(f64);
+    cg_w = (double*)dalloc(f64); cg_r = (double*)dalloc(f64);
+    return (cg_p && cg_q && cg_g && cg_w && cg_r) ? 0 : 3;
+  }
+  CgArgs cga(int mask, double* part) {
+    CgArgs a{};
+    a.x = x_hi; a.s = r_hi; a.p = cg_p; a.q = cg_q; a.g = cg_g; a.w = cg_w; a.r = cg_r;
+    a.st = st_d; a.partial = part; a.Vh = c->g.Vh; a.sh = sh1; a.mask = mask;
+    return a;
+  }
+  template <int OP>
+  cudaError_t cg_op(int mask, double* part = nullptr) {
+    cg_kernel<OP><<<dim3(L1.grid_x, L1.grid_y), 256, 0, c->stream>>>(cga(mask, part));
+    note_launch();
+    return cudaGetLastError();
+  }
+  // r = M^dag s = gamma5 M gamma5 s, ||r||^2 -> part
+  cudaError_t cg_normal_residual(int mask, double* part) {
+    cudaError_t e;
+    if ((e = cg_op<CG_G5>(mask))) return e;
+    if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
+                                hop(tmp64, cg_g, nullptr, nullptr, nullptr, nullptr, 1, mask, false, true, true), L1)))
+      return e;
+    if ((e = launch_hop<double>(COEF_MHAT, DOT_NONE, 18,
+                                hop(cg_w, tmp64, cg_g, nullptr, nullptr, nullptr, 0, mask, false, true, true), L1)))
+      return e;
+    return cg_op<CG_R>(mask, part);
+  }
+  // s = bhat - M x (into r_hi), ||s||^2 -> part
+  cudaError_t cg_true_residual(int mask, double* part) {
+    cudaError_t e;
+    if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
+                                hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, mask, false, true, true), L1)))
+      return e;
+    return launch_hop<double>(COEF_TRUERES, DOT_NORM, 18,
+                              hop(r_hi, tmp64, x_hi, bhat, nullptr, part, 0, mask, false, true, true), L1);
+  }
+  cudaError_t enqueue_cg_init() override {
+    L1.stream = c->stream;
+    cudaError_t e;
+    if ((e = cg_true_residual(MASK_CG, pa))) return e;
+    if ((e = cg_normal_residual(MASK_CG, pb))) return e;
+    if ((e = fin(FIN_CG_INIT, MASK_CG, pa, pb))) return e;
+    return cg_op<CG_P0>(MASK_CG);
+  }
+  cudaError_t enqueue_cg_iter() override {
+    L1.stream = c->stream;
+    cudaError_t e;
+    // q = M p, alpha = <r, r> / ||q||^2
+    if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
+                                hop(tmp64, cg_p, nullptr, nullptr, nullptr, nullptr, 1, MASK_CG, false, true, true), L1)))
+      return e;
+    if ((e = launch_hop<double>(COEF_MHAT, DOT_NORM, 18,
+                                hop(cg_q, tmp64, cg_p, nullptr, nullptr, pa, 0, MASK_CG, false, true, true), L1)))
+      return e;
+    if ((e = fin(FIN_CG_ALPHA, MASK_CG, pa))) return e;
+    if ((e = cg_op<CG_XS>(MASK_CG, pa))) return e;   // x += alpha p, s -= alpha q
+    if ((e = cg_normal_residual(MASK_CG, pb))) return e;
+    if ((e = fin(FIN_CG_BETA, MASK_CG, pa, pb))) return e;
+    // true residual of the systems due a check (every 64 iterations, apparent convergence, the last)
+    if ((e = cg_true_residual(MASK_CG_CHECK, pc))) return e;
+    if ((e = fin(FIN_CG_TRUE, MASK_CG_CHECK, pc))) return e;
+    return cg_op<CG_P>(MASK_CG);
   }
 
   cudaError_t enqueue_solution_to_canon(double* canon) override {

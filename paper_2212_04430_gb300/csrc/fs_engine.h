@@ -84,6 +84,10 @@ class TileBase {
   virtual cudaError_t enqueue_verify() = 0;
   virtual cudaError_t enqueue_solution_to_canon(double* canon) = 0;  // canon[vec[j]] <- x for all j with vec >= 0
   virtual cudaError_t enqueue_dslash(double* canon) = 0;  // canon[vec[j]] <- (D + sigma_j) canon[vec[j]], INIT slots
+  // CGNR fallback (FP64) for the slots flagged FLAG_CG; its vectors are allocated on first use
+  virtual int cg_alloc() = 0;
+  virtual cudaError_t enqueue_cg_init() = 0;
+  virtual cudaError_t enqueue_cg_iter() = 0;
 };
 
 struct Ctx {
@@ -134,6 +138,7 @@ struct SolveOpts {
   double delta;
   int verify;
   int check_every;
+  int cg_max_iter;  // CGNR fallback iterations; 0: no fallback
 };
 
 // A group of systems whose solutions are contracted together (they share the tile

@@ -34,14 +34,18 @@ template <> struct DotK<DOT_R> { static constexpr int K = 2; };
 template <> struct DotK<DOT_TS> { static constexpr int K = 3; };
 template <> struct DotK<DOT_NORM> { static constexpr int K = 1; };
 
-enum Mask { MASK_ALL = 0, MASK_ACTIVE = 1, MASK_UPDATE = 2, MASK_INIT = 3, MASK_HARVEST = 4 };
+enum Mask { MASK_ALL = 0, MASK_ACTIVE = 1, MASK_UPDATE = 2, MASK_INIT = 3, MASK_HARVEST = 4, MASK_CG = 5,
+            MASK_CG_CHECK = 6 };
 
 __device__ __forceinline__ bool selected(const SysState* st, int sys, int mask) {
   if (mask == MASK_ALL) return true;
   const int s = st[sys].status, f = st[sys].flags;
   // a system that broke down earlier in this iteration sits out until its restart
-  if (mask == MASK_ACTIVE) return s == SYS_ACTIVE && !(f & FLAG_RESTART);
-  if (mask == MASK_UPDATE) return s == SYS_ACTIVE && (f & FLAG_UPDATE);
+  if (mask == MASK_ACTIVE) return s == SYS_ACTIVE && !(f & (FLAG_RESTART | FLAG_CG));
+  if (mask == MASK_UPDATE) return s == SYS_ACTIVE && (f & FLAG_UPDATE) && !(f & FLAG_CG);
+  // CGNR fallback systems, and those of them due a true-residual check
+  if (mask == MASK_CG) return s == SYS_ACTIVE && (f & FLAG_CG);
+  if (mask == MASK_CG_CHECK) return s == SYS_ACTIVE && (f & FLAG_CG) && (f & FLAG_UPDATE);
   if (mask == MASK_INIT) return (f & FLAG_INIT) != 0;
   return (f & FLAG_HARVEST) != 0;
 }

@@ -85,6 +85,8 @@ cudaError_t launch_hop(int coef, int dot, int nr, const HopArgs& a, const Launch
     FS_HOP(COEF_DSLASH, DOT_NONE, 18)
     FS_HOP(COEF_MHAT, DOT_R, 18)
     FS_HOP(COEF_MHAT, DOT_TS, 18)
+    FS_HOP(COEF_MHAT, DOT_NORM, 18)   // CGNR fallback: q = M p, ||q||^2
+    FS_HOP(COEF_MHAT, DOT_NONE, 18)   // CGNR fallback: M gamma5 s
     FS_HOP(COEF_PREP, DOT_NORM, 18)
     FS_HOP(COEF_RECON, DOT_NONE, 18)
     FS_HOP(COEF_TRUERES, DOT_NORM, 18)

@@ -38,12 +38,13 @@ class FsError(RuntimeError):
 class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("prec", ctypes.c_int),
                 ("rhs_tile", ctypes.c_int), ("link_compress", ctypes.c_int), ("delta", ctypes.c_double),
-                ("verify", ctypes.c_int), ("pad", ctypes.c_int)]
+                ("verify", ctypes.c_int), ("fallback_iter", ctypes.c_int)]
 
 
 class SysStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("reliable_updates", ctypes.c_int),
-                ("restarts", ctypes.c_int), ("true_resid", ctypes.c_double)]
+                ("restarts", ctypes.c_int), ("true_resid", ctypes.c_double), ("fallback_iters", ctypes.c_int),
+                ("pad", ctypes.c_int)]
 
 
 class MlmcParams(ctypes.Structure):
@@ -133,7 +134,7 @@ def _real(a, shape=None):
     return a
 
 
-def _params(prec="f64", tol=0.0, max_iter=0, rhs_tile=0, link_compress=18, delta=0.0, verify=0):
+def _params(prec="f64", tol=0.0, max_iter=0, rhs_tile=0, link_compress=18, delta=0.0, verify=0, fallback_iter=0):
     p = SolveParams()
     p.tol = tol
     p.max_iter = max_iter
@@ -142,6 +143,7 @@ def _params(prec="f64", tol=0.0, max_iter=0, rhs_tile=0, link_compress=18, delta
     p.link_compress = link_compress
     p.delta = delta
     p.verify = int(verify)
+    p.fallback_iter = int(fallback_iter)
     return p
 
 
@@ -373,7 +375,7 @@ class Server:
 
 def _stats(s):
     return {"iters": s.iters, "status": s.status, "reliable_updates": s.reliable_updates,
-            "restarts": s.restarts, "true_resid": s.true_resid}
+            "restarts": s.restarts, "true_resid": s.true_resid, "fallback_iters": s.fallback_iters}
 
 
 # Module-level functions with the C ABI's names.
