@@ -126,14 +126,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup():
+def dist_setup(backend="nccl"):
+    """Replicas only: one process per GPU, each solving its own noise vectors. The process
+    group carries nothing but the barrier and the two scalar reductions of the timing."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group(backend)
     return ws, rank, local
+
+
+def _reduce_device():
+    import torch.distributed as dist
+    return "cpu" if dist.get_backend() == "gloo" else "cuda"
 
 
 def barrier(ws):
@@ -147,7 +154,7 @@ def max_over_ranks(x, ws):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -157,9 +164,22 @@ def sum_over_ranks(x, ws):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def job_base(rank):
+    """First noise job id of a replica: warm-up, timed and end-to-end steps use
+    base + k, base + 1000 + k and base + 2000 + k, so replicas never share a Z4 vector."""
+    return 100000 * rank
+
+
+def whole_job_rate(ms_local, solves_local, ws):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    ms_max = max_over_ranks(ms_local, ws)
+    total = sum_over_ranks(solves_local, ws)
+    return total / (ms_max / 1e3), ms_max, total
 
 
 # --------------------------------------------------------------------------- CPU oracle
@@ -300,6 +320,8 @@ def main():
         return run_reference(args, w)
     if args.warmup < 1:
         ap.error("--warmup must be >= 1")
+    if args.steps >= 1000 or args.warmup >= 1000:
+        ap.error("--steps and --warmup must be below 1000 (noise job ids of a replica)")
 
     ws, rank, local = dist_setup()
     import torch
@@ -329,7 +351,7 @@ def main():
         return out
 
     solves_per_step = 2 * nvec * (len(w["sigmas"]) - 1) + nvec
-    job0 = 100000 * rank
+    job0 = job_base(rank)
     for k in range(args.warmup):
         step(job0 + k)
     torch.cuda.synchronize()
@@ -356,9 +378,7 @@ def main():
     clk = clocks.stop()
     prof = ctx.profile_read()
     ctx.profile_enable(False)
-    ms_max = max_over_ranks(ms, ws)
-    total_solves = sum_over_ranks(solves_per_step * args.steps, ws)
-    value = total_solves / (ms_max / 1e3)
+    value, ms_max, total_solves = whole_job_rate(ms, solves_per_step * args.steps, ws)
 
     # ---- end to end through the public API with host buffers
     e2e = None
