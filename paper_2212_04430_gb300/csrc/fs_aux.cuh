@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) noise_kernel(double* z_e, double* z_o, co
     cb_coords(g, par, site, x);
     double z[24];
     z4_site(n, lex_index(g, x), z);
-    make_field<double>(par ? z_o : z_e, g.Vh, sh.N).store(site, sys, z);
+    make_field<double>(par ? z_o : z_e, g.Vh, sh.N, true).store(site, sys, z);
   }
 }
 
@@ -72,7 +72,7 @@ __global__ void noise_codes_kernel(uint8_t* codes, NoiseSpec n, int V) {
 // canonical FP64 [nvec][V][24]  ->  e/o tile fields of type Ts (slot j <- vector vec[j], -1 skips)
 template <typename Ts>
 __global__ void __launch_bounds__(256) pack_kernel(void* f_e, void* f_o, const double* canon, const int* vec,
-                                                  Geom g, Shape sh) {
+                                                  Geom g, Shape sh, bool sysmajor) {
   const int lsys = threadIdx.x % sh.NB, lsite = threadIdx.x / sh.NB;
   const int sys = blockIdx.y * sh.NB + lsys;
   if (sys >= sh.N) return;
@@ -91,13 +91,13 @@ __global__ void __launch_bounds__(256) pack_kernel(void* f_e, void* f_o, const d
       const double2 w = *reinterpret_cast<const double2*>(src + k);
       v[k] = w.x; v[k + 1] = w.y;
     }
-    make_field<Ts>(par ? f_o : f_e, g.Vh, sh.N).store(site, sys, v);
+    make_field<Ts>(par ? f_o : f_e, g.Vh, sh.N, sysmajor).store(site, sys, v);
   }
 }
 
 template <typename Ts>
 __global__ void __launch_bounds__(256) unpack_kernel(double* canon, const void* f_e, const void* f_o,
-                                                    const int* vec, Geom g, Shape sh) {
+                                                    const int* vec, Geom g, Shape sh, bool sysmajor) {
   const int lsys = threadIdx.x % sh.NB, lsite = threadIdx.x / sh.NB;
   const int sys = blockIdx.y * sh.NB + lsys;
   if (sys >= sh.N) return;
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) unpack_kernel(double* canon, const void* 
     int x[4];
     cb_coords(g, par, site, x);
     double v[24];
-    make_field<Ts>(const_cast<void*>(par ? f_o : f_e), g.Vh, sh.N).load(site, sys, v);
+    make_field<Ts>(const_cast<void*>(par ? f_o : f_e), g.Vh, sh.N, sysmajor).load(site, sys, v);
     double* dst = canon + ((size_t)vi * g.V + lex_index(g, x)) * 24;
 #pragma unroll
     for (int k = 0; k < 24; k += 2) *reinterpret_cast<double2*>(dst + k) = make_double2(v[k], v[k + 1]);
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(256) contract_kernel(ContractArgs a) {
     int x[4];
     cb_coords(g, par, site, x);
     double psi[24];
-    make_field<double>(const_cast<double*>(par ? a.x_o : a.x_e), g.Vh, a.N).load(site, pr.right, psi);
+    make_field<double>(const_cast<double*>(par ? a.x_o : a.x_e), g.Vh, a.N, true).load(site, pr.right, psi);
     int qi = 0;
     for (int q = 0; q <= a.pmax; q++) {
       int y[4] = {x[0], x[1], x[2], x[3]};
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(256) contract_kernel(ContractArgs a) {
         if (pr.left_kind == 0) {
           z4_site(a.spec[pr.left], lex_index(g, y), lv);
         } else {
-          make_field<double>(const_cast<double*>(ypar ? a.x_o : a.x_e), g.Vh, a.N)
+          make_field<double>(const_cast<double*>(ypar ? a.x_o : a.x_e), g.Vh, a.N, true)
               .load(cb_index(g, y), pr.left, lv);
 #pragma unroll
           for (int k = 12; k < 24; k++) lv[k] = -lv[k];

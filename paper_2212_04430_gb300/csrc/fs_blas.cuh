@@ -80,8 +80,9 @@ __global__ void __launch_bounds__(256) blas_kernel(BlasArgs a) {
   const Field<Ts> s = make_field<Ts>(a.s, Vh, sh.N);
   const Field<Ts> t = make_field<Ts>(a.t, Vh, sh.N);
   const Field<Tx> xl = make_field<Tx>(a.x_lo, Vh, sh.N);
-  const Field<double> xh = make_field<double>(a.x_hi, Vh, sh.N);
-  const Field<double> src = make_field<double>(const_cast<double*>(a.src), Vh, sh.N);
+  // x_hi and src (r_hi, bhat, z) are FP64 reliable-update fields: system-major layout
+  const Field<double> xh = make_field<double>(a.x_hi, Vh, sh.N, true);
+  const Field<double> src = make_field<double>(const_cast<double*>(a.src), Vh, sh.N, true);
 
   for (int chunk = blockIdx.x; chunk < sh.nchunk; chunk += gridDim.x) {
     const int site = chunk * sh.SB + lsite;
@@ -222,10 +223,10 @@ __global__ void __launch_bounds__(256) cg_kernel(CgArgs a) {
   const bool sel = sys < sh.N && selected(a.st, sys, a.mask);
   const double alpha = sel ? a.st[sys].cd[C_ALPHA] : 0.0;
   const double beta = sel ? a.st[sys].cd[C_BETA] : 0.0;
-  const Field<double> fx = make_field<double>(a.x, a.Vh, sh.N), fs = make_field<double>(a.s, a.Vh, sh.N);
-  const Field<double> fp = make_field<double>(a.p, a.Vh, sh.N), fq = make_field<double>(a.q, a.Vh, sh.N);
-  const Field<double> fg = make_field<double>(a.g, a.Vh, sh.N), fw = make_field<double>(a.w, a.Vh, sh.N);
-  const Field<double> fr = make_field<double>(a.r, a.Vh, sh.N);
+  const Field<double> fx = make_field<double>(a.x, a.Vh, sh.N, true), fs = make_field<double>(a.s, a.Vh, sh.N, true);
+  const Field<double> fp = make_field<double>(a.p, a.Vh, sh.N, true), fq = make_field<double>(a.q, a.Vh, sh.N, true);
+  const Field<double> fg = make_field<double>(a.g, a.Vh, sh.N, true), fw = make_field<double>(a.w, a.Vh, sh.N, true);
+  const Field<double> fr = make_field<double>(a.r, a.Vh, sh.N, true);
   for (int chunk = blockIdx.x; chunk < sh.nchunk; chunk += gridDim.x) {
     const int site = chunk * sh.SB + lsite;
     const bool act = sel && site < a.Vh;

@@ -148,14 +148,23 @@ __device__ __forceinline__ void store_vec(Ts* p, const Tm* o) {
   }
 }
 
-// A field view: one parity of a tile of N systems.
+// A field view: one parity of a tile of N systems. Two layouts:
+//  tile         ((c Vh + site) N + sys) VW + v : a warp's consecutive (site, sys) pairs,
+//               system fastest, read 128-bit contiguous; for kernels that work on all
+//               systems of a site together (the inner-precision solver);
+//  system-major ((sys 24/VW + c) Vh + site) VW + v : one system's parity is contiguous;
+//               for kernels that run one system per block (the FP64 reliable-update,
+//               preparation, reconstruction and contraction fields), where a few flagged
+//               systems must not drag the other systems' interleaved data through DRAM.
 template <typename Ts>
 struct Field {
   Ts* ptr;
-  size_t cstride;  // reals between vector slots c and c+1 = Vh * N * VW
+  size_t cstride;    // reals between vector slots c and c+1
+  size_t sitestride; // reals between consecutive sites
+  size_t sysstride;  // reals between consecutive systems
   int N;
   __device__ __forceinline__ size_t off(int site, int sys) const {
-    return ((size_t)site * N + sys) * Store<Ts>::VW;
+    return (size_t)site * sitestride + (size_t)sys * sysstride;
   }
   template <typename Tm>
   __device__ __forceinline__ void load(int site, int sys, Tm (&v)[24]) const {
@@ -174,11 +183,20 @@ struct Field {
 };
 
 template <typename Ts>
-__host__ __device__ inline Field<Ts> make_field(void* p, int Vh, int N) {
+__host__ __device__ inline Field<Ts> make_field(void* p, int Vh, int N, bool sysmajor = false) {
+  constexpr int VW = Store<Ts>::VW;
   Field<Ts> f;
   f.ptr = reinterpret_cast<Ts*>(p);
-  f.cstride = (size_t)Vh * N * Store<Ts>::VW;
   f.N = N;
+  if (sysmajor) {
+    f.cstride = (size_t)Vh * VW;
+    f.sitestride = VW;
+    f.sysstride = (size_t)24 * Vh;
+  } else {
+    f.cstride = (size_t)Vh * N * VW;
+    f.sitestride = (size_t)N * VW;
+    f.sysstride = VW;
+  }
   return f;
 }
 

@@ -96,7 +96,11 @@ class Tile : public TileBase {
   Ctx* c = nullptr;
   Shape sh{};
   Launch L{};
-  Shape sh1{};   // system-major: a block covers 256 sites of ONE system (uniform per-block masks)
+  // system-major: a block covers SYS_SITES sites of ONE system (uniform per-block masks). 128-site
+  // blocks: 4 resident per SM at 128 registers, finer than 256-site blocks for the few
+  // flagged systems of a reliable update (measured 7% faster FP64 hops).
+  static constexpr int SYS_SITES = 128;
+  Shape sh1{};
   Launch L1{};
   Launch LH{};   // hopping kernels: one site chunk per block, so resident blocks sweep the
                  // lattice in order and neighbour spinors are re-read from L2, not DRAM
@@ -137,11 +141,11 @@ class Tile : public TileBase {
     L = c->launch_for(sh);
     sh1 = sh;
     sh1.NB = 1;
-    sh1.SB = 256;
-    sh1.nchunk = (c->g.Vh + 255) / 256;
+    sh1.SB = SYS_SITES;
+    sh1.nchunk = (c->g.Vh + SYS_SITES - 1) / SYS_SITES;
     L1.grid_y = N;
-    L1.block = 256;
-    L1.grid_x = std::min(sh1.nchunk, std::max(1, 4 * c->nsm));
+    L1.block = SYS_SITES;
+    L1.grid_x = std::min(sh1.nchunk, std::max(1, 8 * c->nsm));
     L1.stream = c->stream;
     LH = L;
     LH.grid_x = sh.nchunk;
@@ -180,6 +184,7 @@ class Tile : public TileBase {
     a.gauge = hi ? c->gauge64 : c->gauge_for(prec, nr);
     a.st = st_d; a.partial = part; a.gate = gated ? gate : nullptr; a.work = nullptr;
     a.g = c->g; a.sh = sysmajor ? sh1 : sh; a.p_out = p_out; a.mask = mask;
+    a.sysmajor = sysmajor ? 1 : 0;  // one system per block <-> the FP64 fields' system-major layout
     return a;
   }
   BlasArgs blas(int mask, const double* src, double* part, bool gated, bool sysmajor = false) {
@@ -226,12 +231,13 @@ class Tile : public TileBase {
 
   cudaError_t enqueue_rhs_from_canon(const double* canon) override {
     L.stream = c->stream;
-    return launch_pack<double>(z_e, z_o, canon, vec_d, c->g, sh, L);
+    L1.stream = c->stream;
+    return launch_pack<double>(z_e, z_o, canon, vec_d, c->g, sh1, L1, true);
   }
 
   cudaError_t enqueue_noise() override {
     L1.stream = c->stream;
-    noise_kernel<<<dim3(std::min(2 * sh1.nchunk, 2 * L1.grid_x), N), 256, 0, c->stream>>>(z_e, z_o, spec_d, st_d,
+    noise_kernel<<<dim3(std::min(2 * sh1.nchunk, 2 * L1.grid_x), N), SYS_SITES, 0, c->stream>>>(z_e, z_o, spec_d, st_d,
                                                                                       c->g, sh1);
     note_launch();
     return cudaGetLastError();
@@ -341,13 +347,13 @@ class Tile : public TileBase {
     L.stream = c->stream;
     // in: canon[vec[j]] -> (p, tmp) ; out = (D + sigma) in -> (v, s) -> canon[vec[j]]
     cudaError_t e;
-    if ((e = launch_pack<Ts>(p, tmp, canon, vec_d, c->g, sh, L))) return e;
+    if ((e = launch_pack<Ts>(p, tmp, canon, vec_d, c->g, sh, L, false))) return e;
     const bool f64 = std::is_same<Ts, double>::value;
     HopArgs he = hop(v, tmp, p, nullptr, nullptr, nullptr, 0, MASK_INIT, false, f64);
     HopArgs ho = hop(s, p, tmp, nullptr, nullptr, nullptr, 1, MASK_INIT, false, f64);
     if ((e = hop_lo(COEF_DSLASH, DOT_NONE, he, 1))) return e;
     if ((e = hop_lo(COEF_DSLASH, DOT_NONE, ho, 1))) return e;
-    return launch_unpack<Ts>(canon, v, s, vec_d, c->g, sh, L);
+    return launch_unpack<Ts>(canon, v, s, vec_d, c->g, sh, L, false);
   }
 
   // ---- CGNR fallback on M^dag M, FP64, system-major (only the FLAG_CG slots work) ----
@@ -366,7 +372,7 @@ class Tile : public TileBase {
   }
   template <int OP>
   cudaError_t cg_op(int mask, double* part = nullptr) {
-    cg_kernel<OP><<<dim3(L1.grid_x, L1.grid_y), 256, 0, c->stream>>>(cga(mask, part));
+    cg_kernel<OP><<<dim3(L1.grid_x, L1.grid_y), SYS_SITES, 0, c->stream>>>(cga(mask, part));
     note_launch();
     return cudaGetLastError();
   }
@@ -421,7 +427,8 @@ class Tile : public TileBase {
 
   cudaError_t enqueue_solution_to_canon(double* canon) override {
     L.stream = c->stream;
-    return launch_unpack<double>(canon, x_hi, x_o, vec_d, c->g, sh, L);
+    L1.stream = c->stream;
+    return launch_unpack<double>(canon, x_hi, x_o, vec_d, c->g, sh1, L1, true);
   }
 };
 

@@ -35,9 +35,9 @@ struct Launch {
 template <typename Ts> cudaError_t launch_hop(int coef, int dot, int nr, const HopArgs& a, const Launch& l);
 template <typename Ts> cudaError_t launch_blas(int op, const BlasArgs& a, const Launch& l);
 template <typename Ts> cudaError_t launch_pack(void* fe, void* fo, const double* canon, const int* vec,
-                                               const Geom& g, const Shape& sh, const Launch& l);
+                                               const Geom& g, const Shape& sh, const Launch& l, bool sysmajor);
 template <typename Ts> cudaError_t launch_unpack(double* canon, const void* fe, const void* fo, const int* vec,
-                                                 const Geom& g, const Shape& sh, const Launch& l);
+                                                 const Geom& g, const Shape& sh, const Launch& l, bool sysmajor);
 template <typename Tg> cudaError_t launch_gauge_pack(void* out, const double* canon, const Geom& g, int nr,
                                                      cudaStream_t s);
 

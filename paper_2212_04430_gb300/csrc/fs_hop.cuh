@@ -71,6 +71,7 @@ struct HopArgs {
   Shape sh;
   int p_out;
   int mask;
+  int sysmajor;  // 1: every field operand in the system-major layout (hop_kernel only)
 };
 
 // ---- fixed-order arithmetic ------------------------------------------------------
@@ -283,8 +284,9 @@ __global__ void __launch_bounds__(256, sizeof(Tm) == 8 ? 2 : (sizeof(Ts) == 2 ? 
   const int lsys = threadIdx.x % sh.NB;
   const int lsite = threadIdx.x / sh.NB;
   const int sys = blockIdx.y * sh.NB + lsys;
-  const Field<Ts> in = make_field<Ts>(const_cast<void*>(a.in), g.Vh, sh.N);
-  const Field<Ts> out = make_field<Ts>(a.out, g.Vh, sh.N);
+  const bool smj = a.sysmajor != 0;
+  const Field<Ts> in = make_field<Ts>(const_cast<void*>(a.in), g.Vh, sh.N, smj);
+  const Field<Ts> out = make_field<Ts>(a.out, g.Vh, sh.N, smj);
   const bool sel = sys < sh.N && selected(a.st, sys, a.mask);
 
   Tm ca = 0, cb = 1, cc = 0;
@@ -324,12 +326,12 @@ __global__ void __launch_bounds__(256, sizeof(Tm) == 8 ? 2 : (sizeof(Ts) == 2 ? 
         for (int k = 0; k < 24; k++) o[k] = acc[k];
       } else {
         Tm xv[24];
-        make_field<Ts>(const_cast<void*>(a.X), g.Vh, sh.N).load(site, sys, xv);
+        make_field<Ts>(const_cast<void*>(a.X), g.Vh, sh.N, smj).load(site, sys, xv);
 #pragma unroll
         for (int k = 0; k < 24; k++) o[k] = axpby(ca, xv[k], cb, acc[k]);
         if (COEF == COEF_TRUERES || COEF == COEF_FULLRES) {
           Tm yv[24];
-          make_field<Ts>(const_cast<void*>(a.Y), g.Vh, sh.N).load(site, sys, yv);
+          make_field<Ts>(const_cast<void*>(a.Y), g.Vh, sh.N, smj).load(site, sys, yv);
 #pragma unroll
           for (int k = 0; k < 24; k++) o[k] = fmadd(cc, yv[k], o[k]);
         }
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(256, sizeof(Tm) == 8 ? 2 : (sizeof(Ts) == 2 ? 
       }
       if (DOT == DOT_R) {
         Tm rv[24];
-        make_field<Ts>(const_cast<void*>(a.R), g.Vh, sh.N).load(site, sys, rv);
+        make_field<Ts>(const_cast<void*>(a.R), g.Vh, sh.N, smj).load(site, sys, rv);
         Tm sr = 0, si = 0;
 #pragma unroll
         for (int k = 0; k < 24; k += 2) dot_acc(sr, si, rv[k], rv[k + 1], o[k], o[k + 1]);

@@ -53,6 +53,7 @@ cudaError_t launch_hop_pp(const HopArgs& a, const Launch& l) {
 
 template <typename Ts, typename Tg, typename Tm, int R, int C, int D>
 cudaError_t launch_hop_pf(const HopArgs& a, const Launch& l) {
+  if (a.sysmajor) return cudaErrorInvalidValue;  // inner-precision fields are tile-layout only
   // 32 systems per warp, 8 sites per block: the persistent pipelined kernel
   if (a.sh.NB == 32 && a.sh.SB == 8 && l.block == 256) return launch_hop_pp<Ts, Tg, Tm, R, C, D>(a, l);
   constexpr int PF = hop_pf<Ts>();
@@ -127,16 +128,16 @@ cudaError_t launch_blas(int op, const BlasArgs& a, const Launch& l) {
 
 template <typename Ts>
 cudaError_t launch_pack(void* fe, void* fo, const double* canon, const int* vec, const Geom& g, const Shape& sh,
-                        const Launch& l) {
-  pack_kernel<Ts><<<dim3(l.grid_x, l.grid_y), l.block, 0, l.stream>>>(fe, fo, canon, vec, g, sh);
+                        const Launch& l, bool sysmajor) {
+  pack_kernel<Ts><<<dim3(l.grid_x, l.grid_y), l.block, 0, l.stream>>>(fe, fo, canon, vec, g, sh, sysmajor);
   note_launch();
   return cudaGetLastError();
 }
 
 template <typename Ts>
 cudaError_t launch_unpack(double* canon, const void* fe, const void* fo, const int* vec, const Geom& g,
-                          const Shape& sh, const Launch& l) {
-  unpack_kernel<Ts><<<dim3(l.grid_x, l.grid_y), l.block, 0, l.stream>>>(canon, fe, fo, vec, g, sh);
+                          const Shape& sh, const Launch& l, bool sysmajor) {
+  unpack_kernel<Ts><<<dim3(l.grid_x, l.grid_y), l.block, 0, l.stream>>>(canon, fe, fo, vec, g, sh, sysmajor);
   note_launch();
   return cudaGetLastError();
 }
@@ -156,8 +157,8 @@ cudaError_t launch_gauge_pack(void* out, const double* canon, const Geom& g, int
   template cudaError_t launch_hop<TS>(int, int, int, const HopArgs&, const Launch&);                        \
   template cudaError_t launch_blas<TS>(int, const BlasArgs&, const Launch&);                                \
   template cudaError_t launch_pack<TS>(void*, void*, const double*, const int*, const Geom&, const Shape&,   \
-                                       const Launch&);                                                      \
+                                       const Launch&, bool);                                                \
   template cudaError_t launch_unpack<TS>(double*, const void*, const void*, const int*, const Geom&,         \
-                                         const Shape&, const Launch&);
+                                         const Shape&, const Launch&, bool);
 
 }  // namespace fs

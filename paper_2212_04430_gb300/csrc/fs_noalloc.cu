@@ -120,7 +120,7 @@ extern "C" int wilson_dslash_noalloc(const int dims[4], int bc_t, double m, doub
 
   noalloc_init_kernel<<<(nrhs + 63) / 64, 64, 0, s>>>(st, vec, nrhs, 4.0 + m + sigma);
   fs::gauge_pack_kernel<double, 18><<<(8 * g.Vh + 255) / 256, 256, 0, s>>>(gauge, U, g);
-  fs::pack_kernel<double><<<dim3(std::min(2 * sh.nchunk, 65535), gy), block, 0, s>>>(in_e, in_o, in, vec, g, sh);
+  fs::pack_kernel<double><<<dim3(std::min(2 * sh.nchunk, 65535), gy), block, 0, s>>>(in_e, in_o, in, vec, g, sh, false);
   fs::HopArgs a{};
   a.gauge = gauge;
   a.st = st;
@@ -132,7 +132,7 @@ extern "C" int wilson_dslash_noalloc(const int dims[4], int bc_t, double m, doub
   fs::hop_kernel<double, double, double, 18, fs::COEF_DSLASH, fs::DOT_NONE><<<dim3(sh.nchunk, gy), block, 0, s>>>(a);
   a.out = out_o; a.in = in_e; a.X = in_o; a.p_out = 1;
   fs::hop_kernel<double, double, double, 18, fs::COEF_DSLASH, fs::DOT_NONE><<<dim3(sh.nchunk, gy), block, 0, s>>>(a);
-  fs::unpack_kernel<double><<<dim3(std::min(2 * sh.nchunk, 65535), gy), block, 0, s>>>(out, out_e, out_o, vec, g, sh);
+  fs::unpack_kernel<double><<<dim3(std::min(2 * sh.nchunk, 65535), gy), block, 0, s>>>(out, out_e, out_o, vec, g, sh, false);
   fs::note_launch(6);
   return cudaGetLastError() == cudaSuccess ? FS_OK : FS_ERR_CUDA;
 }
