@@ -251,7 +251,7 @@ def config_of(args, w):
     return {"workload": w["name"], "lattice": "x".join(map(str, w["dims"])), "levels": len(w["sigmas"]),
             "vectors_per_level_per_step": args.vectors or w["vectors"], "estimator": w["estimator"],
             "rhs_tile": args.tile or w["tile"], "storage": w["prec"], "links": "%d-real" % w["link"],
-            "tol": w["tol"], "l2": "working set above L2 (no flush needed)"}
+            "tol": w["tol"], "delta": args.delta or "library", "l2": "working set above L2 (no flush needed)"}
 
 
 # --------------------------------------------------------------------------- serving
@@ -309,6 +309,8 @@ def main():
     ap.add_argument("--workload", default="16x32", choices=sorted(WORKLOADS))
     ap.add_argument("--vectors", type=int, default=0, help="Z4 vectors per level per step")
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--delta", type=float, default=0.0,
+                    help="reliable-update trigger factor (0: library choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=8.0, help="seconds of oracle work per reference step")
@@ -340,7 +342,7 @@ def main():
     ctx.set_stream(stream.cuda_stream)
     ctx.fs_set_gauge(u)
     gam = pkg.gamma_matrix(w["gamma"])
-    kw = dict(prec=w["prec"], tol=w["tol"], rhs_tile=tile, link_compress=w["link"])
+    kw = dict(prec=w["prec"], tol=w["tol"], rhs_tile=tile, link_compress=w["link"], delta=args.delta)
     n = [nvec] * len(w["sigmas"])
 
     def step(job):
@@ -366,10 +368,12 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    iters = []
+    iters, updates, restarts = [], [], []
     for k in range(args.steps):
         out = step(job0 + 1000 + k)
         iters.extend(s["iters"] for s in out["stats"])
+        updates.extend(s["reliable_updates"] for s in out["stats"])
+        restarts.extend(s["restarts"] for s in out["stats"])
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(ws)
@@ -436,6 +440,8 @@ def main():
                 "gpu_launches": launches, "clocks": clk, "serving": serving,
                 "solver": {"mean_iters": float(np.mean(iters)) if iters else None,
                            "max_iters": int(max(iters)) if iters else None,
+                           "mean_reliable_updates": float(np.mean(updates)) if updates else None,
+                           "restarts": int(sum(restarts)),
                            "solves_per_step": solves_per_step}}
         print(json.dumps(line), flush=True)
     ctx.close()
