@@ -273,8 +273,12 @@ enum FinOp { FIN_ALPHA = 0, FIN_OMEGA = 1, FIN_RHO = 2, FIN_TRUE = 3, FIN_UPDATE
              FIN_NORM = 6, FIN_VERIFY = 7, FIN_CG_INIT = 8, FIN_CG_ALPHA = 9, FIN_CG_BETA = 10,
              FIN_CG_TRUE = 11 };
 
+constexpr int FIN_SPLIT = 8;  // blocks per system in a finalize
+
 struct FinArgs {
   SysState* st;
+  double* slice;     // [N][FIN_SPLIT][3] slice sums
+  unsigned* count;   // [N] arrival tickets, zero between finalizes
   const double* pa;  // partials [N][K][ngroups]
   const double* pb;
   const double* pc;
@@ -286,31 +290,6 @@ struct FinArgs {
   double nreal;      // 24 * Vh
   int max_restarts;
 };
-
-template <int K>
-__device__ __forceinline__ void fin_sum(const double* part, int ngroups, int sys, double (&out)[K],
-                                        double* sm) {
-  double acc[K];
-#pragma unroll
-  for (int k = 0; k < K; k++) acc[k] = 0.0;
-  for (int gidx = threadIdx.x; gidx < ngroups; gidx += blockDim.x) {
-#pragma unroll
-    for (int k = 0; k < K; k++) acc[k] += part[((size_t)sys * K + k) * ngroups + gidx];
-  }
-#pragma unroll
-  for (int k = 0; k < K; k++) sm[threadIdx.x * K + k] = acc[k];
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-#pragma unroll
-      for (int k = 0; k < K; k++) sm[threadIdx.x * K + k] += sm[(threadIdx.x + w) * K + k];
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int k = 0; k < K; k++) out[k] = sm[k];
-  __syncthreads();
-}
 
 __device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi, double& cr, double& ci) {
   const double d = br * br + bi * bi;
@@ -336,19 +315,30 @@ __device__ __forceinline__ void set_beta(SysState& s) {
   set_coef(s, C_BETA + 1, q1r * q2i + q1i * q2r);
 }
 
-#ifdef FS_ENGINE_KERNELS
-__global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
-  __shared__ double sm[256 * 3];
-  const int sys = blockIdx.x;
-  if (op == FIN_UPDATE && sys == 0 && threadIdx.x == 0 && a.gate) {
-    // every gated update kernel of this iteration has run (stream order); re-arm
-    *a.gate = 0;
+// Operands summed by each finalize op, in the order its logic consumes them.
+__device__ __forceinline__ int fin_sources(int op, const FinArgs& a, const double* (&p)[3], int (&k)[3]) {
+  switch (op) {
+    case FIN_ALPHA: p[0] = a.pa; k[0] = 2; return 1;
+    case FIN_OMEGA: case FIN_RHO: case FIN_UPDATE: case FIN_INIT: p[0] = a.pa; k[0] = 3; return 1;
+    case FIN_NORM: p[0] = a.pa; p[1] = a.pb; p[2] = a.pc; k[0] = k[1] = k[2] = 1; return 3;
+    case FIN_VERIFY: case FIN_CG_INIT: case FIN_CG_BETA: p[0] = a.pa; p[1] = a.pb; k[0] = k[1] = 1; return 2;
+    default: p[0] = a.pa; k[0] = 1; return 1;  // FIN_TRUE, FIN_CG_ALPHA, FIN_CG_TRUE
   }
-  if (sys >= a.N || !selected(a.st, sys, a.mask)) return;
-  SysState& s = a.st[sys];
+}
+
+template <int K>
+__device__ __forceinline__ void take(double (&v)[K], const double* tot, int& off) {
+#pragma unroll
+  for (int k = 0; k < K; k++) v[k] = tot[off + k];
+  off += K;
+}
+
+// The per-system scalar step of the solver (one thread) from the summed operands.
+__device__ __forceinline__ void fin_logic(const FinArgs& a, int op, SysState& s, const double* tot) {
+  int off = 0;
   if (op == FIN_ALPHA) {
     double rv[2];
-    fin_sum<2>(a.pa, a.ngroups, sys, rv, sm);
+    take<2>(rv, tot, off);
     if (threadIdx.x == 0) {
       double ar = 0, ai = 0;
       if (rv[0] == 0.0 && rv[1] == 0.0) {
@@ -363,7 +353,7 @@ __global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
     }
   } else if (op == FIN_OMEGA) {
     double v[3];
-    fin_sum<3>(a.pa, a.ngroups, sys, v, sm);
+    take<3>(v, tot, off);
     if (threadIdx.x == 0) {
       double wr = 0, wi = 0;
       if (v[2] > 0.0 && isfinite(v[2])) { wr = v[0] / v[2]; wi = v[1] / v[2]; }
@@ -374,7 +364,7 @@ __global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
     }
   } else if (op == FIN_RHO) {
     double v[3];
-    fin_sum<3>(a.pa, a.ngroups, sys, v, sm);
+    take<3>(v, tot, off);
     if (threadIdx.x == 0) {
       s.iters += 1;
       s.rho_old[0] = s.rho[0]; s.rho_old[1] = s.rho[1];
@@ -392,7 +382,7 @@ __global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
     }
   } else if (op == FIN_TRUE) {
     double v[1];
-    fin_sum<1>(a.pa, a.ngroups, sys, v, sm);
+    take<1>(v, tot, off);
     if (threadIdx.x == 0) {
       s.r2_true = v[0];
       s.updates += 1;
@@ -411,7 +401,7 @@ __global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
     }
   } else if (op == FIN_UPDATE || op == FIN_INIT) {
     double v[3];
-    fin_sum<3>(a.pa, a.ngroups, sys, v, sm);
+    take<3>(v, tot, off);
     if (threadIdx.x == 0) {
       s.rho[0] = v[0]; s.rho[1] = v[1];
       s.r2 = v[2];
@@ -431,9 +421,9 @@ __global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
   } else if (op == FIN_NORM) {
     // initial norms: pa = ||bhat||^2, pb = ||z_e||^2, pc = ||z_o||^2
     double bh[1], ze[1], zo[1];
-    fin_sum<1>(a.pa, a.ngroups, sys, bh, sm);
-    fin_sum<1>(a.pb, a.ngroups, sys, ze, sm);
-    fin_sum<1>(a.pc, a.ngroups, sys, zo, sm);
+    take<1>(bh, tot, off);
+    take<1>(ze, tot, off);
+    take<1>(zo, tot, off);
     if (threadIdx.x == 0) {
       s.b2 = ze[0] + zo[0];
       s.r2_true = bh[0];
@@ -453,14 +443,14 @@ __global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
     }
   } else if (op == FIN_VERIFY) {
     double e[1], o[1];
-    fin_sum<1>(a.pa, a.ngroups, sys, e, sm);
-    fin_sum<1>(a.pb, a.ngroups, sys, o, sm);
+    take<1>(e, tot, off);
+    take<1>(o, tot, off);
     if (threadIdx.x == 0) s.r2_full = e[0] + o[0];
   } else if (op == FIN_CG_INIT) {
     // pa = ||s||^2 (s = bhat - M x), pb = ||r||^2 (r = M^dag s)
     double sv[1], rv[1];
-    fin_sum<1>(a.pa, a.ngroups, sys, sv, sm);
-    fin_sum<1>(a.pb, a.ngroups, sys, rv, sm);
+    take<1>(sv, tot, off);
+    take<1>(rv, tot, off);
     if (threadIdx.x == 0) {
       s.r2_true = sv[0];
       s.r2 = sv[0];
@@ -472,7 +462,7 @@ __global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
     }
   } else if (op == FIN_CG_ALPHA) {
     double qv[1];
-    fin_sum<1>(a.pa, a.ngroups, sys, qv, sm);  // ||M p||^2
+    take<1>(qv, tot, off);  // ||M p||^2
     if (threadIdx.x == 0) {
       const double al = s.rho[0] / qv[0];
       if (!(qv[0] > 0.0) || !isfinite(al)) { s.status = SYS_NOCONV; s.flags = 0; }
@@ -482,8 +472,8 @@ __global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
   } else if (op == FIN_CG_BETA) {
     // pa = ||s||^2 after the step, pb = ||r||^2 of the new normal residual
     double sv[1], rv[1];
-    fin_sum<1>(a.pa, a.ngroups, sys, sv, sm);
-    fin_sum<1>(a.pb, a.ngroups, sys, rv, sm);
+    take<1>(sv, tot, off);
+    take<1>(rv, tot, off);
     if (threadIdx.x == 0) {
       s.cg_iters += 1;
       s.r2 = sv[0];
@@ -499,7 +489,7 @@ __global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
     }
   } else if (op == FIN_CG_TRUE) {
     double tv[1];
-    fin_sum<1>(a.pa, a.ngroups, sys, tv, sm);  // ||bhat - M x||^2 in FP64; s now holds that residual
+    take<1>(tv, tot, off);  // ||bhat - M x||^2 in FP64; s now holds that residual
     if (threadIdx.x == 0) {
       s.r2_true = tv[0];
       s.r2 = tv[0];
@@ -509,6 +499,64 @@ __global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
       else s.flags &= ~FLAG_UPDATE;
     }
   }
+}
+
+#ifdef FS_ENGINE_KERNELS
+// Grid (N, FIN_SPLIT): block (sys, y) sums slice y of the system's group partials
+// (fixed slices, fixed in-slice tree) into a.slice; the last block of the system to
+// finish (an atomic ticket; no block ever waits) adds the FIN_SPLIT slice sums in slice
+// order and runs the scalar step. The result depends only on the partials, not on
+// which block finishes last.
+__global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
+  __shared__ double sm[256 * 3];
+  __shared__ unsigned ticket;
+  const int sys = blockIdx.x, y = blockIdx.y;
+  if (op == FIN_UPDATE && sys == 0 && y == 0 && threadIdx.x == 0 && a.gate) {
+    // every gated update kernel of this iteration has run (stream order); re-arm
+    *a.gate = 0;
+  }
+  if (sys >= a.N || !selected(a.st, sys, a.mask)) return;
+  const double* src[3];
+  int kk[3];
+  const int nsrc = fin_sources(op, a, src, kk);
+  const int g0 = (int)((long long)a.ngroups * y / FIN_SPLIT), g1 = (int)((long long)a.ngroups * (y + 1) / FIN_SPLIT);
+  double acc[3] = {0.0, 0.0, 0.0};
+  int nv = 0;
+  for (int q = 0; q < nsrc; q++) {
+    for (int k = 0; k < kk[q]; k++, nv++) {
+      const double* base = src[q] + ((size_t)sys * kk[q] + k) * a.ngroups;
+      double t = 0.0;
+      for (int g = g0 + (int)threadIdx.x; g < g1; g += blockDim.x) t += base[g];
+      acc[nv] = t;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 3; v++) sm[threadIdx.x * 3 + v] = acc[v];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+#pragma unroll
+      for (int v = 0; v < 3; v++) sm[threadIdx.x * 3 + v] += sm[(threadIdx.x + w) * 3 + v];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int v = 0; v < 3; v++) a.slice[((size_t)sys * FIN_SPLIT + y) * 3 + v] = sm[v];
+    __threadfence();
+    ticket = atomicAdd(&a.count[sys], 1u);
+  }
+  __syncthreads();
+  if (ticket != FIN_SPLIT - 1) return;
+  if (threadIdx.x != 0) return;
+  __threadfence();
+  a.count[sys] = 0;  // re-armed for the next finalize of this system
+  double tot[3] = {0.0, 0.0, 0.0};
+  for (int yy = 0; yy < FIN_SPLIT; yy++) {
+#pragma unroll
+    for (int v = 0; v < 3; v++) tot[v] += __ldcg(&a.slice[((size_t)sys * FIN_SPLIT + yy) * 3 + v]);  // L2: other SMs wrote them
+  }
+  fin_logic(a, op, a.st[sys], tot);
 }
 #endif  // FS_ENGINE_KERNELS
 

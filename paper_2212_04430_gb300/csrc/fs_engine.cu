@@ -110,6 +110,8 @@ class Tile : public TileBase {
        *tmp = nullptr;
   double *pa = nullptr, *pb = nullptr, *pc = nullptr;
   int* gate = nullptr;
+  double* fin_slice = nullptr;   // finalize slice sums [MAX_TILE][FIN_SPLIT][3]
+  unsigned* fin_count = nullptr; // finalize arrival tickets [MAX_TILE], zero between finalizes
   double *cg_p = nullptr, *cg_q = nullptr, *cg_g = nullptr, *cg_w = nullptr, *cg_r = nullptr;  // CGNR fallback
   std::vector<void*> owned;
   // K BiCGStab iterations captured once and replayed (launch overhead dominates small lattices)
@@ -162,11 +164,13 @@ class Tile : public TileBase {
     const size_t pbytes = (size_t)N * 3 * ngroups * sizeof(double);
     pa = (double*)dalloc(pbytes); pb = (double*)dalloc(pbytes); pc = (double*)dalloc(pbytes);
     gate = (int*)dalloc(sizeof(int));
+    fin_slice = (double*)dalloc(sizeof(double) * MAX_TILE * FIN_SPLIT * 3);
+    fin_count = (unsigned*)dalloc(sizeof(unsigned) * MAX_TILE);
     st_d = (SysState*)dalloc(sizeof(SysState) * MAX_TILE);
     spec_d = (NoiseSpec*)dalloc(sizeof(NoiseSpec) * MAX_TILE);
     vec_d = (int*)dalloc(sizeof(int) * MAX_TILE);
     const void* req[] = {z_e, z_o, bhat, x_hi, x_o, r_hi, x_lo, r, rhat, p, v, s, t, tmp, tmp64,
-                         pa, pb, pc, gate, st_d, spec_d, vec_d};
+                         pa, pb, pc, gate, fin_slice, fin_count, st_d, spec_d, vec_d};
     for (const void* q : req)
       if (!q) return 3;
     if (cudaMallocHost(&st_h, sizeof(SysState) * MAX_TILE) != cudaSuccess) return 3;
@@ -174,6 +178,7 @@ class Tile : public TileBase {
     if (cudaMallocHost(&vec_h, sizeof(int) * MAX_TILE) != cudaSuccess) return 3;
     memset(st_h, 0, sizeof(SysState) * MAX_TILE);
     cudaMemsetAsync(gate, 0, sizeof(int), c->stream);
+    cudaMemsetAsync(fin_count, 0, sizeof(unsigned) * MAX_TILE, c->stream);
     return 0;
   }
 
@@ -197,11 +202,12 @@ class Tile : public TileBase {
   cudaError_t fin(int op, int mask, const double* a_, const double* b_ = nullptr, const double* c_ = nullptr) {
     FinArgs f{};
     f.st = st_d; f.pa = a_; f.pb = b_; f.pc = c_; f.gate = gate;
+    f.slice = fin_slice; f.count = fin_count;
     f.N = N; f.ngroups = ngroups; f.mask = mask;
     f.target = 0.25;  // rms of a scaled residual entry (keeps FP16 away from both range limits)
     f.nreal = 24.0 * c->g.Vh;
     f.max_restarts = 8;
-    fin_kernel<<<N, 256, 0, c->stream>>>(f, op);
+    fin_kernel<<<dim3(N, FIN_SPLIT), 256, 0, c->stream>>>(f, op);
     note_launch();
     return cudaGetLastError();
   }
