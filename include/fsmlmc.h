@@ -266,6 +266,44 @@ long long fs_kernel_launches(void);
 int wilson_dslash_noalloc(const int dims[4], int bc_t, double m, double sigma, const double* U,
                           const double* in, double* out, int nrhs, void* stream);
 
+/* ---- shift selection and sample allocation (host only; paper Sec. 3.2-3.3) --------------
+ * Inputs come from variance_sample on m sampling shifts s_hat (increasing, s_hat[0] = 0 in
+ * the paper's use): VL_hat[i] = V_L(s_hat_i) and the row-major upper triangle
+ * Vbar_hat[i*m + j] = Vbar_l(s_hat_i, s_hat_j), j >= i (Eq. (sampled_single), Eq. (bar_vl)).
+ * s is the evaluation set (increasing, s[0] = 0). All buffers are caller-owned host memory;
+ * nothing touches the GPU. FS_ERR_ARG for null pointers, m < 2, n < 2, unordered shifts or
+ * s[0] != 0; FS_ERR_INPUT for negative or non-finite variances or iteration counts. */
+
+/* Interpolated variances on the evaluation set, in log space with piecewise cubic Hermite
+ * interpolating polynomials (linear through two points): VL[k] = V_L(s_k) and
+ * Vl[i*n + k] = V_l(s_i, s_k) = (s_k - s_i)^2 Vbar_l(s_i, s_k) for k > i (NaN for k <= i or
+ * where no prediction exists), from the three-stage 2-D interpolation of Sec. 3.2. */
+int fs_interp_variances(const double* s_hat, int m, const double* VL_hat, const double* Vbar_hat,
+                        const double* s, int n, double* VL /*[n]*/, double* Vl /*[n*n]*/);
+
+/* Eq. (opt_shifts): the L shifts after sigma_0 = s_0 = 0 that minimise the multilevel cost
+ * C_FS = eps^-2 F^2, F = sum_l sqrt(C_l V_l) (Eq. (ml_cost_shifts)), with V_l from
+ * fs_interp_variances and C_l the iteration count of the level's solves: iters_hat at the
+ * sampling shifts, next-neighbour interpolated (r(s) = r(s_hat_j), s_hat_{j-1} < s <= s_hat_j),
+ * C_l = r(sigma_l) + r(sigma_{l+1}) for l < L, C_L = r(sigma_L). Outputs idx[L+1] (indices
+ * into s, idx[0] = 0), V[L+1], C[L+1] and F. FS_ERR_ARG also for L outside [1, n-1] or when
+ * no choice of L shifts has predicted variances. */
+int fs_select_shifts(const double* s_hat, int m, const double* VL_hat, const double* Vbar_hat,
+                     const double* iters_hat, const double* s, int n, int L, int* idx, double* V, double* C,
+                     double* F);
+
+/* Eq. (num_samples), Eq. (total_var): N_l = mu sqrt(V_l / C_l), mu = eps2^-1 sum_l sqrt(V_l C_l)
+ * (real-valued; round up for use), and V_FS = sum_l V_l / N_l (= eps2), C_FS = sum_l N_l C_l.
+ * mu, V_FS, C_FS may be NULL. FS_ERR_ARG for eps2 <= 0 or nlev < 1; FS_ERR_INPUT for V < 0,
+ * C <= 0 or non-finite values. */
+int fs_sample_allocation(const double* V, const double* C, int nlev, double eps2, double* N, double* mu,
+                         double* V_FS, double* C_FS);
+
+/* The paper's evaluation set (Sec. 3.3): logspace(-5,-2,4) and logspace(log10(0.011),0,76),
+ * with 0 and the sampling shifts added, sorted and unique. With s = NULL only *n is set;
+ * otherwise cap must be >= *n. */
+int fs_eval_grid(const double* s_hat, int m, double* s, int cap, int* n);
+
 #ifdef __cplusplus
 }
 #endif

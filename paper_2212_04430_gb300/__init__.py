@@ -19,5 +19,9 @@ from .fsmlmc import (  # noqa: F401
     mlmc_level_trace,
     variance_sample,
     fs_noise_codes,
+    fs_interp_variances,
+    fs_select_shifts,
+    fs_sample_allocation,
+    fs_eval_grid,
 )
 from .gamma import gamma_matrix, gamma_mu, gamma5  # noqa: F401

@@ -25,7 +25,8 @@ EXPORTS = ["fs_ctx_create", "fs_ctx_destroy", "fs_last_error", "fs_set_stream", 
            "fs_set_gauge", "wilson_dslash", "shifted_solve", "mlmc_level_trace", "fs_mlmc_num_solves",
            "variance_sample", "fs_noise_codes", "fs_profile_enable", "fs_profile_read", "fs_kernel_launches",
            "wilson_dslash_noalloc", "fs_server_create", "fs_server_submit", "fs_server_poll",
-           "fs_server_stats", "fs_server_destroy"]
+           "fs_server_stats", "fs_server_destroy", "fs_interp_variances", "fs_select_shifts",
+           "fs_sample_allocation", "fs_eval_grid"]
 JOB_MAX_LEVELS = 16
 
 
@@ -111,6 +112,10 @@ def load_library(path=LIB_PATH):
         "fs_server_poll": (I, [P, ctypes.c_uint64, ctypes.POINTER(JobResult), I]),
         "fs_server_stats": (I, [P, ctypes.POINTER(ServerReport)]),
         "fs_server_destroy": (None, [P]),
+        "fs_interp_variances": (I, [dp, I, dp, dp, dp, I, dp, dp]),
+        "fs_select_shifts": (I, [dp, I, dp, dp, dp, dp, I, I, ip, dp, dp, dp]),
+        "fs_sample_allocation": (I, [dp, dp, I, D, dp, dp, dp, dp]),
+        "fs_eval_grid": (I, [dp, I, dp, I, ip]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -300,6 +305,63 @@ def wilson_dslash_noalloc(dims, bc_t, m, sigma, U_ptr, in_ptr, out_ptr, nrhs, st
     return int(L.wilson_dslash_noalloc(arr, int(bc_t), float(m), float(sigma), ctypes.c_void_p(U_ptr),
                                        ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), int(nrhs),
                                        ctypes.c_void_p(stream or 0)))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(rc, what):
+    if rc != FS_OK:
+        raise FsError(rc, what + " failed")
+
+
+def fs_eval_grid(s_hat):
+    """The paper's evaluation set of shifts for the sampling shifts s_hat."""
+    L = load_library()
+    sh = _f64(s_hat)
+    n = ctypes.c_int(0)
+    _check(L.fs_eval_grid(_dptr(sh), len(sh), None, 0, ctypes.byref(n)), "fs_eval_grid")
+    out = np.empty(n.value)
+    _check(L.fs_eval_grid(_dptr(sh), len(sh), _dptr(out), len(out), ctypes.byref(n)), "fs_eval_grid")
+    return out
+
+
+def fs_interp_variances(s_hat, VL_hat, Vbar_hat, s):
+    """(V_L[n], V_l[n, n]) on the evaluation set s; V_l is NaN for k <= i."""
+    L = load_library()
+    sh, vl, vb, ss = _f64(s_hat), _f64(VL_hat), _f64(Vbar_hat), _f64(s)
+    m, n = len(sh), len(ss)
+    VL = np.empty(n)
+    Vl = np.empty((n, n))
+    _check(L.fs_interp_variances(_dptr(sh), m, _dptr(vl), _dptr(vb), _dptr(ss), n, _dptr(VL), _dptr(Vl)),
+           "fs_interp_variances")
+    return VL, Vl
+
+
+def fs_select_shifts(s_hat, VL_hat, Vbar_hat, iters_hat, s, L_shifts):
+    """Optimal shifts: dict with idx, sigma, V, C (per level) and F (C_FS = F^2 / eps^2)."""
+    L = load_library()
+    sh, vl, vb, it, ss = _f64(s_hat), _f64(VL_hat), _f64(Vbar_hat), _f64(iters_hat), _f64(s)
+    idx = (ctypes.c_int * (L_shifts + 1))()
+    V = np.empty(L_shifts + 1)
+    C = np.empty(L_shifts + 1)
+    F = ctypes.c_double(0.0)
+    _check(L.fs_select_shifts(_dptr(sh), len(sh), _dptr(vl), _dptr(vb), _dptr(it), _dptr(ss), len(ss),
+                              int(L_shifts), idx, _dptr(V), _dptr(C), ctypes.byref(F)), "fs_select_shifts")
+    ix = list(idx)
+    return {"idx": ix, "sigma": ss[ix], "V": V, "C": C, "F": F.value}
+
+
+def fs_sample_allocation(V, C, eps2):
+    """(N, mu, V_FS, C_FS) of Eq. (num_samples) / Eq. (total_var)."""
+    L = load_library()
+    v, c = _f64(V), _f64(C)
+    N = np.empty(len(v))
+    mu, vfs, cfs = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(L.fs_sample_allocation(_dptr(v), _dptr(c), len(v), float(eps2), _dptr(N), ctypes.byref(mu),
+                                  ctypes.byref(vfs), ctypes.byref(cfs)), "fs_sample_allocation")
+    return N, mu.value, vfs.value, cfs.value
 
 
 class Server:
