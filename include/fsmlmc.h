@@ -267,12 +267,13 @@ int wilson_dslash_noalloc(const int dims[4], int bc_t, double m, double sigma, c
                           const double* in, double* out, int nrhs, void* stream);
 
 /* ---- shift selection and sample allocation (host only; paper Sec. 3.2-3.3) --------------
- * Inputs come from variance_sample on m sampling shifts s_hat (increasing, s_hat[0] = 0 in
- * the paper's use): VL_hat[i] = V_L(s_hat_i) and the row-major upper triangle
- * Vbar_hat[i*m + j] = Vbar_l(s_hat_i, s_hat_j), j >= i (Eq. (sampled_single), Eq. (bar_vl)).
- * s is the evaluation set (increasing, s[0] = 0). All buffers are caller-owned host memory;
- * nothing touches the GPU. FS_ERR_ARG for null pointers, m < 2, n < 2, unordered shifts or
- * s[0] != 0; FS_ERR_INPUT for negative or non-finite variances or iteration counts. */
+ * Inputs come from variance_sample on m sampling shifts s_hat (increasing; s_hat[0] = 0 in
+ * the paper, whose sigma_0 = 0; any first shift serves as sigma_0): VL_hat[i] = V_L(s_hat_i)
+ * and the row-major upper triangle Vbar_hat[i*m + j] = Vbar_l(s_hat_i, s_hat_j), j >= i
+ * (Eq. (sampled_single), Eq. (bar_vl)). s is the evaluation set (increasing, s[0] = s_hat[0]).
+ * All buffers are caller-owned host memory; nothing touches the GPU. FS_ERR_ARG for null
+ * pointers, m < 2, n < 2, unordered shifts or s[0] != s_hat[0]; FS_ERR_INPUT for negative or
+ * non-finite variances or iteration counts. */
 
 /* Interpolated variances on the evaluation set, in log space with piecewise cubic Hermite
  * interpolating polynomials (linear through two points): VL[k] = V_L(s_k) and
@@ -281,7 +282,7 @@ int wilson_dslash_noalloc(const int dims[4], int bc_t, double m, double sigma, c
 int fs_interp_variances(const double* s_hat, int m, const double* VL_hat, const double* Vbar_hat,
                         const double* s, int n, double* VL /*[n]*/, double* Vl /*[n*n]*/);
 
-/* Eq. (opt_shifts): the L shifts after sigma_0 = s_0 = 0 that minimise the multilevel cost
+/* Eq. (opt_shifts): the L shifts after sigma_0 = s_0 that minimise the multilevel cost
  * C_FS = eps^-2 F^2, F = sum_l sqrt(C_l V_l) (Eq. (ml_cost_shifts)), with V_l from
  * fs_interp_variances and C_l the iteration count of the level's solves: iters_hat at the
  * sampling shifts, next-neighbour interpolated (r(s) = r(s_hat_j), s_hat_{j-1} < s <= s_hat_j),
@@ -299,9 +300,9 @@ int fs_select_shifts(const double* s_hat, int m, const double* VL_hat, const dou
 int fs_sample_allocation(const double* V, const double* C, int nlev, double eps2, double* N, double* mu,
                          double* V_FS, double* C_FS);
 
-/* The paper's evaluation set (Sec. 3.3): logspace(-5,-2,4) and logspace(log10(0.011),0,76),
- * with 0 and the sampling shifts added, sorted and unique. With s = NULL only *n is set;
- * otherwise cap must be >= *n. */
+/* The paper's evaluation set (Sec. 3.3): logspace(-5,-2,4) and logspace(log10(0.011),0,76)
+ * from s_hat[0] up, with the sampling shifts added, sorted and unique (with s_hat[0] = 0 it
+ * starts at 0). With s = NULL only *n is set; otherwise cap must be >= *n. */
 int fs_eval_grid(const double* s_hat, int m, double* s, int cap, int* n);
 
 #ifdef __cplusplus

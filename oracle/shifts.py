@@ -12,7 +12,9 @@ Follows the paper, Sec. 3 (Methods):
   * Eq. (solver_cost_shift) with next-neighbour interpolation of the iteration counts.
   * Eq. (ml_cost_shifts) and Eq. (opt_shifts): the optimal shifts minimise
     C_FS = eps^-2 (sum_l sqrt(C_l V_l))^2 over all choices of L evaluation shifts after
-    sigma_0 = s_0 = 0 (brute force over all combinations, as the paper does).
+    sigma_0 = s_0 (brute force over all combinations, as the paper does). The paper has
+    s_0 = 0; with a positive first sampling shift (sigma_0 = the first listed shift) the
+    evaluation set starts at that shift instead.
   * Eq. (num_samples) and Eq. (total_var): N_l = mu sqrt(V_l / C_l),
     mu = eps^-2 sum_l sqrt(V_l C_l), V_FS = sum_l V_l / N_l.
 
@@ -156,11 +158,11 @@ def level_terms(idx, VL, Vl, r):
 
 
 def select_shifts(s_hat, VL_hat, Vbar_hat, r_hat, s, L):
-    """Eq. (opt_shifts): brute force over 1 <= j_1 < ... < j_L <= n-1 (sigma_0 = s_0 = 0).
+    """Eq. (opt_shifts): brute force over 1 <= j_1 < ... < j_L <= n-1 (sigma_0 = s_0 = s^_0).
     Returns (idx, F) with F = sum_l sqrt(C_l V_l) (C_FS = eps^-2 F^2)."""
     s = np.asarray(s, dtype=float)
-    if s[0] != 0.0:
-        raise ValueError("the evaluation set starts at 0")
+    if s[0] != s_hat[0]:
+        raise ValueError("the evaluation set starts at sigma_0 = s^_0")
     VL = interp_single(s_hat, VL_hat, s)
     Vl = interp_pair(s_hat, Vbar_hat, s)
     r = iteration_cost(s_hat, r_hat, s)
@@ -189,7 +191,8 @@ def sample_allocation(V, C, eps2):
 
 
 def paper_evaluation_set(s_hat):
-    """Sec. 3.3: [logspace(-5,-2,4) logspace(log10(1e-2+1e-3),0,76)], with s_0 = 0 and the
-    sampling shifts added (the evaluation set starts at 0 and contains the sampling set)."""
+    """Sec. 3.3: [logspace(-5,-2,4) logspace(log10(1e-2+1e-3),0,76)] with the sampling shifts
+    added; it contains the sampling set and starts at sigma_0 = s^_0 (0 in the paper)."""
+    s_hat = np.asarray(s_hat, dtype=float)
     grid = np.concatenate([np.logspace(-5, -2, 4), np.logspace(np.log10(1e-2 + 1e-3), 0, 76)])
-    return np.unique(np.concatenate([[0.0], np.asarray(s_hat, dtype=float), grid]))
+    return np.unique(np.concatenate([s_hat, grid[grid >= s_hat[0]]]))

@@ -86,7 +86,8 @@ bool increasing(const double* v, int n) {
 int check_inputs(const double* s_hat, int m, const double* VL_hat, const double* Vbar_hat, const double* s,
                  int n) {
   if (!s_hat || !VL_hat || !Vbar_hat || !s || m < 2 || n < 2) return FS_ERR_ARG;
-  if (!increasing(s_hat, m) || !increasing(s, n) || s[0] != 0.0) return FS_ERR_ARG;
+  // sigma_0 is the first sampling shift (0 in the paper), and the evaluation set starts there
+  if (!increasing(s_hat, m) || !increasing(s, n) || s[0] != s_hat[0]) return FS_ERR_ARG;
   for (int i = 0; i < m; i++) {
     if (!std::isfinite(VL_hat[i]) || VL_hat[i] < 0.0) return FS_ERR_INPUT;
     for (int j = i; j < m; j++)
@@ -224,12 +225,13 @@ int fs_sample_allocation(const double* V, const double* C, int nlev, double eps2
 
 int fs_eval_grid(const double* s_hat, int m, double* s, int cap, int* n) {
   if (!s_hat || !n || m < 1 || !increasing(s_hat, m)) return FS_ERR_ARG;
-  std::vector<double> v = {0.0};
-  for (int k = 0; k < 4; k++) v.push_back(std::pow(10.0, -5.0 + k));  // logspace(-5, -2, 4)
+  std::vector<double> v(s_hat, s_hat + m);
   const double lo = std::log10(1e-2 + 1e-3);
-  for (int k = 0; k < 76; k++)  // logspace(lo, 0, 76), its last point exactly 1
-    v.push_back(k == 75 ? 1.0 : std::pow(10.0, lo + (0.0 - lo) * k / 75.0));
-  v.insert(v.end(), s_hat, s_hat + m);
+  for (int k = 0; k < 80; k++) {
+    // logspace(-5, -2, 4), then logspace(lo, 0, 76) with its last point exactly 1
+    const double x = k < 4 ? std::pow(10.0, -5.0 + k) : (k == 79 ? 1.0 : std::pow(10.0, lo - lo * (k - 4) / 75.0));
+    if (x >= s_hat[0]) v.push_back(x);  // the set starts at sigma_0 = s_hat[0]
+  }
   std::sort(v.begin(), v.end());
   v.erase(std::unique(v.begin(), v.end()), v.end());
   *n = (int)v.size();

@@ -36,9 +36,11 @@ def _sampled(seed, m=5):
 
 
 def test_evaluation_grid():
-    s = pkg.fs_eval_grid(S_HAT)
-    ref = osh.paper_evaluation_set(S_HAT)
-    assert len(s) == len(ref) and np.allclose(s, ref, rtol=1e-14, atol=0)
+    for s_hat in (S_HAT, np.array([0.005, 0.05, 0.25, 0.5, 1.0])):
+        s = pkg.fs_eval_grid(s_hat)
+        ref = osh.paper_evaluation_set(s_hat)
+        assert len(s) == len(ref) and np.allclose(s, ref, rtol=1e-14, atol=0)
+        assert s[0] == s_hat[0]
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2, 3])
@@ -53,10 +55,14 @@ def test_interpolated_manifolds(seed):
     assert np.allclose(Vl[both], ref[both], rtol=1e-11, atol=0)
 
 
-@pytest.mark.parametrize("seed,L,m", [(0, 1, 5), (1, 2, 5), (2, 3, 5), (3, 2, 4), (4, 3, 6)])
-def test_selected_shifts_match_brute_force(seed, L, m):
+@pytest.mark.parametrize("seed,L,m,s0", [(0, 1, 5, 0.0), (1, 2, 5, 0.0), (2, 3, 5, 0.0), (3, 2, 4, 0.0),
+                                         (4, 3, 6, 0.0), (5, 3, 5, 0.005)])
+def test_selected_shifts_match_brute_force(seed, L, m, s0):
     s_hat, VL_hat, vbar, iters = _sampled(seed, m)
+    s_hat = s_hat.copy()
+    s_hat[0] = s0
     s = np.unique(np.concatenate([s_hat, np.linspace(0.0, 1.0, 21), [1e-3, 1e-2]]))
+    s = s[s >= s0]
     got = pkg.fs_select_shifts(s_hat, VL_hat, vbar, iters, s, L)
     idx, F = osh.select_shifts(s_hat, VL_hat, vbar, iters, s, L)
     assert got["F"] == pytest.approx(F, rel=1e-12)
@@ -109,6 +115,6 @@ def test_sample_allocation_parity_and_errors():
         pkg.fs_sample_allocation(V, -C, 1e-3)
     s_hat, VL_hat, vbar, iters = _sampled(1)
     with pytest.raises(pkg.FsError):
-        pkg.fs_select_shifts(s_hat, VL_hat, vbar, iters, np.array([0.1, 0.5, 1.0]), 1)  # s_0 != 0
+        pkg.fs_select_shifts(s_hat, VL_hat, vbar, iters, np.array([0.1, 0.5, 1.0]), 1)  # s_0 != s^_0
     with pytest.raises(pkg.FsError):
         pkg.fs_select_shifts(s_hat, -VL_hat, vbar, iters, S_HAT, 1)
