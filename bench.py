@@ -299,6 +299,45 @@ def run_serving(pkg, inputs, device, n_jobs, rate=20.0, budget_gb=60, max_active
             "restarts": int(sum(r["restarts"] for r in res)), "max_iters": int(max(r["max_iters"] for r in res))}
 
 
+# --------------------------------------------------------------------------- the full method
+def run_pipeline(pkg, ctx, w, kw, levels=4, n_s=5, n_ref=512, n_max=128, seed=9000):
+    """The paper's procedure end to end on the workload's lattice: variance sampling at the
+    sampling shifts (Sec. 3.1, N_s = 5 as in the paper), interpolation and optimal shifts
+    (Sec. 3.2-3.3), sample allocation for a target variance (Eq. (num_samples)), then the
+    split-even level traces (Eq. (fs_trace_est)) whose variance the sampling predicts.
+    Target: the variance of a single-level estimator at sigma_0 with n_ref vectors. N_l is
+    capped at n_max to bound the run; the measured V_l are compared with the predictions."""
+    s_hat = [w["sigmas"][0], 0.05, 0.25, 0.5, 1.0]  # sigma_0 = the workload's first shift
+    gam = pkg.gamma_matrix(w["gamma"])
+    t0 = time.time()
+    vs = ctx.variance_sample(w["m"], s_hat, gam, [w["p"]], n_s, seed=seed, job=1, **kw)
+    t_vs = time.time() - t0
+    s = pkg.fs_eval_grid(s_hat)
+    t1 = time.perf_counter()
+    sel = pkg.fs_select_shifts(s_hat, vs["VL"][0], vs["Vbar"][0], vs["iters"], s, levels - 1)
+    t_sel = time.perf_counter() - t1
+    eps2 = vs["VL"][0][0] / n_ref
+    N, mu, v_fs, c_fs = pkg.fs_sample_allocation(sel["V"], sel["C"], eps2)
+    n_use = [int(min(max(1, np.ceil(x)), n_max)) for x in N]
+    t2 = time.time()
+    out = ctx.mlmc_level_trace(w["m"], sel["sigma"], gam, w["p"], n_use, seed=seed, job=2, estimator="split_even",
+                               **kw)
+    t_tr = time.time() - t2
+    var_meas = [float(v) for v in out["var"]]
+    import math
+    return {"sampling_shifts": s_hat, "n_s": n_s, "evaluation_shifts": len(s), "levels": levels,
+            "sigma": [float(x) for x in sel["sigma"]],
+            "V_pred": [float(x) for x in sel["V"]], "V_meas": var_meas,
+            "iters_sampled": [float(x) for x in vs["iters"]], "C_pred": [float(x) for x in sel["C"]],
+            "eps2": eps2, "N_opt": [float(x) for x in N], "N_used": n_use,
+            "V_FS_pred_at_N_used": float(sum(v / n for v, n in zip(sel["V"], n_use))),
+            "V_FS_meas_at_N_used": float(sum(v / n for v, n in zip(var_meas, n_use))),
+            "cost_ratio_pred": float(c_fs / (n_ref * vs["iters"][0])),
+            "brute_force_combinations": math.comb(len(s) - 1, levels - 1),
+            "t_variance_sample_s": t_vs, "t_select_ms": 1e3 * t_sel, "t_level_traces_s": t_tr,
+            "solves": int(len(out["stats"])), "rc": int(out["rc"])}
+
+
 # --------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -316,6 +355,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=8.0, help="seconds of oracle work per reference step")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--serve-jobs", type=int, default=12, help="jobs in the serving run (0: skip)")
+    ap.add_argument("--no-pipeline", action="store_true",
+                    help="skip the end-to-end run of variance sampling, shift selection and allocation")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -420,6 +461,10 @@ def main():
         if ratio is not None:
             roof["traffic"] = ratio * bytes_per_launch
 
+    pipeline = None
+    if not args.no_pipeline and rank == 0:
+        pipeline = run_pipeline(pkg, ctx, w, kw)
+
     serving = None
     if args.serve_jobs > 0:
         serving = run_serving(pkg, inputs, local, args.serve_jobs)
@@ -437,7 +482,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_of(args, w), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk, "serving": serving,
+                "gpu_launches": launches, "clocks": clk, "serving": serving, "pipeline": pipeline,
                 "solver": {"mean_iters": float(np.mean(iters)) if iters else None,
                            "max_iters": int(max(iters)) if iters else None,
                            "mean_reliable_updates": float(np.mean(updates)) if updates else None,
