@@ -267,6 +267,32 @@ def test_results_identical_alone_and_in_a_mix(prec):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+def test_tile_shapes_give_identical_systems(prec):
+    """Every inner-precision hop variant computes a system the same way: a 64-system tile
+    (the persistent kernel over two 32-system chunks), a 40-system tile (20 systems per
+    warp, the prefetch kernel) and single-system tiles give bit-identical solutions, each
+    within tolerance by the oracle's residual."""
+    dims = (8, 4, 4, 8)
+    u = inputs.gauge_field(dims, "smooth", seed=33, eps=0.4)
+    b = inputs.random_spinor(dims, 41, nvec=40)
+    sig = [0.02]
+    ctx = make_ctx(dims, u)
+    kw = dict(prec=prec, tol=1e-8, link_compress=12)
+    x64, st64, rc = ctx.shifted_solve(-0.25, sig, np.concatenate([b, b[:24]]), rhs_tile=64, **kw)
+    assert rc == 0
+    x40, _, rc = ctx.shifted_solve(-0.25, sig, b, rhs_tile=40, **kw)
+    assert rc == 0
+    for k in (0, 17, 39):
+        x1, _, rc = ctx.shifted_solve(-0.25, sig, b[k:k + 1], rhs_tile=1, **kw)
+        assert rc == 0
+        assert np.array_equal(x64[0, k], x1[0, 0]) and np.array_equal(x40[0, k], x1[0, 0]), k
+        assert rel_resid(u, x1[0, 0], b[k], -0.25, 0.02, dims) <= 1.05e-8
+    # the duplicated right-hand sides in the 64-system tile solve identically too
+    assert np.array_equal(x64[0, 40:], x64[0, :24])
+    ctx.close()
+
+
 def test_product_chain_and_split_even_in_mixed_tiles():
     """Nested (product) and paired (split-even) systems with refill in a small tile."""
     dims = (4, 4, 2, 4)
