@@ -39,6 +39,7 @@ struct BlasArgs {
   int Vh;
   Shape sh;
   int mask;
+  int sysmajor;  // 1: one system per block row, work items over the selected systems
 };
 
 template <typename Tm>
@@ -51,7 +52,8 @@ __device__ __forceinline__ void cmul_acc(Tm (&o)[24], const Tm (&a)[24], Tm cr, 
   }
 }
 
-template <typename Ts, typename Tx, typename Tm, int OP>
+// WL: system-major work-list launch (a.sysmajor); else the tile shape.
+template <typename Ts, typename Tx, typename Tm, int OP, bool WL>
 __global__ void __launch_bounds__(256) blas_kernel(BlasArgs a) {
   if (a.gate != nullptr && *a.gate == 0) return;
   constexpr int K = (OP == OP_XR || OP == OP_SETR) ? 3 : (OP == OP_NORM64 ? 1 : 0);
@@ -60,19 +62,6 @@ __global__ void __launch_bounds__(256) blas_kernel(BlasArgs a) {
   const int Vh = a.Vh;
   const int lsys = threadIdx.x % sh.NB;
   const int lsite = threadIdx.x / sh.NB;
-  const int sys = blockIdx.y * sh.NB + lsys;
-  const bool sel = sys < sh.N && selected(a.st, sys, a.mask);
-  Tm c0r = 0, c0i = 0, c1r = 0, c1i = 0;
-  bool reset = false;
-  if (sel) {
-    const SysState& s = a.st[sys];
-    if (OP == OP_P) { c0r = coef<Tm>(s, C_BETA); c0i = coef<Tm>(s, C_BETA + 1);
-                      c1r = coef<Tm>(s, C_OMEGA); c1i = coef<Tm>(s, C_OMEGA + 1); }
-    if (OP == OP_S) { c0r = coef<Tm>(s, C_ALPHA); c0i = coef<Tm>(s, C_ALPHA + 1); }
-    if (OP == OP_XR) { c0r = coef<Tm>(s, C_ALPHA); c0i = coef<Tm>(s, C_ALPHA + 1);
-                       c1r = coef<Tm>(s, C_OMEGA); c1i = coef<Tm>(s, C_OMEGA + 1); }
-    if (OP == OP_SETR) reset = (s.flags & (FLAG_RESTART | FLAG_INIT)) != 0;
-  }
   const Field<Ts> r = make_field<Ts>(a.r, Vh, sh.N);
   const Field<Ts> rh = make_field<Ts>(a.rhat, Vh, sh.N);
   const Field<Ts> p = make_field<Ts>(a.p, Vh, sh.N);
@@ -84,7 +73,19 @@ __global__ void __launch_bounds__(256) blas_kernel(BlasArgs a) {
   const Field<double> xh = make_field<double>(a.x_hi, Vh, sh.N, true);
   const Field<double> src = make_field<double>(const_cast<double*>(a.src), Vh, sh.N, true);
 
-  for (int chunk = blockIdx.x; chunk < sh.nchunk; chunk += gridDim.x) {
+  // one chunk of sites for system `sys` (sel: the system takes part), block rows sys_base..
+  auto chunk_body = [&](const int sys, const int chunk, const bool sel, const int sys_base) {
+    Tm c0r = 0, c0i = 0, c1r = 0, c1i = 0;
+    bool reset = false;
+    if (sel) {
+      const SysState& st = a.st[sys];
+      if (OP == OP_P) { c0r = coef<Tm>(st, C_BETA); c0i = coef<Tm>(st, C_BETA + 1);
+                        c1r = coef<Tm>(st, C_OMEGA); c1i = coef<Tm>(st, C_OMEGA + 1); }
+      if (OP == OP_S) { c0r = coef<Tm>(st, C_ALPHA); c0i = coef<Tm>(st, C_ALPHA + 1); }
+      if (OP == OP_XR) { c0r = coef<Tm>(st, C_ALPHA); c0i = coef<Tm>(st, C_ALPHA + 1);
+                         c1r = coef<Tm>(st, C_OMEGA); c1i = coef<Tm>(st, C_OMEGA + 1); }
+      if (OP == OP_SETR) reset = (st.flags & (FLAG_RESTART | FLAG_INIT)) != 0;
+    }
     const int site = chunk * sh.SB + lsite;
     const bool act = sel && site < Vh;
     double dv[K > 0 ? K : 1];
@@ -181,7 +182,21 @@ __global__ void __launch_bounds__(256) blas_kernel(BlasArgs a) {
       }
     }
     if constexpr (K > 0) {
-      group_partials<K>(dv, lsite, lsys, blockIdx.y * sh.NB, sh, Vh, chunk, smem, a.partial);
+      group_partials<K>(dv, lsite, lsys, sys_base, sh, Vh, chunk, smem, a.partial);
+    }
+  };
+
+  if constexpr (!WL) {
+    const int sys = blockIdx.y * sh.NB + lsys;
+    const bool sel = sys < sh.N && selected(a.st, sys, a.mask);
+    for (int chunk = blockIdx.x; chunk < sh.nchunk; chunk += gridDim.x) chunk_body(sys, chunk, sel, blockIdx.y * sh.NB);
+  } else {
+    // system-major (NB = 1, grid.y = 1): items (k-th selected system, chunk)
+    __shared__ int slist[64];
+    const int nsel = selected_list(a.st, sh.N, a.mask, slist);
+    for (int item = blockIdx.x; item < nsel * sh.nchunk; item += gridDim.x) {
+      const int sys = slist[item / sh.nchunk];
+      chunk_body(sys, item - (item / sh.nchunk) * sh.nchunk, true, sys);
     }
   }
 }
@@ -217,19 +232,21 @@ __global__ void __launch_bounds__(256) cg_kernel(CgArgs a) {
   constexpr int K = (OP == CG_XS || OP == CG_R) ? 1 : 0;
   __shared__ double smem[256];
   const Shape sh = a.sh;
-  const int lsys = threadIdx.x % sh.NB;
-  const int lsite = threadIdx.x / sh.NB;
-  const int sys = blockIdx.y * sh.NB + lsys;
-  const bool sel = sys < sh.N && selected(a.st, sys, a.mask);
-  const double alpha = sel ? a.st[sys].cd[C_ALPHA] : 0.0;
-  const double beta = sel ? a.st[sys].cd[C_BETA] : 0.0;
+  const int lsite = threadIdx.x;  // system-major: NB = 1
   const Field<double> fx = make_field<double>(a.x, a.Vh, sh.N, true), fs = make_field<double>(a.s, a.Vh, sh.N, true);
   const Field<double> fp = make_field<double>(a.p, a.Vh, sh.N, true), fq = make_field<double>(a.q, a.Vh, sh.N, true);
   const Field<double> fg = make_field<double>(a.g, a.Vh, sh.N, true), fw = make_field<double>(a.w, a.Vh, sh.N, true);
   const Field<double> fr = make_field<double>(a.r, a.Vh, sh.N, true);
-  for (int chunk = blockIdx.x; chunk < sh.nchunk; chunk += gridDim.x) {
+  // work items (k-th system in the fallback, chunk)
+  __shared__ int slist[64];
+  const int nsel = selected_list(a.st, sh.N, a.mask, slist);
+  for (int item = blockIdx.x; item < nsel * sh.nchunk; item += gridDim.x) {
+    const int sys = slist[item / sh.nchunk];
+    const int chunk = item - (item / sh.nchunk) * sh.nchunk;
+    const double alpha = a.st[sys].cd[C_ALPHA];
+    const double beta = a.st[sys].cd[C_BETA];
     const int site = chunk * sh.SB + lsite;
-    const bool act = sel && site < a.Vh;
+    const bool act = site < a.Vh;
     double dv[1] = {0.0};
     if (act) {
       double u[24], v[24];
@@ -264,7 +281,7 @@ __global__ void __launch_bounds__(256) cg_kernel(CgArgs a) {
         fp.store(site, sys, u);
       }
     }
-    if constexpr (K > 0) group_partials<K>(dv, lsite, lsys, blockIdx.y * sh.NB, sh, a.Vh, chunk, smem, a.partial);
+    if constexpr (K > 0) group_partials<K>(dv, lsite, 0, sys, sh, a.Vh, chunk, smem, a.partial);
   }
 }
 

@@ -102,6 +102,7 @@ class Tile : public TileBase {
   static constexpr int SYS_SITES = 128;
   Shape sh1{};
   Launch L1{};
+  Launch LW{};   // system-major work-list launches: resident blocks sweep (selected system, chunk) items
   Launch LH{};   // hopping kernels: one site chunk per block, so resident blocks sweep the
                  // lattice in order and neighbour spinors are re-read from L2, not DRAM
   int ngroups = 0;
@@ -149,6 +150,10 @@ class Tile : public TileBase {
     L1.block = SYS_SITES;
     L1.grid_x = std::min(sh1.nchunk, std::max(1, 8 * c->nsm));
     L1.stream = c->stream;
+    LW.stream = c->stream;
+    LW = L1;
+    LW.grid_y = 1;
+    LW.grid_x = std::max(1, 4 * c->nsm);  // 4 resident 128-site blocks per SM
     LH = L;
     LH.grid_x = sh.nchunk;
     ngroups = c->g.Vh / 8;
@@ -197,6 +202,7 @@ class Tile : public TileBase {
     b.x_lo = x_lo; b.r = r; b.rhat = rhat; b.p = p; b.v = v; b.s = s; b.t = t;
     b.x_hi = x_hi; b.src = src; b.st = st_d; b.partial = part; b.gate = gated ? gate : nullptr;
     b.Vh = c->g.Vh; b.sh = sysmajor ? sh1 : sh; b.mask = mask;
+    b.sysmajor = sysmajor ? 1 : 0;
     return b;
   }
   cudaError_t fin(int op, int mask, const double* a_, const double* b_ = nullptr, const double* c_ = nullptr) {
@@ -238,11 +244,13 @@ class Tile : public TileBase {
   cudaError_t enqueue_rhs_from_canon(const double* canon) override {
     L.stream = c->stream;
     L1.stream = c->stream;
+    LW.stream = c->stream;
     return launch_pack<double>(z_e, z_o, canon, vec_d, c->g, sh1, L1, true);
   }
 
   cudaError_t enqueue_noise() override {
     L1.stream = c->stream;
+    LW.stream = c->stream;
     noise_kernel<<<dim3(std::min(2 * sh1.nchunk, 2 * L1.grid_x), N), SYS_SITES, 0, c->stream>>>(z_e, z_o, spec_d, st_d,
                                                                                       c->g, sh1);
     note_launch();
@@ -253,15 +261,16 @@ class Tile : public TileBase {
   // refilling a few slots costs only their own systems.
   cudaError_t enqueue_init() override {
     L1.stream = c->stream;
+    LW.stream = c->stream;
     cudaError_t e;
     // bhat_e = z_e - D_eo A^-1 z_o, ||bhat||^2
     if ((e = launch_hop<double>(COEF_PREP, DOT_NORM, 18, hop(bhat, z_o, z_e, nullptr, nullptr, pa, 0, MASK_INIT,
-                                                              false, true, true), L1))) return e;
-    if ((e = launch_blas<Ts>(OP_NORM64, blas(MASK_INIT, z_e, pb, false, true), L1))) return e;
-    if ((e = launch_blas<Ts>(OP_NORM64, blas(MASK_INIT, z_o, pc, false, true), L1))) return e;
-    if ((e = launch_blas<Ts>(OP_ZEROX, blas(MASK_INIT, nullptr, nullptr, false, true), L1))) return e;
+                                                              false, true, true), LW))) return e;
+    if ((e = launch_blas<Ts>(OP_NORM64, blas(MASK_INIT, z_e, pb, false, true), LW))) return e;
+    if ((e = launch_blas<Ts>(OP_NORM64, blas(MASK_INIT, z_o, pc, false, true), LW))) return e;
+    if ((e = launch_blas<Ts>(OP_ZEROX, blas(MASK_INIT, nullptr, nullptr, false, true), LW))) return e;
     if ((e = fin(FIN_NORM, MASK_INIT, pa, pb, pc))) return e;
-    if ((e = launch_blas<Ts>(OP_SETR, blas(MASK_INIT, bhat, pa, false, true), L1))) return e;
+    if ((e = launch_blas<Ts>(OP_SETR, blas(MASK_INIT, bhat, pa, false, true), LW))) return e;
     return fin(FIN_INIT, MASK_INIT, pa);
   }
 
@@ -286,16 +295,17 @@ class Tile : public TileBase {
     // system-major shape: a block serves one system, so unflagged systems cost one flag
     // read per block instead of occupying FP64 issue slots inside mixed warps.
     L1.stream = c->stream;
-    if ((e = launch_blas<Ts>(OP_ACCX, blas(MASK_UPDATE, nullptr, nullptr, true, true), L1))) return e;
+    LW.stream = c->stream;
+    if ((e = launch_blas<Ts>(OP_ACCX, blas(MASK_UPDATE, nullptr, nullptr, true, true), LW))) return e;
     if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
                                 hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, MASK_UPDATE, true, true,
-                                    true), L1)))
+                                    true), LW)))
       return e;
     if ((e = launch_hop<double>(COEF_TRUERES, DOT_NORM, 18,
-                                hop(r_hi, tmp64, x_hi, bhat, nullptr, pa, 0, MASK_UPDATE, true, true, true), L1)))
+                                hop(r_hi, tmp64, x_hi, bhat, nullptr, pa, 0, MASK_UPDATE, true, true, true), LW)))
       return e;
     if ((e = fin(FIN_TRUE, MASK_UPDATE, pa))) return e;
-    if ((e = launch_blas<Ts>(OP_SETR, blas(MASK_UPDATE, r_hi, pa, true, true), L1))) return e;
+    if ((e = launch_blas<Ts>(OP_SETR, blas(MASK_UPDATE, r_hi, pa, true, true), LW))) return e;
     return fin(FIN_UPDATE, MASK_UPDATE, pa);
   }
 
@@ -332,19 +342,21 @@ class Tile : public TileBase {
 
   cudaError_t enqueue_recon() override {
     L1.stream = c->stream;
+    LW.stream = c->stream;
     // x_o = A^-1 (z_o - D_oe x_e)
     return launch_hop<double>(COEF_RECON, DOT_NONE, 18,
-                              hop(x_o, x_hi, z_o, nullptr, nullptr, nullptr, 1, MASK_HARVEST, false, true, true), L1);
+                              hop(x_o, x_hi, z_o, nullptr, nullptr, nullptr, 1, MASK_HARVEST, false, true, true), LW);
   }
 
   cudaError_t enqueue_verify() override {
     L1.stream = c->stream;
+    LW.stream = c->stream;
     cudaError_t e;
     if ((e = launch_hop<double>(COEF_FULLRES, DOT_NORM, 18,
-                                hop(r_hi, x_o, x_hi, z_e, nullptr, pa, 0, MASK_HARVEST, false, true, true), L1)))
+                                hop(r_hi, x_o, x_hi, z_e, nullptr, pa, 0, MASK_HARVEST, false, true, true), LW)))
       return e;
     if ((e = launch_hop<double>(COEF_FULLRES, DOT_NORM, 18,
-                                hop(tmp64, x_hi, x_o, z_o, nullptr, pb, 1, MASK_HARVEST, false, true, true), L1)))
+                                hop(tmp64, x_hi, x_o, z_o, nullptr, pb, 1, MASK_HARVEST, false, true, true), LW)))
       return e;
     return fin(FIN_VERIFY, MASK_HARVEST, pa, pb);
   }
@@ -378,7 +390,7 @@ class Tile : public TileBase {
   }
   template <int OP>
   cudaError_t cg_op(int mask, double* part = nullptr) {
-    cg_kernel<OP><<<dim3(L1.grid_x, L1.grid_y), SYS_SITES, 0, c->stream>>>(cga(mask, part));
+    cg_kernel<OP><<<dim3(LW.grid_x, 1), SYS_SITES, 0, c->stream>>>(cga(mask, part));
     note_launch();
     return cudaGetLastError();
   }
@@ -387,10 +399,10 @@ class Tile : public TileBase {
     cudaError_t e;
     if ((e = cg_op<CG_G5>(mask))) return e;
     if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
-                                hop(tmp64, cg_g, nullptr, nullptr, nullptr, nullptr, 1, mask, false, true, true), L1)))
+                                hop(tmp64, cg_g, nullptr, nullptr, nullptr, nullptr, 1, mask, false, true, true), LW)))
       return e;
     if ((e = launch_hop<double>(COEF_MHAT, DOT_NONE, 18,
-                                hop(cg_w, tmp64, cg_g, nullptr, nullptr, nullptr, 0, mask, false, true, true), L1)))
+                                hop(cg_w, tmp64, cg_g, nullptr, nullptr, nullptr, 0, mask, false, true, true), LW)))
       return e;
     return cg_op<CG_R>(mask, part);
   }
@@ -398,13 +410,14 @@ class Tile : public TileBase {
   cudaError_t cg_true_residual(int mask, double* part) {
     cudaError_t e;
     if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
-                                hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, mask, false, true, true), L1)))
+                                hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, mask, false, true, true), LW)))
       return e;
     return launch_hop<double>(COEF_TRUERES, DOT_NORM, 18,
-                              hop(r_hi, tmp64, x_hi, bhat, nullptr, part, 0, mask, false, true, true), L1);
+                              hop(r_hi, tmp64, x_hi, bhat, nullptr, part, 0, mask, false, true, true), LW);
   }
   cudaError_t enqueue_cg_init() override {
     L1.stream = c->stream;
+    LW.stream = c->stream;
     cudaError_t e;
     if ((e = cg_true_residual(MASK_CG, pa))) return e;
     if ((e = cg_normal_residual(MASK_CG, pb))) return e;
@@ -413,13 +426,14 @@ class Tile : public TileBase {
   }
   cudaError_t enqueue_cg_iter() override {
     L1.stream = c->stream;
+    LW.stream = c->stream;
     cudaError_t e;
     // q = M p, alpha = <r, r> / ||q||^2
     if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
-                                hop(tmp64, cg_p, nullptr, nullptr, nullptr, nullptr, 1, MASK_CG, false, true, true), L1)))
+                                hop(tmp64, cg_p, nullptr, nullptr, nullptr, nullptr, 1, MASK_CG, false, true, true), LW)))
       return e;
     if ((e = launch_hop<double>(COEF_MHAT, DOT_NORM, 18,
-                                hop(cg_q, tmp64, cg_p, nullptr, nullptr, pa, 0, MASK_CG, false, true, true), L1)))
+                                hop(cg_q, tmp64, cg_p, nullptr, nullptr, pa, 0, MASK_CG, false, true, true), LW)))
       return e;
     if ((e = fin(FIN_CG_ALPHA, MASK_CG, pa))) return e;
     if ((e = cg_op<CG_XS>(MASK_CG, pa))) return e;   // x += alpha p, s -= alpha q
@@ -434,6 +448,7 @@ class Tile : public TileBase {
   cudaError_t enqueue_solution_to_canon(double* canon) override {
     L.stream = c->stream;
     L1.stream = c->stream;
+    LW.stream = c->stream;
     return launch_unpack<double>(canon, x_hi, x_o, vec_d, c->g, sh1, L1, true);
   }
 };

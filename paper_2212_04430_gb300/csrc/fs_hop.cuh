@@ -271,10 +271,29 @@ __device__ __forceinline__ void group_partials(const double (&vals)[K], int lsit
   __syncthreads();
 }
 
+// Selected systems of a system-major launch (one system per block row, N <= 64), in
+// ascending order, listed by every block itself: work items are then (k-th selected
+// system, chunk), so a launch costs nothing for the systems it skips. Needs >= 64 threads.
+__device__ __forceinline__ int selected_list(const SysState* st, int N, int mask, int* list) {
+  __shared__ unsigned bal[2];
+  const int t = threadIdx.x;
+  const bool s = t < N && t < 64 && selected(st, t, mask);
+  if (t < 64) {
+    const unsigned b = __ballot_sync(0xffffffffu, s);
+    if ((t & 31) == 0) bal[t >> 5] = b;
+  }
+  __syncthreads();
+  if (s) list[__popc(bal[t >> 5] & ((1u << (t & 31)) - 1u)) + (t >= 32 ? __popc(bal[0]) : 0)] = t;
+  const int n = __popc(bal[0]) + __popc(bal[1]);
+  __syncthreads();
+  return n;
+}
+
 // Half-precision storage is held to 3 resident blocks (<= 80 registers, no spills
 // with 18-real links) for latency hiding; FP32 storage needs ~128 registers for its
 // float4 spinors and keeps 2 blocks; FP64 is ALU bound.
-template <typename Ts, typename Tg, typename Tm, int NR, int COEF, int DOT>
+// WL: system-major work-list launch (a.sysmajor); else the tile shape.
+template <typename Ts, typename Tg, typename Tm, int NR, int COEF, int DOT, bool WL = false>
 __global__ void __launch_bounds__(256, sizeof(Tm) == 8 ? 2 : (sizeof(Ts) == 2 ? 3 : 2)) hop_kernel(HopArgs a) {
   if (a.gate != nullptr && *a.gate == 0) return;
   constexpr int K = DotK<DOT>::K;
@@ -283,24 +302,22 @@ __global__ void __launch_bounds__(256, sizeof(Tm) == 8 ? 2 : (sizeof(Ts) == 2 ? 
   const Geom g = a.g;
   const int lsys = threadIdx.x % sh.NB;
   const int lsite = threadIdx.x / sh.NB;
-  const int sys = blockIdx.y * sh.NB + lsys;
-  const bool smj = a.sysmajor != 0;
+  constexpr bool smj = WL;
   const Field<Ts> in = make_field<Ts>(const_cast<void*>(a.in), g.Vh, sh.N, smj);
   const Field<Ts> out = make_field<Ts>(a.out, g.Vh, sh.N, smj);
-  const bool sel = sys < sh.N && selected(a.st, sys, a.mask);
 
-  Tm ca = 0, cb = 1, cc = 0;
-  if (sel) {
-    const SysState& s = a.st[sys];
-    if (COEF == COEF_MHAT) { ca = coef<Tm>(s, C_A); cb = coef<Tm>(s, C_MINV4A); }
-    else if (COEF == COEF_DSLASH) { ca = coef<Tm>(s, C_A); cb = (Tm)-0.5; }
-    else if (COEF == COEF_PREP) { ca = 1; cb = coef<Tm>(s, C_INV2A); }
-    else if (COEF == COEF_RECON) { ca = coef<Tm>(s, C_INVA); cb = coef<Tm>(s, C_INV2A); }
-    else if (COEF == COEF_TRUERES) { ca = coef<Tm>(s, C_MINVA); cb = coef<Tm>(s, C_INV4A); cc = 1; }
-    else if (COEF == COEF_FULLRES) { ca = coef<Tm>(s, C_MINVA); cb = (Tm)0.5; cc = 1; }
-  }
-
-  for (int chunk = blockIdx.x; chunk < sh.nchunk; chunk += gridDim.x) {
+  // one chunk of sites for system `sys` (sel: the system takes part), block rows sys_base..
+  auto chunk_body = [&](const int sys, const int chunk, const bool sel, const int sys_base) {
+    Tm ca = 0, cb = 1, cc = 0;
+    if (sel) {
+      const SysState& s = a.st[sys];
+      if (COEF == COEF_MHAT) { ca = coef<Tm>(s, C_A); cb = coef<Tm>(s, C_MINV4A); }
+      else if (COEF == COEF_DSLASH) { ca = coef<Tm>(s, C_A); cb = (Tm)-0.5; }
+      else if (COEF == COEF_PREP) { ca = 1; cb = coef<Tm>(s, C_INV2A); }
+      else if (COEF == COEF_RECON) { ca = coef<Tm>(s, C_INVA); cb = coef<Tm>(s, C_INV2A); }
+      else if (COEF == COEF_TRUERES) { ca = coef<Tm>(s, C_MINVA); cb = coef<Tm>(s, C_INV4A); cc = 1; }
+      else if (COEF == COEF_FULLRES) { ca = coef<Tm>(s, C_MINVA); cb = (Tm)0.5; cc = 1; }
+    }
     const int site = chunk * sh.SB + lsite;
     const bool act = sel && site < g.Vh;
     if (a.work != nullptr) {  // profiling: (site, system) pairs computed, one atomic per warp
@@ -363,7 +380,21 @@ __global__ void __launch_bounds__(256, sizeof(Tm) == 8 ? 2 : (sizeof(Ts) == 2 ? 
       out.store(site, sys, o);
     }
     if constexpr (K > 0) {
-      group_partials<K>(dv, lsite, lsys, blockIdx.y * sh.NB, sh, g.Vh, chunk, smem, a.partial);
+      group_partials<K>(dv, lsite, lsys, sys_base, sh, g.Vh, chunk, smem, a.partial);
+    }
+  };
+
+  if constexpr (!WL) {
+    const int sys = blockIdx.y * sh.NB + lsys;
+    const bool sel = sys < sh.N && selected(a.st, sys, a.mask);
+    for (int chunk = blockIdx.x; chunk < sh.nchunk; chunk += gridDim.x) chunk_body(sys, chunk, sel, blockIdx.y * sh.NB);
+  } else {
+    // system-major (NB = 1, grid.y = 1): items (k-th selected system, chunk)
+    __shared__ int slist[64];
+    const int nsel = selected_list(a.st, sh.N, a.mask, slist);
+    for (int item = blockIdx.x; item < nsel * sh.nchunk; item += gridDim.x) {
+      const int sys = slist[item / sh.nchunk];
+      chunk_body(sys, item - (item / sh.nchunk) * sh.nchunk, true, sys);
     }
   }
 }

@@ -73,11 +73,12 @@ cudaError_t launch_hop(int coef, int dot, int nr, const HopArgs& a, const Launch
   using Tg = typename GaugeOf<Ts>::T;
   using Tm = MathOf<Ts>;
   const dim3 grid(l.grid_x, l.grid_y), block(l.block);
-#define FS_HOP(C, D, R)                                                  \
-  if (coef == C && dot == D && nr == R) {                                \
-    hop_kernel<Ts, Tg, Tm, R, C, D><<<grid, block, 0, l.stream>>>(a);    \
-    note_launch();                                                       \
-    return cudaGetLastError();                                           \
+#define FS_HOP(C, D, R)                                                           \
+  if (coef == C && dot == D && nr == R) {                                         \
+    if (a.sysmajor) hop_kernel<Ts, Tg, Tm, R, C, D, true><<<grid, block, 0, l.stream>>>(a); \
+    else hop_kernel<Ts, Tg, Tm, R, C, D, false><<<grid, block, 0, l.stream>>>(a);           \
+    note_launch();                                                                \
+    return cudaGetLastError();                                                    \
   }
 #define FS_HOP_PF(C, D, R) \
   if (coef == C && dot == D && nr == R) return launch_hop_pf<Ts, Tg, Tm, R, C, D>(a, l);
@@ -112,14 +113,17 @@ cudaError_t launch_blas(int op, const BlasArgs& a, const Launch& l) {
   using Tx = typename XOf<Ts>::T;
   using Tm = MathOf<Ts>;
   const dim3 grid(l.grid_x, l.grid_y), block(l.block);
+  // the per-iteration solver updates run on the tile shape; the FP64-field operations
+  // (x_hi updates, residual restarts, norms) on the system-major work list
+  if ((op == OP_P || op == OP_S || op == OP_XR) == (a.sysmajor != 0)) return cudaErrorInvalidValue;
   switch (op) {
-    case OP_P: blas_kernel<Ts, Tx, Tm, OP_P><<<grid, block, 0, l.stream>>>(a); break;
-    case OP_S: blas_kernel<Ts, Tx, Tm, OP_S><<<grid, block, 0, l.stream>>>(a); break;
-    case OP_XR: blas_kernel<Ts, Tx, Tm, OP_XR><<<grid, block, 0, l.stream>>>(a); break;
-    case OP_ACCX: blas_kernel<Ts, Tx, Tm, OP_ACCX><<<grid, block, 0, l.stream>>>(a); break;
-    case OP_ZEROX: blas_kernel<Ts, Tx, Tm, OP_ZEROX><<<grid, block, 0, l.stream>>>(a); break;
-    case OP_SETR: blas_kernel<Ts, Tx, Tm, OP_SETR><<<grid, block, 0, l.stream>>>(a); break;
-    case OP_NORM64: blas_kernel<Ts, Tx, Tm, OP_NORM64><<<grid, block, 0, l.stream>>>(a); break;
+    case OP_P: blas_kernel<Ts, Tx, Tm, OP_P, false><<<grid, block, 0, l.stream>>>(a); break;
+    case OP_S: blas_kernel<Ts, Tx, Tm, OP_S, false><<<grid, block, 0, l.stream>>>(a); break;
+    case OP_XR: blas_kernel<Ts, Tx, Tm, OP_XR, false><<<grid, block, 0, l.stream>>>(a); break;
+    case OP_ACCX: blas_kernel<Ts, Tx, Tm, OP_ACCX, true><<<grid, block, 0, l.stream>>>(a); break;
+    case OP_ZEROX: blas_kernel<Ts, Tx, Tm, OP_ZEROX, true><<<grid, block, 0, l.stream>>>(a); break;
+    case OP_SETR: blas_kernel<Ts, Tx, Tm, OP_SETR, true><<<grid, block, 0, l.stream>>>(a); break;
+    case OP_NORM64: blas_kernel<Ts, Tx, Tm, OP_NORM64, true><<<grid, block, 0, l.stream>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   note_launch();
