@@ -56,7 +56,9 @@ DSLASH_TOL = {"f64": 1e-13, "f32": 2e-6, "f16": 4e-3, "bf16": 3e-2}
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
 @pytest.mark.parametrize("dims,bc_t,nrhs", [((2, 2, 2, 2), -1, 1), ((4, 4, 4, 4), -1, 3),
-                                            ((4, 6, 2, 8), 1, 2), ((8, 8, 8, 8), -1, 17)])
+                                            ((4, 6, 2, 8), 1, 2), ((8, 8, 8, 8), -1, 17),
+                                            ((8, 4, 4, 8), -1, 32), ((4, 4, 4, 8), 1, 64),
+                                            ((4, 4, 2, 8), -1, 40)])
 def test_dslash_parity(prec, dims, bc_t, nrhs):
     u = inputs.gauge_field(dims, "haar", seed=1001)
     psi = inputs.random_spinor(dims, 7, nvec=nrhs)
