@@ -460,6 +460,13 @@ def main():
         ratio = hop_traffic_ratio(args.workload)
         if ratio is not None:
             roof["traffic"] = ratio * bytes_per_launch
+        # the second roof of the same kernel: FP32 arithmetic, 1320 flop per (site, system) against
+        # 152 SMs x 128 lanes x 2 flop x 2.07 GHz (at 32 systems and FP16 storage the kernel's
+        # 12.9 flop/B sits on the ridge of the two roofs)
+        alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        alu = 1320.0 * prof["site_systems"] / prof["launches"] / per_launch_s / 1e12
+        roof["second_roof"] = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s",
+                               "frac": alu / alu_peak, "peak_source": "nominal FP32 unit count x max clock"}
 
     pipeline = None
     if not args.no_pipeline and rank == 0:

@@ -185,11 +185,12 @@ int fs_noise_codes(fs_ctx* ctx, uint64_t seed, uint32_t job, uint32_t level, uin
                    uint8_t* codes);
 
 /* Sum over all calls since the last reset of the device time of the hopping (dslash)
- * kernel launches of ctx: number of launches, total milliseconds, and the algorithmic
- * bytes they moved. Timing is recorded only while enabled (CUDA events around each
- * launch on the context's stream). */
+ * kernel launches of ctx: number of launches, total milliseconds, the algorithmic bytes
+ * they moved, and the (site, system) pairs they computed (1320 flop each). Timing is
+ * recorded only while enabled (CUDA events around each launch on the context's stream).
+ * Any output pointer may be NULL. */
 int fs_profile_enable(fs_ctx* ctx, int enable);
-int fs_profile_read(fs_ctx* ctx, long long* launches, double* total_ms, double* bytes);
+int fs_profile_read(fs_ctx* ctx, long long* launches, double* total_ms, double* bytes, double* site_systems);
 
 /* ---- serving ---------------------------------------------------------------------
  * A server on one GPU runs FS-MLMC trace jobs (one mlmc_level_trace each) as they arrive.

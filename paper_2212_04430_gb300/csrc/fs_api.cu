@@ -557,7 +557,7 @@ int fs_profile_enable(fs_ctx* ctx, int enable) {
   return FS_OK;
 }
 
-int fs_profile_read(fs_ctx* ctx, long long* launches, double* total_ms, double* bytes) {
+int fs_profile_read(fs_ctx* ctx, long long* launches, double* total_ms, double* bytes, double* site_systems) {
   if (!ctx) return FS_ERR_ARG;
   Ctx& c = ctx->c;
   if (int rc = set_device(c)) return rc;
@@ -581,6 +581,11 @@ int fs_profile_read(fs_ctx* ctx, long long* launches, double* total_ms, double* 
   if (launches) *launches = c.prof.launches;
   if (total_ms) *total_ms = c.prof.ms;
   if (bytes) *bytes = b;
+  if (site_systems) {
+    double n = 0.0;
+    for (int k = 0; k < 12; k++) n += (double)w[k];
+    *site_systems = n;
+  }
   return FS_OK;
 }
 

@@ -104,7 +104,7 @@ def load_library(path=LIB_PATH):
                                 dp, dp]),
         "fs_noise_codes": (I, [P, U64, U32, U32, U32, ctypes.POINTER(ctypes.c_uint8)]),
         "fs_profile_enable": (I, [P, I]),
-        "fs_profile_read": (I, [P, ctypes.POINTER(ctypes.c_longlong), dp, dp]),
+        "fs_profile_read": (I, [P, ctypes.POINTER(ctypes.c_longlong), dp, dp, dp]),
         "fs_kernel_launches": (ctypes.c_longlong, []),
         "wilson_dslash_noalloc": (I, [ip, I, D, D, P, P, P, I, P]),
         "fs_server_create": (I, [ctypes.POINTER(P), I, ctypes.c_size_t, I]),
@@ -287,8 +287,10 @@ class Context:
         n = ctypes.c_longlong()
         ms = ctypes.c_double()
         by = ctypes.c_double()
-        self._check(self.lib.fs_profile_read(self.h, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
-        return {"launches": n.value, "ms": ms.value, "bytes": by.value}
+        ss = ctypes.c_double()
+        self._check(self.lib.fs_profile_read(self.h, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by),
+                                             ctypes.byref(ss)))
+        return {"launches": n.value, "ms": ms.value, "bytes": by.value, "site_systems": ss.value}
 
 
 def fs_kernel_launches():
