@@ -846,8 +846,10 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
         }
         __syncwarp();
       }
+      // every lane computes (no per-lane branches); a lane whose system sits out reads a
+      // stale ring slot, and its results are neither stored nor summed
       Tm psi[24], u[18];
-      if (sel) {
+      {
         const int slot = slot_of(j, d);
 #pragma unroll
         for (int c = 0; c < CV; c++) fetch_chunk(slot, c, psi + c * VW);
@@ -870,17 +872,15 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
         case 6: issue_ahead(IntC<6>{}, j); break;
         default: issue_ahead(IntC<7>{}, j); break;
       }
-      if (sel) {
-        switch (d) {
-          case 0: hop_dir<0, -1, false>(acc, psi, u, (Tm)1); break;
-          case 1: hop_dir<0, +1, true>(acc, psi, u, (Tm)1); break;
-          case 2: hop_dir<1, -1, false>(acc, psi, u, (Tm)1); break;
-          case 3: hop_dir<1, +1, true>(acc, psi, u, (Tm)1); break;
-          case 4: hop_dir<2, -1, false>(acc, psi, u, (Tm)1); break;
-          case 5: hop_dir<2, +1, true>(acc, psi, u, (Tm)1); break;
-          case 6: hop_dir<3, -1, false>(acc, psi, u, (Tm)1); break;
-          default: hop_dir<3, +1, true>(acc, psi, u, (Tm)1); break;
-        }
+      switch (d) {
+        case 0: hop_dir<0, -1, false>(acc, psi, u, (Tm)1); break;
+        case 1: hop_dir<0, +1, true>(acc, psi, u, (Tm)1); break;
+        case 2: hop_dir<1, -1, false>(acc, psi, u, (Tm)1); break;
+        case 3: hop_dir<1, +1, true>(acc, psi, u, (Tm)1); break;
+        case 4: hop_dir<2, -1, false>(acc, psi, u, (Tm)1); break;
+        case 5: hop_dir<2, +1, true>(acc, psi, u, (Tm)1); break;
+        case 6: hop_dir<3, -1, false>(acc, psi, u, (Tm)1); break;
+        default: hop_dir<3, +1, true>(acc, psi, u, (Tm)1); break;
       }
     }
     double dv[KK];
@@ -890,7 +890,7 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
       // out = ca X + cb (H in), in place of acc, one 16-byte chunk of X at a time
       cp_async_wait<PF - 1>();
       Tm sr = 0, si = 0, tt = 0;
-      if (sel) {
+      {
         const int slot = slot_of(j, 8);
 #pragma unroll
         for (int c = 0; c < CV; c++) {
@@ -908,12 +908,14 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
         }
       }
       issue_ahead(IntC<8>{}, j);
-      if constexpr (DOT == DOT_TS) { dv[0] = (double)sr; dv[1] = (double)si; dv[2] = (double)tt; }
+      if constexpr (DOT == DOT_TS) {
+        dv[0] = sel ? (double)sr : 0.0; dv[1] = sel ? (double)si : 0.0; dv[2] = sel ? (double)tt : 0.0;
+      }
     }
     if constexpr (HAS_R) {
       cp_async_wait<PF - 1>();
       Tm sr = 0, si = 0;
-      if (sel) {
+      {
         const int slot = slot_of(j, NITEM - 1);
 #pragma unroll
         for (int c = 0; c < CV; c++) {
@@ -924,7 +926,7 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
         }
       }
       issue_ahead(IntC<NITEM - 1>{}, j);
-      dv[0] = (double)sr; dv[1] = (double)si;
+      dv[0] = sel ? (double)sr : 0.0; dv[1] = sel ? (double)si : 0.0;
     }
     if (sel) make_field<Ts>(a.out, g.Vh, sh.N).store(site, sys, acc);
     if constexpr (K > 0) {
