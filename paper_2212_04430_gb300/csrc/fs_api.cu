@@ -130,6 +130,7 @@ void fs_ctx_destroy(fs_ctx* ctx) {
   cudaStreamSynchronize(c.stream);
   c.tiles.clear();
   if (c.gauge64) cudaFree(c.gauge64);
+  if (c.wline) cudaFree(c.wline);
   for (auto& kv : c.gauge_lo) cudaFree(kv.second);
   if (c.canon_d) cudaFree(c.canon_d);
   if (c.canon_h) cudaFreeHost(c.canon_h);
@@ -168,6 +169,7 @@ int fs_set_gauge(fs_ctx* ctx, const double* U) {
     return r;
   };
   const size_t nl = (size_t)8 * c.g.Vh;
+  c.wline_mask = 0;  // the contraction's path products belong to the old field
   if (!e) e = need(c.gauge64, nl * 18 * sizeof(double));
   if (!e) e = fs::launch_gauge_pack<double>(c.gauge64, stage, c.g, 18, c.stream);
   struct LoCopy { int prec, nr; size_t bytes; };

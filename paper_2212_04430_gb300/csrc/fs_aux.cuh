@@ -139,8 +139,10 @@ __global__ void gauge_pack_kernel(void* out, const double* canon, Geom g) {
 }
 
 // ---- contraction: c_p = sum_x L(x)^dag Gamma W(x, x + p z) R(x + p z) ----------
-// Walked from the right vector's site x': psi_0 = R(x'), psi_{q+1} = U_z(x' - (q+1) z) psi_q,
-// so psi_q = W(x' - q z, x') R(x') and c_q += L(x' - q z)^dag Gamma psi_q.
+// The straight path products W(x, x + q z) = U_z(x) U_z(x + z) ... U_z(x + (q-1) z) depend on
+// the gauge field alone, so they are built once (transport_kernel) and every contraction
+// applies one FP64 SU(3) product per spin and displacement: psi = W(x, x + q z) R(x + q z),
+// c_q += L(x)^dag Gamma psi.
 struct ContractPair {
   int right;      // slot holding the right vector (solution)
   int left;       // slot of the left vector
@@ -151,7 +153,7 @@ struct ContractPair {
 struct ContractArgs {
   const double* x_e;
   const double* x_o;
-  const double* gauge64;  // FP64 links, 18 reals per link
+  const double* wline;    // W(x, x + q z) for the requested q > 0: [k][18][2 Vh], k counts them
   const NoiseSpec* spec;
   const ContractPair* pairs;
   double* partial;        // [npairs][np][2][nblk]
@@ -170,6 +172,53 @@ struct ContractArgs {
 constexpr int CONTRACT_MAXP = 16;
 
 #ifdef FS_ENGINE_KERNELS
+// W(x, x + q z) for every site x (thread fs = parity * Vh + checkerboard index) and every q with
+// bit q of qmask set (q >= 1), stored as w[k][r][fs], k counting the set bits in increasing q.
+__global__ void __launch_bounds__(256) transport_kernel(double* w, const double* gauge64, Geom g, int qmask,
+                                                        int qmax) {
+  const int fs = blockIdx.x * blockDim.x + threadIdx.x;
+  if (fs >= 2 * g.Vh) return;
+  const int par = fs >= g.Vh ? 1 : 0;
+  const int site = fs - par * g.Vh;
+  int x[4];
+  cb_coords(g, par, site, x);
+  const size_t stride = (size_t)2 * g.Vh;
+  double W[18];
+#pragma unroll
+  for (int r = 0; r < 18; r++) W[r] = (r == 0 || r == 8 || r == 16) ? 1.0 : 0.0;
+  int k = 0;
+  for (int q = 1; q <= qmax; q++) {
+    int v[4] = {x[0], x[1], x[2], x[3]};
+    v[2] = (x[2] + q - 1) % g.L[2];
+    const int vpar = (v[0] + v[1] + v[2] + v[3]) & 1;
+    const double* lk = gauge64 + ((size_t)(vpar * 4 + 2) * g.Vh + cb_index(g, v)) * 18;
+    double nw[18];
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      // column j of W U = W times column j of U
+      double col[6], out[6];
+#pragma unroll
+      for (int i = 0; i < 3; i++) {
+        col[2 * i] = lk[(i * 3 + j) * 2];
+        col[2 * i + 1] = lk[(i * 3 + j) * 2 + 1];
+      }
+      su3_mul<false, double>(W, col, out);
+#pragma unroll
+      for (int i = 0; i < 3; i++) {
+        nw[(i * 3 + j) * 2] = out[2 * i];
+        nw[(i * 3 + j) * 2 + 1] = out[2 * i + 1];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 18; r++) W[r] = nw[r];
+    if ((qmask >> q) & 1) {
+#pragma unroll
+      for (int r = 0; r < 18; r++) w[((size_t)k * 18 + r) * stride + fs] = W[r];
+      k++;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) contract_kernel(ContractArgs a) {
   __shared__ double sm[256 * 2];
   const ContractPair pr = a.pairs[blockIdx.y];
@@ -183,78 +232,74 @@ __global__ void __launch_bounds__(256) contract_kernel(ContractArgs a) {
     const int site = fs - par * g.Vh;
     int x[4];
     cb_coords(g, par, site, x);
-    double psi[24];
-    make_field<double>(const_cast<double*>(par ? a.x_o : a.x_e), g.Vh, a.N, true).load(site, pr.right, psi);
-    int qi = 0;
+    double lv[24];
+    if (pr.left_kind == 0) {
+      z4_site(a.spec[pr.left], lex_index(g, x), lv);
+    } else {
+      make_field<double>(const_cast<double*>(par ? a.x_o : a.x_e), g.Vh, a.N, true).load(site, pr.left, lv);
+#pragma unroll
+      for (int k = 12; k < 24; k++) lv[k] = -lv[k];
+    }
+    const size_t stride = (size_t)2 * g.Vh;
+    int qi = 0, k = 0;
     for (int q = 0; q <= a.pmax; q++) {
+      if (!((a.pmask >> q) & 1)) continue;
       int y[4] = {x[0], x[1], x[2], x[3]};
-      y[2] = ((x[2] - q) % g.L[2] + g.L[2]) % g.L[2];
-      if ((a.pmask >> q) & 1) {
-        double lv[24];
-        const int ypar = (y[0] + y[1] + y[2] + y[3]) & 1;
-        if (pr.left_kind == 0) {
-          z4_site(a.spec[pr.left], lex_index(g, y), lv);
-        } else {
-          make_field<double>(const_cast<double*>(ypar ? a.x_o : a.x_e), g.Vh, a.N, true)
-              .load(cb_index(g, y), pr.left, lv);
-#pragma unroll
-          for (int k = 12; k < 24; k++) lv[k] = -lv[k];
-        }
-        // L^dag Gamma psi
-        double cr = 0, ci = 0;
-        if (a.gmono) {
-          // every Clifford product is a signed / phased permutation in this basis
-#pragma unroll
-          for (int s = 0; s < 4; s++) {
-            const int t = a.gperm[s], k = a.gphase[s];
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-              const double pr_ = psi[t * 6 + c * 2], pi_ = psi[t * 6 + c * 2 + 1];
-              const double gr = k == 0 ? pr_ : (k == 1 ? -pi_ : (k == 2 ? -pr_ : pi_));
-              const double gi = k == 0 ? pi_ : (k == 1 ? pr_ : (k == 2 ? -pi_ : -pr_));
-              const double lr = lv[s * 6 + c * 2], li = lv[s * 6 + c * 2 + 1];
-              cr += lr * gr + li * gi;
-              ci += lr * gi - li * gr;
-            }
-          }
-        } else {
-#pragma unroll
-          for (int s = 0; s < 4; s++) {
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-              double gr = 0, gi = 0;
-#pragma unroll
-              for (int t = 0; t < 4; t++) {
-                const double Gr = a.gamma[(s * 4 + t) * 2], Gi = a.gamma[(s * 4 + t) * 2 + 1];
-                const double pr_ = psi[t * 6 + c * 2], pi_ = psi[t * 6 + c * 2 + 1];
-                gr += Gr * pr_ - Gi * pi_;
-                gi += Gr * pi_ + Gi * pr_;
-              }
-              const double lr = lv[s * 6 + c * 2], li = lv[s * 6 + c * 2 + 1];
-              cr += lr * gr + li * gi;
-              ci += lr * gi - li * gr;
-            }
-          }
-        }
-        acc[qi][0] = cr;
-        acc[qi][1] = ci;
-        qi++;
-      }
-      if (q < a.pmax) {
-        // psi <- U_z(x - (q+1) z) psi
-        int w[4] = {x[0], x[1], x[2], x[3]};
-        w[2] = ((x[2] - q - 1) % g.L[2] + g.L[2]) % g.L[2];
-        const int wpar = (w[0] + w[1] + w[2] + w[3]) & 1;
-        const double* lk = a.gauge64 + ((size_t)(wpar * 4 + 2) * g.Vh + cb_index(g, w)) * 18;
+      y[2] = (x[2] + q) % g.L[2];
+      const int ypar = (y[0] + y[1] + y[2] + y[3]) & 1;
+      double psi[24];
+      make_field<double>(const_cast<double*>(ypar ? a.x_o : a.x_e), g.Vh, a.N, true)
+          .load(cb_index(g, y), pr.right, psi);
+      if (q > 0) {
         double u[18];
 #pragma unroll
-        for (int k = 0; k < 18; k++) u[k] = lk[k];
-        double np_[24];
+        for (int r = 0; r < 18; r++) u[r] = a.wline[((size_t)k * 18 + r) * stride + fs];
+        double t[24];
 #pragma unroll
-        for (int s = 0; s < 4; s++) su3_mul<false, double>(u, psi + s * 6, np_ + s * 6);
+        for (int s = 0; s < 4; s++) su3_mul<false, double>(u, psi + s * 6, t + s * 6);
 #pragma unroll
-        for (int k = 0; k < 24; k++) psi[k] = np_[k];
+        for (int r = 0; r < 24; r++) psi[r] = t[r];
+        k++;
       }
+      // L^dag Gamma psi
+      double cr = 0, ci = 0;
+      if (a.gmono) {
+        // every Clifford product is a signed / phased permutation in this basis
+#pragma unroll
+        for (int s = 0; s < 4; s++) {
+          const int t = a.gperm[s], ph = a.gphase[s];
+#pragma unroll
+          for (int c = 0; c < 3; c++) {
+            const double pr_ = psi[t * 6 + c * 2], pi_ = psi[t * 6 + c * 2 + 1];
+            const double gr = ph == 0 ? pr_ : (ph == 1 ? -pi_ : (ph == 2 ? -pr_ : pi_));
+            const double gi = ph == 0 ? pi_ : (ph == 1 ? pr_ : (ph == 2 ? -pi_ : -pr_));
+            const double lr = lv[s * 6 + c * 2], li = lv[s * 6 + c * 2 + 1];
+            cr += lr * gr + li * gi;
+            ci += lr * gi - li * gr;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int s = 0; s < 4; s++) {
+#pragma unroll
+          for (int c = 0; c < 3; c++) {
+            double gr = 0, gi = 0;
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+              const double Gr = a.gamma[(s * 4 + t) * 2], Gi = a.gamma[(s * 4 + t) * 2 + 1];
+              const double pr_ = psi[t * 6 + c * 2], pi_ = psi[t * 6 + c * 2 + 1];
+              gr += Gr * pr_ - Gi * pi_;
+              gi += Gr * pi_ + Gi * pr_;
+            }
+            const double lr = lv[s * 6 + c * 2], li = lv[s * 6 + c * 2 + 1];
+            cr += lr * gr + li * gi;
+            ci += lr * gi - li * gr;
+          }
+        }
+      }
+      acc[qi][0] = cr;
+      acc[qi][1] = ci;
+      qi++;
     }
   }
   // fixed-shape block reduction per requested displacement

@@ -500,7 +500,30 @@ int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, c
   // results come back in increasing p; callers pass plist sorted
   for (int k = 1; k < np; k++)
     if (plist[k] <= plist[k - 1]) return c->fail(1, "displacements must be increasing");
-  a.x_e = T->x_hi; a.x_o = T->x_o; a.gauge64 = (const double*)c->gauge64; a.spec = T->spec_d;
+  cudaError_t e;
+  const int wmask = pmask & ~1;
+  if (wmask && c->wline_mask != wmask) {
+    // the path products depend on the gauge field and the displacements only: built once
+    const size_t need_w = (size_t)__builtin_popcount(wmask) * 18 * 2 * c->g.Vh * sizeof(double);
+    if (need_w > c->wline_cap) {
+      if (c->wline) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->wline);
+        c->extra_bytes -= c->wline_cap;
+        c->wline = nullptr;
+        c->wline_cap = 0;
+      }
+      if ((e = cudaMalloc((void**)&c->wline, need_w))) return c->cuda_fail(e, "contraction path products");
+      c->wline_cap = need_w;
+      c->extra_bytes += need_w;
+    }
+    transport_kernel<<<(2 * c->g.Vh + 255) / 256, 256, 0, c->stream>>>(c->wline, (const double*)c->gauge64, c->g,
+                                                                      wmask, pmax);
+    note_launch();
+    if ((e = cudaGetLastError())) return c->cuda_fail(e, "contraction path products");
+    c->wline_mask = wmask;
+  }
+  a.x_e = T->x_hi; a.x_o = T->x_o; a.wline = c->wline; a.spec = T->spec_d;
   for (int k = 0; k < 32; k++) a.gamma[k] = gamma[k];
   // detect a monomial Gamma (one entry per row, each +-1 or +-i): applied as a permutation
   a.gmono = 1;
@@ -526,7 +549,6 @@ int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, c
   const size_t res_n = (size_t)rows * np * 2;
   const size_t need = part_n * sizeof(double) + res_n * sizeof(double) + npairs * sizeof(ContractPair) + 256;
   char* buf = nullptr;
-  cudaError_t e;
   if ((e = cudaMallocAsync((void**)&buf, need, c->stream))) return c->cuda_fail(e, "contraction buffers");
   double* part = (double*)buf;
   double* res = part + part_n;

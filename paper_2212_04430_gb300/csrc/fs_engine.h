@@ -100,6 +100,9 @@ struct Ctx {
   bool have_gauge = false;
   void* gauge64 = nullptr;              // [2][4][Vh][18] doubles
   std::map<int, void*> gauge_lo;        // key: prec * 100 + nr
+  double* wline = nullptr;              // straight z-paths W(x, x + q z) of the contraction
+  size_t wline_cap = 0;                 // bytes allocated
+  int wline_mask = 0;                   // the q > 0 they hold (bit q); 0: none or stale
   std::map<long long, std::unique_ptr<TileBase>> tiles;
   double* canon_d = nullptr;            // staging for canonical vectors
   size_t canon_cap = 0;                 // in vectors
