@@ -7,6 +7,12 @@
 // into x_hi (FP64) + x_lo / scale (Tx). A reliable update folds x_lo into x_hi,
 // recomputes r_hi = bhat - M x_hi entirely in FP64 and restarts the sloppy
 // residual from it (the search direction p is kept).
+//
+// One BiCGStab iteration is: v = M p, alpha; s = r - alpha v; t = M s together
+// with <t, s>, ||t||^2, ||s||^2, <rhat, s>, <rhat, t>; then omega = <t, s> / ||t||^2
+// and, by linearity of r = s - omega t, rho' = <rhat, s> - omega <rhat, t> and
+// ||r||^2 = ||s||^2 - 2 Re(conj(omega) <t, s>) + |omega|^2 ||t||^2, so beta is known
+// before r exists and one pass updates x, r and p together.
 #pragma once
 
 #include "fs_hop.cuh"
@@ -14,12 +20,12 @@
 namespace fs {
 
 enum BlasOp {
-  OP_P = 0,       // p = r + beta (p - omega v)
   OP_S = 1,       // s = r - alpha v
-  OP_XR = 2,      // x_lo += alpha p + omega s ; r = s - omega t ; <rhat, r>, ||r||^2
+  OP_XRP = 2,     // x_lo += alpha p + omega s ; r = s - omega t ; p = r + beta (p - omega v)
   OP_ACCX = 3,    // x_hi += x_lo / scale ; x_lo = 0
   OP_ZEROX = 4,   // x_hi = 0 ; x_lo = 0
-  OP_SETR = 5,    // r = scale * src ; on restart/init rhat = r, p = v = 0 ; <rhat, r>, ||r||^2
+  OP_SETR = 5,    // r = scale * src ; on restart/init rhat = p = r, v = 0, else p rescaled ;
+                  // <rhat, r>, ||r||^2
   OP_NORM64 = 6,  // ||src||^2 of an FP64 field
 };
 
@@ -56,7 +62,7 @@ __device__ __forceinline__ void cmul_acc(Tm (&o)[24], const Tm (&a)[24], Tm cr, 
 template <typename Ts, typename Tx, typename Tm, int OP, bool WL>
 __global__ void __launch_bounds__(256) blas_kernel(BlasArgs a) {
   if (a.gate != nullptr && *a.gate == 0) return;
-  constexpr int K = (OP == OP_XR || OP == OP_SETR) ? 3 : (OP == OP_NORM64 ? 1 : 0);
+  constexpr int K = OP == OP_SETR ? 3 : (OP == OP_NORM64 ? 1 : 0);
   __shared__ double smem[256 * (K > 0 ? K : 1)];
   const Shape sh = a.sh;
   const int Vh = a.Vh;
@@ -75,16 +81,15 @@ __global__ void __launch_bounds__(256) blas_kernel(BlasArgs a) {
 
   // one chunk of sites for system `sys` (sel: the system takes part), block rows sys_base..
   auto chunk_body = [&](const int sys, const int chunk, const bool sel, const int sys_base) {
-    Tm c0r = 0, c0i = 0, c1r = 0, c1i = 0;
+    Tm c0r = 0, c0i = 0, c1r = 0, c1i = 0, c2r = 0, c2i = 0;
     bool reset = false;
     if (sel) {
       const SysState& st = a.st[sys];
-      if (OP == OP_P) { c0r = coef<Tm>(st, C_BETA); c0i = coef<Tm>(st, C_BETA + 1);
-                        c1r = coef<Tm>(st, C_OMEGA); c1i = coef<Tm>(st, C_OMEGA + 1); }
       if (OP == OP_S) { c0r = coef<Tm>(st, C_ALPHA); c0i = coef<Tm>(st, C_ALPHA + 1); }
-      if (OP == OP_XR) { c0r = coef<Tm>(st, C_ALPHA); c0i = coef<Tm>(st, C_ALPHA + 1);
-                         c1r = coef<Tm>(st, C_OMEGA); c1i = coef<Tm>(st, C_OMEGA + 1); }
-      if (OP == OP_SETR) reset = (st.flags & (FLAG_RESTART | FLAG_INIT)) != 0;
+      if (OP == OP_XRP) { c0r = coef<Tm>(st, C_ALPHA); c0i = coef<Tm>(st, C_ALPHA + 1);
+                          c1r = coef<Tm>(st, C_OMEGA); c1i = coef<Tm>(st, C_OMEGA + 1);
+                          c2r = coef<Tm>(st, C_BETA); c2i = coef<Tm>(st, C_BETA + 1); }
+      if (OP == OP_SETR) { reset = (st.flags & (FLAG_RESTART | FLAG_INIT)) != 0; c0r = coef<Tm>(st, C_RATIO); }
     }
     const int site = chunk * sh.SB + lsite;
     const bool act = sel && site < Vh;
@@ -92,40 +97,25 @@ __global__ void __launch_bounds__(256) blas_kernel(BlasArgs a) {
 #pragma unroll
     for (int k = 0; k < (K > 0 ? K : 1); k++) dv[k] = 0.0;
     if (act) {
-      if constexpr (OP == OP_P) {
-        Tm rv[24], pv[24], vv[24];
-        r.load(site, sys, rv); p.load(site, sys, pv); v.load(site, sys, vv);
-        Tm w[24];
-#pragma unroll
-        for (int k = 0; k < 24; k++) w[k] = pv[k];
-        cmul_acc(w, vv, -c1r, -c1i);  // p - omega v
-        Tm o[24];
-#pragma unroll
-        for (int k = 0; k < 24; k++) o[k] = rv[k];
-        cmul_acc(o, w, c0r, c0i);
-        p.store(site, sys, o);
-      } else if constexpr (OP == OP_S) {
+      if constexpr (OP == OP_S) {
         Tm rv[24], vv[24];
         r.load(site, sys, rv); v.load(site, sys, vv);
         cmul_acc(rv, vv, -c0r, -c0i);
         s.store(site, sys, rv);
-      } else if constexpr (OP == OP_XR) {
-        Tm xv[24], pv[24], sv[24], tv[24], hv[24];
+      } else if constexpr (OP == OP_XRP) {
+        Tm xv[24], pv[24], sv[24], tv[24], vv[24];
         xl.load(site, sys, xv); p.load(site, sys, pv); s.load(site, sys, sv);
-        t.load(site, sys, tv); rh.load(site, sys, hv);
+        t.load(site, sys, tv); v.load(site, sys, vv);
         cmul_acc(xv, pv, c0r, c0i);
         cmul_acc(xv, sv, c1r, c1i);
         xl.store(site, sys, xv);
         cmul_acc(sv, tv, -c1r, -c1i);  // r = s - omega t
         r.store(site, sys, sv);
-        Tm dr = 0, di = 0, nn = 0;
-#pragma unroll
-        for (int k = 0; k < 24; k += 2) {
-          dr += hv[k] * sv[k] + hv[k + 1] * sv[k + 1];
-          di += hv[k] * sv[k + 1] - hv[k + 1] * sv[k];
-          nn += sv[k] * sv[k] + sv[k + 1] * sv[k + 1];
-        }
-        dv[0] = (double)dr; dv[1] = (double)di; dv[2] = (double)nn;
+        Tm rv[24];
+        r.load(site, sys, rv);         // the stored (rounded) r, as the next iteration sees it
+        cmul_acc(pv, vv, -c1r, -c1i);  // p - omega v
+        cmul_acc(rv, pv, c2r, c2i);    // r + beta (p - omega v)
+        p.store(site, sys, rv);
       } else if constexpr (OP == OP_ACCX) {
         // on a breakdown the sloppy correction is discarded, never folded into x_hi
         const bool keep = !(a.st[sys].flags & FLAG_RESTART);
@@ -144,6 +134,8 @@ __global__ void __launch_bounds__(256) blas_kernel(BlasArgs a) {
         const double sc = a.st[sys].cd[C_SCALE];
         double sv[24];
         src.load(site, sys, sv);
+        Tm iv[24];
+        if (!reset) r.load(site, sys, iv);  // the iterated residual, replaced below
         Tm o[24];
 #pragma unroll
         for (int k = 0; k < 24; k++) o[k] = (Tm)(sc * sv[k]);
@@ -153,16 +145,24 @@ __global__ void __launch_bounds__(256) blas_kernel(BlasArgs a) {
         r.load(site, sys, ov);
         Tm hv[24];
         if (reset) {
+          // fresh start: rhat = p = r (the first direction), v = 0
           rh.store(site, sys, o);
+          p.store(site, sys, o);
 #pragma unroll
           for (int k = 0; k < 24; k++) hv[k] = ov[k];
           Tm z[24];
 #pragma unroll
           for (int k = 0; k < 24; k++) z[k] = 0;
-          p.store(site, sys, z);
           v.store(site, sys, z);
         } else {
+          // p was formed from the iterated residual r_it in the old scale:
+          // p' = ratio (p - r_it) + r' keeps the direction, rescaled, around the new r'
           rh.load(site, sys, hv);
+          Tm pv[24];
+          p.load(site, sys, pv);
+#pragma unroll
+          for (int k = 0; k < 24; k++) pv[k] = fmadd(c0r, pv[k] - iv[k], ov[k]);
+          p.store(site, sys, pv);
         }
         Tm dr = 0, di = 0, nn = 0;
 #pragma unroll
@@ -286,15 +286,16 @@ __global__ void __launch_bounds__(256) cg_kernel(CgArgs a) {
 }
 
 // ---- finalize: one block per system sums its group partials in fixed order ----
-enum FinOp { FIN_ALPHA = 0, FIN_OMEGA = 1, FIN_RHO = 2, FIN_TRUE = 3, FIN_UPDATE = 4, FIN_INIT = 5,
+enum FinOp { FIN_ALPHA = 0, FIN_OMEGA = 1, FIN_TRUE = 3, FIN_UPDATE = 4, FIN_INIT = 5,
              FIN_NORM = 6, FIN_VERIFY = 7, FIN_CG_INIT = 8, FIN_CG_ALPHA = 9, FIN_CG_BETA = 10,
              FIN_CG_TRUE = 11 };
 
 constexpr int FIN_SPLIT = 8;  // blocks per system in a finalize
+constexpr int FIN_MAXV = 8;   // summed values per system, at most
 
 struct FinArgs {
   SysState* st;
-  double* slice;     // [N][FIN_SPLIT][3] slice sums
+  double* slice;     // [N][FIN_SPLIT][FIN_MAXV] slice sums
   unsigned* count;   // [N] arrival tickets, zero between finalizes
   const double* pa;  // partials [N][K][ngroups]
   const double* pb;
@@ -332,11 +333,21 @@ __device__ __forceinline__ void set_beta(SysState& s) {
   set_coef(s, C_BETA + 1, q1r * q2i + q1i * q2r);
 }
 
+// Values a finalize op sums per system (all its sources together).
+__host__ __device__ constexpr int fin_values(int op) {
+  return op == FIN_ALPHA ? 2
+       : op == FIN_OMEGA ? 8
+       : (op == FIN_UPDATE || op == FIN_INIT || op == FIN_NORM) ? 3
+       : (op == FIN_VERIFY || op == FIN_CG_INIT || op == FIN_CG_BETA) ? 2
+       : 1;
+}
+
 // Operands summed by each finalize op, in the order its logic consumes them.
 __device__ __forceinline__ int fin_sources(int op, const FinArgs& a, const double* (&p)[3], int (&k)[3]) {
   switch (op) {
     case FIN_ALPHA: p[0] = a.pa; k[0] = 2; return 1;
-    case FIN_OMEGA: case FIN_RHO: case FIN_UPDATE: case FIN_INIT: p[0] = a.pa; k[0] = 3; return 1;
+    case FIN_OMEGA: p[0] = a.pa; k[0] = 8; return 1;
+    case FIN_UPDATE: case FIN_INIT: p[0] = a.pa; k[0] = 3; return 1;
     case FIN_NORM: p[0] = a.pa; p[1] = a.pb; p[2] = a.pc; k[0] = k[1] = k[2] = 1; return 3;
     case FIN_VERIFY: case FIN_CG_INIT: case FIN_CG_BETA: p[0] = a.pa; p[1] = a.pb; k[0] = k[1] = 1; return 2;
     default: p[0] = a.pa; k[0] = 1; return 1;  // FIN_TRUE, FIN_CG_ALPHA, FIN_CG_TRUE
@@ -369,32 +380,35 @@ __device__ __forceinline__ void fin_logic(const FinArgs& a, int op, SysState& s,
       set_coef(s, C_ALPHA, ar); set_coef(s, C_ALPHA + 1, ai);
     }
   } else if (op == FIN_OMEGA) {
-    double v[3];
-    take<3>(v, tot, off);
+    // v = <t, s>, ||t||^2, ||s||^2, <rhat, s>, <rhat, t>
+    double v[8];
+    take<8>(v, tot, off);
     if (threadIdx.x == 0) {
       double wr = 0, wi = 0;
       if (v[2] > 0.0 && isfinite(v[2])) { wr = v[0] / v[2]; wi = v[1] / v[2]; }
       else s.flags |= FLAG_UPDATE | FLAG_RESTART;
-      if ((s.flags & FLAG_RESTART) && a.gate) atomicExch(a.gate, 1);
       s.omega[0] = wr; s.omega[1] = wi;
       set_coef(s, C_OMEGA, wr); set_coef(s, C_OMEGA + 1, wi);
-    }
-  } else if (op == FIN_RHO) {
-    double v[3];
-    take<3>(v, tot, off);
-    if (threadIdx.x == 0) {
-      s.iters += 1;
-      s.rho_old[0] = s.rho[0]; s.rho_old[1] = s.rho[1];
-      s.rho[0] = v[0]; s.rho[1] = v[1];
-      s.r2 = v[2];
-      set_beta(s);
-      const double isc = s.cd[C_INVSCALE];
-      const double r2hi = v[2] * isc * isc;
-      if (!isfinite(v[2]) || !isfinite(v[0]) || !isfinite(v[1])) s.flags |= FLAG_UPDATE | FLAG_RESTART;
-      if (r2hi <= s.tol2) s.flags |= FLAG_UPDATE;
-      if (v[2] < s.delta2 * s.r2_max) s.flags |= FLAG_UPDATE;
-      if (s.iters >= s.max_iter) s.flags |= FLAG_UPDATE | FLAG_FINAL;
-      if (v[2] > s.r2_max) s.r2_max = v[2];
+      if (!(s.flags & FLAG_RESTART)) {
+        // r = s - omega t: rho' = <rhat, s> - omega <rhat, t>,
+        // ||r||^2 = ||s||^2 - 2 Re(conj(omega) <t, s>) + |omega|^2 ||t||^2
+        s.iters += 1;
+        s.rho_old[0] = s.rho[0]; s.rho_old[1] = s.rho[1];
+        s.rho[0] = v[4] - (wr * v[6] - wi * v[7]);
+        s.rho[1] = v[5] - (wr * v[7] + wi * v[6]);
+        const double r2 = v[3] - 2.0 * (wr * v[0] + wi * v[1]) + (wr * wr + wi * wi) * v[2];
+        s.r2 = r2 > 0.0 ? r2 : 0.0;
+        set_beta(s);
+        const double isc = s.cd[C_INVSCALE];
+        const double r2hi = s.r2 * isc * isc;
+        if (!isfinite(r2) || !isfinite(s.rho[0]) || !isfinite(s.rho[1])) s.flags |= FLAG_UPDATE | FLAG_RESTART;
+        // below this the recurrence for ||r||^2 has lost most of its digits: ask FP64
+        if (!(r2 > 1e-5 * v[3])) s.flags |= FLAG_UPDATE;
+        if (r2hi <= s.tol2) s.flags |= FLAG_UPDATE;
+        if (s.r2 < s.delta2 * s.r2_max) s.flags |= FLAG_UPDATE;
+        if (s.iters >= s.max_iter) s.flags |= FLAG_UPDATE | FLAG_FINAL;
+        if (s.r2 > s.r2_max) s.r2_max = s.r2;
+      }
       if ((s.flags & FLAG_UPDATE) && a.gate) atomicExch(a.gate, 1);
     }
   } else if (op == FIN_TRUE) {
@@ -412,6 +426,7 @@ __device__ __forceinline__ void fin_logic(const FinArgs& a, int op, SysState& s,
         s.flags = 0;
       } else {
         const double sc = a.target * sqrt(a.nreal / v[0]);
+        set_coef(s, C_RATIO, sc * s.cd[C_INVSCALE]);
         set_coef(s, C_SCALE, sc);
         set_coef(s, C_INVSCALE, 1.0 / sc);
       }
@@ -430,9 +445,8 @@ __device__ __forceinline__ void fin_logic(const FinArgs& a, int op, SysState& s,
         s.omega[0] = 1.0; s.omega[1] = 0.0;
         set_coef(s, C_BETA, 0.0); set_coef(s, C_BETA + 1, 0.0);
         set_coef(s, C_OMEGA, 1.0); set_coef(s, C_OMEGA + 1, 0.0);
-      } else {
-        set_beta(s);
       }
+      // (beta of the next iteration comes from FIN_OMEGA; p was rescaled by OP_SETR)
       s.flags = 0;
     }
   } else if (op == FIN_NORM) {
@@ -523,9 +537,10 @@ __device__ __forceinline__ void fin_logic(const FinArgs& a, int op, SysState& s,
 // (fixed slices, fixed in-slice tree) into a.slice; the last block of the system to
 // finish (an atomic ticket; no block ever waits) adds the FIN_SPLIT slice sums in slice
 // order and runs the scalar step. The result depends only on the partials, not on
-// which block finishes last.
+// which block finishes last. NV = fin_values(op).
+template <int NV>
 __global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
-  __shared__ double sm[256 * 3];
+  __shared__ double sm[256 * NV];
   __shared__ unsigned ticket;
   const int sys = blockIdx.x, y = blockIdx.y;
   if (op == FIN_UPDATE && sys == 0 && y == 0 && threadIdx.x == 0 && a.gate) {
@@ -534,32 +549,35 @@ __global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
   }
   if (sys >= a.N || !selected(a.st, sys, a.mask)) return;
   const double* src[3];
-  int kk[3];
-  const int nsrc = fin_sources(op, a, src, kk);
+  int kk[3] = {0, 0, 0};
+  fin_sources(op, a, src, kk);
   const int g0 = (int)((long long)a.ngroups * y / FIN_SPLIT), g1 = (int)((long long)a.ngroups * (y + 1) / FIN_SPLIT);
-  double acc[3] = {0.0, 0.0, 0.0};
-  int nv = 0;
-  for (int q = 0; q < nsrc; q++) {
-    for (int k = 0; k < kk[q]; k++, nv++) {
-      const double* base = src[q] + ((size_t)sys * kk[q] + k) * a.ngroups;
-      double t = 0.0;
-      for (int g = g0 + (int)threadIdx.x; g < g1; g += blockDim.x) t += base[g];
-      acc[nv] = t;
-    }
+  double acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    // value v: entry kidx of source q (sources in order, kk[q] entries each)
+    int q = 0, kidx = v;
+    if (kidx >= kk[0]) { kidx -= kk[0]; q = 1; if (kidx >= kk[1]) { kidx -= kk[1]; q = 2; } }
+    const double* sp = q == 0 ? src[0] : (q == 1 ? src[1] : src[2]);
+    const int kq = q == 0 ? kk[0] : (q == 1 ? kk[1] : kk[2]);
+    const double* base = sp + ((size_t)sys * kq + kidx) * a.ngroups;
+    double t = 0.0;
+    for (int g = g0 + (int)threadIdx.x; g < g1; g += blockDim.x) t += base[g];
+    acc[v] = t;
   }
 #pragma unroll
-  for (int v = 0; v < 3; v++) sm[threadIdx.x * 3 + v] = acc[v];
+  for (int v = 0; v < NV; v++) sm[threadIdx.x * NV + v] = acc[v];
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) {
 #pragma unroll
-      for (int v = 0; v < 3; v++) sm[threadIdx.x * 3 + v] += sm[(threadIdx.x + w) * 3 + v];
+      for (int v = 0; v < NV; v++) sm[threadIdx.x * NV + v] += sm[(threadIdx.x + w) * NV + v];
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int v = 0; v < 3; v++) a.slice[((size_t)sys * FIN_SPLIT + y) * 3 + v] = sm[v];
+    for (int v = 0; v < NV; v++) a.slice[((size_t)sys * FIN_SPLIT + y) * FIN_MAXV + v] = sm[v];
     __threadfence();
     ticket = atomicAdd(&a.count[sys], 1u);
   }
@@ -568,10 +586,13 @@ __global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
   if (threadIdx.x != 0) return;
   __threadfence();
   a.count[sys] = 0;  // re-armed for the next finalize of this system
-  double tot[3] = {0.0, 0.0, 0.0};
+  double tot[FIN_MAXV];
+#pragma unroll
+  for (int v = 0; v < FIN_MAXV; v++) tot[v] = 0.0;
   for (int yy = 0; yy < FIN_SPLIT; yy++) {
 #pragma unroll
-    for (int v = 0; v < 3; v++) tot[v] += __ldcg(&a.slice[((size_t)sys * FIN_SPLIT + yy) * 3 + v]);  // L2: other SMs wrote them
+    for (int v = 0; v < NV; v++)
+      tot[v] += __ldcg(&a.slice[((size_t)sys * FIN_SPLIT + yy) * FIN_MAXV + v]);  // L2: other SMs wrote them
   }
   fin_logic(a, op, a.st[sys], tot);
 }

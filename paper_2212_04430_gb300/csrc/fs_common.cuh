@@ -222,7 +222,8 @@ enum CoefIdx {
   C_OMEGA = 9,    // omega (re, im)
   C_SCALE = 11,   // r_lo = scale * r_hi
   C_INVSCALE = 12,
-  C_MINVA = 13    // -A
+  C_MINVA = 13,   // -A
+  C_RATIO = 14    // new scale / old scale of the last reliable update
 };
 
 struct SysState {
@@ -240,8 +241,8 @@ struct SysState {
   double r2_full;             // ||z - (D + sigma) x||^2 over the full lattice (verification)
   // Coefficients read by the per-site kernels, in both precisions (kernels never
   // do per-thread FP64 scalar arithmetic: FP64 issues at a small fraction of FP32).
-  double cd[14];
-  float cf[14];
+  double cd[15];
+  float cf[15];
   int status;
   int flags;
   int iters;

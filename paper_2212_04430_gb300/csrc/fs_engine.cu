@@ -111,7 +111,7 @@ class Tile : public TileBase {
        *tmp = nullptr;
   double *pa = nullptr, *pb = nullptr, *pc = nullptr;
   int* gate = nullptr;
-  double* fin_slice = nullptr;   // finalize slice sums [MAX_TILE][FIN_SPLIT][3]
+  double* fin_slice = nullptr;   // finalize slice sums [MAX_TILE][FIN_SPLIT][FIN_MAXV]
   unsigned* fin_count = nullptr; // finalize arrival tickets [MAX_TILE], zero between finalizes
   double *cg_p = nullptr, *cg_q = nullptr, *cg_g = nullptr, *cg_w = nullptr, *cg_r = nullptr;  // CGNR fallback
   std::vector<void*> owned;
@@ -166,10 +166,12 @@ class Tile : public TileBase {
     r = dalloc(fts); rhat = dalloc(fts); p = dalloc(fts); v = dalloc(fts); s = dalloc(fts); t = dalloc(fts);
     tmp = dalloc(fts);
     tmp64 = std::is_same<Ts, double>::value ? (double*)tmp : (double*)dalloc(f64);
+    // pa holds up to 8 values per (system, 8-site group) (the t = M s dots), pb and pc up to 3
     const size_t pbytes = (size_t)N * 3 * ngroups * sizeof(double);
-    pa = (double*)dalloc(pbytes); pb = (double*)dalloc(pbytes); pc = (double*)dalloc(pbytes);
+    pa = (double*)dalloc((size_t)N * 8 * ngroups * sizeof(double));
+    pb = (double*)dalloc(pbytes); pc = (double*)dalloc(pbytes);
     gate = (int*)dalloc(sizeof(int));
-    fin_slice = (double*)dalloc(sizeof(double) * MAX_TILE * FIN_SPLIT * 3);
+    fin_slice = (double*)dalloc(sizeof(double) * MAX_TILE * FIN_SPLIT * FIN_MAXV);
     fin_count = (unsigned*)dalloc(sizeof(unsigned) * MAX_TILE);
     st_d = (SysState*)dalloc(sizeof(SysState) * MAX_TILE);
     spec_d = (NoiseSpec*)dalloc(sizeof(NoiseSpec) * MAX_TILE);
@@ -213,7 +215,14 @@ class Tile : public TileBase {
     f.target = 0.25;  // rms of a scaled residual entry (keeps FP16 away from both range limits)
     f.nreal = 24.0 * c->g.Vh;
     f.max_restarts = 8;
-    fin_kernel<<<dim3(N, FIN_SPLIT), 256, 0, c->stream>>>(f, op);
+    const dim3 grid(N, FIN_SPLIT);
+    switch (fin_values(op)) {
+      case 1: fin_kernel<1><<<grid, 256, 0, c->stream>>>(f, op); break;
+      case 2: fin_kernel<2><<<grid, 256, 0, c->stream>>>(f, op); break;
+      case 3: fin_kernel<3><<<grid, 256, 0, c->stream>>>(f, op); break;
+      case 8: fin_kernel<8><<<grid, 256, 0, c->stream>>>(f, op); break;
+      default: return cudaErrorInvalidValue;
+    }
     note_launch();
     return cudaGetLastError();
   }
@@ -277,7 +286,7 @@ class Tile : public TileBase {
   cudaError_t enqueue_iter() override {
     L.stream = c->stream;
     cudaError_t e;
-    if ((e = launch_blas<Ts>(OP_P, blas(MASK_ACTIVE, nullptr, nullptr, false), L))) return e;
+    // p was set by the previous iteration's OP_XRP, or by OP_SETR at a (re)start
     if ((e = hop_lo(COEF_PLAIN, DOT_NONE, hop(tmp, p, nullptr, nullptr, nullptr, nullptr, 1, MASK_ACTIVE, false,
                                               false), 0))) return e;
     if ((e = hop_lo(COEF_MHAT, DOT_R, hop(v, tmp, p, nullptr, rhat, pa, 0, MASK_ACTIVE, false, false), 2)))
@@ -286,12 +295,11 @@ class Tile : public TileBase {
     if ((e = launch_blas<Ts>(OP_S, blas(MASK_ACTIVE, nullptr, nullptr, false), L))) return e;
     if ((e = hop_lo(COEF_PLAIN, DOT_NONE, hop(tmp, s, nullptr, nullptr, nullptr, nullptr, 1, MASK_ACTIVE, false,
                                               false), 0))) return e;
-    if ((e = hop_lo(COEF_MHAT, DOT_TS, hop(t, tmp, s, nullptr, nullptr, pa, 0, MASK_ACTIVE, false, false), 1)))
+    if ((e = hop_lo(COEF_MHAT, DOT_TS, hop(t, tmp, s, nullptr, rhat, pa, 0, MASK_ACTIVE, false, false), 2)))
       return e;
     if ((e = fin(FIN_OMEGA, MASK_ACTIVE, pa))) return e;
-    if ((e = launch_blas<Ts>(OP_XR, blas(MASK_ACTIVE, nullptr, pa, false), L))) return e;
-    if ((e = fin(FIN_RHO, MASK_ACTIVE, pa))) return e;
-    // Reliable update of the systems flagged by FIN_RHO, in FP64. These kernels use the
+    if ((e = launch_blas<Ts>(OP_XRP, blas(MASK_ACTIVE, nullptr, nullptr, false), L))) return e;
+    // Reliable update of the systems flagged by FIN_OMEGA, in FP64. These kernels use the
     // system-major shape: a block serves one system, so unflagged systems cost one flag
     // read per block instead of occupying FP64 issue slots inside mixed warps.
     L1.stream = c->stream;

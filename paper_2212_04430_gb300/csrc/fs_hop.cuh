@@ -28,10 +28,14 @@ enum Coef {
   COEF_FULLRES = 6,  // out = Y - A X + H in / 2          r = z - (D + sigma) x on one parity
 };
 
+// Dot products a hop kernel forms with its output (out) per (8-site group, system):
+//   DOT_R:    <R, out>                                        (out = v, R = rhat)
+//   DOT_TS:   <out, X>, ||out||^2, ||X||^2, <R, X>, <R, out>  (out = t, X = s, R = rhat)
+//   DOT_NORM: ||out||^2
 enum Dot { DOT_NONE = 0, DOT_R = 1, DOT_TS = 2, DOT_NORM = 3 };
 template <int DOT> struct DotK { static constexpr int K = 0; };
 template <> struct DotK<DOT_R> { static constexpr int K = 2; };
-template <> struct DotK<DOT_TS> { static constexpr int K = 3; };
+template <> struct DotK<DOT_TS> { static constexpr int K = 8; };
 template <> struct DotK<DOT_NORM> { static constexpr int K = 1; };
 
 enum Mask { MASK_ALL = 0, MASK_ACTIVE = 1, MASK_UPDATE = 2, MASK_INIT = 3, MASK_HARVEST = 4, MASK_CG = 5,
@@ -98,6 +102,24 @@ __device__ __forceinline__ void norm_acc(Tm& n, Tm a0, Tm a1) {
 // a x + b y
 template <typename Tm>
 __device__ __forceinline__ Tm axpby(Tm a, Tm x, Tm b, Tm y) { return fmadd(b, y, a * x); }
+
+// The DOT_TS values of one site: t = M s, rhat. Each accumulator runs over the
+// entries in index order (the chunked persistent kernel keeps the same order).
+template <typename Tm>
+__device__ __forceinline__ void ts_dots(double (&dv)[8], const Tm (&t)[24], const Tm (&s)[24],
+                                        const Tm (&r)[24]) {
+  Tm tsr = 0, tsi = 0, tt = 0, ss = 0, rsr = 0, rsi = 0, rtr = 0, rti = 0;
+#pragma unroll
+  for (int k = 0; k < 24; k += 2) {
+    dot_acc(tsr, tsi, t[k], t[k + 1], s[k], s[k + 1]);
+    norm_acc(tt, t[k], t[k + 1]);
+    norm_acc(ss, s[k], s[k + 1]);
+    dot_acc(rsr, rsi, r[k], r[k + 1], s[k], s[k + 1]);
+    dot_acc(rtr, rti, r[k], r[k + 1], t[k], t[k + 1]);
+  }
+  dv[0] = (double)tsr; dv[1] = (double)tsi; dv[2] = (double)tt; dv[3] = (double)ss;
+  dv[4] = (double)rsr; dv[5] = (double)rsi; dv[6] = (double)rtr; dv[7] = (double)rti;
+}
 
 // ---- links -----------------------------------------------------------------
 // Third row of a special unitary matrix from its first two: u2 = conj(u0 x u1),
@@ -243,7 +265,9 @@ __device__ __forceinline__ void hop_mu(Tm (&acc)[24], const Field<Ts>& in, const
 }
 
 // Write per-thread values into per-(8-site group, system) partial sums, in fixed order.
-template <int K>
+// Ta: the type the 8 site values are summed in (the kernel's arithmetic type: FP32
+// values are summed in FP32, as every FP32 hop variant does).
+template <int K, typename Ta = double>
 __device__ __forceinline__ void group_partials(const double (&vals)[K], int lsite, int lsys, int sys_base,
                                                const Shape& sh, int Vh, int chunk, double* smem,
                                                double* partial) {
@@ -257,15 +281,15 @@ __device__ __forceinline__ void group_partials(const double (&vals)[K], int lsit
     const int grp = chunk * ngb + lsite;
     const int sys = sys_base + lsys;
     if (grp < ngroups && sys < sh.N) {
-      double s[K];
+      Ta s[K];
 #pragma unroll
-      for (int k = 0; k < K; k++) s[k] = 0.0;
+      for (int k = 0; k < K; k++) s[k] = 0;
       for (int j = 0; j < 8; j++) {
 #pragma unroll
-        for (int k = 0; k < K; k++) s[k] += smem[((lsite * 8 + j) * NB + lsys) * K + k];
+        for (int k = 0; k < K; k++) s[k] += (Ta)smem[((lsite * 8 + j) * NB + lsys) * K + k];
       }
 #pragma unroll
-      for (int k = 0; k < K; k++) partial[((size_t)sys * K + k) * ngroups + grp] = s[k];
+      for (int k = 0; k < K; k++) partial[((size_t)sys * K + k) * ngroups + grp] = (double)s[k];
     }
   }
   __syncthreads();
@@ -352,15 +376,10 @@ __global__ void __launch_bounds__(256, sizeof(Tm) == 8 ? 2 : (sizeof(Ts) == 2 ? 
 #pragma unroll
           for (int k = 0; k < 24; k++) o[k] = fmadd(cc, yv[k], o[k]);
         }
-        if (DOT == DOT_TS) {
-          // <out, X> and <out, out>, out = t, X = s
-          Tm sr = 0, si = 0, tt = 0;
-#pragma unroll
-          for (int k = 0; k < 24; k += 2) {
-            dot_acc(sr, si, o[k], o[k + 1], xv[k], xv[k + 1]);
-            norm_acc(tt, o[k], o[k + 1]);
-          }
-          dv[0] = (double)sr; dv[1] = (double)si; dv[2] = (double)tt;
+        if constexpr (DOT == DOT_TS) {
+          Tm rv[24];
+          make_field<Ts>(const_cast<void*>(a.R), g.Vh, sh.N, smj).load(site, sys, rv);
+          ts_dots(dv, o, xv, rv);
         }
       }
       if (DOT == DOT_R) {
@@ -380,7 +399,7 @@ __global__ void __launch_bounds__(256, sizeof(Tm) == 8 ? 2 : (sizeof(Ts) == 2 ? 
       out.store(site, sys, o);
     }
     if constexpr (K > 0) {
-      group_partials<K>(dv, lsite, lsys, sys_base, sh, g.Vh, chunk, smem, a.partial);
+      group_partials<K, Tm>(dv, lsite, lsys, sys_base, sh, g.Vh, chunk, smem, a.partial);
     }
   };
 
@@ -441,7 +460,7 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
   constexpr int VW = Store<Ts>::VW;
   // items: 0..7 neighbour spinors, 8 = X (epilogue axpy operand), 9 = R (dot partner)
   constexpr bool HAS_X = COEF != COEF_PLAIN;
-  constexpr bool HAS_R = DOT == DOT_R;
+  constexpr bool HAS_R = DOT == DOT_R || DOT == DOT_TS;
   constexpr int NITEM = 8 + (HAS_X ? 1 : 0) + (HAS_R ? 1 : 0);
   extern __shared__ uint4 ring[];
   __shared__ double smem[256 * (K > 0 ? K : 1)];
@@ -609,32 +628,26 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
 #pragma unroll
     for (int k = 0; k < (K > 0 ? K : 1); k++) dv[k] = 0.0;
     if (act) {
-      Tm o[24];
+      Tm o[24], xv[24];
       if constexpr (!HAS_X) {
 #pragma unroll
         for (int k = 0; k < 24; k++) o[k] = acc[k];
       } else {
-        Tm xv[24];
         fetch(8, xv);
 #pragma unroll
         for (int k = 0; k < 24; k++) o[k] = axpby(ca, xv[k], cb, acc[k]);
-        if (DOT == DOT_TS) {
-          Tm sr = 0, si = 0, tt = 0;
-#pragma unroll
-          for (int k = 0; k < 24; k += 2) {
-            dot_acc(sr, si, o[k], o[k + 1], xv[k], xv[k + 1]);
-            norm_acc(tt, o[k], o[k + 1]);
-          }
-          dv[0] = (double)sr; dv[1] = (double)si; dv[2] = (double)tt;
-        }
       }
       if constexpr (HAS_R) {
         Tm rv[24];
         fetch(8 + (HAS_X ? 1 : 0), rv);
-        Tm sr = 0, si = 0;
+        if constexpr (DOT == DOT_TS) {
+          ts_dots(dv, o, xv, rv);
+        } else {
+          Tm sr = 0, si = 0;
 #pragma unroll
-        for (int k = 0; k < 24; k += 2) dot_acc(sr, si, rv[k], rv[k + 1], o[k], o[k + 1]);
-        dv[0] = (double)sr; dv[1] = (double)si;
+          for (int k = 0; k < 24; k += 2) dot_acc(sr, si, rv[k], rv[k + 1], o[k], o[k + 1]);
+          dv[0] = (double)sr; dv[1] = (double)si;
+        }
       }
       make_field<Ts>(a.out, g.Vh, sh.N).store(site, sys, o);
     }
@@ -654,19 +667,19 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
           const int grp = chunk;
           const int sysg = blockIdx.y * 32 + lane;
           if (grp < ngroups && sysg < sh.N) {
-            double sacc[K > 0 ? K : 1];
+            Tm sacc[K > 0 ? K : 1];
 #pragma unroll
-            for (int k = 0; k < K; k++) sacc[k] = 0.0;
+            for (int k = 0; k < K; k++) sacc[k] = 0;
             for (int j = 0; j < 8; j++) {
 #pragma unroll
-              for (int k = 0; k < K; k++) sacc[k] += smem[(j * 32 + lane) * K + k];
+              for (int k = 0; k < K; k++) sacc[k] += (Tm)smem[(j * 32 + lane) * K + k];
             }
 #pragma unroll
-            for (int k = 0; k < K; k++) a.partial[((size_t)sysg * K + k) * ngroups + grp] = sacc[k];
+            for (int k = 0; k < K; k++) a.partial[((size_t)sysg * K + k) * ngroups + grp] = (double)sacc[k];
           }
         }
       } else {
-        group_partials<K>(dv, lsite, lsys, blockIdx.y * sh.NB, sh, g.Vh, chunk, smem, a.partial);
+        group_partials<K, Tm>(dv, lsite, lsys, blockIdx.y * sh.NB, sh, g.Vh, chunk, smem, a.partial);
       }
     }
   }
@@ -705,14 +718,16 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
   constexpr int CV = chunks16<Ts>();
   constexpr int VW = Store<Ts>::VW;
   constexpr bool HAS_X = COEF != COEF_PLAIN;
-  constexpr bool HAS_R = DOT == DOT_R;
+  constexpr bool HAS_R = DOT == DOT_R || DOT == DOT_TS;
   constexpr int NITEM = 8 + (HAS_X ? 1 : 0) + (HAS_R ? 1 : 0);
   static_assert(PF >= 1 && PF < NITEM, "ring depth");
+  static_assert(DOT != DOT_TS || (HAS_X && PF >= 2), "DOT_TS consumes X and R together");
   constexpr int RPC = link_chunks16<Tg>(NR);  // 16-byte chunks per stored link
   constexpr int RP = link_pad<Tg>(NR);
   constexpr int GVW = Store<Tg>::VW;
   extern __shared__ uint4 ring[];             // [PF][CV][256 threads]
-  __shared__ double dsm[2][8][32][KK];        // dot values of chunk parity j & 1: [site][system]
+  // dot values of chunk parity j & 1: [site][system]; FP32 sums, so held exactly as float
+  __shared__ float dsm[2][8][32][KK];
   __shared__ __align__(16) float lsm[8 * 8 * LINK_F32];  // [warp][direction][20]
   __shared__ uint4 lraw[2 * 8 * 8 * RPC];     // raw links, double buffered by chunk parity
   if (a.gate != nullptr && *a.gate == 0) return;
@@ -886,11 +901,40 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
     double dv[KK];
 #pragma unroll
     for (int k = 0; k < KK; k++) dv[k] = 0.0;
-    if constexpr (HAS_X) {
-      // out = ca X + cb (H in), in place of acc, one 16-byte chunk of X at a time
-      cp_async_wait<PF - 1>();
-      Tm sr = 0, si = 0, tt = 0;
+    if constexpr (DOT == DOT_TS) {
+      // X (= s) and R (= rhat) together, one 16-byte chunk of each at a time:
+      // t = ca s + cb (H in) in place of acc, and <t, s>, ||t||^2, ||s||^2, <rhat, s>, <rhat, t>
+      cp_async_wait<PF - 2>();
+      Tm sr = 0, si = 0, tt = 0, ss = 0, qr = 0, qi = 0, tr = 0, ti = 0;
       {
+        const int xslot = slot_of(j, 8), rslot = slot_of(j, 9);
+#pragma unroll
+        for (int c = 0; c < CV; c++) {
+          Tm xv[VW], rv[VW];
+          fetch_chunk(xslot, c, xv);
+          fetch_chunk(rslot, c, rv);
+#pragma unroll
+          for (int k = 0; k < VW; k++) acc[c * VW + k] = axpby(ca, xv[k], cb, acc[c * VW + k]);
+#pragma unroll
+          for (int k = 0; k < VW; k += 2) {
+            const Tm t0 = acc[c * VW + k], t1 = acc[c * VW + k + 1];
+            dot_acc(sr, si, t0, t1, xv[k], xv[k + 1]);
+            norm_acc(tt, t0, t1);
+            norm_acc(ss, xv[k], xv[k + 1]);
+            dot_acc(qr, qi, rv[k], rv[k + 1], xv[k], xv[k + 1]);
+            dot_acc(tr, ti, rv[k], rv[k + 1], t0, t1);
+          }
+        }
+      }
+      issue_ahead(IntC<8>{}, j);
+      issue_ahead(IntC<9>{}, j);
+      dv[0] = sel ? (double)sr : 0.0; dv[1] = sel ? (double)si : 0.0; dv[2] = sel ? (double)tt : 0.0;
+      dv[3] = sel ? (double)ss : 0.0; dv[4] = sel ? (double)qr : 0.0; dv[5] = sel ? (double)qi : 0.0;
+      dv[6] = sel ? (double)tr : 0.0; dv[7] = sel ? (double)ti : 0.0;
+    } else {
+      if constexpr (HAS_X) {
+        // out = ca X + cb (H in), in place of acc, one 16-byte chunk of X at a time
+        cp_async_wait<PF - 1>();
         const int slot = slot_of(j, 8);
 #pragma unroll
         for (int c = 0; c < CV; c++) {
@@ -898,24 +942,13 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
           fetch_chunk(slot, c, xv);
 #pragma unroll
           for (int k = 0; k < VW; k++) acc[c * VW + k] = axpby(ca, xv[k], cb, acc[c * VW + k]);
-          if constexpr (DOT == DOT_TS) {  // <out, X> and <out, out>, out = t, X = s
-#pragma unroll
-            for (int k = 0; k < VW; k += 2) {
-              dot_acc(sr, si, acc[c * VW + k], acc[c * VW + k + 1], xv[k], xv[k + 1]);
-              norm_acc(tt, acc[c * VW + k], acc[c * VW + k + 1]);
-            }
-          }
         }
+        issue_ahead(IntC<8>{}, j);
       }
-      issue_ahead(IntC<8>{}, j);
-      if constexpr (DOT == DOT_TS) {
-        dv[0] = sel ? (double)sr : 0.0; dv[1] = sel ? (double)si : 0.0; dv[2] = sel ? (double)tt : 0.0;
-      }
-    }
-    if constexpr (HAS_R) {
-      cp_async_wait<PF - 1>();
-      Tm sr = 0, si = 0;
-      {
+      if constexpr (HAS_R) {
+        // <rhat, v>, out = v
+        cp_async_wait<PF - 1>();
+        Tm sr = 0, si = 0;
         const int slot = slot_of(j, NITEM - 1);
 #pragma unroll
         for (int c = 0; c < CV; c++) {
@@ -924,30 +957,27 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
 #pragma unroll
           for (int k = 0; k < VW; k += 2) dot_acc(sr, si, rv[k], rv[k + 1], acc[c * VW + k], acc[c * VW + k + 1]);
         }
+        issue_ahead(IntC<NITEM - 1>{}, j);
+        dv[0] = sel ? (double)sr : 0.0; dv[1] = sel ? (double)si : 0.0;
       }
-      issue_ahead(IntC<NITEM - 1>{}, j);
-      dv[0] = sel ? (double)sr : 0.0; dv[1] = sel ? (double)si : 0.0;
     }
     if (sel) make_field<Ts>(a.out, g.Vh, sh.N).store(site, sys, acc);
     if constexpr (K > 0) {
       // the block's 8 sites form the 8-site group `chunk`; summed in site order by one warp
       const int par = j & 1;
 #pragma unroll
-      for (int k = 0; k < K; k++) dsm[par][warp][lane][k] = dv[k];
+      for (int k = 0; k < K; k++) dsm[par][warp][lane][k] = (float)dv[k];
       __syncthreads();
-      if (warp == (j & 7)) {
-        const int chunk = (int)blockIdx.x + j * G;
-        const int ngroups = g.Vh / 8;
-        if (sys < sh.N) {
-          double s[KK];
+      {
+        // value k of the group is summed (in site order, FP32) by warp (k - j) mod 8: the
+        // values are spread over the warps, and the warp that starts rotates with the chunk
+        const int k = (warp + j) & 7;
+        if (k < K && sys < sh.N) {
+          const int chunk = (int)blockIdx.x + j * G;
+          float s = 0.f;
 #pragma unroll
-          for (int k = 0; k < K; k++) s[k] = 0.0;
-          for (int w = 0; w < 8; w++) {
-#pragma unroll
-            for (int k = 0; k < K; k++) s[k] += dsm[par][w][lane][k];
-          }
-#pragma unroll
-          for (int k = 0; k < K; k++) a.partial[((size_t)sys * K + k) * ngroups + chunk] = s[k];
+          for (int w = 0; w < 8; w++) s += dsm[par][w][lane][k];
+          a.partial[((size_t)sys * K + k) * (g.Vh / 8) + chunk] = (double)s;
         }
       }
       // dsm[par] is rewritten two chunks later, after the next barrier: no second barrier

@@ -17,7 +17,7 @@ template <typename Ts> constexpr int hop_pf() { return sizeof(Ts) == 2 ? 4 : 3; 
 // shared memory allows (static ring slots), two resident blocks per SM.
 template <typename Ts, int C, int D>
 constexpr int hop_pp_depth() {
-  constexpr int nitem = 8 + (C != COEF_PLAIN ? 1 : 0) + (D == DOT_R ? 1 : 0);
+  constexpr int nitem = 8 + (C != COEF_PLAIN ? 1 : 0) + (D == DOT_R || D == DOT_TS ? 1 : 0);
   if constexpr (sizeof(Ts) == 2) return nitem == 8 ? 4 : (nitem == 9 ? 3 : 5);
   return 3;
 }
@@ -115,11 +115,10 @@ cudaError_t launch_blas(int op, const BlasArgs& a, const Launch& l) {
   const dim3 grid(l.grid_x, l.grid_y), block(l.block);
   // the per-iteration solver updates run on the tile shape; the FP64-field operations
   // (x_hi updates, residual restarts, norms) on the system-major work list
-  if ((op == OP_P || op == OP_S || op == OP_XR) == (a.sysmajor != 0)) return cudaErrorInvalidValue;
+  if ((op == OP_S || op == OP_XRP) == (a.sysmajor != 0)) return cudaErrorInvalidValue;
   switch (op) {
-    case OP_P: blas_kernel<Ts, Tx, Tm, OP_P, false><<<grid, block, 0, l.stream>>>(a); break;
     case OP_S: blas_kernel<Ts, Tx, Tm, OP_S, false><<<grid, block, 0, l.stream>>>(a); break;
-    case OP_XR: blas_kernel<Ts, Tx, Tm, OP_XR, false><<<grid, block, 0, l.stream>>>(a); break;
+    case OP_XRP: blas_kernel<Ts, Tx, Tm, OP_XRP, false><<<grid, block, 0, l.stream>>>(a); break;
     case OP_ACCX: blas_kernel<Ts, Tx, Tm, OP_ACCX, true><<<grid, block, 0, l.stream>>>(a); break;
     case OP_ZEROX: blas_kernel<Ts, Tx, Tm, OP_ZEROX, true><<<grid, block, 0, l.stream>>>(a); break;
     case OP_SETR: blas_kernel<Ts, Tx, Tm, OP_SETR, true><<<grid, block, 0, l.stream>>>(a); break;

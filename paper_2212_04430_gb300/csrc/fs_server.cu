@@ -56,7 +56,7 @@ size_t estimate(const SJob& j) {
   const size_t f64 = 24 * Vh * tile * 8;
   const size_t fts = 24 * Vh * tile * real_bytes(prec);
   const size_t ftx = 24 * Vh * tile * (prec == FS_PREC_F64 ? 8 : 4);
-  const size_t tile_bytes = 6 * f64 + (prec == FS_PREC_F64 ? 0 : f64) + ftx + 7 * fts + 3 * (size_t)tile * 3 * (Vh / 8) * 8;
+  const size_t tile_bytes = 6 * f64 + (prec == FS_PREC_F64 ? 0 : f64) + ftx + 7 * fts + (8 + 3 + 3) * (size_t)tile * (Vh / 8) * 8;
   const size_t gauge = 8 * Vh * (18 * 8 + 20 * 4 + 12 * 4 + 24 * 2 + 16 * 2);
   const size_t stage = j.P.estimator == FS_EST_PRODUCT ? (size_t)tile * V * 24 * 8 : 0;
   const size_t contract = (size_t)tile * ((2 * Vh + 255) / 256) * 2 * 8 + (64u << 10) +
