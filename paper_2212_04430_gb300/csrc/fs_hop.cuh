@@ -185,11 +185,32 @@ __device__ __forceinline__ void su3_mul(const Tm (&u)[18], const Tm* h, Tm* chi)
   }
 }
 
-// One hop in direction MU with projector (1 + S gamma_mu), S = -1 forward, +1 backward.
-// psi indices: spin s, colour c -> psi[6 s + 2 c + {0 re, 1 im}].
-template <int MU, int S, bool DAG, typename Tm>
-__device__ __forceinline__ void hop_dir(Tm (&acc)[24], const Tm (&psi)[24], const Tm (&u)[18], Tm ph) {
-  Tm h0[6], h1[6];
+// chi = U h - c  or  U^dag h - c: the chains of su3_mul started from -c.
+template <bool DAG, typename Tm>
+__device__ __forceinline__ void su3_mul_sub(const Tm (&u)[18], const Tm* h, const Tm* c, Tm* chi) {
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    Tm re = -c[2 * a], im = -c[2 * a + 1];
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      const int k = DAG ? (b * 3 + a) * 2 : (a * 3 + b) * 2;
+      const Tm ur = u[k];
+      const Tm ui = DAG ? -u[k + 1] : u[k + 1];
+      re = fmadd(ur, h[2 * b], re);
+      im = fmadd(ur, h[2 * b + 1], im);
+      re = fmadd(-ui, h[2 * b + 1], re);
+      im = fmadd(ui, h[2 * b], im);
+    }
+    chi[2 * a] = re;
+    chi[2 * a + 1] = im;
+  }
+}
+
+// Spin projection h = (1 + S gamma_mu) psi on the upper two spins (the lower two follow
+// from them), S = -1 forward, +1 backward. psi index: spin s, colour c, re/im ->
+// psi[6 s + 2 c + {0, 1}]; h[0..5] spin 0, h[6..11] spin 1.
+template <int MU, int S, typename Tm>
+__device__ __forceinline__ void project(const Tm (&psi)[24], Tm (&h)[12]) {
 #pragma unroll
   for (int c = 0; c < 3; c++) {
     const Tm p0r = psi[2 * c], p0i = psi[2 * c + 1];
@@ -206,39 +227,77 @@ __device__ __forceinline__ void hop_dir(Tm (&acc)[24], const Tm (&psi)[24], cons
     } else {                // G4 = 1
       g0r = p2r; g0i = p2i; g1r = p3r; g1i = p3i;
     }
-    h0[2 * c] = p0r + S * g0r; h0[2 * c + 1] = p0i + S * g0i;
-    h1[2 * c] = p1r + S * g1r; h1[2 * c + 1] = p1i + S * g1i;
+    h[2 * c] = p0r + S * g0r; h[2 * c + 1] = p0i + S * g0i;
+    h[6 + 2 * c] = p1r + S * g1r; h[6 + 2 * c + 1] = p1i + S * g1i;
   }
-  if (MU == 3) {
+}
+
+// The antiperiodic boundary phase ph = +-1 of a t hop. In FP64 it is a sign flip done on
+// the integer units (identical to the product, and off the FP64 pipe).
+template <typename Tm>
+__device__ __forceinline__ void apply_phase(Tm (&h)[12], Tm ph) {
+  if constexpr (std::is_same<Tm, double>::value) {
+    const unsigned long long m = ph < 0 ? 0x8000000000000000ull : 0ull;
 #pragma unroll
-    for (int k = 0; k < 6; k++) { h0[k] *= ph; h1[k] *= ph; }
+    for (int k = 0; k < 12; k++) h[k] = __longlong_as_double(__double_as_longlong(h[k]) ^ m);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; k++) h[k] *= ph;
   }
-  Tm x0[6], x1[6];
-  su3_mul<DAG>(u, h0, x0);
-  su3_mul<DAG>(u, h1, x1);
+}
+
+// The two hops of direction mu are formed as a pair. Forward, (1 - gamma_mu) U_mu(x)
+// psi(x + mu): its upper-spin product xf = U h_f (hop_fwd). Backward, (1 + gamma_mu)
+// U_mu(x - mu)^dag psi(x - mu): z = U^dag h_b - xf in one chain per entry, then
+//   upper spins  += xf + xb = 2 xf + z,
+//   lower spins  += G^dag (xb - xf) = G^dag z
+// (the lower spins of a hop are -S G^dag of its upper product). The pair costs twelve
+// operations fewer than two separate accumulations.
+template <int MU, typename Tm>
+__device__ __forceinline__ void hop_fwd(Tm (&xf)[12], const Tm (&psi)[24], const Tm (&u)[18], Tm ph) {
+  Tm h[12];
+  project<MU, -1>(psi, h);
+  if (MU == 3) apply_phase(h, ph);
+  su3_mul<false>(u, h, xf);
+  su3_mul<false>(u, h + 6, xf + 6);
+}
+
+template <int MU, typename Tm>
+__device__ __forceinline__ void hop_bwd(Tm (&acc)[24], const Tm (&xf)[12], const Tm (&psi)[24], const Tm (&u)[18],
+                                        Tm ph) {
+  Tm h[12];
+  project<MU, +1>(psi, h);
+  if (MU == 3) apply_phase(h, ph);
+  Tm z[12];
+  su3_mul_sub<true>(u, h, xf, z);
+  su3_mul_sub<true>(u, h + 6, xf + 6, z + 6);
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    const Tm x0r = x0[2 * c], x0i = x0[2 * c + 1], x1r = x1[2 * c], x1i = x1[2 * c + 1];
-    acc[2 * c] += x0r; acc[2 * c + 1] += x0i;
-    acc[6 + 2 * c] += x1r; acc[6 + 2 * c + 1] += x1i;
-    Tm d0r, d0i, d1r, d1i;  // G^dag chi
-    if (MU == 0) {          // G1^dag = [[0, -i], [-i, 0]]
-      d0r = x1i; d0i = -x1r; d1r = x0i; d1i = -x0r;
-    } else if (MU == 1) {   // G2^dag = [[0, 1], [-1, 0]]
-      d0r = x1r; d0i = x1i; d1r = -x0r; d1i = -x0i;
-    } else if (MU == 2) {   // G3^dag = diag(-i, i)
-      d0r = x0i; d0i = -x0r; d1r = -x1i; d1i = x1r;
-    } else {
-      d0r = x0r; d0i = x0i; d1r = x1r; d1i = x1i;
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+      acc[2 * c + q] = fmadd((Tm)2, xf[2 * c + q], acc[2 * c + q]) + z[2 * c + q];
+      acc[6 + 2 * c + q] = fmadd((Tm)2, xf[6 + 2 * c + q], acc[6 + 2 * c + q]) + z[6 + 2 * c + q];
     }
-    acc[12 + 2 * c] += S * d0r; acc[12 + 2 * c + 1] += S * d0i;
-    acc[18 + 2 * c] += S * d1r; acc[18 + 2 * c + 1] += S * d1i;
+    const Tm z0r = z[2 * c], z0i = z[2 * c + 1], z1r = z[6 + 2 * c], z1i = z[6 + 2 * c + 1];
+    Tm d0r, d0i, d1r, d1i;  // G^dag z
+    if (MU == 0) {          // G1^dag = [[0, -i], [-i, 0]]
+      d0r = z1i; d0i = -z1r; d1r = z0i; d1i = -z0r;
+    } else if (MU == 1) {   // G2^dag = [[0, 1], [-1, 0]]
+      d0r = z1r; d0i = z1i; d1r = -z0r; d1i = -z0i;
+    } else if (MU == 2) {   // G3^dag = diag(-i, i)
+      d0r = z0i; d0i = -z0r; d1r = -z1i; d1i = z1r;
+    } else {
+      d0r = z0r; d0i = z0i; d1r = z1r; d1i = z1i;
+    }
+    acc[12 + 2 * c] += d0r; acc[12 + 2 * c + 1] += d0i;
+    acc[18 + 2 * c] += d1r; acc[18 + 2 * c + 1] += d1i;
   }
 }
 
 template <typename Ts, typename Tg, typename Tm, int NR, int MU>
 __device__ __forceinline__ void hop_mu(Tm (&acc)[24], const Field<Ts>& in, const Tg* gauge, const Geom& g,
                                        int p_out, int site, int sys, const int (&x)[4]) {
+  Tm xf[12];
   // forward: (1 - g_mu) U_mu(x) psi(x + mu)
   {
     int y[4] = {x[0], x[1], x[2], x[3]};
@@ -248,7 +307,7 @@ __device__ __forceinline__ void hop_mu(Tm (&acc)[24], const Field<Ts>& in, const
     Tm psi[24], u[18];
     in.load(cb_index(g, y), sys, psi);
     load_link<Tg, Tm, NR>((const Tg*)gauge, g.Vh, p_out, MU, site, u);
-    hop_dir<MU, -1, false>(acc, psi, u, ph);
+    hop_fwd<MU>(xf, psi, u, ph);
   }
   // backward: (1 + g_mu) U_mu(x - mu)^dag psi(x - mu)
   {
@@ -260,7 +319,7 @@ __device__ __forceinline__ void hop_mu(Tm (&acc)[24], const Field<Ts>& in, const
     Tm psi[24], u[18];
     in.load(nb, sys, psi);
     load_link<Tg, Tm, NR>((const Tg*)gauge, g.Vh, 1 - p_out, MU, nb, u);
-    hop_dir<MU, +1, true>(acc, psi, u, ph);
+    hop_bwd<MU>(acc, xf, psi, u, ph);
   }
 }
 
@@ -332,15 +391,15 @@ __global__ void __launch_bounds__(256, sizeof(Tm) == 8 ? 2 : (sizeof(Ts) == 2 ? 
 
   // one chunk of sites for system `sys` (sel: the system takes part), block rows sys_base..
   auto chunk_body = [&](const int sys, const int chunk, const bool sel, const int sys_base) {
-    Tm ca = 0, cb = 1, cc = 0;
+    Tm ca = 0, cb = 1;
     if (sel) {
       const SysState& s = a.st[sys];
       if (COEF == COEF_MHAT) { ca = coef<Tm>(s, C_A); cb = coef<Tm>(s, C_MINV4A); }
       else if (COEF == COEF_DSLASH) { ca = coef<Tm>(s, C_A); cb = (Tm)-0.5; }
       else if (COEF == COEF_PREP) { ca = 1; cb = coef<Tm>(s, C_INV2A); }
       else if (COEF == COEF_RECON) { ca = coef<Tm>(s, C_INVA); cb = coef<Tm>(s, C_INV2A); }
-      else if (COEF == COEF_TRUERES) { ca = coef<Tm>(s, C_MINVA); cb = coef<Tm>(s, C_INV4A); cc = 1; }
-      else if (COEF == COEF_FULLRES) { ca = coef<Tm>(s, C_MINVA); cb = (Tm)0.5; cc = 1; }
+      else if (COEF == COEF_TRUERES) { ca = coef<Tm>(s, C_MINVA); cb = coef<Tm>(s, C_INV4A); }
+      else if (COEF == COEF_FULLRES) { ca = coef<Tm>(s, C_MINVA); cb = (Tm)0.5; }
     }
     const int site = chunk * sh.SB + lsite;
     const bool act = sel && site < g.Vh;
@@ -368,13 +427,15 @@ __global__ void __launch_bounds__(256, sizeof(Tm) == 8 ? 2 : (sizeof(Ts) == 2 ? 
       } else {
         Tm xv[24];
         make_field<Ts>(const_cast<void*>(a.X), g.Vh, sh.N, smj).load(site, sys, xv);
-#pragma unroll
-        for (int k = 0; k < 24; k++) o[k] = axpby(ca, xv[k], cb, acc[k]);
-        if (COEF == COEF_TRUERES || COEF == COEF_FULLRES) {
+        if constexpr (COEF == COEF_TRUERES || COEF == COEF_FULLRES) {
+          // out = Y + ca X + cb (H in): two multiply-adds per entry
           Tm yv[24];
           make_field<Ts>(const_cast<void*>(a.Y), g.Vh, sh.N, smj).load(site, sys, yv);
 #pragma unroll
-          for (int k = 0; k < 24; k++) o[k] = fmadd(cc, yv[k], o[k]);
+          for (int k = 0; k < 24; k++) o[k] = fmadd(cb, acc[k], fmadd(ca, xv[k], yv[k]));
+        } else {
+#pragma unroll
+          for (int k = 0; k < 24; k++) o[k] = axpby(ca, xv[k], cb, acc[k]);
         }
         if constexpr (DOT == DOT_TS) {
           Tm rv[24];
@@ -582,7 +643,7 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
       __syncthreads();
     }
     const bool staged = warp_mode || stage;
-    Tm acc[24];
+    Tm acc[24], xf[12];
 #pragma unroll
     for (int k = 0; k < 24; k++) acc[k] = 0;
 #pragma unroll
@@ -610,14 +671,14 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
       issue(d + PF);  // the slot just read is refilled
       if (act) {
         switch (d) {
-          case 0: hop_dir<0, -1, false>(acc, psi, u, (Tm)1); break;
-          case 1: hop_dir<0, +1, true>(acc, psi, u, (Tm)1); break;
-          case 2: hop_dir<1, -1, false>(acc, psi, u, (Tm)1); break;
-          case 3: hop_dir<1, +1, true>(acc, psi, u, (Tm)1); break;
-          case 4: hop_dir<2, -1, false>(acc, psi, u, (Tm)1); break;
-          case 5: hop_dir<2, +1, true>(acc, psi, u, (Tm)1); break;
-          case 6: hop_dir<3, -1, false>(acc, psi, u, ph[0]); break;
-          default: hop_dir<3, +1, true>(acc, psi, u, ph[1]); break;
+          case 0: hop_fwd<0>(xf, psi, u, (Tm)1); break;
+          case 1: hop_bwd<0>(acc, xf, psi, u, (Tm)1); break;
+          case 2: hop_fwd<1>(xf, psi, u, (Tm)1); break;
+          case 3: hop_bwd<1>(acc, xf, psi, u, (Tm)1); break;
+          case 4: hop_fwd<2>(xf, psi, u, (Tm)1); break;
+          case 5: hop_bwd<2>(acc, xf, psi, u, (Tm)1); break;
+          case 6: hop_fwd<3>(xf, psi, u, ph[0]); break;
+          default: hop_bwd<3>(acc, xf, psi, u, ph[1]); break;
         }
       }
     }
@@ -836,7 +897,7 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
 
   for (int j = 0; j < nmine; j++) {
     const int site = site_of(j);
-    Tm acc[24];
+    Tm acc[24], xf[12];
 #pragma unroll
     for (int k = 0; k < 24; k++) acc[k] = 0;
     const float* wl = lsm + warp * 8 * LINK_F32;
@@ -888,14 +949,14 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
         default: issue_ahead(IntC<7>{}, j); break;
       }
       switch (d) {
-        case 0: hop_dir<0, -1, false>(acc, psi, u, (Tm)1); break;
-        case 1: hop_dir<0, +1, true>(acc, psi, u, (Tm)1); break;
-        case 2: hop_dir<1, -1, false>(acc, psi, u, (Tm)1); break;
-        case 3: hop_dir<1, +1, true>(acc, psi, u, (Tm)1); break;
-        case 4: hop_dir<2, -1, false>(acc, psi, u, (Tm)1); break;
-        case 5: hop_dir<2, +1, true>(acc, psi, u, (Tm)1); break;
-        case 6: hop_dir<3, -1, false>(acc, psi, u, (Tm)1); break;
-        default: hop_dir<3, +1, true>(acc, psi, u, (Tm)1); break;
+        case 0: hop_fwd<0>(xf, psi, u, (Tm)1); break;
+        case 1: hop_bwd<0>(acc, xf, psi, u, (Tm)1); break;
+        case 2: hop_fwd<1>(xf, psi, u, (Tm)1); break;
+        case 3: hop_bwd<1>(acc, xf, psi, u, (Tm)1); break;
+        case 4: hop_fwd<2>(xf, psi, u, (Tm)1); break;
+        case 5: hop_bwd<2>(acc, xf, psi, u, (Tm)1); break;
+        case 6: hop_fwd<3>(xf, psi, u, (Tm)1); break;
+        default: hop_bwd<3>(acc, xf, psi, u, (Tm)1); break;
       }
     }
     double dv[KK];
