@@ -254,19 +254,21 @@ __device__ __forceinline__ void apply_phase(Tm (&h)[12], Tm ph) {
 // (the lower spins of a hop are -S G^dag of its upper product). The pair costs twelve
 // operations fewer than two separate accumulations.
 template <int MU, typename Tm>
-__device__ __forceinline__ void hop_fwd(Tm (&xf)[12], const Tm (&psi)[24], const Tm (&u)[18], Tm ph) {
-  Tm h[12];
-  project<MU, -1>(psi, h);
+__device__ __forceinline__ void fwd_core(Tm (&xf)[12], Tm (&h)[12], const Tm (&u)[18], Tm ph) {
   if (MU == 3) apply_phase(h, ph);
   su3_mul<false>(u, h, xf);
   su3_mul<false>(u, h + 6, xf + 6);
 }
 
 template <int MU, typename Tm>
-__device__ __forceinline__ void hop_bwd(Tm (&acc)[24], const Tm (&xf)[12], const Tm (&psi)[24], const Tm (&u)[18],
-                                        Tm ph) {
+__device__ __forceinline__ void hop_fwd(Tm (&xf)[12], const Tm (&psi)[24], const Tm (&u)[18], Tm ph) {
   Tm h[12];
-  project<MU, +1>(psi, h);
+  project<MU, -1>(psi, h);
+  fwd_core<MU>(xf, h, u, ph);
+}
+
+template <int MU, typename Tm>
+__device__ __forceinline__ void bwd_core(Tm (&acc)[24], const Tm (&xf)[12], Tm (&h)[12], const Tm (&u)[18], Tm ph) {
   if (MU == 3) apply_phase(h, ph);
   Tm z[12];
   su3_mul_sub<true>(u, h, xf, z);
@@ -291,6 +293,57 @@ __device__ __forceinline__ void hop_bwd(Tm (&acc)[24], const Tm (&xf)[12], const
     }
     acc[12 + 2 * c] += d0r; acc[12 + 2 * c + 1] += d0i;
     acc[18 + 2 * c] += d1r; acc[18 + 2 * c + 1] += d1i;
+  }
+}
+
+template <int MU, typename Tm>
+__device__ __forceinline__ void hop_bwd(Tm (&acc)[24], const Tm (&xf)[12], const Tm (&psi)[24], const Tm (&u)[18],
+                                        Tm ph) {
+  Tm h[12];
+  project<MU, +1>(psi, h);
+  bwd_core<MU>(acc, xf, h, u, ph);
+}
+
+// Mixed-precision adds (sm_100 and later): an FP16 operand enters an FP32 add directly,
+// a + c or a - c rounded once to FP32 -- the value of converting a first, since the
+// conversion is exact.
+__device__ __forceinline__ float add_h(unsigned short a, float c) {
+  float d;
+  asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(a), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float sub_h(unsigned short a, float c) {
+  float d;
+  asm("sub.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(a), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float h2f(unsigned short a) { return __half2float(__ushort_as_half(a)); }
+
+// project<MU, S> on FP16 input: only the lower-spin entries are converted, the upper-spin
+// ones enter the adds directly. Gives exactly the values of project() on converted input.
+template <int MU, int S>
+__device__ __forceinline__ void project_h(const unsigned short (&p)[24], float (&h)[12]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const float p2r = h2f(p[12 + 2 * c]), p2i = h2f(p[12 + 2 * c + 1]);
+    const float p3r = h2f(p[18 + 2 * c]), p3i = h2f(p[18 + 2 * c + 1]);
+    float g0r, g0i, g1r, g1i;  // G psi_dn, as in project()
+    if (MU == 0) {
+      g0r = -p3i; g0i = p3r; g1r = -p2i; g1i = p2r;
+    } else if (MU == 1) {
+      g0r = -p3r; g0i = -p3i; g1r = p2r; g1i = p2i;
+    } else if (MU == 2) {
+      g0r = -p2i; g0i = p2r; g1r = p3i; g1i = -p3r;
+    } else {
+      g0r = p2r; g0i = p2i; g1r = p3r; g1i = p3i;
+    }
+    if (S > 0) {
+      h[2 * c] = add_h(p[2 * c], g0r); h[2 * c + 1] = add_h(p[2 * c + 1], g0i);
+      h[6 + 2 * c] = add_h(p[6 + 2 * c], g1r); h[6 + 2 * c + 1] = add_h(p[6 + 2 * c + 1], g1i);
+    } else {
+      h[2 * c] = sub_h(p[2 * c], g0r); h[2 * c + 1] = sub_h(p[2 * c + 1], g0i);
+      h[6 + 2 * c] = sub_h(p[6 + 2 * c], g1r); h[6 + 2 * c + 1] = sub_h(p[6 + 2 * c + 1], g1i);
+    }
   }
 }
 
@@ -924,11 +977,23 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
       }
       // every lane computes (no per-lane branches); a lane whose system sits out reads a
       // stale ring slot, and its results are neither stored nor summed
+      constexpr bool RAW = std::is_same<Ts, __half>::value;  // FP16: projection on the raw halves
       Tm psi[24], u[18];
+      unsigned short p16[24];
       {
         const int slot = slot_of(j, d);
+        if constexpr (RAW) {
 #pragma unroll
-        for (int c = 0; c < CV; c++) fetch_chunk(slot, c, psi + c * VW);
+          for (int c = 0; c < CV; c++) {
+            const uint4 w = ring[((size_t)slot * CV + c) * 256 + threadIdx.x];
+            const unsigned short* q = reinterpret_cast<const unsigned short*>(&w);
+#pragma unroll
+            for (int e = 0; e < 8; e++) p16[c * 8 + e] = q[e];
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < CV; c++) fetch_chunk(slot, c, psi + c * VW);
+        }
         const float4* src4 = reinterpret_cast<const float4*>(wl + d * LINK_F32);
 #pragma unroll
         for (int q = 0; q < 4; q++) {
@@ -948,15 +1013,29 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
         case 6: issue_ahead(IntC<6>{}, j); break;
         default: issue_ahead(IntC<7>{}, j); break;
       }
-      switch (d) {
-        case 0: hop_fwd<0>(xf, psi, u, (Tm)1); break;
-        case 1: hop_bwd<0>(acc, xf, psi, u, (Tm)1); break;
-        case 2: hop_fwd<1>(xf, psi, u, (Tm)1); break;
-        case 3: hop_bwd<1>(acc, xf, psi, u, (Tm)1); break;
-        case 4: hop_fwd<2>(xf, psi, u, (Tm)1); break;
-        case 5: hop_bwd<2>(acc, xf, psi, u, (Tm)1); break;
-        case 6: hop_fwd<3>(xf, psi, u, (Tm)1); break;
-        default: hop_bwd<3>(acc, xf, psi, u, (Tm)1); break;
+      if constexpr (RAW) {
+        float h[12];
+        switch (d) {
+          case 0: project_h<0, -1>(p16, h); fwd_core<0>(xf, h, u, 1.f); break;
+          case 1: project_h<0, +1>(p16, h); bwd_core<0>(acc, xf, h, u, 1.f); break;
+          case 2: project_h<1, -1>(p16, h); fwd_core<1>(xf, h, u, 1.f); break;
+          case 3: project_h<1, +1>(p16, h); bwd_core<1>(acc, xf, h, u, 1.f); break;
+          case 4: project_h<2, -1>(p16, h); fwd_core<2>(xf, h, u, 1.f); break;
+          case 5: project_h<2, +1>(p16, h); bwd_core<2>(acc, xf, h, u, 1.f); break;
+          case 6: project_h<3, -1>(p16, h); fwd_core<3>(xf, h, u, 1.f); break;
+          default: project_h<3, +1>(p16, h); bwd_core<3>(acc, xf, h, u, 1.f); break;
+        }
+      } else {
+        switch (d) {
+          case 0: hop_fwd<0>(xf, psi, u, (Tm)1); break;
+          case 1: hop_bwd<0>(acc, xf, psi, u, (Tm)1); break;
+          case 2: hop_fwd<1>(xf, psi, u, (Tm)1); break;
+          case 3: hop_bwd<1>(acc, xf, psi, u, (Tm)1); break;
+          case 4: hop_fwd<2>(xf, psi, u, (Tm)1); break;
+          case 5: hop_bwd<2>(acc, xf, psi, u, (Tm)1); break;
+          case 6: hop_fwd<3>(xf, psi, u, (Tm)1); break;
+          default: hop_bwd<3>(acc, xf, psi, u, (Tm)1); break;
+        }
       }
     }
     double dv[KK];
