@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <thread>
 #include <cstring>
 #include <vector>
 
@@ -23,6 +24,70 @@ int set_device(Ctx& c) {
   return e ? c.cuda_fail(e, "cudaSetDevice") : 0;
 }
 
+// Frees what a context owns: a lane leaves the shared gauge copies and paths alone.
+void release(Ctx& c) {
+  cudaStreamSynchronize(c.stream);
+  for (auto& l : c.lanes) release(*l);
+  c.lanes.clear();
+  c.tiles.clear();
+  if (!c.shared) {
+    if (c.gauge64) cudaFree(c.gauge64);
+    if (c.wline) cudaFree(c.wline);
+    for (auto& kv : c.gauge_lo) cudaFree(kv.second);
+  }
+  if (c.canon_d) cudaFree(c.canon_d);
+  if (c.canon_h) cudaFreeHost(c.canon_h);
+  for (auto& ev : c.prof.pending) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+  for (auto& ev : c.prof.pool) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+  if (c.prof.work_d) cudaFree(c.prof.work_d);
+  if (c.own_stream) cudaStreamDestroy(c.own_stream);
+}
+
+// Profiling state of one context: hop launches timed on its stream, (site, system) counters.
+int prof_reset(Ctx& c, bool enable) {
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e) return c.cuda_fail(e, "fs_profile_enable");
+  for (auto& ev : c.prof.pending) c.prof.pool.push_back(ev);
+  c.prof.pending.clear();
+  c.prof.launches = 0;
+  c.prof.ms = 0;
+  c.prof.bytes = 0;
+  c.prof.pending_bytes = 0;
+  if (!c.prof.work_d) {
+    e = cudaMalloc(&c.prof.work_d, 12 * sizeof(unsigned long long));
+    if (e) return c.cuda_fail(e, "profile counters");
+  }
+  e = cudaMemset(c.prof.work_d, 0, 12 * sizeof(unsigned long long));
+  if (e) return c.cuda_fail(e, "profile counters");
+  c.prof.enabled = enable;
+  return 0;
+}
+
+int prof_collect(Ctx& c, long long& launches, double& ms, double& bytes, double& pairs) {
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e) return c.cuda_fail(e, "fs_profile_read");
+  for (auto& ev : c.prof.pending) {
+    float t = 0;
+    if (cudaEventElapsedTime(&t, ev.first, ev.second) == cudaSuccess) c.prof.ms += t;
+    c.prof.pool.push_back(ev);
+  }
+  c.prof.pending.clear();
+  unsigned long long w[12] = {0};
+  if (c.prof.work_d) {
+    e = cudaMemcpy(w, c.prof.work_d, sizeof(w), cudaMemcpyDeviceToHost);
+    if (e) return c.cuda_fail(e, "profile counters");
+  }
+  const double real_bytes[4] = {8.0, 4.0, 2.0, 2.0};
+  double b = c.prof.pending_bytes;
+  for (int pr = 0; pr < 4; pr++)
+    for (int k = 0; k < 3; k++) b += (double)w[pr * 3 + k] * (48.0 + 24.0 * k) * real_bytes[pr];
+  launches += c.prof.launches;
+  ms += c.prof.ms;
+  bytes += b;
+  for (int k = 0; k < 12; k++) pairs += (double)w[k];
+  return 0;
+}
+
 fs::NoiseSpec noise_id(uint64_t seed, uint32_t job, uint32_t level, uint32_t sample, bool g5) {
   fs::NoiseSpec n{};
   n.key0 = (uint32_t)(seed & 0xFFFFFFFFull);
@@ -37,6 +102,7 @@ fs::NoiseSpec noise_id(uint64_t seed, uint32_t job, uint32_t level, uint32_t sam
 struct Opts {
   fs::SolveOpts so;
   int tile;
+  int lanes;  // tiles solved at the same time (mlmc_level_trace); 0 = library choice
 };
 
 int resolve_params(Ctx& c, const fs_solve_params* p, int nsys, double m, Opts& o) {
@@ -65,6 +131,8 @@ int resolve_params(Ctx& c, const fs_solve_params* p, int nsys, double m, Opts& o
   if (tile < 0 || tile > fs::MAX_TILE) return c.fail(FS_ERR_ARG, "rhs_tile must be in [0, 64]");
   if (tile == 0) tile = std::min(32, std::max(1, nsys));
   o.tile = tile;
+  if (d.lanes < 0 || d.lanes > 4) return c.fail(FS_ERR_ARG, "lanes must be in [0, 4]");
+  o.lanes = d.lanes;
   return 0;
 }
 
@@ -86,6 +154,65 @@ fs::TileBase* tile_for(Ctx& c, const std::vector<fs::QJob>& jobs, const Opts& o)
   const int N = std::max(o.tile, gmax);
   if (N > fs::MAX_TILE) return nullptr;
   return c.tile(o.so.prec, N, o.so.nr);
+}
+
+// Solves the jobs on `nl` tiles at the same time, one per lane (a stream, tile and host thread
+// of its own). A system's result does not depend on the tile it ran in, so lanes change only
+// the schedule: while one tile runs its FP64 reliable updates, the other's FP16 iterations
+// use the rest of the GPU. Jobs go to the lanes two at a time in turn, so every lane gets the
+// same mix of shifts. Shared inputs (gauge copies, contraction paths) must exist beforehand.
+int run_lanes(Ctx& c, const std::vector<fs::QJob>& jobs, const Opts& o, const fs::QOut& out, int nl, bool canon) {
+  std::vector<std::vector<fs::QJob>> part(nl);
+  for (size_t i = 0; i < jobs.size(); i++) part[(i / 2) % nl].push_back(jobs[i]);
+  cudaEvent_t ev;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e) return c.cuda_fail(e, "lane event");
+  struct EvGuard {
+    cudaEvent_t ev;
+    ~EvGuard() { cudaEventDestroy(ev); }
+  } guard{ev};
+  // the lanes start after the work enqueued on the caller's stream so far
+  if ((e = cudaEventRecord(ev, c.stream))) return c.cuda_fail(e, "lane start");
+  std::vector<Ctx*> L(nl, nullptr);
+  std::vector<fs::TileBase*> T(nl, nullptr);
+  for (int l = 0; l < nl; l++) {
+    if (part[l].empty()) continue;
+    if (!(L[l] = c.lane(l))) return FS_ERR_CUDA;
+    if (c.prof.enabled && !L[l]->prof.enabled)
+      if (prof_reset(*L[l], true)) return c.fail(FS_ERR_CUDA, L[l]->err);
+    if ((e = cudaStreamWaitEvent(L[l]->stream, ev, 0))) return c.cuda_fail(e, "lane start");
+    if (!(T[l] = tile_for(*L[l], part[l], o)))
+      return c.fail(FS_ERR_OOM, "device allocation of a lane's solver tile failed");
+    if (canon && L[l]->ensure_canon(T[l]->N)) return c.fail(FS_ERR_OOM, L[l]->err);
+  }
+  std::vector<int> lrc(nl, 0), nc(nl, 0);
+  std::vector<std::thread> th;
+  for (int l = 0; l < nl; l++) {
+    if (!L[l]) continue;
+    th.emplace_back([&, l] {
+      if (cudaSetDevice(c.device) != cudaSuccess) {
+        lrc[l] = L[l]->fail(FS_ERR_CUDA, "cudaSetDevice in a lane");
+        return;
+      }
+      fs::QOut ol = out;  // result rows and state entries of different lanes are disjoint
+      ol.noconv = &nc[l];
+      lrc[l] = fs::run_queue(L[l], T[l], part[l], o.so, ol);
+    });
+  }
+  for (auto& t : th) t.join();
+  // the caller's stream continues after every lane
+  for (int l = 0; l < nl && !e; l++) {
+    if (!L[l]) continue;
+    e = cudaEventRecord(ev, L[l]->stream);
+    if (!e) e = cudaStreamWaitEvent(c.stream, ev, 0);
+  }
+  for (int l = 0; l < nl; l++) {
+    if (!L[l]) continue;
+    if (lrc[l]) return c.fail(lrc[l], L[l]->err);
+    if (nc[l] && out.noconv) *out.noconv = 1;
+  }
+  if (e) return c.cuda_fail(e, "lane join");
+  return 0;
 }
 
 }  // namespace
@@ -127,19 +254,10 @@ void fs_ctx_destroy(fs_ctx* ctx) {
   if (!ctx) return;
   Ctx& c = ctx->c;
   cudaSetDevice(c.device);
-  cudaStreamSynchronize(c.stream);
-  c.tiles.clear();
-  if (c.gauge64) cudaFree(c.gauge64);
-  if (c.wline) cudaFree(c.wline);
-  for (auto& kv : c.gauge_lo) cudaFree(kv.second);
-  if (c.canon_d) cudaFree(c.canon_d);
-  if (c.canon_h) cudaFreeHost(c.canon_h);
-  for (auto& ev : c.prof.pending) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
-  for (auto& ev : c.prof.pool) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
-  if (c.prof.work_d) cudaFree(c.prof.work_d);
-  if (c.own_stream) cudaStreamDestroy(c.own_stream);
+  release(c);
   delete ctx;
 }
+
 
 const char* fs_last_error(const fs_ctx* ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
 
@@ -365,10 +483,15 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double
       (void)nan;
     }
   }
-  fs::TileBase* T = tile_for(c, jobs, o);
-  if (!T) return c.fail(FS_ERR_OOM, "device allocation of the solver tile failed");
-  if (P->estimator == FS_EST_PRODUCT)
-    if (int rc = c.ensure_canon(T->N)) return rc;
+  // two tiles at once when the job fills both (lanes = 0); a system's result is the same
+  const int nl = o.lanes > 0 ? o.lanes : (nsolve >= 2 * o.tile ? 2 : 1);
+  fs::TileBase* T = nullptr;
+  if (nl == 1) {
+    T = tile_for(c, jobs, o);
+    if (!T) return c.fail(FS_ERR_OOM, "device allocation of the solver tile failed");
+    if (P->estimator == FS_EST_PRODUCT)
+      if (int rc = c.ensure_canon(T->N)) return rc;
+  }
   std::vector<double> res;
   res.assign((size_t)nsolve * 2, 0.0);
   fs::QOut out;
@@ -379,7 +502,12 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double
   out.states = &st;
   out.noconv = &noconv;
   out.canon_chain_base = 0;
-  if (int rc = fs::run_queue(&c, T, jobs, o.so, out)) return rc;
+  if (nl > 1) {
+    if (int rc = fs::ensure_wline(&c, 1 << P->p, P->p)) return rc;
+    if (int rc = run_lanes(c, jobs, o, out, nl, P->estimator == FS_EST_PRODUCT)) return rc;
+  } else if (int rc = fs::run_queue(&c, T, jobs, o.so, out)) {
+    return rc;
+  }
   for (int l = 0; l <= L; l++) {
     for (int s = 0; s < P->n_samples[l]; s++) {
       const int si = solve_off[l] + s * (l < L ? 2 : 1);
@@ -541,21 +669,9 @@ int fs_profile_enable(fs_ctx* ctx, int enable) {
   if (!ctx) return FS_ERR_ARG;
   Ctx& c = ctx->c;
   if (int rc = set_device(c)) return rc;
-  cudaError_t e = cudaStreamSynchronize(c.stream);
-  if (e) return c.cuda_fail(e, "fs_profile_enable");
-  for (auto& ev : c.prof.pending) c.prof.pool.push_back(ev);
-  c.prof.pending.clear();
-  c.prof.launches = 0;
-  c.prof.ms = 0;
-  c.prof.bytes = 0;
-  c.prof.pending_bytes = 0;
-  if (!c.prof.work_d) {
-    e = cudaMalloc(&c.prof.work_d, 12 * sizeof(unsigned long long));
-    if (e) return c.cuda_fail(e, "profile counters");
-  }
-  e = cudaMemset(c.prof.work_d, 0, 12 * sizeof(unsigned long long));
-  if (e) return c.cuda_fail(e, "profile counters");
-  c.prof.enabled = enable != 0;
+  if (int rc = prof_reset(c, enable != 0)) return rc;
+  for (auto& l : c.lanes)
+    if (prof_reset(*l, enable != 0)) return c.fail(FS_ERR_CUDA, l->err);
   return FS_OK;
 }
 
@@ -563,31 +679,15 @@ int fs_profile_read(fs_ctx* ctx, long long* launches, double* total_ms, double* 
   if (!ctx) return FS_ERR_ARG;
   Ctx& c = ctx->c;
   if (int rc = set_device(c)) return rc;
-  cudaError_t e = cudaStreamSynchronize(c.stream);
-  if (e) return c.cuda_fail(e, "fs_profile_read");
-  for (auto& ev : c.prof.pending) {
-    float ms = 0;
-    if (cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) c.prof.ms += ms;
-    c.prof.pool.push_back(ev);
-  }
-  c.prof.pending.clear();
-  unsigned long long w[12] = {0};
-  if (c.prof.work_d) {
-    e = cudaMemcpy(w, c.prof.work_d, sizeof(w), cudaMemcpyDeviceToHost);
-    if (e) return c.cuda_fail(e, "profile counters");
-  }
-  const double real_bytes[4] = {8.0, 4.0, 2.0, 2.0};
-  double b = c.prof.pending_bytes;
-  for (int pr = 0; pr < 4; pr++)
-    for (int k = 0; k < 3; k++) b += (double)w[pr * 3 + k] * (48.0 + 24.0 * k) * real_bytes[pr];
-  if (launches) *launches = c.prof.launches;
-  if (total_ms) *total_ms = c.prof.ms;
+  long long n = 0;
+  double ms = 0, b = 0, pairs = 0;
+  if (int rc = prof_collect(c, n, ms, b, pairs)) return rc;
+  for (auto& l : c.lanes)
+    if (prof_collect(*l, n, ms, b, pairs)) return c.fail(FS_ERR_CUDA, l->err);
+  if (launches) *launches = n;
+  if (total_ms) *total_ms = ms;
   if (bytes) *bytes = b;
-  if (site_systems) {
-    double n = 0.0;
-    for (int k = 0; k < 12; k++) n += (double)w[k];
-    *site_systems = n;
-  }
+  if (site_systems) *site_systems = pairs;
   return FS_OK;
 }
 

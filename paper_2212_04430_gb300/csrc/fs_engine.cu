@@ -85,7 +85,33 @@ int Ctx::ensure_canon_host(size_t nvec) {
 size_t Ctx::device_bytes() const {
   size_t b = extra_bytes + canon_cap * (size_t)g.V * 24 * sizeof(double);
   for (auto& kv : tiles) b += kv.second->bytes;
+  for (auto& l : lanes) b += l->device_bytes();
   return b;
+}
+
+Ctx* Ctx::lane(int i) {
+  while ((int)lanes.size() <= i) {
+    std::unique_ptr<Ctx> l(new Ctx());
+    l->device = device;
+    l->nsm = nsm;
+    l->g = g;
+    l->shared = true;
+    cudaError_t e = cudaStreamCreateWithFlags(&l->own_stream, cudaStreamNonBlocking);
+    if (e) {
+      cuda_fail(e, "lane stream");
+      return nullptr;
+    }
+    l->stream = l->own_stream;
+    lanes.push_back(std::move(l));
+  }
+  Ctx* l = lanes[i].get();
+  l->have_gauge = have_gauge;
+  l->gauge64 = gauge64;
+  l->gauge_lo = gauge_lo;
+  l->wline = wline;
+  l->wline_mask = wline_mask;
+  l->wline_cap = 0;  // never reallocated or freed by the lane
+  return l;
 }
 
 // ---------------------------------------------------------------------------
@@ -491,6 +517,33 @@ TileBase* Ctx::tile(int prec, int N, int nr) {
   return raw;
 }
 
+int ensure_wline(Ctx* c, int pmask, int pmax) {
+  const int wmask = pmask & ~1;
+  if (!wmask || c->wline_mask == wmask) return 0;
+  if (c->shared) return c->fail(1, "contraction paths of a lane must be built by its owner");
+  cudaError_t e;
+  // the path products depend on the gauge field and the displacements only: built once
+  const size_t need_w = (size_t)__builtin_popcount(wmask) * 18 * 2 * c->g.Vh * sizeof(double);
+  if (need_w > c->wline_cap) {
+    if (c->wline) {
+      cudaStreamSynchronize(c->stream);
+      cudaFree(c->wline);
+      c->extra_bytes -= c->wline_cap;
+      c->wline = nullptr;
+      c->wline_cap = 0;
+    }
+    if ((e = cudaMalloc((void**)&c->wline, need_w))) return c->cuda_fail(e, "contraction path products");
+    c->wline_cap = need_w;
+    c->extra_bytes += need_w;
+  }
+  transport_kernel<<<(2 * c->g.Vh + 255) / 256, 256, 0, c->stream>>>(c->wline, (const double*)c->gauge64, c->g,
+                                                                    wmask, pmax);
+  note_launch();
+  if ((e = cudaGetLastError())) return c->cuda_fail(e, "contraction path products");
+  c->wline_mask = wmask;
+  return 0;
+}
+
 int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, const double* gamma,
                   const std::vector<int>& plist, std::vector<double>& result, int rows) {
   const int np = (int)plist.size();
@@ -509,28 +562,7 @@ int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, c
   for (int k = 1; k < np; k++)
     if (plist[k] <= plist[k - 1]) return c->fail(1, "displacements must be increasing");
   cudaError_t e;
-  const int wmask = pmask & ~1;
-  if (wmask && c->wline_mask != wmask) {
-    // the path products depend on the gauge field and the displacements only: built once
-    const size_t need_w = (size_t)__builtin_popcount(wmask) * 18 * 2 * c->g.Vh * sizeof(double);
-    if (need_w > c->wline_cap) {
-      if (c->wline) {
-        cudaStreamSynchronize(c->stream);
-        cudaFree(c->wline);
-        c->extra_bytes -= c->wline_cap;
-        c->wline = nullptr;
-        c->wline_cap = 0;
-      }
-      if ((e = cudaMalloc((void**)&c->wline, need_w))) return c->cuda_fail(e, "contraction path products");
-      c->wline_cap = need_w;
-      c->extra_bytes += need_w;
-    }
-    transport_kernel<<<(2 * c->g.Vh + 255) / 256, 256, 0, c->stream>>>(c->wline, (const double*)c->gauge64, c->g,
-                                                                      wmask, pmax);
-    note_launch();
-    if ((e = cudaGetLastError())) return c->cuda_fail(e, "contraction path products");
-    c->wline_mask = wmask;
-  }
+  if (int rc = ensure_wline(c, pmask, pmax)) return rc;
   a.x_e = T->x_hi; a.x_o = T->x_o; a.wline = c->wline; a.spec = T->spec_d;
   for (int k = 0; k < 32; k++) a.gamma[k] = gamma[k];
   // detect a monomial Gamma (one entry per row, each +-1 or +-i): applied as a permutation

@@ -122,7 +122,18 @@ struct Ctx {
   int ensure_canon(size_t nvec);
   int ensure_canon_host(size_t nvec);
   size_t device_bytes() const;
+  // Lanes: contexts of their own (stream, tiles, staging, profile) that share this context's
+  // gauge copies and contraction paths (read-only while they run), so that tiles in different
+  // lanes can run at the same time. lane(i) creates lane i on first use and refreshes the shared
+  // pointers; nullptr on failure (message in err).
+  std::vector<std::unique_ptr<Ctx>> lanes;
+  bool shared = false;  // a lane: the gauge copies and contraction paths are not its own
+  Ctx* lane(int i);
 };
+
+// The contraction's straight z-paths W(x, x + q z) for the displacements q > 0 in pmask,
+// built once per gauge field (fs_engine.cu); 0 or an error code (message in c->err).
+int ensure_wline(Ctx* c, int pmask, int pmax);
 
 // One system to solve.
 struct SysSpec {

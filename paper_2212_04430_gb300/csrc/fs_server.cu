@@ -61,7 +61,8 @@ size_t estimate(const SJob& j) {
   const size_t stage = j.P.estimator == FS_EST_PRODUCT ? (size_t)tile * V * 24 * 8 : 0;
   const size_t contract = (size_t)tile * ((2 * Vh + 255) / 256) * 2 * 8 + (64u << 10) +
                           (j.P.p > 0 ? V * 18 * 8 : 0);  // partial sums + the path products
-  return tile_bytes + gauge + stage + contract + (32u << 20);
+  const size_t lanes = (size_t)std::max(1, j.P.solve.lanes);
+  return lanes * (tile_bytes + stage) + gauge + contract + (32u << 20);
 }
 
 }  // namespace
@@ -198,6 +199,8 @@ int fs_server_submit(fs_server* s, const fs_job* job, uint64_t* ticket) {
   j->nsamp.assign(P.n_samples, P.n_samples + P.nlev);
   j->gamma.assign(P.gamma, P.gamma + 32);
   j->P = P;
+  // the server overlaps whole jobs; one tile per job unless the caller asked for more lanes
+  if (j->P.solve.lanes == 0) j->P.solve.lanes = 1;
   j->P.sigma = j->sigma.data();
   j->P.n_samples = j->nsamp.data();
   j->P.gamma = j->gamma.data();

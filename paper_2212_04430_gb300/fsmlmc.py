@@ -39,7 +39,7 @@ class FsError(RuntimeError):
 class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("prec", ctypes.c_int),
                 ("rhs_tile", ctypes.c_int), ("link_compress", ctypes.c_int), ("delta", ctypes.c_double),
-                ("verify", ctypes.c_int), ("fallback_iter", ctypes.c_int)]
+                ("verify", ctypes.c_int), ("fallback_iter", ctypes.c_int), ("lanes", ctypes.c_int)]
 
 
 class SysStats(ctypes.Structure):
@@ -139,7 +139,8 @@ def _real(a, shape=None):
     return a
 
 
-def _params(prec="f64", tol=0.0, max_iter=0, rhs_tile=0, link_compress=18, delta=0.0, verify=0, fallback_iter=0):
+def _params(prec="f64", tol=0.0, max_iter=0, rhs_tile=0, link_compress=18, delta=0.0, verify=0, fallback_iter=0,
+            lanes=0):
     p = SolveParams()
     p.tol = tol
     p.max_iter = max_iter
@@ -149,6 +150,7 @@ def _params(prec="f64", tol=0.0, max_iter=0, rhs_tile=0, link_compress=18, delta
     p.delta = delta
     p.verify = int(verify)
     p.fallback_iter = int(fallback_iter)
+    p.lanes = int(lanes)
     return p
 
 

@@ -311,6 +311,31 @@ def test_product_chain_and_split_even_in_mixed_tiles():
     ctx.close()
 
 
+@pytest.mark.parametrize("est", ["diff", "product"])
+def test_lanes_give_identical_results(est):
+    """Tiles solved at the same time (lanes, each on a stream and host thread of its own,
+    sharing the gauge copies and the contraction paths) give exactly the per-sample values,
+    traces, variances and per-system iteration counts of a single tile: a system's result
+    does not depend on its tile, so lanes change only the schedule."""
+    dims = (4, 4, 4, 8)
+    u = inputs.gauge_field(dims, "smooth", seed=23, eps=0.4)
+    sig = [0.01, 0.1, 0.6]
+    g = pkg.gamma_matrix("g3")
+    n = [12, 10, 9]
+    ctx = make_ctx(dims, u)
+    kw = dict(prec="f16", tol=1e-8, rhs_tile=8)
+    one = ctx.mlmc_level_trace(-0.3, sig, g, 2, n, seed=6, job=3, estimator=est, lanes=1, **kw)
+    assert one["rc"] == 0
+    for nl in (2, 3):
+        many = ctx.mlmc_level_trace(-0.3, sig, g, 2, n, seed=6, job=3, estimator=est, lanes=nl, **kw)
+        assert many["rc"] == 0
+        for lev in range(3):
+            assert np.array_equal(one["samples"][lev], many["samples"][lev]), (nl, lev)
+        assert np.array_equal(one["trace"], many["trace"]) and np.array_equal(one["var"], many["var"])
+        assert [s["iters"] for s in one["stats"]] == [s["iters"] for s in many["stats"]]
+    ctx.close()
+
+
 def test_contraction_with_a_dense_gamma():
     """A Gamma that is not a Clifford product (dense complex 4x4) takes the general path of
     the contraction; Clifford products take the permutation path (the tests above)."""
