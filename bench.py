@@ -331,7 +331,8 @@ def config_of(args, w):
     return {"workload": w["name"], "lattice": "x".join(map(str, w["dims"])), "levels": len(w["sigmas"]),
             "vectors_per_level_per_step": args.vectors or w["vectors"], "estimator": w["estimator"],
             "rhs_tile": args.tile or w["tile"], "storage": w["prec"], "links": "%d-real" % w["link"],
-            "tol": w["tol"], "delta": args.delta or "library", "l2": "working set above L2 (no flush needed)"}
+            "tol": w["tol"], "delta": args.delta or "library", "lanes": args.lanes or "library",
+            "l2": "working set above L2 (no flush needed)"}
 
 
 # --------------------------------------------------------------------------- serving
@@ -431,6 +432,8 @@ def main():
     ap.add_argument("--delta", type=float, default=0.0,
                     help="reliable-update trigger factor (0: library choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lanes", type=int, default=0, help="tiles solved at once (0: library choice)")
+    ap.add_argument("--roof-steps", type=int, default=2, help="single-lane steps timed for the roofline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=8.0, help="seconds of oracle work per reference step")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -466,9 +469,10 @@ def main():
     kw = dict(prec=w["prec"], tol=w["tol"], rhs_tile=tile, link_compress=w["link"], delta=args.delta)
     n = [nvec] * len(w["sigmas"])
 
-    def step(job):
+    def step(job, lanes=None):
         out = ctx.mlmc_level_trace(w["m"], w["sigmas"], gam, w["p"], n, seed=w["noise_seed"],
-                                   job=job, estimator=w["estimator"], **kw)
+                                   job=job, estimator=w["estimator"],
+                                   lanes=args.lanes if lanes is None else lanes, **kw)
         if out["rc"] != 0:
             raise RuntimeError("solver did not converge: %s" % ctx.last_error())
         return out
@@ -479,8 +483,7 @@ def main():
         step(job0 + k)
     torch.cuda.synchronize()
 
-    # ---- device-resident timed region
-    ctx.profile_enable(True)
+    # ---- device-resident timed region (the library's own launch shape: two lanes by default)
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     barrier(ws)
@@ -501,8 +504,6 @@ def main():
     ms = e0.elapsed_time(e1)
     launches = pkg.fsmlmc.fs_kernel_launches() - l0
     clk = clocks.stop()
-    prof = ctx.profile_read()
-    ctx.profile_enable(False)
     value, ms_max, total_solves = whole_job_rate(ms, solves_per_step * args.steps, ws)
 
     # ---- end to end through the public API with host buffers
@@ -526,6 +527,15 @@ def main():
         e2e = {"value": total_solves / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    # ---- roofline pass: the same step on one lane, every hop launch timed with CUDA events on
+    # its stream (with two lanes a launch shares the GPU with the other lane's kernels, and its
+    # duration would measure that sharing rather than the kernel)
+    ctx.profile_enable(True)
+    for k in range(args.roof_steps):
+        step(job0 + 3000 + k, lanes=1)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+
     peaks, peak_kind = load_peaks()
     roof = None
     if prof["launches"] > 0 and prof["ms"] > 0:
@@ -536,7 +546,9 @@ def main():
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                 "kernel": "hop_kernel (even-odd Wilson hopping term, inner precision)",
                 "launches": prof["launches"], "avg_launch_us": per_launch_s * 1e6,
-                "algorithmic_bytes_per_launch": bytes_per_launch, "peak_source": peak_kind}
+                "algorithmic_bytes_per_launch": bytes_per_launch, "peak_source": peak_kind,
+                "pass": "hop launches of %d single-lane steps of the same workload, timed with CUDA events on "
+                        "their stream" % args.roof_steps}
         ratio = hop_traffic_ratio(args.workload)
         if ratio is not None:
             roof["traffic"] = ratio * bytes_per_launch
