@@ -433,6 +433,7 @@ def main():
                     help="reliable-update trigger factor (0: library choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lanes", type=int, default=0, help="tiles solved at once (0: library choice)")
+    ap.add_argument("--no-fp64-baseline", action="store_true", help="skip the FP64 single-RHS GPU solver")
     ap.add_argument("--roof-steps", type=int, default=2, help="single-lane steps timed for the roofline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=8.0, help="seconds of oracle work per reference step")
@@ -560,6 +561,29 @@ def main():
         roof["second_roof"] = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s",
                                "frac": alu / alu_peak, "peak_source": "nominal FP32 unit count x max clock"}
 
+    # ---- the plain FP64 single-RHS GPU solver (the same library in FP64 with one system per tile
+    # and one lane: no reduced-precision storage, no batching) on a sample of the same job
+    fp64 = None
+    if not args.no_fp64_baseline and rank == 0:
+        nb = max(1, nvec // 8)
+        n64 = [nb] * len(w["sigmas"])
+        solves64 = 2 * nb * (len(w["sigmas"]) - 1) + nb
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        out64 = ctx.mlmc_level_trace(w["m"], w["sigmas"], gam, w["p"], n64, seed=w["noise_seed"],
+                                     job=job0 + 4000, estimator=w["estimator"], prec="f64", tol=w["tol"],
+                                     rhs_tile=1, link_compress=18, lanes=1)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        if out64["rc"] != 0:
+            raise RuntimeError("FP64 solver did not converge: %s" % ctx.last_error())
+        v64 = solves64 / (g0.elapsed_time(g1) / 1e3)
+        fp64 = {"value": v64, "unit": "solves/s", "value_over_this": value / v64,
+                "sample": "%d Z4 vectors per level (%d solves) of the same job, FP64 storage and arithmetic, "
+                          "one system per tile, one lane, tol %g" % (nb, solves64, w["tol"]),
+                "mean_iters": float(np.mean([st["iters"] for st in out64["stats"]]))}
+
     pipeline = None
     if not args.no_pipeline and rank == 0:
         pipeline = run_pipeline(pkg, ctx, w, kw)
@@ -589,6 +613,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_of(args, w), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "serving": serving, "pipeline": pipeline,
+                "fp64_single_rhs": fp64,
                 "solver": {"mean_iters": float(np.mean(iters)) if iters else None,
                            "max_iters": int(max(iters)) if iters else None,
                            "mean_reliable_updates": float(np.mean(updates)) if updates else None,

@@ -131,6 +131,13 @@ int fs_set_stream(fs_ctx* ctx, void* stream);
 /* Device memory currently held by ctx, in bytes. */
 size_t fs_ctx_device_bytes(const fs_ctx* ctx);
 
+/* The tile size the autotuner chose for storage precision `prec` and `link_compress` on this
+   context, or 0 if it has not run. A library addition (the paper has no counterpart): when a
+   call leaves fs_solve_params.rhs_tile = 0 and has at least 16 systems, the first such call
+   per precision and link format times a BiCGStab iteration per system on tiles of 8, 16, 32
+   and 64 systems (at most the call's system count) and keeps the fastest for the context. */
+int fs_tuned_tile(const fs_ctx* ctx, int prec, int link_compress);
+
 /* Upload the gauge field U (host, [4][V][3][3][2] doubles). Builds the FP64 copy used
  * for true residuals and contractions and the lower-precision copies on demand.
  * FS_ERR_INPUT if U holds a non-finite value. */

@@ -133,6 +133,12 @@ int resolve_params(Ctx& c, const fs_solve_params* p, int nsys, double m, Opts& o
   o.tile = tile;
   if (d.lanes < 0 || d.lanes > 4) return c.fail(FS_ERR_ARG, "lanes must be in [0, 4]");
   o.lanes = d.lanes;
+  if (d.rhs_tile == 0 && nsys >= 16 && c.have_gauge) {
+    // library choice with enough systems to matter: the autotuned tile (measured once)
+    if (int rc = set_device(c)) return rc;
+    const int t = fs::autotune_tile(&c, o.so, std::min(nsys, fs::MAX_TILE));
+    if (t > 0) o.tile = t;
+  }
   return 0;
 }
 
@@ -268,6 +274,13 @@ int fs_set_stream(fs_ctx* ctx, void* stream) {
 }
 
 size_t fs_ctx_device_bytes(const fs_ctx* ctx) { return ctx ? ctx->c.device_bytes() : 0; }
+
+int fs_tuned_tile(const fs_ctx* ctx, int prec, int link_compress) {
+  if (!ctx) return 0;
+  const int nr = prec == FS_PREC_F64 ? 18 : (link_compress == 0 ? 18 : link_compress);
+  auto it = ctx->c.tuned_tile.find(prec * 100 + nr);
+  return it == ctx->c.tuned_tile.end() ? 0 : it->second;
+}
 
 int fs_set_gauge(fs_ctx* ctx, const double* U) {
   if (!ctx) return FS_ERR_ARG;

@@ -87,6 +87,83 @@ int run_cg(Ctx* c, TileBase* T, const std::vector<int>& slots, const SolveOpts& 
 
 }  // namespace
 
+// Tile autotuner. The tile size sets how many systems share each site's links in the hop
+// kernels, which kernel variant runs (the persistent kernel for 32-system chunks, the
+// prefetch kernel otherwise) and how many blocks the BLAS steps launch; the FP64 reliable
+// updates run per system and do not depend on it. So the candidates (8, 16, 32, 64 systems)
+// are compared by the time of a BiCGStab iteration per system: each tile is filled with Z4
+// right-hand sides through the normal initialisation, iterated 4 times untimed and 8 times
+// timed with CUDA events (the graph path the solver uses). A candidate that is not the best so
+// far is released at once, and every slot of the chosen tile is left idle.
+int autotune_tile(Ctx* c, const SolveOpts& o, int nmax) {
+  const int key = o.prec * 100 + o.nr;
+  auto it = c->tuned_tile.find(key);
+  if (it != c->tuned_tile.end()) return std::min(it->second, nmax);
+  static const int cand[] = {8, 16, 32, 64};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return 0;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return 0; }
+  SolveOpts to = o;
+  to.max_iter = 1 << 20;  // no system stops during the trial
+  to.delta = 0.0;         // and none takes a reliable update (per system, the same for every tile)
+  double best_t = 0.0;
+  int best = 0;
+  for (int N : cand) {
+    if (N > nmax) break;
+    TileBase* T = c->tile(o.prec, N, o.nr);
+    if (!T) break;  // no room for a tile this large
+    std::vector<int> all(N);
+    for (int j = 0; j < N; j++) {
+      all[j] = j;
+      init_state(T->st_h[j], 0.1, to);
+      NoiseSpec n{};
+      n.key0 = 0x5EEDu;
+      n.job = 0xFFFFFFFFu;
+      n.sample = (uint32_t)j;
+      n.flags = NOISE_VALID | NOISE_RHS;
+      T->spec_h[j] = n;
+    }
+    cudaError_t e = upload_slots(c, T, all);
+    if (!e) e = T->enqueue_noise();
+    if (!e) e = T->enqueue_init();
+    if (!e) e = T->enqueue_iters(4);  // eager (first use) or graph, untimed
+    if (!e) e = T->enqueue_iters(4);
+    if (!e) e = cudaEventRecord(e0, c->stream);
+    if (!e) e = T->enqueue_iters(4);
+    if (!e) e = T->enqueue_iters(4);
+    if (!e) e = cudaEventRecord(e1, c->stream);
+    if (!e) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+    // leave every slot idle for the solver
+    for (int j = 0; j < N; j++) {
+      memset(&T->st_h[j], 0, sizeof(SysState));
+      T->st_h[j].status = SYS_IDLE;
+    }
+    if (!e) e = upload_slots(c, T, all);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      c->cuda_fail(e, "tile autotuner");
+      return 0;
+    }
+    const double per = ms / (8.0 * N);
+    // keep only the best tile so far: at most two candidates hold device memory at once
+    if (best == 0 || per < best_t) {
+      if (best) c->tiles.erase(((long long)o.prec * 1000 + best) * 100 + o.nr);
+      best_t = per;
+      best = N;
+    } else {
+      c->tiles.erase(((long long)o.prec * 1000 + N) * 100 + o.nr);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best > 0) c->tuned_tile[key] = best;
+  return best;
+}
+
 int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpts& o, const QOut& out) {
   const int N = T->N;
   for (const QJob& q : jobs)

@@ -129,6 +129,7 @@ struct Ctx {
   std::vector<std::unique_ptr<Ctx>> lanes;
   bool shared = false;  // a lane: the gauge copies and contraction paths are not its own
   Ctx* lane(int i);
+  std::map<int, int> tuned_tile;  // autotuned systems per tile, key: prec * 100 + nr
 };
 
 // The contraction's straight z-paths W(x, x + q z) for the displacements q > 0 in pmask,
@@ -180,6 +181,10 @@ struct QOut {
 
 // Continuous batching of the jobs over the slots of tile T (fs_driver.cu).
 int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpts& o, const QOut& out);
+
+// Tile autotuner (fs_driver.cu): systems per tile for (o.prec, o.nr) on this lattice, at most
+// nmax; measured once per context and format, then cached in c->tuned_tile. 0 on failure.
+int autotune_tile(Ctx* c, const SolveOpts& o, int nmax);
 
 // Contractions over the solutions held in a tile.
 int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, const double* gamma,

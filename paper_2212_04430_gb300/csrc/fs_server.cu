@@ -201,6 +201,9 @@ int fs_server_submit(fs_server* s, const fs_job* job, uint64_t* ticket) {
   j->P = P;
   // the server overlaps whole jobs; one tile per job unless the caller asked for more lanes
   if (j->P.solve.lanes == 0) j->P.solve.lanes = 1;
+  // the admission estimate assumes at most 32-system tiles where the caller left the choice
+  // open; jobs are not autotuned (a trial holds candidate tiles beside the admitted jobs)
+  if (j->P.solve.rhs_tile == 0) j->P.solve.rhs_tile = std::max(1, std::min(32, fs_mlmc_num_solves(&P)));
   j->P.sigma = j->sigma.data();
   j->P.n_samples = j->nsamp.data();
   j->P.gamma = j->gamma.data();

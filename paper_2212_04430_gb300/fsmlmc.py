@@ -26,7 +26,7 @@ EXPORTS = ["fs_ctx_create", "fs_ctx_destroy", "fs_last_error", "fs_set_stream", 
            "variance_sample", "fs_noise_codes", "fs_profile_enable", "fs_profile_read", "fs_kernel_launches",
            "wilson_dslash_noalloc", "fs_server_create", "fs_server_submit", "fs_server_poll",
            "fs_server_stats", "fs_server_destroy", "fs_interp_variances", "fs_select_shifts",
-           "fs_sample_allocation", "fs_eval_grid"]
+           "fs_sample_allocation", "fs_eval_grid", "fs_tuned_tile"]
 JOB_MAX_LEVELS = 16
 
 
@@ -95,6 +95,7 @@ def load_library(path=LIB_PATH):
         "fs_last_error": (ctypes.c_char_p, [P]),
         "fs_set_stream": (I, [P, P]),
         "fs_ctx_device_bytes": (ctypes.c_size_t, [P]),
+        "fs_tuned_tile": (I, [P, I, I]),
         "fs_set_gauge": (I, [P, dp]),
         "wilson_dslash": (I, [P, D, D, dp, dp, I, I, I]),
         "shifted_solve": (I, [P, D, dp, I, dp, I, dp, ctypes.POINTER(SolveParams), ctypes.POINTER(SysStats)]),
@@ -193,6 +194,11 @@ class Context:
 
     def device_bytes(self):
         return int(self.lib.fs_ctx_device_bytes(self.h))
+
+    def tuned_tile(self, prec="f16", link_compress=18):
+        """Systems per tile the autotuner chose for this precision and link format (0: not run)."""
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        return int(self.lib.fs_tuned_tile(self.h, p, int(link_compress)))
 
     def fs_set_gauge(self, U):
         u = _real(U)

@@ -336,6 +336,30 @@ def test_lanes_give_identical_results(est):
     ctx.close()
 
 
+def test_autotuned_tile():
+    """rhs_tile = 0 lets the library pick the tile: the autotuner times a BiCGStab iteration per
+    system on the candidate tiles once per precision and link format, and the chosen tile gives
+    exactly the results of the same call with that tile given explicitly."""
+    dims = (4, 4, 4, 8)
+    u = inputs.gauge_field(dims, "smooth", seed=29, eps=0.4)
+    sig = [0.02, 0.3]
+    g = pkg.gamma_matrix("g5")
+    n = [10, 12]
+    ctx = make_ctx(dims, u)
+    assert ctx.tuned_tile("f16", 12) == 0
+    kw = dict(prec="f16", tol=1e-8, link_compress=12)
+    auto = ctx.mlmc_level_trace(-0.3, sig, g, 1, n, seed=4, job=1, rhs_tile=0, **kw)
+    t = ctx.tuned_tile("f16", 12)
+    assert t in (8, 16, 32) and auto["rc"] == 0  # 32 solves: the 64-system tile is not a candidate
+    fixed = ctx.mlmc_level_trace(-0.3, sig, g, 1, n, seed=4, job=1, rhs_tile=t, lanes=1, **kw)
+    for lev in range(2):
+        assert np.array_equal(auto["samples"][lev], fixed["samples"][lev]), lev
+    # measured once: a second call keeps the choice
+    ctx.mlmc_level_trace(-0.3, sig, g, 1, n, seed=4, job=2, rhs_tile=0, **kw)
+    assert ctx.tuned_tile("f16", 12) == t
+    ctx.close()
+
+
 def test_contraction_with_a_dense_gamma():
     """A Gamma that is not a Clifford product (dense complex 4x4) takes the general path of
     the contraction; Clifford products take the permutation path (the tests above)."""
