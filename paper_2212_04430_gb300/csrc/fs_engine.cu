@@ -129,6 +129,13 @@ class Tile : public TileBase {
   Shape sh1{};
   Launch L1{};
   Launch LW{};   // system-major work-list launches: resident blocks sweep (selected system, chunk) items
+  // the FP64 hop's work list: three resident 128-site blocks per SM (its launch bounds), since
+  // items go to blocks in turn and a block beyond the resident ones would run its share last
+  Launch lwh() const {
+    Launch l = LW;
+    l.grid_x = std::max(1, 3 * c->nsm);
+    return l;
+  }
   Launch LH{};   // hopping kernels: one site chunk per block, so resident blocks sweep the
                  // lattice in order and neighbour spinors are re-read from L2, not DRAM
   int ngroups = 0;
@@ -300,7 +307,7 @@ class Tile : public TileBase {
     cudaError_t e;
     // bhat_e = z_e - D_eo A^-1 z_o, ||bhat||^2
     if ((e = launch_hop<double>(COEF_PREP, DOT_NORM, 18, hop(bhat, z_o, z_e, nullptr, nullptr, pa, 0, MASK_INIT,
-                                                              false, true, true), LW))) return e;
+                                                              false, true, true), lwh()))) return e;
     if ((e = launch_blas<Ts>(OP_NORM64, blas(MASK_INIT, z_e, pb, false, true), LW))) return e;
     if ((e = launch_blas<Ts>(OP_NORM64, blas(MASK_INIT, z_o, pc, false, true), LW))) return e;
     if ((e = launch_blas<Ts>(OP_ZEROX, blas(MASK_INIT, nullptr, nullptr, false, true), LW))) return e;
@@ -333,10 +340,10 @@ class Tile : public TileBase {
     if ((e = launch_blas<Ts>(OP_ACCX, blas(MASK_UPDATE, nullptr, nullptr, true, true), LW))) return e;
     if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
                                 hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, MASK_UPDATE, true, true,
-                                    true), LW)))
+                                    true), lwh())))
       return e;
     if ((e = launch_hop<double>(COEF_TRUERES, DOT_NORM, 18,
-                                hop(r_hi, tmp64, x_hi, bhat, nullptr, pa, 0, MASK_UPDATE, true, true, true), LW)))
+                                hop(r_hi, tmp64, x_hi, bhat, nullptr, pa, 0, MASK_UPDATE, true, true, true), lwh())))
       return e;
     if ((e = fin(FIN_TRUE, MASK_UPDATE, pa))) return e;
     if ((e = launch_blas<Ts>(OP_SETR, blas(MASK_UPDATE, r_hi, pa, true, true), LW))) return e;
@@ -379,7 +386,7 @@ class Tile : public TileBase {
     LW.stream = c->stream;
     // x_o = A^-1 (z_o - D_oe x_e)
     return launch_hop<double>(COEF_RECON, DOT_NONE, 18,
-                              hop(x_o, x_hi, z_o, nullptr, nullptr, nullptr, 1, MASK_HARVEST, false, true, true), LW);
+                              hop(x_o, x_hi, z_o, nullptr, nullptr, nullptr, 1, MASK_HARVEST, false, true, true), lwh());
   }
 
   cudaError_t enqueue_verify() override {
@@ -387,10 +394,10 @@ class Tile : public TileBase {
     LW.stream = c->stream;
     cudaError_t e;
     if ((e = launch_hop<double>(COEF_FULLRES, DOT_NORM, 18,
-                                hop(r_hi, x_o, x_hi, z_e, nullptr, pa, 0, MASK_HARVEST, false, true, true), LW)))
+                                hop(r_hi, x_o, x_hi, z_e, nullptr, pa, 0, MASK_HARVEST, false, true, true), lwh())))
       return e;
     if ((e = launch_hop<double>(COEF_FULLRES, DOT_NORM, 18,
-                                hop(tmp64, x_hi, x_o, z_o, nullptr, pb, 1, MASK_HARVEST, false, true, true), LW)))
+                                hop(tmp64, x_hi, x_o, z_o, nullptr, pb, 1, MASK_HARVEST, false, true, true), lwh())))
       return e;
     return fin(FIN_VERIFY, MASK_HARVEST, pa, pb);
   }
@@ -433,10 +440,10 @@ class Tile : public TileBase {
     cudaError_t e;
     if ((e = cg_op<CG_G5>(mask))) return e;
     if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
-                                hop(tmp64, cg_g, nullptr, nullptr, nullptr, nullptr, 1, mask, false, true, true), LW)))
+                                hop(tmp64, cg_g, nullptr, nullptr, nullptr, nullptr, 1, mask, false, true, true), lwh())))
       return e;
     if ((e = launch_hop<double>(COEF_MHAT, DOT_NONE, 18,
-                                hop(cg_w, tmp64, cg_g, nullptr, nullptr, nullptr, 0, mask, false, true, true), LW)))
+                                hop(cg_w, tmp64, cg_g, nullptr, nullptr, nullptr, 0, mask, false, true, true), lwh())))
       return e;
     return cg_op<CG_R>(mask, part);
   }
@@ -444,10 +451,10 @@ class Tile : public TileBase {
   cudaError_t cg_true_residual(int mask, double* part) {
     cudaError_t e;
     if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
-                                hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, mask, false, true, true), LW)))
+                                hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, mask, false, true, true), lwh())))
       return e;
     return launch_hop<double>(COEF_TRUERES, DOT_NORM, 18,
-                              hop(r_hi, tmp64, x_hi, bhat, nullptr, part, 0, mask, false, true, true), LW);
+                              hop(r_hi, tmp64, x_hi, bhat, nullptr, part, 0, mask, false, true, true), lwh());
   }
   cudaError_t enqueue_cg_init() override {
     L1.stream = c->stream;
@@ -464,10 +471,10 @@ class Tile : public TileBase {
     cudaError_t e;
     // q = M p, alpha = <r, r> / ||q||^2
     if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
-                                hop(tmp64, cg_p, nullptr, nullptr, nullptr, nullptr, 1, MASK_CG, false, true, true), LW)))
+                                hop(tmp64, cg_p, nullptr, nullptr, nullptr, nullptr, 1, MASK_CG, false, true, true), lwh())))
       return e;
     if ((e = launch_hop<double>(COEF_MHAT, DOT_NORM, 18,
-                                hop(cg_q, tmp64, cg_p, nullptr, nullptr, pa, 0, MASK_CG, false, true, true), LW)))
+                                hop(cg_q, tmp64, cg_p, nullptr, nullptr, pa, 0, MASK_CG, false, true, true), lwh())))
       return e;
     if ((e = fin(FIN_CG_ALPHA, MASK_CG, pa))) return e;
     if ((e = cg_op<CG_XS>(MASK_CG, pa))) return e;   // x += alpha p, s -= alpha q

@@ -429,8 +429,11 @@ __device__ __forceinline__ int selected_list(const SysState* st, int N, int mask
 // with 18-real links) for latency hiding; FP32 storage needs ~128 registers for its
 // float4 spinors and keeps 2 blocks; FP64 is ALU bound.
 // WL: system-major work-list launch (a.sysmajor); else the tile shape.
+// WL launches (system-major work lists) use 128-thread blocks: bounds for three of them per
+// SM leave the FP64 hop 168 registers; tile-shaped launches use 256-thread blocks.
 template <typename Ts, typename Tg, typename Tm, int NR, int COEF, int DOT, bool WL = false>
-__global__ void __launch_bounds__(256, sizeof(Tm) == 8 ? 2 : (sizeof(Ts) == 2 ? 3 : 2)) hop_kernel(HopArgs a) {
+__global__ void __launch_bounds__(WL ? 128 : 256, WL ? 3 : (sizeof(Tm) == 8 ? 2 : (sizeof(Ts) == 2 ? 3 : 2)))
+    hop_kernel(HopArgs a) {
   if (a.gate != nullptr && *a.gate == 0) return;
   constexpr int K = DotK<DOT>::K;
   __shared__ double smem[256 * (K > 0 ? K : 1)];
