@@ -583,17 +583,23 @@ __global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
   }
   __syncthreads();
   if (ticket != FIN_SPLIT - 1) return;
-  if (threadIdx.x != 0) return;
+  // the last block: thread v adds value v's FIN_SPLIT slice sums in slice order
+  __shared__ double tsum[FIN_MAXV];
   __threadfence();
+  if (threadIdx.x < NV) {
+    const int v = threadIdx.x;
+    double t = 0.0;
+#pragma unroll
+    for (int yy = 0; yy < FIN_SPLIT; yy++)
+      t += __ldcg(&a.slice[((size_t)sys * FIN_SPLIT + yy) * FIN_MAXV + v]);  // L2: other SMs wrote them
+    tsum[v] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   a.count[sys] = 0;  // re-armed for the next finalize of this system
   double tot[FIN_MAXV];
 #pragma unroll
-  for (int v = 0; v < FIN_MAXV; v++) tot[v] = 0.0;
-  for (int yy = 0; yy < FIN_SPLIT; yy++) {
-#pragma unroll
-    for (int v = 0; v < NV; v++)
-      tot[v] += __ldcg(&a.slice[((size_t)sys * FIN_SPLIT + yy) * FIN_MAXV + v]);  // L2: other SMs wrote them
-  }
+  for (int v = 0; v < FIN_MAXV; v++) tot[v] = v < NV ? tsum[v] : 0.0;
   fin_logic(a, op, a.st[sys], tot);
 }
 #endif  // FS_ENGINE_KERNELS
