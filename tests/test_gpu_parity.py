@@ -360,6 +360,27 @@ def test_autotuned_tile():
     ctx.close()
 
 
+def test_new_gauge_field_rebuilds_the_contraction_paths():
+    """The straight z-paths W(x, x + p z) are cached per gauge field: after fs_set_gauge with a
+    new field, a contraction at p > 0 equals the one of a fresh context holding that field."""
+    dims = (4, 4, 4, 8)
+    u1 = inputs.gauge_field(dims, "smooth", seed=51, eps=0.4)
+    u2 = inputs.gauge_field(dims, "smooth", seed=52, eps=0.4)
+    sig = [0.05, 0.5]
+    g = pkg.gamma_matrix("g3")
+    kw = dict(prec="f64", tol=1e-10, rhs_tile=4)
+    ctx = make_ctx(dims, u1)
+    ctx.mlmc_level_trace(-0.3, sig, g, 3, [3, 3], seed=9, job=1, **kw)
+    ctx.fs_set_gauge(u2)
+    again = ctx.mlmc_level_trace(-0.3, sig, g, 3, [3, 3], seed=9, job=1, **kw)
+    ctx.close()
+    fresh_ctx = make_ctx(dims, u2)
+    fresh = fresh_ctx.mlmc_level_trace(-0.3, sig, g, 3, [3, 3], seed=9, job=1, **kw)
+    fresh_ctx.close()
+    for lev in range(2):
+        assert np.array_equal(again["samples"][lev], fresh["samples"][lev]), lev
+
+
 def test_contraction_with_a_dense_gamma():
     """A Gamma that is not a Clifford product (dense complex 4x4) takes the general path of
     the contraction; Clifford products take the permutation path (the tests above)."""
