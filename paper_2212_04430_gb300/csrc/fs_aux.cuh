@@ -143,6 +143,9 @@ __global__ void gauge_pack_kernel(void* out, const double* canon, Geom g) {
 // the gauge field alone, so they are built once (transport_kernel) and every contraction
 // applies one FP64 SU(3) product per spin and displacement: psi = W(x, x + q z) R(x + q z),
 // c_q += L(x)^dag Gamma psi.
+// With a Z4 noise left vector and a monomial Gamma the product is taken from the left instead:
+// xi = Gamma^dag L is again Z4 (xi_{perm s} = (-i)^{phase s} L_s), so eta = W^dag xi needs
+// sign flips, swaps and additions only, and c_q += eta^dag R(x + q z): half the FP64 work.
 struct ContractPair {
   int right;      // slot holding the right vector (solution)
   int left;       // slot of the left vector
@@ -232,8 +235,29 @@ __global__ void __launch_bounds__(256) contract_kernel(ContractArgs a) {
     const int site = fs - par * g.Vh;
     int x[4];
     cb_coords(g, par, site, x);
+    // Z4 left vector with a monomial Gamma: the phase codes of xi = Gamma^dag L, xk[t] holding
+    // 2 bits per colour of spin t (unrolled over the permutation: no indexed local arrays)
+    const bool z4 = pr.left_kind == 0 && a.gmono;
+    unsigned xk[4] = {0u, 0u, 0u, 0u};
     double lv[24];
-    if (pr.left_kind == 0) {
+    if (z4) {
+      const NoiseSpec ns = a.spec[pr.left];
+      const uint4 o = philox4x32_10(make_uint4((uint32_t)lex_index(g, x), ns.sample, ns.level, ns.job),
+                                    make_uint2(ns.key0, ns.key1));
+#pragma unroll
+      for (int s2 = 0; s2 < 4; s2++) {
+        unsigned codes = 0u;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          const int j = 3 * s2 + c;
+          const unsigned kl = ((o.x >> (2 * j)) & 3u) + (((ns.flags & NOISE_G5) && s2 >= 2) ? 2u : 0u);
+          codes |= ((kl - (unsigned)a.gphase[s2]) & 3u) << (2 * c);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; t++)
+          if (a.gperm[s2] == t) xk[t] = codes;
+      }
+    } else if (pr.left_kind == 0) {
       z4_site(a.spec[pr.left], lex_index(g, x), lv);
     } else {
       make_field<double>(const_cast<double*>(par ? a.x_o : a.x_e), g.Vh, a.N, true).load(site, pr.left, lv);
@@ -250,6 +274,42 @@ __global__ void __launch_bounds__(256) contract_kernel(ContractArgs a) {
       double psi[24];
       make_field<double>(const_cast<double*>(ypar ? a.x_o : a.x_e), g.Vh, a.N, true)
           .load(cb_index(g, y), pr.right, psi);
+      if (z4) {
+        // c_q += sum_t eta_t^dag R_t, eta_t = W^dag xi_t (xi_t = i^code per colour)
+        double u[18];
+        if (q > 0) {
+#pragma unroll
+          for (int r = 0; r < 18; r++) u[r] = a.wline[((size_t)k * 18 + r) * stride + fs];
+          k++;
+        }
+        double cr = 0, ci = 0;
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+#pragma unroll
+          for (int b = 0; b < 3; b++) {
+            double er = 0.0, ei = 0.0;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+              // conj(W_cb) i^kc, with W the identity at q = 0
+              const unsigned kc = (xk[t] >> (2 * c)) & 3u;
+              const double wr = q > 0 ? u[(c * 3 + b) * 2] : (c == b ? 1.0 : 0.0);
+              const double wi = q > 0 ? u[(c * 3 + b) * 2 + 1] : 0.0;
+              const unsigned long long flip = (kc & 2u) ? 0x8000000000000000ull : 0ull;
+              const double rr = __longlong_as_double(__double_as_longlong((kc & 1u) ? wi : wr) ^ flip);
+              const double ri = __longlong_as_double(__double_as_longlong((kc & 1u) ? wr : -wi) ^ flip);
+              if (c == 0) { er = rr; ei = ri; }
+              else { er += rr; ei += ri; }
+            }
+            const double rrv = psi[t * 6 + b * 2], riv = psi[t * 6 + b * 2 + 1];
+            cr = fma(er, rrv, cr); cr = fma(ei, riv, cr);
+            ci = fma(er, riv, ci); ci = fma(-ei, rrv, ci);
+          }
+        }
+        acc[qi][0] = cr;
+        acc[qi][1] = ci;
+        qi++;
+        continue;
+      }
       if (q > 0) {
         double u[18];
 #pragma unroll
