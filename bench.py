@@ -419,6 +419,35 @@ def run_pipeline(pkg, ctx, w, kw, levels=4, n_s=5, n_ref=512, n_max=128, seed=90
             "solves": int(len(out["stats"])), "rc": int(out["rc"])}
 
 
+def run_probing(pkg, ctx, w, kw, p=4, k=4, n_s=1, seed=9100):
+    """Probed and spin-colour diluted level traces on the workload's lattice (Sec. 2.1, Sec. 3.1):
+    displacement-p distance-k colours (the paper's p4k4 set; the greedy colouring of the library)
+    and full dilution, n_s samples per level, each the sum over its 12 c pieces. The pieces are
+    sparse right-hand sides generated on the device; solves/s is timed with CUDA events."""
+    import torch
+    t0 = time.perf_counter()
+    col, nc = pkg.fs_probing_colors(w["dims"], k, p)
+    t_col = time.perf_counter() - t0
+    gam = pkg.gamma_matrix(w["gamma"])
+    n = [n_s] * len(w["sigmas"])
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = ctx.mlmc_level_trace(w["m"], w["sigmas"], gam, w["p"], n, seed=seed, job=1, estimator=w["estimator"],
+                               colors=col, ncolors=nc, dilute=True, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if out["rc"] != 0:
+        raise RuntimeError("probed solves did not converge: %s" % ctx.last_error())
+    solves = len(out["stats"])
+    sec = e0.elapsed_time(e1) / 1e3
+    return {"value": solves / sec, "unit": "solves/s", "probing": "p%dk%d" % (p, k), "colors": int(nc),
+            "pieces_per_sample": 12 * int(nc), "samples_per_level": n_s, "solves": solves, "seconds": sec,
+            "t_coloring_s": t_col, "mean_iters": float(np.mean([st["iters"] for st in out["stats"]])),
+            "trace": [[float(t.real), float(t.imag)] for t in out["trace"]]}
+
+
 # --------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -439,6 +468,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=8.0, help="seconds of oracle work per reference step")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--serve-jobs", type=int, default=12, help="jobs in the serving run (0: skip)")
+    ap.add_argument("--no-probing", action="store_true",
+                    help="skip the probed and spin-colour diluted level traces (p4k4 colours)")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="skip the end-to-end run of variance sampling, shift selection and allocation")
     args = ap.parse_args()
@@ -588,6 +619,10 @@ def main():
     if not args.no_pipeline and rank == 0:
         pipeline = run_pipeline(pkg, ctx, w, kw)
 
+    probing = None
+    if not args.no_probing and rank == 0:
+        probing = run_probing(pkg, ctx, w, kw)
+
     serving = None
     if args.serve_jobs > 0:
         serving = run_serving(pkg, inputs, local, args.serve_jobs)
@@ -613,7 +648,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_of(args, w), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "serving": serving, "pipeline": pipeline,
-                "fp64_single_rhs": fp64,
+                "fp64_single_rhs": fp64, "probing": probing,
                 "solver": {"mean_iters": float(np.mean(iters)) if iters else None,
                            "max_iters": int(max(iters)) if iters else None,
                            "mean_reliable_updates": float(np.mean(updates)) if updates else None,

@@ -116,6 +116,14 @@ typedef struct fs_mlmc_params {
   uint32_t job;             /* Philox counter word 3                                        */
   int estimator;            /* enum fs_estimator                                            */
   fs_solve_params solve;
+  /* Probing and dilution of the noise (Sec. 2.1, Eq. (probing_vectors); Sec. 3.1). A sample
+     is then the sum of the level estimator over its pieces: the sample's Z4 vector restricted
+     to the sites of one probing colour j < ncolors and, with dilute = 1, to one spin-colour
+     index a = 3 s + c < 12; pieces are listed colour-major. */
+  const int32_t* colors;    /* [V] probing colour of every site (canonical order), values in
+                               [0, ncolors) with every colour used; NULL = no probing          */
+  int ncolors;              /* number of colours when colors != NULL                         */
+  int dilute;               /* 1: full spin-colour dilution (12 pieces per colour); 0: none  */
 } fs_mlmc_params;
 
 /* ---- context ------------------------------------------------------------------ */
@@ -171,9 +179,26 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* params, double* trace, d
                      double* samples, fs_sys_stats* stats);
 
 /* Number of shifted solves mlmc_level_trace performs: per level l < L two solves per
- * sample (DIFF: z at s_l then z at s_{l+1}; SPLIT_EVEN: gamma_5 z at s_l then z at s_{l+1};
- * PRODUCT: z at s_{l+1} then its solution at s_l), one per sample at level L. */
+ * sample and piece (DIFF: z at s_l then z at s_{l+1}; SPLIT_EVEN: gamma_5 z at s_l then z at
+ * s_{l+1}; PRODUCT: z at s_{l+1} then its solution at s_l), one per sample and piece at level
+ * L; a sample has ncolors * (dilute ? 12 : 1) pieces when probing (1 without), so the count
+ * is the paper's 12 c m N_s for one shift and full dilution. Solves are listed level-major,
+ * then by sample, then by piece. -1 if the count exceeds 2^31 - 1 or params is invalid. */
 int fs_mlmc_num_solves(const fs_mlmc_params* params);
+
+/* Greedy probing colours (Sec. 2.1): a distance-k colouring of the lattice graph of D (the
+ * nearest-neighbour graph of the periodic 4D lattice, hop distance), or, for p > 0, the
+ * displacement-p colouring of the symmetric part of Pi_p D^k, in which site x differs in colour
+ * from every site within distance k of x + p z and of x - p z (z = lattice axis 2, the axis of
+ * Omega_p). Sites are coloured in canonical order, each taking the smallest colour that none of
+ * its already coloured conflicting sites has. Host-only (no device work, no context).
+ *   dims     lattice sizes, each >= 1; V = Lx Ly Lz Lt < 2^31
+ *   k        distance, 1..16; p displacement, 0 <= p < Lz
+ *   colors   out: [V] colours (canonical site order), caller-owned
+ *   ncolors  out: the number of colours c
+ * FS_ERR_ARG for a null pointer or an argument out of range, FS_ERR_OOM if host memory runs
+ * out. */
+int fs_probing_colors(const int dims[4], int k, int p, int32_t* colors, int* ncolors);
 
 /* Variance sampling, Sec. 3.1 algorithm, for the m_shifts sampling shifts s_hat
  * (s_hat_0 < ... ) and every displacement p[k], k < np, with Ns Z4 noise vectors

@@ -23,5 +23,6 @@ from .fsmlmc import (  # noqa: F401
     fs_select_shifts,
     fs_sample_allocation,
     fs_eval_grid,
+    fs_probing_colors,
 )
 from .gamma import gamma_matrix, gamma_mu, gamma5  # noqa: F401

@@ -35,6 +35,7 @@ void release(Ctx& c) {
     if (c.wline) cudaFree(c.wline);
     for (auto& kv : c.gauge_lo) cudaFree(kv.second);
   }
+  if (c.colors_own && c.colors_d) cudaFree(c.colors_d);
   if (c.canon_d) cudaFree(c.canon_d);
   if (c.canon_h) cudaFreeHost(c.canon_h);
   for (auto& ev : c.prof.pending) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
@@ -416,10 +417,23 @@ int shifted_solve(fs_ctx* ctx, double m, const double* sigma, int nshift, const 
   return noconv ? c.fail(FS_ERR_NOCONV, "some systems reached max_iter") : FS_OK;
 }
 
+// Pieces of one sample: probing colours times spin-colour components (Sec. 2.1, Sec. 3.1).
+int num_pieces(const fs_mlmc_params* p) {
+  if (p->dilute != 0 && p->dilute != 1) return -1;
+  if (p->colors && (p->ncolors < 1 || p->ncolors > (1 << 26))) return -1;
+  return (p->colors ? p->ncolors : 1) * (p->dilute ? 12 : 1);
+}
+
 int fs_mlmc_num_solves(const fs_mlmc_params* p) {
   if (!p || p->nlev < 1 || !p->n_samples) return -1;
+  const int pieces = num_pieces(p);
+  if (pieces < 1) return -1;
   long long n = 0;
-  for (int l = 0; l < p->nlev; l++) n += (long long)p->n_samples[l] * (l + 1 < p->nlev ? 2 : 1);
+  for (int l = 0; l < p->nlev; l++) {
+    if (p->n_samples[l] < 0) return -1;
+    n += (long long)p->n_samples[l] * (l + 1 < p->nlev ? 2 : 1);
+  }
+  n *= pieces;
   return n > 0x7FFFFFFF ? -1 : (int)n;
 }
 
@@ -443,57 +457,86 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double
     if (std::fabs(4.0 + P->m + P->sigma[l]) < 1e-12) return c.fail(FS_ERR_ARG, "4 + m + sigma must be nonzero");
   }
   const int nsolve = fs_mlmc_num_solves(P);
-  if (nsolve < 0) return c.fail(FS_ERR_ARG, "too many solves");
+  if (nsolve < 0) return c.fail(FS_ERR_ARG, "too many solves, or bad ncolors / dilute");
+  const int npieces = num_pieces(P);
+  const int ncomp = P->dilute ? 12 : 1;
+  if (P->colors) {
+    // every site has a colour in range and every colour is used (no piece has an empty support)
+    std::vector<char> used(P->ncolors, 0);
+    for (long long x = 0; x < c.g.V; x++) {
+      const int32_t j = P->colors[x];
+      if (j < 0 || j >= P->ncolors) return c.fail(FS_ERR_ARG, "probing colour out of range");
+      used[j] = 1;
+    }
+    for (int j = 0; j < P->ncolors; j++)
+      if (!used[j]) return c.fail(FS_ERR_ARG, "every probing colour must be used");
+  }
   Opts o;
   if (int rc = resolve_params(c, &P->solve, nsolve, P->m, o)) return rc;
   if (int rc = set_device(c)) return rc;
+  if (P->colors)
+    if (int rc = fs::upload_colors(&c, P->colors)) return rc;
   const std::vector<int> plist = {P->p};
   std::vector<double> csum(total * 2, 0.0);  // per-sample values, level-major
   std::vector<long long> off(L + 2, 0);
   for (int l = 0; l <= L; l++) off[l + 1] = off[l] + P->n_samples[l];
   std::vector<fs::SysState> st(nsolve);
   std::vector<int> solve_off(L + 2, 0);
-  for (int l = 0; l <= L; l++) solve_off[l + 1] = solve_off[l] + P->n_samples[l] * (l < L ? 2 : 1);
+  for (int l = 0; l <= L; l++) solve_off[l + 1] = solve_off[l] + P->n_samples[l] * npieces * (l < L ? 2 : 1);
   int noconv = 0;
+  // the noise of one piece: the sample's Z4 vector restricted to a colour and a component
+  auto piece_noise = [&](int l, int s, int piece, bool g5) {
+    fs::NoiseSpec n = noise_id(P->seed, P->job, l, s, g5);
+    if (P->colors) {
+      n.flags |= fs::NOISE_COLOR;
+      n.color = piece / ncomp;
+    }
+    if (P->dilute) {
+      n.flags |= fs::NOISE_COMP;
+      n.comp = piece % ncomp;
+    }
+    return n;
+  };
   // one result row per solve; the level sample is combined from the rows below
   std::vector<fs::QJob> jobs;
-  const double nan = std::nan("");
   for (int l = 0; l <= L; l++) {
     for (int s = 0; s < P->n_samples[l]; s++) {
-      const int si = solve_off[l] + s * (l < L ? 2 : 1);
-      fs::QJob q;
-      if (l == L) {
-        q.sys = {fs::SysSpec{P->sigma[L], 0, -1, noise_id(P->seed, P->job, l, s, false)}};
-        q.stat_index = {si};
-        q.pairs = {{0, 0, 0, si}};
-        jobs.push_back(q);
-      } else if (P->estimator == FS_EST_DIFF) {
-        // the two solves of a DIFF sample are independent: one group each packs slots best
-        fs::QJob q2;
-        q.sys = {fs::SysSpec{P->sigma[l], 0, -1, noise_id(P->seed, P->job, l, s, false)}};
-        q.stat_index = {si};
-        q.pairs = {{0, 0, 0, si}};
-        q2.sys = {fs::SysSpec{P->sigma[l + 1], 0, -1, noise_id(P->seed, P->job, l, s, false)}};
-        q2.stat_index = {si + 1};
-        q2.pairs = {{0, 0, 0, si + 1}};
-        jobs.push_back(q);
-        jobs.push_back(q2);
-      } else if (P->estimator == FS_EST_SPLIT_EVEN) {
-        q.sys = {fs::SysSpec{P->sigma[l], 0, -1, noise_id(P->seed, P->job, l, s, true)},
-                 fs::SysSpec{P->sigma[l + 1], 0, -1, noise_id(P->seed, P->job, l, s, false)}};
-        q.stat_index = {si, si + 1};
-        q.pairs = {{1, 0, 1, si}};  // y^dag Gamma Omega_p x_{l+1}, y = gamma_5 x~_l
-        jobs.push_back(q);
-      } else {
-        // PRODUCT: x1 = (D + s_{l+1})^-1 z, then (D + s_l)^-1 x1 in the same slot
-        q.sys = {fs::SysSpec{P->sigma[l + 1], 0, -1, noise_id(P->seed, P->job, l, s, false)}};
-        q.chain = {P->sigma[l]};
-        q.stat_index = {si};
-        q.stat_index2 = {si + 1};
-        q.pairs = {{0, 0, 0, si}};
-        jobs.push_back(q);
+      for (int piece = 0; piece < npieces; piece++) {
+        const int si = solve_off[l] + (s * npieces + piece) * (l < L ? 2 : 1);
+        const fs::NoiseSpec z = piece_noise(l, s, piece, false);
+        fs::QJob q;
+        if (l == L) {
+          q.sys = {fs::SysSpec{P->sigma[L], 0, -1, z}};
+          q.stat_index = {si};
+          q.pairs = {{0, 0, 0, si}};
+          jobs.push_back(q);
+        } else if (P->estimator == FS_EST_DIFF) {
+          // the two solves of a DIFF sample are independent: one group each packs slots best
+          fs::QJob q2;
+          q.sys = {fs::SysSpec{P->sigma[l], 0, -1, z}};
+          q.stat_index = {si};
+          q.pairs = {{0, 0, 0, si}};
+          q2.sys = {fs::SysSpec{P->sigma[l + 1], 0, -1, z}};
+          q2.stat_index = {si + 1};
+          q2.pairs = {{0, 0, 0, si + 1}};
+          jobs.push_back(q);
+          jobs.push_back(q2);
+        } else if (P->estimator == FS_EST_SPLIT_EVEN) {
+          q.sys = {fs::SysSpec{P->sigma[l], 0, -1, piece_noise(l, s, piece, true)},
+                   fs::SysSpec{P->sigma[l + 1], 0, -1, z}};
+          q.stat_index = {si, si + 1};
+          q.pairs = {{1, 0, 1, si}};  // y^dag Gamma Omega_p x_{l+1}, y = gamma_5 x~_l
+          jobs.push_back(q);
+        } else {
+          // PRODUCT: x1 = (D + s_{l+1})^-1 z, then (D + s_l)^-1 x1 in the same slot
+          q.sys = {fs::SysSpec{P->sigma[l + 1], 0, -1, z}};
+          q.chain = {P->sigma[l]};
+          q.stat_index = {si};
+          q.stat_index2 = {si + 1};
+          q.pairs = {{0, 0, 0, si}};
+          jobs.push_back(q);
+        }
       }
-      (void)nan;
     }
   }
   // two tiles at once when the job fills both (lanes = 0); a system's result is the same
@@ -521,18 +564,21 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double
   } else if (int rc = fs::run_queue(&c, T, jobs, o.so, out)) {
     return rc;
   }
+  // a sample is the sum of its pieces' estimators, in piece order
   for (int l = 0; l <= L; l++) {
     for (int s = 0; s < P->n_samples[l]; s++) {
-      const int si = solve_off[l] + s * (l < L ? 2 : 1);
-      double re, im;
-      if (l == L) {
-        re = res[(size_t)si * 2]; im = res[(size_t)si * 2 + 1];
-      } else if (P->estimator == FS_EST_DIFF) {
-        re = res[(size_t)si * 2] - res[(size_t)(si + 1) * 2];
-        im = res[(size_t)si * 2 + 1] - res[(size_t)(si + 1) * 2 + 1];
-      } else {
-        const double ds = P->sigma[l + 1] - P->sigma[l];
-        re = ds * res[(size_t)si * 2]; im = ds * res[(size_t)si * 2 + 1];
+      double re = 0.0, im = 0.0;
+      for (int piece = 0; piece < npieces; piece++) {
+        const int si = solve_off[l] + (s * npieces + piece) * (l < L ? 2 : 1);
+        if (l == L) {
+          re += res[(size_t)si * 2]; im += res[(size_t)si * 2 + 1];
+        } else if (P->estimator == FS_EST_DIFF) {
+          re += res[(size_t)si * 2] - res[(size_t)(si + 1) * 2];
+          im += res[(size_t)si * 2 + 1] - res[(size_t)(si + 1) * 2 + 1];
+        } else {
+          const double ds = P->sigma[l + 1] - P->sigma[l];
+          re += ds * res[(size_t)si * 2]; im += ds * res[(size_t)si * 2 + 1];
+        }
       }
       csum[(off[l] + s) * 2] = re;
       csum[(off[l] + s) * 2 + 1] = im;

@@ -19,20 +19,36 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 }
 
 // Noise source of one tile slot: z(x, s, c) = i^k, k = (Philox(x, sample, level, job; seed).x >> 2(3s+c)) & 3.
+// Probing and dilution (Sec. 2.1, Eq. (probing_vectors); Sec. 3.1) restrict it to the sites whose
+// probing colour is `color` (NOISE_COLOR) and to the one spin-colour index comp = 3 s + c
+// (NOISE_COMP): the pieces of one sample share its Z4 vector.
 struct NoiseSpec {
   uint32_t key0, key1, job, level, sample;
   uint32_t flags;  // NOISE_* bits
+  int32_t color;   // probing colour of the piece (NOISE_COLOR)
+  int32_t comp;    // spin-colour index of the piece, 0..11 (NOISE_COMP)
 };
-enum { NOISE_G5 = 1, NOISE_VALID = 2, NOISE_RHS = 4 };  // gamma_5 z ; has a noise identity ; z is the rhs
+// gamma_5 z ; has a noise identity ; z is the rhs ; colour-restricted ; one spin-colour index
+enum { NOISE_G5 = 1, NOISE_VALID = 2, NOISE_RHS = 4, NOISE_COLOR = 8, NOISE_COMP = 16 };
 
-__device__ __forceinline__ void z4_site(const NoiseSpec& n, int lex, double (&z)[24]) {
+// Spin-colour indices (bit j = 3 s + c) that noise n keeps at canonical site lex; colors is the
+// probing colour of every site, read only for a colour-restricted source.
+__device__ __forceinline__ unsigned noise_keep(const NoiseSpec& n, const int* colors, int lex) {
+  unsigned keep = 0xFFFu;
+  if ((n.flags & NOISE_COLOR) && colors[lex] != n.color) keep = 0u;
+  if (n.flags & NOISE_COMP) keep &= 1u << n.comp;
+  return keep;
+}
+
+__device__ __forceinline__ void z4_site(const NoiseSpec& n, int lex, double (&z)[24], unsigned keep = 0xFFFu) {
   const uint4 o = philox4x32_10(make_uint4((uint32_t)lex, n.sample, n.level, n.job), make_uint2(n.key0, n.key1));
 #pragma unroll
   for (int j = 0; j < 12; j++) {
     const uint32_t k = (o.x >> (2 * j)) & 3u;
+    const bool on = (keep >> j) & 1u;
     // i^k: 0 -> 1, 1 -> i, 2 -> -1, 3 -> -i
-    double re = (k == 0) ? 1.0 : ((k == 2) ? -1.0 : 0.0);
-    double im = (k == 1) ? 1.0 : ((k == 3) ? -1.0 : 0.0);
+    double re = !on ? 0.0 : ((k == 0) ? 1.0 : ((k == 2) ? -1.0 : 0.0));
+    double im = !on ? 0.0 : ((k == 1) ? 1.0 : ((k == 3) ? -1.0 : 0.0));
     if ((n.flags & NOISE_G5) && j >= 6) { re = -re; im = -im; }
     z[2 * j] = re;
     z[2 * j + 1] = im;
@@ -42,7 +58,7 @@ __device__ __forceinline__ void z4_site(const NoiseSpec& n, int lex, double (&z)
 #ifdef FS_ENGINE_KERNELS
 // z for slots flagged INIT with a noise source, both parities (FP64 e/o tile fields).
 __global__ void __launch_bounds__(256) noise_kernel(double* z_e, double* z_o, const NoiseSpec* spec,
-                                                    const SysState* st, Geom g, Shape sh) {
+                                                    const SysState* st, const int* colors, Geom g, Shape sh) {
   const int lsys = threadIdx.x % sh.NB, lsite = threadIdx.x / sh.NB;
   const int sys = blockIdx.y * sh.NB + lsys;
   if (sys >= sh.N || !(st[sys].flags & FLAG_INIT) || !(spec[sys].flags & NOISE_RHS)) return;
@@ -54,7 +70,8 @@ __global__ void __launch_bounds__(256) noise_kernel(double* z_e, double* z_o, co
     int x[4];
     cb_coords(g, par, site, x);
     double z[24];
-    z4_site(n, lex_index(g, x), z);
+    const int lex = lex_index(g, x);
+    z4_site(n, lex, z, noise_keep(n, colors, lex));
     make_field<double>(par ? z_o : z_e, g.Vh, sh.N, true).store(site, sys, z);
   }
 }
@@ -158,6 +175,7 @@ struct ContractArgs {
   const double* x_o;
   const double* wline;    // W(x, x + q z) for the requested q > 0: [k][18][2 Vh], k counts them
   const NoiseSpec* spec;
+  const int* colors;      // probing colour per canonical site (colour-restricted noise only)
   const ContractPair* pairs;
   double* partial;        // [npairs][np][2][nblk]
   double gamma[32];       // Gamma, 4x4 complex, row major
@@ -235,14 +253,18 @@ __global__ void __launch_bounds__(256) contract_kernel(ContractArgs a) {
     const int site = fs - par * g.Vh;
     int x[4];
     cb_coords(g, par, site, x);
-    // Z4 left vector with a monomial Gamma: the phase codes of xi = Gamma^dag L, xk[t] holding
-    // 2 bits per colour of spin t (unrolled over the permutation: no indexed local arrays)
-    const bool z4 = pr.left_kind == 0 && a.gmono;
+    const int lex = lex_index(g, x);
+    // a probed / diluted noise left vector that vanishes at this site contributes nothing
+    const unsigned keep = pr.left_kind == 0 ? noise_keep(a.spec[pr.left], a.colors, lex) : 0xFFFu;
+    // Z4 left vector (all 12 entries present) with a monomial Gamma: the phase codes of
+    // xi = Gamma^dag L, xk[t] holding 2 bits per colour of spin t (unrolled over the
+    // permutation: no indexed local arrays)
+    const bool z4 = pr.left_kind == 0 && a.gmono && keep == 0xFFFu;
     unsigned xk[4] = {0u, 0u, 0u, 0u};
     double lv[24];
     if (z4) {
       const NoiseSpec ns = a.spec[pr.left];
-      const uint4 o = philox4x32_10(make_uint4((uint32_t)lex_index(g, x), ns.sample, ns.level, ns.job),
+      const uint4 o = philox4x32_10(make_uint4((uint32_t)lex, ns.sample, ns.level, ns.job),
                                     make_uint2(ns.key0, ns.key1));
 #pragma unroll
       for (int s2 = 0; s2 < 4; s2++) {
@@ -258,7 +280,7 @@ __global__ void __launch_bounds__(256) contract_kernel(ContractArgs a) {
           if (a.gperm[s2] == t) xk[t] = codes;
       }
     } else if (pr.left_kind == 0) {
-      z4_site(a.spec[pr.left], lex_index(g, x), lv);
+      z4_site(a.spec[pr.left], lex, lv, keep);
     } else {
       make_field<double>(const_cast<double*>(par ? a.x_o : a.x_e), g.Vh, a.N, true).load(site, pr.left, lv);
 #pragma unroll
@@ -266,7 +288,8 @@ __global__ void __launch_bounds__(256) contract_kernel(ContractArgs a) {
     }
     const size_t stride = (size_t)2 * g.Vh;
     int qi = 0, k = 0;
-    for (int q = 0; q <= a.pmax; q++) {
+    const int qend = keep ? a.pmax : -1;
+    for (int q = 0; q <= qend; q++) {
       if (!((a.pmask >> q) & 1)) continue;
       int y[4] = {x[0], x[1], x[2], x[3]};
       y[2] = (x[2] + q) % g.L[2];

@@ -111,6 +111,8 @@ Ctx* Ctx::lane(int i) {
   l->wline = wline;
   l->wline_mask = wline_mask;
   l->wline_cap = 0;  // never reallocated or freed by the lane
+  l->colors_d = colors_d;
+  l->colors_own = false;
   return l;
 }
 
@@ -293,8 +295,8 @@ class Tile : public TileBase {
   cudaError_t enqueue_noise() override {
     L1.stream = c->stream;
     LW.stream = c->stream;
-    noise_kernel<<<dim3(std::min(2 * sh1.nchunk, 2 * L1.grid_x), N), SYS_SITES, 0, c->stream>>>(z_e, z_o, spec_d, st_d,
-                                                                                      c->g, sh1);
+    noise_kernel<<<dim3(std::min(2 * sh1.nchunk, 2 * L1.grid_x), N), SYS_SITES, 0, c->stream>>>(
+        z_e, z_o, spec_d, st_d, c->colors_d, c->g, sh1);
     note_launch();
     return cudaGetLastError();
   }
@@ -551,6 +553,22 @@ int ensure_wline(Ctx* c, int pmask, int pmax) {
   return 0;
 }
 
+int upload_colors(Ctx* c, const int* colors) {
+  if (c->shared) return c->fail(1, "the probing colours of a lane are set by its owner");
+  cudaError_t e;
+  if (!c->colors_d) {
+    if ((e = cudaMalloc((void**)&c->colors_d, (size_t)c->g.V * sizeof(int)))) {
+      c->colors_d = nullptr;
+      return c->cuda_fail(e, "probing colours");
+    }
+    c->colors_own = true;
+    c->extra_bytes += (size_t)c->g.V * sizeof(int);
+  }
+  if ((e = cudaMemcpyAsync(c->colors_d, colors, (size_t)c->g.V * sizeof(int), cudaMemcpyHostToDevice, c->stream)))
+    return c->cuda_fail(e, "probing colours");
+  return 0;
+}
+
 int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, const double* gamma,
                   const std::vector<int>& plist, std::vector<double>& result, int rows) {
   const int np = (int)plist.size();
@@ -570,7 +588,7 @@ int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, c
     if (plist[k] <= plist[k - 1]) return c->fail(1, "displacements must be increasing");
   cudaError_t e;
   if (int rc = ensure_wline(c, pmask, pmax)) return rc;
-  a.x_e = T->x_hi; a.x_o = T->x_o; a.wline = c->wline; a.spec = T->spec_d;
+  a.x_e = T->x_hi; a.x_o = T->x_o; a.wline = c->wline; a.spec = T->spec_d; a.colors = c->colors_d;
   for (int k = 0; k < 32; k++) a.gamma[k] = gamma[k];
   // detect a monomial Gamma (one entry per row, each +-1 or +-i): applied as a permutation
   a.gmono = 1;

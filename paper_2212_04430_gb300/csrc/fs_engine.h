@@ -103,6 +103,8 @@ struct Ctx {
   double* wline = nullptr;              // straight z-paths W(x, x + q z) of the contraction
   size_t wline_cap = 0;                 // bytes allocated
   int wline_mask = 0;                   // the q > 0 they hold (bit q); 0: none or stale
+  int* colors_d = nullptr;              // probing colour per canonical site, [V] (probed noise)
+  bool colors_own = false;              // colors_d allocated by this context
   std::map<long long, std::unique_ptr<TileBase>> tiles;
   double* canon_d = nullptr;            // staging for canonical vectors
   size_t canon_cap = 0;                 // in vectors
@@ -135,6 +137,9 @@ struct Ctx {
 // The contraction's straight z-paths W(x, x + q z) for the displacements q > 0 in pmask,
 // built once per gauge field (fs_engine.cu); 0 or an error code (message in c->err).
 int ensure_wline(Ctx* c, int pmask, int pmax);
+
+// Copies the probing colours (host, [V] in canonical site order) to c->colors_d, on c's stream.
+int upload_colors(Ctx* c, const int* colors);
 
 // One system to solve.
 struct SysSpec {

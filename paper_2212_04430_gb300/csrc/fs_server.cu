@@ -37,6 +37,7 @@ struct SJob {
   int bc_t = -1;
   std::vector<double> U, sigma, gamma;
   std::vector<int> nsamp;
+  std::vector<int32_t> colors;  // probing colours, [V] (empty: no probing)
   fs_mlmc_params P{};
   size_t est = 0;
   double t_submit = 0, t_start = 0, t_end = 0;
@@ -60,7 +61,8 @@ size_t estimate(const SJob& j) {
   const size_t gauge = 8 * Vh * (18 * 8 + 20 * 4 + 12 * 4 + 24 * 2 + 16 * 2);
   const size_t stage = j.P.estimator == FS_EST_PRODUCT ? (size_t)tile * V * 24 * 8 : 0;
   const size_t contract = (size_t)tile * ((2 * Vh + 255) / 256) * 2 * 8 + (64u << 10) +
-                          (j.P.p > 0 ? V * 18 * 8 : 0);  // partial sums + the path products
+                          (j.P.p > 0 ? V * 18 * 8 : 0) +  // partial sums + the path products
+                          (j.P.colors ? V * 4 : 0);       // + the probing colours
   const size_t lanes = (size_t)std::max(1, j.P.solve.lanes);
   return lanes * (tile_bytes + stage) + gauge + contract + (32u << 20);
 }
@@ -198,6 +200,7 @@ int fs_server_submit(fs_server* s, const fs_job* job, uint64_t* ticket) {
   j->sigma.assign(P.sigma, P.sigma + P.nlev);
   j->nsamp.assign(P.n_samples, P.n_samples + P.nlev);
   j->gamma.assign(P.gamma, P.gamma + 32);
+  if (P.colors) j->colors.assign(P.colors, P.colors + V);
   j->P = P;
   // the server overlaps whole jobs; one tile per job unless the caller asked for more lanes
   if (j->P.solve.lanes == 0) j->P.solve.lanes = 1;
@@ -207,6 +210,7 @@ int fs_server_submit(fs_server* s, const fs_job* job, uint64_t* ticket) {
   j->P.sigma = j->sigma.data();
   j->P.n_samples = j->nsamp.data();
   j->P.gamma = j->gamma.data();
+  j->P.colors = P.colors ? j->colors.data() : nullptr;
   j->est = estimate(*j);
   if (j->est > s->budget) return FS_ERR_BUDGET;
   std::lock_guard<std::mutex> lock(s->mu);

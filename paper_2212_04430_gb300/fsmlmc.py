@@ -26,7 +26,7 @@ EXPORTS = ["fs_ctx_create", "fs_ctx_destroy", "fs_last_error", "fs_set_stream", 
            "variance_sample", "fs_noise_codes", "fs_profile_enable", "fs_profile_read", "fs_kernel_launches",
            "wilson_dslash_noalloc", "fs_server_create", "fs_server_submit", "fs_server_poll",
            "fs_server_stats", "fs_server_destroy", "fs_interp_variances", "fs_select_shifts",
-           "fs_sample_allocation", "fs_eval_grid", "fs_tuned_tile"]
+           "fs_sample_allocation", "fs_eval_grid", "fs_tuned_tile", "fs_probing_colors"]
 JOB_MAX_LEVELS = 16
 
 
@@ -52,7 +52,8 @@ class MlmcParams(ctypes.Structure):
     _fields_ = [("m", ctypes.c_double), ("nlev", ctypes.c_int), ("p", ctypes.c_int),
                 ("sigma", ctypes.POINTER(ctypes.c_double)), ("n_samples", ctypes.POINTER(ctypes.c_int)),
                 ("gamma", ctypes.POINTER(ctypes.c_double)), ("seed", ctypes.c_uint64),
-                ("job", ctypes.c_uint32), ("estimator", ctypes.c_int), ("solve", SolveParams)]
+                ("job", ctypes.c_uint32), ("estimator", ctypes.c_int), ("solve", SolveParams),
+                ("colors", ctypes.POINTER(ctypes.c_int32)), ("ncolors", ctypes.c_int), ("dilute", ctypes.c_int)]
 
 
 class Job(ctypes.Structure):
@@ -117,6 +118,7 @@ def load_library(path=LIB_PATH):
         "fs_select_shifts": (I, [dp, I, dp, dp, dp, dp, I, I, ip, dp, dp, dp]),
         "fs_sample_allocation": (I, [dp, dp, I, D, dp, dp, dp, dp]),
         "fs_eval_grid": (I, [dp, I, dp, I, ip]),
+        "fs_probing_colors": (I, [ip, I, I, ctypes.POINTER(ctypes.c_int32), ip]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -124,6 +126,19 @@ def load_library(path=LIB_PATH):
         f.argtypes = args
     _lib = L
     return L
+
+
+def _set_probing(P, colors, ncolors, dilute):
+    """Fill the probing / dilution fields of an MlmcParams; returns the array to keep alive."""
+    P.dilute = int(bool(dilute))
+    if colors is None:
+        P.colors = None
+        P.ncolors = 0
+        return None
+    col = np.ascontiguousarray(colors, dtype=np.int32).ravel()
+    P.colors = col.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    P.ncolors = int(ncolors) if ncolors is not None else (int(col.max()) + 1 if col.size else 0)
+    return col
 
 
 def _dptr(a):
@@ -231,7 +246,10 @@ class Context:
                                                 ctypes.byref(p), st), allow_noconv=True)
         return x.view(np.complex128)[..., 0], [_stats(s) for s in st], rc
 
-    def mlmc_level_trace(self, m, sigmas, gamma, p, n_samples, seed, job=0, estimator="diff", **kw):
+    def mlmc_level_trace(self, m, sigmas, gamma, p, n_samples, seed, job=0, estimator="diff", colors=None,
+                         ncolors=None, dilute=False, **kw):
+        """Level traces; colors ([V] probing colours, canonical order) and dilute (full spin-colour
+        dilution) make every sample the sum of the estimator over its pieces."""
         sig = np.ascontiguousarray(sigmas, dtype=np.float64)
         ns = np.ascontiguousarray(n_samples, dtype=np.int32)
         if ns.size == 1 and sig.size > 1:
@@ -248,7 +266,10 @@ class Context:
         P.job = int(job)
         P.estimator = ESTIMATOR[estimator] if isinstance(estimator, str) else int(estimator)
         P.solve = _params(**kw)
+        keep = _set_probing(P, colors, ncolors, dilute)  # noqa: F841 (alive through the call)
         nsolve = self.lib.fs_mlmc_num_solves(ctypes.byref(P))
+        if nsolve < 0:
+            raise FsError(1, "fs_mlmc_num_solves: bad sample counts, ncolors or dilute")
         trace = np.zeros((sig.size, 2))
         var = np.zeros(sig.size)
         samples = np.zeros((int(ns.sum()), 2))
@@ -337,6 +358,18 @@ def fs_eval_grid(s_hat):
     return out
 
 
+def fs_probing_colors(dims, k, p=0):
+    """Greedy distance-k (displacement-p along z) probing colours: (int32 [V], ncolors)."""
+    L = load_library()
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    v = int(np.prod([int(x) for x in dims]))
+    out = np.empty(v, dtype=np.int32)
+    n = ctypes.c_int(0)
+    _check(L.fs_probing_colors(d, int(k), int(p), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                               ctypes.byref(n)), "fs_probing_colors")
+    return out, n.value
+
+
 def fs_interp_variances(s_hat, VL_hat, Vbar_hat, s):
     """(V_L[n], V_l[n, n]) on the evaluation set s; V_l is NaN for k <= i."""
     L = load_library()
@@ -385,7 +418,8 @@ class Server:
         if rc != FS_OK:
             raise FsError(rc, "fs_server_create failed")
 
-    def submit(self, dims, U, m, sigmas, gamma, p, n_samples, seed, job=0, estimator="diff", bc_t=-1, **kw):
+    def submit(self, dims, U, m, sigmas, gamma, p, n_samples, seed, job=0, estimator="diff", bc_t=-1, colors=None,
+               ncolors=None, dilute=False, **kw):
         """Queue one trace job (arrays are copied); returns the ticket."""
         u = _real(U)
         sig = np.ascontiguousarray(sigmas, dtype=np.float64)
@@ -407,6 +441,7 @@ class Server:
         P.job = int(job)
         P.estimator = ESTIMATOR[estimator] if isinstance(estimator, str) else int(estimator)
         P.solve = _params(**kw)
+        keep = _set_probing(P, colors, ncolors, dilute)  # noqa: F841 (alive through the call)
         t = ctypes.c_uint64()
         rc = self.lib.fs_server_submit(self.h, ctypes.byref(J), ctypes.byref(t))
         if rc != FS_OK:
