@@ -158,3 +158,36 @@ def exact_mean_and_variance(a, cls):
         mean += np.trace(sub)
         var += float((np.abs(sub) ** 2).sum() - (np.abs(np.diag(sub)) ** 2).sum())
     return complex(mean), var
+
+
+def probed_variance_sample(u, m, s_hat, gamma, p_list, n_s, seed, job, dims, colors, ncolors, dilute,
+                           bc_t=-1, solver=None):
+    """Sec. 3.1 variance sampling with probed / diluted noise: for each noise vector z_k the
+    sums over its pieces z_piece of a_i = z_piece^dag Gamma Omega_p x^(i) and
+    b_ij = y^(i)^dag Gamma Omega_p x^(j), with x^(i) = (D+s_i)^-1 z_piece and
+    y^(i) = (D+s_i)^-dag z_piece (the adjoint solve taken as written, no shortcut), then the
+    practical variances of Eq. (practical_variance). Same outputs as
+    estimators.variance_sample."""
+    from . import estimators as est
+    v = int(np.prod(dims))
+    if solver is None:
+        solver = est.make_solver(u, m, dims, bc_t)
+    ms = len(s_hat)
+    npl = len(p_list)
+    a = np.zeros((n_s, npl, ms), dtype=np.complex128)
+    b = np.zeros((n_s, npl, ms, ms), dtype=np.complex128)
+    for k in range(n_s):
+        for (j, comp) in pieces(ncolors, dilute):
+            z = probed_noise(v, seed, job, philox.VARIANCE_SAMPLE_LEVEL, k, colors, j, comp)
+            xs = [solver(z, s) for s in s_hat]
+            ys = [est.adjoint_solution(solver, z, s) for s in s_hat]
+            for pi, p in enumerate(p_list):
+                for i in range(ms):
+                    a[k, pi, i] += est.contract(u, z, xs[i], gamma, p, dims)
+                    for jj in range(i, ms):
+                        b[k, pi, i, jj] += est.contract(u, ys[i], xs[jj], gamma, p, dims)
+    VL = est.practical_variance(a)
+    Vbar = np.where(np.triu(np.ones((ms, ms), dtype=bool))[None], est.practical_variance(b), 0.0)
+    sh = np.asarray(s_hat, dtype=np.float64)
+    Vl = (sh[None, None, :] - sh[None, :, None]) ** 2 * Vbar
+    return {"a": a, "b": b, "VL": VL, "Vbar": Vbar, "Vl": Vl}

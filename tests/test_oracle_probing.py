@@ -143,3 +143,37 @@ def test_probing_removes_the_near_diagonal_variance():
     m_prob, v_prob = opr.exact_mean_and_variance(a, opr.classes(dims, color, nc, True))
     assert m_plain == pytest.approx(np.trace(a)) and m_prob == pytest.approx(np.trace(a))
     assert v_prob < 0.5 * v_plain
+
+
+def test_probed_variance_sample_with_single_site_colours_is_exact():
+    """Single-site colours and full dilution: every noise vector gives a_i = Tr(Gamma Omega_p A_i)
+    and b_ij = Tr(A_i Gamma Omega_p A_j), A_i = (D + s_i)^-1 (the pieces are the unit vectors, and
+    y^(i)^dag = e^dag A_i), so both sampled variances vanish."""
+    dims = (2, 2, 2, 2)
+    v = int(np.prod(dims))
+    u = inputs.gauge_field(dims, "haar", seed=84)
+    s_hat = [0.1, 0.6]
+    gam = np.diag([1, -1, 1, -1]).astype(complex)
+    solver = oest.make_dense_solver(u, -0.2, dims)
+    out = opr.probed_variance_sample(u, -0.2, s_hat, gam, [0, 1], 2, 3, 0, dims, np.arange(v), v, True,
+                                     solver=solver)
+    inv = [osolve.dense_inverse(u, -0.2, s, dims, -1) for s in s_hat]
+    for pi, p in enumerate([0, 1]):
+        g = osolve.dense_GammaOmega(u, gam, p, dims)
+        for i in range(2):
+            assert np.allclose(out["a"][:, pi, i], np.trace(g @ inv[i]), rtol=1e-10)
+            for j in range(i, 2):
+                assert np.allclose(out["b"][:, pi, i, j], np.trace(inv[i] @ g @ inv[j]), rtol=1e-10)
+    scale = max(np.abs(out["a"]).max(), np.abs(out["b"]).max()) ** 2
+    assert np.abs(out["VL"]).max() < 1e-12 * scale and np.abs(out["Vbar"]).max() < 1e-12 * scale
+
+
+def test_probed_variance_sample_without_pieces_is_the_plain_algorithm():
+    dims = (2, 2, 4, 2)
+    u = inputs.gauge_field(dims, "smooth", seed=85, eps=0.5)
+    solver = oest.make_dense_solver(u, -0.25, dims)
+    gam = np.diag([1, 1, -1, -1]).astype(complex)
+    a = opr.probed_variance_sample(u, -0.25, [0.05, 0.3], gam, [1], 3, 5, 1, dims, None, 0, False, solver=solver)
+    b = oest.variance_sample(u, -0.25, [0.05, 0.3], gam, [1], 3, 5, 1, dims, -1, solver)
+    for key in ("a", "b", "VL", "Vbar"):
+        assert np.allclose(a[key], b[key], rtol=1e-13, atol=1e-13), key
