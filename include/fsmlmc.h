@@ -215,6 +215,19 @@ int variance_sample(fs_ctx* ctx, double m, const double* s_hat, int m_shifts, co
                     const fs_solve_params* params, double* VL, double* Vbar, double* a, double* b,
                     double* iters);
 
+/* variance_sample with probed and diluted noise (Sec. 2.1, Eq. (probing_vectors); Sec. 3.1):
+ * each noise vector z_k is split into pieces, its restrictions to the sites of one colour
+ * j < ncolors (colors: [V] in canonical order, values in [0, ncolors), every colour used; NULL =
+ * no probing) and, with dilute = 1, to one spin-colour index (12 pieces per colour), and a_i,
+ * b_ij are the sums over the pieces. With dilute = 1 every piece lives on one spin s, so
+ * gamma_5 z = +-z and y^(i) = +-gamma_5 x^(i) needs no second solve: 12 c m N_s solves in all
+ * (Sec. 3.1), against 2 m N_s c' without dilution (c' = ncolors or 1). Outputs and errors as
+ * variance_sample; iters averages every solve at the shift. */
+int variance_sample_probed(fs_ctx* ctx, double m, const double* s_hat, int m_shifts, const double* gamma,
+                           const int* p, int np, int Ns, uint64_t seed, uint32_t job,
+                           const fs_solve_params* params, const int32_t* colors, int ncolors, int dilute,
+                           double* VL, double* Vbar, double* a, double* b, double* iters);
+
 /* The Z4 noise vector (seed, job, level, sample) as integer codes k (z = i^k),
  * host [V][4][3] bytes, generated on the device (bit-exact RNG checks). */
 int fs_noise_codes(fs_ctx* ctx, uint64_t seed, uint32_t job, uint32_t level, uint32_t sample,

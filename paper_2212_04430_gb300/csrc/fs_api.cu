@@ -603,15 +603,22 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double
   return noconv ? c.fail(FS_ERR_NOCONV, "some systems reached max_iter") : FS_OK;
 }
 
-int variance_sample(fs_ctx* ctx, double m, const double* s_hat, int ms, const double* gamma, const int* p, int np,
-                    int Ns, uint64_t seed, uint32_t job, const fs_solve_params* params, double* VL, double* Vbar,
-                    double* a_out, double* b_out, double* iters) {
-  if (!ctx) return FS_ERR_ARG;
-  Ctx& c = ctx->c;
+namespace {
+
+// Variance sampling (Sec. 3.1 algorithm) with optional probed / diluted noise: a noise vector's
+// a_i and b_ij are sums over its pieces. With full spin-colour dilution a piece lives on one spin
+// s, so gamma_5 z = eps z (eps = +1 for s < 2, -1 otherwise) and the adjoint solution is
+// y^(i) = gamma_5 (D+s_i)^-1 gamma_5 z = eps gamma_5 x^(i): no second solve (Sec. 3.1).
+int variance_sample_impl(Ctx& c, double m, const double* s_hat, int ms, const double* gamma, const int* p, int np,
+                         int Ns, uint64_t seed, uint32_t job, const fs_solve_params* params, const int32_t* colors,
+                         int ncolors, int dilute, double* VL, double* Vbar, double* a_out, double* b_out,
+                         double* iters) {
   if (!s_hat || !gamma || !p || !VL || !Vbar) return c.fail(FS_ERR_ARG, "null pointer");
   if (ms < 1 || 2 * ms > fs::MAX_TILE) return c.fail(FS_ERR_ARG, "m_shifts must be in [1, 32]");
   if (np < 1 || np > fs::CONTRACT_MAXP) return c.fail(FS_ERR_ARG, "np must be in [1, 16]");
   if (Ns < 1) return c.fail(FS_ERR_ARG, "Ns must be >= 1");
+  if (dilute != 0 && dilute != 1) return c.fail(FS_ERR_ARG, "dilute must be 0 or 1");
+  if (colors && (ncolors < 1 || ncolors > (1 << 26))) return c.fail(FS_ERR_ARG, "bad ncolors");
   if (!c.have_gauge) return c.fail(FS_ERR_STATE, "no gauge field set");
   if (!std::isfinite(m) || !finite_array(s_hat, ms) || !finite_array(gamma, 32))
     return c.fail(FS_ERR_INPUT, "non-finite mass, shift or Gamma");
@@ -619,44 +626,85 @@ int variance_sample(fs_ctx* ctx, double m, const double* s_hat, int ms, const do
     if (i > 0 && !(s_hat[i] > s_hat[i - 1])) return c.fail(FS_ERR_ARG, "sampling shifts must increase");
     if (std::fabs(4.0 + m + s_hat[i]) < 1e-12) return c.fail(FS_ERR_ARG, "4 + m + sigma must be nonzero");
   }
+  if (colors) {
+    std::vector<char> used(ncolors, 0);
+    for (long long x = 0; x < c.g.V; x++) {
+      if (colors[x] < 0 || colors[x] >= ncolors) return c.fail(FS_ERR_ARG, "probing colour out of range");
+      used[colors[x]] = 1;
+    }
+    for (int j = 0; j < ncolors; j++)
+      if (!used[j]) return c.fail(FS_ERR_ARG, "every probing colour must be used");
+  }
+  const int ncomp = dilute ? 12 : 1;
+  const long long npieces_ll = (long long)(colors ? ncolors : 1) * ncomp;
+  const int gsize = dilute ? ms : 2 * ms;  // systems per piece: x^(i), and y^(i) unless diluted
+  if ((long long)Ns * npieces_ll * gsize > 0x7FFFFFFF) return c.fail(FS_ERR_ARG, "too many solves");
+  const int npieces = (int)npieces_ll;
   // displacements are contracted in increasing order; map back to the caller's order
   std::vector<int> order(np);
   for (int k = 0; k < np; k++) order[k] = k;
   std::sort(order.begin(), order.end(), [&](int a, int b) { return p[a] < p[b]; });
   std::vector<int> plist(np);
   for (int k = 0; k < np; k++) plist[k] = p[order[k]];
+  const int nsys = Ns * npieces * gsize;
   Opts o;
-  if (int rc = resolve_params(c, params, 2 * ms * Ns, m, o)) return rc;
+  if (int rc = resolve_params(c, params, nsys, m, o)) return rc;
   if (int rc = set_device(c)) return rc;
-  o.tile = std::max(2 * ms, (o.tile / (2 * ms)) * (2 * ms));
-  const int per = ms + ms * (ms + 1) / 2;  // contraction rows per noise vector
-  std::vector<fs::QJob> groups(Ns);
+  if (colors)
+    if (int rc = fs::upload_colors(&c, colors)) return rc;
+  o.tile = std::max(gsize, (o.tile / gsize) * gsize);
+  const int per = ms + ms * (ms + 1) / 2;  // contraction rows per piece
+  const size_t ngroups = (size_t)Ns * npieces;
+  std::vector<fs::QJob> groups(ngroups);
   for (int k = 0; k < Ns; k++) {
-    fs::QJob& g = groups[k];
-    for (int i = 0; i < ms; i++)
-      g.sys.push_back(fs::SysSpec{s_hat[i], 0, -1, noise_id(seed, job, 0x80000000u, k, false)});
-    for (int i = 0; i < ms; i++)
-      g.sys.push_back(fs::SysSpec{s_hat[i], 0, -1, noise_id(seed, job, 0x80000000u, k, true)});
-    for (int i = 0; i < 2 * ms; i++) g.stat_index.push_back(k * 2 * ms + i);
-    int row = k * per;
-    for (int i = 0; i < ms; i++) g.pairs.push_back({i, i, 0, row++});               // a_i
-    for (int i = 0; i < ms; i++)
-      for (int j = i; j < ms; j++) g.pairs.push_back({j, ms + i, 1, row++});        // b_ij
+    for (int pc = 0; pc < npieces; pc++) {
+      const size_t gi = (size_t)k * npieces + pc;
+      fs::QJob& g = groups[gi];
+      auto piece = [&](bool g5) {
+        fs::NoiseSpec n = noise_id(seed, job, 0x80000000u, k, g5);
+        if (colors) {
+          n.flags |= fs::NOISE_COLOR;
+          n.color = pc / ncomp;
+        }
+        if (dilute) {
+          n.flags |= fs::NOISE_COMP;
+          n.comp = pc % ncomp;
+        }
+        return n;
+      };
+      for (int i = 0; i < ms; i++) g.sys.push_back(fs::SysSpec{s_hat[i], 0, -1, piece(false)});
+      if (!dilute)
+        for (int i = 0; i < ms; i++) g.sys.push_back(fs::SysSpec{s_hat[i], 0, -1, piece(true)});
+      for (int i = 0; i < gsize; i++) g.stat_index.push_back((int)(gi * gsize + i));
+      int row = (int)(gi * per);
+      for (int i = 0; i < ms; i++) g.pairs.push_back({i, i, 0, row++});  // a_i
+      for (int i = 0; i < ms; i++)
+        for (int j = i; j < ms; j++)  // b_ij: y^(i) = gamma_5 x~^(i), x~ solved for gamma_5 z (or eps x^(i))
+          g.pairs.push_back({j, dilute ? i : ms + i, 1, row++});
+    }
   }
-  std::vector<double> res((size_t)Ns * per * np * 2, 0.0);
-  std::vector<fs::SysState> st((size_t)Ns * 2 * ms);
+  std::vector<double> res(ngroups * per * np * 2, 0.0);
+  std::vector<fs::SysState> st((size_t)nsys);
   int noconv = 0;
   fs::TileBase* T = tile_for(c, groups, o);
   if (!T) return c.fail(FS_ERR_OOM, "device allocation of the solver tile failed");
   fs::QOut out;
   out.gamma = gamma;
   out.plist = &plist;
-  out.rows = Ns * per;
+  out.rows = (int)(ngroups * per);
   out.result = &res;
   out.states = &st;
   out.noconv = &noconv;
   if (int rc = fs::run_queue(&c, T, groups, o.so, out)) return rc;
-  auto val = [&](int k, int r, int q, int ri) { return res[(((size_t)k * per + r) * np + q) * 2 + ri]; };
+  // a noise vector's value of row r: the sum over its pieces (b rows carry eps with dilution)
+  auto val = [&](int k, int r, int q, int ri) {
+    double sum = 0.0;
+    for (int pc = 0; pc < npieces; pc++) {
+      const double sgn = (dilute && r >= ms && (pc % ncomp) / 3 >= 2) ? -1.0 : 1.0;
+      sum += sgn * res[((((size_t)k * npieces + pc) * per + r) * np + q) * 2 + ri];
+    }
+    return sum;
+  };
   for (int qs = 0; qs < np; qs++) {
     const int q = order[qs];  // caller's index of the qs-th smallest displacement
     for (int i = 0; i < ms; i++) {
@@ -700,13 +748,36 @@ int variance_sample(fs_ctx* ctx, double m, const double* s_hat, int ms, const do
     }
   }
   if (iters) {
+    // mean iterations of every solve at shift i (x^(i), and y^(i) unless diluted)
     for (int i = 0; i < ms; i++) {
       double sum = 0;
-      for (int k = 0; k < Ns; k++) sum += st[(size_t)k * 2 * ms + i].iters + st[(size_t)k * 2 * ms + ms + i].iters;
-      iters[i] = sum / (2.0 * Ns);
+      for (size_t gi = 0; gi < ngroups; gi++) {
+        sum += st[gi * gsize + i].iters;
+        if (!dilute) sum += st[gi * gsize + ms + i].iters;
+      }
+      iters[i] = sum / ((double)ngroups * (dilute ? 1 : 2));
     }
   }
   return noconv ? c.fail(FS_ERR_NOCONV, "some systems reached max_iter") : FS_OK;
+}
+
+}  // namespace
+
+int variance_sample(fs_ctx* ctx, double m, const double* s_hat, int ms, const double* gamma, const int* p, int np,
+                    int Ns, uint64_t seed, uint32_t job, const fs_solve_params* params, double* VL, double* Vbar,
+                    double* a_out, double* b_out, double* iters) {
+  if (!ctx) return FS_ERR_ARG;
+  return variance_sample_impl(ctx->c, m, s_hat, ms, gamma, p, np, Ns, seed, job, params, nullptr, 0, 0, VL, Vbar,
+                              a_out, b_out, iters);
+}
+
+int variance_sample_probed(fs_ctx* ctx, double m, const double* s_hat, int ms, const double* gamma, const int* p,
+                           int np, int Ns, uint64_t seed, uint32_t job, const fs_solve_params* params,
+                           const int32_t* colors, int ncolors, int dilute, double* VL, double* Vbar, double* a_out,
+                           double* b_out, double* iters) {
+  if (!ctx) return FS_ERR_ARG;
+  return variance_sample_impl(ctx->c, m, s_hat, ms, gamma, p, np, Ns, seed, job, params, colors, ncolors, dilute,
+                              VL, Vbar, a_out, b_out, iters);
 }
 
 int fs_noise_codes(fs_ctx* ctx, uint64_t seed, uint32_t job, uint32_t level, uint32_t sample, uint8_t* codes) {

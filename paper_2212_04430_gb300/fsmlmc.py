@@ -26,7 +26,8 @@ EXPORTS = ["fs_ctx_create", "fs_ctx_destroy", "fs_last_error", "fs_set_stream", 
            "variance_sample", "fs_noise_codes", "fs_profile_enable", "fs_profile_read", "fs_kernel_launches",
            "wilson_dslash_noalloc", "fs_server_create", "fs_server_submit", "fs_server_poll",
            "fs_server_stats", "fs_server_destroy", "fs_interp_variances", "fs_select_shifts",
-           "fs_sample_allocation", "fs_eval_grid", "fs_tuned_tile", "fs_probing_colors"]
+           "fs_sample_allocation", "fs_eval_grid", "fs_tuned_tile", "fs_probing_colors",
+           "variance_sample_probed"]
 JOB_MAX_LEVELS = 16
 
 
@@ -104,6 +105,8 @@ def load_library(path=LIB_PATH):
         "fs_mlmc_num_solves": (I, [ctypes.POINTER(MlmcParams)]),
         "variance_sample": (I, [P, D, dp, I, dp, ip, I, I, U64, U32, ctypes.POINTER(SolveParams), dp, dp, dp,
                                 dp, dp]),
+        "variance_sample_probed": (I, [P, D, dp, I, dp, ip, I, I, U64, U32, ctypes.POINTER(SolveParams),
+                                       ctypes.POINTER(ctypes.c_int32), I, I, dp, dp, dp, dp, dp]),
         "fs_noise_codes": (I, [P, U64, U32, U32, U32, ctypes.POINTER(ctypes.c_uint8)]),
         "fs_profile_enable": (I, [P, I]),
         "fs_profile_read": (I, [P, ctypes.POINTER(ctypes.c_longlong), dp, dp, dp]),
@@ -283,7 +286,10 @@ class Context:
                 "total": complex(tr.sum()), "v_fs": float((var / ns).sum()),
                 "stats": [_stats(s) for s in st[:nsolve]], "rc": rc}
 
-    def variance_sample(self, m, s_hat, gamma, p_list, n_s, seed, job=0, **kw):
+    def variance_sample(self, m, s_hat, gamma, p_list, n_s, seed, job=0, colors=None, ncolors=None, dilute=False,
+                        **kw):
+        """Sec. 3.1 variance sampling; colors / dilute select probed and diluted noise
+        (variance_sample_probed), each noise vector then summed over its pieces."""
         sh = np.ascontiguousarray(s_hat, dtype=np.float64)
         pl = np.ascontiguousarray(p_list, dtype=np.int32)
         ms, npl = sh.size, pl.size
@@ -294,10 +300,19 @@ class Context:
         b = np.zeros((n_s, npl, ms, ms, 2))
         iters = np.zeros(ms)
         prm = _params(**kw)
-        rc = self._check(self.lib.variance_sample(self.h, m, _dptr(sh), ms, _dptr(g),
-                                                  pl.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), npl, n_s,
-                                                  int(seed), int(job), ctypes.byref(prm), _dptr(VL), _dptr(Vbar),
-                                                  _dptr(a), _dptr(b), _dptr(iters)), allow_noconv=True)
+        plp = pl.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        if colors is None and not dilute:
+            rc = self._check(self.lib.variance_sample(self.h, m, _dptr(sh), ms, _dptr(g), plp, npl, n_s, int(seed),
+                                                      int(job), ctypes.byref(prm), _dptr(VL), _dptr(Vbar),
+                                                      _dptr(a), _dptr(b), _dptr(iters)), allow_noconv=True)
+        else:
+            col = None if colors is None else np.ascontiguousarray(colors, dtype=np.int32).ravel()
+            nc = 0 if col is None else (int(ncolors) if ncolors is not None else int(col.max()) + 1)
+            cp = None if col is None else col.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            rc = self._check(self.lib.variance_sample_probed(self.h, m, _dptr(sh), ms, _dptr(g), plp, npl, n_s,
+                                                             int(seed), int(job), ctypes.byref(prm), cp, nc,
+                                                             int(bool(dilute)), _dptr(VL), _dptr(Vbar), _dptr(a),
+                                                             _dptr(b), _dptr(iters)), allow_noconv=True)
         return {"VL": VL, "Vbar": Vbar, "a": a[..., 0] + 1j * a[..., 1], "b": b[..., 0] + 1j * b[..., 1],
                 "Vl": (sh[None, None, :] - sh[None, :, None]) ** 2 * Vbar, "iters": iters, "rc": rc}
 

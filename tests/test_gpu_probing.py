@@ -159,3 +159,72 @@ def test_bad_colour_tables_are_refused():
             ctx.mlmc_level_trace(-0.3, [0.1], np.eye(4), 0, [1], seed=1, colors=bad, ncolors=nc)
         assert e.value.code == pkg.fsmlmc.FS_ERR_ARG
     ctx.close()
+
+
+# ---------------------------------------------------------------- variance sampling
+def _cmp_variance(out, ref, tol):
+    for key in ("a", "b"):
+        scale = max(np.abs(ref[key]).max(), 1e-300)
+        assert np.abs(out[key] - ref[key]).max() < tol * scale, key
+    for key in ("VL", "Vbar"):
+        scale = max(np.abs(ref["a" if key == "VL" else "b"]).max() ** 2, 1e-300)
+        assert np.abs(out[key] - ref[key]).max() < 10 * tol * scale, key
+
+
+def test_variance_sample_probed_and_diluted():
+    """Full dilution takes y^(i) = +-gamma_5 x^(i) instead of the adjoint solve; the oracle solves
+    the adjoint system as written, so this checks the shortcut along with the pieces."""
+    dims = (4, 4, 4, 4)
+    u = inputs.gauge_field(dims, "smooth", seed=306, eps=0.5)
+    s_hat = [0.02, 0.2, 0.8]
+    col, nc = opr.greedy_coloring(dims, 1, 1)
+    ctx = make_ctx(dims, u)
+    out = ctx.variance_sample(-0.3, s_hat, pkg.gamma_matrix("g3"), [0, 1, 2], 2, seed=12, job=1, colors=col,
+                              ncolors=nc, dilute=True, prec="f64", tol=1e-12, rhs_tile=30)
+    assert out["rc"] == 0
+    solver = oest.make_dense_solver(u, -0.3, dims)
+    ref = opr.probed_variance_sample(u, -0.3, s_hat, odirac.gamma_product(["g3"]), [0, 1, 2], 2, 12, 1, dims, col,
+                                     nc, True, solver=solver)
+    _cmp_variance(out, ref, 1e-9)
+    ctx.close()
+
+
+def test_variance_sample_probed_without_dilution_mixed_precision():
+    dims = (4, 4, 4, 4)
+    u = inputs.gauge_field(dims, "smooth", seed=307, eps=0.4)
+    s_hat = [0.05, 0.5]
+    col, nc = opr.greedy_coloring(dims, 2, 0)
+    ctx = make_ctx(dims, u)
+    out = ctx.variance_sample(-0.25, s_hat, pkg.gamma_matrix("g5g3"), [1], 3, seed=13, colors=col, ncolors=nc,
+                              prec="f32", tol=1e-10, rhs_tile=32)
+    assert out["rc"] == 0
+    solver = oest.make_dense_solver(u, -0.25, dims)
+    ref = opr.probed_variance_sample(u, -0.25, s_hat, odirac.gamma_product(["g5", "g3"]), [1], 3, 13, 0, dims, col,
+                                     nc, False, solver=solver)
+    _cmp_variance(out, ref, 1e-6)
+    ctx.close()
+
+
+def test_variance_sample_single_site_colours_is_exact():
+    """Single-site colours and full dilution: a_i = Tr(Gamma Omega_p A_i) and
+    b_ij = Tr(A_i Gamma Omega_p A_j) for every noise vector (dense matrices, not the oracle's
+    sampling code), and both variances vanish."""
+    from oracle import solve as osolve
+    dims = (2, 2, 4, 2)
+    v = int(np.prod(dims))
+    u = inputs.gauge_field(dims, "haar", seed=308)
+    s_hat = [0.1, 0.6]
+    ctx = make_ctx(dims, u)
+    out = ctx.variance_sample(-0.2, s_hat, pkg.gamma_matrix("g3"), [0, 1], 2, seed=3, colors=np.arange(v),
+                              dilute=True, prec="f64", tol=1e-12, rhs_tile=64)
+    assert out["rc"] == 0
+    inv = [osolve.dense_inverse(u, -0.2, s, dims, -1) for s in s_hat]
+    for pi, p in enumerate([0, 1]):
+        g = osolve.dense_GammaOmega(u, odirac.gamma_product(["g3"]), p, dims)
+        for i in range(2):
+            ta = np.trace(g @ inv[i])
+            assert np.abs(out["a"][:, pi, i] - ta).max() <= 1e-9 * abs(ta)
+            for j in range(i, 2):
+                tb = np.trace(inv[i] @ g @ inv[j])
+                assert np.abs(out["b"][:, pi, i, j] - tb).max() <= 1e-9 * abs(tb)
+    ctx.close()
