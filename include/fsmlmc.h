@@ -124,6 +124,15 @@ typedef struct fs_mlmc_params {
                                [0, ncolors) with every colour used; NULL = no probing          */
   int ncolors;              /* number of colours when colors != NULL                         */
   int dilute;               /* 1: full spin-colour dilution (12 pieces per colour); 0: none  */
+  /* Hopping parameter expansion of the last level (Sec. 3.1, the remark after
+     Eq. (sampled_single)), applied when m + sigma_L > 0: with D + s = A (1 - kappa H),
+     A = 4 + m + s, kappa = 1 / (2A), the last level's samples become
+       T_exact + z^dag Gamma Omega_p (kappa H)^K (D + sigma_L)^-1 z,
+       T_exact = sum_{k<K} Tr(Gamma Omega_p (kappa H)^k) / A,
+     T_exact computed exactly from displacement-p distance-(K-1) probing vectors with full
+     spin-colour dilution (12 c FP64 vectors, K - 1 kappa H applications each). Same
+     expectation, lower variance. 0 = off; K in 1..8 (the paper uses 4). */
+  int hpe_order;
 } fs_mlmc_params;
 
 /* ---- context ------------------------------------------------------------------ */
@@ -221,12 +230,16 @@ int variance_sample(fs_ctx* ctx, double m, const double* s_hat, int m_shifts, co
  * no probing) and, with dilute = 1, to one spin-colour index (12 pieces per colour), and a_i,
  * b_ij are the sums over the pieces. With dilute = 1 every piece lives on one spin s, so
  * gamma_5 z = +-z and y^(i) = +-gamma_5 x^(i) needs no second solve: 12 c m N_s solves in all
- * (Sec. 3.1), against 2 m N_s c' without dilution (c' = ncolors or 1). Outputs and errors as
- * variance_sample; iters averages every solve at the shift. */
+ * (Sec. 3.1), against 2 m N_s c' without dilution (c' = ncolors or 1).
+ * hpe_order = K > 0: at every sampling shift with m + s_i > 0, a_i is the remainder of the
+ * hopping parameter expansion, z^dag Gamma Omega_p (kappa_i H)^K x^(i) (see fs_mlmc_params),
+ * so VL is the variance of the expanded estimator; its exact low orders shift every sample
+ * alike and are not added (Sec. 3.1: not needed for the sampling). b_ij is unchanged.
+ * Outputs and errors as variance_sample; iters averages every solve at the shift. */
 int variance_sample_probed(fs_ctx* ctx, double m, const double* s_hat, int m_shifts, const double* gamma,
                            const int* p, int np, int Ns, uint64_t seed, uint32_t job,
                            const fs_solve_params* params, const int32_t* colors, int ncolors, int dilute,
-                           double* VL, double* Vbar, double* a, double* b, double* iters);
+                           int hpe_order, double* VL, double* Vbar, double* a, double* b, double* iters);
 
 /* The Z4 noise vector (seed, job, level, sample) as integer codes k (z = i^k),
  * host [V][4][3] bytes, generated on the device (bit-exact RNG checks). */

@@ -460,6 +460,9 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double
   if (nsolve < 0) return c.fail(FS_ERR_ARG, "too many solves, or bad ncolors / dilute");
   const int npieces = num_pieces(P);
   const int ncomp = P->dilute ? 12 : 1;
+  if (P->hpe_order < 0 || P->hpe_order > 8) return c.fail(FS_ERR_ARG, "hpe_order must be in [0, 8]");
+  // the expansion converges for A = 4 + m + sigma > 4 only (Sec. 3.1 uses it where m + s > 0)
+  const bool hpe = P->hpe_order > 0 && P->m + P->sigma[L] > 0.0;
   if (P->colors) {
     // every site has a colour in range and every colour is used (no piece has an empty support)
     std::vector<char> used(P->ncolors, 0);
@@ -474,8 +477,6 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double
   Opts o;
   if (int rc = resolve_params(c, &P->solve, nsolve, P->m, o)) return rc;
   if (int rc = set_device(c)) return rc;
-  if (P->colors)
-    if (int rc = fs::upload_colors(&c, P->colors)) return rc;
   const std::vector<int> plist = {P->p};
   std::vector<double> csum(total * 2, 0.0);  // per-sample values, level-major
   std::vector<long long> off(L + 2, 0);
@@ -509,6 +510,10 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double
           q.sys = {fs::SysSpec{P->sigma[L], 0, -1, z}};
           q.stat_index = {si};
           q.pairs = {{0, 0, 0, si}};
+          if (hpe) {  // z^dag Gamma Omega_p (kappa H)^K x; the exact low orders are added below
+            q.sys[0].hpe = 1;
+            q.pairs[0].right_kind = 1;
+          }
           jobs.push_back(q);
         } else if (P->estimator == FS_EST_DIFF) {
           // the two solves of a DIFF sample are independent: one group each packs slots best
@@ -548,12 +553,25 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double
     if (P->estimator == FS_EST_PRODUCT)
       if (int rc = c.ensure_canon(T->N)) return rc;
   }
+  // exact low orders of the expansion (probing colours of their own, so computed before the
+  // caller's colours are uploaded), on the owner's tile
+  double t_exact[2] = {0.0, 0.0};
+  if (hpe) {
+    fs::TileBase* TE = T ? T : tile_for(c, jobs, o);
+    if (!TE) return c.fail(FS_ERR_OOM, "device allocation of the solver tile failed");
+    if (int rc = fs::ensure_wline(&c, 1 << P->p, P->p)) return rc;
+    if (int rc = fs::hpe_exact(&c, TE, o.so, P->sigma[L], P->hpe_order, P->p, P->gamma, P->seed, t_exact))
+      return rc;
+  }
+  if (P->colors)
+    if (int rc = fs::upload_colors(&c, P->colors)) return rc;
   std::vector<double> res;
   res.assign((size_t)nsolve * 2, 0.0);
   fs::QOut out;
   out.gamma = P->gamma;
   out.plist = &plist;
   out.rows = nsolve;
+  out.hpe_order = hpe ? P->hpe_order : 0;
   out.result = &res;
   out.states = &st;
   out.noconv = &noconv;
@@ -579,6 +597,10 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double
           const double ds = P->sigma[l + 1] - P->sigma[l];
           re += ds * res[(size_t)si * 2]; im += ds * res[(size_t)si * 2 + 1];
         }
+      }
+      if (l == L && hpe) {
+        re += t_exact[0];
+        im += t_exact[1];
       }
       csum[(off[l] + s) * 2] = re;
       csum[(off[l] + s) * 2 + 1] = im;
@@ -611,8 +633,9 @@ namespace {
 // y^(i) = gamma_5 (D+s_i)^-1 gamma_5 z = eps gamma_5 x^(i): no second solve (Sec. 3.1).
 int variance_sample_impl(Ctx& c, double m, const double* s_hat, int ms, const double* gamma, const int* p, int np,
                          int Ns, uint64_t seed, uint32_t job, const fs_solve_params* params, const int32_t* colors,
-                         int ncolors, int dilute, double* VL, double* Vbar, double* a_out, double* b_out,
-                         double* iters) {
+                         int ncolors, int dilute, int hpe_order, double* VL, double* Vbar, double* a_out,
+                         double* b_out, double* iters) {
+  if (hpe_order < 0 || hpe_order > 8) return c.fail(FS_ERR_ARG, "hpe_order must be in [0, 8]");
   if (!s_hat || !gamma || !p || !VL || !Vbar) return c.fail(FS_ERR_ARG, "null pointer");
   if (ms < 1 || 2 * ms > fs::MAX_TILE) return c.fail(FS_ERR_ARG, "m_shifts must be in [1, 32]");
   if (np < 1 || np > fs::CONTRACT_MAXP) return c.fail(FS_ERR_ARG, "np must be in [1, 16]");
@@ -677,7 +700,16 @@ int variance_sample_impl(Ctx& c, double m, const double* s_hat, int ms, const do
         for (int i = 0; i < ms; i++) g.sys.push_back(fs::SysSpec{s_hat[i], 0, -1, piece(true)});
       for (int i = 0; i < gsize; i++) g.stat_index.push_back((int)(gi * gsize + i));
       int row = (int)(gi * per);
-      for (int i = 0; i < ms; i++) g.pairs.push_back({i, i, 0, row++});  // a_i
+      for (int i = 0; i < ms; i++) {
+        // a_i; with the expansion (m + s_i > 0) the remainder z^dag Gamma Omega_p (kappa H)^K x^(i),
+        // whose variance is V_L (the exact low orders shift every sample alike)
+        fs::ContractPair q{i, i, 0, row++};
+        if (hpe_order > 0 && m + s_hat[i] > 0.0) {
+          g.sys[i].hpe = 1;
+          q.right_kind = 1;
+        }
+        g.pairs.push_back(q);
+      }
       for (int i = 0; i < ms; i++)
         for (int j = i; j < ms; j++)  // b_ij: y^(i) = gamma_5 x~^(i), x~ solved for gamma_5 z (or eps x^(i))
           g.pairs.push_back({j, dilute ? i : ms + i, 1, row++});
@@ -695,6 +727,7 @@ int variance_sample_impl(Ctx& c, double m, const double* s_hat, int ms, const do
   out.result = &res;
   out.states = &st;
   out.noconv = &noconv;
+  out.hpe_order = hpe_order;
   if (int rc = fs::run_queue(&c, T, groups, o.so, out)) return rc;
   // a noise vector's value of row r: the sum over its pieces (b rows carry eps with dilution)
   auto val = [&](int k, int r, int q, int ri) {
@@ -767,17 +800,17 @@ int variance_sample(fs_ctx* ctx, double m, const double* s_hat, int ms, const do
                     int Ns, uint64_t seed, uint32_t job, const fs_solve_params* params, double* VL, double* Vbar,
                     double* a_out, double* b_out, double* iters) {
   if (!ctx) return FS_ERR_ARG;
-  return variance_sample_impl(ctx->c, m, s_hat, ms, gamma, p, np, Ns, seed, job, params, nullptr, 0, 0, VL, Vbar,
-                              a_out, b_out, iters);
+  return variance_sample_impl(ctx->c, m, s_hat, ms, gamma, p, np, Ns, seed, job, params, nullptr, 0, 0, 0, VL,
+                              Vbar, a_out, b_out, iters);
 }
 
 int variance_sample_probed(fs_ctx* ctx, double m, const double* s_hat, int ms, const double* gamma, const int* p,
                            int np, int Ns, uint64_t seed, uint32_t job, const fs_solve_params* params,
-                           const int32_t* colors, int ncolors, int dilute, double* VL, double* Vbar, double* a_out,
-                           double* b_out, double* iters) {
+                           const int32_t* colors, int ncolors, int dilute, int hpe_order, double* VL, double* Vbar,
+                           double* a_out, double* b_out, double* iters) {
   if (!ctx) return FS_ERR_ARG;
   return variance_sample_impl(ctx->c, m, s_hat, ms, gamma, p, np, Ns, seed, job, params, colors, ncolors, dilute,
-                              VL, Vbar, a_out, b_out, iters);
+                              hpe_order, VL, Vbar, a_out, b_out, iters);
 }
 
 int fs_noise_codes(fs_ctx* ctx, uint64_t seed, uint32_t job, uint32_t level, uint32_t sample, uint8_t* codes) {

@@ -168,11 +168,14 @@ struct ContractPair {
   int left;       // slot of the left vector
   int left_kind;  // 0: noise of slot `left` ; 1: gamma_5 * solution of slot `left`
   int out;        // output row
+  int right_kind = 0;  // 0: the solution of slot `right` ; 1: slot `right` of the pair y_e / y_o
 };
 
 struct ContractArgs {
   const double* x_e;
   const double* x_o;
+  const double* y_e;      // right vectors of the right_kind 1 pairs (hopping parameter expansion)
+  const double* y_o;
   const double* wline;    // W(x, x + q z) for the requested q > 0: [k][18][2 Vh], k counts them
   const NoiseSpec* spec;
   const int* colors;      // probing colour per canonical site (colour-restricted noise only)
@@ -295,8 +298,8 @@ __global__ void __launch_bounds__(256) contract_kernel(ContractArgs a) {
       y[2] = (x[2] + q) % g.L[2];
       const int ypar = (y[0] + y[1] + y[2] + y[3]) & 1;
       double psi[24];
-      make_field<double>(const_cast<double*>(ypar ? a.x_o : a.x_e), g.Vh, a.N, true)
-          .load(cb_index(g, y), pr.right, psi);
+      const double* rf = pr.right_kind ? (ypar ? a.y_o : a.y_e) : (ypar ? a.x_o : a.x_e);
+      make_field<double>(const_cast<double*>(rf), g.Vh, a.N, true).load(cb_index(g, y), pr.right, psi);
       if (z4) {
         // c_q += sum_t eta_t^dag R_t, eta_t = W^dag xi_t (xi_t = i^code per colour)
         double u[18];

@@ -13,6 +13,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <numeric>
+
+#include "fsmlmc.h"
 
 namespace fs {
 
@@ -164,6 +167,91 @@ int autotune_tile(Ctx* c, const SolveOpts& o, int nmax) {
   return best;
 }
 
+// Exact low orders of the hopping parameter expansion. D + s = A (1 - kappa H), so
+// (D + s)^-1 = sum_{k<K} (kappa H)^k / A + (kappa H)^K (D + s)^-1, and the traces of the first K
+// terms are deterministic. Order 0 is Tr(Gamma Omega_p) = 3 V tr(Gamma) for p = 0 (Omega_p moves
+// every site otherwise). Orders 1..K-1 link site x only to sites within distance K - 1 of x + p z,
+// so with displacement-p distance-(K-1) colours no two distinct sites of one colour are linked,
+// and for the pieces e (one colour, one spin-colour index, unit-modulus Z4 entries)
+// sum_e e^dag Gamma Omega_p (kappa H)^k e is the trace exactly. The pieces fill the tile N at a
+// time; each power is one FP64 kappa H application (work list over the pieces) and one
+// contraction.
+int hpe_exact(Ctx* c, TileBase* T, const SolveOpts& o, double sigma, int K, int p, const double* gamma,
+              uint64_t seed, double out[2]) {
+  const double A = 4.0 + o.m + sigma;
+  double tr = 0.0, ti = 0.0;
+  const int pz = p % c->g.L[2];
+  if (pz == 0)
+    for (int s = 0; s < 4; s++) {
+      tr += 3.0 * c->g.V * gamma[(s * 4 + s) * 2];
+      ti += 3.0 * c->g.V * gamma[(s * 4 + s) * 2 + 1];
+    }
+  if (K > 1) {
+    std::vector<int32_t> colors((size_t)c->g.V);
+    int nc = 0;
+    if (int rc = fs_probing_colors(c->g.L, K - 1, pz, colors.data(), &nc))
+      return c->fail(rc, "probing colours of the hopping parameter expansion");
+    if (int rc = upload_colors(c, colors.data())) return rc;
+    const int N = T->N;
+    const long long npieces = 12LL * nc;
+    const std::vector<int> plist = {p};
+    std::vector<int> all(N);
+    std::iota(all.begin(), all.end(), 0);
+    cudaError_t e;
+    for (long long base = 0; base < npieces; base += N) {
+      const int nb = (int)std::min<long long>(N, npieces - base);
+      // the host mirrors are rewritten below: every earlier upload must have executed
+      if ((e = cudaStreamSynchronize(c->stream))) return c->cuda_fail(e, "hopping parameter expansion");
+      std::vector<ContractPair> pairs;
+      for (int j = 0; j < N; j++) {
+        if (j < nb) {
+          init_state(T->st_h[j], sigma, o);  // FLAG_INIT: the noise kernel writes the piece
+          T->st_h[j].flags |= FLAG_HPE;
+          NoiseSpec n{};
+          n.key0 = (uint32_t)(seed & 0xFFFFFFFFull);
+          n.key1 = (uint32_t)(seed >> 32);
+          n.level = 0x40000000u;
+          n.flags = NOISE_VALID | NOISE_RHS | NOISE_COLOR | NOISE_COMP;
+          n.color = (int)((base + j) / 12);
+          n.comp = (int)((base + j) % 12);
+          T->spec_h[j] = n;
+          ContractPair q{j, j, 0, j};
+          q.right_kind = 1;
+          pairs.push_back(q);
+        } else {
+          memset(&T->st_h[j], 0, sizeof(SysState));
+          memset(&T->spec_h[j], 0, sizeof(NoiseSpec));
+        }
+      }
+      if ((e = upload_slots(c, T, all))) return c->cuda_fail(e, "hopping parameter expansion");
+      if ((e = T->enqueue_noise())) return c->cuda_fail(e, "hopping parameter expansion");
+      int from = PAIR_Z;
+      for (int k = 1; k < K; k++) {
+        const int to = (from == PAIR_S) ? PAIR_X : PAIR_S;
+        if ((e = T->enqueue_kappa_hop(from, to))) return c->cuda_fail(e, "hopping parameter expansion");
+        std::vector<double> part;
+        if (int rc = contract_tile(c, T, pairs, gamma, plist, part, N, to)) return rc;
+        for (int j = 0; j < nb; j++) {
+          tr += part[(size_t)j * 2];
+          ti += part[(size_t)j * 2 + 1];
+        }
+        from = to;
+      }
+    }
+    // leave the tile idle for the solves
+    if ((e = cudaStreamSynchronize(c->stream))) return c->cuda_fail(e, "hopping parameter expansion");
+    for (int j = 0; j < N; j++) {
+      memset(&T->st_h[j], 0, sizeof(SysState));
+      memset(&T->spec_h[j], 0, sizeof(NoiseSpec));
+    }
+    if ((e = upload_slots(c, T, all))) return c->cuda_fail(e, "hopping parameter expansion");
+    if ((e = cudaStreamSynchronize(c->stream))) return c->cuda_fail(e, "hopping parameter expansion");
+  }
+  out[0] = tr / A;
+  out[1] = ti / A;
+  return 0;
+}
+
 int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpts& o, const QOut& out) {
   const int N = T->N;
   for (const QJob& q : jobs)
@@ -308,6 +396,29 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
       if (out.states && !si.empty() && si[slot[j].member] >= 0) (*out.states)[si[slot[j].member]] = T->st_h[j];
     }
 
+    // hopping parameter expansion: y = (kappa H)^K x for the finished systems that take it
+    // (their right-hand side and scratch pairs are free now; x stays for the other contractions)
+    int right_pair = PAIR_X;
+    if (out.hpe_order > 0 && !done_jobs.empty()) {
+      std::vector<int> hpe_slots;
+      for (int j = 0; j < N; j++)
+        if (slot[j].job >= 0 && slot[j].done && jobs[slot[j].job].sys[slot[j].member].hpe &&
+            std::find(done_jobs.begin(), done_jobs.end(), slot[j].job) != done_jobs.end()) {
+          T->st_h[j].flags |= FLAG_HPE;
+          hpe_slots.push_back(j);
+        }
+      if (!hpe_slots.empty()) {
+        if ((e = upload_slots(c, T, hpe_slots))) return c->cuda_fail(e, "upload expansion flags");
+        int from = PAIR_X;
+        for (int k = 0; k < out.hpe_order; k++) {
+          const int to = (k % 2 == 0) ? PAIR_S : PAIR_Z;
+          if ((e = T->enqueue_kappa_hop(from, to))) return c->cuda_fail(e, "hopping parameter expansion");
+          from = to;
+        }
+        right_pair = hpe_result_pair(out.hpe_order);
+      }
+    }
+
     // contractions of the completed groups
     if (out.result && np > 0 && !done_jobs.empty()) {
       std::vector<ContractPair> pairs;
@@ -323,7 +434,7 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
       }
       if (!pairs.empty()) {
         std::vector<double> part;
-        if (int rc = contract_tile(c, T, pairs, out.gamma, *out.plist, part, out.rows)) return rc;
+        if (int rc = contract_tile(c, T, pairs, out.gamma, *out.plist, part, out.rows, right_pair)) return rc;
         for (const ContractPair& p : pairs)
           for (int q2 = 0; q2 < np * 2; q2++)
             (*out.result)[(size_t)p.out * np * 2 + q2] = part[(size_t)p.out * np * 2 + q2];

@@ -404,6 +404,25 @@ class Tile : public TileBase {
     return fin(FIN_VERIFY, MASK_HARVEST, pa, pb);
   }
 
+  double* field_pair(int id, int parity) override {
+    if (id == PAIR_X) return parity ? x_o : x_hi;
+    if (id == PAIR_Z) return parity ? z_o : z_e;
+    return parity ? tmp64 : r_hi;
+  }
+
+  cudaError_t enqueue_kappa_hop(int from, int to) override {
+    L1.stream = c->stream;
+    LW.stream = c->stream;
+    // even <- kappa H_eo (odd), odd <- kappa H_oe (even); FP64 work list over the FLAG_HPE slots
+    cudaError_t e = launch_hop<double>(COEF_KAPPA, DOT_NONE, 18,
+                                       hop(field_pair(to, 0), field_pair(from, 1), nullptr, nullptr, nullptr, nullptr,
+                                           0, MASK_HPE, false, true, true), lwh());
+    if (e) return e;
+    return launch_hop<double>(COEF_KAPPA, DOT_NONE, 18,
+                              hop(field_pair(to, 1), field_pair(from, 0), nullptr, nullptr, nullptr, nullptr, 1,
+                                  MASK_HPE, false, true, true), lwh());
+  }
+
   cudaError_t enqueue_dslash(double* canon) override {
     L.stream = c->stream;
     // in: canon[vec[j]] -> (p, tmp) ; out = (D + sigma) in -> (v, s) -> canon[vec[j]]
@@ -570,7 +589,7 @@ int upload_colors(Ctx* c, const int* colors) {
 }
 
 int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, const double* gamma,
-                  const std::vector<int>& plist, std::vector<double>& result, int rows) {
+                  const std::vector<int>& plist, std::vector<double>& result, int rows, int right_pair) {
   const int np = (int)plist.size();
   const int npairs = (int)pairs.size();
   if (npairs == 0) return 0;
@@ -589,6 +608,8 @@ int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, c
   cudaError_t e;
   if (int rc = ensure_wline(c, pmask, pmax)) return rc;
   a.x_e = T->x_hi; a.x_o = T->x_o; a.wline = c->wline; a.spec = T->spec_d; a.colors = c->colors_d;
+  a.y_e = T->field_pair(right_pair, 0);
+  a.y_o = T->field_pair(right_pair, 1);
   for (int k = 0; k < 32; k++) a.gamma[k] = gamma[k];
   // detect a monomial Gamma (one entry per row, each +-1 or +-i): applied as a permutation
   a.gmono = 1;

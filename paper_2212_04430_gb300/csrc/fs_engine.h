@@ -84,6 +84,12 @@ class TileBase {
   virtual cudaError_t enqueue_verify() = 0;
   virtual cudaError_t enqueue_solution_to_canon(double* canon) = 0;  // canon[vec[j]] <- x for all j with vec >= 0
   virtual cudaError_t enqueue_dslash(double* canon) = 0;  // canon[vec[j]] <- (D + sigma_j) canon[vec[j]], INIT slots
+  // FP64 field pairs (even, odd) of every slot: PAIR_X the solution (x_hi, x_o), PAIR_Z the
+  // right-hand side (z_e, z_o), PAIR_S scratch (r_hi and the FP64 temporary); the last two are
+  // free once a system has finished
+  virtual double* field_pair(int id, int parity) = 0;
+  // pair `to` <- kappa H (pair `from`), full lattice, FP64, for the FLAG_HPE slots
+  virtual cudaError_t enqueue_kappa_hop(int from, int to) = 0;
   // CGNR fallback (FP64) for the slots flagged FLAG_CG; its vectors are allocated on first use
   virtual int cg_alloc() = 0;
   virtual cudaError_t enqueue_cg_init() = 0;
@@ -141,12 +147,16 @@ int ensure_wline(Ctx* c, int pmask, int pmax);
 // Copies the probing colours (host, [V] in canonical site order) to c->colors_d, on c's stream.
 int upload_colors(Ctx* c, const int* colors);
 
+enum { PAIR_X = 0, PAIR_Z = 1, PAIR_S = 2 };
+
 // One system to solve.
 struct SysSpec {
   double sigma;
   int rhs_kind;        // 0: Z4 noise, 1: canonical vector `vec` (device staging)
   int vec;             // canonical vector index for rhs_kind 1
   NoiseSpec noise;     // noise identity (the right-hand side and/or the contraction's left vector)
+  int hpe = 0;         // 1: the solution takes QOut::hpe_order kappa H applications (into the field
+                       // pair of hpe_result_pair) before the contractions that read it (right_kind 1)
 };
 
 struct SolveOpts {
@@ -182,7 +192,12 @@ struct QOut {
   double* x_host = nullptr;                 // solutions, [out_index][V][24]
   int canon_out_base = 0;                   // staging vectors [base, base + N) for outputs
   int canon_chain_base = 0;                 // staging vectors [base, base + N) for follow-up rhs
+  int hpe_order = 0;                        // K of the hopping parameter expansion (SysSpec::hpe)
 };
+
+// Field pair that holds (kappa H)^K x after the expansion's K hops from PAIR_X (alternating
+// between PAIR_S and PAIR_Z).
+inline int hpe_result_pair(int K) { return (K % 2) ? PAIR_S : PAIR_Z; }
 
 // Continuous batching of the jobs over the slots of tile T (fs_driver.cu).
 int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpts& o, const QOut& out);
@@ -191,9 +206,18 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
 // nmax; measured once per context and format, then cached in c->tuned_tile. 0 on failure.
 int autotune_tile(Ctx* c, const SolveOpts& o, int nmax);
 
-// Contractions over the solutions held in a tile.
+// Contractions over the solutions held in a tile; pairs with right_kind 1 read their right vector
+// from field pair `right_pair` instead of the solution.
 int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, const double* gamma,
-                  const std::vector<int>& plist, std::vector<double>& result /* [rows][np][2] */, int rows);
+                  const std::vector<int>& plist, std::vector<double>& result /* [rows][np][2] */, int rows,
+                  int right_pair = PAIR_X);
+
+// Exact low orders of the hopping parameter expansion (Sec. 3.1, the remark after
+// Eq. (sampled_single)): T = sum_{k<K} Tr(Gamma Omega_p (kappa H)^k) / A, A = 4 + m + sigma,
+// from displacement-p distance-(K-1) probing vectors with full spin-colour dilution on the idle
+// tile T (fs_driver.cu). out = {re, im}; 0 or an error code (message in c->err).
+int hpe_exact(Ctx* c, TileBase* T, const SolveOpts& o, double sigma, int K, int p, const double* gamma,
+              uint64_t seed, double out[2]);
 
 double* pinned_alloc(size_t bytes);
 void note_launch(int n = 1);          // library-wide count of kernel launches

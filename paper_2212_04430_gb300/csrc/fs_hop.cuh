@@ -26,6 +26,7 @@ enum Coef {
   COEF_RECON = 4,    // out = X / A + H in / (2A)         x_o = A^-1 (z_o - D_oe x_e)
   COEF_TRUERES = 5,  // out = Y - A X + H in / (4A)       r = bhat - M x
   COEF_FULLRES = 6,  // out = Y - A X + H in / 2          r = z - (D + sigma) x on one parity
+  COEF_KAPPA = 7,    // out = H in / (2A) = kappa H in     hopping parameter expansion, D + s = A (1 - kappa H)
 };
 
 // Dot products a hop kernel forms with its output (out) per (8-site group, system):
@@ -39,7 +40,7 @@ template <> struct DotK<DOT_TS> { static constexpr int K = 8; };
 template <> struct DotK<DOT_NORM> { static constexpr int K = 1; };
 
 enum Mask { MASK_ALL = 0, MASK_ACTIVE = 1, MASK_UPDATE = 2, MASK_INIT = 3, MASK_HARVEST = 4, MASK_CG = 5,
-            MASK_CG_CHECK = 6 };
+            MASK_CG_CHECK = 6, MASK_HPE = 7 };
 
 __device__ __forceinline__ bool selected(const SysState* st, int sys, int mask) {
   if (mask == MASK_ALL) return true;
@@ -51,6 +52,7 @@ __device__ __forceinline__ bool selected(const SysState* st, int sys, int mask) 
   if (mask == MASK_CG) return s == SYS_ACTIVE && (f & FLAG_CG);
   if (mask == MASK_CG_CHECK) return s == SYS_ACTIVE && (f & FLAG_CG) && (f & FLAG_UPDATE);
   if (mask == MASK_INIT) return (f & FLAG_INIT) != 0;
+  if (mask == MASK_HPE) return (f & FLAG_HPE) != 0;
   return (f & FLAG_HARVEST) != 0;
 }
 
@@ -456,6 +458,7 @@ __global__ void __launch_bounds__(WL ? 128 : 256, WL ? 3 : (sizeof(Tm) == 8 ? 2 
       else if (COEF == COEF_RECON) { ca = coef<Tm>(s, C_INVA); cb = coef<Tm>(s, C_INV2A); }
       else if (COEF == COEF_TRUERES) { ca = coef<Tm>(s, C_MINVA); cb = coef<Tm>(s, C_INV4A); }
       else if (COEF == COEF_FULLRES) { ca = coef<Tm>(s, C_MINVA); cb = (Tm)0.5; }
+      else if (COEF == COEF_KAPPA) { cb = coef<Tm>(s, C_INV2A); }
     }
     const int site = chunk * sh.SB + lsite;
     const bool act = sel && site < g.Vh;
@@ -480,6 +483,9 @@ __global__ void __launch_bounds__(WL ? 128 : 256, WL ? 3 : (sizeof(Tm) == 8 ? 2 
       if (COEF == COEF_PLAIN) {
 #pragma unroll
         for (int k = 0; k < 24; k++) o[k] = acc[k];
+      } else if (COEF == COEF_KAPPA) {
+#pragma unroll
+        for (int k = 0; k < 24; k++) o[k] = cb * acc[k];
       } else {
         Tm xv[24];
         make_field<Ts>(const_cast<void*>(a.X), g.Vh, sh.N, smj).load(site, sys, xv);

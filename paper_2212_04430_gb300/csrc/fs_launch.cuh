@@ -93,6 +93,7 @@ cudaError_t launch_hop(int coef, int dot, int nr, const HopArgs& a, const Launch
     FS_HOP(COEF_RECON, DOT_NONE, 18)
     FS_HOP(COEF_TRUERES, DOT_NORM, 18)
     FS_HOP(COEF_FULLRES, DOT_NORM, 18)
+    FS_HOP(COEF_KAPPA, DOT_NONE, 18)  // hopping parameter expansion
   } else {
     FS_HOP_PF(COEF_PLAIN, DOT_NONE, 18)
     FS_HOP_PF(COEF_DSLASH, DOT_NONE, 18)

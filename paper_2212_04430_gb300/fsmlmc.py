@@ -54,7 +54,8 @@ class MlmcParams(ctypes.Structure):
                 ("sigma", ctypes.POINTER(ctypes.c_double)), ("n_samples", ctypes.POINTER(ctypes.c_int)),
                 ("gamma", ctypes.POINTER(ctypes.c_double)), ("seed", ctypes.c_uint64),
                 ("job", ctypes.c_uint32), ("estimator", ctypes.c_int), ("solve", SolveParams),
-                ("colors", ctypes.POINTER(ctypes.c_int32)), ("ncolors", ctypes.c_int), ("dilute", ctypes.c_int)]
+                ("colors", ctypes.POINTER(ctypes.c_int32)), ("ncolors", ctypes.c_int), ("dilute", ctypes.c_int),
+                ("hpe_order", ctypes.c_int)]
 
 
 class Job(ctypes.Structure):
@@ -106,7 +107,7 @@ def load_library(path=LIB_PATH):
         "variance_sample": (I, [P, D, dp, I, dp, ip, I, I, U64, U32, ctypes.POINTER(SolveParams), dp, dp, dp,
                                 dp, dp]),
         "variance_sample_probed": (I, [P, D, dp, I, dp, ip, I, I, U64, U32, ctypes.POINTER(SolveParams),
-                                       ctypes.POINTER(ctypes.c_int32), I, I, dp, dp, dp, dp, dp]),
+                                       ctypes.POINTER(ctypes.c_int32), I, I, I, dp, dp, dp, dp, dp]),
         "fs_noise_codes": (I, [P, U64, U32, U32, U32, ctypes.POINTER(ctypes.c_uint8)]),
         "fs_profile_enable": (I, [P, I]),
         "fs_profile_read": (I, [P, ctypes.POINTER(ctypes.c_longlong), dp, dp, dp]),
@@ -250,9 +251,10 @@ class Context:
         return x.view(np.complex128)[..., 0], [_stats(s) for s in st], rc
 
     def mlmc_level_trace(self, m, sigmas, gamma, p, n_samples, seed, job=0, estimator="diff", colors=None,
-                         ncolors=None, dilute=False, **kw):
+                         ncolors=None, dilute=False, hpe_order=0, **kw):
         """Level traces; colors ([V] probing colours, canonical order) and dilute (full spin-colour
-        dilution) make every sample the sum of the estimator over its pieces."""
+        dilution) make every sample the sum of the estimator over its pieces; hpe_order = K uses
+        the hopping parameter expansion on the last level when m + sigma_L > 0."""
         sig = np.ascontiguousarray(sigmas, dtype=np.float64)
         ns = np.ascontiguousarray(n_samples, dtype=np.int32)
         if ns.size == 1 and sig.size > 1:
@@ -270,6 +272,7 @@ class Context:
         P.estimator = ESTIMATOR[estimator] if isinstance(estimator, str) else int(estimator)
         P.solve = _params(**kw)
         keep = _set_probing(P, colors, ncolors, dilute)  # noqa: F841 (alive through the call)
+        P.hpe_order = int(hpe_order)
         nsolve = self.lib.fs_mlmc_num_solves(ctypes.byref(P))
         if nsolve < 0:
             raise FsError(1, "fs_mlmc_num_solves: bad sample counts, ncolors or dilute")
@@ -287,9 +290,9 @@ class Context:
                 "stats": [_stats(s) for s in st[:nsolve]], "rc": rc}
 
     def variance_sample(self, m, s_hat, gamma, p_list, n_s, seed, job=0, colors=None, ncolors=None, dilute=False,
-                        **kw):
-        """Sec. 3.1 variance sampling; colors / dilute select probed and diluted noise
-        (variance_sample_probed), each noise vector then summed over its pieces."""
+                        hpe_order=0, **kw):
+        """Sec. 3.1 variance sampling; colors / dilute select probed and diluted noise and
+        hpe_order the hopping parameter expansion of a_i (variance_sample_probed)."""
         sh = np.ascontiguousarray(s_hat, dtype=np.float64)
         pl = np.ascontiguousarray(p_list, dtype=np.int32)
         ms, npl = sh.size, pl.size
@@ -301,7 +304,7 @@ class Context:
         iters = np.zeros(ms)
         prm = _params(**kw)
         plp = pl.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
-        if colors is None and not dilute:
+        if colors is None and not dilute and not hpe_order:
             rc = self._check(self.lib.variance_sample(self.h, m, _dptr(sh), ms, _dptr(g), plp, npl, n_s, int(seed),
                                                       int(job), ctypes.byref(prm), _dptr(VL), _dptr(Vbar),
                                                       _dptr(a), _dptr(b), _dptr(iters)), allow_noconv=True)
@@ -311,7 +314,8 @@ class Context:
             cp = None if col is None else col.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
             rc = self._check(self.lib.variance_sample_probed(self.h, m, _dptr(sh), ms, _dptr(g), plp, npl, n_s,
                                                              int(seed), int(job), ctypes.byref(prm), cp, nc,
-                                                             int(bool(dilute)), _dptr(VL), _dptr(Vbar), _dptr(a),
+                                                             int(bool(dilute)), int(hpe_order), _dptr(VL),
+                                                             _dptr(Vbar), _dptr(a),
                                                              _dptr(b), _dptr(iters)), allow_noconv=True)
         return {"VL": VL, "Vbar": Vbar, "a": a[..., 0] + 1j * a[..., 1], "b": b[..., 0] + 1j * b[..., 1],
                 "Vl": (sh[None, None, :] - sh[None, :, None]) ** 2 * Vbar, "iters": iters, "rc": rc}
@@ -434,7 +438,7 @@ class Server:
             raise FsError(rc, "fs_server_create failed")
 
     def submit(self, dims, U, m, sigmas, gamma, p, n_samples, seed, job=0, estimator="diff", bc_t=-1, colors=None,
-               ncolors=None, dilute=False, **kw):
+               ncolors=None, dilute=False, hpe_order=0, **kw):
         """Queue one trace job (arrays are copied); returns the ticket."""
         u = _real(U)
         sig = np.ascontiguousarray(sigmas, dtype=np.float64)
@@ -457,6 +461,7 @@ class Server:
         P.estimator = ESTIMATOR[estimator] if isinstance(estimator, str) else int(estimator)
         P.solve = _params(**kw)
         keep = _set_probing(P, colors, ncolors, dilute)  # noqa: F841 (alive through the call)
+        P.hpe_order = int(hpe_order)
         t = ctypes.c_uint64()
         rc = self.lib.fs_server_submit(self.h, ctypes.byref(J), ctypes.byref(t))
         if rc != FS_OK:
