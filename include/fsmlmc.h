@@ -131,7 +131,8 @@ typedef struct fs_mlmc_params {
        T_exact = sum_{k<K} Tr(Gamma Omega_p (kappa H)^k) / A,
      T_exact computed exactly from displacement-p distance-(K-1) probing vectors with full
      spin-colour dilution (12 c FP64 vectors, K - 1 kappa H applications each). Same
-     expectation, lower variance. 0 = off; K in 1..8 (the paper uses 4). */
+     expectation, lower variance. 0 = off; K in 1..8 (the paper uses 4); needs p < Lz
+     (FS_ERR_ARG otherwise). */
   int hpe_order;
 } fs_mlmc_params;
 

@@ -463,6 +463,8 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double
   if (P->hpe_order < 0 || P->hpe_order > 8) return c.fail(FS_ERR_ARG, "hpe_order must be in [0, 8]");
   // the expansion converges for A = 4 + m + sigma > 4 only (Sec. 3.1 uses it where m + s > 0)
   const bool hpe = P->hpe_order > 0 && P->m + P->sigma[L] > 0.0;
+  // the exact low orders take Omega_0 = 1; a displacement of a whole period is a Polyakov loop
+  if (hpe && P->p >= c.g.L[2]) return c.fail(FS_ERR_ARG, "hpe_order needs p < Lz");
   if (P->colors) {
     // every site has a colour in range and every colour is used (no piece has an empty support)
     std::vector<char> used(P->ncolors, 0);

@@ -180,7 +180,8 @@ int hpe_exact(Ctx* c, TileBase* T, const SolveOpts& o, double sigma, int K, int 
               uint64_t seed, double out[2]) {
   const double A = 4.0 + o.m + sigma;
   double tr = 0.0, ti = 0.0;
-  const int pz = p % c->g.L[2];
+  if (p < 0 || p >= c->g.L[2]) return c->fail(1, "the expansion's exact part needs 0 <= p < Lz");
+  const int pz = p;
   if (pz == 0)
     for (int s = 0; s < 4; s++) {
       tr += 3.0 * c->g.V * gamma[(s * 4 + s) * 2];

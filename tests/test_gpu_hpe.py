@@ -162,3 +162,32 @@ def test_variance_sampling_with_the_expansion():
     assert np.abs(out["b"] - plain["b"]).max() < 1e-9 * np.abs(plain["b"]).max()
     assert np.allclose(out["VL"], oest.practical_variance(a_ref), rtol=1e-7, atol=1e-12)
     ctx.close()
+
+
+def test_expansion_edge_cases():
+    """Order 1 (the exact part is order 0 alone, no probing); the product estimator's last level;
+    m + sigma_L <= 0 leaves the samples plain; p >= Lz and orders outside 0..8 are refused."""
+    dims = (4, 4, 4, 4)
+    v = int(np.prod(dims))
+    u = inputs.gauge_field(dims, "smooth", seed=406, eps=0.4)
+    g = pkg.gamma_matrix("g3")
+    go = odirac.gamma_product(["g3"])
+    ctx = make_ctx(dims, u)
+    kw = dict(prec="f64", tol=1e-12, rhs_tile=8)
+    solver = oest.make_dense_solver(u, -0.1, dims)
+    # K = 1, p = 0: T_exact = 3V tr(Gamma) / A = 0 for gamma_3; the remainder takes one kappa H
+    one = ctx.mlmc_level_trace(-0.1, [0.2, 0.5], g, 0, [1, 3], seed=4, estimator="product", hpe_order=1, **kw)
+    assert one["rc"] == 0
+    for s in range(3):
+        z = philox.z4_noise(v, 4, 0, 1, s)
+        ref = ohpe.stochastic_part(u, solver, z, -0.1, 0.5, go, 0, 1, dims)
+        assert abs(one["samples"][1][s] - ref) < 1e-9 * max(1.0, abs(ref))
+    # m + sigma_L <= 0: no expansion
+    a = ctx.mlmc_level_trace(-0.6, [0.3], g, 1, [2], seed=5, hpe_order=4, **kw)
+    b = ctx.mlmc_level_trace(-0.6, [0.3], g, 1, [2], seed=5, **kw)
+    assert np.array_equal(a["samples"][0], b["samples"][0])
+    for bad in (dict(p=4, hpe_order=4), dict(p=1, hpe_order=9), dict(p=1, hpe_order=-1)):
+        with pytest.raises(pkg.FsError) as e:
+            ctx.mlmc_level_trace(-0.1, [0.5], g, bad["p"], [1], seed=1, hpe_order=bad["hpe_order"], **kw)
+        assert e.value.code == pkg.fsmlmc.FS_ERR_ARG
+    ctx.close()
