@@ -381,17 +381,19 @@ def run_serving(pkg, inputs, device, n_jobs, rate=20.0, budget_gb=60, max_active
 
 
 # --------------------------------------------------------------------------- the full method
-def run_pipeline(pkg, ctx, w, kw, levels=4, n_s=5, n_ref=512, n_max=128, seed=9000):
+def run_pipeline(pkg, ctx, w, kw, levels=4, n_s=5, n_ref=512, n_max=128, seed=9000, hpe_order=0):
     """The paper's procedure end to end on the workload's lattice: variance sampling at the
     sampling shifts (Sec. 3.1, N_s = 5 as in the paper), interpolation and optimal shifts
     (Sec. 3.2-3.3), sample allocation for a target variance (Eq. (num_samples)), then the
     split-even level traces (Eq. (fs_trace_est)) whose variance the sampling predicts.
     Target: the variance of a single-level estimator at sigma_0 with n_ref vectors. N_l is
-    capped at n_max to bound the run; the measured V_l are compared with the predictions."""
+    capped at n_max to bound the run; the measured V_l are compared with the predictions.
+    hpe_order = K follows the paper further: V_L is sampled with the hopping parameter expansion
+    at the sampling shifts with m + s > 0, and the last level uses it when m + sigma_L > 0."""
     s_hat = [w["sigmas"][0], 0.05, 0.25, 0.5, 1.0]  # sigma_0 = the workload's first shift
     gam = pkg.gamma_matrix(w["gamma"])
     t0 = time.time()
-    vs = ctx.variance_sample(w["m"], s_hat, gam, [w["p"]], n_s, seed=seed, job=1, **kw)
+    vs = ctx.variance_sample(w["m"], s_hat, gam, [w["p"]], n_s, seed=seed, job=1, hpe_order=hpe_order, **kw)
     t_vs = time.time() - t0
     s = pkg.fs_eval_grid(s_hat)
     t1 = time.perf_counter()
@@ -402,11 +404,12 @@ def run_pipeline(pkg, ctx, w, kw, levels=4, n_s=5, n_ref=512, n_max=128, seed=90
     n_use = [int(min(max(1, np.ceil(x)), n_max)) for x in N]
     t2 = time.time()
     out = ctx.mlmc_level_trace(w["m"], sel["sigma"], gam, w["p"], n_use, seed=seed, job=2, estimator="split_even",
-                               **kw)
+                               hpe_order=hpe_order, **kw)
     t_tr = time.time() - t2
     var_meas = [float(v) for v in out["var"]]
     import math
-    return {"sampling_shifts": s_hat, "n_s": n_s, "evaluation_shifts": len(s), "levels": levels,
+    return {"hpe_order": hpe_order, "sampling_shifts": s_hat, "n_s": n_s, "evaluation_shifts": len(s),
+            "levels": levels,
             "sigma": [float(x) for x in sel["sigma"]],
             "V_pred": [float(x) for x in sel["V"]], "V_meas": var_meas,
             "iters_sampled": [float(x) for x in vs["iters"]], "C_pred": [float(x) for x in sel["C"]],
@@ -647,6 +650,8 @@ def main():
     pipeline = None
     if not args.no_pipeline and rank == 0:
         pipeline = run_pipeline(pkg, ctx, w, kw)
+        # the paper's variant: V_L sampled with the hopping parameter expansion (order 4) where m + s > 0
+        pipeline["with_hpe"] = run_pipeline(pkg, ctx, w, kw, hpe_order=4)
 
     probing = None
     if not args.no_probing and rank == 0:
