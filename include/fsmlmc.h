@@ -176,6 +176,15 @@ int wilson_dslash(fs_ctx* ctx, double m, double sigma, const double* in, double*
 int shifted_solve(fs_ctx* ctx, double m, const double* sigma, int nshift, const double* b, int nrhs,
                   double* x, const fs_solve_params* params, fs_sys_stats* stats);
 
+/* shifted_solve on caller-owned device arrays (e.g. torch tensors): b device [nrhs][V][24],
+ * x device [nshift][nrhs][V][24] (canonical layout, FP64), both on the context's GPU and
+ * 16-byte aligned (FS_ERR_ARG otherwise); sigma and stats stay on the host. The work runs on
+ * the context's stream (fs_set_stream) and the call returns when x is written. b is read in
+ * place and not checked for non-finite values (they surface as FS_ERR_NOCONV). Same arithmetic
+ * as shifted_solve: the solutions are identical. */
+int shifted_solve_dev(fs_ctx* ctx, double m, const double* sigma, int nshift, const double* b, int nrhs,
+                      double* x, const fs_solve_params* params, fs_sys_stats* stats);
+
 /* FS-MLMC trace estimate, Eq. (fs_trace_est): for every level l < nlev, N_l Z4 noise
  * vectors z_{s,l} (Philox counter {site, s, l, job}) give samples c_{s,l} of the chosen
  * estimator. Outputs (host, caller-owned):

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <thread>
 #include <cstring>
 #include <vector>
@@ -411,6 +412,55 @@ int shifted_solve(fs_ctx* ctx, double m, const double* sigma, int nshift, const 
   out.noconv = &noconv;
   out.x_host = x;
   out.canon_out_base = nrhs;
+  if (int rc = fs::run_queue(&c, T, jobs, o.so, out)) return rc;
+  if (stats)
+    for (int i = 0; i < S; i++) fill_stats(st[i], &stats[i], o.so.verify != 0);
+  return noconv ? c.fail(FS_ERR_NOCONV, "some systems reached max_iter") : FS_OK;
+}
+
+int shifted_solve_dev(fs_ctx* ctx, double m, const double* sigma, int nshift, const double* b, int nrhs, double* x,
+                      const fs_solve_params* params, fs_sys_stats* stats) {
+  if (!ctx) return FS_ERR_ARG;
+  Ctx& c = ctx->c;
+  if (nshift < 0 || nrhs < 0) return c.fail(FS_ERR_ARG, "negative count");
+  if (nshift == 0 || nrhs == 0) return FS_OK;
+  if (!sigma || !b || !x) return c.fail(FS_ERR_ARG, "null pointer");
+  if (!c.have_gauge) return c.fail(FS_ERR_STATE, "no gauge field set");
+  if (!std::isfinite(m) || !finite_array(sigma, nshift)) return c.fail(FS_ERR_INPUT, "non-finite mass or shift");
+  for (int j = 0; j < nshift; j++)
+    if (std::fabs(4.0 + m + sigma[j]) < 1e-12) return c.fail(FS_ERR_ARG, "4 + m + sigma must be nonzero");
+  if (int rc = set_device(c)) return rc;
+  // both arrays must be device (or managed) memory of this context's GPU, 16-byte aligned
+  for (const void* q : {(const void*)b, (const void*)x}) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+      cudaGetLastError();
+      return c.fail(FS_ERR_ARG, "b and x must be device pointers");
+    }
+    if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != c.device)
+      return c.fail(FS_ERR_ARG, "b and x must be device memory of the context's GPU");
+    if (reinterpret_cast<uintptr_t>(q) % 16) return c.fail(FS_ERR_ARG, "b and x must be 16-byte aligned");
+  }
+  Opts o;
+  const int S = nshift * nrhs;
+  if ((long long)nshift * nrhs > 0x7FFFFFFF) return c.fail(FS_ERR_ARG, "too many systems");
+  if (int rc = resolve_params(c, params, S, m, o)) return rc;
+  std::vector<fs::QJob> jobs(S);
+  for (int i = 0; i < S; i++) {
+    const int j = i / nrhs, k = i % nrhs;
+    jobs[i].sys = {fs::SysSpec{sigma[j], 1, k, fs::NoiseSpec{}}};
+    jobs[i].stat_index = {i};
+    jobs[i].out_index = {i};
+  }
+  fs::TileBase* T = tile_for(c, jobs, o);
+  if (!T) return c.fail(FS_ERR_OOM, "device allocation of the solver tile failed");
+  int noconv = 0;
+  std::vector<fs::SysState> st(S);
+  fs::QOut out;
+  out.states = &st;
+  out.noconv = &noconv;
+  out.rhs_canon = b;
+  out.x_dev = x;
   if (int rc = fs::run_queue(&c, T, jobs, o.so, out)) return rc;
   if (stats)
     for (int i = 0; i < S; i++) fill_stats(st[i], &stats[i], o.so.verify != 0);

@@ -300,7 +300,8 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
     if ((e = upload_slots(c, T, adm))) return c->cuda_fail(e, "upload slot state");
     if (any_vec && (e = upload_vec(c, T))) return c->cuda_fail(e, "upload vector map");
     if ((e = mark())) return c->cuda_fail(e, "upload fence");
-    if (any_vec && (e = T->enqueue_rhs_from_canon(c->canon_d))) return c->cuda_fail(e, "pack right-hand sides");
+    if (any_vec && (e = T->enqueue_rhs_from_canon(out.rhs_canon ? out.rhs_canon : c->canon_d)))
+      return c->cuda_fail(e, "pack right-hand sides");
     if (any_noise && (e = T->enqueue_noise())) return c->cuda_fail(e, "noise");
     if ((e = T->enqueue_init())) return c->cuda_fail(e, "solver initialisation");
     return 0;
@@ -442,8 +443,25 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
       }
     }
 
-    // solution vectors requested by the caller
-    if (out.x_host) {
+    // solution vectors requested by the caller: unpacked straight into the caller's device array
+    if (out.x_dev) {
+      for (int j = 0; j < N; j++) T->vec_h[j] = -1;
+      bool any = false;
+      for (int j : harvest) {
+        if (slot[j].phase != 0 || std::find(chain_slots.begin(), chain_slots.end(), j) != chain_slots.end())
+          continue;
+        const QJob& q = jobs[slot[j].job];
+        if (q.out_index.empty() || q.out_index[slot[j].member] < 0) continue;
+        T->vec_h[j] = q.out_index[slot[j].member];
+        any = true;
+      }
+      if (any) {
+        if ((e = upload_vec(c, T))) return c->cuda_fail(e, "upload vector map");
+        if ((e = T->enqueue_solution_to_canon(out.x_dev))) return c->cuda_fail(e, "unpack solutions");
+        // the map upload must land before the host rewrites vec_h
+        if ((e = cudaStreamSynchronize(c->stream))) return c->cuda_fail(e, "unpack solutions");
+      }
+    } else if (out.x_host) {
       std::vector<std::pair<int, int>> copies;  // slot, output index
       for (int j = 0; j < N; j++) T->vec_h[j] = -1;
       int used = 0;

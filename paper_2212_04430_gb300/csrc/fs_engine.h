@@ -193,6 +193,8 @@ struct QOut {
   int canon_out_base = 0;                   // staging vectors [base, base + N) for outputs
   int canon_chain_base = 0;                 // staging vectors [base, base + N) for follow-up rhs
   int hpe_order = 0;                        // K of the hopping parameter expansion (SysSpec::hpe)
+  const double* rhs_canon = nullptr;        // caller's device right-hand sides [vec][V][24] (else staging)
+  double* x_dev = nullptr;                  // caller's device solutions [out_index][V][24]
 };
 
 // Field pair that holds (kappa H)^K x after the expansion's K hops from PAIR_X (alternating

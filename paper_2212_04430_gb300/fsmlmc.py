@@ -27,7 +27,7 @@ EXPORTS = ["fs_ctx_create", "fs_ctx_destroy", "fs_last_error", "fs_set_stream", 
            "wilson_dslash_noalloc", "fs_server_create", "fs_server_submit", "fs_server_poll",
            "fs_server_stats", "fs_server_destroy", "fs_interp_variances", "fs_select_shifts",
            "fs_sample_allocation", "fs_eval_grid", "fs_tuned_tile", "fs_probing_colors",
-           "variance_sample_probed"]
+           "variance_sample_probed", "shifted_solve_dev"]
 JOB_MAX_LEVELS = 16
 
 
@@ -102,6 +102,7 @@ def load_library(path=LIB_PATH):
         "fs_set_gauge": (I, [P, dp]),
         "wilson_dslash": (I, [P, D, D, dp, dp, I, I, I]),
         "shifted_solve": (I, [P, D, dp, I, dp, I, dp, ctypes.POINTER(SolveParams), ctypes.POINTER(SysStats)]),
+        "shifted_solve_dev": (I, [P, D, dp, I, P, I, P, ctypes.POINTER(SolveParams), ctypes.POINTER(SysStats)]),
         "mlmc_level_trace": (I, [P, ctypes.POINTER(MlmcParams), dp, dp, dp, ctypes.POINTER(SysStats)]),
         "fs_mlmc_num_solves": (I, [ctypes.POINTER(MlmcParams)]),
         "variance_sample": (I, [P, D, dp, I, dp, ip, I, I, U64, U32, ctypes.POINTER(SolveParams), dp, dp, dp,
@@ -249,6 +250,17 @@ class Context:
         rc = self._check(self.lib.shifted_solve(self.h, m, _dptr(sig), len(sig), _dptr(bb), nrhs, _dptr(x),
                                                 ctypes.byref(p), st), allow_noconv=True)
         return x.view(np.complex128)[..., 0], [_stats(s) for s in st], rc
+
+    def shifted_solve_dev(self, m, sigmas, b_ptr, nrhs, x_ptr, **kw):
+        """shifted_solve on device arrays: b_ptr / x_ptr are device addresses (e.g. a float64 torch
+        tensor's data_ptr()) of [nrhs][V][24] and [nshift][nrhs][V][24]; returns the stats."""
+        sig = np.ascontiguousarray(sigmas, dtype=np.float64)
+        prm = _params(**kw)
+        st = (SysStats * max(sig.size * nrhs, 1))()
+        self._check(self.lib.shifted_solve_dev(self.h, m, _dptr(sig), sig.size, ctypes.c_void_p(int(b_ptr)),
+                                               int(nrhs), ctypes.c_void_p(int(x_ptr)), ctypes.byref(prm), st),
+                    allow_noconv=True)
+        return [_stats(s) for s in st[:sig.size * nrhs]]
 
     def mlmc_level_trace(self, m, sigmas, gamma, p, n_samples, seed, job=0, estimator="diff", colors=None,
                          ncolors=None, dilute=False, hpe_order=0, **kw):

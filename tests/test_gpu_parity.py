@@ -396,3 +396,30 @@ def test_contraction_with_a_dense_gamma():
     for lev in range(2):
         assert sample_err(out["samples"][lev], ref[lev]) < 1e-9, lev
     ctx.close()
+
+
+def test_shifted_solve_on_device_arrays():
+    """shifted_solve_dev on torch device tensors gives the host call's solutions exactly (the same
+    arithmetic), and refuses host memory."""
+    torch = pytest.importorskip("torch")
+    dims = (4, 4, 4, 8)
+    v = int(np.prod(dims))
+    u = inputs.gauge_field(dims, "smooth", seed=31, eps=0.4)
+    rng = np.random.default_rng(5)
+    b = (rng.normal(size=(3, v, 4, 3)) + 1j * rng.normal(size=(3, v, 4, 3)))
+    sig = [0.02, 0.3]
+    ctx = make_ctx(dims, u)
+    kw = dict(prec="f16", tol=1e-9, rhs_tile=4, link_compress=12)
+    x_host, st_host, _ = ctx.shifted_solve(-0.3, sig, b, **kw)
+    bd = torch.from_numpy(np.ascontiguousarray(b).view(np.float64).reshape(3, v, 24)).to("cuda:0")
+    xd = torch.zeros((2, 3, v, 24), dtype=torch.float64, device="cuda:0")
+    torch.cuda.synchronize()
+    st = ctx.shifted_solve_dev(-0.3, sig, bd.data_ptr(), 3, xd.data_ptr(), **kw)
+    x = xd.cpu().numpy().view(np.complex128).reshape(2, 3, v, 4, 3)
+    assert np.array_equal(x, np.asarray(x_host).reshape(x.shape))
+    assert [s["iters"] for s in st] == [s["iters"] for s in st_host]
+    hb = np.zeros((3, v, 24))
+    with pytest.raises(pkg.FsError) as e:
+        ctx.shifted_solve_dev(-0.3, sig, hb.ctypes.data, 3, xd.data_ptr(), **kw)
+    assert e.value.code == pkg.fsmlmc.FS_ERR_ARG
+    ctx.close()
