@@ -556,12 +556,13 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    iters, updates, restarts = [], [], []
+    iters, updates, restarts, resid = [], [], [], []
     for k in range(args.steps):
         out = step(job0 + 1000 + k)
         iters.extend(s["iters"] for s in out["stats"])
         updates.extend(s["reliable_updates"] for s in out["stats"])
         restarts.extend(s["restarts"] for s in out["stats"])
+        resid.extend(s["true_resid"] for s in out["stats"])
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(ws)
@@ -689,6 +690,9 @@ def main():
                            "max_iters": int(max(iters)) if iters else None,
                            "mean_reliable_updates": float(np.mean(updates)) if updates else None,
                            "restarts": int(sum(restarts)),
+                           "max_true_resid": float(max(resid)) if resid else None,
+                           "true_resid_note": "the library's FP64 ||bhat - M x|| / ||z|| at the last reliable "
+                                              "update of each timed solve (stopping rule: <= tol)",
                            "solves_per_step": solves_per_step}}
         print(json.dumps(line), flush=True)
     ctx.close()

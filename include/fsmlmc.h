@@ -205,6 +205,17 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* params, double* trace, d
  * then by sample, then by piece. -1 if the count exceeds 2^31 - 1 or params is invalid. */
 int fs_mlmc_num_solves(const fs_mlmc_params* params);
 
+/* Exact low orders of the hopping parameter expansion (Sec. 3.1, the remark after
+ * Eq. (sampled_single)): out = {re, im} of T = sum_{k<K} Tr(Gamma Omega_p (kappa H)^k) / A,
+ * A = 4 + m + sigma, kappa = 1 / (2A), H the hopping term of D (D + sigma = A (1 - kappa H)).
+ * Computed with displacement-p distance-(K-1) probing colours (fs_probing_colors) and full
+ * spin-colour dilution: 12 c FP64 vectors (pieces of a Z4 vector from `seed`; the result does not
+ * depend on it), K - 1 kappa H applications each, one contraction per order. The value
+ * mlmc_level_trace adds to every last-level sample with hpe_order = K. params: rhs_tile (0 = 64
+ * pieces at a time); the other fields are unused. K in 1..8, 0 <= p < Lz, else FS_ERR_ARG. */
+int fs_hpe_exact_trace(fs_ctx* ctx, double m, double sigma, const double* gamma, int p, int K, uint64_t seed,
+                       const fs_solve_params* params, double* out);
+
 /* Greedy probing colours (Sec. 2.1): a distance-k colouring of the lattice graph of D (the
  * nearest-neighbour graph of the periodic 4D lattice, hop distance), or, for p > 0, the
  * displacement-p colouring of the symmetric part of Pi_p D^k, in which site x differs in colour

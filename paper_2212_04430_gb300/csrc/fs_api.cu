@@ -467,6 +467,27 @@ int shifted_solve_dev(fs_ctx* ctx, double m, const double* sigma, int nshift, co
   return noconv ? c.fail(FS_ERR_NOCONV, "some systems reached max_iter") : FS_OK;
 }
 
+int fs_hpe_exact_trace(fs_ctx* ctx, double m, double sigma, const double* gamma, int p, int K, uint64_t seed,
+                       const fs_solve_params* params, double* out) {
+  if (!ctx) return FS_ERR_ARG;
+  Ctx& c = ctx->c;
+  if (!gamma || !out) return c.fail(FS_ERR_ARG, "null pointer");
+  if (!c.have_gauge) return c.fail(FS_ERR_STATE, "no gauge field set");
+  if (K < 1 || K > 8) return c.fail(FS_ERR_ARG, "K must be in [1, 8]");
+  if (p < 0 || p >= c.g.L[2]) return c.fail(FS_ERR_ARG, "p must be in [0, Lz)");
+  if (!std::isfinite(m) || !std::isfinite(sigma) || !finite_array(gamma, 32))
+    return c.fail(FS_ERR_INPUT, "non-finite mass, shift or Gamma");
+  if (std::fabs(4.0 + m + sigma) < 1e-12) return c.fail(FS_ERR_ARG, "4 + m + sigma must be nonzero");
+  Opts o;
+  if (int rc = resolve_params(c, params, 12, m, o)) return rc;  // 12 < 16: no tile autotuning
+  if (!params || params->rhs_tile == 0) o.tile = fs::MAX_TILE;  // the probing pieces fill whole tiles
+  if (int rc = set_device(c)) return rc;
+  fs::TileBase* T = c.tile(o.so.prec, o.tile, o.so.nr);
+  if (!T) return c.fail(FS_ERR_OOM, "device allocation of the solver tile failed");
+  if (int rc = fs::ensure_wline(&c, 1 << p, p)) return rc;
+  return fs::hpe_exact(&c, T, o.so, sigma, K, p, gamma, seed, out);
+}
+
 // Pieces of one sample: probing colours times spin-colour components (Sec. 2.1, Sec. 3.1).
 int num_pieces(const fs_mlmc_params* p) {
   if (p->dilute != 0 && p->dilute != 1) return -1;

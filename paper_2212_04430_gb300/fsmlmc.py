@@ -27,7 +27,7 @@ EXPORTS = ["fs_ctx_create", "fs_ctx_destroy", "fs_last_error", "fs_set_stream", 
            "wilson_dslash_noalloc", "fs_server_create", "fs_server_submit", "fs_server_poll",
            "fs_server_stats", "fs_server_destroy", "fs_interp_variances", "fs_select_shifts",
            "fs_sample_allocation", "fs_eval_grid", "fs_tuned_tile", "fs_probing_colors",
-           "variance_sample_probed", "shifted_solve_dev"]
+           "variance_sample_probed", "shifted_solve_dev", "fs_hpe_exact_trace"]
 JOB_MAX_LEVELS = 16
 
 
@@ -103,6 +103,7 @@ def load_library(path=LIB_PATH):
         "wilson_dslash": (I, [P, D, D, dp, dp, I, I, I]),
         "shifted_solve": (I, [P, D, dp, I, dp, I, dp, ctypes.POINTER(SolveParams), ctypes.POINTER(SysStats)]),
         "shifted_solve_dev": (I, [P, D, dp, I, P, I, P, ctypes.POINTER(SolveParams), ctypes.POINTER(SysStats)]),
+        "fs_hpe_exact_trace": (I, [P, D, D, dp, I, I, U64, ctypes.POINTER(SolveParams), dp]),
         "mlmc_level_trace": (I, [P, ctypes.POINTER(MlmcParams), dp, dp, dp, ctypes.POINTER(SysStats)]),
         "fs_mlmc_num_solves": (I, [ctypes.POINTER(MlmcParams)]),
         "variance_sample": (I, [P, D, dp, I, dp, ip, I, I, U64, U32, ctypes.POINTER(SolveParams), dp, dp, dp,
@@ -250,6 +251,16 @@ class Context:
         rc = self._check(self.lib.shifted_solve(self.h, m, _dptr(sig), len(sig), _dptr(bb), nrhs, _dptr(x),
                                                 ctypes.byref(p), st), allow_noconv=True)
         return x.view(np.complex128)[..., 0], [_stats(s) for s in st], rc
+
+    def hpe_exact_trace(self, m, sigma, gamma, p, K, seed=0, **kw):
+        """Exact low orders sum_{k<K} Tr(Gamma Omega_p (kappa H)^k) / A of the hopping parameter
+        expansion (complex)."""
+        g = _gamma.to_abi(gamma)
+        out = np.zeros(2)
+        prm = _params(**kw)
+        self._check(self.lib.fs_hpe_exact_trace(self.h, m, sigma, _dptr(g), int(p), int(K), int(seed),
+                                                ctypes.byref(prm), _dptr(out)))
+        return complex(out[0], out[1])
 
     def shifted_solve_dev(self, m, sigmas, b_ptr, nrhs, x_ptr, **kw):
         """shifted_solve on device arrays: b_ptr / x_ptr are device addresses (e.g. a float64 torch

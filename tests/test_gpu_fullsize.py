@@ -85,3 +85,29 @@ def test_config5_24x64_variance_samples():
         got = out["a"][0, p, 4]
         assert abs(got - ref) <= 1e-9 * max(abs(ref), 1.0), (p, got, ref)
     ctx.close()
+
+
+def test_expansion_exact_part_closed_forms_16x32():
+    """The hopping parameter expansion's exact low orders at the benchmark size, against closed
+    forms that hold for any gauge field (paths of length k < K from x + p z back to x): p = 1,
+    K = 2 gives 3V kappa tr(G (1 + g_z)) / A; p = 3, K = 4 (only the straight path,
+    (1 + g_z)^3 = 4 (1 + g_z)) gives 12V kappa^3 tr(G (1 + g_z)) / A; p = 0, K = 4 gives
+    3V tr(G) / A; p = 4, K = 4 gives 0 (no path is short enough)."""
+    dims = (16, 16, 16, 32)
+    v = int(np.prod(dims))
+    u = inputs.gauge_field(dims, "smooth", seed=1003, eps=0.4)
+    m, s = -0.35, 0.6
+    A = 4.0 + m + s
+    kappa = 1.0 / (2.0 * A)
+    ctx = pkg.Context(dims, bc_t=-1, device=0)
+    ctx.fs_set_gauge(u)
+    for name, go in (("g3", odirac.gamma_product(["g3"])), ("g5g3", odirac.gamma_product(["g5", "g3"])),
+                     ("1", odirac.IDENT4)):
+        g = go if name == "1" else pkg.gamma_matrix(name)
+        t1 = np.trace(go @ (odirac.IDENT4 + odirac.GAMMA[2]))
+        cases = [(1, 2, 3 * v * kappa * t1 / A), (3, 4, 12 * v * kappa ** 3 * t1 / A),
+                 (0, 4, 3 * v * np.trace(go) / A), (4, 4, 0.0)]
+        for p, K, ref in cases:
+            got = ctx.hpe_exact_trace(m, s, g, p, K, seed=7)
+            assert abs(got - ref) <= 1e-11 * max(1.0, abs(3 * v / A)), (name, p, K, got, ref)
+    ctx.close()
