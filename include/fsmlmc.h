@@ -197,6 +197,14 @@ int shifted_solve_dev(fs_ctx* ctx, double m, const double* sigma, int nshift, co
 int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* params, double* trace, double* var,
                      double* samples, fs_sys_stats* stats);
 
+/* mlmc_level_trace for several displacements at once: the traces for p[0..np) (distinct, each
+ * 0..30, np <= 16; params->p is ignored) from the same solves, as the paper uses one set of
+ * inversions for all displacements (Sec. 4); the contraction forms them in one pass. Outputs in
+ * the order of p: trace [np][nlev][2], var [np][nlev], samples (optional) [np][sum N_l][2];
+ * stats as mlmc_level_trace. With hpe_order every p needs p < Lz and gets its own exact part. */
+int mlmc_level_traces(fs_ctx* ctx, const fs_mlmc_params* params, const int* p, int np, double* trace,
+                      double* var, double* samples, fs_sys_stats* stats);
+
 /* Number of shifted solves mlmc_level_trace performs: per level l < L two solves per
  * sample and piece (DIFF: z at s_l then z at s_{l+1}; SPLIT_EVEN: gamma_5 z at s_l then z at
  * s_{l+1}; PRODUCT: z at s_{l+1} then its solution at s_l), one per sample and piece at level

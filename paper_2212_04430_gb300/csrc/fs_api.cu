@@ -508,14 +508,33 @@ int fs_mlmc_num_solves(const fs_mlmc_params* p) {
   return n > 0x7FFFFFFF ? -1 : (int)n;
 }
 
-int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double* var, double* samples,
-                     fs_sys_stats* stats) {
-  if (!ctx) return FS_ERR_ARG;
-  Ctx& c = ctx->c;
-  if (!P || !trace || !var) return c.fail(FS_ERR_ARG, "null pointer");
+namespace {
+
+// Level traces for the displacements p_in[0..np) from the same solves (the contraction forms all of
+// them in one pass); outputs per displacement in the caller's order: trace [np][nlev][2],
+// var [np][nlev], samples [np][sum N_l][2].
+int mlmc_impl(Ctx& c, const fs_mlmc_params* P, const int* p_in, int np, double* trace, double* var, double* samples,
+              fs_sys_stats* stats) {
+  if (!P || !trace || !var || !p_in) return c.fail(FS_ERR_ARG, "null pointer");
   if (P->nlev < 1 || !P->sigma || !P->n_samples || !P->gamma) return c.fail(FS_ERR_ARG, "bad level parameters");
   if (!c.have_gauge) return c.fail(FS_ERR_STATE, "no gauge field set");
-  if (P->p < 0 || P->p > 30) return c.fail(FS_ERR_ARG, "p must be in [0, 30]");
+  if (np < 1 || np > fs::CONTRACT_MAXP) return c.fail(FS_ERR_ARG, "np must be in [1, 16]");
+  // displacements are contracted in increasing order; order[qs] is the caller's index of the
+  // qs-th smallest
+  std::vector<int> order(np);
+  for (int k = 0; k < np; k++) {
+    if (p_in[k] < 0 || p_in[k] > 30) return c.fail(FS_ERR_ARG, "p must be in [0, 30]");
+    order[k] = k;
+  }
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return p_in[a] < p_in[b]; });
+  std::vector<int> plist(np);
+  int pmask = 0, pmax = 0;
+  for (int k = 0; k < np; k++) {
+    plist[k] = p_in[order[k]];
+    if (pmask & (1 << plist[k])) return c.fail(FS_ERR_ARG, "displacements must be distinct");
+    pmask |= 1 << plist[k];
+    pmax = std::max(pmax, plist[k]);
+  }
   if (P->estimator < FS_EST_DIFF || P->estimator > FS_EST_PRODUCT) return c.fail(FS_ERR_ARG, "bad estimator");
   if (!std::isfinite(P->m) || !finite_array(P->sigma, P->nlev) || !finite_array(P->gamma, 32))
     return c.fail(FS_ERR_INPUT, "non-finite mass, shift or Gamma");
@@ -535,7 +554,7 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double
   // the expansion converges for A = 4 + m + sigma > 4 only (Sec. 3.1 uses it where m + s > 0)
   const bool hpe = P->hpe_order > 0 && P->m + P->sigma[L] > 0.0;
   // the exact low orders take Omega_0 = 1; a displacement of a whole period is a Polyakov loop
-  if (hpe && P->p >= c.g.L[2]) return c.fail(FS_ERR_ARG, "hpe_order needs p < Lz");
+  if (hpe && pmax >= c.g.L[2]) return c.fail(FS_ERR_ARG, "hpe_order needs p < Lz");
   if (P->colors) {
     // every site has a colour in range and every colour is used (no piece has an empty support)
     std::vector<char> used(P->ncolors, 0);
@@ -550,8 +569,7 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double
   Opts o;
   if (int rc = resolve_params(c, &P->solve, nsolve, P->m, o)) return rc;
   if (int rc = set_device(c)) return rc;
-  const std::vector<int> plist = {P->p};
-  std::vector<double> csum(total * 2, 0.0);  // per-sample values, level-major
+  std::vector<double> csum((size_t)np * total * 2, 0.0);  // per-sample values [np][level-major][2]
   std::vector<long long> off(L + 2, 0);
   for (int l = 0; l <= L; l++) off[l + 1] = off[l] + P->n_samples[l];
   std::vector<fs::SysState> st(nsolve);
@@ -628,18 +646,20 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double
   }
   // exact low orders of the expansion (probing colours of their own, so computed before the
   // caller's colours are uploaded), on the owner's tile
-  double t_exact[2] = {0.0, 0.0};
+  std::vector<double> t_exact((size_t)np * 2, 0.0);  // per sorted displacement
   if (hpe) {
     fs::TileBase* TE = T ? T : tile_for(c, jobs, o);
     if (!TE) return c.fail(FS_ERR_OOM, "device allocation of the solver tile failed");
-    if (int rc = fs::ensure_wline(&c, 1 << P->p, P->p)) return rc;
-    if (int rc = fs::hpe_exact(&c, TE, o.so, P->sigma[L], P->hpe_order, P->p, P->gamma, P->seed, t_exact))
-      return rc;
+    if (int rc = fs::ensure_wline(&c, pmask, pmax)) return rc;
+    for (int qs = 0; qs < np; qs++)
+      if (int rc = fs::hpe_exact(&c, TE, o.so, P->sigma[L], P->hpe_order, plist[qs], P->gamma, P->seed,
+                                 &t_exact[(size_t)qs * 2]))
+        return rc;
   }
   if (P->colors)
     if (int rc = fs::upload_colors(&c, P->colors)) return rc;
   std::vector<double> res;
-  res.assign((size_t)nsolve * 2, 0.0);
+  res.assign((size_t)nsolve * np * 2, 0.0);
   fs::QOut out;
   out.gamma = P->gamma;
   out.plist = &plist;
@@ -650,52 +670,74 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double
   out.noconv = &noconv;
   out.canon_chain_base = 0;
   if (nl > 1) {
-    if (int rc = fs::ensure_wline(&c, 1 << P->p, P->p)) return rc;
+    if (int rc = fs::ensure_wline(&c, pmask, pmax)) return rc;
     if (int rc = run_lanes(c, jobs, o, out, nl, P->estimator == FS_EST_PRODUCT)) return rc;
   } else if (int rc = fs::run_queue(&c, T, jobs, o.so, out)) {
     return rc;
   }
-  // a sample is the sum of its pieces' estimators, in piece order
-  for (int l = 0; l <= L; l++) {
-    for (int s = 0; s < P->n_samples[l]; s++) {
-      double re = 0.0, im = 0.0;
-      for (int piece = 0; piece < npieces; piece++) {
-        const int si = solve_off[l] + (s * npieces + piece) * (l < L ? 2 : 1);
-        if (l == L) {
-          re += res[(size_t)si * 2]; im += res[(size_t)si * 2 + 1];
-        } else if (P->estimator == FS_EST_DIFF) {
-          re += res[(size_t)si * 2] - res[(size_t)(si + 1) * 2];
-          im += res[(size_t)si * 2 + 1] - res[(size_t)(si + 1) * 2 + 1];
-        } else {
-          const double ds = P->sigma[l + 1] - P->sigma[l];
-          re += ds * res[(size_t)si * 2]; im += ds * res[(size_t)si * 2 + 1];
+  // a sample is the sum of its pieces' estimators, in piece order; res rows are [solve][np][2]
+  auto r = [&](int si, int qs, int ri) { return res[((size_t)si * np + qs) * 2 + ri]; };
+  for (int qs = 0; qs < np; qs++) {
+    const size_t qo = (size_t)order[qs] * total;  // the caller's displacement index
+    for (int l = 0; l <= L; l++) {
+      for (int s = 0; s < P->n_samples[l]; s++) {
+        double re = 0.0, im = 0.0;
+        for (int piece = 0; piece < npieces; piece++) {
+          const int si = solve_off[l] + (s * npieces + piece) * (l < L ? 2 : 1);
+          if (l == L) {
+            re += r(si, qs, 0); im += r(si, qs, 1);
+          } else if (P->estimator == FS_EST_DIFF) {
+            re += r(si, qs, 0) - r(si + 1, qs, 0);
+            im += r(si, qs, 1) - r(si + 1, qs, 1);
+          } else {
+            const double ds = P->sigma[l + 1] - P->sigma[l];
+            re += ds * r(si, qs, 0); im += ds * r(si, qs, 1);
+          }
         }
+        if (l == L && hpe) {
+          re += t_exact[(size_t)qs * 2];
+          im += t_exact[(size_t)qs * 2 + 1];
+        }
+        csum[(qo + off[l] + s) * 2] = re;
+        csum[(qo + off[l] + s) * 2 + 1] = im;
       }
-      if (l == L && hpe) {
-        re += t_exact[0];
-        im += t_exact[1];
-      }
-      csum[(off[l] + s) * 2] = re;
-      csum[(off[l] + s) * 2 + 1] = im;
     }
   }
   // per-level mean and practical variance, Eq. (practical_variance)
-  for (int l = 0; l <= L; l++) {
-    const int n = P->n_samples[l];
-    double sr = 0, si = 0, s2 = 0;
-    for (int s = 0; s < n; s++) {
-      const double re = csum[(off[l] + s) * 2], im = csum[(off[l] + s) * 2 + 1];
-      sr += re; si += im; s2 += re * re + im * im;
+  for (int q = 0; q < np; q++) {
+    const size_t qo = (size_t)q * total;
+    for (int l = 0; l <= L; l++) {
+      const int n = P->n_samples[l];
+      double sr = 0, si = 0, s2 = 0;
+      for (int s = 0; s < n; s++) {
+        const double re = csum[(qo + off[l] + s) * 2], im = csum[(qo + off[l] + s) * 2 + 1];
+        sr += re; si += im; s2 += re * re + im * im;
+      }
+      const double tr = sr / n, ti = si / n;
+      trace[((size_t)q * P->nlev + l) * 2] = tr;
+      trace[((size_t)q * P->nlev + l) * 2 + 1] = ti;
+      var[(size_t)q * P->nlev + l] = s2 / n - (tr * tr + ti * ti);
     }
-    const double tr = sr / n, ti = si / n;
-    trace[2 * l] = tr;
-    trace[2 * l + 1] = ti;
-    var[l] = s2 / n - (tr * tr + ti * ti);
   }
   if (samples) memcpy(samples, csum.data(), csum.size() * sizeof(double));
   if (stats)
     for (int k = 0; k < nsolve; k++) fill_stats(st[k], &stats[k], o.so.verify != 0);
   return noconv ? c.fail(FS_ERR_NOCONV, "some systems reached max_iter") : FS_OK;
+}
+
+}  // namespace
+
+int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* P, double* trace, double* var, double* samples,
+                     fs_sys_stats* stats) {
+  if (!ctx) return FS_ERR_ARG;
+  if (!P) return ctx->c.fail(FS_ERR_ARG, "null pointer");
+  return mlmc_impl(ctx->c, P, &P->p, 1, trace, var, samples, stats);
+}
+
+int mlmc_level_traces(fs_ctx* ctx, const fs_mlmc_params* P, const int* p, int np, double* trace, double* var,
+                      double* samples, fs_sys_stats* stats) {
+  if (!ctx) return FS_ERR_ARG;
+  return mlmc_impl(ctx->c, P, p, np, trace, var, samples, stats);
 }
 
 namespace {

@@ -27,7 +27,8 @@ EXPORTS = ["fs_ctx_create", "fs_ctx_destroy", "fs_last_error", "fs_set_stream", 
            "wilson_dslash_noalloc", "fs_server_create", "fs_server_submit", "fs_server_poll",
            "fs_server_stats", "fs_server_destroy", "fs_interp_variances", "fs_select_shifts",
            "fs_sample_allocation", "fs_eval_grid", "fs_tuned_tile", "fs_probing_colors",
-           "variance_sample_probed", "shifted_solve_dev", "fs_hpe_exact_trace"]
+           "variance_sample_probed", "shifted_solve_dev", "fs_hpe_exact_trace",
+           "mlmc_level_traces"]
 JOB_MAX_LEVELS = 16
 
 
@@ -105,6 +106,7 @@ def load_library(path=LIB_PATH):
         "shifted_solve_dev": (I, [P, D, dp, I, P, I, P, ctypes.POINTER(SolveParams), ctypes.POINTER(SysStats)]),
         "fs_hpe_exact_trace": (I, [P, D, D, dp, I, I, U64, ctypes.POINTER(SolveParams), dp]),
         "mlmc_level_trace": (I, [P, ctypes.POINTER(MlmcParams), dp, dp, dp, ctypes.POINTER(SysStats)]),
+        "mlmc_level_traces": (I, [P, ctypes.POINTER(MlmcParams), ip, I, dp, dp, dp, ctypes.POINTER(SysStats)]),
         "fs_mlmc_num_solves": (I, [ctypes.POINTER(MlmcParams)]),
         "variance_sample": (I, [P, D, dp, I, dp, ip, I, I, U64, U32, ctypes.POINTER(SolveParams), dp, dp, dp,
                                 dp, dp]),
@@ -277,7 +279,11 @@ class Context:
                          ncolors=None, dilute=False, hpe_order=0, **kw):
         """Level traces; colors ([V] probing colours, canonical order) and dilute (full spin-colour
         dilution) make every sample the sum of the estimator over its pieces; hpe_order = K uses
-        the hopping parameter expansion on the last level when m + sigma_L > 0."""
+        the hopping parameter expansion on the last level when m + sigma_L > 0. A sequence p gives
+        the traces for every displacement from the same solves (mlmc_level_traces): a list of
+        result dicts in the order of p."""
+        multi = not np.isscalar(p)
+        plist = np.ascontiguousarray(np.atleast_1d(p), dtype=np.int32)
         sig = np.ascontiguousarray(sigmas, dtype=np.float64)
         ns = np.ascontiguousarray(n_samples, dtype=np.int32)
         if ns.size == 1 and sig.size > 1:
@@ -286,7 +292,7 @@ class Context:
         P = MlmcParams()
         P.m = m
         P.nlev = sig.size
-        P.p = int(p)
+        P.p = int(plist[0])
         P.sigma = _dptr(sig)
         P.n_samples = ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
         P.gamma = _dptr(g)
@@ -299,18 +305,29 @@ class Context:
         nsolve = self.lib.fs_mlmc_num_solves(ctypes.byref(P))
         if nsolve < 0:
             raise FsError(1, "fs_mlmc_num_solves: bad sample counts, ncolors or dilute")
-        trace = np.zeros((sig.size, 2))
-        var = np.zeros(sig.size)
-        samples = np.zeros((int(ns.sum()), 2))
+        npl = plist.size
+        trace = np.zeros((npl, sig.size, 2))
+        var = np.zeros((npl, sig.size))
+        samples = np.zeros((npl, int(ns.sum()), 2))
         st = (SysStats * max(nsolve, 1))()
-        rc = self._check(self.lib.mlmc_level_trace(self.h, ctypes.byref(P), _dptr(trace), _dptr(var),
-                                                   _dptr(samples), st), allow_noconv=True)
-        tr = trace[:, 0] + 1j * trace[:, 1]
-        smp = samples[:, 0] + 1j * samples[:, 1]
+        if multi:
+            rc = self._check(self.lib.mlmc_level_traces(self.h, ctypes.byref(P),
+                                                        plist.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), npl,
+                                                        _dptr(trace), _dptr(var), _dptr(samples), st),
+                             allow_noconv=True)
+        else:
+            rc = self._check(self.lib.mlmc_level_trace(self.h, ctypes.byref(P), _dptr(trace), _dptr(var),
+                                                       _dptr(samples), st), allow_noconv=True)
+        stats = [_stats(s) for s in st[:nsolve]]
         offs = np.concatenate([[0], np.cumsum(ns)])
-        return {"trace": tr, "var": var, "samples": [smp[offs[l]:offs[l + 1]] for l in range(sig.size)],
-                "total": complex(tr.sum()), "v_fs": float((var / ns).sum()),
-                "stats": [_stats(s) for s in st[:nsolve]], "rc": rc}
+        res = []
+        for q in range(npl):
+            tr = trace[q, :, 0] + 1j * trace[q, :, 1]
+            smp = samples[q, :, 0] + 1j * samples[q, :, 1]
+            res.append({"p": int(plist[q]), "trace": tr, "var": var[q],
+                        "samples": [smp[offs[l]:offs[l + 1]] for l in range(sig.size)],
+                        "total": complex(tr.sum()), "v_fs": float((var[q] / ns).sum()), "stats": stats, "rc": rc})
+        return res if multi else res[0]
 
     def variance_sample(self, m, s_hat, gamma, p_list, n_s, seed, job=0, colors=None, ncolors=None, dilute=False,
                         hpe_order=0, **kw):

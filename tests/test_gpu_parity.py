@@ -423,3 +423,27 @@ def test_shifted_solve_on_device_arrays():
         ctx.shifted_solve_dev(-0.3, sig, hb.ctypes.data, 3, xd.data_ptr(), **kw)
     assert e.value.code == pkg.fsmlmc.FS_ERR_ARG
     ctx.close()
+
+
+@pytest.mark.parametrize("hpe_order", [0, 4])
+def test_several_displacements_from_one_set_of_solves(hpe_order):
+    """mlmc_level_traces: the traces for p = 3, 0, 1 from the same solves equal three
+    single-displacement calls exactly (each displacement is its own sum in the one contraction
+    pass), in the caller's order; with the expansion each p has its own exact part."""
+    dims = (4, 4, 8, 4)
+    u = inputs.gauge_field(dims, "smooth", seed=33, eps=0.4)
+    sig = [0.02, 0.2, 0.7]
+    n = [3, 2, 4]
+    g = pkg.gamma_matrix("g3")
+    ctx = make_ctx(dims, u)
+    kw = dict(seed=12, job=1, estimator="split_even", prec="f32", tol=1e-9, rhs_tile=8, hpe_order=hpe_order)
+    many = ctx.mlmc_level_trace(-0.2, sig, g, [3, 0, 1], n, **kw)
+    assert [r["p"] for r in many] == [3, 0, 1]
+    for r in many:
+        one = ctx.mlmc_level_trace(-0.2, sig, g, r["p"], n, **kw)
+        for lev in range(3):
+            assert np.array_equal(r["samples"][lev], one["samples"][lev]), (r["p"], lev)
+        assert np.array_equal(r["var"], one["var"])
+    with pytest.raises(pkg.FsError):
+        ctx.mlmc_level_trace(-0.2, sig, g, [1, 1], n, **kw)
+    ctx.close()
