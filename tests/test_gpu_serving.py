@@ -85,3 +85,34 @@ def test_budget_admission_and_poll_timeout():
     with pytest.raises(pkg.FsError):
         srv.poll(123456789, timeout_ms=0)  # unknown ticket
     srv.close()
+
+
+def test_probed_and_expanded_jobs_in_a_concurrent_mix():
+    """Jobs with probing colours, spin-colour dilution and the hopping parameter expansion run
+    concurrently with plain ones (every job copies its own colour table; every worker context
+    uploads its own): each result equals the job run alone."""
+    from oracle import probing as opr  # the colours are inputs here; the library does not use the oracle
+    specs = []
+    for k, dims in enumerate([(4, 4, 4, 4), (4, 4, 8, 4), (4, 4, 4, 8), (6, 4, 4, 4)]):
+        col, nc = opr.greedy_coloring(dims, 1 + k % 2, k % 3)
+        specs.append(dict(dims=dims, u=inputs.gauge_field(dims, "smooth", seed=7000 + k, eps=0.4),
+                          sig=[0.05, 0.3 + 0.1 * k], n=[2, 3], p=k % 3, seed=8000 + k,
+                          extra=[dict(colors=col, ncolors=nc, dilute=True), dict(hpe_order=4),
+                                 dict(colors=col, ncolors=nc, hpe_order=2), {}][k]))
+    g = pkg.gamma_matrix("g3")
+    kw = dict(prec="f16", tol=1e-8, rhs_tile=16)
+    alone = []
+    for s in specs:
+        ctx = pkg.Context(s["dims"])
+        ctx.fs_set_gauge(s["u"])
+        alone.append(ctx.mlmc_level_trace(-0.1, s["sig"], g, s["p"], s["n"], seed=s["seed"], lanes=1, **kw,
+                                          **s["extra"]))
+        ctx.close()
+    srv = pkg.Server(device=0, hbm_budget_bytes=16 << 30, max_active=4)
+    tickets = [srv.submit(s["dims"], s["u"], -0.1, s["sig"], g, s["p"], s["n"], s["seed"], **kw, **s["extra"])
+               for s in specs]
+    results = [srv.poll(t) for t in tickets]
+    srv.close()
+    for a, r in zip(alone, results):
+        assert r["status"] == 0
+        assert np.array_equal(r["trace"], a["trace"]) and np.array_equal(r["var"], a["var"])
