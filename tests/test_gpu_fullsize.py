@@ -111,3 +111,31 @@ def test_expansion_exact_part_closed_forms_16x32():
             got = ctx.hpe_exact_trace(m, s, g, p, K, seed=7)
             assert abs(got - ref) <= 1e-11 * max(1.0, abs(3 * v / A)), (name, p, K, got, ref)
     ctx.close()
+
+
+def test_expansion_remainder_16x32():
+    """The last level with the hopping parameter expansion at the benchmark size (sigma_L = 0.6,
+    p = 4, K = 4: the exact part is 0, no path of length < 4 reaches back): each GPU sample equals
+    z^dag gamma_3 Omega_4 (kappa H)^4 x with the oracle's H applied to the GPU solution x (the same
+    system solved through shifted_solve, bit-identical)."""
+    from oracle import hpe as ohpe
+    dims = (16, 16, 16, 32)
+    v = int(np.prod(dims))
+    u = inputs.gauge_field(dims, "smooth", seed=1003, eps=0.4)
+    m, s = -0.35, 0.6
+    kw = dict(prec="f16", tol=1e-8, rhs_tile=2, link_compress=12)
+    ctx = pkg.Context(dims)
+    ctx.fs_set_gauge(u)
+    out = ctx.mlmc_level_trace(m, [s], pkg.gamma_matrix("g3"), 4, [2], seed=2003, job=9, hpe_order=4, **kw)
+    assert out["rc"] == 0
+    kappa = 1.0 / (2.0 * (4.0 + m + s))
+    for smp in range(2):
+        z = ophilox.z4_noise(v, 2003, 9, 0, smp)
+        x, st, rc = ctx.shifted_solve(m, [s], z, **kw)
+        y = x[0, 0]
+        for _ in range(4):
+            y = kappa * ohpe.apply_H(u, y, dims)
+        ref = oest.contract(u, z, y, odirac.GAMMA[2], 4, dims)
+        got = out["samples"][0][smp]
+        assert abs(got - ref) <= 1e-9 * max(abs(ref), 1.0), (smp, got, ref)
+    ctx.close()
