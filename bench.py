@@ -480,6 +480,41 @@ def run_hpe(pkg, ctx, w, kw, K=4, n=64, seed=9200):
             "note": "seconds_hpe includes the exact low orders (12 c probing vectors, K-1 FP64 kappa H each)"}
 
 
+def run_variance_24x64(pkg, inputs, device, n_s=6, seed=2005):
+    """The 24^3x64 variance-sampling job (5 sampling shifts, p = 0..8, FP16 storage, 12-real links,
+    60-system tiles = 6 noise vectors) on n_s Z4 vectors: solves/s through variance_sample, timed
+    with CUDA events; the gauge upload is outside the timed region."""
+    import torch
+    dims = (24, 24, 24, 64)
+    u = inputs.gauge_field(dims, "smooth", seed=1005, eps=0.5)
+    ctx = pkg.Context(dims, bc_t=-1, device=device)
+    stream = torch.cuda.current_stream()
+    try:
+        ctx.set_stream(stream.cuda_stream)
+        ctx.fs_set_gauge(u)
+        s_hat = [0.0, 0.05, 0.25, 0.5, 1.0]
+        kw = dict(prec="f16", tol=1e-8, rhs_tile=60, link_compress=12)
+        g = pkg.gamma_matrix("g3")
+        ctx.variance_sample(-0.38, s_hat, g, list(range(9)), 1, seed=seed, job=0, **kw)  # warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = ctx.variance_sample(-0.38, s_hat, g, list(range(9)), n_s, seed=seed, job=1, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if out["rc"] != 0:
+            raise RuntimeError("24^3x64 solves did not converge: %s" % ctx.last_error())
+        sec = e0.elapsed_time(e1) / 1e3
+        solves = 2 * len(s_hat) * n_s
+        return {"workload": "24^3x64 variance sampling, eps=0.5, m=-0.38, s_hat={0,0.05,0.25,0.5,1.0}, gamma3, "
+                            "p=0..8, FP16 storage, 12-real links, 60-system tiles",
+                "value": solves / sec, "unit": "solves/s", "solves": solves, "seconds": sec,
+                "mean_iters_per_shift": [float(x) for x in out["iters"]],
+                "device_bytes": int(ctx.device_bytes())}
+    finally:
+        ctx.close()
+
+
 # --------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -500,6 +535,7 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=8.0, help="seconds of oracle work per reference step")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--serve-jobs", type=int, default=12, help="jobs in the serving run (0: skip)")
+    ap.add_argument("--no-large", action="store_true", help="skip the 24^3x64 variance-sampling measurement")
     ap.add_argument("--no-probing", action="store_true",
                     help="skip the probed and spin-colour diluted level traces (p4k4 colours)")
     ap.add_argument("--no-pipeline", action="store_true",
@@ -654,6 +690,10 @@ def main():
         # the paper's variant: V_L sampled with the hopping parameter expansion (order 4) where m + s > 0
         pipeline["with_hpe"] = run_pipeline(pkg, ctx, w, kw, hpe_order=4)
 
+    large = None
+    if not args.no_large and rank == 0:
+        large = run_variance_24x64(pkg, inputs, local)
+
     probing = None
     if not args.no_probing and rank == 0:
         probing = run_probing(pkg, ctx, w, kw)
@@ -685,7 +725,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_of(args, w), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "serving": serving, "pipeline": pipeline,
-                "fp64_single_rhs": fp64, "probing": probing,
+                "fp64_single_rhs": fp64, "probing": probing, "variance_sampling_24x64": large,
                 "solver": {"mean_iters": float(np.mean(iters)) if iters else None,
                            "max_iters": int(max(iters)) if iters else None,
                            "mean_reliable_updates": float(np.mean(updates)) if updates else None,
