@@ -790,7 +790,9 @@ int variance_sample_impl(Ctx& c, double m, const double* s_hat, int ms, const do
   if (int rc = set_device(c)) return rc;
   if (colors)
     if (int rc = fs::upload_colors(&c, colors)) return rc;
-  o.tile = std::max(gsize, (o.tile / gsize) * gsize);
+  // keep the requested tile even where whole groups leave a few slots idle: a multiple of 32
+  // systems runs the persistent FP16 hop, which outweighs the idle slots
+  o.tile = std::max(gsize, o.tile);
   const int per = ms + ms * (ms + 1) / 2;  // contraction rows per piece
   const size_t ngroups = (size_t)Ns * npieces;
   std::vector<fs::QJob> groups(ngroups);

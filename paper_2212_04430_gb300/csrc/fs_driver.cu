@@ -260,6 +260,27 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
   const int np = out.plist ? (int)out.plist->size() : 0;
   const size_t vlen = (size_t)c->g.V * 24;
 
+  // Staging (groups of several systems contracted together): a finished system leaves the tile at
+  // once, its FP64 solution (and expanded vector) copied to a staging column reserved for it at
+  // admission, and the group is contracted from staging when its last member arrives. Without it
+  // a group holds all its slots until its slowest member converges (a variance-sampling group
+  // spans five shifts). Not for follow-up solves or caller-requested solution vectors.
+  bool staged = out.result && np > 0 && !out.x_host && !out.x_dev;
+  int gmax = 1;
+  for (const QJob& q : jobs) {
+    gmax = std::max(gmax, (int)q.sys.size());
+    for (double ch : q.chain)
+      if (!std::isnan(ch)) staged = false;
+  }
+  if (gmax < 2) staged = false;
+  const int S = 2 * N;  // reserved columns bound the groups in flight to twice the tile
+  if (staged && T->stage_alloc(S, out.hpe_order > 0) != 0) staged = false;  // no room: groups keep their slots
+  std::vector<int> stage_free;
+  if (staged)
+    for (int k = S - 1; k >= 0; k--) stage_free.push_back(k);
+  std::vector<std::vector<int>> stage_col(staged ? jobs.size() : 0);
+  const size_t colsz = (size_t)24 * c->g.Vh;  // doubles of one staged parity column
+
   struct Slot {
     int job = -1, member = -1, phase = 0;
     bool done = false;
@@ -307,15 +328,25 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
     return 0;
   };
 
+  // groups completed and systems finished since the last harvest: kept across a pass that runs
+  // the CGNR fallback first, so that no completion is lost
+  std::vector<int> done_jobs;
+  std::vector<int> newly_done;
   while (finished < jobs.size()) {
     if ((e = wait_fence())) return c->cuda_fail(e, "upload fence");
     // ---- admit whole groups into free slots
     std::vector<int> adm;
     bool any_vec = false, any_noise = false;
     for (int j = 0; j < N; j++) T->vec_h[j] = -1;
-    while (next < jobs.size() && free_slots.size() >= jobs[next].sys.size()) {
+    while (next < jobs.size() && free_slots.size() >= jobs[next].sys.size() &&
+           (!staged || stage_free.size() >= jobs[next].sys.size())) {
       const QJob& q = jobs[next];
       remaining[next] = (int)q.sys.size();
+      if (staged)
+        for (size_t k = 0; k < q.sys.size(); k++) {
+          stage_col[next].push_back(stage_free.back());
+          stage_free.pop_back();
+        }
       for (size_t k = 0; k < q.sys.size(); k++) {
         const int j = free_slots.back();
         free_slots.pop_back();
@@ -347,7 +378,6 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
 
     // ---- find finished systems
     std::vector<int> chain_slots;
-    std::vector<int> done_jobs;
     std::vector<int> cg_slots;
     for (int j = 0; j < N; j++) {
       Slot& sl = slot[j];
@@ -366,6 +396,7 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
         continue;
       }
       sl.done = true;
+      newly_done.push_back(j);
       if (--remaining[sl.job] == 0) done_jobs.push_back(sl.job);
     }
     if (!cg_slots.empty()) {
@@ -375,14 +406,18 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
       for (int j : cg_slots) slot[j].cg_tried = true;
       continue;
     }
-    if (chain_slots.empty() && done_jobs.empty()) continue;
+    if (chain_slots.empty() && done_jobs.empty() && !(staged && !newly_done.empty())) continue;
 
     // ---- harvest: reconstruct the odd sites (and verify) of every slot leaving its phase
+    // (staged: every finished system; else the systems of completed groups)
     std::vector<int> harvest = chain_slots;
-    for (int j = 0; j < N; j++)
-      if (slot[j].job >= 0 && slot[j].done &&
-          std::find(done_jobs.begin(), done_jobs.end(), slot[j].job) != done_jobs.end())
-        harvest.push_back(j);
+    if (staged)
+      harvest.insert(harvest.end(), newly_done.begin(), newly_done.end());
+    else
+      for (int j = 0; j < N; j++)
+        if (slot[j].job >= 0 && slot[j].done &&
+            std::find(done_jobs.begin(), done_jobs.end(), slot[j].job) != done_jobs.end())
+          harvest.push_back(j);
     for (int j : harvest) T->st_h[j].flags |= FLAG_HARVEST;
     if ((e = upload_slots(c, T, harvest))) return c->cuda_fail(e, "upload harvest flags");
     if ((e = T->enqueue_recon())) return c->cuda_fail(e, "reconstruct odd sites");
@@ -401,14 +436,18 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
     // hopping parameter expansion: y = (kappa H)^K x for the finished systems that take it
     // (their right-hand side and scratch pairs are free now; x stays for the other contractions)
     int right_pair = PAIR_X;
-    if (out.hpe_order > 0 && !done_jobs.empty()) {
+    std::vector<char> is_hpe(N, 0);
+    if (out.hpe_order > 0 && (!done_jobs.empty() || (staged && !newly_done.empty()))) {
       std::vector<int> hpe_slots;
-      for (int j = 0; j < N; j++)
-        if (slot[j].job >= 0 && slot[j].done && jobs[slot[j].job].sys[slot[j].member].hpe &&
-            std::find(done_jobs.begin(), done_jobs.end(), slot[j].job) != done_jobs.end()) {
-          T->st_h[j].flags |= FLAG_HPE;
-          hpe_slots.push_back(j);
-        }
+      for (int j = 0; j < N; j++) {
+        if (slot[j].job < 0 || !slot[j].done || !jobs[slot[j].job].sys[slot[j].member].hpe) continue;
+        const bool now = staged ? std::find(newly_done.begin(), newly_done.end(), j) != newly_done.end()
+                                : std::find(done_jobs.begin(), done_jobs.end(), slot[j].job) != done_jobs.end();
+        if (!now) continue;
+        T->st_h[j].flags |= FLAG_HPE;
+        hpe_slots.push_back(j);
+        is_hpe[j] = 1;
+      }
       if (!hpe_slots.empty()) {
         if ((e = upload_slots(c, T, hpe_slots))) return c->cuda_fail(e, "upload expansion flags");
         int from = PAIR_X;
@@ -421,13 +460,47 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
       }
     }
 
+    // staged: the finished systems' vectors go to their columns and their slots are free at once
+    if (staged && !newly_done.empty()) {
+      const size_t cb = colsz * sizeof(double);
+      for (int j : newly_done) {
+        const size_t col = (size_t)stage_col[slot[j].job][slot[j].member];
+        const cudaMemcpyKind d2d = cudaMemcpyDeviceToDevice;
+        e = cudaMemcpyAsync(T->stage_x_e + col * colsz, T->x_hi + (size_t)j * colsz, cb, d2d, c->stream);
+        if (!e) e = cudaMemcpyAsync(T->stage_x_o + col * colsz, T->x_o + (size_t)j * colsz, cb, d2d, c->stream);
+        if (!e && is_hpe[j]) {
+          e = cudaMemcpyAsync(T->stage_y_e + col * colsz, T->field_pair(right_pair, 0) + (size_t)j * colsz, cb, d2d,
+                              c->stream);
+          if (!e)
+            e = cudaMemcpyAsync(T->stage_y_o + col * colsz, T->field_pair(right_pair, 1) + (size_t)j * colsz, cb,
+                                d2d, c->stream);
+        }
+        T->stage_spec_h[col] = T->spec_h[j];
+        if (!e)
+          e = cudaMemcpyAsync(T->stage_spec_d + col, T->stage_spec_h + col, sizeof(NoiseSpec), cudaMemcpyHostToDevice,
+                              c->stream);
+        if (e) return c->cuda_fail(e, "stage solutions");
+      }
+      for (int j : newly_done) {
+        memset(&T->st_h[j], 0, sizeof(SysState));
+        memset(&T->spec_h[j], 0, sizeof(NoiseSpec));
+        slot[j] = Slot{};
+        free_slots.push_back(j);
+      }
+      if ((e = upload_slots(c, T, newly_done))) return c->cuda_fail(e, "release slots");
+      if ((e = mark())) return c->cuda_fail(e, "upload fence");
+    }
+
     // contractions of the completed groups
     if (out.result && np > 0 && !done_jobs.empty()) {
       std::vector<ContractPair> pairs;
       for (int g : done_jobs) {
         std::vector<int> member_slot(jobs[g].sys.size(), -1);
-        for (int j = 0; j < N; j++)
-          if (slot[j].job == g) member_slot[slot[j].member] = j;
+        if (staged)
+          member_slot = stage_col[g];
+        else
+          for (int j = 0; j < N; j++)
+            if (slot[j].job == g) member_slot[slot[j].member] = j;
         for (ContractPair p : jobs[g].pairs) {
           p.right = member_slot[p.right];
           p.left = member_slot[p.left];
@@ -436,7 +509,10 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
       }
       if (!pairs.empty()) {
         std::vector<double> part;
-        if (int rc = contract_tile(c, T, pairs, out.gamma, *out.plist, part, out.rows, right_pair)) return rc;
+        const StageView sv{T->stage_x_e, T->stage_x_o, T->stage_y_e, T->stage_y_o, T->stage_spec_d, S};
+        if (int rc = contract_tile(c, T, pairs, out.gamma, *out.plist, part, out.rows, right_pair,
+                                   staged ? &sv : nullptr))
+          return rc;
         for (const ContractPair& p : pairs)
           for (int q2 = 0; q2 < np * 2; q2++)
             (*out.result)[(size_t)p.out * np * 2 + q2] = part[(size_t)p.out * np * 2 + q2];
@@ -487,9 +563,15 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
       }
     }
 
-    // release the slots of completed groups
+    // release the slots of completed groups (staged: their columns; the slots are free already)
     std::vector<int> released;
     for (int g : done_jobs) {
+      if (staged) {
+        for (int col : stage_col[g]) stage_free.push_back(col);
+        stage_col[g].clear();
+        finished++;
+        continue;
+      }
       for (int j = 0; j < N; j++) {
         if (slot[j].job != g) continue;
         memset(&T->st_h[j], 0, sizeof(SysState));
@@ -504,6 +586,8 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
       if ((e = upload_slots(c, T, released))) return c->cuda_fail(e, "release slots");
       if ((e = mark())) return c->cuda_fail(e, "upload fence");
     }
+    done_jobs.clear();
+    newly_done.clear();
 
     // follow-up solves: the phase-0 solution becomes the right-hand side of the same slot
     if (!chain_slots.empty()) {

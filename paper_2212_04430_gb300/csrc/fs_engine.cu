@@ -160,6 +160,7 @@ class Tile : public TileBase {
     for (void* q : owned) cudaFree(q);
     if (st_h) cudaFreeHost(st_h);
     if (spec_h) cudaFreeHost(spec_h);
+    if (stage_spec_h) cudaFreeHost(stage_spec_h);
     if (vec_h) cudaFreeHost(vec_h);
   }
 
@@ -410,6 +411,29 @@ class Tile : public TileBase {
     return parity ? tmp64 : r_hi;
   }
 
+  int stage_alloc(int S, bool with_y) override {
+    if (S <= stage_cols && (!with_y || stage_y_e)) return 0;
+    const int cols = std::max(S, stage_cols);
+    const size_t col = (size_t)24 * c->g.Vh * sizeof(double);
+    double* xe = (double*)dalloc(col * cols);
+    double* xo = (double*)dalloc(col * cols);
+    double* ye = (with_y || stage_y_e) ? (double*)dalloc(col * cols) : nullptr;
+    double* yo = (with_y || stage_y_e) ? (double*)dalloc(col * cols) : nullptr;
+    NoiseSpec* sd = (NoiseSpec*)dalloc(sizeof(NoiseSpec) * cols);
+    NoiseSpec* sh_ = nullptr;
+    if (cudaMallocHost(&sh_, sizeof(NoiseSpec) * cols) != cudaSuccess) sh_ = nullptr;
+    if (!xe || !xo || !sd || !sh_ || ((with_y || stage_y_e) && (!ye || !yo))) {
+      if (sh_) cudaFreeHost(sh_);
+      return 3;  // the partial allocations stay owned by the tile and are freed with it
+    }
+    if (stage_spec_h) cudaFreeHost(stage_spec_h);
+    stage_x_e = xe; stage_x_o = xo; stage_y_e = ye; stage_y_o = yo;
+    stage_spec_d = sd; stage_spec_h = sh_;
+    memset(stage_spec_h, 0, sizeof(NoiseSpec) * cols);
+    stage_cols = cols;
+    return 0;
+  }
+
   cudaError_t enqueue_kappa_hop(int from, int to) override {
     L1.stream = c->stream;
     LW.stream = c->stream;
@@ -589,7 +613,8 @@ int upload_colors(Ctx* c, const int* colors) {
 }
 
 int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, const double* gamma,
-                  const std::vector<int>& plist, std::vector<double>& result, int rows, int right_pair) {
+                  const std::vector<int>& plist, std::vector<double>& result, int rows, int right_pair,
+                  const StageView* sv) {
   const int np = (int)plist.size();
   const int npairs = (int)pairs.size();
   if (npairs == 0) return 0;
@@ -610,6 +635,10 @@ int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, c
   a.x_e = T->x_hi; a.x_o = T->x_o; a.wline = c->wline; a.spec = T->spec_d; a.colors = c->colors_d;
   a.y_e = T->field_pair(right_pair, 0);
   a.y_o = T->field_pair(right_pair, 1);
+  a.N = T->N;
+  if (sv) {  // staged vectors: system-major columns addressed like the tile's FP64 fields
+    a.x_e = sv->x_e; a.x_o = sv->x_o; a.y_e = sv->y_e; a.y_o = sv->y_o; a.spec = sv->spec; a.N = sv->N;
+  }
   for (int k = 0; k < 32; k++) a.gamma[k] = gamma[k];
   // detect a monomial Gamma (one entry per row, each +-1 or +-i): applied as a permutation
   a.gmono = 1;
@@ -629,7 +658,7 @@ int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, c
     if (found < 0) a.gmono = 0;
     a.gperm[r] = found;
   }
-  a.g = c->g; a.N = T->N; a.pmask = pmask; a.pmax = pmax; a.np = np;
+  a.g = c->g; a.pmask = pmask; a.pmax = pmax; a.np = np;
   a.nblk = (2 * c->g.Vh + 255) / 256;
   const size_t part_n = (size_t)npairs * np * 2 * a.nblk;
   const size_t res_n = (size_t)rows * np * 2;

@@ -90,6 +90,15 @@ class TileBase {
   virtual double* field_pair(int id, int parity) = 0;
   // pair `to` <- kappa H (pair `from`), full lattice, FP64, for the FLAG_HPE slots
   virtual cudaError_t enqueue_kappa_hop(int from, int to) = 0;
+  // Staging of finished solutions (run_queue): S columns laid out like the tile's FP64 fields
+  // (system-major, one column = one system's parity, 24 Vh doubles, contiguous), so a slot's
+  // solution moves with plain device copies and its slot is free at once. y holds the
+  // expansion's (kappa H)^K x when requested. Allocated on first use; 0 or 3 (out of memory).
+  double *stage_x_e = nullptr, *stage_x_o = nullptr, *stage_y_e = nullptr, *stage_y_o = nullptr;
+  NoiseSpec* stage_spec_d = nullptr;
+  NoiseSpec* stage_spec_h = nullptr;  // pinned mirror
+  int stage_cols = 0;
+  virtual int stage_alloc(int S, bool with_y) = 0;
   // CGNR fallback (FP64) for the slots flagged FLAG_CG; its vectors are allocated on first use
   virtual int cg_alloc() = 0;
   virtual cudaError_t enqueue_cg_init() = 0;
@@ -208,11 +217,18 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
 // nmax; measured once per context and format, then cached in c->tuned_tile. 0 on failure.
 int autotune_tile(Ctx* c, const SolveOpts& o, int nmax);
 
-// Contractions over the solutions held in a tile; pairs with right_kind 1 read their right vector
-// from field pair `right_pair` instead of the solution.
+// Where contract_tile reads its vectors when they are not the tile's own: the staging columns.
+struct StageView {
+  const double *x_e, *x_o, *y_e, *y_o;
+  const NoiseSpec* spec;
+  int N;
+};
+
+// Contractions over the solutions held in a tile (or, with sv, in its staging columns); pairs
+// with right_kind 1 read their right vector from field pair `right_pair` (sv: the staged y).
 int contract_tile(Ctx* c, TileBase* T, const std::vector<ContractPair>& pairs, const double* gamma,
                   const std::vector<int>& plist, std::vector<double>& result /* [rows][np][2] */, int rows,
-                  int right_pair = PAIR_X);
+                  int right_pair = PAIR_X, const StageView* sv = nullptr);
 
 // Exact low orders of the hopping parameter expansion (Sec. 3.1, the remark after
 // Eq. (sampled_single)): T = sum_{k<K} Tr(Gamma Omega_p (kappa H)^k) / A, A = 4 + m + sigma,

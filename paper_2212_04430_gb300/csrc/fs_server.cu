@@ -63,8 +63,12 @@ size_t estimate(const SJob& j) {
   const size_t contract = (size_t)tile * ((2 * Vh + 255) / 256) * 2 * 8 + (64u << 10) +
                           (j.P.p > 0 ? V * 18 * 8 : 0) +  // partial sums + the path products
                           (j.P.colors ? V * 4 : 0);       // + the probing colours
+  // staging of finished solutions for groups of several systems (split-even pairs): 2 tile
+  // columns of FP64 vectors, twice with the expansion's vectors
+  const size_t staging = j.P.estimator == FS_EST_SPLIT_EVEN
+                             ? (size_t)2 * tile * 24 * V * 8 * (j.P.hpe_order > 0 ? 2 : 1) : 0;
   const size_t lanes = (size_t)std::max(1, j.P.solve.lanes);
-  return lanes * (tile_bytes + stage) + gauge + contract + (32u << 20);
+  return lanes * (tile_bytes + stage + staging) + gauge + contract + (32u << 20);
 }
 
 }  // namespace
