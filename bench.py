@@ -480,9 +480,9 @@ def run_hpe(pkg, ctx, w, kw, K=4, n=64, seed=9200):
             "note": "seconds_hpe includes the exact low orders (12 c probing vectors, K-1 FP64 kappa H each)"}
 
 
-def run_variance_24x64(pkg, inputs, device, n_s=6, seed=2005):
+def run_variance_24x64(pkg, inputs, device, n_s=24, seed=2005):
     """The 24^3x64 variance-sampling job (5 sampling shifts, p = 0..8, FP16 storage, 12-real links,
-    64-system tiles holding 6 noise vectors' 60 systems) on n_s Z4 vectors: solves/s through variance_sample, timed
+    64-system tiles, groups of 10 systems per noise vector refilled as slots free) on n_s Z4 vectors: solves/s through variance_sample, timed
     with CUDA events; the gauge upload is outside the timed region."""
     import torch
     dims = (24, 24, 24, 64)
