@@ -31,9 +31,10 @@ import numpy as np  # noqa: E402
 METRIC = "shifted Wilson solves/s at 1e-8 resid; dslash HBM GB/s vs peak; p50/p99 latency"
 
 WORKLOADS = {
-    # the 16^3x32 FS-MLMC job (4 levels, 512 Z4 vectors per level in 32-system tiles)
+    # the 16^3x32 FS-MLMC job (4 levels, 512 Z4 vectors per level in 32-system tiles); a step is a
+    # quarter of it, 128 vectors per level (the tiles drain once per call: 32 per call lost 8%)
     "16x32": dict(key="16x32", dims=(16, 16, 16, 32), eps=0.4, gauge_seed=1003, noise_seed=2003, m=-0.35,
-                  sigmas=[0.005, 0.03, 0.15, 0.6], gamma="g3", p=4, vectors=32, tile=32, prec="f16",
+                  sigmas=[0.005, 0.03, 0.15, 0.6], gamma="g3", p=4, vectors=128, tile=32, prec="f16",
                   link=12, tol=1e-8, estimator="diff",
                   name="16^3x32 Wilson FS-MLMC, 4 levels {0.005,0.03,0.15,0.6}, m=-0.35, eps=0.4, gamma3, p=4"),
     # the 8^4 FS-MLMC job (3 levels, 256 Z4 vectors per level in 16-system tiles)
