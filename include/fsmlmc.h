@@ -285,8 +285,9 @@ int fs_profile_read(fs_ctx* ctx, long long* launches, double* total_ms, double* 
 
 /* ---- serving ---------------------------------------------------------------------
  * A server on one GPU runs FS-MLMC trace jobs (one mlmc_level_trace each) as they arrive.
- * Jobs are admitted first in first out when one of `max_active` slots is free and the
- * job's device-memory estimate fits `hbm_budget_bytes` next to the running jobs; every
+ * Jobs are admitted when one of `max_active` slots is free and the job's device-memory
+ * estimate fits `hbm_budget_bytes` next to the running jobs, least work first with a bound on
+ * the wait (fs_server_set_admission; first in, first out on request); every
  * running job has its own worker thread, context and CUDA stream, so their work overlaps
  * on the device, and inside a job the solves are continuously batched. A job's results
  * depend only on its own inputs and are identical alone or in a mix. */
@@ -331,6 +332,13 @@ int fs_server_submit(fs_server* server, const fs_job* job, uint64_t* ticket);
  * A result is returned once, then the ticket is forgotten. */
 int fs_server_poll(fs_server* server, uint64_t ticket, fs_job_result* result, int timeout_ms);
 int fs_server_stats(fs_server* server, fs_server_report* stats);
+/* Admission order (a library addition; the paper has no server). least_work_first = 1 (the
+ * default): among the queued jobs whose memory estimate fits the budget, the one with the least
+ * work (solves x lattice sites) starts first, which shortens the median latency; a job queued for
+ * max_wait_ms (default 10000) goes next regardless and no later job passes it, so no job waits
+ * for ever. least_work_first = 0: first in, first out. FS_ERR_ARG for other values or a negative
+ * wait. */
+int fs_server_set_admission(fs_server* server, int least_work_first, double max_wait_ms);
 /* Finishes queued and running jobs, then stops the workers. */
 void fs_server_destroy(fs_server* server);
 

@@ -40,6 +40,7 @@ struct SJob {
   std::vector<int32_t> colors;  // probing colours, [V] (empty: no probing)
   fs_mlmc_params P{};
   size_t est = 0;
+  double work = 0;  // solves x lattice sites: the admission order's measure of a job's size
   double t_submit = 0, t_start = 0, t_end = 0;
   bool done = false;
   fs_job_result res{};
@@ -89,6 +90,24 @@ struct fs_server {
   std::vector<double> latencies;
   long long completed = 0, solves = 0;
   double t_first = -1, t_last = 0;
+  // admission order: least work first among the jobs that fit the budget, except that a job
+  // queued for max_wait_ms goes next (oldest first) and no job passes it; least_work_first = 0
+  // is first in, first out
+  int least_work_first = 1;
+  double max_wait_ms = 10000.0;
+
+  // index in `queue` of the job to admit now, or -1 (called with mu held)
+  int pick() const {
+    if (queue.empty()) return -1;
+    if (!least_work_first) return reserved + queue.front()->est <= budget ? 0 : -1;
+    const double t = now_ms();
+    for (size_t i = 0; i < queue.size(); i++)
+      if (t - queue[i]->t_submit >= max_wait_ms) return reserved + queue[i]->est <= budget ? (int)i : -1;
+    int best = -1;
+    for (size_t i = 0; i < queue.size(); i++)
+      if (reserved + queue[i]->est <= budget && (best < 0 || queue[i]->work < queue[best]->work)) best = (int)i;
+    return best;
+  }
 
   void worker() {
     fs_ctx* ctx = nullptr;
@@ -98,12 +117,12 @@ struct fs_server {
       SJob* j = nullptr;
       {
         std::unique_lock<std::mutex> lock(mu);
-        cv_work.wait(lock, [&] {
-          return (stop && queue.empty()) || (!queue.empty() && reserved + queue.front()->est <= budget);
-        });
+        int k = -1;
+        // re-checked at least every 100 ms: a job reaching max_wait_ms changes the choice
+        while (!(stop && queue.empty()) && (k = pick()) < 0) cv_work.wait_for(lock, std::chrono::milliseconds(100));
         if (queue.empty()) break;  // stopping and drained
-        j = queue.front();
-        queue.pop_front();
+        j = queue[k];
+        queue.erase(queue.begin() + k);
         reserved += j->est;
         active += 1;
         j->t_start = now_ms();
@@ -216,6 +235,7 @@ int fs_server_submit(fs_server* s, const fs_job* job, uint64_t* ticket) {
   j->P.gamma = j->gamma.data();
   j->P.colors = P.colors ? j->colors.data() : nullptr;
   j->est = estimate(*j);
+  j->work = (double)std::max(0, fs_mlmc_num_solves(&j->P)) * (double)V;
   if (j->est > s->budget) return FS_ERR_BUDGET;
   std::lock_guard<std::mutex> lock(s->mu);
   if (s->stop) return FS_ERR_STATE;
@@ -239,6 +259,17 @@ int fs_server_poll(fs_server* s, uint64_t ticket, fs_job_result* out, int timeou
   else if (!s->cv_done.wait_for(lock, std::chrono::milliseconds(timeout_ms), pred)) return FS_ERR_TIMEOUT;
   *out = j->res;
   s->jobs.erase(it);  // a result is handed out once
+  return FS_OK;
+}
+
+int fs_server_set_admission(fs_server* s, int least_work_first, double max_wait_ms) {
+  if (!s || (least_work_first != 0 && least_work_first != 1) || !(max_wait_ms >= 0.0)) return FS_ERR_ARG;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->least_work_first = least_work_first;
+    s->max_wait_ms = max_wait_ms;
+  }
+  s->cv_work.notify_all();
   return FS_OK;
 }
 

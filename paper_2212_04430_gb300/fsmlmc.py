@@ -28,7 +28,7 @@ EXPORTS = ["fs_ctx_create", "fs_ctx_destroy", "fs_last_error", "fs_set_stream", 
            "fs_server_stats", "fs_server_destroy", "fs_interp_variances", "fs_select_shifts",
            "fs_sample_allocation", "fs_eval_grid", "fs_tuned_tile", "fs_probing_colors",
            "variance_sample_probed", "shifted_solve_dev", "fs_hpe_exact_trace",
-           "mlmc_level_traces"]
+           "mlmc_level_traces", "fs_server_set_admission"]
 JOB_MAX_LEVELS = 16
 
 
@@ -122,6 +122,7 @@ def load_library(path=LIB_PATH):
         "fs_server_poll": (I, [P, ctypes.c_uint64, ctypes.POINTER(JobResult), I]),
         "fs_server_stats": (I, [P, ctypes.POINTER(ServerReport)]),
         "fs_server_destroy": (None, [P]),
+        "fs_server_set_admission": (I, [P, I, D]),
         "fs_interp_variances": (I, [dp, I, dp, dp, dp, I, dp, dp]),
         "fs_select_shifts": (I, [dp, I, dp, dp, dp, dp, I, I, ip, dp, dp, dp]),
         "fs_sample_allocation": (I, [dp, dp, I, D, dp, dp, dp, dp]),
@@ -507,6 +508,12 @@ class Server:
         if rc != FS_OK:
             raise FsError(rc, "fs_server_submit failed")
         return t.value
+
+    def set_admission(self, least_work_first=True, max_wait_ms=10000.0):
+        """Admission order: least work first with a waiting-time bound (default), or FIFO."""
+        rc = self.lib.fs_server_set_admission(self.h, int(bool(least_work_first)), float(max_wait_ms))
+        if rc != FS_OK:
+            raise FsError(rc, "fs_server_set_admission failed")
 
     def poll(self, ticket, timeout_ms=-1):
         """Result dict of a finished job, or None on timeout."""

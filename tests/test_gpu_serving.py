@@ -116,3 +116,32 @@ def test_probed_and_expanded_jobs_in_a_concurrent_mix():
     for a, r in zip(alone, results):
         assert r["status"] == 0
         assert np.array_equal(r["trace"], a["trace"]) and np.array_equal(r["var"], a["var"])
+
+
+def test_least_work_first_admission():
+    """With one worker busy, a large and then a small job queue up: the small one starts first
+    (least work first); with FIFO requested, the large one does; a job older than max_wait_ms goes
+    next whatever its size."""
+    small, large = (4, 4, 4, 4), (8, 8, 8, 8)
+    u_s = inputs.gauge_field(small, "smooth", seed=91, eps=0.3)
+    u_l = inputs.gauge_field(large, "smooth", seed=92, eps=0.3)
+    g = pkg.gamma_matrix("g3")
+    kw = dict(prec="f32", tol=1e-8, rhs_tile=16)
+
+    def order(least_work_first, max_wait_ms):
+        srv = pkg.Server(device=0, hbm_budget_bytes=8 << 30, max_active=1)
+        srv.set_admission(least_work_first, max_wait_ms)
+        busy = srv.submit(large, u_l, -0.2, [0.02, 0.3], g, 1, [48, 48], seed=1, **kw)  # occupies the worker
+        big = srv.submit(large, u_l, -0.2, [0.02, 0.3], g, 1, [16, 16], seed=2, **kw)
+        tiny = srv.submit(small, u_s, -0.2, [0.3], g, 0, [2], seed=3, **kw)
+        r = {k: srv.poll(t) for k, t in (("busy", busy), ("big", big), ("tiny", tiny))}
+        srv.close()
+        assert all(x["status"] == 0 for x in r.values())
+        return r
+
+    r = order(True, 60000.0)
+    assert r["tiny"]["queue_ms"] < r["big"]["queue_ms"]
+    r = order(False, 60000.0)
+    assert r["big"]["queue_ms"] < r["tiny"]["queue_ms"]
+    r = order(True, 0.0)  # every queued job counts as waited out: oldest first
+    assert r["big"]["queue_ms"] < r["tiny"]["queue_ms"]
