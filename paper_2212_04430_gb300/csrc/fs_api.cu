@@ -488,6 +488,20 @@ int fs_hpe_exact_trace(fs_ctx* ctx, double m, double sigma, const double* gamma,
   return fs::hpe_exact(&c, T, o.so, sigma, K, p, gamma, seed, out);
 }
 
+// Probing colours of a call: every site has a colour in [0, ncolors) and every colour is used
+// (no piece of a sample has an empty support).
+static int check_colors(Ctx& c, const int32_t* colors, int ncolors) {
+  std::vector<char> used(ncolors, 0);
+  for (long long x = 0; x < c.g.V; x++) {
+    const int32_t j = colors[x];
+    if (j < 0 || j >= ncolors) return c.fail(FS_ERR_ARG, "probing colour out of range");
+    used[j] = 1;
+  }
+  for (int j = 0; j < ncolors; j++)
+    if (!used[j]) return c.fail(FS_ERR_ARG, "every probing colour must be used");
+  return 0;
+}
+
 // Pieces of one sample: probing colours times spin-colour components (Sec. 2.1, Sec. 3.1).
 int num_pieces(const fs_mlmc_params* p) {
   if (p->dilute != 0 && p->dilute != 1) return -1;
@@ -555,17 +569,8 @@ int mlmc_impl(Ctx& c, const fs_mlmc_params* P, const int* p_in, int np, double* 
   const bool hpe = P->hpe_order > 0 && P->m + P->sigma[L] > 0.0;
   // the exact low orders take Omega_0 = 1; a displacement of a whole period is a Polyakov loop
   if (hpe && pmax >= c.g.L[2]) return c.fail(FS_ERR_ARG, "hpe_order needs p < Lz");
-  if (P->colors) {
-    // every site has a colour in range and every colour is used (no piece has an empty support)
-    std::vector<char> used(P->ncolors, 0);
-    for (long long x = 0; x < c.g.V; x++) {
-      const int32_t j = P->colors[x];
-      if (j < 0 || j >= P->ncolors) return c.fail(FS_ERR_ARG, "probing colour out of range");
-      used[j] = 1;
-    }
-    for (int j = 0; j < P->ncolors; j++)
-      if (!used[j]) return c.fail(FS_ERR_ARG, "every probing colour must be used");
-  }
+  if (P->colors)
+    if (int rc = check_colors(c, P->colors, P->ncolors)) return rc;
   Opts o;
   if (int rc = resolve_params(c, &P->solve, nsolve, P->m, o)) return rc;
   if (int rc = set_device(c)) return rc;
@@ -764,15 +769,8 @@ int variance_sample_impl(Ctx& c, double m, const double* s_hat, int ms, const do
     if (i > 0 && !(s_hat[i] > s_hat[i - 1])) return c.fail(FS_ERR_ARG, "sampling shifts must increase");
     if (std::fabs(4.0 + m + s_hat[i]) < 1e-12) return c.fail(FS_ERR_ARG, "4 + m + sigma must be nonzero");
   }
-  if (colors) {
-    std::vector<char> used(ncolors, 0);
-    for (long long x = 0; x < c.g.V; x++) {
-      if (colors[x] < 0 || colors[x] >= ncolors) return c.fail(FS_ERR_ARG, "probing colour out of range");
-      used[colors[x]] = 1;
-    }
-    for (int j = 0; j < ncolors; j++)
-      if (!used[j]) return c.fail(FS_ERR_ARG, "every probing colour must be used");
-  }
+  if (colors)
+    if (int rc = check_colors(c, colors, ncolors)) return rc;
   const int ncomp = dilute ? 12 : 1;
   const long long npieces_ll = (long long)(colors ? ncolors : 1) * ncomp;
   const int gsize = dilute ? ms : 2 * ms;  // systems per piece: x^(i), and y^(i) unless diluted
