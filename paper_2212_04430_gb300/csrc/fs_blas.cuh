@@ -307,6 +307,7 @@ struct FinArgs {
   double target;     // rms target of the scaled residual entries
   double nreal;      // 24 * Vh
   int max_restarts;
+  int first_approx;  // a system's first reliable update took its true residual in FP32
 };
 
 __device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi, double& cr, double& ci) {
@@ -415,9 +416,12 @@ __device__ __forceinline__ void fin_logic(const FinArgs& a, int op, SysState& s,
     double v[1];
     take<1>(v, tot, off);
     if (threadIdx.x == 0) {
+      // an FP32 residual (the first update) restarts the iteration but never decides convergence:
+      // a system below tol goes on and its next update, in FP64, checks it
+      const bool approx = a.first_approx && s.updates == 0;
       s.r2_true = v[0];
       s.updates += 1;
-      if (v[0] <= s.tol2) {
+      if (v[0] <= s.tol2 && !approx) {
         s.status = SYS_CONVERGED;
         s.flags = 0;
       } else if ((s.flags & FLAG_FINAL) || !isfinite(v[0]) ||
@@ -425,7 +429,7 @@ __device__ __forceinline__ void fin_logic(const FinArgs& a, int op, SysState& s,
         s.status = SYS_NOCONV;
         s.flags = 0;
       } else {
-        const double sc = a.target * sqrt(a.nreal / v[0]);
+        const double sc = a.target * sqrt(a.nreal / fmax(v[0], 1e-300));
         set_coef(s, C_RATIO, sc * s.cd[C_INVSCALE]);
         set_coef(s, C_SCALE, sc);
         set_coef(s, C_INVSCALE, 1.0 / sc);

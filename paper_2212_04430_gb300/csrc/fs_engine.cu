@@ -251,6 +251,7 @@ class Tile : public TileBase {
     f.target = 0.25;  // rms of a scaled residual entry (keeps FP16 away from both range limits)
     f.nreal = 24.0 * c->g.Vh;
     f.max_restarts = 8;
+    f.first_approx = std::is_same<Ts, double>::value ? 0 : 1;
     const dim3 grid(N, FIN_SPLIT);
     switch (fin_values(op)) {
       case 1: fin_kernel<1><<<grid, 256, 0, c->stream>>>(f, op); break;
@@ -341,12 +342,25 @@ class Tile : public TileBase {
     L1.stream = c->stream;
     LW.stream = c->stream;
     if ((e = launch_blas<Ts>(OP_ACCX, blas(MASK_UPDATE, nullptr, nullptr, true, true), LW))) return e;
+    // A system's first update restarts from a residual of about delta ||b||, which FP32 arithmetic
+    // on the FP64 iterate meets to a small fraction of itself: that one runs on the FP32 pipe
+    // (links in FP32) instead of the FP64 pipe; every later update, which also decides
+    // convergence, is FP64. The FP64 storage mode keeps FP64 throughout.
+    int later = MASK_UPDATE;
+    if constexpr (!std::is_same<Ts, double>::value) {
+      later = MASK_UPDATE_LATER;
+      HopArgs h1 = hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, MASK_UPDATE_FIRST, true, true, true);
+      HopArgs h2 = hop(r_hi, tmp64, x_hi, bhat, nullptr, pa, 0, MASK_UPDATE_FIRST, true, true, true);
+      h1.gauge = h2.gauge = c->gauge_for(PREC_F32, 18);
+      if ((e = launch_hop64_f32(COEF_PLAIN, DOT_NONE, h1, lwh()))) return e;
+      if ((e = launch_hop64_f32(COEF_TRUERES, DOT_NORM, h2, lwh()))) return e;
+    }
     if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
-                                hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, MASK_UPDATE, true, true,
-                                    true), lwh())))
+                                hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, later, true, true, true),
+                                lwh())))
       return e;
     if ((e = launch_hop<double>(COEF_TRUERES, DOT_NORM, 18,
-                                hop(r_hi, tmp64, x_hi, bhat, nullptr, pa, 0, MASK_UPDATE, true, true, true), lwh())))
+                                hop(r_hi, tmp64, x_hi, bhat, nullptr, pa, 0, later, true, true, true), lwh())))
       return e;
     if ((e = fin(FIN_TRUE, MASK_UPDATE, pa))) return e;
     if ((e = launch_blas<Ts>(OP_SETR, blas(MASK_UPDATE, r_hi, pa, true, true), LW))) return e;

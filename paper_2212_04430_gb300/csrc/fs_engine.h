@@ -33,6 +33,10 @@ struct Launch {
 };
 
 template <typename Ts> cudaError_t launch_hop(int coef, int dot, int nr, const HopArgs& a, const Launch& l);
+// FP64 fields, FP32 links (18 reals) and FP32 arithmetic, system-major work list: the true residual
+// of a system's first reliable update (fs_kern_f32.cu); COEF_PLAIN / DOT_NONE and COEF_TRUERES /
+// DOT_NORM only.
+cudaError_t launch_hop64_f32(int coef, int dot, const HopArgs& a, const Launch& l);
 template <typename Ts> cudaError_t launch_blas(int op, const BlasArgs& a, const Launch& l);
 template <typename Ts> cudaError_t launch_pack(void* fe, void* fo, const double* canon, const int* vec,
                                                const Geom& g, const Shape& sh, const Launch& l, bool sysmajor);

@@ -39,8 +39,9 @@ template <> struct DotK<DOT_R> { static constexpr int K = 2; };
 template <> struct DotK<DOT_TS> { static constexpr int K = 8; };
 template <> struct DotK<DOT_NORM> { static constexpr int K = 1; };
 
+// MASK_UPDATE_FIRST / _LATER split the reliable updates into a system's first one and the rest
 enum Mask { MASK_ALL = 0, MASK_ACTIVE = 1, MASK_UPDATE = 2, MASK_INIT = 3, MASK_HARVEST = 4, MASK_CG = 5,
-            MASK_CG_CHECK = 6, MASK_HPE = 7 };
+            MASK_CG_CHECK = 6, MASK_HPE = 7, MASK_UPDATE_FIRST = 8, MASK_UPDATE_LATER = 9 };
 
 __device__ __forceinline__ bool selected(const SysState* st, int sys, int mask) {
   if (mask == MASK_ALL) return true;
@@ -48,6 +49,9 @@ __device__ __forceinline__ bool selected(const SysState* st, int sys, int mask) 
   // a system that broke down earlier in this iteration sits out until its restart
   if (mask == MASK_ACTIVE) return s == SYS_ACTIVE && !(f & (FLAG_RESTART | FLAG_CG));
   if (mask == MASK_UPDATE) return s == SYS_ACTIVE && (f & FLAG_UPDATE) && !(f & FLAG_CG);
+  if (mask == MASK_UPDATE_FIRST || mask == MASK_UPDATE_LATER)
+    return s == SYS_ACTIVE && (f & FLAG_UPDATE) && !(f & FLAG_CG) &&
+           ((st[sys].updates == 0) == (mask == MASK_UPDATE_FIRST));
   // CGNR fallback systems, and those of them due a true-residual check
   if (mask == MASK_CG) return s == SYS_ACTIVE && (f & FLAG_CG);
   if (mask == MASK_CG_CHECK) return s == SYS_ACTIVE && (f & FLAG_CG) && (f & FLAG_UPDATE);
