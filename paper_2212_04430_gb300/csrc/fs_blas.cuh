@@ -22,7 +22,8 @@ namespace fs {
 enum BlasOp {
   OP_S = 1,       // s = r - alpha v
   OP_XRP = 2,     // x_lo += alpha p + omega s ; r = s - omega t ; p = r + beta (p - omega v)
-  OP_ACCX = 3,    // x_hi += x_lo / scale ; x_lo = 0
+  OP_ACCX = 3,    // x_hi += x_lo / scale ; x_lo = 0 ; with src: src = x_lo / scale for the
+                  // systems at an even update k >= 2 (the change the correction residual needs)
   OP_ZEROX = 4,   // x_hi = 0 ; x_lo = 0
   OP_SETR = 5,    // r = scale * src ; on restart/init rhat = p = r, v = 0, else p rescaled ;
                   // <rhat, r>, ||r||^2
@@ -120,8 +121,15 @@ __global__ void __launch_bounds__(256) blas_kernel(BlasArgs a) {
         // on a breakdown the sloppy correction is discarded, never folded into x_hi
         const bool keep = !(a.st[sys].flags & FLAG_RESTART);
         const double isc = a.st[sys].cd[C_INVSCALE];
+        const int ku = a.st[sys].updates;
         double hv[24], lv[24];
         xh.load(site, sys, hv); xl.load(site, sys, lv);
+        if (a.src != nullptr && ku >= 2 && !(ku & 1)) {
+          double dx[24];
+#pragma unroll
+          for (int k = 0; k < 24; k++) dx[k] = keep ? isc * lv[k] : 0.0;
+          src.store(site, sys, dx);
+        }
 #pragma unroll
         for (int k = 0; k < 24; k++) { if (keep) hv[k] += isc * lv[k]; lv[k] = 0.0; }
         xh.store(site, sys, hv); xl.store(site, sys, lv);
@@ -416,9 +424,10 @@ __device__ __forceinline__ void fin_logic(const FinArgs& a, int op, SysState& s,
     double v[1];
     take<1>(v, tot, off);
     if (threadIdx.x == 0) {
-      // an FP32 residual (the first update) restarts the iteration but never decides convergence:
-      // a system below tol goes on and its next update, in FP64, checks it
-      const bool approx = a.first_approx && s.updates == 0;
+      // an FP32-arithmetic residual (update 0, or a correction at an even update k >= 2) restarts
+      // the iteration but never decides convergence: a system below tol goes on and its next
+      // update, a full FP64 residual, checks it
+      const bool approx = a.first_approx && !(s.updates & 1);
       s.r2_true = v[0];
       s.updates += 1;
       if (v[0] <= s.tol2 && !approx) {

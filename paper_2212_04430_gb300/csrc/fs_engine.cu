@@ -341,19 +341,30 @@ class Tile : public TileBase {
     // read per block instead of occupying FP64 issue slots inside mixed warps.
     L1.stream = c->stream;
     LW.stream = c->stream;
-    if ((e = launch_blas<Ts>(OP_ACCX, blas(MASK_UPDATE, nullptr, nullptr, true, true), LW))) return e;
-    // A system's first update restarts from a residual of about delta ||b||, which FP32 arithmetic
-    // on the FP64 iterate meets to a small fraction of itself: that one runs on the FP32 pipe
-    // (links in FP32) instead of the FP64 pipe; every later update, which also decides
-    // convergence, is FP64. The FP64 storage mode keeps FP64 throughout.
+    // Mixed precision: FP32 arithmetic (FP32 links, FP64 fields, the FP32 pipe) where it meets
+    // the update's need, FP64 where the residual decides convergence.
+    //  - update 0 restarts from a residual of about delta ||b||: r = bhat - M x_hi in FP32
+    //    arithmetic errs by about eps32 A ||x||, a small fraction of it;
+    //  - odd updates: the full residual in FP64 (and only these end a solve);
+    //  - even updates k >= 2: r = r_prev - M dx, dx = x_lo / scale the iterate's change since the
+    //    previous (FP64) update, held in x_o (free until the odd sites are reconstructed); the
+    //    FP32 error is about eps32 A ||dx||, relative to the small dx instead of x.
+    // The FP64 storage mode keeps FP64 throughout.
+    constexpr bool mixed = !std::is_same<Ts, double>::value;
+    if ((e = launch_blas<Ts>(OP_ACCX, blas(MASK_UPDATE, mixed ? x_o : nullptr, nullptr, true, true), LW))) return e;
     int later = MASK_UPDATE;
-    if constexpr (!std::is_same<Ts, double>::value) {
+    if constexpr (mixed) {
       later = MASK_UPDATE_LATER;
+      void* g32 = c->gauge_for(PREC_F32, 18);
       HopArgs h1 = hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, MASK_UPDATE_FIRST, true, true, true);
       HopArgs h2 = hop(r_hi, tmp64, x_hi, bhat, nullptr, pa, 0, MASK_UPDATE_FIRST, true, true, true);
-      h1.gauge = h2.gauge = c->gauge_for(PREC_F32, 18);
+      HopArgs h3 = hop(tmp64, x_o, nullptr, nullptr, nullptr, nullptr, 1, MASK_UPDATE_CORR, true, true, true);
+      HopArgs h4 = hop(r_hi, tmp64, x_o, r_hi, nullptr, pa, 0, MASK_UPDATE_CORR, true, true, true);
+      h1.gauge = h2.gauge = h3.gauge = h4.gauge = g32;
       if ((e = launch_hop64_f32(COEF_PLAIN, DOT_NONE, h1, lwh()))) return e;
       if ((e = launch_hop64_f32(COEF_TRUERES, DOT_NORM, h2, lwh()))) return e;
+      if ((e = launch_hop64_f32(COEF_PLAIN, DOT_NONE, h3, lwh()))) return e;
+      if ((e = launch_hop64_f32(COEF_TRUERES, DOT_NORM, h4, lwh()))) return e;
     }
     if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
                                 hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, later, true, true, true),

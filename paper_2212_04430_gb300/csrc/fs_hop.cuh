@@ -39,9 +39,12 @@ template <> struct DotK<DOT_R> { static constexpr int K = 2; };
 template <> struct DotK<DOT_TS> { static constexpr int K = 8; };
 template <> struct DotK<DOT_NORM> { static constexpr int K = 1; };
 
-// MASK_UPDATE_FIRST / _LATER split the reliable updates into a system's first one and the rest
+// The reliable updates of a mixed-precision solve by their index k (SysState::updates): k = 0
+// MASK_UPDATE_FIRST, odd k MASK_UPDATE_LATER (full FP64 residual), even k >= 2 MASK_UPDATE_CORR
+// (the previous residual corrected by the iterate's change)
 enum Mask { MASK_ALL = 0, MASK_ACTIVE = 1, MASK_UPDATE = 2, MASK_INIT = 3, MASK_HARVEST = 4, MASK_CG = 5,
-            MASK_CG_CHECK = 6, MASK_HPE = 7, MASK_UPDATE_FIRST = 8, MASK_UPDATE_LATER = 9 };
+            MASK_CG_CHECK = 6, MASK_HPE = 7, MASK_UPDATE_FIRST = 8, MASK_UPDATE_LATER = 9,
+            MASK_UPDATE_CORR = 10 };
 
 __device__ __forceinline__ bool selected(const SysState* st, int sys, int mask) {
   if (mask == MASK_ALL) return true;
@@ -49,9 +52,11 @@ __device__ __forceinline__ bool selected(const SysState* st, int sys, int mask) 
   // a system that broke down earlier in this iteration sits out until its restart
   if (mask == MASK_ACTIVE) return s == SYS_ACTIVE && !(f & (FLAG_RESTART | FLAG_CG));
   if (mask == MASK_UPDATE) return s == SYS_ACTIVE && (f & FLAG_UPDATE) && !(f & FLAG_CG);
-  if (mask == MASK_UPDATE_FIRST || mask == MASK_UPDATE_LATER)
-    return s == SYS_ACTIVE && (f & FLAG_UPDATE) && !(f & FLAG_CG) &&
-           ((st[sys].updates == 0) == (mask == MASK_UPDATE_FIRST));
+  if (mask == MASK_UPDATE_FIRST || mask == MASK_UPDATE_LATER || mask == MASK_UPDATE_CORR) {
+    if (!(s == SYS_ACTIVE && (f & FLAG_UPDATE) && !(f & FLAG_CG))) return false;
+    const int k = st[sys].updates;
+    return mask == MASK_UPDATE_FIRST ? k == 0 : (mask == MASK_UPDATE_LATER ? (k & 1) != 0 : k >= 2 && !(k & 1));
+  }
   // CGNR fallback systems, and those of them due a true-residual check
   if (mask == MASK_CG) return s == SYS_ACTIVE && (f & FLAG_CG);
   if (mask == MASK_CG_CHECK) return s == SYS_ACTIVE && (f & FLAG_CG) && (f & FLAG_UPDATE);
