@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) blas_kernel(BlasArgs a) {
         const int ku = a.st[sys].updates;
         double hv[24], lv[24];
         xh.load(site, sys, hv); xl.load(site, sys, lv);
-        if (a.src != nullptr && ku >= 2 && !(ku & 1)) {
+        if (a.src != nullptr && ku >= 2 && !(ku & 1) && !(a.st[sys].flags & FLAG_CHECK)) {
           double dx[24];
 #pragma unroll
           for (int k = 0; k < 24; k++) dx[k] = keep ? isc * lv[k] : 0.0;
@@ -412,10 +412,10 @@ __device__ __forceinline__ void fin_logic(const FinArgs& a, int op, SysState& s,
         const double r2hi = s.r2 * isc * isc;
         if (!isfinite(r2) || !isfinite(s.rho[0]) || !isfinite(s.rho[1])) s.flags |= FLAG_UPDATE | FLAG_RESTART;
         // below this the recurrence for ||r||^2 has lost most of its digits: ask FP64
-        if (!(r2 > 1e-5 * v[3])) s.flags |= FLAG_UPDATE;
-        if (r2hi <= s.tol2) s.flags |= FLAG_UPDATE;
+        if (!(r2 > 1e-5 * v[3])) s.flags |= FLAG_UPDATE | FLAG_CHECK;
+        if (r2hi <= s.tol2) s.flags |= FLAG_UPDATE | FLAG_CHECK;
         if (s.r2 < s.delta2 * s.r2_max) s.flags |= FLAG_UPDATE;
-        if (s.iters >= s.max_iter) s.flags |= FLAG_UPDATE | FLAG_FINAL;
+        if (s.iters >= s.max_iter) s.flags |= FLAG_UPDATE | FLAG_FINAL | FLAG_CHECK;
         if (s.r2 > s.r2_max) s.r2_max = s.r2;
       }
       if ((s.flags & FLAG_UPDATE) && a.gate) atomicExch(a.gate, 1);
@@ -427,7 +427,7 @@ __device__ __forceinline__ void fin_logic(const FinArgs& a, int op, SysState& s,
       // an FP32-arithmetic residual (update 0, or a correction at an even update k >= 2) restarts
       // the iteration but never decides convergence: a system below tol goes on and its next
       // update, a full FP64 residual, checks it
-      const bool approx = a.first_approx && !(s.updates & 1);
+      const bool approx = a.first_approx && !(s.updates & 1) && !(s.flags & FLAG_CHECK);
       s.r2_true = v[0];
       s.updates += 1;
       if (v[0] <= s.tol2 && !approx) {

@@ -41,7 +41,8 @@ template <> struct DotK<DOT_NORM> { static constexpr int K = 1; };
 
 // The reliable updates of a mixed-precision solve by their index k (SysState::updates): k = 0
 // MASK_UPDATE_FIRST, odd k MASK_UPDATE_LATER (full FP64 residual), even k >= 2 MASK_UPDATE_CORR
-// (the previous residual corrected by the iterate's change)
+// (the previous residual corrected by the iterate's change); an update that may end the solve
+// (FLAG_CHECK) is MASK_UPDATE_LATER whatever its index
 enum Mask { MASK_ALL = 0, MASK_ACTIVE = 1, MASK_UPDATE = 2, MASK_INIT = 3, MASK_HARVEST = 4, MASK_CG = 5,
             MASK_CG_CHECK = 6, MASK_HPE = 7, MASK_UPDATE_FIRST = 8, MASK_UPDATE_LATER = 9,
             MASK_UPDATE_CORR = 10 };
@@ -55,7 +56,9 @@ __device__ __forceinline__ bool selected(const SysState* st, int sys, int mask) 
   if (mask == MASK_UPDATE_FIRST || mask == MASK_UPDATE_LATER || mask == MASK_UPDATE_CORR) {
     if (!(s == SYS_ACTIVE && (f & FLAG_UPDATE) && !(f & FLAG_CG))) return false;
     const int k = st[sys].updates;
-    return mask == MASK_UPDATE_FIRST ? k == 0 : (mask == MASK_UPDATE_LATER ? (k & 1) != 0 : k >= 2 && !(k & 1));
+    const bool check = (f & FLAG_CHECK) != 0;  // a possible last update: always full FP64
+    if (mask == MASK_UPDATE_LATER) return (k & 1) != 0 || check;
+    return !check && (mask == MASK_UPDATE_FIRST ? k == 0 : k >= 2 && !(k & 1));
   }
   // CGNR fallback systems, and those of them due a true-residual check
   if (mask == MASK_CG) return s == SYS_ACTIVE && (f & FLAG_CG);
