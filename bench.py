@@ -619,7 +619,7 @@ def main():
         step(job0 + k)
     torch.cuda.synchronize()
 
-    # ---- device-resident timed region (the library's own launch shape: two lanes by default)
+    # ---- device-resident timed region (the library's own launch shape: three lanes by default)
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     barrier(ws)
@@ -665,7 +665,7 @@ def main():
                "d2h_bytes_per_step": d2h}
 
     # ---- roofline pass: the same step on one lane, every hop launch timed with CUDA events on
-    # its stream (with two lanes a launch shares the GPU with the other lane's kernels, and its
+    # its stream (with several lanes a launch shares the GPU with the other lanes' kernels, and its
     # duration would measure that sharing rather than the kernel)
     ctx.profile_enable(True)
     for k in range(args.roof_steps):

@@ -90,9 +90,10 @@ typedef struct fs_solve_params {
                           M^dag M x = M^dag b, M^dag = gamma5 M gamma5, for at most this many
                           iterations; 0 = 4 * max_iter, < 0 = no fallback                     */
   int lanes;           /* mlmc_level_trace only: tiles solved at the same time, each on a stream
-                          and host thread of its own (1..4); 0 = library choice: 2 when the
-                          job has at least two tiles of systems, else 1. A system's result does
-                          not depend on its lane. Every lane holds a tile of device memory. */
+                          and host thread of its own (1..4); 0 = library choice: as many tiles
+                          as the job fills, at most 3. A system's result does not depend on its
+                          lane. Every lane holds a tile of device memory; a lane whose tile does
+                          not fit is dropped and its share goes to the others. */
 } fs_solve_params;
 
 typedef struct fs_sys_stats {

@@ -170,6 +170,17 @@ fs::TileBase* tile_for(Ctx& c, const std::vector<fs::QJob>& jobs, const Opts& o)
 // use the rest of the GPU. Jobs go to the lanes two at a time in turn, so every lane gets the
 // same mix of shifts. Shared inputs (gauge copies, contraction paths) must exist beforehand.
 int run_lanes(Ctx& c, const std::vector<fs::QJob>& jobs, const Opts& o, const fs::QOut& out, int nl, bool canon) {
+  // every lane needs a tile: lanes beyond the first whose tile does not fit in device memory are
+  // dropped (the jobs go to the others), so more lanes than memory allows never fail a call
+  for (int l = 1; l < nl; l++) {
+    Ctx* ln = c.lane(l);
+    if (!ln) return FS_ERR_CUDA;
+    if (!tile_for(*ln, jobs, o)) {
+      cudaGetLastError();
+      nl = l;
+      break;
+    }
+  }
   std::vector<std::vector<fs::QJob>> part(nl);
   for (size_t i = 0; i < jobs.size(); i++) part[(i / 2) % nl].push_back(jobs[i]);
   cudaEvent_t ev;
@@ -189,7 +200,7 @@ int run_lanes(Ctx& c, const std::vector<fs::QJob>& jobs, const Opts& o, const fs
     if (c.prof.enabled && !L[l]->prof.enabled)
       if (prof_reset(*L[l], true)) return c.fail(FS_ERR_CUDA, L[l]->err);
     if ((e = cudaStreamWaitEvent(L[l]->stream, ev, 0))) return c.cuda_fail(e, "lane start");
-    if (!(T[l] = tile_for(*L[l], part[l], o)))
+    if (!(T[l] = tile_for(*L[l], jobs, o)))  // the tile the check above allocated
       return c.fail(FS_ERR_OOM, "device allocation of a lane's solver tile failed");
     if (canon && L[l]->ensure_canon(T[l]->N)) return c.fail(FS_ERR_OOM, L[l]->err);
   }
@@ -640,8 +651,9 @@ int mlmc_impl(Ctx& c, const fs_mlmc_params* P, const int* p_in, int np, double* 
       }
     }
   }
-  // two tiles at once when the job fills both (lanes = 0); a system's result is the same
-  const int nl = o.lanes > 0 ? o.lanes : (nsolve >= 2 * o.tile ? 2 : 1);
+  // several tiles at once when the job fills them (lanes = 0: three, as many as the job fills);
+  // a system's result is the same in any lane
+  const int nl = o.lanes > 0 ? o.lanes : std::max(1, std::min(3, nsolve / std::max(1, o.tile)));
   fs::TileBase* T = nullptr;
   if (nl == 1) {
     T = tile_for(c, jobs, o);
