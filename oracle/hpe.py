@@ -76,21 +76,6 @@ def exact_part_probed(u, m, sigma, gamma, p, K, dims, colors, ncolors, bc_t=-1):
     return complex(t)
 
 
-def hpe_samples(u, m, sigma, gamma, p, K, n_samples, seed, job, level, dims, t_exact, bc_t=-1, solver=None):
-    """Samples T_exact + z_s^dag Gamma Omega_p (kappa H)^K (D + sigma)^-1 z_s for the Z4 vectors
-    (seed, job, level, s), s < n_samples."""
-    from . import estimators as est
-    from . import philox
-    v = int(np.prod(dims))
-    if solver is None:
-        solver = est.make_solver(u, m, dims, bc_t)
-    out = []
-    for s in range(n_samples):
-        z = philox.z4_noise(v, seed, job, level, s)
-        out.append(t_exact + stochastic_part(u, solver, z, m, sigma, gamma, p, K, dims, bc_t))
-    return np.array(out, dtype=np.complex128)
-
-
 def remainder_matrix(u, m, sigma, gamma, p, K, dims, bc_t=-1):
     """Dense Gamma Omega_p (kappa H)^K (D + sigma)^-1 (its Z4 variance is the HPE estimator's)."""
     A = 4.0 + m + sigma
