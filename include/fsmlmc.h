@@ -41,6 +41,13 @@
 #include <stddef.h>
 #include <stdint.h>
 
+/* Only the functions declared here are exported from the shared library. */
+#if defined(__GNUC__)
+#define FS_API __attribute__((visibility("default")))
+#else
+#define FS_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -141,40 +148,40 @@ typedef struct fs_mlmc_params {
 
 /* Create a context for a lattice on CUDA device `device`. bc_t = -1 (antiperiodic in t)
  * or +1 (periodic). FS_ERR_ARG for odd or non-positive dims or V >= 2^31 / 24. */
-int fs_ctx_create(fs_ctx** ctx, const int dims[4], int bc_t, int device);
-void fs_ctx_destroy(fs_ctx* ctx);
+FS_API int fs_ctx_create(fs_ctx** ctx, const int dims[4], int bc_t, int device);
+FS_API void fs_ctx_destroy(fs_ctx* ctx);
 /* Message of the last error on ctx ("" if none); valid until the next call on ctx. */
-const char* fs_last_error(const fs_ctx* ctx);
+FS_API const char* fs_last_error(const fs_ctx* ctx);
 /* Issue all work of ctx on `stream` (a cudaStream_t; NULL restores the context's own). */
-int fs_set_stream(fs_ctx* ctx, void* stream);
+FS_API int fs_set_stream(fs_ctx* ctx, void* stream);
 /* Device memory currently held by ctx, in bytes. */
-size_t fs_ctx_device_bytes(const fs_ctx* ctx);
+FS_API size_t fs_ctx_device_bytes(const fs_ctx* ctx);
 
 /* The tile size the autotuner chose for storage precision `prec` and `link_compress` on this
    context, or 0 if it has not run. A library addition (the paper has no counterpart): when a
    call leaves fs_solve_params.rhs_tile = 0 and has at least 16 systems, the first such call
    per precision and link format times a BiCGStab iteration per system on tiles of 8, 16, 32
    and 64 systems (at most the call's system count) and keeps the fastest for the context. */
-int fs_tuned_tile(const fs_ctx* ctx, int prec, int link_compress);
+FS_API int fs_tuned_tile(const fs_ctx* ctx, int prec, int link_compress);
 
 /* Upload the gauge field U (host, [4][V][3][3][2] doubles). Builds the FP64 copy used
  * for true residuals and contractions and the lower-precision copies on demand.
  * FS_ERR_INPUT if U holds a non-finite value. */
-int fs_set_gauge(fs_ctx* ctx, const double* U);
+FS_API int fs_set_gauge(fs_ctx* ctx, const double* U);
 
 /* ---- the operations of the paper -------------------------------------------------- */
 
 /* out_k = (D + sigma I) in_k for k < nrhs, full lattice (the operator of
  * Eq. (shifted_linear_systems)). in/out: host [nrhs][V][4][3][2]. prec selects the
  * storage precision of the device vectors (F64 computes in FP64, others in FP32). */
-int wilson_dslash(fs_ctx* ctx, double m, double sigma, const double* in, double* out, int nrhs,
+FS_API int wilson_dslash(fs_ctx* ctx, double m, double sigma, const double* in, double* out, int nrhs,
                   int prec, int link_compress);
 
 /* Solve (D + sigma_j I) x_{j,k} = b_k, Eq. (shifted_linear_systems), for every shift j < nshift
  * and right-hand side k < nrhs, with even-odd preconditioned BiCGStab batched over systems.
  * b: host [nrhs][V][24]; x: host [nshift][nrhs][V][24]; stats (optional): [nshift][nrhs].
  * Returns FS_ERR_NOCONV if any system stopped at max_iter (x and stats still written). */
-int shifted_solve(fs_ctx* ctx, double m, const double* sigma, int nshift, const double* b, int nrhs,
+FS_API int shifted_solve(fs_ctx* ctx, double m, const double* sigma, int nshift, const double* b, int nrhs,
                   double* x, const fs_solve_params* params, fs_sys_stats* stats);
 
 /* shifted_solve on caller-owned device arrays (e.g. torch tensors): b device [nrhs][V][24],
@@ -183,7 +190,7 @@ int shifted_solve(fs_ctx* ctx, double m, const double* sigma, int nshift, const 
  * the context's stream (fs_set_stream) and the call returns when x is written. b is read in
  * place and not checked for non-finite values (they surface as FS_ERR_NOCONV). Same arithmetic
  * as shifted_solve: the solutions are identical. */
-int shifted_solve_dev(fs_ctx* ctx, double m, const double* sigma, int nshift, const double* b, int nrhs,
+FS_API int shifted_solve_dev(fs_ctx* ctx, double m, const double* sigma, int nshift, const double* b, int nrhs,
                       double* x, const fs_solve_params* params, fs_sys_stats* stats);
 
 /* FS-MLMC trace estimate, Eq. (fs_trace_est): for every level l < nlev, N_l Z4 noise
@@ -195,7 +202,7 @@ int shifted_solve_dev(fs_ctx* ctx, double m, const double* sigma, int nshift, co
  *   stats   [number of solves] (optional), in the order the solves are listed in
  *           fs_mlmc_num_solves' documentation.
  * The total trace is sum_l T_l and V_FS = sum_l V_l / N_l (Eq. (total_var)). */
-int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* params, double* trace, double* var,
+FS_API int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* params, double* trace, double* var,
                      double* samples, fs_sys_stats* stats);
 
 /* mlmc_level_trace for several displacements at once: the traces for p[0..np) (distinct, each
@@ -203,7 +210,7 @@ int mlmc_level_trace(fs_ctx* ctx, const fs_mlmc_params* params, double* trace, d
  * inversions for all displacements (Sec. 4); the contraction forms them in one pass. Outputs in
  * the order of p: trace [np][nlev][2], var [np][nlev], samples (optional) [np][sum N_l][2];
  * stats as mlmc_level_trace. With hpe_order every p needs p < Lz and gets its own exact part. */
-int mlmc_level_traces(fs_ctx* ctx, const fs_mlmc_params* params, const int* p, int np, double* trace,
+FS_API int mlmc_level_traces(fs_ctx* ctx, const fs_mlmc_params* params, const int* p, int np, double* trace,
                       double* var, double* samples, fs_sys_stats* stats);
 
 /* Number of shifted solves mlmc_level_trace performs: per level l < L two solves per
@@ -212,7 +219,7 @@ int mlmc_level_traces(fs_ctx* ctx, const fs_mlmc_params* params, const int* p, i
  * L; a sample has ncolors * (dilute ? 12 : 1) pieces when probing (1 without), so the count
  * is the paper's 12 c m N_s for one shift and full dilution. Solves are listed level-major,
  * then by sample, then by piece. -1 if the count exceeds 2^31 - 1 or params is invalid. */
-int fs_mlmc_num_solves(const fs_mlmc_params* params);
+FS_API int fs_mlmc_num_solves(const fs_mlmc_params* params);
 
 /* Exact low orders of the hopping parameter expansion (Sec. 3.1, the remark after
  * Eq. (sampled_single)): out = {re, im} of T = sum_{k<K} Tr(Gamma Omega_p (kappa H)^k) / A,
@@ -222,7 +229,7 @@ int fs_mlmc_num_solves(const fs_mlmc_params* params);
  * depend on it), K - 1 kappa H applications each, one contraction per order. The value
  * mlmc_level_trace adds to every last-level sample with hpe_order = K. params: rhs_tile (0 = 64
  * pieces at a time); the other fields are unused. K in 1..8, 0 <= p < Lz, else FS_ERR_ARG. */
-int fs_hpe_exact_trace(fs_ctx* ctx, double m, double sigma, const double* gamma, int p, int K, uint64_t seed,
+FS_API int fs_hpe_exact_trace(fs_ctx* ctx, double m, double sigma, const double* gamma, int p, int K, uint64_t seed,
                        const fs_solve_params* params, double* out);
 
 /* Greedy probing colours (Sec. 2.1): a distance-k colouring of the lattice graph of D (the
@@ -237,7 +244,7 @@ int fs_hpe_exact_trace(fs_ctx* ctx, double m, double sigma, const double* gamma,
  *   ncolors  out: the number of colours c
  * FS_ERR_ARG for a null pointer or an argument out of range, FS_ERR_OOM if host memory runs
  * out. */
-int fs_probing_colors(const int dims[4], int k, int p, int32_t* colors, int* ncolors);
+FS_API int fs_probing_colors(const int dims[4], int k, int p, int32_t* colors, int* ncolors);
 
 /* Variance sampling, Sec. 3.1 algorithm, for the m_shifts sampling shifts s_hat
  * (s_hat_0 < ... ) and every displacement p[k], k < np, with Ns Z4 noise vectors
@@ -249,7 +256,7 @@ int fs_probing_colors(const int dims[4], int k, int p, int32_t* colors, int* nco
  *   VL [np][m_shifts], Vbar [np][m_shifts][m_shifts] (entries j < i set to 0),
  *   a (optional) [Ns][np][m_shifts][2], b (optional) [Ns][np][m_shifts][m_shifts][2],
  *   iters (optional) [m_shifts] mean BiCGStab iterations of the solves at each shift. */
-int variance_sample(fs_ctx* ctx, double m, const double* s_hat, int m_shifts, const double* gamma,
+FS_API int variance_sample(fs_ctx* ctx, double m, const double* s_hat, int m_shifts, const double* gamma,
                     const int* p, int np, int Ns, uint64_t seed, uint32_t job,
                     const fs_solve_params* params, double* VL, double* Vbar, double* a, double* b,
                     double* iters);
@@ -266,14 +273,14 @@ int variance_sample(fs_ctx* ctx, double m, const double* s_hat, int m_shifts, co
  * so VL is the variance of the expanded estimator; its exact low orders shift every sample
  * alike and are not added (Sec. 3.1: not needed for the sampling). b_ij is unchanged.
  * Outputs and errors as variance_sample; iters averages every solve at the shift. */
-int variance_sample_probed(fs_ctx* ctx, double m, const double* s_hat, int m_shifts, const double* gamma,
+FS_API int variance_sample_probed(fs_ctx* ctx, double m, const double* s_hat, int m_shifts, const double* gamma,
                            const int* p, int np, int Ns, uint64_t seed, uint32_t job,
                            const fs_solve_params* params, const int32_t* colors, int ncolors, int dilute,
                            int hpe_order, double* VL, double* Vbar, double* a, double* b, double* iters);
 
 /* The Z4 noise vector (seed, job, level, sample) as integer codes k (z = i^k),
  * host [V][4][3] bytes, generated on the device (bit-exact RNG checks). */
-int fs_noise_codes(fs_ctx* ctx, uint64_t seed, uint32_t job, uint32_t level, uint32_t sample,
+FS_API int fs_noise_codes(fs_ctx* ctx, uint64_t seed, uint32_t job, uint32_t level, uint32_t sample,
                    uint8_t* codes);
 
 /* Sum over all calls since the last reset of the device time of the hopping (dslash)
@@ -281,8 +288,8 @@ int fs_noise_codes(fs_ctx* ctx, uint64_t seed, uint32_t job, uint32_t level, uin
  * they moved, and the (site, system) pairs they computed (1320 flop each). Timing is
  * recorded only while enabled (CUDA events around each launch on the context's stream).
  * Any output pointer may be NULL. */
-int fs_profile_enable(fs_ctx* ctx, int enable);
-int fs_profile_read(fs_ctx* ctx, long long* launches, double* total_ms, double* bytes, double* site_systems);
+FS_API int fs_profile_enable(fs_ctx* ctx, int enable);
+FS_API int fs_profile_read(fs_ctx* ctx, long long* launches, double* total_ms, double* bytes, double* site_systems);
 
 /* ---- serving ---------------------------------------------------------------------
  * A server on one GPU runs FS-MLMC trace jobs (one mlmc_level_trace each) as they arrive.
@@ -325,26 +332,26 @@ typedef struct fs_server_report {
 } fs_server_report;
 
 /* FS_ERR_ARG for max_active outside [1, 64] or a zero budget. */
-int fs_server_create(fs_server** server, int device, size_t hbm_budget_bytes, int max_active);
+FS_API int fs_server_create(fs_server** server, int device, size_t hbm_budget_bytes, int max_active);
 /* Queue a job; FS_ERR_BUDGET if its estimate alone exceeds the budget, FS_ERR_ARG for bad
  * dims or more than FS_JOB_MAX_LEVELS levels. */
-int fs_server_submit(fs_server* server, const fs_job* job, uint64_t* ticket);
+FS_API int fs_server_submit(fs_server* server, const fs_job* job, uint64_t* ticket);
 /* Wait up to timeout_ms (< 0: forever) for a job; FS_ERR_TIMEOUT if it is not done yet.
  * A result is returned once, then the ticket is forgotten. */
-int fs_server_poll(fs_server* server, uint64_t ticket, fs_job_result* result, int timeout_ms);
-int fs_server_stats(fs_server* server, fs_server_report* stats);
+FS_API int fs_server_poll(fs_server* server, uint64_t ticket, fs_job_result* result, int timeout_ms);
+FS_API int fs_server_stats(fs_server* server, fs_server_report* stats);
 /* Admission order (a library addition; the paper has no server). least_work_first = 1 (the
  * default): among the queued jobs whose memory estimate fits the budget, the one with the least
  * work (solves x lattice sites) starts first, which shortens the median latency; a job queued for
  * max_wait_ms (default 10000) goes next regardless and no later job passes it, so no job waits
  * for ever. least_work_first = 0: first in, first out. FS_ERR_ARG for other values or a negative
  * wait. */
-int fs_server_set_admission(fs_server* server, int least_work_first, double max_wait_ms);
+FS_API int fs_server_set_admission(fs_server* server, int least_work_first, double max_wait_ms);
 /* Finishes queued and running jobs, then stops the workers. */
-void fs_server_destroy(fs_server* server);
+FS_API void fs_server_destroy(fs_server* server);
 
 /* Number of CUDA kernels this library has launched in the process (all contexts). */
-long long fs_kernel_launches(void);
+FS_API long long fs_kernel_launches(void);
 
 /* ---- allocation-free variant ------------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that may not
@@ -364,7 +371,7 @@ long long fs_kernel_launches(void);
  * are queued. All calls on a device share the array, so calls whose work overlaps on
  * the GPU (unordered streams) race and corrupt each other; each call rewrites every
  * scratch field it reads, so the contents left by the previous call do not matter. */
-int wilson_dslash_noalloc(const int dims[4], int bc_t, double m, double sigma, const double* U,
+FS_API int wilson_dslash_noalloc(const int dims[4], int bc_t, double m, double sigma, const double* U,
                           const double* in, double* out, int nrhs, void* stream);
 
 /* ---- shift selection and sample allocation (host only; paper Sec. 3.2-3.3) --------------
@@ -380,7 +387,7 @@ int wilson_dslash_noalloc(const int dims[4], int bc_t, double m, double sigma, c
  * interpolating polynomials (linear through two points): VL[k] = V_L(s_k) and
  * Vl[i*n + k] = V_l(s_i, s_k) = (s_k - s_i)^2 Vbar_l(s_i, s_k) for k > i (NaN for k <= i or
  * where no prediction exists), from the three-stage 2-D interpolation of Sec. 3.2. */
-int fs_interp_variances(const double* s_hat, int m, const double* VL_hat, const double* Vbar_hat,
+FS_API int fs_interp_variances(const double* s_hat, int m, const double* VL_hat, const double* Vbar_hat,
                         const double* s, int n, double* VL /*[n]*/, double* Vl /*[n*n]*/);
 
 /* Eq. (opt_shifts): the L shifts after sigma_0 = s_0 that minimise the multilevel cost
@@ -390,7 +397,7 @@ int fs_interp_variances(const double* s_hat, int m, const double* VL_hat, const 
  * C_l = r(sigma_l) + r(sigma_{l+1}) for l < L, C_L = r(sigma_L). Outputs idx[L+1] (indices
  * into s, idx[0] = 0), V[L+1], C[L+1] and F. FS_ERR_ARG also for L outside [1, n-1] or when
  * no choice of L shifts has predicted variances. */
-int fs_select_shifts(const double* s_hat, int m, const double* VL_hat, const double* Vbar_hat,
+FS_API int fs_select_shifts(const double* s_hat, int m, const double* VL_hat, const double* Vbar_hat,
                      const double* iters_hat, const double* s, int n, int L, int* idx, double* V, double* C,
                      double* F);
 
@@ -398,13 +405,13 @@ int fs_select_shifts(const double* s_hat, int m, const double* VL_hat, const dou
  * (real-valued; round up for use), and V_FS = sum_l V_l / N_l (= eps2), C_FS = sum_l N_l C_l.
  * mu, V_FS, C_FS may be NULL. FS_ERR_ARG for eps2 <= 0 or nlev < 1; FS_ERR_INPUT for V < 0,
  * C <= 0 or non-finite values. */
-int fs_sample_allocation(const double* V, const double* C, int nlev, double eps2, double* N, double* mu,
+FS_API int fs_sample_allocation(const double* V, const double* C, int nlev, double eps2, double* N, double* mu,
                          double* V_FS, double* C_FS);
 
 /* The paper's evaluation set (Sec. 3.3): logspace(-5,-2,4) and logspace(log10(0.011),0,76)
  * from s_hat[0] up, with the sampling shifts added, sorted and unique (with s_hat[0] = 0 it
  * starts at 0). With s = NULL only *n is set; otherwise cap must be >= *n. */
-int fs_eval_grid(const double* s_hat, int m, double* s, int cap, int* n);
+FS_API int fs_eval_grid(const double* s_hat, int m, double* s, int cap, int* n);
 
 #ifdef __cplusplus
 }

@@ -514,7 +514,7 @@ static int check_colors(Ctx& c, const int32_t* colors, int ncolors) {
 }
 
 // Pieces of one sample: probing colours times spin-colour components (Sec. 2.1, Sec. 3.1).
-int num_pieces(const fs_mlmc_params* p) {
+static int num_pieces(const fs_mlmc_params* p) {
   if (p->dilute != 0 && p->dilute != 1) return -1;
   if (p->colors && (p->ncolors < 1 || p->ncolors > (1 << 26))) return -1;
   return (p->colors ? p->ncolors : 1) * (p->dilute ? 12 : 1);
