@@ -552,7 +552,7 @@ def run_pipeline_paper_noise(pkg, ctx, w, kw, levels=4, n_s=5, n_max=4, seed=930
 
 
 # --------------------------------------------------------------------------- GPU arm
-def main():
+def build_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -576,6 +576,11 @@ def main():
                     help="skip the probed and spin-colour diluted level traces (p4k4 colours)")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="skip the end-to-end run of variance sampling, shift selection and allocation")
+    return ap
+
+
+def main():
+    ap = build_parser()
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
