@@ -177,3 +177,22 @@ def test_probed_variance_sample_without_pieces_is_the_plain_algorithm():
     b = oest.variance_sample(u, -0.25, [0.05, 0.3], gam, [1], 3, 5, 1, dims, -1, solver)
     for key in ("a", "b", "VL", "Vbar"):
         assert np.allclose(a[key], b[key], rtol=1e-13, atol=1e-13), key
+
+
+def test_dilution_gives_the_adjoint_solution_without_a_solve():
+    """Sec. 3.1: with full spin-colour dilution a piece z lives on one spin s, so gamma_5 z = eps z
+    (eps = +1 for s < 2, -1 otherwise) and y = (D + s)^-dag z = gamma_5 (D + s)^-1 gamma_5 z equals
+    eps gamma_5 x, x = (D + s)^-1 z: the identity the library's diluted variance sampling uses
+    instead of a second solve, checked here against the adjoint solve taken as written."""
+    dims = (2, 2, 4, 2)
+    v = int(np.prod(dims))
+    u = inputs.gauge_field(dims, "haar", seed=86)
+    solver = oest.make_dense_solver(u, -0.3, dims)
+    color, nc = opr.greedy_coloring(dims, 1, 0)
+    for comp in (0, 4, 7, 11):
+        z = opr.probed_noise(v, 3, 0, 0, 1, color, 1, comp)
+        eps = 1.0 if comp // 3 < 2 else -1.0
+        y = oest.adjoint_solution(solver, z, 0.2)
+        x = solver(z, 0.2)
+        g5x = x * np.array([1, 1, -1, -1])[None, :, None]
+        assert np.allclose(y, eps * g5x, rtol=1e-12, atol=1e-13), comp
