@@ -824,30 +824,150 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pf(HopArgs a) {
 
 namespace fs {
 
-// ---- persistent, cross-chunk pipelined variant (32 systems per warp) -------------
-// A warp holds one site and the 32 systems of a system chunk (lane = system); a
-// block holds the 8 sites of one site chunk, i.e. one 8-site dot group. The grid
-// is persistent (resident blocks x SMs) and each block sweeps the site chunks
-// blockIdx.x, blockIdx.x + gridDim.x, ... Every thread streams its operands,
-// item n = j NITEM + i (chunk j, operand i: the 8 neighbour spinors, then X and R),
-// through a ring of PF shared-memory slots, PF items ahead of the arithmetic and
-// across chunk boundaries, so the copies of the next site overlap the arithmetic
-// of the current one. The raw links of a chunk travel with its item 0 (lanes 0-7,
-// one direction each); lane d then reconstructs link d once for the warp, folding
-// in the antiperiodic t phase, and the 32 lanes read it from shared memory.
-// Neighbour indices are computed lane-parallel (lane d: direction d & 7) and
-// broadcast with a shuffle when an item is issued.
-template <typename Tg>
-__host__ __device__ constexpr int link_chunks16(int nr) {
-  return link_pad<Tg>(nr) * (int)sizeof(Tg) / 16;
+// ---- persistent paired variant: two systems per thread in packed FP32 arithmetic -----
+// A 32-system tile chunk at one site is held by 16 lanes: lane q computes systems q and
+// q + 16 in the two halves of packed FP32 instructions (fma/add/mul .f32x2: one issue slot
+// for two systems, each half rounded exactly as the scalar instruction), so every system
+// goes through the same sequence of roundings as in the scalar hop kernels. A warp holds
+// two sites, a 128-thread block the 8 sites of one 8-site dot group, and the persistent
+// grid (resident blocks x SMs) sweeps the site chunks blockIdx.x, blockIdx.x + gridDim.x, ...
+//
+// Operands stream through a per-thread ring of PF shared-memory slots (cp.async, 16 B per
+// copy), item n = j NITEM + i of chunk j (the 8 neighbour spinors, then X and R), PF items
+// ahead of the arithmetic and across chunk boundaries. The raw links of a chunk travel with
+// its item 0; lane d < 8 of each half-warp rebuilds link d of its site once and stores it as
+// (s u_r, u_i) per entry, s = -1 for the forward links, with the t boundary phase folded in.
+// The forward hop therefore forms -U h directly and the backward chain starts from it; the
+// packed operands (s u_r, s u_r), (u_i, u_i) and (-u_i, -u_i) are formed in registers
+// (measured faster than storing them pre-paired: half the shared-memory link reads).
+namespace pk {
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// -a (a sign flip, which the packed instructions take as an operand modifier) and a - b
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+
+constexpr int LINK_PK = 18;              // floats per link: 9 entries (s u_r, u_i)
+constexpr int SITE_PK = 8 * LINK_PK + 4;  // per site; the 4 pad floats put the two sites of a
+                                          // warp on different banks
+
+// nxf = -U h_f, the forward hop's upper-spin product negated (links stored with s = -1): row
+// by row, both spin halves together (four independent chains), in su3_mul's multiply-add order.
+__device__ __forceinline__ void fwd_pk(float2 (&nxf)[12], const float2 (&h)[12], const float* L) {
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    float2 r0, i0, r1, i1;
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      const float2 w = *reinterpret_cast<const float2*>(L + 2 * (a * 3 + b));
+      const float2 ur = make_float2(w.x, w.x), up = make_float2(w.y, w.y), um = make_float2(-w.y, -w.y);
+      if (b == 0) {
+        r0 = mul2(ur, h[0]); i0 = mul2(ur, h[1]); r1 = mul2(ur, h[6]); i1 = mul2(ur, h[7]);
+      } else {
+        r0 = fma2(ur, h[2 * b], r0); i0 = fma2(ur, h[2 * b + 1], i0);
+        r1 = fma2(ur, h[6 + 2 * b], r1); i1 = fma2(ur, h[6 + 2 * b + 1], i1);
+      }
+      r0 = fma2(up, h[2 * b + 1], r0); i0 = fma2(um, h[2 * b], i0);
+      r1 = fma2(up, h[6 + 2 * b + 1], r1); i1 = fma2(um, h[6 + 2 * b], i1);
+    }
+    nxf[2 * a] = r0; nxf[2 * a + 1] = i0; nxf[6 + 2 * a] = r1; nxf[6 + 2 * a + 1] = i1;
+  }
+}
+
+// Backward hop of direction MU (bwd_core, packed): row c of z = U^dag h_b - xf for both spin
+// halves (the chains of su3_mul_sub, started from nxf = -xf), then at once
+//   upper spins += 2 xf + z,   lower spins += G^dag z.
+template <int MU>
+__device__ __forceinline__ void bwd_pk(float2 (&acc)[24], const float2 (&nxf)[12], const float2 (&h)[12],
+                                       const float* L) {
+  const float2 m2 = make_float2(-2.f, -2.f);
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    float2 z0r, z0i, z1r, z1i;
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      const float2 w = *reinterpret_cast<const float2*>(L + 2 * (b * 3 + c));
+      const float2 ur = make_float2(w.x, w.x), up = make_float2(w.y, w.y), um = make_float2(-w.y, -w.y);
+      if (b == 0) {
+        z0r = fma2(ur, h[0], nxf[2 * c]); z0i = fma2(ur, h[1], nxf[2 * c + 1]);
+        z1r = fma2(ur, h[6], nxf[6 + 2 * c]); z1i = fma2(ur, h[7], nxf[6 + 2 * c + 1]);
+      } else {
+        z0r = fma2(ur, h[2 * b], z0r); z0i = fma2(ur, h[2 * b + 1], z0i);
+        z1r = fma2(ur, h[6 + 2 * b], z1r); z1i = fma2(ur, h[6 + 2 * b + 1], z1i);
+      }
+      z0r = fma2(up, h[2 * b + 1], z0r); z0i = fma2(um, h[2 * b], z0i);
+      z1r = fma2(up, h[6 + 2 * b + 1], z1r); z1i = fma2(um, h[6 + 2 * b], z1i);
+    }
+    acc[2 * c] = add2(fma2(m2, nxf[2 * c], acc[2 * c]), z0r);
+    acc[2 * c + 1] = add2(fma2(m2, nxf[2 * c + 1], acc[2 * c + 1]), z0i);
+    acc[6 + 2 * c] = add2(fma2(m2, nxf[6 + 2 * c], acc[6 + 2 * c]), z1r);
+    acc[6 + 2 * c + 1] = add2(fma2(m2, nxf[6 + 2 * c + 1], acc[6 + 2 * c + 1]), z1i);
+    float2& a0r = acc[12 + 2 * c];
+    float2& a0i = acc[12 + 2 * c + 1];
+    float2& a1r = acc[18 + 2 * c];
+    float2& a1i = acc[18 + 2 * c + 1];
+    if (MU == 0) {         // G1^dag = [[0, -i], [-i, 0]]
+      a0r = add2(a0r, z1i); a0i = sub2(a0i, z1r); a1r = add2(a1r, z0i); a1i = sub2(a1i, z0r);
+    } else if (MU == 1) {  // G2^dag = [[0, 1], [-1, 0]]
+      a0r = add2(a0r, z1r); a0i = add2(a0i, z1i); a1r = sub2(a1r, z0r); a1i = sub2(a1i, z0i);
+    } else if (MU == 2) {  // G3^dag = diag(-i, i)
+      a0r = add2(a0r, z0i); a0i = sub2(a0i, z0r); a1r = sub2(a1r, z1i); a1i = add2(a1i, z1r);
+    } else {
+      a0r = add2(a0r, z0r); a0i = add2(a0i, z0i); a1r = add2(a1r, z1r); a1i = add2(a1i, z1i);
+    }
+  }
+}
+
+// Spin projection of both systems (scalar: the destination registers of the two halves are
+// free, so the pairs cost no moves). FP16 input takes the mixed-precision adds of project_h.
+template <int MU, int S, typename Ts, int CV>
+__device__ __forceinline__ void project_pk(const uint4 (&wa)[CV], const uint4 (&wb)[CV], float2 (&h)[12]) {
+  float ha[12], hb[12];
+  if constexpr (std::is_same<Ts, __half>::value) {
+    unsigned short pa[24], pb[24];
+#pragma unroll
+    for (int c = 0; c < CV; c++) {
+      const unsigned short* qa = reinterpret_cast<const unsigned short*>(&wa[c]);
+      const unsigned short* qb = reinterpret_cast<const unsigned short*>(&wb[c]);
+#pragma unroll
+      for (int e = 0; e < 8; e++) { pa[c * 8 + e] = qa[e]; pb[c * 8 + e] = qb[e]; }
+    }
+    project_h<MU, S>(pa, ha);
+    project_h<MU, S>(pb, hb);
+  } else {
+    constexpr int VW = Store<Ts>::VW;
+    float psa[24], psb[24];
+#pragma unroll
+    for (int c = 0; c < CV; c++) {
+      load_vec<Ts, float>(reinterpret_cast<const Ts*>(&wa[c]), psa + c * VW);
+      load_vec<Ts, float>(reinterpret_cast<const Ts*>(&wb[c]), psb + c * VW);
+    }
+    project<MU, S>(psa, ha);
+    project<MU, S>(psb, hb);
+  }
+#pragma unroll
+  for (int k = 0; k < 12; k++) h[k] = make_float2(ha[k], hb[k]);
+}
+}  // namespace pk
+
+template <typename Ts, int PF, int K>
+__host__ __device__ constexpr size_t hop_pk_smem() {
+  // ring [PF][CV][2 systems][128 threads] x 16 B
+  return (size_t)PF * chunks16<Ts>() * 2 * 128 * 16;
 }
 
 template <bool COND> struct BoolC { static constexpr bool value = COND; };
 template <int I> struct IntC { static constexpr int value = I; };
 
-template <typename Ts, typename Tg, typename Tm, int NR, int COEF, int DOT, int PF>
-__global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
-  static_assert(!std::is_same<Tm, double>::value, "the pipelined hop kernel computes in FP32");
+template <typename Tg>
+__host__ __device__ constexpr int link_chunks16(int nr) {
+  return link_pad<Tg>(nr) * (int)sizeof(Tg) / 16;
+}
+
+template <typename Ts, typename Tg, int NR, int COEF, int DOT, int PF>
+__global__ void __launch_bounds__(128, 3) hop_kernel_pk(HopArgs a) {
+  using namespace pk;
   constexpr int K = DotK<DOT>::K;
   constexpr int KK = K > 0 ? K : 1;
   constexpr int CV = chunks16<Ts>();
@@ -855,42 +975,44 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
   constexpr bool HAS_X = COEF != COEF_PLAIN;
   constexpr bool HAS_R = DOT == DOT_R || DOT == DOT_TS;
   constexpr int NITEM = 8 + (HAS_X ? 1 : 0) + (HAS_R ? 1 : 0);
-  static_assert(PF >= 1 && PF < NITEM, "ring depth");
+  static_assert(PF >= 1 && PF < NITEM && PF <= 6, "ring depth");
   static_assert(DOT != DOT_TS || (HAS_X && PF >= 2), "DOT_TS consumes X and R together");
   constexpr int RPC = link_chunks16<Tg>(NR);  // 16-byte chunks per stored link
   constexpr int RP = link_pad<Tg>(NR);
   constexpr int GVW = Store<Tg>::VW;
-  extern __shared__ uint4 ring[];             // [PF][CV][256 threads]
-  // dot values of chunk parity j & 1: [site][system]; FP32 sums, so held exactly as float
-  __shared__ float dsm[2][8][32][KK];
-  __shared__ __align__(16) float lsm[8 * 8 * LINK_F32];  // [warp][direction][20]
-  __shared__ uint4 lraw[2 * 8 * 8 * RPC];     // raw links, double buffered by chunk parity
+  extern __shared__ uint4 ring[];             // [PF][CV][2][128]
+  // dot values of chunk parity j & 1: [site][value][system]; FP32 sums, so held exactly as float
+  __shared__ float dsm[2][8][KK][32];
+  __shared__ __align__(16) float lsm[4 * 2 * SITE_PK];   // [warp][half][direction][LINK_PK]
+  __shared__ uint4 lraw[2 * 4 * 2 * 8 * RPC];            // raw links, double buffered by chunk parity
   if (a.gate != nullptr && *a.gate == 0) return;
   const Shape sh = a.sh;
   const Geom g = a.g;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int sys = blockIdx.y * 32 + lane;
-  const bool sel = sys < sh.N && selected(a.st, sys, a.mask);
-  Tm ca = 0, cb = 1;
-  if (sel) {
-    const SysState& s = a.st[sys];
-    if (COEF == COEF_MHAT) { ca = coef<Tm>(s, C_A); cb = coef<Tm>(s, C_MINV4A); }
-    else if (COEF == COEF_DSLASH) { ca = coef<Tm>(s, C_A); cb = (Tm)-0.5; }
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int half = lane >> 4, q = lane & 15;
+  const int ls = 2 * warp + half;              // site of the chunk
+  const int sa = blockIdx.y * 32 + q, sb = sa + 16;
+  const bool sel_a = sa < sh.N && selected(a.st, sa, a.mask);
+  const bool sel_b = sb < sh.N && selected(a.st, sb, a.mask);
+  float2 ca = make_float2(0.f, 0.f), cb = make_float2(1.f, 1.f);
+  if (COEF == COEF_MHAT || COEF == COEF_DSLASH) {
+    if (sel_a) { ca.x = coef<float>(a.st[sa], C_A); cb.x = COEF == COEF_MHAT ? coef<float>(a.st[sa], C_MINV4A) : -0.5f; }
+    if (sel_b) { ca.y = coef<float>(a.st[sb], C_A); cb.y = COEF == COEF_MHAT ? coef<float>(a.st[sb], C_MINV4A) : -0.5f; }
   }
   const size_t cstride = (size_t)g.Vh * sh.N * VW;  // elements between 16-byte chunks c and c+1
   const size_t rowstride = (size_t)sh.N * VW;        // elements between consecutive sites
-  const Ts* in_base = (const Ts*)a.in + (size_t)sys * VW;
+  const Ts* in_a = (const Ts*)a.in + (size_t)sa * VW;
   const int G = gridDim.x;
   const int nmine = (sh.nchunk - (int)blockIdx.x + G - 1) / G;  // chunks of this block (uniform)
   if (a.work != nullptr) {  // profiling: (site, system) pairs computed, one atomic per warp
-    const unsigned m = __ballot_sync(0xffffffffu, sel);
-    if (lane == 0 && m && nmine > 0) atomicAdd(a.work, (unsigned long long)__popc(m) * (unsigned long long)nmine);
+    const int m = __popc(__ballot_sync(0xffffffffu, sel_a)) + __popc(__ballot_sync(0xffffffffu, sel_b));
+    if (lane == 0 && m && nmine > 0) atomicAdd(a.work, (unsigned long long)m * (unsigned long long)nmine);
   }
-  const int dl = lane & 7, mul = dl >> 1;  // the direction this lane computes neighbours for
-  auto site_of = [&](int j) { return ((int)blockIdx.x + j * G) * 8 + warp; };
-  // neighbour of site in direction dl, and the boundary phase of that hop
-  // (unrolled over mu with selects: a lane-dependent array index would put the
-  // geometry in local memory)
+  const int dl = q & 7, mul = dl >> 1;  // the direction this lane computes neighbours for
+  auto site_of = [&](int j) { return ((int)blockIdx.x + j * G) * 8 + ls; };
+  // neighbour of site in direction dl, and the boundary phase of that hop (unrolled over mu
+  // with selects: a lane-dependent array index would put the geometry in local memory)
   auto neighbour = [&](int site, int& nb, float& ph) {
     int x[4];
     cb_coords(g, a.p_out, site, x);
@@ -916,7 +1038,11 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
   if (nmine > 0) neighbour(site_of(0), nbc, phc);
   if (nmine > 1) neighbour(site_of(1), nbn, phn);
 
-  auto slot_of = [&](int j, int i) { return (NITEM % PF == 0) ? (i % PF) : ((j * NITEM + i) % PF); };
+  auto slot_of = [&](int j, int i) {  // compile-time where PF divides the items per chunk
+    if constexpr (NITEM % PF == 0) return i % PF;
+    else return (int)(((unsigned)j * NITEM + i) % PF);
+  };
+  auto ring_at = [&](int slot, int c, int s) -> uint4* { return ring + (((size_t)slot * CV + c) * 2 + s) * 128 + tid; };
   // issue operand I of chunk j (NEXT: j is the chunk after the current one)
   auto issue = [&](auto Ic, auto NEXTc, int j) {
     constexpr int I = decltype(Ic)::value;
@@ -924,27 +1050,31 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
     if (j < nmine) {
       const int nbl = NEXT ? nbn : nbc;
       const int site = site_of(j);
-      if (I == 0 && lane < 8) {
-        // raw link of direction d = lane: U_mu(x) forward, U_mu(x - mu) backward
-        const int ls = (dl & 1) ? nbl : site;
+      if (I == 0 && q < 8) {
+        // raw link of direction d = q: U_mu(x) forward, U_mu(x - mu) backward
+        const int lsite = (dl & 1) ? nbl : site;
         const int par = (dl & 1) ? 1 - a.p_out : a.p_out;
-        const Tg* src = (const Tg*)a.gauge + ((size_t)(par * 4 + mul) * g.Vh + ls) * RP;
-        uint4* dst = lraw + (((j & 1) * 8 + warp) * 8 + dl) * RPC;
+        const Tg* src = (const Tg*)a.gauge + ((size_t)(par * 4 + mul) * g.Vh + lsite) * RP;
+        uint4* dst = lraw + ((((j & 1) * 4 + warp) * 2 + half) * 8 + dl) * RPC;
 #pragma unroll
         for (int c = 0; c < RPC; c++) cp_async16(dst + c, src + c * (16 / sizeof(Tg)));
       }
       const Ts* src;
       if constexpr (I < 8) {
-        const int nbi = __shfl_sync(0xffffffffu, nbl, I);
-        src = in_base + (size_t)nbi * rowstride;
+        const int nbi = __shfl_sync(0xffffffffu, nbl, (lane & 16) | I);
+        src = in_a + (size_t)nbi * rowstride;
       } else {
         const Ts* base = (HAS_X && I == 8) ? (const Ts*)a.X : (const Ts*)a.R;
-        src = base + (size_t)site * rowstride + (size_t)sys * VW;
+        src = base + (size_t)site * rowstride + (size_t)sa * VW;
       }
-      if (sel) {
-        uint4* dst = ring + (size_t)slot_of(j, I) * CV * 256 + threadIdx.x;
+      const int slot = slot_of(j, I);
+      if (sel_a) {
 #pragma unroll
-        for (int c = 0; c < CV; c++) cp_async16(dst + c * 256, src + c * cstride);
+        for (int c = 0; c < CV; c++) cp_async16(ring_at(slot, c, 0), src + c * cstride);
+      }
+      if (sel_b) {
+#pragma unroll
+        for (int c = 0; c < CV; c++) cp_async16(ring_at(slot, c, 1), src + c * cstride + 16 * VW);
       }
     }
     cp_async_commit();  // one group per item (empty when idle) keeps the wait counts uniform
@@ -955,9 +1085,14 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
     if constexpr (N2 < NITEM) issue(IntC<N2>{}, BoolC<false>{}, j);
     else issue(IntC<N2 - NITEM>{}, BoolC<true>{}, j + 1);
   };
-  auto fetch_chunk = [&](int slot, int c, Tm* v) {
-    const uint4 w = ring[((size_t)slot * CV + c) * 256 + threadIdx.x];
-    load_vec<Ts, Tm>(reinterpret_cast<const Ts*>(&w), v);
+  // 16-byte chunk c of both systems' operand in `slot`, converted to FP32 pairs
+  auto fetch_pk = [&](int slot, int c, float2* v) {
+    float xa[VW], xb[VW];
+    const uint4 wa = *ring_at(slot, c, 0), wb = *ring_at(slot, c, 1);
+    load_vec<Ts, float>(reinterpret_cast<const Ts*>(&wa), xa);
+    load_vec<Ts, float>(reinterpret_cast<const Ts*>(&wb), xb);
+#pragma unroll
+    for (int k = 0; k < VW; k++) v[k] = make_float2(xa[k], xb[k]);
   };
 
   // prologue: the first PF operands of chunk 0
@@ -967,62 +1102,44 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
   if constexpr (PF > 3) issue(IntC<3>{}, BoolC<false>{}, 0);
   if constexpr (PF > 4) issue(IntC<4>{}, BoolC<false>{}, 0);
   if constexpr (PF > 5) issue(IntC<5>{}, BoolC<false>{}, 0);
-  static_assert(PF <= 6, "prologue covers at most 6 ring slots");
 
+  const float* wl = lsm + (warp * 2 + half) * SITE_PK;
   for (int j = 0; j < nmine; j++) {
     const int site = site_of(j);
-    Tm acc[24], xf[12];
+    float2 acc[24], nxf[12];
 #pragma unroll
-    for (int k = 0; k < 24; k++) acc[k] = 0;
-    const float* wl = lsm + warp * 8 * LINK_F32;
+    for (int k = 0; k < 24; k++) acc[k] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int d = 0; d < 8; d++) {
       cp_async_wait<PF - 1>();
       if (d == 0) {
-        // this chunk's raw links arrived with its item 0: lane d reconstructs link d
+        // this chunk's raw links arrived with its item 0: lane d < 8 of each half rebuilds
+        // link d of its site, folds in the t boundary phase and stores it sign-paired
         __syncwarp();  // every lane is done with the previous chunk's links
-        if (lane < 8) {
-          const Tg* rawp = reinterpret_cast<const Tg*>(lraw + (((j & 1) * 8 + warp) * 8 + lane) * RPC);
-          Tm tmp[RP];
+        if (q < 8) {
+          const Tg* rawp = reinterpret_cast<const Tg*>(lraw + ((((j & 1) * 4 + warp) * 2 + half) * 8 + q) * RPC);
+          float tmp[RP];
 #pragma unroll
-          for (int c = 0; c < RP / GVW; c++) load_vec<Tg, Tm>(rawp + c * GVW, tmp + c * GVW);
-          Tm u[18];
+          for (int c = 0; c < RP / GVW; c++) load_vec<Tg, float>(rawp + c * GVW, tmp + c * GVW);
+          float u[18];
 #pragma unroll
           for (int k = 0; k < NR; k++) u[k] = tmp[k];
           if constexpr (NR == 12) link_row3(u);
-          float* dst = lsm + (warp * 8 + lane) * LINK_F32;
+          const float sr = (q & 1) ? phc : -phc;  // forward links negated
+          float* dst = lsm + (warp * 2 + half) * SITE_PK + q * LINK_PK;
 #pragma unroll
-          for (int q = 0; q < 18; q++) dst[q] = (float)u[q] * phc;  // t phase folded in (lanes 6, 7)
+          for (int k = 0; k < 9; k++)
+            *reinterpret_cast<float2*>(dst + 2 * k) = make_float2(u[2 * k] * sr, u[2 * k + 1] * phc);
         }
         __syncwarp();
       }
-      // every lane computes (no per-lane branches); a lane whose system sits out reads a
-      // stale ring slot, and its results are neither stored nor summed
-      constexpr bool RAW = std::is_same<Ts, __half>::value;  // FP16: projection on the raw halves
-      Tm psi[24], u[18];
-      unsigned short p16[24];
+      // every lane computes (no per-lane branches); a system that sits out reads a stale
+      // ring slot, and its results are neither stored nor summed
+      uint4 wa[CV], wb[CV];
       {
         const int slot = slot_of(j, d);
-        if constexpr (RAW) {
 #pragma unroll
-          for (int c = 0; c < CV; c++) {
-            const uint4 w = ring[((size_t)slot * CV + c) * 256 + threadIdx.x];
-            const unsigned short* q = reinterpret_cast<const unsigned short*>(&w);
-#pragma unroll
-            for (int e = 0; e < 8; e++) p16[c * 8 + e] = q[e];
-          }
-        } else {
-#pragma unroll
-          for (int c = 0; c < CV; c++) fetch_chunk(slot, c, psi + c * VW);
-        }
-        const float4* src4 = reinterpret_cast<const float4*>(wl + d * LINK_F32);
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const float4 w = src4[q];
-          u[4 * q] = w.x; u[4 * q + 1] = w.y; u[4 * q + 2] = w.z; u[4 * q + 3] = w.w;
-        }
-        const float2 w2 = *reinterpret_cast<const float2*>(wl + d * LINK_F32 + 16);
-        u[16] = w2.x; u[17] = w2.y;
+        for (int c = 0; c < CV; c++) { wa[c] = *ring_at(slot, c, 0); wb[c] = *ring_at(slot, c, 1); }
       }
       switch (d) {  // the slot just read is refilled (d is a constant after unrolling)
         case 0: issue_ahead(IntC<0>{}, j); break;
@@ -1034,64 +1151,54 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
         case 6: issue_ahead(IntC<6>{}, j); break;
         default: issue_ahead(IntC<7>{}, j); break;
       }
-      if constexpr (RAW) {
-        float h[12];
-        switch (d) {
-          case 0: project_h<0, -1>(p16, h); fwd_core<0>(xf, h, u, 1.f); break;
-          case 1: project_h<0, +1>(p16, h); bwd_core<0>(acc, xf, h, u, 1.f); break;
-          case 2: project_h<1, -1>(p16, h); fwd_core<1>(xf, h, u, 1.f); break;
-          case 3: project_h<1, +1>(p16, h); bwd_core<1>(acc, xf, h, u, 1.f); break;
-          case 4: project_h<2, -1>(p16, h); fwd_core<2>(xf, h, u, 1.f); break;
-          case 5: project_h<2, +1>(p16, h); bwd_core<2>(acc, xf, h, u, 1.f); break;
-          case 6: project_h<3, -1>(p16, h); fwd_core<3>(xf, h, u, 1.f); break;
-          default: project_h<3, +1>(p16, h); bwd_core<3>(acc, xf, h, u, 1.f); break;
-        }
-      } else {
-        switch (d) {
-          case 0: hop_fwd<0>(xf, psi, u, (Tm)1); break;
-          case 1: hop_bwd<0>(acc, xf, psi, u, (Tm)1); break;
-          case 2: hop_fwd<1>(xf, psi, u, (Tm)1); break;
-          case 3: hop_bwd<1>(acc, xf, psi, u, (Tm)1); break;
-          case 4: hop_fwd<2>(xf, psi, u, (Tm)1); break;
-          case 5: hop_bwd<2>(acc, xf, psi, u, (Tm)1); break;
-          case 6: hop_fwd<3>(xf, psi, u, (Tm)1); break;
-          default: hop_bwd<3>(acc, xf, psi, u, (Tm)1); break;
-        }
+      float2 h[12];
+      const float* L = wl + d * LINK_PK;
+      switch (d) {
+        case 0: project_pk<0, -1, Ts, CV>(wa, wb, h); fwd_pk(nxf, h, L); break;
+        case 1: project_pk<0, +1, Ts, CV>(wa, wb, h); bwd_pk<0>(acc, nxf, h, L); break;
+        case 2: project_pk<1, -1, Ts, CV>(wa, wb, h); fwd_pk(nxf, h, L); break;
+        case 3: project_pk<1, +1, Ts, CV>(wa, wb, h); bwd_pk<1>(acc, nxf, h, L); break;
+        case 4: project_pk<2, -1, Ts, CV>(wa, wb, h); fwd_pk(nxf, h, L); break;
+        case 5: project_pk<2, +1, Ts, CV>(wa, wb, h); bwd_pk<2>(acc, nxf, h, L); break;
+        case 6: project_pk<3, -1, Ts, CV>(wa, wb, h); fwd_pk(nxf, h, L); break;
+        default: project_pk<3, +1, Ts, CV>(wa, wb, h); bwd_pk<3>(acc, nxf, h, L); break;
       }
     }
-    double dv[KK];
+    float2 dv[KK];
 #pragma unroll
-    for (int k = 0; k < KK; k++) dv[k] = 0.0;
+    for (int k = 0; k < KK; k++) dv[k] = make_float2(0.f, 0.f);
     if constexpr (DOT == DOT_TS) {
       // X (= s) and R (= rhat) together, one 16-byte chunk of each at a time:
       // t = ca s + cb (H in) in place of acc, and <t, s>, ||t||^2, ||s||^2, <rhat, s>, <rhat, t>
       cp_async_wait<PF - 2>();
-      Tm sr = 0, si = 0, tt = 0, ss = 0, qr = 0, qi = 0, tr = 0, ti = 0;
+      float2 sr = dv[0], si = dv[0], tt = dv[0], ss = dv[0], qr = dv[0], qi = dv[0], tr = dv[0], ti = dv[0];
       {
         const int xslot = slot_of(j, 8), rslot = slot_of(j, 9);
 #pragma unroll
         for (int c = 0; c < CV; c++) {
-          Tm xv[VW], rv[VW];
-          fetch_chunk(xslot, c, xv);
-          fetch_chunk(rslot, c, rv);
+          float2 xv[VW], rv[VW];
+          fetch_pk(xslot, c, xv);
+          fetch_pk(rslot, c, rv);
 #pragma unroll
-          for (int k = 0; k < VW; k++) acc[c * VW + k] = axpby(ca, xv[k], cb, acc[c * VW + k]);
+          for (int k = 0; k < VW; k++) acc[c * VW + k] = fma2(cb, acc[c * VW + k], mul2(ca, xv[k]));
 #pragma unroll
           for (int k = 0; k < VW; k += 2) {
-            const Tm t0 = acc[c * VW + k], t1 = acc[c * VW + k + 1];
-            dot_acc(sr, si, t0, t1, xv[k], xv[k + 1]);
-            norm_acc(tt, t0, t1);
-            norm_acc(ss, xv[k], xv[k + 1]);
-            dot_acc(qr, qi, rv[k], rv[k + 1], xv[k], xv[k + 1]);
-            dot_acc(tr, ti, rv[k], rv[k + 1], t0, t1);
+            const float2 t0 = acc[c * VW + k], t1 = acc[c * VW + k + 1];
+            const float2 nt1 = neg2(t1), nr1 = neg2(rv[k + 1]);
+            sr = fma2(t0, xv[k], sr); sr = fma2(t1, xv[k + 1], sr);
+            si = fma2(t0, xv[k + 1], si); si = fma2(nt1, xv[k], si);
+            tt = fma2(t0, t0, tt); tt = fma2(t1, t1, tt);
+            ss = fma2(xv[k], xv[k], ss); ss = fma2(xv[k + 1], xv[k + 1], ss);
+            qr = fma2(rv[k], xv[k], qr); qr = fma2(rv[k + 1], xv[k + 1], qr);
+            qi = fma2(rv[k], xv[k + 1], qi); qi = fma2(nr1, xv[k], qi);
+            tr = fma2(rv[k], t0, tr); tr = fma2(rv[k + 1], t1, tr);
+            ti = fma2(rv[k], t1, ti); ti = fma2(nr1, t0, ti);
           }
         }
       }
       issue_ahead(IntC<8>{}, j);
       issue_ahead(IntC<9>{}, j);
-      dv[0] = sel ? (double)sr : 0.0; dv[1] = sel ? (double)si : 0.0; dv[2] = sel ? (double)tt : 0.0;
-      dv[3] = sel ? (double)ss : 0.0; dv[4] = sel ? (double)qr : 0.0; dv[5] = sel ? (double)qi : 0.0;
-      dv[6] = sel ? (double)tr : 0.0; dv[7] = sel ? (double)ti : 0.0;
+      dv[0] = sr; dv[1] = si; dv[2] = tt; dv[3] = ss; dv[4] = qr; dv[5] = qi; dv[6] = tr; dv[7] = ti;
     } else {
       if constexpr (HAS_X) {
         // out = ca X + cb (H in), in place of acc, one 16-byte chunk of X at a time
@@ -1099,46 +1206,65 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_pp(HopArgs a) {
         const int slot = slot_of(j, 8);
 #pragma unroll
         for (int c = 0; c < CV; c++) {
-          Tm xv[VW];
-          fetch_chunk(slot, c, xv);
+          float2 xv[VW];
+          fetch_pk(slot, c, xv);
 #pragma unroll
-          for (int k = 0; k < VW; k++) acc[c * VW + k] = axpby(ca, xv[k], cb, acc[c * VW + k]);
+          for (int k = 0; k < VW; k++) acc[c * VW + k] = fma2(cb, acc[c * VW + k], mul2(ca, xv[k]));
         }
         issue_ahead(IntC<8>{}, j);
       }
       if constexpr (HAS_R) {
         // <rhat, v>, out = v
         cp_async_wait<PF - 1>();
-        Tm sr = 0, si = 0;
+        float2 sr = dv[0], si = dv[0];
         const int slot = slot_of(j, NITEM - 1);
 #pragma unroll
         for (int c = 0; c < CV; c++) {
-          Tm rv[VW];
-          fetch_chunk(slot, c, rv);
+          float2 rv[VW];
+          fetch_pk(slot, c, rv);
 #pragma unroll
-          for (int k = 0; k < VW; k += 2) dot_acc(sr, si, rv[k], rv[k + 1], acc[c * VW + k], acc[c * VW + k + 1]);
+          for (int k = 0; k < VW; k += 2) {
+            const float2 o0 = acc[c * VW + k], o1 = acc[c * VW + k + 1];
+            sr = fma2(rv[k], o0, sr); sr = fma2(rv[k + 1], o1, sr);
+            si = fma2(rv[k], o1, si); si = fma2(neg2(rv[k + 1]), o0, si);
+          }
         }
         issue_ahead(IntC<NITEM - 1>{}, j);
-        dv[0] = sel ? (double)sr : 0.0; dv[1] = sel ? (double)si : 0.0;
+        dv[0] = sr; dv[1] = si;
       }
     }
-    if (sel) make_field<Ts>(a.out, g.Vh, sh.N).store(site, sys, acc);
+    {
+      // store both systems
+      Ts* ob = (Ts*)a.out + (size_t)site * rowstride + (size_t)sa * VW;
+#pragma unroll
+      for (int c = 0; c < CV; c++) {
+        float va[VW], vb[VW];
+#pragma unroll
+        for (int k = 0; k < VW; k++) { va[k] = acc[c * VW + k].x; vb[k] = acc[c * VW + k].y; }
+        if (sel_a) store_vec<Ts, float>(ob + c * cstride, va);
+        if (sel_b) store_vec<Ts, float>(ob + c * cstride + 16 * VW, vb);
+      }
+    }
     if constexpr (K > 0) {
-      // the block's 8 sites form the 8-site group `chunk`; summed in site order by one warp
+      // the block's 8 sites form the 8-site group `chunk`; each value summed in site order
       const int par = j & 1;
 #pragma unroll
-      for (int k = 0; k < K; k++) dsm[par][warp][lane][k] = (float)dv[k];
+      for (int k = 0; k < K; k++) {
+        dsm[par][ls][k][q] = sel_a ? dv[k].x : 0.f;
+        dsm[par][ls][k][q + 16] = sel_b ? dv[k].y : 0.f;
+      }
       __syncthreads();
-      {
-        // value k of the group is summed (in site order, FP32) by warp (k - j) mod 8: the
-        // values are spread over the warps, and the warp that starts rotates with the chunk
-        const int k = (warp + j) & 7;
-        if (k < K && sys < sh.N) {
-          const int chunk = (int)blockIdx.x + j * G;
-          float s = 0.f;
+      const int chunk = (int)blockIdx.x + j * G;
 #pragma unroll
-          for (int w = 0; w < 8; w++) s += dsm[par][w][lane][k];
-          a.partial[((size_t)sys * K + k) * (g.Vh / 8) + chunk] = (double)s;
+      for (int r = 0; r < (K * 32 + 127) / 128; r++) {
+        const int idx = r * 128 + tid;  // (value k, system) of the group
+        const int k = idx >> 5, s = idx & 31;
+        const int sys = blockIdx.y * 32 + s;
+        if (k < K && sys < sh.N) {
+          float acc1 = 0.f;
+#pragma unroll
+          for (int w = 0; w < 8; w++) acc1 += dsm[par][w][k][s];
+          a.partial[((size_t)sys * K + k) * (g.Vh / 8) + chunk] = (double)acc1;
         }
       }
       // dsm[par] is rewritten two chunks later, after the next barrier: no second barrier

@@ -13,13 +13,12 @@ using MathOf = typename std::conditional<std::is_same<Ts, double>::value, double
 // Directions kept in flight by the prefetching hop kernel (shared-memory ring slots).
 template <typename Ts> constexpr int hop_pf() { return sizeof(Ts) == 2 ? 4 : 3; }
 
-// Ring depth of the persistent kernel: a divisor of the items per site where the
-// shared memory allows (static ring slots), two resident blocks per SM.
+// Ring depth of the persistent paired kernel: four operands in flight for 16-bit storage
+// (measured on the 16^3x32 hop: 2 or 3 slots leave the 10-operand launches waiting on L2), which
+// keeps three 128-thread blocks resident per SM; FP32 storage has twice the bytes per operand.
 template <typename Ts, int C, int D>
-constexpr int hop_pp_depth() {
-  constexpr int nitem = 8 + (C != COEF_PLAIN ? 1 : 0) + (D == DOT_R || D == DOT_TS ? 1 : 0);
-  if constexpr (sizeof(Ts) == 2) return nitem == 8 ? 4 : (nitem == 9 ? 3 : 5);
-  return 3;
+constexpr int hop_pk_depth() {
+  return sizeof(Ts) <= 2 ? 4 : 2;
 }
 
 struct PersistentGrid {
@@ -27,11 +26,13 @@ struct PersistentGrid {
   int blocks_per_sm = 0, nsm = 0;
 };
 
+// The persistent paired hop for 32-system chunks (hop_kernel_pk): 128-thread blocks of 8 sites,
+// as many as are resident (never more blocks than site chunks).
 template <typename Ts, typename Tg, typename Tm, int R, int C, int D>
-cudaError_t launch_hop_pp(const HopArgs& a, const Launch& l) {
-  constexpr int PF = hop_pp_depth<Ts, C, D>();
-  auto kern = hop_kernel_pp<Ts, Tg, Tm, R, C, D, PF>;
-  const size_t smem = hop_pf_smem<Ts, PF>(256);
+cudaError_t launch_hop_pk(const HopArgs& a, const Launch& l) {
+  constexpr int PF = hop_pk_depth<Ts, C, D>();
+  auto kern = hop_kernel_pk<Ts, Tg, R, C, D, PF>;
+  const size_t smem = hop_pk_smem<Ts, PF, DotK<D>::K>();
   // thread-safe one-time set-up: shared-memory opt-in and the resident grid
   static const PersistentGrid pg = [&] {
     PersistentGrid p;
@@ -39,14 +40,14 @@ cudaError_t launch_hop_pp(const HopArgs& a, const Launch& l) {
     if ((p.err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return p;
     if ((p.err = cudaGetDevice(&dev))) return p;
     if ((p.err = cudaDeviceGetAttribute(&p.nsm, cudaDevAttrMultiProcessorCount, dev))) return p;
-    p.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p.blocks_per_sm, kern, 256, smem);
+    p.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p.blocks_per_sm, kern, 128, smem);
     if (!p.err && p.blocks_per_sm < 1) p.err = cudaErrorInvalidConfiguration;
     return p;
   }();
   if (pg.err) return pg.err;
   const int gy = l.grid_y;
   const int gx = std::max(1, std::min(a.sh.nchunk, pg.blocks_per_sm * pg.nsm / std::max(gy, 1)));
-  kern<<<dim3(gx, gy), 256, smem, l.stream>>>(a);
+  kern<<<dim3(gx, gy), 128, smem, l.stream>>>(a);
   note_launch();
   return cudaGetLastError();
 }
@@ -54,8 +55,8 @@ cudaError_t launch_hop_pp(const HopArgs& a, const Launch& l) {
 template <typename Ts, typename Tg, typename Tm, int R, int C, int D>
 cudaError_t launch_hop_pf(const HopArgs& a, const Launch& l) {
   if (a.sysmajor) return cudaErrorInvalidValue;  // inner-precision fields are tile-layout only
-  // 32 systems per warp, 8 sites per block: the persistent pipelined kernel
-  if (a.sh.NB == 32 && a.sh.SB == 8 && l.block == 256) return launch_hop_pp<Ts, Tg, Tm, R, C, D>(a, l);
+  // 32-system chunks, 8 sites per block: the persistent paired kernel
+  if (a.sh.NB == 32 && a.sh.SB == 8 && l.block == 256) return launch_hop_pk<Ts, Tg, Tm, R, C, D>(a, l);
   constexpr int PF = hop_pf<Ts>();
   const size_t smem = hop_pf_smem<Ts, PF>(l.block);
   // thread-safe one-time set-up (several server workers may launch concurrently)
