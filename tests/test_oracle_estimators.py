@@ -108,6 +108,22 @@ def test_split_even_cyclic_equality():
     assert np.abs(lhs - rhs).max() > 1e-3
 
 
+def test_practical_variance_normalisation_by_hand():
+    """Eq. (practical_variance) as printed divides by N (reading C6), not N - 1. Sample sets
+    worked by hand: {1, i, -1, -i} has mean 0 and mean |c|^2 = 1, so 1 (N - 1 would give 4/3);
+    {2, 4}: 10 - 9 = 1 (N - 1: 2); {1+i, 1-i, 3+i}: 14/3 - 26/9 = 16/9 (N - 1: 8/3). A column
+    per sample set checks that levels are kept apart."""
+    assert abs(estimators.practical_variance([1, 1j, -1, -1j]) - 1.0) < 1e-12
+    assert abs(estimators.practical_variance([2.0, 4.0]) - 1.0) < 1e-12
+    assert abs(estimators.practical_variance([1 + 1j, 1 - 1j, 3 + 1j]) - 16.0 / 9.0) < 1e-12
+    cols = np.array([[1, 2.0], [1j, 4.0], [-1, 2.0], [-1j, 4.0]])
+    assert np.allclose(estimators.practical_variance(cols), [1.0, 1.0], rtol=0, atol=1e-12)
+    # a constant set has no variance, a single sample none either (up to the rounding of the
+    # one-pass form)
+    assert abs(estimators.practical_variance([3 - 2j] * 5)) < 1e-12
+    assert abs(estimators.practical_variance([7.5])) < 1e-12
+
+
 def _mc_check(samples, exact_mean, exact_var):
     c = np.asarray(samples)
     n = c.size
