@@ -171,7 +171,7 @@ def _oracle_levels(u, m, sig, gam, p, n, seed, job, dims, est):
     return oest.level_samples(u, m, sig, gam, p, n, seed, job, dims, -1, est, solver)
 
 
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f16", 1e-6)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f16", 1e-6), ("bf16", 1e-6)])
 def test_mlmc_config1_samples(prec, tol):
     """4^4 Haar links, m = -0.4, shifts {0, 0.4}, Gamma = I, p = 0, 64 Z4 vectors per level."""
     dims = (4, 4, 4, 4)
@@ -188,6 +188,27 @@ def test_mlmc_config1_samples(prec, tol):
         assert sample_err(out["samples"][lev], ref[lev]) < tol, lev
         m2 = np.mean(np.abs(ref[lev]) ** 2)
         assert abs(out["var"][lev] - oest.practical_variance(ref[lev])) <= 10 * tol * m2
+    ctx.close()
+
+
+def test_mlmc_config2_samples_against_oracle_bicgstab():
+    """Config 2: 8^4 smoothed links (eps = 0.3), m = -0.2, shifts {0.02, 0.1, 0.5}, Gamma =
+    gamma5 gamma3, z-displacement p = 2, FP32 storage with FP64 reliable updates, 16-system tiles;
+    the level samples against the oracle's own BiCGStab solutions (no dense inverse at this size)
+    on the same noise, at the mixed-precision tolerance."""
+    dims = (8, 8, 8, 8)
+    m, sig, p, seed, job = -0.2, [0.02, 0.1, 0.5], 2, 2002, 0
+    u = inputs.gauge_field(dims, "smooth", seed=1002, eps=0.3)
+    n = [2, 2, 2]
+    ctx = make_ctx(dims, u)
+    out = ctx.mlmc_level_trace(m, sig, pkg.gamma_matrix("g5g3"), p, n, seed=seed, job=job, estimator="diff",
+                               prec="f32", tol=1e-10, rhs_tile=16)
+    assert out["rc"] == 0
+    solver = oest.make_solver(u, m, dims, -1, tol=1e-12)
+    ref = oest.level_samples(u, m, sig, odirac.gamma_product(["g5", "g3"]), p, n, seed, job, dims, -1, oest.DIFF,
+                             solver)
+    for lev in range(3):
+        assert sample_err(out["samples"][lev], ref[lev]) < 1e-6, (lev, out["samples"][lev], ref[lev])
     ctx.close()
 
 
