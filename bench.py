@@ -127,6 +127,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measure_arith_peaks(pkg, index, seconds):
+    """The FP32 and FP64 roofs measured on this GPU (fs_measure_peak: independent FMA chains on
+    every SM), with the SM clock sampled while each runs; `at_max_clock` rescales the rate by
+    max / median sampled clock (time x median MHz)."""
+    out = {}
+    for kind in ("f32", "f32x2", "f64"):
+        clk = ClockSampler(index)
+        clk.start()
+        tf, ms = pkg.fs_measure_peak(kind, seconds)
+        c = clk.stop()
+        entry = {"tflops": tf, "ms": ms, "sm_mhz": c.get("sm_mhz"), "sm_max_mhz": c.get("sm_max_mhz"),
+                 "reasons": c.get("reasons")}
+        if c.get("sm_mhz") and c.get("sm_max_mhz"):
+            entry["at_max_clock"] = tf * c["sm_max_mhz"] / c["sm_mhz"]
+        out[kind] = entry
+    out["how"] = ("fs_measure_peak: 8 independent multiply-add chains per thread, all SMs filled, "
+                  "launches repeated for %.1f s, timed with CUDA events; 2 flop per multiply-add" % seconds)
+    return out
+
+
 def dist_setup(backend="nccl"):
     """Replicas only: one process per GPU, each solving its own noise vectors. The process
     group carries nothing but the barrier and the two scalar reductions of the timing."""
@@ -568,6 +588,8 @@ def build_parser():
     ap.add_argument("--no-fp64-baseline", action="store_true", help="skip the FP64 single-RHS GPU solver")
     ap.add_argument("--roof-steps", type=int, default=2, help="single-lane steps timed for the roofline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the measured FP32 / FP64 roofs")
+    ap.add_argument("--peak-seconds", type=float, default=2.0, help="timed seconds per measured roof")
     ap.add_argument("--ref-budget", type=float, default=8.0, help="seconds of oracle work per reference step")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--serve-jobs", type=int, default=12, help="jobs in the serving run (0: skip)")
@@ -676,7 +698,13 @@ def main():
     for k in range(args.roof_steps):
         step(job0 + 3000 + k, lanes=1)
     prof = ctx.profile_read()
+    prof64 = ctx.profile_read_fp64()
     ctx.profile_enable(False)
+
+    # ---- the FP32 and FP64 roofs of this GPU, measured (rank 0; the GPU is otherwise idle here)
+    arith = None
+    if rank == 0 and not args.no_peaks:
+        arith = measure_arith_peaks(pkg, torch.cuda.current_device(), args.peak_seconds)
 
     peaks, peak_kind = load_peaks()
     roof = None
@@ -694,13 +722,27 @@ def main():
         ratio = hop_traffic_ratio(args.workload)
         if ratio is not None:
             roof["traffic"] = ratio * bytes_per_launch
-        # the second roof of the same kernel: FP32 arithmetic, 1320 flop per (site, system) against
-        # 152 SMs x 128 lanes x 2 flop x 2.07 GHz (at 32 systems and FP16 storage the kernel's
-        # 12.9 flop/B sits on the ridge of the two roofs)
-        alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        # the second roof of the same kernel: FP32 arithmetic, 1320 flop per (site, system) (at 32
+        # systems and FP16 storage the kernel's 12.9 flop/B sits on the ridge of the two roofs),
+        # against the FP32 rate measured on this GPU (else the nominal unit count x max clock)
         alu = 1320.0 * prof["site_systems"] / prof["launches"] / per_launch_s / 1e12
+        if arith is not None:
+            alu_peak = max(arith["f32"]["tflops"], arith["f32x2"]["tflops"])
+            src = "measured (fs_measure_peak, the faster of scalar and packed FP32 FMA chains)"
+        else:
+            alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+            src = "nominal FP32 unit count x max clock"
         roof["second_roof"] = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s",
-                               "frac": alu / alu_peak, "peak_source": "nominal FP32 unit count x max clock"}
+                               "frac": alu / alu_peak, "peak_source": src}
+        # the FP64-arithmetic work-list hops of the same pass (preparation, FP64 reliable-update
+        # residuals, reconstruction, verification) against the measured FP64 rate
+        if prof64["launches"] > 0 and prof64["ms"] > 0 and arith is not None:
+            f64 = 1320.0 * prof64["site_systems"] / (prof64["ms"] / 1e3) / 1e12
+            roof["fp64_hops"] = {"bound": "fp64", "achieved": f64, "peak": arith["f64"]["tflops"],
+                                 "unit": "TFLOP/s", "frac": f64 / arith["f64"]["tflops"],
+                                 "launches": prof64["launches"], "avg_launch_us": prof64["ms"] * 1e3 / prof64["launches"],
+                                 "site_systems_per_launch": prof64["site_systems"] / prof64["launches"],
+                                 "peak_source": "measured (fs_measure_peak, FP64 FMA chains)"}
 
     # ---- the plain FP64 single-RHS GPU solver (the same library in FP64 with one system per tile
     # and one lane: no reduced-precision storage, no batching) on a sample of the same job
@@ -771,7 +813,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_of(args, w), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk, "serving": serving, "pipeline": pipeline,
+                "gpu_launches": launches, "clocks": clk, "arith_peaks": arith, "serving": serving,
+                "pipeline": pipeline,
                 "fp64_single_rhs": fp64, "probing": probing, "variance_sampling_24x64": large,
                 "solver": {"mean_iters": float(np.mean(iters)) if iters else None,
                            "max_iters": int(max(iters)) if iters else None,

@@ -290,6 +290,11 @@ FS_API int fs_noise_codes(fs_ctx* ctx, uint64_t seed, uint32_t job, uint32_t lev
  * Any output pointer may be NULL. */
 FS_API int fs_profile_enable(fs_ctx* ctx, int enable);
 FS_API int fs_profile_read(fs_ctx* ctx, long long* launches, double* total_ms, double* bytes, double* site_systems);
+/* The same for the FP64-arithmetic hops on the system-major work lists of a mixed-precision or
+ * FP64 solve (the even-odd preparation, the FP64 reliable-update residuals, the odd-site
+ * reconstruction and the verification residual): launches, device milliseconds and the
+ * (site, system) pairs they computed (1320 flop each on the FP64 pipe). */
+FS_API int fs_profile_read_fp64(fs_ctx* ctx, long long* launches, double* total_ms, double* site_systems);
 
 /* ---- serving ---------------------------------------------------------------------
  * A server on one GPU runs FS-MLMC trace jobs (one mlmc_level_trace each) as they arrive.
@@ -353,6 +358,18 @@ FS_API void fs_server_destroy(fs_server* server);
 /* Number of CUDA kernels this library has launched in the process (all contexts). */
 FS_API long long fs_kernel_launches(void);
 
+/* ---- measured arithmetic roofs --------------------------------------------------------
+ * The paper has no counterpart; the hop kernels sit at the ridge of this GPU's HBM and FP32
+ * roofs, and these measure the FP32 and FP64 roofs on the device itself. fs_measure_peak runs
+ * independent fused multiply-add chains (scalar FP32, packed FP32 pairs, or FP64) on every SM of
+ * the current device, with as many threads as fit, for about `seconds` (at most 60) on a stream of
+ * its own, and writes the rate in TFLOP/s (2 flop per multiply-add) and the elapsed time of the
+ * timed launches (CUDA events). The caller samples clocks alongside if it wants a clock-normalised
+ * figure. FS_ERR_ARG for a bad kind or time; FS_ERR_CUDA if a CUDA call fails or an error was
+ * already pending (left untouched). */
+enum fs_peak_kind { FS_PEAK_F32 = 0, FS_PEAK_F32X2 = 1, FS_PEAK_F64 = 2 };
+FS_API int fs_measure_peak(int kind, double seconds, double* tflops, double* elapsed_ms);
+
 /* ---- allocation-free variant ------------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that may not
  * allocate device memory while they run: work recorded into a CUDA stream capture,
@@ -370,7 +387,11 @@ FS_API long long fs_kernel_launches(void);
  * `stream` (a cudaStream_t, NULL = legacy default stream): it returns once its kernels
  * are queued. All calls on a device share the array, so calls whose work overlaps on
  * the GPU (unordered streams) race and corrupt each other; each call rewrites every
- * scratch field it reads, so the contents left by the previous call do not matter. */
+ * scratch field it reads, so the contents left by the previous call do not matter.
+ * The cached device address does not survive cudaDeviceReset: do not call again in a
+ * process after a reset. A CUDA error already pending when the call starts (left by
+ * other work) makes it return FS_ERR_CUDA without launching and without clearing that
+ * error; a failure of one of its own launches returns FS_ERR_CUDA too. */
 FS_API int wilson_dslash_noalloc(const int dims[4], int bc_t, double m, double sigma, const double* U,
                           const double* in, double* out, int nrhs, void* stream);
 
@@ -407,6 +428,22 @@ FS_API int fs_select_shifts(const double* s_hat, int m, const double* VL_hat, co
  * C <= 0 or non-finite values. */
 FS_API int fs_sample_allocation(const double* V, const double* C, int nlev, double eps2, double* N, double* mu,
                          double* V_FS, double* C_FS);
+
+/* The FS estimate and its variance from the per-level results of mlmc_level_trace(s):
+ * total[q] = sum_l trace[q][l] (complex), the level estimates of Eq. (fs_trace_est) summed
+ * into the estimate of Tr(Gamma Omega_p (D + sigma_0)^-1), and v_fs[q] = sum_l var[q][l] / N_l,
+ * Eq. (total_var) (the levels use independent noise). trace [np][nlev][2] and var [np][nlev]
+ * as mlmc_level_traces writes them (np = 1 for mlmc_level_trace), N_l = n_samples[l]; total
+ * [np][2], v_fs [np]. Host only. FS_ERR_ARG for null pointers, nlev < 1, np < 1 or a level
+ * with no samples; FS_ERR_INPUT for non-finite values. */
+FS_API int fs_trace_total(const double* trace, const double* var, const int* n_samples, int nlev, int np,
+                          double* total, double* v_fs);
+
+/* Eq. (sampled_prod): the level variance of a pair of sampling shifts,
+ * Vl[q][i][j] = (s_hat_j - s_hat_i)^2 Vbar[q][i][j] for j >= i and 0 below the diagonal, from
+ * variance_sample's Vbar [np][m][m] (upper triangle) and its m shifts s_hat. Host only.
+ * FS_ERR_ARG for null pointers, m < 1 or np < 1; FS_ERR_INPUT for non-finite Vbar. */
+FS_API int fs_sampled_level_variances(const double* s_hat, int m, const double* Vbar, int np, double* Vl);
 
 /* The paper's evaluation set (Sec. 3.3): logspace(-5,-2,4) and logspace(log10(0.011),0,76)
  * from s_hat[0] up, with the sampling shifts added, sorted and unique (with s_hat[0] = 0 it

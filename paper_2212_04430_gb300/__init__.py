@@ -24,5 +24,8 @@ from .fsmlmc import (  # noqa: F401
     fs_sample_allocation,
     fs_eval_grid,
     fs_probing_colors,
+    fs_trace_total,
+    fs_sampled_level_variances,
+    fs_measure_peak,
 )
 from .gamma import gamma_matrix, gamma_mu, gamma5  # noqa: F401

@@ -12,6 +12,26 @@
 
 namespace {
 
+// Eq. (practical_variance) of n complex samples c[2k], c[2k+1]: (1/n) sum_k |c_k - t|^2 with the
+// sample mean t = (tr, ti), the biased 1/n form the paper prints. Two passes (the mean first): the
+// one-pass (1/n) sum |c_k|^2 - |t|^2 loses digits to cancellation when the mean is large next to
+// the spread, and can even come out negative.
+double practical_var(const double* c, int n, double& tr, double& ti) {
+  double sr = 0.0, si = 0.0;
+  for (int k = 0; k < n; k++) {
+    sr += c[2 * k];
+    si += c[2 * k + 1];
+  }
+  tr = sr / n;
+  ti = si / n;
+  double s2 = 0.0;
+  for (int k = 0; k < n; k++) {
+    const double dr = c[2 * k] - tr, di = c[2 * k + 1] - ti;
+    s2 += dr * dr + di * di;
+  }
+  return s2 / n;
+}
+
 using fs::Ctx;
 
 bool finite_array(const double* a, size_t n) {
@@ -40,6 +60,7 @@ void release(Ctx& c) {
   if (c.canon_d) cudaFree(c.canon_d);
   if (c.canon_h) cudaFreeHost(c.canon_h);
   for (auto& ev : c.prof.pending) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+  for (auto& ev : c.prof.pending64) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
   for (auto& ev : c.prof.pool) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
   if (c.prof.work_d) cudaFree(c.prof.work_d);
   if (c.own_stream) cudaStreamDestroy(c.own_stream);
@@ -50,22 +71,29 @@ int prof_reset(Ctx& c, bool enable) {
   cudaError_t e = cudaStreamSynchronize(c.stream);
   if (e) return c.cuda_fail(e, "fs_profile_enable");
   for (auto& ev : c.prof.pending) c.prof.pool.push_back(ev);
+  for (auto& ev : c.prof.pending64) c.prof.pool.push_back(ev);
   c.prof.pending.clear();
+  c.prof.pending64.clear();
   c.prof.launches = 0;
   c.prof.ms = 0;
   c.prof.bytes = 0;
   c.prof.pending_bytes = 0;
+  c.prof.launches64 = 0;
+  c.prof.ms64 = 0;
   if (!c.prof.work_d) {
-    e = cudaMalloc(&c.prof.work_d, 12 * sizeof(unsigned long long));
+    e = cudaMalloc(&c.prof.work_d, fs::PROF_SLOTS * sizeof(unsigned long long));
     if (e) return c.cuda_fail(e, "profile counters");
   }
-  e = cudaMemset(c.prof.work_d, 0, 12 * sizeof(unsigned long long));
+  e = cudaMemset(c.prof.work_d, 0, fs::PROF_SLOTS * sizeof(unsigned long long));
   if (e) return c.cuda_fail(e, "profile counters");
   c.prof.enabled = enable;
   return 0;
 }
 
-int prof_collect(Ctx& c, long long& launches, double& ms, double& bytes, double& pairs) {
+// Folds the finished launches' event times into the totals (idempotent: the counters are read
+// afresh each time) and adds this context's inner-precision hop figures (hi = false) or those of
+// its FP64-arithmetic work-list hops (hi = true, bytes unused).
+int prof_collect(Ctx& c, long long& launches, double& ms, double& bytes, double& pairs, bool hi = false) {
   cudaError_t e = cudaStreamSynchronize(c.stream);
   if (e) return c.cuda_fail(e, "fs_profile_read");
   for (auto& ev : c.prof.pending) {
@@ -74,10 +102,22 @@ int prof_collect(Ctx& c, long long& launches, double& ms, double& bytes, double&
     c.prof.pool.push_back(ev);
   }
   c.prof.pending.clear();
-  unsigned long long w[12] = {0};
+  for (auto& ev : c.prof.pending64) {
+    float t = 0;
+    if (cudaEventElapsedTime(&t, ev.first, ev.second) == cudaSuccess) c.prof.ms64 += t;
+    c.prof.pool.push_back(ev);
+  }
+  c.prof.pending64.clear();
+  unsigned long long w[fs::PROF_SLOTS] = {0};
   if (c.prof.work_d) {
     e = cudaMemcpy(w, c.prof.work_d, sizeof(w), cudaMemcpyDeviceToHost);
     if (e) return c.cuda_fail(e, "profile counters");
+  }
+  if (hi) {
+    launches += c.prof.launches64;
+    ms += c.prof.ms64;
+    pairs += (double)w[12];
+    return 0;
   }
   const double real_bytes[4] = {8.0, 4.0, 2.0, 2.0};
   double b = c.prof.pending_bytes;
@@ -724,16 +764,10 @@ int mlmc_impl(Ctx& c, const fs_mlmc_params* P, const int* p_in, int np, double* 
   for (int q = 0; q < np; q++) {
     const size_t qo = (size_t)q * total;
     for (int l = 0; l <= L; l++) {
-      const int n = P->n_samples[l];
-      double sr = 0, si = 0, s2 = 0;
-      for (int s = 0; s < n; s++) {
-        const double re = csum[(qo + off[l] + s) * 2], im = csum[(qo + off[l] + s) * 2 + 1];
-        sr += re; si += im; s2 += re * re + im * im;
-      }
-      const double tr = sr / n, ti = si / n;
+      double tr, ti;
+      var[(size_t)q * P->nlev + l] = practical_var(&csum[(qo + off[l]) * 2], P->n_samples[l], tr, ti);
       trace[((size_t)q * P->nlev + l) * 2] = tr;
       trace[((size_t)q * P->nlev + l) * 2 + 1] = ti;
-      var[(size_t)q * P->nlev + l] = s2 / n - (tr * tr + ti * ti);
     }
   }
   if (samples) memcpy(samples, csum.data(), csum.size() * sizeof(double));
@@ -867,18 +901,19 @@ int variance_sample_impl(Ctx& c, double m, const double* s_hat, int ms, const do
   };
   for (int qs = 0; qs < np; qs++) {
     const int q = order[qs];  // caller's index of the qs-th smallest displacement
+    std::vector<double> cs((size_t)Ns * 2);
+    double tr, ti;
     for (int i = 0; i < ms; i++) {
-      double sr = 0, si = 0, s2 = 0;
       for (int k = 0; k < Ns; k++) {
         const double re = val(k, i, qs, 0), im = val(k, i, qs, 1);
-        sr += re; si += im; s2 += re * re + im * im;
+        cs[(size_t)k * 2] = re;
+        cs[(size_t)k * 2 + 1] = im;
         if (a_out) {
           a_out[(((size_t)k * np + q) * ms + i) * 2] = re;
           a_out[(((size_t)k * np + q) * ms + i) * 2 + 1] = im;
         }
       }
-      sr /= Ns; si /= Ns;
-      VL[(size_t)q * ms + i] = s2 / Ns - (sr * sr + si * si);
+      VL[(size_t)q * ms + i] = practical_var(cs.data(), Ns, tr, ti);
     }
     int r = ms;
     for (int i = 0; i < ms; i++) {
@@ -892,17 +927,16 @@ int variance_sample_impl(Ctx& c, double m, const double* s_hat, int ms, const do
             }
           continue;
         }
-        double sr = 0, si = 0, s2 = 0;
         for (int k = 0; k < Ns; k++) {
           const double re = val(k, r, qs, 0), im = val(k, r, qs, 1);
-          sr += re; si += im; s2 += re * re + im * im;
+          cs[(size_t)k * 2] = re;
+          cs[(size_t)k * 2 + 1] = im;
           if (b_out) {
             b_out[((((size_t)k * np + q) * ms + i) * ms + j) * 2] = re;
             b_out[((((size_t)k * np + q) * ms + i) * ms + j) * 2 + 1] = im;
           }
         }
-        sr /= Ns; si /= Ns;
-        Vbar[((size_t)q * ms + i) * ms + j] = s2 / Ns - (sr * sr + si * si);
+        Vbar[((size_t)q * ms + i) * ms + j] = practical_var(cs.data(), Ns, tr, ti);
         r++;
       }
     }
@@ -977,6 +1011,21 @@ int fs_profile_read(fs_ctx* ctx, long long* launches, double* total_ms, double* 
   if (launches) *launches = n;
   if (total_ms) *total_ms = ms;
   if (bytes) *bytes = b;
+  if (site_systems) *site_systems = pairs;
+  return FS_OK;
+}
+
+int fs_profile_read_fp64(fs_ctx* ctx, long long* launches, double* total_ms, double* site_systems) {
+  if (!ctx) return FS_ERR_ARG;
+  Ctx& c = ctx->c;
+  if (int rc = set_device(c)) return rc;
+  long long n = 0;
+  double ms = 0, b = 0, pairs = 0;
+  if (int rc = prof_collect(c, n, ms, b, pairs, true)) return rc;
+  for (auto& l : c.lanes)
+    if (prof_collect(*l, n, ms, b, pairs, true)) return c.fail(FS_ERR_CUDA, l->err);
+  if (launches) *launches = n;
+  if (total_ms) *total_ms = ms;
   if (site_systems) *site_systems = pairs;
   return FS_OK;
 }

@@ -287,6 +287,26 @@ class Tile : public TileBase {
     return e;
   }
 
+  // An FP64-arithmetic hop on the system-major work list, timed while profiling is on.
+  cudaError_t hop_hi(int coef, int dot, const HopArgs& a, const Launch& l) {
+    HopProfile& pf = c->prof;
+    if (!pf.enabled) return launch_hop<double>(coef, dot, 18, a, l);
+    cudaEvent_t e0, e1;
+    if (!pf.pool.empty()) {
+      e0 = pf.pool.back().first; e1 = pf.pool.back().second; pf.pool.pop_back();
+    } else {
+      cudaEventCreate(&e0); cudaEventCreate(&e1);
+    }
+    HopArgs b = a;
+    b.work = pf.work_d + 12;
+    cudaEventRecord(e0, l.stream);
+    cudaError_t e = launch_hop<double>(coef, dot, 18, b, l);
+    cudaEventRecord(e1, l.stream);
+    pf.pending64.push_back({e0, e1});
+    pf.launches64 += 1;
+    return e;
+  }
+
   cudaError_t enqueue_rhs_from_canon(const double* canon) override {
     L.stream = c->stream;
     L1.stream = c->stream;
@@ -310,8 +330,8 @@ class Tile : public TileBase {
     LW.stream = c->stream;
     cudaError_t e;
     // bhat_e = z_e - D_eo A^-1 z_o, ||bhat||^2
-    if ((e = launch_hop<double>(COEF_PREP, DOT_NORM, 18, hop(bhat, z_o, z_e, nullptr, nullptr, pa, 0, MASK_INIT,
-                                                              false, true, true), lwh()))) return e;
+    if ((e = hop_hi(COEF_PREP, DOT_NORM, hop(bhat, z_o, z_e, nullptr, nullptr, pa, 0, MASK_INIT, false, true, true),
+                    lwh()))) return e;
     if ((e = launch_blas<Ts>(OP_NORM64, blas(MASK_INIT, z_e, pb, false, true), LW))) return e;
     if ((e = launch_blas<Ts>(OP_NORM64, blas(MASK_INIT, z_o, pc, false, true), LW))) return e;
     if ((e = launch_blas<Ts>(OP_ZEROX, blas(MASK_INIT, nullptr, nullptr, false, true), LW))) return e;
@@ -366,12 +386,11 @@ class Tile : public TileBase {
       if ((e = launch_hop64_f32(COEF_PLAIN, DOT_NONE, h3, lwh()))) return e;
       if ((e = launch_hop64_f32(COEF_TRUERES, DOT_NORM, h4, lwh()))) return e;
     }
-    if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
-                                hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, later, true, true, true),
-                                lwh())))
+    if ((e = hop_hi(COEF_PLAIN, DOT_NONE,
+                    hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, later, true, true, true), lwh())))
       return e;
-    if ((e = launch_hop<double>(COEF_TRUERES, DOT_NORM, 18,
-                                hop(r_hi, tmp64, x_hi, bhat, nullptr, pa, 0, later, true, true, true), lwh())))
+    if ((e = hop_hi(COEF_TRUERES, DOT_NORM, hop(r_hi, tmp64, x_hi, bhat, nullptr, pa, 0, later, true, true, true),
+                    lwh())))
       return e;
     if ((e = fin(FIN_TRUE, MASK_UPDATE, pa))) return e;
     if ((e = launch_blas<Ts>(OP_SETR, blas(MASK_UPDATE, r_hi, pa, true, true), LW))) return e;
@@ -413,19 +432,19 @@ class Tile : public TileBase {
     L1.stream = c->stream;
     LW.stream = c->stream;
     // x_o = A^-1 (z_o - D_oe x_e)
-    return launch_hop<double>(COEF_RECON, DOT_NONE, 18,
-                              hop(x_o, x_hi, z_o, nullptr, nullptr, nullptr, 1, MASK_HARVEST, false, true, true), lwh());
+    return hop_hi(COEF_RECON, DOT_NONE,
+                  hop(x_o, x_hi, z_o, nullptr, nullptr, nullptr, 1, MASK_HARVEST, false, true, true), lwh());
   }
 
   cudaError_t enqueue_verify() override {
     L1.stream = c->stream;
     LW.stream = c->stream;
     cudaError_t e;
-    if ((e = launch_hop<double>(COEF_FULLRES, DOT_NORM, 18,
-                                hop(r_hi, x_o, x_hi, z_e, nullptr, pa, 0, MASK_HARVEST, false, true, true), lwh())))
+    if ((e = hop_hi(COEF_FULLRES, DOT_NORM, hop(r_hi, x_o, x_hi, z_e, nullptr, pa, 0, MASK_HARVEST, false, true, true),
+                    lwh())))
       return e;
-    if ((e = launch_hop<double>(COEF_FULLRES, DOT_NORM, 18,
-                                hop(tmp64, x_hi, x_o, z_o, nullptr, pb, 1, MASK_HARVEST, false, true, true), lwh())))
+    if ((e = hop_hi(COEF_FULLRES, DOT_NORM, hop(tmp64, x_hi, x_o, z_o, nullptr, pb, 1, MASK_HARVEST, false, true, true),
+                    lwh())))
       return e;
     return fin(FIN_VERIFY, MASK_HARVEST, pa, pb);
   }

@@ -58,8 +58,15 @@ struct HopProfile {
   double ms = 0.0;
   double bytes = 0.0;
   double pending_bytes = 0.0;
-  unsigned long long* work_d = nullptr;  // (site, system) pairs per [precision][extra fields read]
+  unsigned long long* work_d = nullptr;  // (site, system) pairs per [precision][extra fields read], then
+                                         // [12] those of the FP64-arithmetic work-list hops
+  // the FP64-arithmetic work-list hops (preparation, reliable-update residuals, reconstruction,
+  // verification), timed separately: they run on the FP64 pipe
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending64;
+  long long launches64 = 0;
+  double ms64 = 0.0;
 };
+constexpr int PROF_SLOTS = 13;
 
 class TileBase {
  public:

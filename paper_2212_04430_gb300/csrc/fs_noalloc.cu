@@ -24,6 +24,13 @@
 // last call: every field a call reads is rewritten by that call first (nothing
 // relies on a zeroed array), and calls whose work overlaps on the GPU (different
 // streams, no ordering between them) race on the array and corrupt each other.
+// The cached address belongs to the device's current context: after a
+// cudaDeviceReset it is stale and the entry point must not be called again in
+// that process.
+//
+// Errors: a CUDA error already pending when the call starts (left by unrelated
+// work) makes it return FS_ERR_CUDA at once, without touching or clearing that
+// error; otherwise each of its own launches is checked.
 #include <algorithm>
 #include <mutex>
 
@@ -80,6 +87,8 @@ extern "C" int wilson_dslash_noalloc(const int dims[4], int bc_t, double m, doub
   const size_t need = gauge_bytes + 4 * field_bytes + state_bytes + vec_bytes;
   if (need > FS_NOALLOC_SCRATCH_BYTES) return FS_ERR_BUDGET;  // lattice x nrhs beyond the fixed scratch
 
+  // an error left pending by other work is not ours to clear: refuse before launching anything
+  if (cudaPeekAtLastError() != cudaSuccess) return FS_ERR_CUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= FS_NOALLOC_MAX_DEVICES) {
     cudaGetLastError();
@@ -118,9 +127,23 @@ extern "C" int wilson_dslash_noalloc(const int dims[4], int bc_t, double m, doub
   const int gy = (nrhs + sh.NB - 1) / sh.NB;
   const int block = sh.SB * sh.NB;
 
+  // no error was pending on entry, so an error read here comes from this call's own launches
+  int launched = 0;
+  auto launched_ok = [&]() {
+    launched++;
+    return cudaGetLastError() == cudaSuccess;
+  };
   noalloc_init_kernel<<<(nrhs + 63) / 64, 64, 0, s>>>(st, vec, nrhs, 4.0 + m + sigma);
-  fs::gauge_pack_kernel<double, 18><<<(8 * g.Vh + 255) / 256, 256, 0, s>>>(gauge, U, g);
-  fs::pack_kernel<double><<<dim3(std::min(2 * sh.nchunk, 65535), gy), block, 0, s>>>(in_e, in_o, in, vec, g, sh, false);
+  bool ok = launched_ok();
+  if (ok) {
+    fs::gauge_pack_kernel<double, 18><<<(8 * g.Vh + 255) / 256, 256, 0, s>>>(gauge, U, g);
+    ok = launched_ok();
+  }
+  if (ok) {
+    fs::pack_kernel<double><<<dim3(std::min(2 * sh.nchunk, 65535), gy), block, 0, s>>>(in_e, in_o, in, vec, g, sh,
+                                                                                     false);
+    ok = launched_ok();
+  }
   fs::HopArgs a{};
   a.gauge = gauge;
   a.st = st;
@@ -128,11 +151,21 @@ extern "C" int wilson_dslash_noalloc(const int dims[4], int bc_t, double m, doub
   a.sh = sh;
   a.mask = fs::MASK_INIT;
   // out_e = A in_e - H_eo in_o / 2 ; out_o = A in_o - H_oe in_e / 2
-  a.out = out_e; a.in = in_o; a.X = in_e; a.p_out = 0;
-  fs::hop_kernel<double, double, double, 18, fs::COEF_DSLASH, fs::DOT_NONE><<<dim3(sh.nchunk, gy), block, 0, s>>>(a);
-  a.out = out_o; a.in = in_e; a.X = in_o; a.p_out = 1;
-  fs::hop_kernel<double, double, double, 18, fs::COEF_DSLASH, fs::DOT_NONE><<<dim3(sh.nchunk, gy), block, 0, s>>>(a);
-  fs::unpack_kernel<double><<<dim3(std::min(2 * sh.nchunk, 65535), gy), block, 0, s>>>(out, out_e, out_o, vec, g, sh, false);
-  fs::note_launch(6);
-  return cudaGetLastError() == cudaSuccess ? FS_OK : FS_ERR_CUDA;
+  if (ok) {
+    a.out = out_e; a.in = in_o; a.X = in_e; a.p_out = 0;
+    fs::hop_kernel<double, double, double, 18, fs::COEF_DSLASH, fs::DOT_NONE><<<dim3(sh.nchunk, gy), block, 0, s>>>(a);
+    ok = launched_ok();
+  }
+  if (ok) {
+    a.out = out_o; a.in = in_e; a.X = in_o; a.p_out = 1;
+    fs::hop_kernel<double, double, double, 18, fs::COEF_DSLASH, fs::DOT_NONE><<<dim3(sh.nchunk, gy), block, 0, s>>>(a);
+    ok = launched_ok();
+  }
+  if (ok) {
+    fs::unpack_kernel<double><<<dim3(std::min(2 * sh.nchunk, 65535), gy), block, 0, s>>>(out, out_e, out_o, vec, g,
+                                                                                       sh, false);
+    ok = launched_ok();
+  }
+  fs::note_launch(launched);
+  return ok ? FS_OK : FS_ERR_CUDA;
 }

@@ -1,9 +1,12 @@
 // Serving loop: continuous batching of FS-MLMC trace jobs on one GPU.
 //
 // Jobs (a gauge field and the parameters of one mlmc_level_trace call) are queued
-// as they arrive. A job is admitted, first in first out, when an active slot is
-// free and its device-memory estimate fits the budget next to the jobs already
-// running. Every active job runs on its own worker thread with its own context and
+// as they arrive. A job is admitted when an active slot is free and its
+// device-memory estimate fits the budget next to the jobs already running. Among
+// the queued jobs that fit, the one with the least work (solves x lattice sites)
+// goes first by default; a job that has waited max_wait_ms goes next whatever its
+// size, and no later job passes it, so none waits for ever. fs_server_set_admission
+// selects first in, first out instead. Every active job runs on its own worker thread with its own context and
 // CUDA stream, so the work of concurrent jobs overlaps on the device; inside a
 // job the solves are continuously batched over the slots of its tile. A job's
 // results depend only on its own inputs (per-system kernels, fixed-order

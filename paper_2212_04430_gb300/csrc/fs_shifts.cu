@@ -2,8 +2,9 @@
 //
 // From the variances sampled by variance_sample (V_L at the m sampling shifts, Vbar_l at
 // every pair s^_i <= s^_j) and the iteration counts at the sampling shifts, predict V_L,
-// V_l and the solver cost on an evaluation set s (s_0 = 0), then choose the L shifts after
-// sigma_0 = 0 that minimise the multilevel cost, Eq. (ml_cost_shifts),
+// V_l and the solver cost on an evaluation set s that starts at the first sampling shift
+// (s_0 = s^_0; 0 in the paper, whose sigma_0 = 0), then choose the L shifts after
+// sigma_0 = s_0 that minimise the multilevel cost, Eq. (ml_cost_shifts),
 //   C_FS = eps^-2 F^2,  F = sum_l sqrt(C_l V_l),
 // and the per-level sample counts N_l = mu sqrt(V_l / C_l), Eq. (num_samples).
 //
@@ -220,6 +221,45 @@ int fs_sample_allocation(const double* V, const double* C, int nlev, double eps2
   if (mu) *mu = m;
   if (V_FS) *V_FS = vfs;
   if (C_FS) *C_FS = cfs;
+  return FS_OK;
+}
+
+int fs_trace_total(const double* trace, const double* var, const int* n_samples, int nlev, int np, double* total,
+                   double* v_fs) {
+  if (!trace || !var || !n_samples || !total || !v_fs || nlev < 1 || np < 1) return FS_ERR_ARG;
+  for (int l = 0; l < nlev; l++)
+    if (n_samples[l] < 1) return FS_ERR_ARG;
+  for (int q = 0; q < np; q++) {
+    double tr = 0.0, ti = 0.0, v = 0.0;
+    for (int l = 0; l < nlev; l++) {
+      const size_t k = (size_t)q * nlev + l;
+      if (!std::isfinite(trace[2 * k]) || !std::isfinite(trace[2 * k + 1]) || !std::isfinite(var[k]))
+        return FS_ERR_INPUT;
+      tr += trace[2 * k];  // Eq. (fs_trace_est): the level estimates add up to the trace
+      ti += trace[2 * k + 1];
+      v += var[k] / n_samples[l];  // Eq. (total_var): independent levels, V_l / N_l each
+    }
+    total[2 * q] = tr;
+    total[2 * q + 1] = ti;
+    v_fs[q] = v;
+  }
+  return FS_OK;
+}
+
+int fs_sampled_level_variances(const double* s_hat, int m, const double* Vbar, int np, double* Vl) {
+  if (!s_hat || !Vbar || !Vl || m < 1 || np < 1) return FS_ERR_ARG;
+  for (int q = 0; q < np; q++)
+    for (int i = 0; i < m; i++)
+      for (int j = 0; j < m; j++) {
+        const size_t k = ((size_t)q * m + i) * m + j;
+        if (j < i) {
+          Vl[k] = 0.0;
+          continue;
+        }
+        if (!std::isfinite(Vbar[k])) return FS_ERR_INPUT;
+        const double ds = s_hat[j] - s_hat[i];
+        Vl[k] = ds * ds * Vbar[k];  // Eq. (sampled_prod)
+      }
   return FS_OK;
 }
 

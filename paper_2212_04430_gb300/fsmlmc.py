@@ -28,7 +28,8 @@ EXPORTS = ["fs_ctx_create", "fs_ctx_destroy", "fs_last_error", "fs_set_stream", 
            "fs_server_stats", "fs_server_destroy", "fs_interp_variances", "fs_select_shifts",
            "fs_sample_allocation", "fs_eval_grid", "fs_tuned_tile", "fs_probing_colors",
            "variance_sample_probed", "shifted_solve_dev", "fs_hpe_exact_trace",
-           "mlmc_level_traces", "fs_server_set_admission"]
+           "mlmc_level_traces", "fs_server_set_admission", "fs_trace_total", "fs_sampled_level_variances",
+           "fs_measure_peak", "fs_profile_read_fp64"]
 JOB_MAX_LEVELS = 16
 
 
@@ -115,6 +116,7 @@ def load_library(path=LIB_PATH):
         "fs_noise_codes": (I, [P, U64, U32, U32, U32, ctypes.POINTER(ctypes.c_uint8)]),
         "fs_profile_enable": (I, [P, I]),
         "fs_profile_read": (I, [P, ctypes.POINTER(ctypes.c_longlong), dp, dp, dp]),
+        "fs_profile_read_fp64": (I, [P, ctypes.POINTER(ctypes.c_longlong), dp, dp]),
         "fs_kernel_launches": (ctypes.c_longlong, []),
         "wilson_dslash_noalloc": (I, [ip, I, D, D, P, P, P, I, P]),
         "fs_server_create": (I, [ctypes.POINTER(P), I, ctypes.c_size_t, I]),
@@ -127,6 +129,9 @@ def load_library(path=LIB_PATH):
         "fs_select_shifts": (I, [dp, I, dp, dp, dp, dp, I, I, ip, dp, dp, dp]),
         "fs_sample_allocation": (I, [dp, dp, I, D, dp, dp, dp, dp]),
         "fs_eval_grid": (I, [dp, I, dp, I, ip]),
+        "fs_trace_total": (I, [dp, dp, ip, I, I, dp, dp]),
+        "fs_measure_peak": (I, [I, D, dp, dp]),
+        "fs_sampled_level_variances": (I, [dp, I, dp, I, dp]),
         "fs_probing_colors": (I, [ip, I, I, ctypes.POINTER(ctypes.c_int32), ip]),
     }
     for name, (res, args) in sig.items():
@@ -320,6 +325,7 @@ class Context:
             rc = self._check(self.lib.mlmc_level_trace(self.h, ctypes.byref(P), _dptr(trace), _dptr(var),
                                                        _dptr(samples), st), allow_noconv=True)
         stats = [_stats(s) for s in st[:nsolve]]
+        total, v_fs = fs_trace_total(trace, var, ns)
         offs = np.concatenate([[0], np.cumsum(ns)])
         res = []
         for q in range(npl):
@@ -327,7 +333,8 @@ class Context:
             smp = samples[q, :, 0] + 1j * samples[q, :, 1]
             res.append({"p": int(plist[q]), "trace": tr, "var": var[q],
                         "samples": [smp[offs[l]:offs[l + 1]] for l in range(sig.size)],
-                        "total": complex(tr.sum()), "v_fs": float((var[q] / ns).sum()), "stats": stats, "rc": rc})
+                        "total": complex(total[q, 0], total[q, 1]), "v_fs": float(v_fs[q]), "stats": stats,
+                        "rc": rc})
         return res if multi else res[0]
 
     def variance_sample(self, m, s_hat, gamma, p_list, n_s, seed, job=0, colors=None, ncolors=None, dilute=False,
@@ -359,7 +366,7 @@ class Context:
                                                              _dptr(Vbar), _dptr(a),
                                                              _dptr(b), _dptr(iters)), allow_noconv=True)
         return {"VL": VL, "Vbar": Vbar, "a": a[..., 0] + 1j * a[..., 1], "b": b[..., 0] + 1j * b[..., 1],
-                "Vl": (sh[None, None, :] - sh[None, :, None]) ** 2 * Vbar, "iters": iters, "rc": rc}
+                "Vl": fs_sampled_level_variances(sh, Vbar), "iters": iters, "rc": rc}
 
     def fs_noise_codes(self, seed, job, level, sample):
         codes = np.empty((self.V, 4, 3), dtype=np.uint8)
@@ -380,6 +387,13 @@ class Context:
         self._check(self.lib.fs_profile_read(self.h, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by),
                                              ctypes.byref(ss)))
         return {"launches": n.value, "ms": ms.value, "bytes": by.value, "site_systems": ss.value}
+
+    def profile_read_fp64(self):
+        n = ctypes.c_longlong()
+        ms = ctypes.c_double()
+        ss = ctypes.c_double()
+        self._check(self.lib.fs_profile_read_fp64(self.h, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(ss)))
+        return {"launches": n.value, "ms": ms.value, "site_systems": ss.value}
 
 
 def fs_kernel_launches():
@@ -456,6 +470,47 @@ def fs_select_shifts(s_hat, VL_hat, Vbar_hat, iters_hat, s, L_shifts):
     return {"idx": ix, "sigma": ss[ix], "V": V, "C": C, "F": F.value}
 
 
+def fs_trace_total(trace, var, n_samples):
+    """(total [np][2], v_fs [np]) of Eq. (fs_trace_est) summed over levels and Eq. (total_var), from
+    mlmc_level_trace(s) output trace [np][nlev][2] (or [nlev][2]) and var [np][nlev]."""
+    L = load_library()
+    tr = _f64(trace)
+    vr = _f64(var)
+    ns = np.ascontiguousarray(n_samples, dtype=np.int32)
+    nlev = ns.size
+    npl = vr.size // nlev
+    total = np.empty((npl, 2))
+    v_fs = np.empty(npl)
+    _check(L.fs_trace_total(_dptr(tr), _dptr(vr), ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), nlev, npl,
+                            _dptr(total), _dptr(v_fs)), "fs_trace_total")
+    return total, v_fs
+
+
+def fs_sampled_level_variances(s_hat, Vbar):
+    """Vl [np][m][m] of Eq. (sampled_prod) from variance_sample's Vbar [np][m][m]."""
+    L = load_library()
+    sh = _f64(s_hat)
+    vb = _f64(Vbar)
+    m = sh.size
+    out = np.empty(vb.shape)
+    _check(L.fs_sampled_level_variances(_dptr(sh), m, _dptr(vb), vb.size // (m * m), _dptr(out)),
+           "fs_sampled_level_variances")
+    return out
+
+
+PEAK_KIND = {"f32": 0, "f32x2": 1, "f64": 2}
+
+
+def fs_measure_peak(kind, seconds=2.0):
+    """(TFLOP/s, elapsed ms) of independent FMA chains on the current device: kind "f32" (scalar
+    FP32), "f32x2" (packed FP32 pairs) or "f64"."""
+    L = load_library()
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(L.fs_measure_peak(PEAK_KIND[kind], float(seconds), ctypes.byref(tf), ctypes.byref(ms)),
+           "fs_measure_peak")
+    return tf.value, ms.value
+
+
 def fs_sample_allocation(V, C, eps2):
     """(N, mu, V_FS, C_FS) of Eq. (num_samples) / Eq. (total_var)."""
     L = load_library()
@@ -468,8 +523,9 @@ def fs_sample_allocation(V, C, eps2):
 
 
 class Server:
-    """fs_server: FIFO admission by device-memory budget, one worker (context + stream) per
-    active job, continuous batching inside each job."""
+    """fs_server: admission by device-memory budget (least work first by default, with an aging
+    limit; first in, first out through set_admission), one worker (context + stream) per active
+    job, continuous batching inside each job."""
 
     def __init__(self, device=0, hbm_budget_bytes=60 << 30, max_active=4):
         self.lib = load_library()
