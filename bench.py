@@ -35,12 +35,12 @@ WORKLOADS = {
     # quarter of it, 128 vectors per level (the tiles drain once per call: 32 per call lost 8%)
     "16x32": dict(key="16x32", dims=(16, 16, 16, 32), eps=0.4, gauge_seed=1003, noise_seed=2003, m=-0.35,
                   sigmas=[0.005, 0.03, 0.15, 0.6], gamma="g3", p=4, vectors=128, tile=32, prec="f16",
-                  link=12, tol=1e-8, estimator="diff",
+                  link=12, tol=1e-8, estimator="split_even",
                   name="16^3x32 Wilson FS-MLMC, 4 levels {0.005,0.03,0.15,0.6}, m=-0.35, eps=0.4, gamma3, p=4"),
     # the 8^4 FS-MLMC job (3 levels, 256 Z4 vectors per level in 16-system tiles)
     "8x8": dict(key="8x8", dims=(8, 8, 8, 8), eps=0.3, gauge_seed=1002, noise_seed=2002, m=-0.2,
                 sigmas=[0.02, 0.1, 0.5], gamma="g5g3", p=2, vectors=256, tile=16, prec="f32", link=18,
-                tol=1e-8, estimator="diff",
+                tol=1e-8, estimator="split_even",
                 name="8^4 Wilson FS-MLMC, 3 levels {0.02,0.1,0.5}, m=-0.2, eps=0.3, gamma5 gamma3, p=2"),
 }
 
@@ -362,10 +362,11 @@ CLIFFORD = ["1", "g1", "g2", "g3", "g4", "g5", "g1g2", "g1g3", "g1g4", "g2g3", "
             "g5g3", "g5g4"]
 
 
-def run_serving(pkg, inputs, device, n_jobs, rate=20.0, budget_gb=60, max_active=4, seed=4004):
+def run_serving(pkg, inputs, device, n_jobs, rate=20.0, budget_gb=60, max_active=4, seed=4004, vectors=(32, 256)):
     """Poisson arrivals (mean `rate` jobs/s) of trace jobs: lattice uniform over 8^4, 12^3x24,
-    16^3x32; 2..6 log-uniform shifts in [0.005, 1]; 32..256 Z4 vectors per level; p in 0..4;
-    Gamma uniform over the 16 Clifford products; FP16 or BF16 inner solves; m = -0.2, eps = 0.3."""
+    16^3x32; 2..6 log-uniform shifts in [0.005, 1]; `vectors` (32..256 in the serving workload)
+    Z4 vectors per level; p in 0..4; Gamma uniform over the 16 Clifford products; FP16 or BF16
+    inner solves; m = -0.2, eps = 0.3. One gauge field per lattice, shared by its jobs."""
     rng = np.random.default_rng(seed)
     gauges = {d: inputs.gauge_field(d, "smooth", seed=4100 + i, eps=0.3) for i, d in enumerate(SERVE_LATTICES)}
     jobs = []
@@ -373,7 +374,8 @@ def run_serving(pkg, inputs, device, n_jobs, rate=20.0, budget_gb=60, max_active
         dims = SERVE_LATTICES[int(rng.integers(len(SERVE_LATTICES)))]
         nlev = int(rng.integers(2, 7))
         sig = np.sort(np.exp(rng.uniform(np.log(0.005), 0.0, size=nlev)))
-        jobs.append(dict(dims=dims, sig=sig, n=[int(rng.integers(32, 257))] * nlev, p=int(rng.integers(0, 5)),
+        jobs.append(dict(dims=dims, sig=sig, n=[int(rng.integers(vectors[0], vectors[1] + 1))] * nlev,
+                         p=int(rng.integers(0, 5)),
                          gamma=pkg.gamma_matrix(CLIFFORD[int(rng.integers(16))]),
                          prec=["f16", "bf16"][int(rng.integers(2))], gap=float(rng.exponential(1.0 / rate))))
     srv = pkg.Server(device=device, hbm_budget_bytes=int(budget_gb) << 30, max_active=max_active)
@@ -394,11 +396,54 @@ def run_serving(pkg, inputs, device, n_jobs, rate=20.0, budget_gb=60, max_active
     bad = [dict(status=r["status"], prec=j["prec"], lattice="x".join(map(str, j["dims"])),
                 sigma_min=float(j["sig"][0]), noconv=r["noconv"], restarts=r["restarts"], max_iters=r["max_iters"])
            for r, j in zip(res, jobs) if r["status"] != 0]
-    return {"jobs": n_jobs, "arrival_rate_per_s": rate, "budget_gb": budget_gb, "max_active": max_active,
+    qms = np.array([r["queue_ms"] for r in res])
+    svc = np.array([r["latency_ms"] - r["queue_ms"] for r in res])
+    return {"jobs": n_jobs, "completed": int(st["completed"]), "arrival_rate_per_s": rate,
+            "vectors_per_level": list(vectors), "budget_gb": budget_gb, "max_active": max_active,
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "mean_ms": st["mean_ms"],
+            "queue_ms_p50": float(np.percentile(qms, 50)), "queue_ms_p99": float(np.percentile(qms, 99)),
+            "service_ms_p50": float(np.percentile(svc, 50)), "service_ms_p99": float(np.percentile(svc, 99)),
             "solves": int(st["solves"]), "solves_per_s": st["solves"] / wall, "wall_s": wall,
+            "offered_solves_per_s": float(st["solves"]) / max(sum(j["gap"] for j in jobs), 1e-9),
+            "gauge_reuses": int(st["gauge_reuses"]),
             "failed_jobs": len(bad), "failures": bad,
             "restarts": int(sum(r["restarts"] for r in res)), "max_iters": int(max(r["max_iters"] for r in res))}
+
+
+# --------------------------------------------------------------------------- estimator choice
+def run_estimators(pkg, ctx, w, kw, n=64, seed=9500):
+    """The three level estimators of the telescoping sum on the workload, the same N_l each:
+    per level the practical variance V_l (Eq. (practical_variance)), the solver cost C_l of one
+    sample (the iterations of its solves: two for l < L, one for the last level) and V_l C_l, and
+    the multilevel cost F^2 = (sum_l sqrt(V_l C_l))^2 of Eq. (ml_cost_shifts) (the cost of reaching
+    a given variance, up to the factor 1/eps^2). The smallest F^2 is the cheapest estimator."""
+    gam = pkg.gamma_matrix(w["gamma"])
+    nl = len(w["sigmas"])
+    res = {}
+    for est in ("diff", "split_even", "product"):
+        t0 = time.time()
+        out = ctx.mlmc_level_trace(w["m"], w["sigmas"], gam, w["p"], [n] * nl, seed=seed, job=50,
+                                   estimator=est, **kw)
+        dt = time.time() - t0
+        st = out["stats"]
+        k, levels, F = 0, [], 0.0
+        for lev in range(nl):
+            per = 2 if lev < nl - 1 else 1
+            its = [sum(st[k + s * per + q]["iters"] for q in range(per)) for s in range(n)]
+            k += n * per
+            c = float(np.mean(its))
+            v = float(out["var"][lev])
+            levels.append({"V": v, "C_iters": c, "VC": v * c,
+                           "trace": [float(out["trace"][lev].real), float(out["trace"][lev].imag)]})
+            F += np.sqrt(max(v, 0.0) * c)
+        res[est] = {"levels": levels, "F2": float(F * F), "V_FS_at_N": float(out["v_fs"]),
+                    "total": [float(out["total"].real), float(out["total"].imag)], "seconds": dt,
+                    "solves": int(len(st))}
+    best = min(res, key=lambda e: res[e]["F2"])
+    res["cheapest"] = best
+    res["note"] = ("%d Z4 vectors per level, the same noise for every estimator (seed %d); F2 = "
+                   "(sum_l sqrt(V_l C_l))^2 with C_l in BiCGStab iterations per sample" % (n, seed))
+    return res
 
 
 # --------------------------------------------------------------------------- the full method
@@ -589,10 +634,13 @@ def build_parser():
     ap.add_argument("--roof-steps", type=int, default=2, help="single-lane steps timed for the roofline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-peaks", action="store_true", help="skip the measured FP32 / FP64 roofs")
+    ap.add_argument("--no-estimators", action="store_true", help="skip the DIFF / SPLIT_EVEN / PRODUCT comparison")
     ap.add_argument("--peak-seconds", type=float, default=2.0, help="timed seconds per measured roof")
     ap.add_argument("--ref-budget", type=float, default=8.0, help="seconds of oracle work per reference step")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--serve-jobs", type=int, default=12, help="jobs in the serving run (0: skip)")
+    ap.add_argument("--serve-jobs", type=int, default=200, help="jobs in the 20 jobs/s serving run (0: skip)")
+    ap.add_argument("--stable-jobs", type=int, default=200, help="jobs in the stable-load serving run (0: skip)")
+    ap.add_argument("--stable-rate", type=float, default=4.0, help="arrival rate of the stable-load run, jobs/s")
     ap.add_argument("--no-large", action="store_true", help="skip the 24^3x64 variance-sampling measurement")
     ap.add_argument("--no-probing", action="store_true",
                     help="skip the probed and spin-colour diluted level traces (p4k4 colours)")
@@ -779,6 +827,10 @@ def main():
         except Exception as ex:
             pipeline["paper_noise"] = {"error": str(ex)}
 
+    estimators = None
+    if not args.no_estimators and rank == 0:
+        estimators = run_estimators(pkg, ctx, w, kw)
+
     large = None
     if not args.no_large and rank == 0:
         large = run_variance_24x64(pkg, inputs, local)
@@ -789,9 +841,16 @@ def main():
         if w["m"] + w["sigmas"][-1] > 0:
             probing["hpe"] = run_hpe(pkg, ctx, w, kw)
 
-    serving = None
+    serving = serving_stable = None
     if args.serve_jobs > 0:
+        # the serving workload at its arrival rate (20 jobs/s), above what one GPU serves: latency
+        # there is mostly queueing
         serving = run_serving(pkg, inputs, local, args.serve_jobs)
+    if args.stable_jobs > 0:
+        # a stable queue: the same lattices, shifts, Gamma, p and precisions with 8..32 vectors per
+        # level, arriving below the server's capacity, so latency is the batching's own
+        serving_stable = run_serving(pkg, inputs, local, args.stable_jobs, rate=args.stable_rate, seed=4005,
+                                     vectors=(8, 32))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -814,6 +873,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_of(args, w), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "arith_peaks": arith, "serving": serving,
+                "serving_stable": serving_stable, "estimators": estimators,
                 "pipeline": pipeline,
                 "fp64_single_rhs": fp64, "probing": probing, "variance_sampling_24x64": large,
                 "solver": {"mean_iters": float(np.mean(iters)) if iters else None,

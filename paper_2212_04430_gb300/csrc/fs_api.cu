@@ -1015,6 +1015,14 @@ int fs_profile_read(fs_ctx* ctx, long long* launches, double* total_ms, double* 
   return FS_OK;
 }
 
+int fs_set_iteration_bound(fs_ctx* ctx, long long bound) {
+  if (!ctx) return FS_ERR_ARG;
+  if (bound < 0) return ctx->c.fail(FS_ERR_ARG, "negative iteration bound");
+  ctx->c.iter_bound = bound;
+  for (auto& l : ctx->c.lanes) l->iter_bound = bound;
+  return FS_OK;
+}
+
 int fs_profile_read_fp64(fs_ctx* ctx, long long* launches, double* total_ms, double* site_systems) {
   if (!ctx) return FS_ERR_ARG;
   Ctx& c = ctx->c;

@@ -28,6 +28,8 @@ enum BlasOp {
   OP_SETR = 5,    // r = scale * src ; on restart/init rhat = p = r, v = 0, else p rescaled ;
                   // <rhat, r>, ||r||^2
   OP_NORM64 = 6,  // ||src||^2 of an FP64 field
+  OP_RECON = 7,   // x_hi <- src2 / A + src / (2A): the odd sites x_o = A^-1 (z_o - D_oe x_e) from
+                  // src = H_oe x_e of the final FP64 residual (x_hi: the x_o field, src2: z_o)
 };
 
 struct BlasArgs {
@@ -40,6 +42,7 @@ struct BlasArgs {
   void* t;
   double* x_hi;
   const double* src;
+  const double* src2;
   const SysState* st;
   double* partial;
   const int* gate;
@@ -79,6 +82,7 @@ __global__ void __launch_bounds__(256) blas_kernel(BlasArgs a) {
   // x_hi and src (r_hi, bhat, z) are FP64 reliable-update fields: system-major layout
   const Field<double> xh = make_field<double>(a.x_hi, Vh, sh.N, true);
   const Field<double> src = make_field<double>(const_cast<double*>(a.src), Vh, sh.N, true);
+  const Field<double> src2 = make_field<double>(const_cast<double*>(a.src2), Vh, sh.N, true);
 
   // one chunk of sites for system `sys` (sel: the system takes part), block rows sys_base..
   auto chunk_body = [&](const int sys, const int chunk, const bool sel, const int sys_base) {
@@ -133,6 +137,15 @@ __global__ void __launch_bounds__(256) blas_kernel(BlasArgs a) {
 #pragma unroll
         for (int k = 0; k < 24; k++) { if (keep) hv[k] += isc * lv[k]; lv[k] = 0.0; }
         xh.store(site, sys, hv); xl.store(site, sys, lv);
+      } else if constexpr (OP == OP_RECON) {
+        // the epilogue of the reconstruction hop, fma(1/(2A), H_oe x_e, z_o / A), on the stored
+        // H_oe x_e: the same rounding, so the same x_o bit for bit
+        const double ca = a.st[sys].cd[C_INVA], cb = a.st[sys].cd[C_INV2A];
+        double hv[24], zv[24], ov[24];
+        src.load(site, sys, hv); src2.load(site, sys, zv);
+#pragma unroll
+        for (int k = 0; k < 24; k++) ov[k] = fmadd(cb, hv[k], ca * zv[k]);
+        xh.store(site, sys, ov);
       } else if constexpr (OP == OP_ZEROX) {
         double z[24];
 #pragma unroll
@@ -316,6 +329,7 @@ struct FinArgs {
   double nreal;      // 24 * Vh
   int max_restarts;
   int first_approx;  // a system's first reliable update took its true residual in FP32
+  int hx_kept;       // the FP64 scratch of a converged system is kept until its harvest
 };
 
 __device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi, double& cr, double& ci) {
@@ -432,7 +446,7 @@ __device__ __forceinline__ void fin_logic(const FinArgs& a, int op, SysState& s,
       s.updates += 1;
       if (v[0] <= s.tol2 && !approx) {
         s.status = SYS_CONVERGED;
-        s.flags = 0;
+        s.flags = a.hx_kept ? FLAG_HX : 0;  // the FP64 hop just left H_oe x_e in the scratch
       } else if ((s.flags & FLAG_FINAL) || !isfinite(v[0]) ||
                  ((s.flags & FLAG_RESTART) && s.restarts >= a.max_restarts)) {
         s.status = SYS_NOCONV;

@@ -209,9 +209,11 @@ template <typename Tg> __host__ __device__ constexpr int link_pad(int nr) {
 enum SysStatus { SYS_IDLE = 0, SYS_ACTIVE = 1, SYS_CONVERGED = 2, SYS_NOCONV = 3 };
 // FLAG_CG: the system is in the CGNR fallback; FLAG_HPE: a finished system whose solution takes
 // the hopping parameter expansion's kappa H applications before its contraction; FLAG_CHECK: the
-// update may end the solve (sloppy residual at tol, or max_iter), so its residual is full FP64
+// update may end the solve (sloppy residual at tol, or max_iter), so its residual is full FP64;
+// FLAG_HX: a converged system whose FP64 scratch still holds H_oe x_e of its final residual, so the
+// odd sites follow from it without another hop
 enum SysFlags { FLAG_UPDATE = 1, FLAG_RESTART = 2, FLAG_FINAL = 4, FLAG_INIT = 8, FLAG_HARVEST = 16,
-                FLAG_CG = 32, FLAG_HPE = 64, FLAG_CHECK = 128 };
+                FLAG_CG = 32, FLAG_HPE = 64, FLAG_CHECK = 128, FLAG_HX = 256 };
 
 // Indices into SysState::cd / cf.
 enum CoefIdx {

@@ -60,6 +60,17 @@ cudaError_t upload_vec(Ctx* c, TileBase* T) {
   return cudaMemcpyAsync(T->vec_d, T->vec_h, sizeof(int) * T->N, cudaMemcpyHostToDevice, c->stream);
 }
 
+// Every slot of T idle, on the host mirror and the device (the stream synchronised): a call that
+// stops early (its iteration bound ran out) leaves no system running into the next call.
+void idle_all(Ctx* c, TileBase* T) {
+  for (int j = 0; j < T->N; j++) {
+    T->st_h[j].status = SYS_IDLE;
+    T->st_h[j].flags = 0;
+  }
+  if (cudaMemcpyAsync(T->st_d, T->st_h, sizeof(SysState) * T->N, cudaMemcpyHostToDevice, c->stream) == cudaSuccess)
+    cudaStreamSynchronize(c->stream);
+}
+
 // CGNR fallback for the slots BiCGStab left unconverged: bounded host loop of
 // device iterations; returns with the stream idle and st_h current.
 int run_cg(Ctx* c, TileBase* T, const std::vector<int>& slots, const SolveOpts& o) {
@@ -75,7 +86,7 @@ int run_cg(Ctx* c, TileBase* T, const std::vector<int>& slots, const SolveOpts& 
   if (!e) e = T->enqueue_cg_init();
   if (e) return c->cuda_fail(e, "CGNR fallback initialisation");
   const int every = 16;
-  const long long bound = (long long)o.cg_max_iter + 2 * every;
+  const long long bound = c->iter_bound > 0 ? c->iter_bound : (long long)o.cg_max_iter + 2 * every;
   for (long long it = 0;; it += every) {
     for (int k = 0; k < every && !e; k++) e = T->enqueue_cg_iter();
     if (!e) e = cudaMemcpyAsync(T->st_h, T->st_d, sizeof(SysState) * T->N, cudaMemcpyDeviceToHost, c->stream);
@@ -84,7 +95,10 @@ int run_cg(Ctx* c, TileBase* T, const std::vector<int>& slots, const SolveOpts& 
     bool active = false;
     for (int j : slots) active |= T->st_h[j].status == SYS_ACTIVE;
     if (!active) return 0;
-    if (it > bound) return c->fail(6, "CGNR fallback did not terminate within its iteration bound");
+    if (it > bound) {
+      idle_all(c, T);
+      return c->fail(6, "CGNR fallback did not terminate within its iteration bound");
+    }
   }
 }
 
@@ -294,8 +308,12 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
   cudaError_t e;
   const int every = std::max(1, o.check_every);
   long long iters_run = 0;
-  // every system stops at max_iter (FLAG_FINAL); a follow-up solve doubles that
-  const long long bound = ((long long)o.max_iter * 2 + 64) * (long long)(jobs.size() + 1);
+  // every system stops at max_iter (FLAG_FINAL); a follow-up solve doubles that (the caller's
+  // watchdog bound, fs_set_iteration_bound, replaces it)
+  const long long bound =
+      c->iter_bound > 0 ? c->iter_bound : ((long long)o.max_iter * 2 + 64) * (long long)(jobs.size() + 1);
+  // no slot carries a system over from an earlier call that stopped early
+  idle_all(c, T);
 
   // The host mirrors st_h / spec_h / vec_h are pinned and uploaded asynchronously: the host
   // must not write them again until the copies that read them have executed. Every batch
@@ -374,7 +392,10 @@ int run_queue(Ctx* c, TileBase* T, const std::vector<QJob>& jobs, const SolveOpt
     if ((e = cudaMemcpyAsync(T->st_h, T->st_d, sizeof(SysState) * N, cudaMemcpyDeviceToHost, c->stream)))
       return c->cuda_fail(e, "download system state");
     if ((e = cudaStreamSynchronize(c->stream))) return c->cuda_fail(e, "solver iteration");
-    if (iters_run > bound) return c->fail(6, "solver did not terminate within its iteration bound");
+    if (iters_run > bound) {
+      idle_all(c, T);
+      return c->fail(6, "solver did not terminate within its iteration bound");
+    }
 
     // ---- find finished systems
     std::vector<int> chain_slots;

@@ -105,6 +105,7 @@ Ctx* Ctx::lane(int i) {
     lanes.push_back(std::move(l));
   }
   Ctx* l = lanes[i].get();
+  l->iter_bound = iter_bound;
   l->have_gauge = have_gauge;
   l->gauge64 = gauge64;
   l->gauge_lo = gauge_lo;
@@ -252,6 +253,9 @@ class Tile : public TileBase {
     f.nreal = 24.0 * c->g.Vh;
     f.max_restarts = 8;
     f.first_approx = std::is_same<Ts, double>::value ? 0 : 1;
+    // tmp64 is a buffer of its own in the mixed precisions (FP64 storage shares it with tmp,
+    // which the other systems' iterations overwrite)
+    f.hx_kept = std::is_same<Ts, double>::value ? 0 : 1;
     const dim3 grid(N, FIN_SPLIT);
     switch (fin_values(op)) {
       case 1: fin_kernel<1><<<grid, 256, 0, c->stream>>>(f, op); break;
@@ -431,9 +435,15 @@ class Tile : public TileBase {
   cudaError_t enqueue_recon() override {
     L1.stream = c->stream;
     LW.stream = c->stream;
-    // x_o = A^-1 (z_o - D_oe x_e)
+    // x_o = A^-1 (z_o - D_oe x_e): from the H_oe x_e that the final FP64 residual left in tmp64 where
+    // it is still there (a vector operation), else by an FP64 hop
+    BlasArgs b = blas(MASK_HARVEST_HX, tmp64, nullptr, false, true);
+    b.x_hi = x_o;
+    b.src2 = z_o;
+    cudaError_t e = launch_blas<Ts>(OP_RECON, b, LW);
+    if (e) return e;
     return hop_hi(COEF_RECON, DOT_NONE,
-                  hop(x_o, x_hi, z_o, nullptr, nullptr, nullptr, 1, MASK_HARVEST, false, true, true), lwh());
+                  hop(x_o, x_hi, z_o, nullptr, nullptr, nullptr, 1, MASK_HARVEST_HOP, false, true, true), lwh());
   }
 
   cudaError_t enqueue_verify() override {

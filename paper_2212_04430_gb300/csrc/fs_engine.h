@@ -158,6 +158,7 @@ struct Ctx {
   bool shared = false;  // a lane: the gauge copies and contraction paths are not its own
   Ctx* lane(int i);
   std::map<int, int> tuned_tile;  // autotuned systems per tile, key: prec * 100 + nr
+  long long iter_bound = 0;       // watchdog of the host solve loops (iterations); 0: built-in bound
 };
 
 // The contraction's straight z-paths W(x, x + q z) for the displacements q > 0 in pmask,

@@ -45,7 +45,7 @@ template <> struct DotK<DOT_NORM> { static constexpr int K = 1; };
 // (FLAG_CHECK) is MASK_UPDATE_LATER whatever its index
 enum Mask { MASK_ALL = 0, MASK_ACTIVE = 1, MASK_UPDATE = 2, MASK_INIT = 3, MASK_HARVEST = 4, MASK_CG = 5,
             MASK_CG_CHECK = 6, MASK_HPE = 7, MASK_UPDATE_FIRST = 8, MASK_UPDATE_LATER = 9,
-            MASK_UPDATE_CORR = 10 };
+            MASK_UPDATE_CORR = 10, MASK_HARVEST_HX = 11, MASK_HARVEST_HOP = 12 };
 
 __device__ __forceinline__ bool selected(const SysState* st, int sys, int mask) {
   if (mask == MASK_ALL) return true;
@@ -65,6 +65,9 @@ __device__ __forceinline__ bool selected(const SysState* st, int sys, int mask) 
   if (mask == MASK_CG_CHECK) return s == SYS_ACTIVE && (f & FLAG_CG) && (f & FLAG_UPDATE);
   if (mask == MASK_INIT) return (f & FLAG_INIT) != 0;
   if (mask == MASK_HPE) return (f & FLAG_HPE) != 0;
+  // harvested systems split by whether H_oe x_e of the final residual is still at hand
+  if (mask == MASK_HARVEST_HX) return (f & FLAG_HARVEST) && (f & FLAG_HX);
+  if (mask == MASK_HARVEST_HOP) return (f & FLAG_HARVEST) && !(f & FLAG_HX);
   return (f & FLAG_HARVEST) != 0;
 }
 

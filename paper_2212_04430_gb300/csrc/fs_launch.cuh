@@ -125,6 +125,7 @@ cudaError_t launch_blas(int op, const BlasArgs& a, const Launch& l) {
     case OP_ZEROX: blas_kernel<Ts, Tx, Tm, OP_ZEROX, true><<<grid, block, 0, l.stream>>>(a); break;
     case OP_SETR: blas_kernel<Ts, Tx, Tm, OP_SETR, true><<<grid, block, 0, l.stream>>>(a); break;
     case OP_NORM64: blas_kernel<Ts, Tx, Tm, OP_NORM64, true><<<grid, block, 0, l.stream>>>(a); break;
+    case OP_RECON: blas_kernel<Ts, Tx, Tm, OP_RECON, true><<<grid, block, 0, l.stream>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   note_launch();

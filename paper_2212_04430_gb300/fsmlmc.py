@@ -29,7 +29,7 @@ EXPORTS = ["fs_ctx_create", "fs_ctx_destroy", "fs_last_error", "fs_set_stream", 
            "fs_sample_allocation", "fs_eval_grid", "fs_tuned_tile", "fs_probing_colors",
            "variance_sample_probed", "shifted_solve_dev", "fs_hpe_exact_trace",
            "mlmc_level_traces", "fs_server_set_admission", "fs_trace_total", "fs_sampled_level_variances",
-           "fs_measure_peak", "fs_profile_read_fp64"]
+           "fs_measure_peak", "fs_profile_read_fp64", "fs_set_iteration_bound"]
 JOB_MAX_LEVELS = 16
 
 
@@ -76,7 +76,7 @@ class ServerReport(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_longlong), ("queued", ctypes.c_longlong), ("active", ctypes.c_longlong),
                 ("solves", ctypes.c_longlong), ("reserved_bytes", ctypes.c_size_t), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
-                ("solves_per_s", ctypes.c_double)]
+                ("solves_per_s", ctypes.c_double), ("gauge_reuses", ctypes.c_longlong)]
 
 
 _lib = None
@@ -117,6 +117,7 @@ def load_library(path=LIB_PATH):
         "fs_profile_enable": (I, [P, I]),
         "fs_profile_read": (I, [P, ctypes.POINTER(ctypes.c_longlong), dp, dp, dp]),
         "fs_profile_read_fp64": (I, [P, ctypes.POINTER(ctypes.c_longlong), dp, dp]),
+        "fs_set_iteration_bound": (I, [P, ctypes.c_longlong]),
         "fs_kernel_launches": (ctypes.c_longlong, []),
         "wilson_dslash_noalloc": (I, [ip, I, D, D, P, P, P, I, P]),
         "fs_server_create": (I, [ctypes.POINTER(P), I, ctypes.c_size_t, I]),
@@ -281,9 +282,10 @@ class Context:
                     allow_noconv=True)
         return [_stats(s) for s in st[:sig.size * nrhs]]
 
-    def mlmc_level_trace(self, m, sigmas, gamma, p, n_samples, seed, job=0, estimator="diff", colors=None,
+    def mlmc_level_trace(self, m, sigmas, gamma, p, n_samples, seed, job=0, estimator="split_even", colors=None,
                          ncolors=None, dilute=False, hpe_order=0, **kw):
-        """Level traces; colors ([V] probing colours, canonical order) and dilute (full spin-colour
+        """Level traces (estimator: "split_even" by default, Eq. (fs_trace_est), measured cheapest on the
+        16^3x32 job; "diff" and "product" are the other two); colors ([V] probing colours, canonical order) and dilute (full spin-colour
         dilution) make every sample the sum of the estimator over its pieces; hpe_order = K uses
         the hopping parameter expansion on the last level when m + sigma_L > 0. A sequence p gives
         the traces for every displacement from the same solves (mlmc_level_traces): a list of
@@ -387,6 +389,10 @@ class Context:
         self._check(self.lib.fs_profile_read(self.h, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by),
                                              ctypes.byref(ss)))
         return {"launches": n.value, "ms": ms.value, "bytes": by.value, "site_systems": ss.value}
+
+    def set_iteration_bound(self, bound):
+        """Watchdog of the host solve loops (0: the built-in bound); FS_ERR_TIMEOUT when exceeded."""
+        self._check(self.lib.fs_set_iteration_bound(self.h, int(bound)))
 
     def profile_read_fp64(self):
         n = ctypes.c_longlong()
@@ -534,8 +540,8 @@ class Server:
         if rc != FS_OK:
             raise FsError(rc, "fs_server_create failed")
 
-    def submit(self, dims, U, m, sigmas, gamma, p, n_samples, seed, job=0, estimator="diff", bc_t=-1, colors=None,
-               ncolors=None, dilute=False, hpe_order=0, **kw):
+    def submit(self, dims, U, m, sigmas, gamma, p, n_samples, seed, job=0, estimator="split_even", bc_t=-1,
+               colors=None, ncolors=None, dilute=False, hpe_order=0, **kw):
         """Queue one trace job (arrays are copied); returns the ticket."""
         u = _real(U)
         sig = np.ascontiguousarray(sigmas, dtype=np.float64)
@@ -625,7 +631,7 @@ def shifted_solve(ctx, m, sigmas, b, **kw):
     return ctx.shifted_solve(m, sigmas, b, **kw)
 
 
-def mlmc_level_trace(ctx, m, sigmas, gamma, p, n_samples, seed, job=0, estimator="diff", **kw):
+def mlmc_level_trace(ctx, m, sigmas, gamma, p, n_samples, seed, job=0, estimator="split_even", **kw):
     return ctx.mlmc_level_trace(m, sigmas, gamma, p, n_samples, seed, job, estimator, **kw)
 
 

@@ -89,3 +89,35 @@ def test_fallback_inside_level_traces(est):
     for lev in range(2):
         assert sample_err(out["samples"][lev], ref[lev]) < 1e-7, lev
     ctx.close()
+
+
+def test_iteration_bound_runs_out_with_timeout_and_the_context_recovers():
+    """The host solve loops' watchdog (fs_set_iteration_bound), made to run out on the host: a
+    bound of 8 BiCGStab iterations is far below what a 1e-10 solve needs, so the call returns
+    FS_ERR_TIMEOUT with its message; no GPU fault or device-side injection is involved. The
+    context stays usable: with the built-in bound restored the same solve, and a level trace on
+    several lanes, reach their tolerance (the oracle's residual)."""
+    dims = (4, 4, 4, 4)
+    u = inputs.gauge_field(dims, "haar", seed=1000)
+    b = inputs.random_spinor(dims, 23, nvec=6)
+    ctx = make_ctx(dims, u)
+    kw = dict(prec="f16", tol=1e-10, rhs_tile=4)
+    ctx.set_iteration_bound(8)
+    with pytest.raises(pkg.FsError) as e:
+        ctx.shifted_solve(-0.4, [0.05], b, **kw)
+    assert e.value.code == pkg.fsmlmc.FS_ERR_TIMEOUT
+    assert "iteration bound" in str(e.value)
+    with pytest.raises(pkg.FsError) as e:
+        ctx.mlmc_level_trace(-0.4, [0.05, 0.4], np.eye(4), 0, [6, 6], seed=31, job=2, lanes=2, **kw)
+    assert e.value.code == pkg.fsmlmc.FS_ERR_TIMEOUT
+    with pytest.raises(pkg.FsError) as e:
+        ctx.set_iteration_bound(-1)
+    assert e.value.code == pkg.fsmlmc.FS_ERR_ARG
+    ctx.set_iteration_bound(0)
+    x, st, rc = ctx.shifted_solve(-0.4, [0.05], b, **kw)
+    assert rc == 0
+    for k in range(6):
+        assert rel_resid(u, x[0, k], b[k], -0.4, 0.05, dims) <= 1.05e-10, k
+    out = ctx.mlmc_level_trace(-0.4, [0.05, 0.4], np.eye(4), 0, [6, 6], seed=31, job=2, lanes=2, **kw)
+    assert out["rc"] == 0
+    ctx.close()

@@ -61,7 +61,8 @@ def test_config3_16x32_level_samples_and_residuals():
     sig = [0.005, 0.03, 0.15, 0.6]
     m, p, seed, job = -0.35, 4, 2003, 77
     kw = dict(prec="f16", tol=1e-8, rhs_tile=32, link_compress=12)
-    out = ctx.mlmc_level_trace(m, sig, pkg.gamma_matrix("g3"), p, [2, 2, 2, 2], seed=seed, job=job, **kw)
+    out = ctx.mlmc_level_trace(m, sig, pkg.gamma_matrix("g3"), p, [2, 2, 2, 2], seed=seed, job=job, estimator="diff",
+                               **kw)
     assert out["rc"] == 0
     # sampled noise of the job, bit-exact at full size
     for lev in (0, 3):

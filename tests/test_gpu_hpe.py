@@ -60,7 +60,8 @@ def test_last_level_with_the_expansion(p, K):
     g = pkg.gamma_matrix("g3")
     go = odirac.gamma_product(["g3"])
     ctx = make_ctx(dims, u)
-    out = ctx.mlmc_level_trace(m, sig, g, p, n, seed=21, job=1, hpe_order=K, prec="f64", tol=1e-12, rhs_tile=16)
+    out = ctx.mlmc_level_trace(m, sig, g, p, n, seed=21, job=1, hpe_order=K, estimator="diff", prec="f64", tol=1e-12,
+                               rhs_tile=16)
     assert out["rc"] == 0
     solver = oest.make_dense_solver(u, m, dims)
     ref, _ = _oracle_last_level(u, m, sig[1], go, p, K, n, 21, 1, dims, solver)

@@ -236,7 +236,7 @@ def test_mlmc_dense_expectation_config1():
     sig = [0.0, 0.4]
     n = [256, 256]
     ctx = make_ctx(dims, u)
-    out = ctx.mlmc_level_trace(-0.4, sig, np.eye(4), 0, n, seed=2001, job=1, prec="f32", tol=1e-10)
+    out = ctx.mlmc_level_trace(-0.4, sig, np.eye(4), 0, n, seed=2001, job=1, estimator="diff", prec="f32", tol=1e-10)
     mats = oest.exact_level_matrices(u, -0.4, sig, odirac.IDENT4, 0, dims, -1, oest.DIFF)
     for lev in range(2):
         exact = np.trace(mats[lev])
