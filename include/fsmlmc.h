@@ -168,6 +168,12 @@ FS_API size_t fs_ctx_device_bytes(const fs_ctx* ctx);
    per precision and link format times a BiCGStab iteration per system on tiles of 8, 16, 32
    and 64 systems (at most the call's system count) and keeps the fastest for the context. */
 FS_API int fs_tuned_tile(const fs_ctx* ctx, int prec, int link_compress);
+/* The whole tuned shape: the tile as above and, for tiles of 32-system chunks in the inner
+   precisions (the persistent hop kernel), the ring depth and resident blocks per SM the same trial
+   chose among {default, 3} x {as many as fit, 2} (0 = the default); all 0 if it has not run. The
+   shape never changes a result: every system is computed the same way in every launch shape. */
+FS_API int fs_tuned_shape(const fs_ctx* ctx, int prec, int link_compress, int* tile, int* ring_depth,
+                          int* blocks_per_sm);
 
 /* Upload the gauge field U (host, [4][V][3][3][2] doubles). Builds the FP64 copy used
  * for true residuals and contractions and the lower-precision copies on demand.

@@ -328,6 +328,23 @@ int fs_set_stream(fs_ctx* ctx, void* stream) {
 
 size_t fs_ctx_device_bytes(const fs_ctx* ctx) { return ctx ? ctx->c.device_bytes() : 0; }
 
+int fs_tuned_shape(const fs_ctx* ctx, int prec, int link_compress, int* tile, int* ring_depth, int* blocks_per_sm) {
+  if (!ctx || !tile || !ring_depth || !blocks_per_sm) return FS_ERR_ARG;
+  const int nr = prec == FS_PREC_F64 ? 18 : (link_compress == 0 ? 18 : link_compress);
+  *tile = 0;
+  *ring_depth = 0;
+  *blocks_per_sm = 0;
+  auto it = ctx->c.tuned_tile.find(prec * 100 + nr);
+  if (it == ctx->c.tuned_tile.end()) return FS_OK;
+  *tile = it->second;
+  auto sh = ctx->c.tuned_shape.find((long long)(prec * 100 + nr) * 1000 + it->second);
+  if (sh != ctx->c.tuned_shape.end()) {
+    *ring_depth = sh->second.depth;
+    *blocks_per_sm = sh->second.blocks;
+  }
+  return FS_OK;
+}
+
 int fs_tuned_tile(const fs_ctx* ctx, int prec, int link_compress) {
   if (!ctx) return 0;
   const int nr = prec == FS_PREC_F64 ? 18 : (link_compress == 0 ? 18 : link_compress);

@@ -123,12 +123,10 @@ int autotune_tile(Ctx* c, const SolveOpts& o, int nmax) {
   SolveOpts to = o;
   to.max_iter = 1 << 20;  // no system stops during the trial
   to.delta = 0.0;         // and none takes a reliable update (per system, the same for every tile)
-  double best_t = 0.0;
-  int best = 0;
-  for (int N : cand) {
-    if (N > nmax) break;
-    TileBase* T = c->tile(o.prec, N, o.nr);
-    if (!T) break;  // no room for a tile this large
+  // fills T with Z4 right-hand sides, runs 4 untimed and 8 timed BiCGStab iterations on the graph
+  // path and returns their milliseconds (every slot left idle afterwards); < 0 on failure
+  auto trial = [&](TileBase* T) -> float {
+    const int N = T->N;
     std::vector<int> all(N);
     for (int j = 0; j < N; j++) {
       all[j] = j;
@@ -152,7 +150,6 @@ int autotune_tile(Ctx* c, const SolveOpts& o, int nmax) {
     if (!e) e = cudaEventSynchronize(e1);
     float ms = 0.f;
     if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
-    // leave every slot idle for the solver
     for (int j = 0; j < N; j++) {
       memset(&T->st_h[j], 0, sizeof(SysState));
       T->st_h[j].status = SYS_IDLE;
@@ -160,11 +157,24 @@ int autotune_tile(Ctx* c, const SolveOpts& o, int nmax) {
     if (!e) e = upload_slots(c, T, all);
     if (!e) e = cudaStreamSynchronize(c->stream);
     if (e) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
       c->cuda_fail(e, "tile autotuner");
-      return 0;
+      return -1.f;
     }
+    return ms;
+  };
+  auto done = [&](int r) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return r;
+  };
+  double best_t = 0.0;
+  int best = 0;
+  for (int N : cand) {
+    if (N > nmax) break;
+    TileBase* T = c->tile(o.prec, N, o.nr);
+    if (!T) break;  // no room for a tile this large
+    const float ms = trial(T);
+    if (ms < 0.f) return done(0);
     const double per = ms / (8.0 * N);
     // keep only the best tile so far: at most two candidates hold device memory at once
     if (best == 0 || per < best_t) {
@@ -175,10 +185,29 @@ int autotune_tile(Ctx* c, const SolveOpts& o, int nmax) {
       c->tiles.erase(((long long)o.prec * 1000 + N) * 100 + o.nr);
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  // the launch shape of the persistent hop (tiles of 32-system chunks in the inner precision):
+  // ring depth and resident blocks per SM, timed on the chosen tile in the same way
+  if (best > 0 && best % 32 == 0 && o.prec != PREC_F64) {
+    TileBase* T = c->tile(o.prec, best, o.nr);
+    if (T) {
+      static const PkShape shapes[] = {{0, 0}, {3, 0}, {0, 2}, {3, 2}};
+      PkShape pick{};
+      float pick_ms = 0.f;
+      for (const PkShape& sh : shapes) {
+        T->set_shape(sh);
+        const float ms = trial(T);
+        if (ms < 0.f) return done(0);
+        if (pick_ms == 0.f || ms < pick_ms) {
+          pick_ms = ms;
+          pick = sh;
+        }
+      }
+      T->set_shape(pick);
+      c->tuned_shape[(long long)key * 1000 + best] = pick;
+    }
+  }
   if (best > 0) c->tuned_tile[key] = best;
-  return best;
+  return done(best);
 }
 
 // Exact low orders of the hopping parameter expansion. D + s = A (1 - kappa H), so

@@ -106,6 +106,7 @@ Ctx* Ctx::lane(int i) {
   }
   Ctx* l = lanes[i].get();
   l->iter_bound = iter_bound;
+  l->tuned_shape = tuned_shape;
   l->have_gauge = have_gauge;
   l->gauge64 = gauge64;
   l->gauge_lo = gauge_lo;
@@ -268,10 +269,20 @@ class Tile : public TileBase {
     return cudaGetLastError();
   }
 
+  void set_shape(const PkShape& s) override {
+    if (s.depth == shape.depth && s.blocks == shape.blocks) return;
+    shape = s;
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+    gk = 0;
+  }
+
   // Timed hop launch in the inner precision (the kernel the roofline is about).
   cudaError_t hop_lo(int coef, int dot, const HopArgs& a, int nextra) {
     HopProfile& pf = c->prof;
     LH.stream = c->stream;
+    LH.pk_depth = shape.depth;
+    LH.pk_blocks = shape.blocks;
     if (!pf.enabled) return launch_hop<Ts>(coef, dot, nr, a, LH);
     cudaEvent_t e0, e1;
     if (!pf.pool.empty()) {
@@ -619,6 +630,8 @@ TileBase* Ctx::tile(int prec, int N, int nr) {
     if (t->alloc(this, N, nr) != 0) return nullptr;
   }
   TileBase* raw = t.get();
+  auto sh = tuned_shape.find((long long)(prec * 100 + nr) * 1000 + N);
+  if (sh != tuned_shape.end()) raw->set_shape(sh->second);
   tiles[key] = std::move(t);
   return raw;
 }

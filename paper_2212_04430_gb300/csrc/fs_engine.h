@@ -30,6 +30,13 @@ struct Launch {
   int grid_y;
   int block;
   cudaStream_t stream;
+  int pk_depth = 0;   // persistent FP16/BF16/FP32 hop: ring depth (0: the default of its storage)
+  int pk_blocks = 0;  // its resident blocks per SM (0: as many as fit)
+};
+
+// Launch shape of the persistent hop picked by the autotuner for a (precision, link format, tile).
+struct PkShape {
+  int depth = 0, blocks = 0;
 };
 
 template <typename Ts> cudaError_t launch_hop(int coef, int dot, int nr, const HopArgs& a, const Launch& l);
@@ -71,6 +78,9 @@ constexpr int PROF_SLOTS = 13;
 class TileBase {
  public:
   virtual ~TileBase() {}
+  // the persistent hop's launch shape; a change drops the captured iteration graph
+  virtual void set_shape(const PkShape& s) = 0;
+  PkShape shape;
   int N = 0;
   int nr = 18;
   int prec = 0;
@@ -158,6 +168,7 @@ struct Ctx {
   bool shared = false;  // a lane: the gauge copies and contraction paths are not its own
   Ctx* lane(int i);
   std::map<int, int> tuned_tile;  // autotuned systems per tile, key: prec * 100 + nr
+  std::map<long long, PkShape> tuned_shape;  // autotuned hop shape, key: (prec * 100 + nr) * 1000 + N
   long long iter_bound = 0;       // watchdog of the host solve loops (iterations); 0: built-in bound
 };
 

@@ -16,9 +16,14 @@ template <typename Ts> constexpr int hop_pf() { return sizeof(Ts) == 2 ? 4 : 3; 
 // Ring depth of the persistent paired kernel: four operands in flight for 16-bit storage
 // (measured on the 16^3x32 hop: 2 or 3 slots leave the 10-operand launches waiting on L2), which
 // keeps three 128-thread blocks resident per SM; FP32 storage has twice the bytes per operand.
-template <typename Ts, int C, int D>
+// The autotuner may pick the other depth of hop_pk_depths for a tile.
+template <typename Ts>
 constexpr int hop_pk_depth() {
   return sizeof(Ts) <= 2 ? 4 : 2;
+}
+template <typename Ts>
+constexpr int hop_pk_alt_depth() {
+  return 3;
 }
 
 struct PersistentGrid {
@@ -26,11 +31,11 @@ struct PersistentGrid {
   int blocks_per_sm = 0, nsm = 0;
 };
 
-// The persistent paired hop for 32-system chunks (hop_kernel_pk): 128-thread blocks of 8 sites,
-// as many as are resident (never more blocks than site chunks).
-template <typename Ts, typename Tg, typename Tm, int R, int C, int D>
-cudaError_t launch_hop_pk(const HopArgs& a, const Launch& l) {
-  constexpr int PF = hop_pk_depth<Ts, C, D>();
+// The persistent paired hop for 32-system chunks (hop_kernel_pk) at ring depth PF: 128-thread
+// blocks of 8 sites, as many as are resident (capped at l.pk_blocks per SM when set), never more
+// blocks than site chunks.
+template <typename Ts, typename Tg, int R, int C, int D, int PF>
+cudaError_t launch_hop_pk_at(const HopArgs& a, const Launch& l) {
   auto kern = hop_kernel_pk<Ts, Tg, R, C, D, PF>;
   const size_t smem = hop_pk_smem<Ts, PF, DotK<D>::K>();
   // thread-safe one-time set-up: shared-memory opt-in and the resident grid
@@ -45,11 +50,18 @@ cudaError_t launch_hop_pk(const HopArgs& a, const Launch& l) {
     return p;
   }();
   if (pg.err) return pg.err;
+  const int per_sm = l.pk_blocks > 0 ? std::min(l.pk_blocks, pg.blocks_per_sm) : pg.blocks_per_sm;
   const int gy = l.grid_y;
-  const int gx = std::max(1, std::min(a.sh.nchunk, pg.blocks_per_sm * pg.nsm / std::max(gy, 1)));
+  const int gx = std::max(1, std::min(a.sh.nchunk, per_sm * pg.nsm / std::max(gy, 1)));
   kern<<<dim3(gx, gy), 128, smem, l.stream>>>(a);
   note_launch();
   return cudaGetLastError();
+}
+
+template <typename Ts, typename Tg, typename Tm, int R, int C, int D>
+cudaError_t launch_hop_pk(const HopArgs& a, const Launch& l) {
+  if (l.pk_depth == hop_pk_alt_depth<Ts>()) return launch_hop_pk_at<Ts, Tg, R, C, D, hop_pk_alt_depth<Ts>()>(a, l);
+  return launch_hop_pk_at<Ts, Tg, R, C, D, hop_pk_depth<Ts>()>(a, l);
 }
 
 template <typename Ts, typename Tg, typename Tm, int R, int C, int D>

@@ -29,7 +29,7 @@ EXPORTS = ["fs_ctx_create", "fs_ctx_destroy", "fs_last_error", "fs_set_stream", 
            "fs_sample_allocation", "fs_eval_grid", "fs_tuned_tile", "fs_probing_colors",
            "variance_sample_probed", "shifted_solve_dev", "fs_hpe_exact_trace",
            "mlmc_level_traces", "fs_server_set_admission", "fs_trace_total", "fs_sampled_level_variances",
-           "fs_measure_peak", "fs_profile_read_fp64", "fs_set_iteration_bound"]
+           "fs_measure_peak", "fs_profile_read_fp64", "fs_set_iteration_bound", "fs_tuned_shape"]
 JOB_MAX_LEVELS = 16
 
 
@@ -118,6 +118,7 @@ def load_library(path=LIB_PATH):
         "fs_profile_read": (I, [P, ctypes.POINTER(ctypes.c_longlong), dp, dp, dp]),
         "fs_profile_read_fp64": (I, [P, ctypes.POINTER(ctypes.c_longlong), dp, dp]),
         "fs_set_iteration_bound": (I, [P, ctypes.c_longlong]),
+        "fs_tuned_shape": (I, [P, I, I, ip, ip, ip]),
         "fs_kernel_launches": (ctypes.c_longlong, []),
         "wilson_dslash_noalloc": (I, [ip, I, D, D, P, P, P, I, P]),
         "fs_server_create": (I, [ctypes.POINTER(P), I, ctypes.c_size_t, I]),
@@ -229,6 +230,14 @@ class Context:
         """Systems per tile the autotuner chose for this precision and link format (0: not run)."""
         p = PREC[prec] if isinstance(prec, str) else int(prec)
         return int(self.lib.fs_tuned_tile(self.h, p, int(link_compress)))
+
+    def tuned_shape(self, prec="f16", link_compress=18):
+        """(tile, ring depth, resident blocks per SM) the autotuner chose (0: default / not run)."""
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        t, d, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.fs_tuned_shape(self.h, p, int(link_compress), ctypes.byref(t), ctypes.byref(d),
+                                            ctypes.byref(b)))
+        return t.value, d.value, b.value
 
     def fs_set_gauge(self, U):
         u = _real(U)

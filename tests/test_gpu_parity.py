@@ -381,6 +381,33 @@ def test_autotuned_tile():
     ctx.close()
 
 
+def test_autotuned_launch_shape_changes_no_result():
+    """On tiles of 32-system chunks the autotuner also picks the persistent hop's ring depth and
+    resident blocks per SM (one of four shapes); a fresh context at the same tile, in the default
+    shape, gives bit-identical samples."""
+    dims = (8, 8, 8, 8)
+    u = inputs.gauge_field(dims, "smooth", seed=31, eps=0.3)
+    sig = [0.05, 0.4]
+    g = pkg.gamma_matrix("g3")
+    n = [48, 48]
+    kw = dict(prec="f16", tol=1e-8, link_compress=12)
+    ctx = make_ctx(dims, u)
+    auto = ctx.mlmc_level_trace(-0.2, sig, g, 1, n, seed=6, job=3, rhs_tile=0, **kw)
+    assert auto["rc"] == 0
+    t, depth, blocks = ctx.tuned_shape("f16", 12)
+    assert t in (8, 16, 32, 64)
+    if t % 32 == 0:
+        assert depth in (0, 3) and blocks in (0, 2), (depth, blocks)
+    else:
+        assert depth == 0 and blocks == 0
+    ctx.close()
+    fresh = make_ctx(dims, u)
+    fixed = fresh.mlmc_level_trace(-0.2, sig, g, 1, n, seed=6, job=3, rhs_tile=t, lanes=1, **kw)
+    for lev in range(2):
+        assert np.array_equal(auto["samples"][lev], fixed["samples"][lev]), lev
+    fresh.close()
+
+
 def test_new_gauge_field_rebuilds_the_contraction_paths():
     """The straight z-paths W(x, x + p z) are cached per gauge field: after fs_set_gauge with a
     new field, a contraction at p > 0 equals the one of a fresh context holding that field."""
