@@ -19,6 +19,7 @@ from .gauge import (
     smoothed_su3,
     gauge_field,
     unit_gauge,
+    abelian_field,
     random_gauge_rotation,
     gauge_transform,
     random_spinor,
@@ -31,6 +32,7 @@ __all__ = [
     "smoothed_su3",
     "gauge_field",
     "unit_gauge",
+    "abelian_field",
     "random_gauge_rotation",
     "gauge_transform",
     "random_spinor",

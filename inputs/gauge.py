@@ -79,6 +79,26 @@ def gauge_field(dims, kind="haar", seed=0, eps=0.3):
     return np.ascontiguousarray(links.reshape(4, v, 3, 3))
 
 
+def abelian_field(dims, n=1, mu=0, nu=1):
+    """A constant abelian field strength in the (mu, nu) plane, embedded as a phase times the
+    3x3 identity: every plaquette U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag equals e^{iB},
+    B = 2 pi n / (L_mu L_nu) (the flux through each periodic plane is quantised). Landau gauge:
+    U_nu(x) = e^{i B x_mu}, U_mu(x) = 1 except on the last mu slice, U_mu = e^{-i B L_mu x_nu}
+    there; the other links are 1. Returns (links complex128[4][V][3][3], B)."""
+    lx, ly, lz, lt = dims
+    L = (lx, ly, lz, lt)
+    v = lattice_volume(dims)
+    s = np.arange(v)
+    c = np.stack([s % lx, (s // lx) % ly, (s // (lx * ly)) % lz, s // (lx * ly * lz)])
+    b = 2.0 * np.pi * n / (L[mu] * L[nu])
+    ph = np.ones((4, v), dtype=np.complex128)
+    ph[nu] = np.exp(1j * b * c[mu])
+    last = c[mu] == L[mu] - 1
+    ph[mu] = np.where(last, np.exp(-1j * b * L[mu] * c[nu]), 1.0)
+    links = ph[:, :, None, None] * np.eye(3, dtype=np.complex128)
+    return np.ascontiguousarray(links), b
+
+
 def random_gauge_rotation(dims, seed):
     """Haar-random g(x) in SU(3) per site, complex128[V][3][3]."""
     rng = np.random.Generator(np.random.PCG64(seed))

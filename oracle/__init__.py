@@ -19,6 +19,7 @@ Modules:
   estimators  level traces (Eq. fs_trace_est), practical variance
               (Eq. practical_variance), variance sampling (Sec. 3.1 algorithm)
   freefield   momentum-space closed form for free-field traces and spectrum
+  clover      the clover (Sheikholeslami-Wohlert) term of the Wilson-clover operator
 """
 
-from . import dirac, philox, solve, estimators, freefield  # noqa: F401
+from . import dirac, philox, solve, estimators, freefield, clover  # noqa: F401

@@ -66,10 +66,11 @@ def exact_var_paper(a):
     return 2.0 * exact_z4_variance(a)
 
 
-def make_solver(u, m, dims, bc_t=-1, tol=1e-12):
-    """Returns solve(z, sigma) -> (D + sigma)^-1 z by BiCGStab (canonical flat arrays)."""
+def make_solver(u, m, dims, bc_t=-1, tol=1e-12, cterm=None):
+    """Returns solve(z, sigma) -> (D + sigma)^-1 z by BiCGStab (canonical flat arrays); with
+    cterm (`clover.clover_term`) the operator is the Wilson-clover D_sw."""
     def _solve(z, sigma):
-        res = solve.shifted_solve(u, z, m, sigma, dims, bc_t, tol=tol)
+        res = solve.shifted_solve(u, z, m, sigma, dims, bc_t, tol=tol, cterm=cterm)
         if not res.converged:
             raise RuntimeError("oracle BiCGStab did not converge (sigma=%g, resid=%g)"
                                % (sigma, res.rel_resid))
@@ -77,14 +78,14 @@ def make_solver(u, m, dims, bc_t=-1, tol=1e-12):
     return _solve
 
 
-def make_dense_solver(u, m, dims, bc_t=-1):
+def make_dense_solver(u, m, dims, bc_t=-1, cterm=None):
     """Same interface, through dense LU inverses (tiny lattices only)."""
     cache = {}
     v = int(np.prod(dims))
 
     def _solve(z, sigma):
         if sigma not in cache:
-            cache[sigma] = solve.dense_inverse(u, m, sigma, dims, bc_t)
+            cache[sigma] = solve.dense_inverse(u, m, sigma, dims, bc_t, cterm)
         return (cache[sigma] @ z.ravel()).reshape(v, 4, 3)
     return _solve
 

@@ -63,14 +63,18 @@ def bicgstab(apply_A, b, tol=1e-12, max_iter=20000, x0=None):
     return SolveResult(x, it, true_r, bool(true_r <= 10 * tol))
 
 
-def shifted_solve(u, z, m, sigma, dims, bc_t=-1, tol=1e-12, max_iter=20000):
-    """x = (D + sigma I)^-1 z by BiCGStab. z, x: canonical flat complex128[V][4][3]."""
+def shifted_solve(u, z, m, sigma, dims, bc_t=-1, tol=1e-12, max_iter=20000, cterm=None):
+    """x = (D + sigma I)^-1 z by BiCGStab. z, x: canonical flat complex128[V][4][3].
+    cterm: the clover term of `clover` (D_sw in place of D_W), or None."""
     shp = dirac.lattice_shape(dims)
     ul = u.reshape((4,) + shp + (3, 3))
 
     def apply_A(vec):
         f = vec.reshape(shp + (4, 3))
-        return dirac.apply_D(ul, f, m, sigma, bc_t).ravel()
+        out = dirac.apply_D(ul, f, m, sigma, bc_t)
+        if cterm is not None:
+            out = out + np.einsum("...satb,...tb->...sa", cterm, f)
+        return out.ravel()
 
     res = bicgstab(apply_A, z.ravel(), tol=tol, max_iter=max_iter)
     res.x = res.x.reshape(z.shape)
@@ -99,11 +103,11 @@ def neighbour(dims, mu, step):
     return site_index(n, dims), wrapped
 
 
-def dense_operator(u, m, sigma, dims, bc_t=-1):
+def dense_operator(u, m, sigma, dims, bc_t=-1, cterm=None):
     """Dense matrix of D + sigma I, complex128[12V, 12V], index = 12 site + 3 spin + colour.
 
     Assembled block by block from the definition in `dirac`:
-      [x, x]      (4 + m + sigma) I
+      [x, x]      (4 + m + sigma) I            (+ the clover block C(x) for D_sw)
       [x, x+mu]   -1/2 (1 - gamma_mu) (x) U_mu(x)          (times bc_t on a t wrap)
       [x, x-mu]   -1/2 (1 + gamma_mu) (x) U_mu(x-mu)^dag   (times bc_t on a t wrap)
     """
@@ -111,6 +115,8 @@ def dense_operator(u, m, sigma, dims, bc_t=-1):
     mat = np.zeros((v, 12, v, 12), dtype=np.complex128)
     sites = np.arange(v)
     mat[sites, :, sites, :] += (4.0 + m + sigma) * np.eye(12)
+    if cterm is not None:
+        mat[sites, :, sites, :] += cterm.reshape(v, 12, 12)
     for mu in range(4):
         fwd, fw_wrap = neighbour(dims, mu, +1)
         bwd, bw_wrap = neighbour(dims, mu, -1)
@@ -124,8 +130,8 @@ def dense_operator(u, m, sigma, dims, bc_t=-1):
     return mat.reshape(12 * v, 12 * v)
 
 
-def dense_inverse(u, m, sigma, dims, bc_t=-1):
-    return np.linalg.inv(dense_operator(u, m, sigma, dims, bc_t))
+def dense_inverse(u, m, sigma, dims, bc_t=-1, cterm=None):
+    return np.linalg.inv(dense_operator(u, m, sigma, dims, bc_t, cterm))
 
 
 def dense_GammaOmega(u, gamma, p, dims):
