@@ -180,6 +180,22 @@ FS_API int fs_tuned_shape(const fs_ctx* ctx, int prec, int link_compress, int* t
  * FS_ERR_INPUT if U holds a non-finite value. */
 FS_API int fs_set_gauge(fs_ctx* ctx, const double* U);
 
+/* The Wilson-clover operator (Sec. 4 computes with the clover discretisation): with c_sw != 0
+ * every operation of ctx below (wilson_dslash, the solves, the trace estimators) applies
+ *   D_sw + sigma I = D + sigma I + C,   C(x) = (c_sw / 2) sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x),
+ * sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu], F_{mu nu} = (Q_{mu nu} - Q_{mu nu}^dag) / (8i), Q_{mu nu}(x)
+ * the sum of the four counter-clockwise plaquettes of the (mu, nu) plane at x (the paper states no
+ * normalisation: this is the reading). C is Hermitian, commutes with gamma_5 and is eigen-
+ * decomposed once per gauge field into a table of V Vh complex 6x6 blocks (about 5.6 KB per
+ * site in FP64 + FP32), so that (A + C)^-1 for every shift costs two 6x6 products per chirality.
+ * The table is built now if a gauge field is set, else by the next fs_set_gauge, and rebuilt by
+ * every fs_set_gauge; c_sw = 0 frees it and restores the Wilson operator. With the clover term
+ * the reliable updates are all FP64 and there is no CGNR fallback; the hopping parameter
+ * expansion (hpe_order, fs_hpe_exact_trace) is refused with FS_ERR_ARG, and
+ * wilson_dslash_noalloc stays the Wilson operator. FS_ERR_INPUT for a non-finite c_sw,
+ * FS_ERR_STATE on a lane, 3 when the table does not fit. */
+FS_API int fs_set_clover(fs_ctx* ctx, double c_sw);
+
 /* ---- the operations of the paper -------------------------------------------------- */
 
 /* out_k = (D + sigma I) in_k for k < nrhs, full lattice (the operator of

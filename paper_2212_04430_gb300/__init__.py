@@ -14,6 +14,7 @@ from .fsmlmc import (  # noqa: F401
     load_library,
     fs_ctx_create,
     fs_set_gauge,
+    fs_set_clover,
     wilson_dslash,
     shifted_solve,
     mlmc_level_trace,

@@ -55,6 +55,8 @@ void release(Ctx& c) {
     if (c.gauge64) cudaFree(c.gauge64);
     if (c.wline) cudaFree(c.wline);
     for (auto& kv : c.gauge_lo) cudaFree(kv.second);
+    if (c.clover64) cudaFree(c.clover64);
+    if (c.clover32) cudaFree(c.clover32);
   }
   if (c.colors_own && c.colors_d) cudaFree(c.colors_d);
   if (c.canon_d) cudaFree(c.canon_d);
@@ -166,7 +168,8 @@ int resolve_params(Ctx& c, const fs_solve_params* p, int nsys, double m, Opts& o
   if (o.so.delta >= 1.0) return c.fail(FS_ERR_ARG, "delta must be < 1");
   o.so.verify = d.verify;
   o.so.check_every = 4;
-  if (d.fallback_iter < 0) o.so.cg_max_iter = 0;
+  // the CGNR fallback and the hopping parameter expansion are the Wilson operator's
+  if (d.fallback_iter < 0 || c.c_sw != 0.0) o.so.cg_max_iter = 0;
   else if (d.fallback_iter > 0) o.so.cg_max_iter = d.fallback_iter;
   else o.so.cg_max_iter = (int)std::min<long long>(4LL * o.so.max_iter, 1 << 30);
   int tile = d.rhs_tile;
@@ -393,6 +396,43 @@ int fs_set_gauge(fs_ctx* ctx, const double* U) {
   if (!e) e = cudaStreamSynchronize(c.stream);
   if (e) return c.cuda_fail(e, "fs_set_gauge");
   c.have_gauge = true;
+  if (c.c_sw != 0.0) {  // the clover table belongs to the field
+    if (int rc = fs::clover_build(&c, c.c_sw)) {
+      c.have_gauge = false;
+      return rc;
+    }
+  }
+  return FS_OK;
+}
+
+int fs_set_clover(fs_ctx* ctx, double c_sw) {
+  if (!ctx) return FS_ERR_ARG;
+  Ctx& c = ctx->c;
+  if (!std::isfinite(c_sw)) return c.fail(FS_ERR_INPUT, "non-finite c_sw");
+  if (c.shared) return c.fail(FS_ERR_STATE, "a lane takes its owner's clover term");
+  if (int rc = set_device(c)) return rc;
+  if (cudaError_t e = cudaStreamSynchronize(c.stream)) return c.cuda_fail(e, "fs_set_clover");
+  for (auto& l : c.lanes)
+    if (cudaError_t e = cudaStreamSynchronize(l->stream)) return c.cuda_fail(e, "fs_set_clover");
+  if (c_sw == 0.0) {
+    if (c.clover64) {
+      cudaFree(c.clover64);
+      cudaFree(c.clover32);
+      c.extra_bytes -= (size_t)2 * c.g.Vh * 2 * fs::CLV_REALS * (sizeof(double) + sizeof(float));
+    }
+    c.clover64 = nullptr;
+    c.clover32 = nullptr;
+    c.c_sw = 0.0;
+  } else if (c.have_gauge) {
+    if (int rc = fs::clover_build(&c, c_sw)) return rc;
+  } else {
+    c.c_sw = c_sw;  // built with the gauge field
+  }
+  for (auto& l : c.lanes) {
+    l->c_sw = c.c_sw;
+    l->clover64 = c.clover64;
+    l->clover32 = c.clover32;
+  }
   return FS_OK;
 }
 
@@ -539,6 +579,8 @@ int fs_hpe_exact_trace(fs_ctx* ctx, double m, double sigma, const double* gamma,
                        const fs_solve_params* params, double* out) {
   if (!ctx) return FS_ERR_ARG;
   Ctx& c = ctx->c;
+  if (c.c_sw != 0.0)
+    return c.fail(FS_ERR_ARG, "the hopping parameter expansion is the Wilson operator's (clover term set)");
   if (!gamma || !out) return c.fail(FS_ERR_ARG, "null pointer");
   if (!c.have_gauge) return c.fail(FS_ERR_STATE, "no gauge field set");
   if (K < 1 || K > 8) return c.fail(FS_ERR_ARG, "K must be in [1, 8]");
@@ -633,6 +675,8 @@ int mlmc_impl(Ctx& c, const fs_mlmc_params* P, const int* p_in, int np, double* 
   const int npieces = num_pieces(P);
   const int ncomp = P->dilute ? 12 : 1;
   if (P->hpe_order < 0 || P->hpe_order > 8) return c.fail(FS_ERR_ARG, "hpe_order must be in [0, 8]");
+  if (P->hpe_order > 0 && c.c_sw != 0.0)
+    return c.fail(FS_ERR_ARG, "the hopping parameter expansion is the Wilson operator's (clover term set)");
   // the expansion converges for A = 4 + m + sigma > 4 only (Sec. 3.1 uses it where m + s > 0)
   const bool hpe = P->hpe_order > 0 && P->m + P->sigma[L] > 0.0;
   // the exact low orders take Omega_0 = 1; a displacement of a whole period is a Polyakov loop
@@ -819,6 +863,8 @@ int variance_sample_impl(Ctx& c, double m, const double* s_hat, int ms, const do
                          int ncolors, int dilute, int hpe_order, double* VL, double* Vbar, double* a_out,
                          double* b_out, double* iters) {
   if (hpe_order < 0 || hpe_order > 8) return c.fail(FS_ERR_ARG, "hpe_order must be in [0, 8]");
+  if (hpe_order > 0 && c.c_sw != 0.0)
+    return c.fail(FS_ERR_ARG, "the hopping parameter expansion is the Wilson operator's (clover term set)");
   if (!s_hat || !gamma || !p || !VL || !Vbar) return c.fail(FS_ERR_ARG, "null pointer");
   if (ms < 1 || 2 * ms > fs::MAX_TILE) return c.fail(FS_ERR_ARG, "m_shifts must be in [1, 32]");
   if (np < 1 || np > fs::CONTRACT_MAXP) return c.fail(FS_ERR_ARG, "np must be in [1, 16]");

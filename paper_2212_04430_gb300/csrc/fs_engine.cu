@@ -115,6 +115,9 @@ Ctx* Ctx::lane(int i) {
   l->wline_cap = 0;  // never reallocated or freed by the lane
   l->colors_d = colors_d;
   l->colors_own = false;
+  l->c_sw = c_sw;
+  l->clover64 = clover64;
+  l->clover32 = clover32;
   return l;
 }
 
@@ -151,6 +154,7 @@ class Tile : public TileBase {
   double* fin_slice = nullptr;   // finalize slice sums [MAX_TILE][FIN_SPLIT][FIN_MAXV]
   unsigned* fin_count = nullptr; // finalize arrival tickets [MAX_TILE], zero between finalizes
   double *cg_p = nullptr, *cg_q = nullptr, *cg_g = nullptr, *cg_w = nullptr, *cg_r = nullptr;  // CGNR fallback
+  void* cw = nullptr;            // C x of the Wilson-clover operator (inner precision, tile layout)
   std::vector<void*> owned;
   // K BiCGStab iterations captured once and replayed (launch overhead dominates small lattices)
   cudaGraphExec_t gexec = nullptr;
@@ -227,9 +231,30 @@ class Tile : public TileBase {
     return 0;
   }
 
+  int clover_alloc() override {
+    if (cw) return 0;
+    cw = dalloc((size_t)24 * c->g.Vh * N * sizeof(Ts));
+    return cw ? 0 : 3;
+  }
+  bool clv() const { return c->c_sw != 0.0; }
+  // A clover pass over the systems of `mask`: the tile layout in the storage precision, or the
+  // FP64 system-major work list (sysmajor).
+  cudaError_t clover_pass(int mode, void* out, const void* in, const void* Y, int parity, int mask, bool gated,
+                          bool sysmajor) {
+    ClovArgs a{};
+    a.out = out; a.in = in; a.Y = Y;
+    a.table = (sysmajor || std::is_same<Ts, double>::value) ? (const void*)c->clover64 : (const void*)c->clover32;
+    a.st = st_d; a.gate = gated ? gate : nullptr;
+    a.g = c->g; a.sh = sysmajor ? sh1 : sh; a.parity = parity; a.mask = mask;
+    a.sysmajor = sysmajor ? 1 : 0;
+    if (sysmajor) return launch_clover<double>(mode, a, LW);
+    return launch_clover<Ts>(mode, a, L);
+  }
+
   HopArgs hop(void* out, const void* in, const void* X, const void* Y, const void* R, double* part, int p_out,
               int mask, bool gated, bool hi, bool sysmajor = false) {
     HopArgs a{};
+    a.clover = clv() ? 1 : 0;
     a.out = out; a.in = in; a.X = X; a.Y = Y; a.R = R;
     a.gauge = hi ? c->gauge64 : c->gauge_for(prec, nr);
     a.st = st_d; a.partial = part; a.gate = gated ? gate : nullptr; a.work = nullptr;
@@ -253,10 +278,11 @@ class Tile : public TileBase {
     f.target = 0.25;  // rms of a scaled residual entry (keeps FP16 away from both range limits)
     f.nreal = 24.0 * c->g.Vh;
     f.max_restarts = 8;
-    f.first_approx = std::is_same<Ts, double>::value ? 0 : 1;
+    // the Wilson-clover reliable updates are all FP64 and leave A_oo^-1 H_oe x_e in the scratch
+    f.first_approx = std::is_same<Ts, double>::value || clv() ? 0 : 1;
     // tmp64 is a buffer of its own in the mixed precisions (FP64 storage shares it with tmp,
     // which the other systems' iterations overwrite)
-    f.hx_kept = std::is_same<Ts, double>::value ? 0 : 1;
+    f.hx_kept = std::is_same<Ts, double>::value || clv() ? 0 : 1;
     const dim3 grid(N, FIN_SPLIT);
     switch (fin_values(op)) {
       case 1: fin_kernel<1><<<grid, 256, 0, c->stream>>>(f, op); break;
@@ -344,8 +370,13 @@ class Tile : public TileBase {
     L1.stream = c->stream;
     LW.stream = c->stream;
     cudaError_t e;
-    // bhat_e = z_e - D_eo A^-1 z_o, ||bhat||^2
-    if ((e = hop_hi(COEF_PREP, DOT_NORM, hop(bhat, z_o, z_e, nullptr, nullptr, pa, 0, MASK_INIT, false, true, true),
+    // bhat_e = z_e - D_eo A^-1 z_o, ||bhat||^2 (Wilson-clover: A_oo^-1 z_o by a clover pass first)
+    const double* zin = z_o;
+    if (clv()) {
+      if ((e = clover_pass(CLV_INV, tmp64, z_o, nullptr, 1, MASK_INIT, false, true))) return e;
+      zin = tmp64;
+    }
+    if ((e = hop_hi(COEF_PREP, DOT_NORM, hop(bhat, zin, z_e, nullptr, nullptr, pa, 0, MASK_INIT, false, true, true),
                     lwh()))) return e;
     if ((e = launch_blas<Ts>(OP_NORM64, blas(MASK_INIT, z_e, pb, false, true), LW))) return e;
     if ((e = launch_blas<Ts>(OP_NORM64, blas(MASK_INIT, z_o, pc, false, true), LW))) return e;
@@ -358,16 +389,24 @@ class Tile : public TileBase {
   cudaError_t enqueue_iter() override {
     L.stream = c->stream;
     cudaError_t e;
+    const bool cl = clv();
     // p was set by the previous iteration's OP_XRP, or by OP_SETR at a (re)start
     if ((e = hop_lo(COEF_PLAIN, DOT_NONE, hop(tmp, p, nullptr, nullptr, nullptr, nullptr, 1, MASK_ACTIVE, false,
                                               false), 0))) return e;
-    if ((e = hop_lo(COEF_MHAT, DOT_R, hop(v, tmp, p, nullptr, rhat, pa, 0, MASK_ACTIVE, false, false), 2)))
+    // Wilson-clover: M-hat p = (A + C_ee) p - H_eo (A + C_oo)^-1 H_oe p / 4, the site factors by passes
+    if (cl && ((e = clover_pass(CLV_INV, tmp, tmp, nullptr, 1, MASK_ACTIVE, false, false)) ||
+               (e = clover_pass(CLV_MUL, cw, p, nullptr, 0, MASK_ACTIVE, false, false))))
+      return e;
+    if ((e = hop_lo(COEF_MHAT, DOT_R, hop(v, tmp, p, cl ? cw : nullptr, rhat, pa, 0, MASK_ACTIVE, false, false), 2)))
       return e;
     if ((e = fin(FIN_ALPHA, MASK_ACTIVE, pa))) return e;
     if ((e = launch_blas<Ts>(OP_S, blas(MASK_ACTIVE, nullptr, nullptr, false), L))) return e;
     if ((e = hop_lo(COEF_PLAIN, DOT_NONE, hop(tmp, s, nullptr, nullptr, nullptr, nullptr, 1, MASK_ACTIVE, false,
                                               false), 0))) return e;
-    if ((e = hop_lo(COEF_MHAT, DOT_TS, hop(t, tmp, s, nullptr, rhat, pa, 0, MASK_ACTIVE, false, false), 2)))
+    if (cl && ((e = clover_pass(CLV_INV, tmp, tmp, nullptr, 1, MASK_ACTIVE, false, false)) ||
+               (e = clover_pass(CLV_MUL, cw, s, nullptr, 0, MASK_ACTIVE, false, false))))
+      return e;
+    if ((e = hop_lo(COEF_MHAT, DOT_TS, hop(t, tmp, s, cl ? cw : nullptr, rhat, pa, 0, MASK_ACTIVE, false, false), 2)))
       return e;
     if ((e = fin(FIN_OMEGA, MASK_ACTIVE, pa))) return e;
     if ((e = launch_blas<Ts>(OP_XRP, blas(MASK_ACTIVE, nullptr, nullptr, false), L))) return e;
@@ -385,8 +424,24 @@ class Tile : public TileBase {
     //    previous (FP64) update, held in x_o (free until the odd sites are reconstructed); the
     //    FP32 error is about eps32 A ||dx||, relative to the small dx instead of x.
     // The FP64 storage mode keeps FP64 throughout.
+    // The Wilson-clover operator takes every update in FP64: r = bhat - C_ee x - A x + H_eo A_oo^-1 H_oe x / 4,
+    // the clover parts by passes (x_o, free until the reconstruction, holds bhat - C_ee x).
     constexpr bool mixed = !std::is_same<Ts, double>::value;
-    if ((e = launch_blas<Ts>(OP_ACCX, blas(MASK_UPDATE, mixed ? x_o : nullptr, nullptr, true, true), LW))) return e;
+    if ((e = launch_blas<Ts>(OP_ACCX, blas(MASK_UPDATE, mixed && !cl ? x_o : nullptr, nullptr, true, true), LW)))
+      return e;
+    if (cl) {
+      if ((e = hop_hi(COEF_PLAIN, DOT_NONE,
+                      hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, MASK_UPDATE, true, true, true), lwh())))
+        return e;
+      if ((e = clover_pass(CLV_INV, tmp64, tmp64, nullptr, 1, MASK_UPDATE, true, true))) return e;
+      if ((e = clover_pass(CLV_SUB, x_o, x_hi, bhat, 0, MASK_UPDATE, true, true))) return e;
+      if ((e = hop_hi(COEF_TRUERES, DOT_NORM,
+                      hop(r_hi, tmp64, x_hi, x_o, nullptr, pa, 0, MASK_UPDATE, true, true, true), lwh())))
+        return e;
+      if ((e = fin(FIN_TRUE, MASK_UPDATE, pa))) return e;
+      if ((e = launch_blas<Ts>(OP_SETR, blas(MASK_UPDATE, r_hi, pa, true, true), LW))) return e;
+      return fin(FIN_UPDATE, MASK_UPDATE, pa);
+    }
     int later = MASK_UPDATE;
     if constexpr (mixed) {
       later = MASK_UPDATE_LATER;
@@ -422,7 +477,7 @@ class Tile : public TileBase {
       iters_eager++;
       return e;
     }
-    if (!gexec || gk != k) {
+    if (!gexec || gk != k || gclv != (int)clv()) {
       if (gexec) cudaGraphExecDestroy(gexec);
       gexec = nullptr;
       cudaGraph_t graph = nullptr;
@@ -437,22 +492,31 @@ class Tile : public TileBase {
       if (graph) cudaGraphDestroy(graph);
       if (e) return e;
       gk = k;
+      gclv = (int)clv();
     }
     note_launch((int)gnodes);
     return cudaGraphLaunch(gexec, c->stream);
   }
   int iters_eager = 0;
+  int gclv = -1;  // the clover term's state when the graph was captured
 
   cudaError_t enqueue_recon() override {
     L1.stream = c->stream;
     LW.stream = c->stream;
     // x_o = A^-1 (z_o - D_oe x_e): from the H_oe x_e that the final FP64 residual left in tmp64 where
     // it is still there (a vector operation), else by an FP64 hop
+    cudaError_t e;
+    if (clv()) {
+      // x_o = (A + C_oo)^-1 (z_o + H_oe x_e / 2)
+      if ((e = hop_hi(COEF_RECON, DOT_NONE,
+                      hop(x_o, x_hi, z_o, nullptr, nullptr, nullptr, 1, MASK_HARVEST, false, true, true), lwh())))
+        return e;
+      return clover_pass(CLV_INV, x_o, x_o, nullptr, 1, MASK_HARVEST, false, true);
+    }
     BlasArgs b = blas(MASK_HARVEST_HX, tmp64, nullptr, false, true);
     b.x_hi = x_o;
     b.src2 = z_o;
-    cudaError_t e = launch_blas<Ts>(OP_RECON, b, LW);
-    if (e) return e;
+    if ((e = launch_blas<Ts>(OP_RECON, b, LW))) return e;
     return hop_hi(COEF_RECON, DOT_NONE,
                   hop(x_o, x_hi, z_o, nullptr, nullptr, nullptr, 1, MASK_HARVEST_HOP, false, true, true), lwh());
   }
@@ -461,10 +525,18 @@ class Tile : public TileBase {
     L1.stream = c->stream;
     LW.stream = c->stream;
     cudaError_t e;
-    if ((e = hop_hi(COEF_FULLRES, DOT_NORM, hop(r_hi, x_o, x_hi, z_e, nullptr, pa, 0, MASK_HARVEST, false, true, true),
+    // r = z - (D + sigma) x on both parities; Wilson-clover: z - C x first, by a pass
+    const double *ye = z_e, *yo = z_o;
+    if (clv()) {
+      if ((e = clover_pass(CLV_SUB, r_hi, x_hi, z_e, 0, MASK_HARVEST, false, true))) return e;
+      if ((e = clover_pass(CLV_SUB, tmp64, x_o, z_o, 1, MASK_HARVEST, false, true))) return e;
+      ye = r_hi;
+      yo = tmp64;
+    }
+    if ((e = hop_hi(COEF_FULLRES, DOT_NORM, hop(r_hi, x_o, x_hi, ye, nullptr, pa, 0, MASK_HARVEST, false, true, true),
                     lwh())))
       return e;
-    if ((e = hop_hi(COEF_FULLRES, DOT_NORM, hop(tmp64, x_hi, x_o, z_o, nullptr, pb, 1, MASK_HARVEST, false, true, true),
+    if ((e = hop_hi(COEF_FULLRES, DOT_NORM, hop(tmp64, x_hi, x_o, yo, nullptr, pb, 1, MASK_HARVEST, false, true, true),
                     lwh())))
       return e;
     return fin(FIN_VERIFY, MASK_HARVEST, pa, pb);
@@ -518,9 +590,13 @@ class Tile : public TileBase {
     cudaError_t e;
     if ((e = launch_pack<Ts>(p, tmp, canon, vec_d, c->g, sh, L, false))) return e;
     const bool f64 = std::is_same<Ts, double>::value;
-    HopArgs he = hop(v, tmp, p, nullptr, nullptr, nullptr, 0, MASK_INIT, false, f64);
-    HopArgs ho = hop(s, p, tmp, nullptr, nullptr, nullptr, 1, MASK_INIT, false, f64);
+    const bool cl = clv();
+    // Wilson-clover: C x of each parity by a pass, added through Y (the field cw)
+    HopArgs he = hop(v, tmp, p, cl ? cw : nullptr, nullptr, nullptr, 0, MASK_INIT, false, f64);
+    HopArgs ho = hop(s, p, tmp, cl ? cw : nullptr, nullptr, nullptr, 1, MASK_INIT, false, f64);
+    if (cl && (e = clover_pass(CLV_MUL, cw, p, nullptr, 0, MASK_INIT, false, false))) return e;
     if ((e = hop_lo(COEF_DSLASH, DOT_NONE, he, 1))) return e;
+    if (cl && (e = clover_pass(CLV_MUL, cw, tmp, nullptr, 1, MASK_INIT, false, false))) return e;
     if ((e = hop_lo(COEF_DSLASH, DOT_NONE, ho, 1))) return e;
     return launch_unpack<Ts>(canon, v, s, vec_d, c->g, sh, L, false);
   }
@@ -607,7 +683,13 @@ class Tile : public TileBase {
 TileBase* Ctx::tile(int prec, int N, int nr) {
   const long long key = ((long long)prec * 1000 + N) * 100 + nr;
   auto it = tiles.find(key);
-  if (it != tiles.end()) return it->second.get();
+  if (it != tiles.end()) {
+    if (c_sw != 0.0 && it->second->clover_alloc() != 0) {
+      fail(3, "device allocation of the clover field failed");
+      return nullptr;
+    }
+    return it->second.get();
+  }
   std::unique_ptr<TileBase> t;
   switch (prec) {
     case PREC_F64: t.reset(new Tile<double>()); break;
@@ -630,6 +712,10 @@ TileBase* Ctx::tile(int prec, int N, int nr) {
     if (t->alloc(this, N, nr) != 0) return nullptr;
   }
   TileBase* raw = t.get();
+  if (c_sw != 0.0 && raw->clover_alloc() != 0) {
+    fail(3, "device allocation of the clover field failed");
+    return nullptr;
+  }
   auto sh = tuned_shape.find((long long)(prec * 100 + nr) * 1000 + N);
   if (sh != tuned_shape.end()) raw->set_shape(sh->second);
   tiles[key] = std::move(t);

@@ -13,6 +13,7 @@
 
 #include "fs_aux.cuh"
 #include "fs_blas.cuh"
+#include "fs_clover.cuh"
 #include "fs_hop.cuh"
 
 namespace fs {
@@ -45,6 +46,9 @@ template <typename Ts> cudaError_t launch_hop(int coef, int dot, int nr, const H
 // DOT_NORM only.
 cudaError_t launch_hop64_f32(int coef, int dot, const HopArgs& a, const Launch& l);
 template <typename Ts> cudaError_t launch_blas(int op, const BlasArgs& a, const Launch& l);
+// Clover passes (fs_clover.cuh): tile layout in the storage precision (FP32 table and arithmetic
+// for the inner precisions), or the FP64 system-major work list when a.sysmajor (Ts = double).
+template <typename Ts> cudaError_t launch_clover(int mode, const ClovArgs& a, const Launch& l);
 template <typename Ts> cudaError_t launch_pack(void* fe, void* fo, const double* canon, const int* vec,
                                                const Geom& g, const Shape& sh, const Launch& l, bool sysmajor);
 template <typename Ts> cudaError_t launch_unpack(double* canon, const void* fe, const void* fo, const int* vec,
@@ -96,6 +100,8 @@ class TileBase {
   double* x_hi = nullptr;    // solution, even sites (FP64)
   double* x_o = nullptr;     // solution, odd sites (FP64, after reconstruction)
   virtual int alloc(Ctx* c, int N, int nr) = 0;
+  // the field that holds C x for the Wilson-clover operator, allocated when the clover term is on
+  virtual int clover_alloc() = 0;
   virtual cudaError_t enqueue_rhs_from_canon(const double* canon) = 0;  // z <- canon[vec[j]] for INIT slots
   virtual cudaError_t enqueue_noise() = 0;  // z <- Z4 noise for INIT slots with a noise rhs
   virtual cudaError_t enqueue_init() = 0;
@@ -170,7 +176,14 @@ struct Ctx {
   std::map<int, int> tuned_tile;  // autotuned systems per tile, key: prec * 100 + nr
   std::map<long long, PkShape> tuned_shape;  // autotuned hop shape, key: (prec * 100 + nr) * 1000 + N
   long long iter_bound = 0;       // watchdog of the host solve loops (iterations); 0: built-in bound
+  // the clover term (Wilson-clover operator) when c_sw != 0: per-site tables of the gauge field
+  double c_sw = 0.0;
+  double* clover64 = nullptr;     // [2][Vh][2][CLV_REALS]
+  float* clover32 = nullptr;
 };
+
+// Builds c's clover tables from its FP64 gauge copy (fs_clover.cu); 0 or an error code.
+int clover_build(Ctx* c, double c_sw);
 
 // The contraction's straight z-paths W(x, x + q z) for the displacements q > 0 in pmask,
 // built once per gauge field (fs_engine.cu); 0 or an error code (message in c->err).

@@ -93,6 +93,7 @@ struct HopArgs {
   int p_out;
   int mask;
   int sysmajor;  // 1: every field operand in the system-major layout (hop_kernel only)
+  int clover;    // 1: the Wilson-clover operator (hop_kernel only; the site terms come from passes)
 };
 
 // ---- fixed-order arithmetic ------------------------------------------------------
@@ -448,7 +449,9 @@ __device__ __forceinline__ int selected_list(const SysState* st, int N, int mask
 // WL: system-major work-list launch (a.sysmajor); else the tile shape.
 // WL launches (system-major work lists) use 128-thread blocks: bounds for three of them per
 // SM leave the FP64 hop 168 registers; tile-shaped launches use 256-thread blocks.
-template <typename Ts, typename Tg, typename Tm, int NR, int COEF, int DOT, bool WL = false>
+// CLV: the Wilson-clover M-hat / D_sw epilogue, out = Y + A X + cb (H in) with Y = C X from a
+// clover pass (the other coefficient changes of the clover operator follow a.clover at run time).
+template <typename Ts, typename Tg, typename Tm, int NR, int COEF, int DOT, bool WL = false, bool CLV = false>
 __global__ void __launch_bounds__(WL ? 128 : 256, WL ? 3 : (sizeof(Tm) == 8 ? 2 : (sizeof(Ts) == 2 ? 3 : 2)))
     hop_kernel(HopArgs a) {
   if (a.gate != nullptr && *a.gate == 0) return;
@@ -467,11 +470,14 @@ __global__ void __launch_bounds__(WL ? 128 : 256, WL ? 3 : (sizeof(Tm) == 8 ? 2 
     Tm ca = 0, cb = 1;
     if (sel) {
       const SysState& s = a.st[sys];
-      if (COEF == COEF_MHAT) { ca = coef<Tm>(s, C_A); cb = coef<Tm>(s, C_MINV4A); }
+      // with the clover term the site factors A^-1 come from clover passes on the operands
+      // (in = A_oo^-1 H x, z_o pre-inverted, x_o inverted afterwards) and C x enters through Y
+      const bool cl = a.clover != 0;
+      if (COEF == COEF_MHAT) { ca = coef<Tm>(s, C_A); cb = cl ? (Tm)-0.25 : coef<Tm>(s, C_MINV4A); }
       else if (COEF == COEF_DSLASH) { ca = coef<Tm>(s, C_A); cb = (Tm)-0.5; }
-      else if (COEF == COEF_PREP) { ca = 1; cb = coef<Tm>(s, C_INV2A); }
-      else if (COEF == COEF_RECON) { ca = coef<Tm>(s, C_INVA); cb = coef<Tm>(s, C_INV2A); }
-      else if (COEF == COEF_TRUERES) { ca = coef<Tm>(s, C_MINVA); cb = coef<Tm>(s, C_INV4A); }
+      else if (COEF == COEF_PREP) { ca = 1; cb = cl ? (Tm)0.5 : coef<Tm>(s, C_INV2A); }
+      else if (COEF == COEF_RECON) { ca = cl ? (Tm)1 : coef<Tm>(s, C_INVA); cb = cl ? (Tm)0.5 : coef<Tm>(s, C_INV2A); }
+      else if (COEF == COEF_TRUERES) { ca = coef<Tm>(s, C_MINVA); cb = cl ? (Tm)0.25 : coef<Tm>(s, C_INV4A); }
       else if (COEF == COEF_FULLRES) { ca = coef<Tm>(s, C_MINVA); cb = (Tm)0.5; }
       else if (COEF == COEF_KAPPA) { cb = coef<Tm>(s, C_INV2A); }
     }
@@ -504,7 +510,7 @@ __global__ void __launch_bounds__(WL ? 128 : 256, WL ? 3 : (sizeof(Tm) == 8 ? 2 
       } else {
         Tm xv[24];
         make_field<Ts>(const_cast<void*>(a.X), g.Vh, sh.N, smj).load(site, sys, xv);
-        if constexpr (COEF == COEF_TRUERES || COEF == COEF_FULLRES) {
+        if constexpr (COEF == COEF_TRUERES || COEF == COEF_FULLRES || CLV) {
           // out = Y + ca X + cb (H in): two multiply-adds per entry
           Tm yv[24];
           make_field<Ts>(const_cast<void*>(a.Y), g.Vh, sh.N, smj).load(site, sys, yv);

@@ -86,6 +86,26 @@ cudaError_t launch_hop(int coef, int dot, int nr, const HopArgs& a, const Launch
   using Tg = typename GaugeOf<Ts>::T;
   using Tm = MathOf<Ts>;
   const dim3 grid(l.grid_x, l.grid_y), block(l.block);
+  // Wilson-clover M-hat and D_sw on the tile layout: the generic kernel with the Y operand (C X)
+#define FS_HOP_CLV(C, D, R)                                                                  \
+  if (coef == C && dot == D && nr == R) {                                                    \
+    hop_kernel<Ts, Tg, Tm, R, C, D, false, true><<<grid, block, 0, l.stream>>>(a);           \
+    note_launch();                                                                           \
+    return cudaGetLastError();                                                               \
+  }
+  if (a.clover && (coef == COEF_MHAT || coef == COEF_DSLASH)) {
+    if (a.sysmajor) return cudaErrorInvalidValue;  // the work-list forms are the Wilson operator's
+    FS_HOP_CLV(COEF_MHAT, DOT_R, 18)
+    FS_HOP_CLV(COEF_MHAT, DOT_TS, 18)
+    FS_HOP_CLV(COEF_DSLASH, DOT_NONE, 18)
+    if constexpr (!std::is_same<Ts, double>::value) {
+      FS_HOP_CLV(COEF_MHAT, DOT_R, 12)
+      FS_HOP_CLV(COEF_MHAT, DOT_TS, 12)
+      FS_HOP_CLV(COEF_DSLASH, DOT_NONE, 12)
+    }
+    return cudaErrorInvalidValue;
+  }
+#undef FS_HOP_CLV
 #define FS_HOP(C, D, R)                                                           \
   if (coef == C && dot == D && nr == R) {                                         \
     if (a.sysmajor) hop_kernel<Ts, Tg, Tm, R, C, D, true><<<grid, block, 0, l.stream>>>(a); \
@@ -145,6 +165,26 @@ cudaError_t launch_blas(int op, const BlasArgs& a, const Launch& l) {
 }
 
 template <typename Ts>
+cudaError_t launch_clover(int mode, const ClovArgs& a, const Launch& l) {
+  using Tm = MathOf<Ts>;
+  using Tc = typename std::conditional<std::is_same<Ts, double>::value, double, float>::type;
+  const dim3 grid(l.grid_x, l.grid_y), block(l.block);
+  if (a.sysmajor && !std::is_same<Ts, double>::value) return cudaErrorInvalidValue;  // FP64 fields only
+#define FS_CLV(M)                                                                                         \
+  if (mode == M) {                                                                                        \
+    if (a.sysmajor) clover_kernel<Ts, Tc, Tm, M, true><<<grid, block, 0, l.stream>>>(a);                 \
+    else clover_kernel<Ts, Tc, Tm, M, false><<<grid, block, 0, l.stream>>>(a);                           \
+    note_launch();                                                                                        \
+    return cudaGetLastError();                                                                            \
+  }
+  FS_CLV(CLV_MUL)
+  FS_CLV(CLV_SUB)
+  FS_CLV(CLV_INV)
+#undef FS_CLV
+  return cudaErrorInvalidValue;
+}
+
+template <typename Ts>
 cudaError_t launch_pack(void* fe, void* fo, const double* canon, const int* vec, const Geom& g, const Shape& sh,
                         const Launch& l, bool sysmajor) {
   pack_kernel<Ts><<<dim3(l.grid_x, l.grid_y), l.block, 0, l.stream>>>(fe, fo, canon, vec, g, sh, sysmajor);
@@ -174,6 +214,7 @@ cudaError_t launch_gauge_pack(void* out, const double* canon, const Geom& g, int
 #define FS_INSTANTIATE(TS)                                                                                   \
   template cudaError_t launch_hop<TS>(int, int, int, const HopArgs&, const Launch&);                        \
   template cudaError_t launch_blas<TS>(int, const BlasArgs&, const Launch&);                                \
+  template cudaError_t launch_clover<TS>(int, const ClovArgs&, const Launch&);                              \
   template cudaError_t launch_pack<TS>(void*, void*, const double*, const int*, const Geom&, const Shape&,   \
                                        const Launch&, bool);                                                \
   template cudaError_t launch_unpack<TS>(double*, const void*, const void*, const int*, const Geom&,         \

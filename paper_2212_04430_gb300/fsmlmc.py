@@ -29,7 +29,8 @@ EXPORTS = ["fs_ctx_create", "fs_ctx_destroy", "fs_last_error", "fs_set_stream", 
            "fs_sample_allocation", "fs_eval_grid", "fs_tuned_tile", "fs_probing_colors",
            "variance_sample_probed", "shifted_solve_dev", "fs_hpe_exact_trace",
            "mlmc_level_traces", "fs_server_set_admission", "fs_trace_total", "fs_sampled_level_variances",
-           "fs_measure_peak", "fs_profile_read_fp64", "fs_set_iteration_bound", "fs_tuned_shape"]
+           "fs_measure_peak", "fs_profile_read_fp64", "fs_set_iteration_bound", "fs_tuned_shape",
+           "fs_set_clover"]
 JOB_MAX_LEVELS = 16
 
 
@@ -102,6 +103,7 @@ def load_library(path=LIB_PATH):
         "fs_ctx_device_bytes": (ctypes.c_size_t, [P]),
         "fs_tuned_tile": (I, [P, I, I]),
         "fs_set_gauge": (I, [P, dp]),
+        "fs_set_clover": (I, [P, ctypes.c_double]),
         "wilson_dslash": (I, [P, D, D, dp, dp, I, I, I]),
         "shifted_solve": (I, [P, D, dp, I, dp, I, dp, ctypes.POINTER(SolveParams), ctypes.POINTER(SysStats)]),
         "shifted_solve_dev": (I, [P, D, dp, I, P, I, P, ctypes.POINTER(SolveParams), ctypes.POINTER(SysStats)]),
@@ -246,6 +248,12 @@ class Context:
         self._check(self.lib.fs_set_gauge(self.h, _dptr(u)))
 
     set_gauge = fs_set_gauge
+
+    def fs_set_clover(self, c_sw):
+        """The Wilson-clover operator with coefficient c_sw for every later operation (0: Wilson)."""
+        self._check(self.lib.fs_set_clover(self.h, float(c_sw)))
+
+    set_clover = fs_set_clover
 
     def wilson_dslash(self, m, sigma, psi, prec="f64", link_compress=18):
         """(D + sigma) psi for psi complex [V][4][3] or [nrhs][V][4][3]."""
@@ -630,6 +638,10 @@ def fs_ctx_create(dims, bc_t=-1, device=0):
 
 def fs_set_gauge(ctx, U):
     return ctx.fs_set_gauge(U)
+
+
+def fs_set_clover(ctx, c_sw):
+    return ctx.fs_set_clover(c_sw)
 
 
 def wilson_dslash(ctx, m, sigma, psi, prec="f64", link_compress=18):

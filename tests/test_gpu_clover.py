@@ -1,0 +1,216 @@
+"""The Wilson-clover operator on the GPU (fs_set_clover) against the FP64 oracle's clover term.
+
+Sec. 4 computes with the clover discretisation; the oracle's reading of the term (oracle/clover.py,
+pinned by tests/test_oracle_clover.py) is C(x) = (c_sw / 2) sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x).
+
+Tolerances (from the arithmetic):
+  * wilson_dslash with the clover term: the Wilson tolerances (FP64 1e-13, FP32 2e-6, FP16 4e-3,
+    BF16 3e-2); the FP64 table comes from a Jacobi eigen-decomposition converged to 1e-15 of the
+    block's norm, the FP32 table adds FP32 rounding (~1e-7), both far inside these bounds.
+  * solutions: the oracle's true relative residual of D_sw <= tol, as the solver's stopping rule;
+    dense LU at 1e-10 for FP64 solves at 1e-12.
+  * level samples: relative 1e-9 (FP64 solves at 1e-12), 1e-6 (mixed solves at 1e-10).
+"""
+
+import numpy as np
+import pytest
+
+import inputs
+from oracle import clover as oclover
+from oracle import dirac as odirac
+from oracle import estimators as oest
+from oracle import solve as osolve
+from helpers import lattice_u, rel_err, sample_err
+
+pkg = pytest.importorskip("paper_2212_04430_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def cterm_of(u, dims, c_sw):
+    return oclover.clover_term(lattice_u(u, dims), c_sw)
+
+
+def oracle_Dsw(u, psi, m, sigma, dims, cterm, bc_t=-1):
+    """(D_sw + sigma) psi with the oracle, canonical flat in/out [..., V, 4, 3]."""
+    shp = odirac.lattice_shape(dims)
+    lead = psi.shape[:-3]
+    out = oclover.apply_Dsw(lattice_u(u, dims), psi.reshape(lead + shp + (4, 3)), m, sigma, bc_t, cterm)
+    return out.reshape(psi.shape)
+
+
+def rel_resid_sw(u, x, b, m, sigma, dims, cterm, bc_t=-1):
+    r = b - oracle_Dsw(u, x, m, sigma, dims, cterm, bc_t)
+    return float(np.linalg.norm(r.ravel()) / np.linalg.norm(b.ravel()))
+
+
+def make_ctx(dims, u, c_sw, bc_t=-1):
+    ctx = pkg.Context(dims, bc_t=bc_t, device=0)
+    ctx.fs_set_gauge(u)
+    ctx.fs_set_clover(c_sw)
+    return ctx
+
+
+DSLASH_TOL = {"f64": 1e-13, "f32": 2e-6, "f16": 4e-3, "bf16": 3e-2}
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("dims,bc_t,nrhs,kind", [((2, 2, 2, 2), -1, 1, "haar"), ((4, 4, 4, 4), -1, 3, "haar"),
+                                                 ((4, 6, 2, 8), 1, 2, "smooth"), ((8, 4, 4, 8), -1, 32, "haar"),
+                                                 ((4, 4, 2, 8), -1, 40, "smooth")])
+def test_dslash_clover_parity(prec, dims, bc_t, nrhs, kind):
+    u = inputs.gauge_field(dims, kind, seed=1201, eps=0.5)
+    psi = inputs.random_spinor(dims, 17, nvec=nrhs)
+    c_sw = 1.3
+    ctx = make_ctx(dims, u, c_sw, bc_t)
+    ref = oracle_Dsw(u, psi, -0.4, 0.15, dims, cterm_of(u, dims, c_sw), bc_t)
+    # the clover term is a visible part of the result
+    assert rel_err(oracle_Dsw(u, psi, -0.4, 0.15, dims, cterm_of(u, dims, 0.0), bc_t), ref) > 1e-2
+    for nr in ((18,) if prec == "f64" else (18, 12)):
+        got = ctx.wilson_dslash(-0.4, 0.15, psi, prec=prec, link_compress=nr)
+        assert rel_err(got, ref) < DSLASH_TOL[prec], (prec, nr, rel_err(got, ref))
+    ctx.close()
+
+
+@pytest.mark.parametrize("plane", [(0, 1), (2, 3)])
+def test_dslash_clover_constant_abelian_field(plane):
+    """Degenerate blocks: on a constant abelian field every site's clover block has two eigenvalues,
+    each three times (the colour identity), and the free field has C = 0 (the table's eigenvalues
+    are all zero)."""
+    dims = (4, 6, 4, 4)
+    u, _ = inputs.abelian_field(dims, n=1, mu=plane[0], nu=plane[1])
+    psi = inputs.random_spinor(dims, 18, nvec=4)
+    ctx = make_ctx(dims, u, 1.7)
+    got = ctx.wilson_dslash(-0.3, 0.0, psi, prec="f64")
+    assert rel_err(got, oracle_Dsw(u, psi, -0.3, 0.0, dims, cterm_of(u, dims, 1.7))) < 1e-13
+    ctx.fs_set_gauge(inputs.unit_gauge(dims))
+    got = ctx.wilson_dslash(-0.3, 0.0, psi, prec="f64")
+    from helpers import oracle_D
+    assert rel_err(got, oracle_D(inputs.unit_gauge(dims), psi, -0.3, 0.0, dims)) < 1e-13
+    ctx.close()
+
+
+def test_clover_switching_and_new_gauge_field():
+    """c_sw = 0 restores the Wilson operator bit for bit; a clover term set before the gauge field
+    is built with it; a new gauge field rebuilds the table."""
+    dims = (4, 4, 4, 4)
+    u = inputs.gauge_field(dims, "haar", seed=1202)
+    u2 = inputs.gauge_field(dims, "smooth", seed=1203, eps=0.6)
+    psi = inputs.random_spinor(dims, 19, nvec=2)
+    plain = pkg.Context(dims)
+    plain.fs_set_gauge(u)
+    wilson = plain.wilson_dslash(-0.2, 0.1, psi, prec="f32")
+    ctx = pkg.Context(dims)
+    ctx.fs_set_clover(0.9)  # before the gauge field
+    ctx.fs_set_gauge(u)
+    got = ctx.wilson_dslash(-0.2, 0.1, psi, prec="f64")
+    assert rel_err(got, oracle_Dsw(u, psi, -0.2, 0.1, dims, cterm_of(u, dims, 0.9))) < 1e-13
+    ctx.fs_set_gauge(u2)
+    got = ctx.wilson_dslash(-0.2, 0.1, psi, prec="f64")
+    assert rel_err(got, oracle_Dsw(u2, psi, -0.2, 0.1, dims, cterm_of(u2, dims, 0.9))) < 1e-13
+    ctx.fs_set_gauge(u)
+    ctx.fs_set_clover(0.0)
+    assert np.array_equal(ctx.wilson_dslash(-0.2, 0.1, psi, prec="f32"), wilson)
+    with pytest.raises(pkg.FsError) as e:
+        ctx.fs_set_clover(float("nan"))
+    assert e.value.code == pkg.fsmlmc.FS_ERR_INPUT
+    ctx.close()
+    plain.close()
+
+
+@pytest.mark.parametrize("prec,tol,nr", [("f64", 1e-10, 18), ("f32", 1e-8, 18), ("f16", 1e-8, 12),
+                                         ("bf16", 1e-8, 18)])
+def test_shifted_solve_clover_residual(prec, tol, nr):
+    dims = (4, 4, 4, 8)
+    u = inputs.gauge_field(dims, "smooth", seed=1204, eps=0.5)
+    b = inputs.random_spinor(dims, 20, nvec=3)
+    sig = [0.0, 0.3]
+    c_sw = 1.1
+    cterm = cterm_of(u, dims, c_sw)
+    ctx = make_ctx(dims, u, c_sw)
+    x, st, rc = ctx.shifted_solve(-0.3, sig, b, prec=prec, tol=tol, rhs_tile=6, link_compress=nr, verify=1)
+    assert rc == 0
+    for j, s in enumerate(sig):
+        for k in range(3):
+            r = rel_resid_sw(u, x[j, k], b[k], -0.3, s, dims, cterm)
+            assert r <= tol * 1.05, (prec, j, k, r)
+            stt = st[j * 3 + k]
+            assert stt["status"] == 2 and abs(stt["true_resid"] - r) <= 0.05 * r + 1e-15
+    ctx.close()
+
+
+def test_shifted_solve_clover_matches_dense():
+    dims = (2, 2, 2, 4)
+    u = inputs.gauge_field(dims, "smooth", seed=1205, eps=0.6)
+    b = inputs.random_spinor(dims, 21, nvec=2)
+    cterm = cterm_of(u, dims, 1.0)
+    ctx = make_ctx(dims, u, 1.0)
+    x, st, rc = ctx.shifted_solve(-0.25, [0.05], b, prec="f64", tol=1e-12, rhs_tile=2)
+    assert rc == 0
+    dense = osolve.dense_operator(u, -0.25, 0.05, dims, -1, cterm)
+    for k in range(2):
+        ref = np.linalg.solve(dense, b[k].ravel()).reshape(b[k].shape)
+        assert rel_err(x[0, k], ref) < 1e-10
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol,est", [("f64", 1e-9, "split_even"), ("f64", 1e-9, "diff"),
+                                          ("f16", 1e-6, "split_even")])
+def test_mlmc_clover_samples_against_dense(prec, tol, est):
+    dims = (4, 4, 2, 4)
+    u = inputs.gauge_field(dims, "smooth", seed=1206, eps=0.5)
+    c_sw, m, sig, p = 1.2, -0.25, [0.0, 0.1, 0.5], 1
+    cterm = cterm_of(u, dims, c_sw)
+    gam = pkg.gamma_matrix("g5g3")
+    n = [4, 3, 3]
+    ctx = make_ctx(dims, u, c_sw)
+    out = ctx.mlmc_level_trace(m, sig, gam, p, n, seed=91, job=2, estimator=est, prec=prec,
+                               tol=1e-12 if prec == "f64" else 1e-10, rhs_tile=8)
+    assert out["rc"] == 0
+    solver = oest.make_dense_solver(u, m, dims, -1, cterm)
+    ref = oest.level_samples(u, m, sig, odirac.gamma_product(["g5", "g3"]), p, n, 91, 2, dims, -1,
+                             oest.ESTIMATORS[est], solver)
+    for lev in range(3):
+        assert sample_err(out["samples"][lev], ref[lev]) < tol, (est, lev)
+    ctx.close()
+
+
+def test_clover_tile_shapes_give_identical_systems():
+    """The clover passes and the clover M-hat compute a system the same way in every tile shape:
+    64-, 40- and 1-system tiles give bit-identical FP16 solutions."""
+    dims = (8, 4, 4, 8)
+    u = inputs.gauge_field(dims, "smooth", seed=1207, eps=0.4)
+    b = inputs.random_spinor(dims, 22, nvec=40)
+    ctx = make_ctx(dims, u, 1.0)
+    kw = dict(prec="f16", tol=1e-8, link_compress=12)
+    x64, _, rc = ctx.shifted_solve(-0.25, [0.02], np.concatenate([b, b[:24]]), rhs_tile=64, **kw)
+    assert rc == 0
+    x40, _, rc = ctx.shifted_solve(-0.25, [0.02], b, rhs_tile=40, **kw)
+    assert rc == 0
+    cterm = cterm_of(u, dims, 1.0)
+    for k in (0, 23, 39):
+        x1, _, rc = ctx.shifted_solve(-0.25, [0.02], b[k:k + 1], rhs_tile=1, **kw)
+        assert rc == 0
+        assert np.array_equal(x64[0, k], x1[0, 0]) and np.array_equal(x40[0, k], x1[0, 0]), k
+        assert rel_resid_sw(u, x1[0, 0], b[k], -0.25, 0.02, dims, cterm) <= 1.05e-8
+    ctx.close()
+
+
+def test_clover_refuses_the_hopping_parameter_expansion():
+    dims = (4, 4, 4, 4)
+    u = inputs.gauge_field(dims, "smooth", seed=1208, eps=0.3)
+    ctx = make_ctx(dims, u, 1.0)
+    g = pkg.gamma_matrix("g5")
+    with pytest.raises(pkg.FsError) as e:
+        ctx.mlmc_level_trace(-0.2, [0.0, 0.5], g, 0, [2, 2], seed=1, hpe_order=2)
+    assert e.value.code == pkg.fsmlmc.FS_ERR_ARG
+    with pytest.raises(pkg.FsError) as e:
+        ctx.hpe_exact_trace(-0.2, 0.5, g, 0, 2)
+    assert e.value.code == pkg.fsmlmc.FS_ERR_ARG
+    ctx.close()
