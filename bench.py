@@ -353,7 +353,8 @@ def config_of(args, w):
             "vectors_per_level_per_step": args.vectors or w["vectors"], "estimator": w["estimator"],
             "rhs_tile": args.tile or w["tile"], "storage": w["prec"], "links": "%d-real" % w["link"],
             "tol": w["tol"], "delta": args.delta or "library", "lanes": args.lanes or "library",
-            "l2": "working set above L2 (no flush needed)"}
+            "l2": "working set above L2 (no flush needed)",
+            "operator": "Wilson-clover, c_sw = %g" % args.clover if args.clover else "Wilson"}
 
 
 # --------------------------------------------------------------------------- serving
@@ -443,6 +444,48 @@ def run_estimators(pkg, ctx, w, kw, n=64, seed=9500):
     res["cheapest"] = best
     res["note"] = ("%d Z4 vectors per level, the same noise for every estimator (seed %d); F2 = "
                    "(sum_l sqrt(V_l C_l))^2 with C_l in BiCGStab iterations per sample" % (n, seed))
+    return res
+
+
+def run_clover(pkg, ctx, w, kw, n=64, c_sw=1.0, seed=9600):
+    """The same level traces with the Wilson and the Wilson-clover operator (Sec. 4 computes with
+    the clover discretisation), n Z4 vectors per level, one timed step each on the same noise:
+    solves/s, BiCGStab iterations, and the cost of one system-iteration (the clover M-hat adds
+    two site-local passes per application: (A + C_oo)^-1 on H_oe p and C_ee p)."""
+    import torch
+    gam = pkg.gamma_matrix(w["gamma"])
+    nl = len(w["sigmas"])
+    res = {}
+    stream = torch.cuda.current_stream()
+    for name, c in (("wilson", 0.0), ("clover", c_sw)):
+        t0 = time.time()
+        ctx.fs_set_clover(c)
+        build_s = time.time() - t0
+        ctx.mlmc_level_trace(w["m"], w["sigmas"], gam, w["p"], [4] * nl, seed=seed, job=60, estimator=w["estimator"],
+                             **kw)  # warm-up: graphs and clover fields of this tile
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = ctx.mlmc_level_trace(w["m"], w["sigmas"], gam, w["p"], [n] * nl, seed=seed, job=61,
+                                   estimator=w["estimator"], **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if out["rc"] != 0:
+            raise RuntimeError("%s solves did not converge: %s" % (name, ctx.last_error()))
+        s = e0.elapsed_time(e1) / 1e3
+        its = [st["iters"] for st in out["stats"]]
+        res[name] = {"solves_per_s": len(its) / s, "seconds": s, "solves": len(its),
+                     "mean_iters": float(np.mean(its)), "system_iterations_per_s": float(np.sum(its)) / s,
+                     "max_true_resid": float(max(st["true_resid"] for st in out["stats"])),
+                     "total": [float(out["total"].real), float(out["total"].imag)]}
+        if c:
+            res[name]["c_sw"] = c
+            res[name]["table_build_s"] = build_s
+    ctx.fs_set_clover(0.0)
+    res["iteration_cost_ratio"] = res["wilson"]["system_iterations_per_s"] / res["clover"]["system_iterations_per_s"]
+    res["note"] = ("%d Z4 vectors per level (seed %d), the workload's precision, tile and lanes; "
+                   "iteration_cost_ratio = Wilson / clover system-iterations per second" % (n, seed))
     return res
 
 
@@ -646,6 +689,9 @@ def build_parser():
                     help="skip the probed and spin-colour diluted level traces (p4k4 colours)")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="skip the end-to-end run of variance sampling, shift selection and allocation")
+    ap.add_argument("--clover", type=float, default=0.0,
+                    help="c_sw of the Wilson-clover operator for the whole timed step (0: Wilson)")
+    ap.add_argument("--no-clover", action="store_true", help="skip the Wilson / Wilson-clover comparison")
     return ap
 
 
@@ -676,6 +722,8 @@ def main():
     ctx = pkg.Context(dims, bc_t=-1, device=local)
     ctx.set_stream(stream.cuda_stream)
     ctx.fs_set_gauge(u)
+    if args.clover:
+        ctx.fs_set_clover(args.clover)  # the table is rebuilt by every fs_set_gauge below
     gam = pkg.gamma_matrix(w["gamma"])
     kw = dict(prec=w["prec"], tol=w["tol"], rhs_tile=tile, link_compress=w["link"], delta=args.delta)
     n = [nvec] * len(w["sigmas"])
@@ -819,7 +867,8 @@ def main():
     if not args.no_pipeline and rank == 0:
         pipeline = run_pipeline(pkg, ctx, w, kw)
         # the paper's variant: V_L sampled with the hopping parameter expansion (order 4) where m + s > 0
-        pipeline["with_hpe"] = run_pipeline(pkg, ctx, w, kw, hpe_order=4)
+        if not args.clover:  # the expansion is the Wilson operator's
+            pipeline["with_hpe"] = run_pipeline(pkg, ctx, w, kw, hpe_order=4)
         # and with the paper's noise as well; an auxiliary measurement, so a failure is reported in
         # the line instead of ending the run
         try:
@@ -831,6 +880,10 @@ def main():
     if not args.no_estimators and rank == 0:
         estimators = run_estimators(pkg, ctx, w, kw)
 
+    clover = None
+    if not args.no_clover and not args.clover and rank == 0:
+        clover = run_clover(pkg, ctx, w, kw)
+
     large = None
     if not args.no_large and rank == 0:
         large = run_variance_24x64(pkg, inputs, local)
@@ -838,7 +891,7 @@ def main():
     probing = None
     if not args.no_probing and rank == 0:
         probing = run_probing(pkg, ctx, w, kw)
-        if w["m"] + w["sigmas"][-1] > 0:
+        if w["m"] + w["sigmas"][-1] > 0 and not args.clover:
             probing["hpe"] = run_hpe(pkg, ctx, w, kw)
 
     serving = serving_stable = None
@@ -873,7 +926,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_of(args, w), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "arith_peaks": arith, "serving": serving,
-                "serving_stable": serving_stable, "estimators": estimators,
+                "serving_stable": serving_stable, "estimators": estimators, "wilson_clover": clover,
                 "pipeline": pipeline,
                 "fp64_single_rhs": fp64, "probing": probing, "variance_sampling_24x64": large,
                 "solver": {"mean_iters": float(np.mean(iters)) if iters else None,

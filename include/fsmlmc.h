@@ -186,7 +186,7 @@ FS_API int fs_set_gauge(fs_ctx* ctx, const double* U);
  * sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu], F_{mu nu} = (Q_{mu nu} - Q_{mu nu}^dag) / (8i), Q_{mu nu}(x)
  * the sum of the four counter-clockwise plaquettes of the (mu, nu) plane at x (the paper states no
  * normalisation: this is the reading). C is Hermitian, commutes with gamma_5 and is eigen-
- * decomposed once per gauge field into a table of V Vh complex 6x6 blocks (about 5.6 KB per
+ * decomposed once per gauge field into a table of V Vh complex 6x6 blocks (about 2.7 KB per
  * site in FP64 + FP32), so that (A + C)^-1 for every shift costs two 6x6 products per chirality.
  * The table is built now if a gauge field is set, else by the next fs_set_gauge, and rebuilt by
  * every fs_set_gauge; c_sw = 0 frees it and restores the Wilson operator. With the clover term

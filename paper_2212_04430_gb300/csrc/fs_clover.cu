@@ -192,9 +192,21 @@ __global__ void __launch_bounds__(64) clover_build_kernel(ClovBuild b) {
           }
     }
   for (int blk = 0; blk < 2; blk++) {
+    const size_t o = ((size_t)id * 2 + blk) * CLV_REALS;
+    // packed C (before the rotations overwrite it): diagonal, then the entries above it
+    for (int i = 0; i < 6; i++) {
+      b.t64[o + CLV_C + i] = cr[blk][i * 7];
+      b.t32[o + CLV_C + i] = (float)cr[blk][i * 7];
+      for (int j = i + 1; j < 6; j++) {
+        const size_t u = o + CLV_C + 6 + 2 * clv_upper(i, j);
+        b.t64[u] = cr[blk][i * 6 + j];
+        b.t64[u + 1] = ci[blk][i * 6 + j];
+        b.t32[u] = (float)cr[blk][i * 6 + j];
+        b.t32[u + 1] = (float)ci[blk][i * 6 + j];
+      }
+    }
     double vr[36], vi[36], lam[6];
     jacobi6(cr[blk], ci[blk], vr, vi, lam);
-    const size_t o = ((size_t)id * 2 + blk) * CLV_REALS;
     for (int k = 0; k < 36; k++) {
       b.t64[o + 2 * k] = vr[k];
       b.t64[o + 2 * k + 1] = vi[k];

@@ -9,17 +9,23 @@
 // {0, 1} and {2, 3}.
 //
 // Table: each block is eigen-decomposed once per gauge field, C_b = V_b diag(lambda_b) V_b^dag, so
-// that for every shift of every system (a + C)^-1 = V diag(1 / (a + lambda)) V^dag and C itself
-// are two 6x6 products and a diagonal per block: one table serves all the shifts of a tile.
-// Layout: [parity 2][Vh][block 2][CLV_REALS], per block V row-major (36 complex: V[i][j], column j
-// the j-th eigenvector) then the 6 eigenvalues.
+// that for every shift of every system (a + C)^-1 = V diag(1 / (a + lambda)) V^dag is two 6x6
+// products and a diagonal per block: one table serves all the shifts of a tile. C itself is
+// applied from its packed Hermitian form (one 6x6 product, 132 multiply-adds per block instead of
+// 288). Layout: [parity 2][Vh][block 2][CLV_REALS], per block V row-major (36 complex: V[i][j],
+// column j the j-th eigenvector), the 6 eigenvalues, then C_b packed: its 6 (real) diagonal
+// entries and its 15 entries above the diagonal, (0,1), (0,2), ..., (0,5), (1,2), ..., (4,5).
 #pragma once
 
 #include "fs_hop.cuh"
 
 namespace fs {
 
-constexpr int CLV_REALS = 78;  // 72 (V) + 6 (lambda) per chirality block
+constexpr int CLV_REALS = 114;  // 72 (V) + 6 (lambda) + 36 (C packed) per chirality block
+constexpr int CLV_C = 78;       // offset of the packed C in a block
+
+// index of the upper-triangle entry (i < j) in the packed C (complex entries after the diagonal)
+__host__ __device__ constexpr int clv_upper(int i, int j) { return i * 5 - i * (i - 1) / 2 + (j - i - 1); }
 
 enum ClovMode {
   CLV_MUL = 0,  // out = C in
@@ -44,42 +50,72 @@ struct ClovArgs {
 // One site of one system: the two chirality blocks of the spinor v (index 6 spin + 2 colour + re/im).
 template <int MODE, typename Tc, typename Tm>
 __device__ __forceinline__ void clover_site(const Tc* __restrict__ tab, Tm a, const Tm (&v)[24], Tm (&o)[24]) {
+  if constexpr (MODE != CLV_INV) {
+    // o = C v from the packed blocks: row i, d_i v_i + sum_{j != i} C_ij v_j, C_ji = conj(C_ij)
+#pragma unroll
+    for (int b = 0; b < 2; b++) {
+      const Tc* t = tab + b * CLV_REALS + CLV_C;
+#pragma unroll
+      for (int i = 0; i < 6; i++) {
+        const Tm d = (Tm)t[i];
+        Tm re = d * v[12 * b + 2 * i], im = d * v[12 * b + 2 * i + 1];
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+          if (j == i) continue;
+          const int u = 6 + 2 * (i < j ? clv_upper(i, j) : clv_upper(j, i));
+          const Tm cr = (Tm)t[u], ci = i < j ? (Tm)t[u + 1] : -(Tm)t[u + 1];
+          const Tm pr = v[12 * b + 2 * j], pi = v[12 * b + 2 * j + 1];
+          re = fmadd(cr, pr, re);
+          re = fmadd(-ci, pi, re);
+          im = fmadd(cr, pi, im);
+          im = fmadd(ci, pr, im);
+        }
+        o[12 * b + 2 * i] = re;
+        o[12 * b + 2 * i + 1] = im;
+      }
+    }
+    return;
+  }
+  // (a + C)^-1 v = V diag(1 / (a + lambda)) V^dag v, one eigenvector (column j of V) at a time:
+  // w_j = sum_i conj(V_ij) psi_i, w_j /= a + lambda_j, o_i += V_ij w_j (psi_i: spin 2b + i / 3,
+  // colour i % 3), so only one column is live
 #pragma unroll
   for (int b = 0; b < 2; b++) {
     const Tc* t = tab + b * CLV_REALS;
-    // w_j = sum_i conj(V_ij) psi_i, psi_i = spinor entry (spin 2b + i / 3, colour i % 3)
-    Tm wr[6], wi[6];
+    Tm orr[6], oi[6];
+#pragma unroll
+    for (int i = 0; i < 6; i++) orr[i] = oi[i] = 0;
 #pragma unroll
     for (int j = 0; j < 6; j++) {
+      Tm vr[6], vi[6];
+#pragma unroll
+      for (int i = 0; i < 6; i++) {
+        vr[i] = (Tm)t[2 * (i * 6 + j)];
+        vi[i] = (Tm)t[2 * (i * 6 + j) + 1];
+      }
       Tm re = 0, im = 0;
 #pragma unroll
       for (int i = 0; i < 6; i++) {
-        const Tm vr = (Tm)t[2 * (i * 6 + j)], vi = (Tm)t[2 * (i * 6 + j) + 1];
         const Tm pr = v[12 * b + 2 * i], pi = v[12 * b + 2 * i + 1];
-        re = fmadd(vr, pr, re);
-        re = fmadd(vi, pi, re);
-        im = fmadd(vr, pi, im);
-        im = fmadd(-vi, pr, im);
+        re = fmadd(vr[i], pr, re);
+        re = fmadd(vi[i], pi, re);
+        im = fmadd(vr[i], pi, im);
+        im = fmadd(-vi[i], pr, im);
       }
-      const Tm lam = (Tm)t[72 + j];
-      const Tm f = MODE == CLV_INV ? (Tm)1 / (a + lam) : lam;
-      wr[j] = f * re;
-      wi[j] = f * im;
+      const Tm f = (Tm)1 / (a + (Tm)t[72 + j]);
+      const Tm wr = f * re, wi = f * im;
+#pragma unroll
+      for (int i = 0; i < 6; i++) {
+        orr[i] = fmadd(vr[i], wr, orr[i]);
+        orr[i] = fmadd(-vi[i], wi, orr[i]);
+        oi[i] = fmadd(vr[i], wi, oi[i]);
+        oi[i] = fmadd(vi[i], wr, oi[i]);
+      }
     }
-    // out_i = sum_j V_ij w_j
 #pragma unroll
     for (int i = 0; i < 6; i++) {
-      Tm re = 0, im = 0;
-#pragma unroll
-      for (int j = 0; j < 6; j++) {
-        const Tm vr = (Tm)t[2 * (i * 6 + j)], vi = (Tm)t[2 * (i * 6 + j) + 1];
-        re = fmadd(vr, wr[j], re);
-        re = fmadd(-vi, wi[j], re);
-        im = fmadd(vr, wi[j], im);
-        im = fmadd(vi, wr[j], im);
-      }
-      o[12 * b + 2 * i] = re;
-      o[12 * b + 2 * i + 1] = im;
+      o[12 * b + 2 * i] = orr[i];
+      o[12 * b + 2 * i + 1] = oi[i];
     }
   }
 }

@@ -510,7 +510,14 @@ __global__ void __launch_bounds__(WL ? 128 : 256, WL ? 3 : (sizeof(Tm) == 8 ? 2 
       } else {
         Tm xv[24];
         make_field<Ts>(const_cast<void*>(a.X), g.Vh, sh.N, smj).load(site, sys, xv);
-        if constexpr (COEF == COEF_TRUERES || COEF == COEF_FULLRES || CLV) {
+        if constexpr (CLV) {
+          // Wilson-clover M-hat / D_sw: out = ca X + (cb (H in) + Y), Y = C X, in this rounding
+          // order (the persistent kernel consumes Y before X)
+          Tm yv[24];
+          make_field<Ts>(const_cast<void*>(a.Y), g.Vh, sh.N, smj).load(site, sys, yv);
+#pragma unroll
+          for (int k = 0; k < 24; k++) o[k] = fmadd(ca, xv[k], fmadd(cb, acc[k], yv[k]));
+        } else if constexpr (COEF == COEF_TRUERES || COEF == COEF_FULLRES) {
           // out = Y + ca X + cb (H in): two multiply-adds per entry
           Tm yv[24];
           make_field<Ts>(const_cast<void*>(a.Y), g.Vh, sh.N, smj).load(site, sys, yv);
@@ -974,7 +981,9 @@ __host__ __device__ constexpr int link_chunks16(int nr) {
   return link_pad<Tg>(nr) * (int)sizeof(Tg) / 16;
 }
 
-template <typename Ts, typename Tg, int NR, int COEF, int DOT, int PF>
+// CLV: the Wilson-clover M-hat, out = ca X + (cb (H in) + Y) with Y = C X from a clover pass
+// (an operand item of its own, consumed before X).
+template <typename Ts, typename Tg, int NR, int COEF, int DOT, int PF, bool CLV = false>
 __global__ void __launch_bounds__(128, 3) hop_kernel_pk(HopArgs a) {
   using namespace pk;
   constexpr int K = DotK<DOT>::K;
@@ -982,8 +991,13 @@ __global__ void __launch_bounds__(128, 3) hop_kernel_pk(HopArgs a) {
   constexpr int CV = chunks16<Ts>();
   constexpr int VW = Store<Ts>::VW;
   constexpr bool HAS_X = COEF != COEF_PLAIN;
+  constexpr bool HAS_Y = CLV;
   constexpr bool HAS_R = DOT == DOT_R || DOT == DOT_TS;
-  constexpr int NITEM = 8 + (HAS_X ? 1 : 0) + (HAS_R ? 1 : 0);
+  static_assert(!CLV || COEF == COEF_MHAT, "the clover operand belongs to M-hat");
+  constexpr int NITEM = 8 + (HAS_X ? 1 : 0) + (HAS_Y ? 1 : 0) + (HAS_R ? 1 : 0);
+  constexpr int IY = 8;                    // Y, when present
+  constexpr int IX = 8 + (HAS_Y ? 1 : 0);  // X
+  constexpr int IR = NITEM - 1;            // R
   static_assert(PF >= 1 && PF < NITEM && PF <= 6, "ring depth");
   static_assert(DOT != DOT_TS || (HAS_X && PF >= 2), "DOT_TS consumes X and R together");
   constexpr int RPC = link_chunks16<Tg>(NR);  // 16-byte chunks per stored link
@@ -1006,8 +1020,9 @@ __global__ void __launch_bounds__(128, 3) hop_kernel_pk(HopArgs a) {
   const bool sel_b = sb < sh.N && selected(a.st, sb, a.mask);
   float2 ca = make_float2(0.f, 0.f), cb = make_float2(1.f, 1.f);
   if (COEF == COEF_MHAT || COEF == COEF_DSLASH) {
-    if (sel_a) { ca.x = coef<float>(a.st[sa], C_A); cb.x = COEF == COEF_MHAT ? coef<float>(a.st[sa], C_MINV4A) : -0.5f; }
-    if (sel_b) { ca.y = coef<float>(a.st[sb], C_A); cb.y = COEF == COEF_MHAT ? coef<float>(a.st[sb], C_MINV4A) : -0.5f; }
+    // Wilson-clover: the site factors come from clover passes, H_eo A_oo^-1 H_oe p / 4
+    if (sel_a) { ca.x = coef<float>(a.st[sa], C_A); cb.x = COEF == COEF_MHAT ? (CLV ? -0.25f : coef<float>(a.st[sa], C_MINV4A)) : -0.5f; }
+    if (sel_b) { ca.y = coef<float>(a.st[sb], C_A); cb.y = COEF == COEF_MHAT ? (CLV ? -0.25f : coef<float>(a.st[sb], C_MINV4A)) : -0.5f; }
   }
   const size_t cstride = (size_t)g.Vh * sh.N * VW;  // elements between 16-byte chunks c and c+1
   const size_t rowstride = (size_t)sh.N * VW;        // elements between consecutive sites
@@ -1073,7 +1088,7 @@ __global__ void __launch_bounds__(128, 3) hop_kernel_pk(HopArgs a) {
         const int nbi = __shfl_sync(0xffffffffu, nbl, (lane & 16) | I);
         src = in_a + (size_t)nbi * rowstride;
       } else {
-        const Ts* base = (HAS_X && I == 8) ? (const Ts*)a.X : (const Ts*)a.R;
+        const Ts* base = (HAS_Y && I == IY) ? (const Ts*)a.Y : (HAS_X && I == IX) ? (const Ts*)a.X : (const Ts*)a.R;
         src = base + (size_t)site * rowstride + (size_t)sa * VW;
       }
       const int slot = slot_of(j, I);
@@ -1176,20 +1191,34 @@ __global__ void __launch_bounds__(128, 3) hop_kernel_pk(HopArgs a) {
     float2 dv[KK];
 #pragma unroll
     for (int k = 0; k < KK; k++) dv[k] = make_float2(0.f, 0.f);
+    if constexpr (HAS_Y) {
+      // cb (H in) + Y in place of acc, one 16-byte chunk of Y at a time
+      cp_async_wait<PF - 1>();
+      const int slot = slot_of(j, IY);
+#pragma unroll
+      for (int c = 0; c < CV; c++) {
+        float2 yv[VW];
+        fetch_pk(slot, c, yv);
+#pragma unroll
+        for (int k = 0; k < VW; k++) acc[c * VW + k] = fma2(cb, acc[c * VW + k], yv[k]);
+      }
+      issue_ahead(IntC<IY>{}, j);
+    }
     if constexpr (DOT == DOT_TS) {
       // X (= s) and R (= rhat) together, one 16-byte chunk of each at a time:
       // t = ca s + cb (H in) in place of acc, and <t, s>, ||t||^2, ||s||^2, <rhat, s>, <rhat, t>
       cp_async_wait<PF - 2>();
       float2 sr = dv[0], si = dv[0], tt = dv[0], ss = dv[0], qr = dv[0], qi = dv[0], tr = dv[0], ti = dv[0];
       {
-        const int xslot = slot_of(j, 8), rslot = slot_of(j, 9);
+        const int xslot = slot_of(j, IX), rslot = slot_of(j, IR);
 #pragma unroll
         for (int c = 0; c < CV; c++) {
           float2 xv[VW], rv[VW];
           fetch_pk(xslot, c, xv);
           fetch_pk(rslot, c, rv);
 #pragma unroll
-          for (int k = 0; k < VW; k++) acc[c * VW + k] = fma2(cb, acc[c * VW + k], mul2(ca, xv[k]));
+          for (int k = 0; k < VW; k++)
+            acc[c * VW + k] = HAS_Y ? fma2(ca, xv[k], acc[c * VW + k]) : fma2(cb, acc[c * VW + k], mul2(ca, xv[k]));
 #pragma unroll
           for (int k = 0; k < VW; k += 2) {
             const float2 t0 = acc[c * VW + k], t1 = acc[c * VW + k + 1];
@@ -1205,28 +1234,29 @@ __global__ void __launch_bounds__(128, 3) hop_kernel_pk(HopArgs a) {
           }
         }
       }
-      issue_ahead(IntC<8>{}, j);
-      issue_ahead(IntC<9>{}, j);
+      issue_ahead(IntC<IX>{}, j);
+      issue_ahead(IntC<IR>{}, j);
       dv[0] = sr; dv[1] = si; dv[2] = tt; dv[3] = ss; dv[4] = qr; dv[5] = qi; dv[6] = tr; dv[7] = ti;
     } else {
       if constexpr (HAS_X) {
         // out = ca X + cb (H in), in place of acc, one 16-byte chunk of X at a time
         cp_async_wait<PF - 1>();
-        const int slot = slot_of(j, 8);
+        const int slot = slot_of(j, IX);
 #pragma unroll
         for (int c = 0; c < CV; c++) {
           float2 xv[VW];
           fetch_pk(slot, c, xv);
 #pragma unroll
-          for (int k = 0; k < VW; k++) acc[c * VW + k] = fma2(cb, acc[c * VW + k], mul2(ca, xv[k]));
+          for (int k = 0; k < VW; k++)
+            acc[c * VW + k] = HAS_Y ? fma2(ca, xv[k], acc[c * VW + k]) : fma2(cb, acc[c * VW + k], mul2(ca, xv[k]));
         }
-        issue_ahead(IntC<8>{}, j);
+        issue_ahead(IntC<IX>{}, j);
       }
       if constexpr (HAS_R) {
         // <rhat, v>, out = v
         cp_async_wait<PF - 1>();
         float2 sr = dv[0], si = dv[0];
-        const int slot = slot_of(j, NITEM - 1);
+        const int slot = slot_of(j, IR);
 #pragma unroll
         for (int c = 0; c < CV; c++) {
           float2 rv[VW];
@@ -1238,7 +1268,7 @@ __global__ void __launch_bounds__(128, 3) hop_kernel_pk(HopArgs a) {
             si = fma2(rv[k], o1, si); si = fma2(neg2(rv[k + 1]), o0, si);
           }
         }
-        issue_ahead(IntC<NITEM - 1>{}, j);
+        issue_ahead(IntC<IR>{}, j);
         dv[0] = sr; dv[1] = si;
       }
     }

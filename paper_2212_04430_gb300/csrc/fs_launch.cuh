@@ -34,9 +34,9 @@ struct PersistentGrid {
 // The persistent paired hop for 32-system chunks (hop_kernel_pk) at ring depth PF: 128-thread
 // blocks of 8 sites, as many as are resident (capped at l.pk_blocks per SM when set), never more
 // blocks than site chunks.
-template <typename Ts, typename Tg, int R, int C, int D, int PF>
+template <typename Ts, typename Tg, int R, int C, int D, int PF, bool CLV = false>
 cudaError_t launch_hop_pk_at(const HopArgs& a, const Launch& l) {
-  auto kern = hop_kernel_pk<Ts, Tg, R, C, D, PF>;
+  auto kern = hop_kernel_pk<Ts, Tg, R, C, D, PF, CLV>;
   const size_t smem = hop_pk_smem<Ts, PF, DotK<D>::K>();
   // thread-safe one-time set-up: shared-memory opt-in and the resident grid
   static const PersistentGrid pg = [&] {
@@ -58,17 +58,21 @@ cudaError_t launch_hop_pk_at(const HopArgs& a, const Launch& l) {
   return cudaGetLastError();
 }
 
-template <typename Ts, typename Tg, typename Tm, int R, int C, int D>
+template <typename Ts, typename Tg, typename Tm, int R, int C, int D, bool CLV = false>
 cudaError_t launch_hop_pk(const HopArgs& a, const Launch& l) {
-  if (l.pk_depth == hop_pk_alt_depth<Ts>()) return launch_hop_pk_at<Ts, Tg, R, C, D, hop_pk_alt_depth<Ts>()>(a, l);
-  return launch_hop_pk_at<Ts, Tg, R, C, D, hop_pk_depth<Ts>()>(a, l);
+  if (l.pk_depth == hop_pk_alt_depth<Ts>())
+    return launch_hop_pk_at<Ts, Tg, R, C, D, hop_pk_alt_depth<Ts>(), CLV>(a, l);
+  return launch_hop_pk_at<Ts, Tg, R, C, D, hop_pk_depth<Ts>(), CLV>(a, l);
 }
+
+// the shapes the persistent paired kernel serves: 32-system chunks of 8 sites
+inline bool pk_shape(const HopArgs& a, const Launch& l) { return a.sh.NB == 32 && a.sh.SB == 8 && l.block == 256; }
 
 template <typename Ts, typename Tg, typename Tm, int R, int C, int D>
 cudaError_t launch_hop_pf(const HopArgs& a, const Launch& l) {
   if (a.sysmajor) return cudaErrorInvalidValue;  // inner-precision fields are tile-layout only
   // 32-system chunks, 8 sites per block: the persistent paired kernel
-  if (a.sh.NB == 32 && a.sh.SB == 8 && l.block == 256) return launch_hop_pk<Ts, Tg, Tm, R, C, D>(a, l);
+  if (pk_shape(a, l)) return launch_hop_pk<Ts, Tg, Tm, R, C, D>(a, l);
   constexpr int PF = hop_pf<Ts>();
   const size_t smem = hop_pf_smem<Ts, PF>(l.block);
   // thread-safe one-time set-up (several server workers may launch concurrently)
@@ -86,9 +90,12 @@ cudaError_t launch_hop(int coef, int dot, int nr, const HopArgs& a, const Launch
   using Tg = typename GaugeOf<Ts>::T;
   using Tm = MathOf<Ts>;
   const dim3 grid(l.grid_x, l.grid_y), block(l.block);
-  // Wilson-clover M-hat and D_sw on the tile layout: the generic kernel with the Y operand (C X)
+  // Wilson-clover M-hat and D_sw on the tile layout, with the Y operand (C X): the persistent
+  // paired kernel for the M-hat of 32-system chunks in the inner precisions, else the generic one
 #define FS_HOP_CLV(C, D, R)                                                                  \
   if (coef == C && dot == D && nr == R) {                                                    \
+    if constexpr (!std::is_same<Ts, double>::value && C == COEF_MHAT)                        \
+      if (pk_shape(a, l)) return launch_hop_pk<Ts, Tg, Tm, R, C, D, true>(a, l);             \
     hop_kernel<Ts, Tg, Tm, R, C, D, false, true><<<grid, block, 0, l.stream>>>(a);           \
     note_launch();                                                                           \
     return cudaGetLastError();                                                               \
