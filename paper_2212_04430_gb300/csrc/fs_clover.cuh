@@ -47,6 +47,11 @@ struct ClovArgs {
   int sysmajor;
 };
 
+// products rounded on their own (never contracted into a neighbouring add), so that the paired
+// pass below rounds every lane exactly as this scalar one
+__device__ __forceinline__ float mulrn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mulrn(double a, double b) { return __dmul_rn(a, b); }
+
 // One site of one system: the two chirality blocks of the spinor v (index 6 spin + 2 colour + re/im).
 template <int MODE, typename Tc, typename Tm>
 __device__ __forceinline__ void clover_site(const Tc* __restrict__ tab, Tm a, const Tm (&v)[24], Tm (&o)[24]) {
@@ -58,7 +63,7 @@ __device__ __forceinline__ void clover_site(const Tc* __restrict__ tab, Tm a, co
 #pragma unroll
       for (int i = 0; i < 6; i++) {
         const Tm d = (Tm)t[i];
-        Tm re = d * v[12 * b + 2 * i], im = d * v[12 * b + 2 * i + 1];
+        Tm re = mulrn(d, v[12 * b + 2 * i]), im = mulrn(d, v[12 * b + 2 * i + 1]);
 #pragma unroll
         for (int j = 0; j < 6; j++) {
           if (j == i) continue;
@@ -103,7 +108,7 @@ __device__ __forceinline__ void clover_site(const Tc* __restrict__ tab, Tm a, co
         im = fmadd(-vi[i], pr, im);
       }
       const Tm f = (Tm)1 / (a + (Tm)t[72 + j]);
-      const Tm wr = f * re, wi = f * im;
+      const Tm wr = mulrn(f, re), wi = mulrn(f, im);
 #pragma unroll
       for (int i = 0; i < 6; i++) {
         orr[i] = fmadd(vr[i], wr, orr[i]);
@@ -117,6 +122,123 @@ __device__ __forceinline__ void clover_site(const Tc* __restrict__ tab, Tm a, co
       o[12 * b + 2 * i] = orr[i];
       o[12 * b + 2 * i + 1] = oi[i];
     }
+  }
+}
+
+// clover_site for two systems of one site at once (the lanes of packed FP32 instructions, the
+// table entries broadcast to both): per lane the same operations in the same order as the scalar
+// form, so the results are bit-identical to it.
+template <int MODE>
+__device__ __forceinline__ void clover_site_pk(const float* __restrict__ tab, float2 a, const float2 (&v)[24],
+                                               float2 (&o)[24]) {
+  using namespace pk;
+  if constexpr (MODE != CLV_INV) {
+#pragma unroll
+    for (int b = 0; b < 2; b++) {
+      const float* t = tab + b * CLV_REALS + CLV_C;
+#pragma unroll
+      for (int i = 0; i < 6; i++) {
+        const float2 d = make_float2(t[i], t[i]);
+        float2 re = mul2(d, v[12 * b + 2 * i]), im = mul2(d, v[12 * b + 2 * i + 1]);
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+          if (j == i) continue;
+          const int u = 6 + 2 * (i < j ? clv_upper(i, j) : clv_upper(j, i));
+          const float cr = t[u], ci = i < j ? t[u + 1] : -t[u + 1];
+          const float2 c2 = make_float2(cr, cr), i2 = make_float2(ci, ci), ni2 = make_float2(-ci, -ci);
+          const float2 pr = v[12 * b + 2 * j], pi = v[12 * b + 2 * j + 1];
+          re = fma2(c2, pr, re);
+          re = fma2(ni2, pi, re);
+          im = fma2(c2, pi, im);
+          im = fma2(i2, pr, im);
+        }
+        o[12 * b + 2 * i] = re;
+        o[12 * b + 2 * i + 1] = im;
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int b = 0; b < 2; b++) {
+    const float* t = tab + b * CLV_REALS;
+    float2 orr[6], oi[6];
+#pragma unroll
+    for (int i = 0; i < 6; i++) orr[i] = oi[i] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+      float vr[6], vi[6];
+#pragma unroll
+      for (int i = 0; i < 6; i++) {
+        vr[i] = t[2 * (i * 6 + j)];
+        vi[i] = t[2 * (i * 6 + j) + 1];
+      }
+      float2 re = make_float2(0.f, 0.f), im = re;
+#pragma unroll
+      for (int i = 0; i < 6; i++) {
+        const float2 pr = v[12 * b + 2 * i], pi = v[12 * b + 2 * i + 1];
+        re = fma2(make_float2(vr[i], vr[i]), pr, re);
+        re = fma2(make_float2(vi[i], vi[i]), pi, re);
+        im = fma2(make_float2(vr[i], vr[i]), pi, im);
+        im = fma2(make_float2(-vi[i], -vi[i]), pr, im);
+      }
+      const float lam = t[72 + j];
+      const float2 f = make_float2(1.f / (a.x + lam), 1.f / (a.y + lam));
+      const float2 wr = mul2(f, re), wi = mul2(f, im);
+#pragma unroll
+      for (int i = 0; i < 6; i++) {
+        orr[i] = fma2(make_float2(vr[i], vr[i]), wr, orr[i]);
+        orr[i] = fma2(make_float2(-vi[i], -vi[i]), wi, orr[i]);
+        oi[i] = fma2(make_float2(vr[i], vr[i]), wi, oi[i]);
+        oi[i] = fma2(make_float2(vi[i], vi[i]), wr, oi[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+      o[12 * b + 2 * i] = orr[i];
+      o[12 * b + 2 * i + 1] = oi[i];
+    }
+  }
+}
+
+// The paired pass over a tile of an even number of systems per block row (NB): NB / 2 threads per
+// site, each holding systems (2k, 2k + 1) of its row; blockDim.x / (NB / 2) sites per block.
+template <typename Ts, int MODE>
+__global__ void __launch_bounds__(256, 2) clover_kernel_pk(ClovArgs a) {
+  if (a.gate != nullptr && *a.gate == 0) return;
+  const Shape sh = a.sh;
+  const Geom g = a.g;
+  const int P = sh.NB / 2;
+  const int pi = threadIdx.x % P, ls = threadIdx.x / P;
+  const int S2 = blockDim.x / P;
+  const int s0 = blockIdx.y * sh.NB + 2 * pi, s1 = s0 + 1;
+  const bool sel0 = selected(a.st, s0, a.mask), sel1 = selected(a.st, s1, a.mask);
+  if (!sel0 && !sel1) return;  // no barriers below
+  const float2 A = make_float2(sel0 ? coef<float>(a.st[s0], C_A) : 1.f, sel1 ? coef<float>(a.st[s1], C_A) : 1.f);
+  const Field<Ts> in = make_field<Ts>(const_cast<void*>(a.in), g.Vh, sh.N, false);
+  const Field<Ts> out = make_field<Ts>(a.out, g.Vh, sh.N, false);
+  const Field<Ts> Y = make_field<Ts>(const_cast<void*>(a.Y), g.Vh, sh.N, false);
+  const float* table = (const float*)a.table;
+  const int nchunk2 = (g.Vh + S2 - 1) / S2;
+  for (int chunk = blockIdx.x; chunk < nchunk2; chunk += gridDim.x) {
+    const int site = chunk * S2 + ls;
+    if (site >= g.Vh) continue;
+    float v0[24], v1[24];
+    in.load(site, s0, v0);
+    in.load(site, s1, v1);
+    float2 v[24], o[24];
+#pragma unroll
+    for (int k = 0; k < 24; k++) v[k] = make_float2(v0[k], v1[k]);
+    clover_site_pk<MODE>(table + ((size_t)a.parity * g.Vh + site) * 2 * CLV_REALS, A, v, o);
+    if constexpr (MODE == CLV_SUB) {
+      Y.load(site, s0, v0);
+      Y.load(site, s1, v1);
+#pragma unroll
+      for (int k = 0; k < 24; k++) o[k] = make_float2(v0[k] - o[k].x, v1[k] - o[k].y);
+    }
+#pragma unroll
+    for (int k = 0; k < 24; k++) { v0[k] = o[k].x; v1[k] = o[k].y; }
+    if (sel0) out.store(site, s0, v0);
+    if (sel1) out.store(site, s1, v1);
   }
 }
 

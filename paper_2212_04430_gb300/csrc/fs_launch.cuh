@@ -177,8 +177,16 @@ cudaError_t launch_clover(int mode, const ClovArgs& a, const Launch& l) {
   using Tc = typename std::conditional<std::is_same<Ts, double>::value, double, float>::type;
   const dim3 grid(l.grid_x, l.grid_y), block(l.block);
   if (a.sysmajor && !std::is_same<Ts, double>::value) return cudaErrorInvalidValue;  // FP64 fields only
+  // the paired pass where the block rows hold an even number of systems that divides 512
+  const bool paired = !std::is_same<Ts, double>::value && !a.sysmajor && a.sh.NB % 2 == 0 && 256 % (a.sh.NB / 2) == 0;
 #define FS_CLV(M)                                                                                         \
   if (mode == M) {                                                                                        \
+    if constexpr (!std::is_same<Ts, double>::value)                                                       \
+      if (paired) {                                                                                       \
+        clover_kernel_pk<Ts, M><<<grid, 256, 0, l.stream>>>(a);                                           \
+        note_launch();                                                                                    \
+        return cudaGetLastError();                                                                        \
+      }                                                                                                   \
     if (a.sysmajor) clover_kernel<Ts, Tc, Tm, M, true><<<grid, block, 0, l.stream>>>(a);                 \
     else clover_kernel<Ts, Tc, Tm, M, false><<<grid, block, 0, l.stream>>>(a);                           \
     note_launch();                                                                                        \
