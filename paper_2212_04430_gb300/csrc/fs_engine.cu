@@ -239,15 +239,17 @@ class Tile : public TileBase {
   bool clv() const { return c->c_sw != 0.0; }
   // A clover pass over the systems of `mask`: the tile layout in the storage precision, or the
   // FP64 system-major work list (sysmajor).
+  // f32: the FP64 work list in FP32 arithmetic (the FP32-arithmetic reliable updates).
   cudaError_t clover_pass(int mode, void* out, const void* in, const void* Y, int parity, int mask, bool gated,
-                          bool sysmajor) {
+                          bool sysmajor, bool f32 = false) {
     ClovArgs a{};
     a.out = out; a.in = in; a.Y = Y;
-    a.table = (sysmajor || std::is_same<Ts, double>::value) ? (const void*)c->clover64 : (const void*)c->clover32;
+    a.table = ((sysmajor && !f32) || std::is_same<Ts, double>::value) ? (const void*)c->clover64
+                                                                      : (const void*)c->clover32;
     a.st = st_d; a.gate = gated ? gate : nullptr;
     a.g = c->g; a.sh = sysmajor ? sh1 : sh; a.parity = parity; a.mask = mask;
     a.sysmajor = sysmajor ? 1 : 0;
-    if (sysmajor) return launch_clover<double>(mode, a, LW);
+    if (sysmajor) return f32 ? launch_clover64_f32(mode, a, LW) : launch_clover<double>(mode, a, LW);
     return launch_clover<Ts>(mode, a, L);
   }
 
@@ -278,8 +280,8 @@ class Tile : public TileBase {
     f.target = 0.25;  // rms of a scaled residual entry (keeps FP16 away from both range limits)
     f.nreal = 24.0 * c->g.Vh;
     f.max_restarts = 8;
-    // the Wilson-clover reliable updates are all FP64 and leave A_oo^-1 H_oe x_e in the scratch
-    f.first_approx = std::is_same<Ts, double>::value || clv() ? 0 : 1;
+    // (the Wilson-clover updates leave A_oo^-1 H_oe x_e in the scratch, not H_oe x_e)
+    f.first_approx = std::is_same<Ts, double>::value ? 0 : 1;
     // tmp64 is a buffer of its own in the mixed precisions (FP64 storage shares it with tmp,
     // which the other systems' iterations overwrite)
     f.hx_kept = std::is_same<Ts, double>::value || clv() ? 0 : 1;
@@ -424,19 +426,37 @@ class Tile : public TileBase {
     //    previous (FP64) update, held in x_o (free until the odd sites are reconstructed); the
     //    FP32 error is about eps32 A ||dx||, relative to the small dx instead of x.
     // The FP64 storage mode keeps FP64 throughout.
-    // The Wilson-clover operator takes every update in FP64: r = bhat - C_ee x - A x + H_eo A_oo^-1 H_oe x / 4,
-    // the clover parts by passes (x_o, free until the reconstruction, holds bhat - C_ee x).
     constexpr bool mixed = !std::is_same<Ts, double>::value;
-    if ((e = launch_blas<Ts>(OP_ACCX, blas(MASK_UPDATE, mixed && !cl ? x_o : nullptr, nullptr, true, true), LW)))
-      return e;
+    if ((e = launch_blas<Ts>(OP_ACCX, blas(MASK_UPDATE, mixed ? x_o : nullptr, nullptr, true, true), LW))) return e;
     if (cl) {
+      // Wilson-clover: r = bhat - C_ee x - A x + H_eo A_oo^-1 H_oe x / 4, the clover parts by passes, in the
+      // same three forms as below (x_o holds bhat - C_ee x for a full residual, dx for a correction,
+      // whose r_prev - C_ee dx is formed in place)
+      int lat = MASK_UPDATE;
+      if constexpr (mixed) {
+        lat = MASK_UPDATE_LATER;
+        void* g32 = c->gauge_for(PREC_F32, 18);
+        HopArgs h1 = hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, MASK_UPDATE_FIRST, true, true, true);
+        HopArgs h2 = hop(r_hi, tmp64, x_hi, x_o, nullptr, pa, 0, MASK_UPDATE_FIRST, true, true, true);
+        HopArgs h3 = hop(tmp64, x_o, nullptr, nullptr, nullptr, nullptr, 1, MASK_UPDATE_CORR, true, true, true);
+        HopArgs h4 = hop(r_hi, tmp64, x_o, r_hi, nullptr, pa, 0, MASK_UPDATE_CORR, true, true, true);
+        h1.gauge = h2.gauge = h3.gauge = h4.gauge = g32;
+        if ((e = launch_hop64_f32(COEF_PLAIN, DOT_NONE, h1, lwh()))) return e;
+        if ((e = clover_pass(CLV_INV, tmp64, tmp64, nullptr, 1, MASK_UPDATE_FIRST, true, true, true))) return e;
+        if ((e = clover_pass(CLV_SUB, x_o, x_hi, bhat, 0, MASK_UPDATE_FIRST, true, true, true))) return e;
+        if ((e = launch_hop64_f32(COEF_TRUERES, DOT_NORM, h2, lwh()))) return e;
+        if ((e = launch_hop64_f32(COEF_PLAIN, DOT_NONE, h3, lwh()))) return e;
+        if ((e = clover_pass(CLV_INV, tmp64, tmp64, nullptr, 1, MASK_UPDATE_CORR, true, true, true))) return e;
+        if ((e = clover_pass(CLV_SUB, r_hi, x_o, r_hi, 0, MASK_UPDATE_CORR, true, true, true))) return e;
+        if ((e = launch_hop64_f32(COEF_TRUERES, DOT_NORM, h4, lwh()))) return e;
+      }
       if ((e = hop_hi(COEF_PLAIN, DOT_NONE,
-                      hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, MASK_UPDATE, true, true, true), lwh())))
+                      hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, lat, true, true, true), lwh())))
         return e;
-      if ((e = clover_pass(CLV_INV, tmp64, tmp64, nullptr, 1, MASK_UPDATE, true, true))) return e;
-      if ((e = clover_pass(CLV_SUB, x_o, x_hi, bhat, 0, MASK_UPDATE, true, true))) return e;
-      if ((e = hop_hi(COEF_TRUERES, DOT_NORM,
-                      hop(r_hi, tmp64, x_hi, x_o, nullptr, pa, 0, MASK_UPDATE, true, true, true), lwh())))
+      if ((e = clover_pass(CLV_INV, tmp64, tmp64, nullptr, 1, lat, true, true))) return e;
+      if ((e = clover_pass(CLV_SUB, x_o, x_hi, bhat, 0, lat, true, true))) return e;
+      if ((e = hop_hi(COEF_TRUERES, DOT_NORM, hop(r_hi, tmp64, x_hi, x_o, nullptr, pa, 0, lat, true, true, true),
+                      lwh())))
         return e;
       if ((e = fin(FIN_TRUE, MASK_UPDATE, pa))) return e;
       if ((e = launch_blas<Ts>(OP_SETR, blas(MASK_UPDATE, r_hi, pa, true, true), LW))) return e;

@@ -45,6 +45,9 @@ template <typename Ts> cudaError_t launch_hop(int coef, int dot, int nr, const H
 // of a system's first reliable update (fs_kern_f32.cu); COEF_PLAIN / DOT_NONE and COEF_TRUERES /
 // DOT_NORM only.
 cudaError_t launch_hop64_f32(int coef, int dot, const HopArgs& a, const Launch& l);
+// The clover passes of those updates: FP64 fields, the FP32 table and FP32 arithmetic, system-major
+// work list (fs_kern_f32.cu); CLV_SUB and CLV_INV only.
+cudaError_t launch_clover64_f32(int mode, const ClovArgs& a, const Launch& l);
 template <typename Ts> cudaError_t launch_blas(int op, const BlasArgs& a, const Launch& l);
 // Clover passes (fs_clover.cuh): tile layout in the storage precision (FP32 table and arithmetic
 // for the inner precisions), or the FP64 system-major work list when a.sysmajor (Ts = double).

@@ -17,4 +17,14 @@ cudaError_t launch_hop64_f32(int coef, int dot, const HopArgs& a, const Launch& 
   note_launch();
   return cudaGetLastError();
 }
+
+cudaError_t launch_clover64_f32(int mode, const ClovArgs& a, const Launch& l) {
+  const dim3 grid(l.grid_x, l.grid_y), block(l.block);
+  if (!a.sysmajor) return cudaErrorInvalidValue;
+  if (mode == CLV_SUB) clover_kernel<double, float, float, CLV_SUB, true><<<grid, block, 0, l.stream>>>(a);
+  else if (mode == CLV_INV) clover_kernel<double, float, float, CLV_INV, true><<<grid, block, 0, l.stream>>>(a);
+  else return cudaErrorInvalidValue;
+  note_launch();
+  return cudaGetLastError();
+}
 }  // namespace fs
