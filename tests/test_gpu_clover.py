@@ -214,3 +214,30 @@ def test_clover_refuses_the_hopping_parameter_expansion():
         ctx.hpe_exact_trace(-0.2, 0.5, g, 0, 2)
     assert e.value.code == pkg.fsmlmc.FS_ERR_ARG
     ctx.close()
+
+
+def test_clover_16x32_dslash_and_solves_at_the_bench_precision():
+    """The bench lattice, links and precision with the clover term: the FP16 dslash (12-real links,
+    16-system tile, the paired clover pass) against the oracle's D_sw on sampled vectors, and solves
+    at the bench's smallest and largest shift certified by the oracle's own D_sw residual."""
+    dims = (16, 16, 16, 32)
+    u = inputs.gauge_field(dims, "smooth", seed=1003, eps=0.4)
+    c_sw = 1.0
+    cterm = cterm_of(u, dims, c_sw)
+    ctx = make_ctx(dims, u, c_sw)
+    psi = inputs.random_spinor(dims, 23, nvec=16)
+    got = ctx.wilson_dslash(-0.35, 0.03, psi, prec="f16", link_compress=12)
+    for k in (0, 7, 15):
+        ref = oracle_Dsw(u, psi[k], -0.35, 0.03, dims, cterm)
+        assert rel_err(got[k], ref) < DSLASH_TOL["f16"], (k, rel_err(got[k], ref))
+    del got, psi
+    b = inputs.random_spinor(dims, 24, nvec=2)
+    sig = [0.005, 0.6]
+    x, st, rc = ctx.shifted_solve(-0.35, sig, b, prec="f16", tol=1e-8, rhs_tile=4, link_compress=12)
+    assert rc == 0
+    for j, s in enumerate(sig):
+        for k in range(2):
+            r = rel_resid_sw(u, x[j, k], b[k], -0.35, s, dims, cterm)
+            assert r <= 1.05e-8, (s, k, r)
+            assert st[j * 2 + k]["status"] == 2
+    ctx.close()
