@@ -181,6 +181,29 @@ def test_mlmc_clover_samples_against_dense(prec, tol, est):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f16", 1e-6)])
+def test_variance_sample_clover_against_dense(prec, tol):
+    """Sec. 3.1's sampling (a_i, b_ij and the sampled variances) with the clover term: the adjoint
+    solves use gamma_5-hermiticity, which D_sw keeps."""
+    dims = (4, 4, 2, 4)
+    u = inputs.gauge_field(dims, "smooth", seed=1209, eps=0.5)
+    c_sw, m = 1.1, -0.3
+    s_hat = [0.0, 0.1, 0.4]
+    plist = [1, 0]
+    ns = 3
+    ctx = make_ctx(dims, u, c_sw)
+    out = ctx.variance_sample(m, s_hat, pkg.gamma_matrix("g3"), plist, ns, seed=2006, job=1, prec=prec,
+                              tol=1e-12 if prec == "f64" else 1e-10)
+    solver = oest.make_dense_solver(u, m, dims, -1, cterm_of(u, dims, c_sw))
+    ref = oest.variance_sample(u, m, s_hat, odirac.GAMMA[2], plist, ns, 2006, 1, dims, -1, solver)
+    for pi in range(len(plist)):
+        for i in range(len(s_hat)):
+            assert sample_err(out["a"][:, pi, i], ref["a"][:, pi, i]) < tol
+            for j in range(i, len(s_hat)):
+                assert sample_err(out["b"][:, pi, i, j], ref["b"][:, pi, i, j]) < tol
+    ctx.close()
+
+
 def test_clover_tile_shapes_give_identical_systems():
     """The clover passes and the clover M-hat compute a system the same way in every tile shape:
     64-, 40- and 1-system tiles give bit-identical FP16 solutions."""
