@@ -186,14 +186,16 @@ FS_API int fs_set_gauge(fs_ctx* ctx, const double* U);
  * sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu], F_{mu nu} = (Q_{mu nu} - Q_{mu nu}^dag) / (8i), Q_{mu nu}(x)
  * the sum of the four counter-clockwise plaquettes of the (mu, nu) plane at x (the paper states no
  * normalisation: this is the reading). C is Hermitian, commutes with gamma_5 and is eigen-
- * decomposed once per gauge field into a table of V Vh complex 6x6 blocks (about 2.7 KB per
- * site in FP64 + FP32), so that (A + C)^-1 for every shift costs two 6x6 products per chirality.
+ * decomposed once per gauge field into a table of two complex 6x6 blocks per site (about 2.7 KB
+ * per site in FP64 + FP32), so that (A + C)^-1 for every shift costs two 6x6 products per chirality.
  * The table is built now if a gauge field is set, else by the next fs_set_gauge, and rebuilt by
  * every fs_set_gauge; c_sw = 0 frees it and restores the Wilson operator. With the clover term
- * the reliable updates are all FP64 and there is no CGNR fallback; the hopping parameter
- * expansion (hpe_order, fs_hpe_exact_trace) is refused with FS_ERR_ARG, and
- * wilson_dslash_noalloc stays the Wilson operator. FS_ERR_INPUT for a non-finite c_sw,
- * FS_ERR_STATE on a lane, 3 when the table does not fit. */
+ * there is no CGNR fallback, the hopping parameter expansion (hpe_order, fs_hpe_exact_trace) is
+ * the generalised one of Sec. 3.1, D_sw + sigma = A(x) (1 - K), K = A(x)^-1 H / 2 with
+ * A(x) = 4 + m + sigma + C(x): T_exact = sum_{k<K} Tr(Gamma Omega_p K^k A^-1) and the remainder
+ * z^dag Gamma Omega_p K^K (D_sw + sigma)^-1 z, and wilson_dslash_noalloc stays the Wilson
+ * operator. FS_ERR_INPUT for a non-finite c_sw, FS_ERR_STATE on a lane, 3 when the table does
+ * not fit. */
 FS_API int fs_set_clover(fs_ctx* ctx, double c_sw);
 
 /* ---- the operations of the paper -------------------------------------------------- */
@@ -255,7 +257,10 @@ FS_API int fs_mlmc_num_solves(const fs_mlmc_params* params);
  * spin-colour dilution: 12 c FP64 vectors (pieces of a Z4 vector from `seed`; the result does not
  * depend on it), K - 1 kappa H applications each, one contraction per order. The value
  * mlmc_level_trace adds to every last-level sample with hpe_order = K. params: rhs_tile (0 = 64
- * pieces at a time); the other fields are unused. K in 1..8, 0 <= p < Lz, else FS_ERR_ARG. */
+ * pieces at a time); the other fields are unused. K in 1..8, 0 <= p < Lz, else FS_ERR_ARG.
+ * With the clover term (fs_set_clover) the generalised expansion: T = sum_{k<K} Tr(Gamma Omega_p
+ * K^k A^-1), K = A(x)^-1 H / 2, A(x) = A + C(x), every order (order 0 included) from the pieces,
+ * with distance-max(K-1, 1) colours. */
 FS_API int fs_hpe_exact_trace(fs_ctx* ctx, double m, double sigma, const double* gamma, int p, int K, uint64_t seed,
                        const fs_solve_params* params, double* out);
 

@@ -579,8 +579,6 @@ int fs_hpe_exact_trace(fs_ctx* ctx, double m, double sigma, const double* gamma,
                        const fs_solve_params* params, double* out) {
   if (!ctx) return FS_ERR_ARG;
   Ctx& c = ctx->c;
-  if (c.c_sw != 0.0)
-    return c.fail(FS_ERR_ARG, "the hopping parameter expansion is the Wilson operator's (clover term set)");
   if (!gamma || !out) return c.fail(FS_ERR_ARG, "null pointer");
   if (!c.have_gauge) return c.fail(FS_ERR_STATE, "no gauge field set");
   if (K < 1 || K > 8) return c.fail(FS_ERR_ARG, "K must be in [1, 8]");
@@ -675,8 +673,6 @@ int mlmc_impl(Ctx& c, const fs_mlmc_params* P, const int* p_in, int np, double* 
   const int npieces = num_pieces(P);
   const int ncomp = P->dilute ? 12 : 1;
   if (P->hpe_order < 0 || P->hpe_order > 8) return c.fail(FS_ERR_ARG, "hpe_order must be in [0, 8]");
-  if (P->hpe_order > 0 && c.c_sw != 0.0)
-    return c.fail(FS_ERR_ARG, "the hopping parameter expansion is the Wilson operator's (clover term set)");
   // the expansion converges for A = 4 + m + sigma > 4 only (Sec. 3.1 uses it where m + s > 0)
   const bool hpe = P->hpe_order > 0 && P->m + P->sigma[L] > 0.0;
   // the exact low orders take Omega_0 = 1; a displacement of a whole period is a Polyakov loop
@@ -863,8 +859,6 @@ int variance_sample_impl(Ctx& c, double m, const double* s_hat, int ms, const do
                          int ncolors, int dilute, int hpe_order, double* VL, double* Vbar, double* a_out,
                          double* b_out, double* iters) {
   if (hpe_order < 0 || hpe_order > 8) return c.fail(FS_ERR_ARG, "hpe_order must be in [0, 8]");
-  if (hpe_order > 0 && c.c_sw != 0.0)
-    return c.fail(FS_ERR_ARG, "the hopping parameter expansion is the Wilson operator's (clover term set)");
   if (!s_hat || !gamma || !p || !VL || !Vbar) return c.fail(FS_ERR_ARG, "null pointer");
   if (ms < 1 || 2 * ms > fs::MAX_TILE) return c.fail(FS_ERR_ARG, "m_shifts must be in [1, 32]");
   if (np < 1 || np > fs::CONTRACT_MAXP) return c.fail(FS_ERR_ARG, "np must be in [1, 16]");

@@ -221,19 +221,23 @@ int autotune_tile(Ctx* c, const SolveOpts& o, int nmax) {
 // contraction.
 int hpe_exact(Ctx* c, TileBase* T, const SolveOpts& o, double sigma, int K, int p, const double* gamma,
               uint64_t seed, double out[2]) {
-  const double A = 4.0 + o.m + sigma;
+  // Wilson-clover (the generalised expansion): T = sum_{k<K} Tr(Gamma Omega_p K^k A^-1), K = A(x)^-1 H / 2,
+  // A(x) = A + C(x) per site, every order from the pieces (order 0 has no closed form), no 1/A
+  const bool clv = c->c_sw != 0.0;
+  const double A = clv ? 1.0 : 4.0 + o.m + sigma;
   double tr = 0.0, ti = 0.0;
   if (p < 0 || p >= c->g.L[2]) return c->fail(1, "the expansion's exact part needs 0 <= p < Lz");
   const int pz = p;
-  if (pz == 0)
+  if (pz == 0 && !clv)
     for (int s = 0; s < 4; s++) {
       tr += 3.0 * c->g.V * gamma[(s * 4 + s) * 2];
       ti += 3.0 * c->g.V * gamma[(s * 4 + s) * 2 + 1];
     }
-  if (K > 1) {
+  if (K > 1 || clv) {
     std::vector<int32_t> colors((size_t)c->g.V);
     int nc = 0;
-    if (int rc = fs_probing_colors(c->g.L, K - 1, pz, colors.data(), &nc))
+    // (order 0 alone, with the clover term: distance-1 colours, finer than it needs)
+    if (int rc = fs_probing_colors(c->g.L, std::max(K - 1, 1), pz, colors.data(), &nc))
       return c->fail(rc, "probing colours of the hopping parameter expansion");
     if (int rc = upload_colors(c, colors.data())) return rc;
     const int N = T->N;
@@ -270,6 +274,17 @@ int hpe_exact(Ctx* c, TileBase* T, const SolveOpts& o, double sigma, int K, int 
       if ((e = upload_slots(c, T, all))) return c->cuda_fail(e, "hopping parameter expansion");
       if ((e = T->enqueue_noise())) return c->cuda_fail(e, "hopping parameter expansion");
       int from = PAIR_Z;
+      if (clv) {
+        // order 0: A(x)^-1 e
+        if ((e = T->enqueue_site_inverse(PAIR_Z, PAIR_S))) return c->cuda_fail(e, "hopping parameter expansion");
+        std::vector<double> part;
+        if (int rc = contract_tile(c, T, pairs, gamma, plist, part, N, PAIR_S)) return rc;
+        for (int j = 0; j < nb; j++) {
+          tr += part[(size_t)j * 2];
+          ti += part[(size_t)j * 2 + 1];
+        }
+        from = PAIR_S;
+      }
       for (int k = 1; k < K; k++) {
         const int to = (from == PAIR_S) ? PAIR_X : PAIR_S;
         if ((e = T->enqueue_kappa_hop(from, to))) return c->cuda_fail(e, "hopping parameter expansion");

@@ -595,13 +595,25 @@ class Tile : public TileBase {
     L1.stream = c->stream;
     LW.stream = c->stream;
     // even <- kappa H_eo (odd), odd <- kappa H_oe (even); FP64 work list over the FLAG_HPE slots
+    // (Wilson-clover: H / 2, then A(x)^-1 in place)
     cudaError_t e = launch_hop<double>(COEF_KAPPA, DOT_NONE, 18,
                                        hop(field_pair(to, 0), field_pair(from, 1), nullptr, nullptr, nullptr, nullptr,
                                            0, MASK_HPE, false, true, true), lwh());
     if (e) return e;
-    return launch_hop<double>(COEF_KAPPA, DOT_NONE, 18,
-                              hop(field_pair(to, 1), field_pair(from, 0), nullptr, nullptr, nullptr, nullptr, 1,
-                                  MASK_HPE, false, true, true), lwh());
+    if ((e = launch_hop<double>(COEF_KAPPA, DOT_NONE, 18,
+                                hop(field_pair(to, 1), field_pair(from, 0), nullptr, nullptr, nullptr, nullptr, 1,
+                                    MASK_HPE, false, true, true), lwh())))
+      return e;
+    return clv() ? enqueue_site_inverse(to, to) : cudaSuccess;
+  }
+
+  cudaError_t enqueue_site_inverse(int from, int to) override {
+    if (!clv()) return cudaErrorInvalidValue;
+    L1.stream = c->stream;
+    LW.stream = c->stream;
+    cudaError_t e = clover_pass(CLV_INV, field_pair(to, 0), field_pair(from, 0), nullptr, 0, MASK_HPE, false, true);
+    if (e) return e;
+    return clover_pass(CLV_INV, field_pair(to, 1), field_pair(from, 1), nullptr, 1, MASK_HPE, false, true);
   }
 
   cudaError_t enqueue_dslash(double* canon) override {

@@ -118,8 +118,12 @@ class TileBase {
   // right-hand side (z_e, z_o), PAIR_S scratch (r_hi and the FP64 temporary); the last two are
   // free once a system has finished
   virtual double* field_pair(int id, int parity) = 0;
-  // pair `to` <- kappa H (pair `from`), full lattice, FP64, for the FLAG_HPE slots
+  // pair `to` <- kappa H (pair `from`), full lattice, FP64, for the FLAG_HPE slots (Wilson-clover:
+  // to <- A(x)^-1 H from / 2, the generalised expansion)
   virtual cudaError_t enqueue_kappa_hop(int from, int to) = 0;
+  // pair `to` <- A(x)^-1 (pair `from`) with A(x) = 4 + m + sigma + C(x), FP64, for the FLAG_HPE slots
+  // (the Wilson-clover operator only)
+  virtual cudaError_t enqueue_site_inverse(int from, int to) = 0;
   // Staging of finished solutions (run_queue): S columns laid out like the tile's FP64 fields
   // (system-major, one column = one system's parity, 24 Vh doubles, contiguous), so a slot's
   // solution moves with plain device copies and its slot is free at once. y holds the

@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(WL ? 128 : 256, WL ? 3 : (sizeof(Tm) == 8 ? 2 
       else if (COEF == COEF_RECON) { ca = cl ? (Tm)1 : coef<Tm>(s, C_INVA); cb = cl ? (Tm)0.5 : coef<Tm>(s, C_INV2A); }
       else if (COEF == COEF_TRUERES) { ca = coef<Tm>(s, C_MINVA); cb = cl ? (Tm)0.25 : coef<Tm>(s, C_INV4A); }
       else if (COEF == COEF_FULLRES) { ca = coef<Tm>(s, C_MINVA); cb = (Tm)0.5; }
-      else if (COEF == COEF_KAPPA) { cb = coef<Tm>(s, C_INV2A); }
+      else if (COEF == COEF_KAPPA) { cb = cl ? (Tm)0.5 : coef<Tm>(s, C_INV2A); }  // clover: then A(x)^-1
     }
     const int site = chunk * sh.SB + lsite;
     const bool act = sel && site < g.Vh;

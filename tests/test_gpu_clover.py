@@ -225,18 +225,51 @@ def test_clover_tile_shapes_give_identical_systems():
     ctx.close()
 
 
-def test_clover_refuses_the_hopping_parameter_expansion():
+@pytest.mark.parametrize("p,K", [(0, 4), (1, 3), (0, 1)])
+def test_last_level_with_the_generalised_expansion(p, K):
+    """Sec. 3.1's expansion for the clover action: the last level's samples are T_exact +
+    z^dag G Om K^K (D_sw + s)^-1 z, K = A(x)^-1 H / 2, against the oracle's own probing and dense
+    solves."""
+    from oracle import hpe as ohpe
+    from oracle import philox as ophilox
+    from oracle import probing as opr
     dims = (4, 4, 4, 4)
-    u = inputs.gauge_field(dims, "smooth", seed=1208, eps=0.3)
-    ctx = make_ctx(dims, u, 1.0)
-    g = pkg.gamma_matrix("g5")
-    with pytest.raises(pkg.FsError) as e:
-        ctx.mlmc_level_trace(-0.2, [0.0, 0.5], g, 0, [2, 2], seed=1, hpe_order=2)
-    assert e.value.code == pkg.fsmlmc.FS_ERR_ARG
-    with pytest.raises(pkg.FsError) as e:
-        ctx.hpe_exact_trace(-0.2, 0.5, g, 0, 2)
-    assert e.value.code == pkg.fsmlmc.FS_ERR_ARG
+    v = int(np.prod(dims))
+    u = inputs.gauge_field(dims, "smooth", seed=1210, eps=0.5)
+    c_sw, m, sig = 1.0, -0.2, [0.05, 0.6]
+    ct = cterm_of(u, dims, c_sw)
+    n = [2, 4]
+    ctx = make_ctx(dims, u, c_sw)
+    out = ctx.mlmc_level_trace(m, sig, pkg.gamma_matrix("g3"), p, n, seed=22, job=1, hpe_order=K, estimator="diff",
+                               prec="f64", tol=1e-12, rhs_tile=16)
+    assert out["rc"] == 0
+    go = odirac.gamma_product(["g3"])
+    col, nc = opr.greedy_coloring(dims, K - 1, p)
+    t_exact = ohpe.exact_part_probed(u, m, sig[1], go, p, K, dims, col, nc, cterm=ct)
+    solver = oest.make_dense_solver(u, m, dims, -1, ct)
+    ref = np.array([t_exact + ohpe.stochastic_part(u, solver, ophilox.z4_noise(v, 22, 1, 1, s), m, sig[1], go, p, K,
+                                                   dims, cterm=ct) for s in range(n[1])])
+    assert sample_err(out["samples"][1], ref) < 1e-9, (out["samples"][1], ref)
+    # the exact part alone, through its own entry point
+    got = ctx.hpe_exact_trace(m, sig[1], pkg.gamma_matrix("g3"), p, K)
     ctx.close()
+    assert abs(got - t_exact) <= 1e-9 * max(1.0, abs(t_exact)), (got, t_exact)
+
+
+def test_generalised_expansion_reduces_the_last_level_variance():
+    dims = (4, 4, 4, 8)
+    u = inputs.gauge_field(dims, "smooth", seed=1211, eps=0.4)
+    m, sig = -0.2, [0.8]
+    g = pkg.gamma_matrix("g3")
+    ctx = make_ctx(dims, u, 1.0)
+    kw = dict(prec="f32", tol=1e-9, rhs_tile=64)
+    plain = ctx.mlmc_level_trace(m, sig, g, 1, [128], seed=31, **kw)
+    hpe = ctx.mlmc_level_trace(m, sig, g, 1, [128], seed=31, hpe_order=4, **kw)
+    ctx.close()
+    assert plain["rc"] == 0 and hpe["rc"] == 0
+    assert hpe["var"][0] < 0.5 * plain["var"][0]
+    se = np.sqrt(plain["var"][0] / 128 + hpe["var"][0] / 128)
+    assert abs(hpe["trace"][0] - plain["trace"][0]) < 5 * se
 
 
 def test_clover_16x32_dslash_and_solves_at_the_bench_precision():
