@@ -482,6 +482,9 @@ def run_clover(pkg, ctx, w, kw, n=64, c_sw=1.0, seed=9600):
         if c:
             res[name]["c_sw"] = c
             res[name]["table_build_s"] = build_s
+            if w["m"] + w["sigmas"][-1] > 0:
+                # the generalised hopping parameter expansion of the last level (Sec. 3.1)
+                res[name]["hpe"] = run_hpe(pkg, ctx, w, kw)
     ctx.fs_set_clover(0.0)
     res["iteration_cost_ratio"] = res["wilson"]["system_iterations_per_s"] / res["clover"]["system_iterations_per_s"]
     res["note"] = ("%d Z4 vectors per level (seed %d), the workload's precision, tile and lanes; "

@@ -190,7 +190,8 @@ FS_API int fs_set_gauge(fs_ctx* ctx, const double* U);
  * per site in FP64 + FP32), so that (A + C)^-1 for every shift costs two 6x6 products per chirality.
  * The table is built now if a gauge field is set, else by the next fs_set_gauge, and rebuilt by
  * every fs_set_gauge; c_sw = 0 frees it and restores the Wilson operator. With the clover term
- * there is no CGNR fallback, the hopping parameter expansion (hpe_order, fs_hpe_exact_trace) is
+ * the CGNR fallback runs on the clover M-hat (still M-hat^dag = gamma_5 M-hat gamma_5), the
+ * hopping parameter expansion (hpe_order, fs_hpe_exact_trace) is
  * the generalised one of Sec. 3.1, D_sw + sigma = A(x) (1 - K), K = A(x)^-1 H / 2 with
  * A(x) = 4 + m + sigma + C(x): T_exact = sum_{k<K} Tr(Gamma Omega_p K^k A^-1) and the remainder
  * z^dag Gamma Omega_p K^K (D_sw + sigma)^-1 z, and wilson_dslash_noalloc stays the Wilson

@@ -168,8 +168,7 @@ int resolve_params(Ctx& c, const fs_solve_params* p, int nsys, double m, Opts& o
   if (o.so.delta >= 1.0) return c.fail(FS_ERR_ARG, "delta must be < 1");
   o.so.verify = d.verify;
   o.so.check_every = 4;
-  // the CGNR fallback and the hopping parameter expansion are the Wilson operator's
-  if (d.fallback_iter < 0 || c.c_sw != 0.0) o.so.cg_max_iter = 0;
+  if (d.fallback_iter < 0) o.so.cg_max_iter = 0;
   else if (d.fallback_iter > 0) o.so.cg_max_iter = d.fallback_iter;
   else o.so.cg_max_iter = (int)std::min<long long>(4LL * o.so.max_iter, 1 << 30);
   int tile = d.rhs_tile;

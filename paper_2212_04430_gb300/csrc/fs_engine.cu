@@ -653,16 +653,25 @@ class Tile : public TileBase {
     note_launch();
     return cudaGetLastError();
   }
+  // out = M-hat in on the FP64 work list over mask, ||out||^2 -> part when part != nullptr. The
+  // Wilson-clover M-hat takes its clover passes, with C_ee in in x_o (free until the reconstruction).
+  cudaError_t mhat64(double* out, const double* in, int mask, double* part) {
+    cudaError_t e;
+    if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
+                                hop(tmp64, in, nullptr, nullptr, nullptr, nullptr, 1, mask, false, true, true), lwh())))
+      return e;
+    const bool cl = clv();
+    if (cl && ((e = clover_pass(CLV_INV, tmp64, tmp64, nullptr, 1, mask, false, true)) ||
+               (e = clover_pass(CLV_MUL, x_o, in, nullptr, 0, mask, false, true))))
+      return e;
+    return launch_hop<double>(COEF_MHAT, part ? DOT_NORM : DOT_NONE, 18,
+                              hop(out, tmp64, in, cl ? x_o : nullptr, nullptr, part, 0, mask, false, true, true), lwh());
+  }
   // r = M^dag s = gamma5 M gamma5 s, ||r||^2 -> part
   cudaError_t cg_normal_residual(int mask, double* part) {
     cudaError_t e;
     if ((e = cg_op<CG_G5>(mask))) return e;
-    if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
-                                hop(tmp64, cg_g, nullptr, nullptr, nullptr, nullptr, 1, mask, false, true, true), lwh())))
-      return e;
-    if ((e = launch_hop<double>(COEF_MHAT, DOT_NONE, 18,
-                                hop(cg_w, tmp64, cg_g, nullptr, nullptr, nullptr, 0, mask, false, true, true), lwh())))
-      return e;
+    if ((e = mhat64(cg_w, cg_g, mask, nullptr))) return e;
     return cg_op<CG_R>(mask, part);
   }
   // s = bhat - M x (into r_hi), ||s||^2 -> part
@@ -671,8 +680,14 @@ class Tile : public TileBase {
     if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
                                 hop(tmp64, x_hi, nullptr, nullptr, nullptr, nullptr, 1, mask, false, true, true), lwh())))
       return e;
+    const double* y = bhat;
+    if (clv()) {  // bhat - C_ee x - A x + H_eo A_oo^-1 H_oe x / 4
+      if ((e = clover_pass(CLV_INV, tmp64, tmp64, nullptr, 1, mask, false, true))) return e;
+      if ((e = clover_pass(CLV_SUB, x_o, x_hi, bhat, 0, mask, false, true))) return e;
+      y = x_o;
+    }
     return launch_hop<double>(COEF_TRUERES, DOT_NORM, 18,
-                              hop(r_hi, tmp64, x_hi, bhat, nullptr, part, 0, mask, false, true, true), lwh());
+                              hop(r_hi, tmp64, x_hi, y, nullptr, part, 0, mask, false, true, true), lwh());
   }
   cudaError_t enqueue_cg_init() override {
     L1.stream = c->stream;
@@ -688,12 +703,7 @@ class Tile : public TileBase {
     LW.stream = c->stream;
     cudaError_t e;
     // q = M p, alpha = <r, r> / ||q||^2
-    if ((e = launch_hop<double>(COEF_PLAIN, DOT_NONE, 18,
-                                hop(tmp64, cg_p, nullptr, nullptr, nullptr, nullptr, 1, MASK_CG, false, true, true), lwh())))
-      return e;
-    if ((e = launch_hop<double>(COEF_MHAT, DOT_NORM, 18,
-                                hop(cg_q, tmp64, cg_p, nullptr, nullptr, pa, 0, MASK_CG, false, true, true), lwh())))
-      return e;
+    if ((e = mhat64(cg_q, cg_p, MASK_CG, pa))) return e;
     if ((e = fin(FIN_CG_ALPHA, MASK_CG, pa))) return e;
     if ((e = cg_op<CG_XS>(MASK_CG, pa))) return e;   // x += alpha p, s -= alpha q
     if ((e = cg_normal_residual(MASK_CG, pb))) return e;

@@ -101,7 +101,18 @@ cudaError_t launch_hop(int coef, int dot, int nr, const HopArgs& a, const Launch
     return cudaGetLastError();                                                               \
   }
   if (a.clover && (coef == COEF_MHAT || coef == COEF_DSLASH)) {
-    if (a.sysmajor) return cudaErrorInvalidValue;  // the work-list forms are the Wilson operator's
+    if (a.sysmajor) {
+      // the FP64 work-list M-hat of the CGNR fallback
+      if constexpr (std::is_same<Ts, double>::value) {
+        if (coef == COEF_MHAT && nr == 18 && (dot == DOT_NONE || dot == DOT_NORM)) {
+          if (dot == DOT_NONE) hop_kernel<Ts, Tg, Tm, 18, COEF_MHAT, DOT_NONE, true, true><<<grid, block, 0, l.stream>>>(a);
+          else hop_kernel<Ts, Tg, Tm, 18, COEF_MHAT, DOT_NORM, true, true><<<grid, block, 0, l.stream>>>(a);
+          note_launch();
+          return cudaGetLastError();
+        }
+      }
+      return cudaErrorInvalidValue;
+    }
     FS_HOP_CLV(COEF_MHAT, DOT_R, 18)
     FS_HOP_CLV(COEF_MHAT, DOT_TS, 18)
     FS_HOP_CLV(COEF_DSLASH, DOT_NONE, 18)

@@ -272,6 +272,31 @@ def test_generalised_expansion_reduces_the_last_level_variance():
     assert abs(hpe["trace"][0] - plain["trace"][0]) < 5 * se
 
 
+@pytest.mark.parametrize("prec", ["f64", "f16"])
+def test_cgnr_fallback_with_the_clover_term(prec):
+    """BiCGStab cut short (max_iter = 2, from the host) hands every system to the FP64 CGNR
+    fallback on the clover M-hat; the solutions meet tol by the oracle's D_sw residual and agree
+    with dense LU."""
+    dims = (4, 4, 2, 4)
+    u = inputs.gauge_field(dims, "smooth", seed=1212, eps=0.5)
+    b = inputs.random_spinor(dims, 25, nvec=2)
+    sig, tol, c_sw, m = [0.0, 0.4], 1e-10, 1.0, -0.3
+    ct = cterm_of(u, dims, c_sw)
+    ctx = make_ctx(dims, u, c_sw)
+    x, st, rc = ctx.shifted_solve(m, sig, b, prec=prec, tol=tol, max_iter=2, fallback_iter=20000, rhs_tile=4,
+                                  verify=1)
+    ctx.close()
+    assert rc == 0
+    for j, s in enumerate(sig):
+        dense = osolve.dense_operator(u, m, s, dims, -1, ct)
+        for k in range(2):
+            stt = st[j * 2 + k]
+            assert stt["status"] == 2 and stt["fallback_iters"] > 0, stt
+            assert rel_resid_sw(u, x[j, k], b[k], m, s, dims, ct) <= tol * 1.05
+            ref = np.linalg.solve(dense, b[k].ravel()).reshape(b[k].shape)
+            assert rel_err(x[j, k], ref) < 1e-7
+
+
 def test_clover_16x32_dslash_and_solves_at_the_bench_precision():
     """The bench lattice, links and precision with the clover term: the FP16 dslash (12-real links,
     16-system tile, the paired clover pass) against the oracle's D_sw on sampled vectors, and solves
