@@ -346,6 +346,8 @@ typedef struct fs_job {
   int bc_t;
   const double* U;          /* host gauge field [4][V][3][3][2]; copied by fs_server_submit   */
   fs_mlmc_params params;    /* as for mlmc_level_trace; its arrays are copied at submit       */
+  double c_sw;              /* the clover coefficient of the job's operator (fs_set_clover);
+                               0: Wilson                                                       */
 } fs_job;
 
 typedef struct fs_job_result {

@@ -15,6 +15,7 @@
 // completed jobs.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -38,6 +39,7 @@ struct SJob {
   uint64_t ticket = 0;
   int dims[4] = {0, 0, 0, 0};
   int bc_t = -1;
+  double c_sw = 0.0;
   std::vector<double> U, sigma, gamma;
   std::vector<int> nsamp;
   std::vector<int32_t> colors;  // probing colours, [V] (empty: no probing)
@@ -72,7 +74,9 @@ size_t estimate(const SJob& j) {
   const size_t staging = j.P.estimator == FS_EST_SPLIT_EVEN
                              ? (size_t)2 * tile * 24 * V * 8 * (j.P.hpe_order > 0 ? 2 : 1) : 0;
   const size_t lanes = (size_t)std::max(1, j.P.solve.lanes);
-  return lanes * (tile_bytes + stage + staging) + gauge + contract + (32u << 20);
+  // the clover table (2 x 114 reals per site in FP64 and FP32) and each tile's C x field
+  const size_t clover = j.c_sw != 0.0 ? V * 2 * 114 * (8 + 4) + lanes * fts : 0;
+  return lanes * (tile_bytes + stage + staging) + gauge + contract + clover + (32u << 20);
 }
 
 }  // namespace
@@ -120,6 +124,7 @@ struct fs_server {
     // job on this worker with the same lattice and a byte-identical field skips the upload, and
     // the context keeps its packed copies and contraction paths
     std::vector<double> resident;
+    double resident_csw = 0.0;  // the clover coefficient of the context's operator
     cudaSetDevice(device);
     while (true) {
       SJob* j = nullptr;
@@ -142,6 +147,7 @@ struct fs_server {
         if (ctx) fs_ctx_destroy(ctx);
         ctx = nullptr;
         resident.clear();
+        resident_csw = 0.0;
         rc = fs_ctx_create(&ctx, j->dims, j->bc_t, device);
         if (rc == FS_OK) {
           std::copy(j->dims, j->dims + 4, cdims);
@@ -150,11 +156,19 @@ struct fs_server {
       }
       const bool gauge_resident = rc == FS_OK && !resident.empty() && resident.size() == j->U.size() &&
                                   std::memcmp(resident.data(), j->U.data(), j->U.size() * sizeof(double)) == 0;
+      // the clover table belongs to (field, c_sw): built once for a new field (the coefficient
+      // is dropped first so that the upload does not build a table for the old one)
       if (rc == FS_OK && !gauge_resident) {
-        rc = fs_set_gauge(ctx, j->U.data());
+        if (resident_csw != j->c_sw && resident_csw != 0.0) rc = fs_set_clover(ctx, 0.0);
+        if (rc == FS_OK) rc = fs_set_gauge(ctx, j->U.data());
         if (rc == FS_OK) resident.swap(j->U);  // the job needs its host copy no longer
         else resident.clear();
+        if (rc == FS_OK && resident_csw != j->c_sw) rc = fs_set_clover(ctx, j->c_sw);
+      } else if (rc == FS_OK && resident_csw != j->c_sw) {
+        rc = fs_set_clover(ctx, j->c_sw);
       }
+      if (rc == FS_OK) resident_csw = j->c_sw;
+      else resident.clear();
       if (gauge_resident) {
         std::lock_guard<std::mutex> lock(mu);
         gauge_reuses += 1;
@@ -238,6 +252,8 @@ int fs_server_submit(fs_server* s, const fs_job* job, uint64_t* ticket) {
   std::unique_ptr<SJob> j(new SJob());
   std::copy(job->dims, job->dims + 4, j->dims);
   j->bc_t = job->bc_t;
+  if (!std::isfinite(job->c_sw)) return FS_ERR_INPUT;
+  j->c_sw = job->c_sw;
   j->U.assign(job->U, job->U + (size_t)4 * V * 18);
   j->sigma.assign(P.sigma, P.sigma + P.nlev);
   j->nsamp.assign(P.n_samples, P.n_samples + P.nlev);

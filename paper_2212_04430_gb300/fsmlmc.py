@@ -63,7 +63,7 @@ class MlmcParams(ctypes.Structure):
 
 class Job(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int * 4), ("bc_t", ctypes.c_int), ("U", ctypes.POINTER(ctypes.c_double)),
-                ("params", MlmcParams)]
+                ("params", MlmcParams), ("c_sw", ctypes.c_double)]
 
 
 class JobResult(ctypes.Structure):
@@ -558,8 +558,9 @@ class Server:
             raise FsError(rc, "fs_server_create failed")
 
     def submit(self, dims, U, m, sigmas, gamma, p, n_samples, seed, job=0, estimator="split_even", bc_t=-1,
-               colors=None, ncolors=None, dilute=False, hpe_order=0, **kw):
-        """Queue one trace job (arrays are copied); returns the ticket."""
+               colors=None, ncolors=None, dilute=False, hpe_order=0, c_sw=0.0, **kw):
+        """Queue one trace job (arrays are copied; c_sw: the clover coefficient, 0 = Wilson);
+        returns the ticket."""
         u = _real(U)
         sig = np.ascontiguousarray(sigmas, dtype=np.float64)
         ns = np.ascontiguousarray(n_samples, dtype=np.int32)
@@ -569,6 +570,7 @@ class Server:
             J.dims[k] = int(dims[k])
         J.bc_t = int(bc_t)
         J.U = _dptr(u)
+        J.c_sw = float(c_sw)
         P = J.params
         P.m = m
         P.nlev = sig.size

@@ -297,6 +297,28 @@ def test_cgnr_fallback_with_the_clover_term(prec):
             assert rel_err(x[j, k], ref) < 1e-7
 
 
+def test_server_runs_clover_and_wilson_jobs_as_a_context_does():
+    """Jobs with and without the clover term on one worker (same lattice and field, so the field
+    stays resident while the coefficient changes, then a new field): each result is bit-identical
+    to the same call on a context of its own."""
+    dims = (4, 4, 4, 4)
+    u1 = inputs.gauge_field(dims, "smooth", seed=1213, eps=0.4)
+    u2 = inputs.gauge_field(dims, "smooth", seed=1214, eps=0.4)
+    m, sig, p, n = -0.2, [0.05, 0.5], 1, [3, 3]
+    g = pkg.gamma_matrix("g3")
+    kw = dict(prec="f32", tol=1e-10, rhs_tile=8)
+    jobs = [(u1, 0.0), (u1, 1.0), (u1, 1.4), (u2, 1.4), (u2, 0.0)]
+    srv = pkg.Server(device=0, hbm_budget_bytes=8 << 30, max_active=1)
+    tickets = [srv.submit(dims, u, m, sig, g, p, n, 40 + i, job=i, c_sw=c, **kw) for i, (u, c) in enumerate(jobs)]
+    res = [srv.poll(t) for t in tickets]
+    srv.close()
+    for i, (u, c) in enumerate(jobs):
+        ctx = make_ctx(dims, u, c)
+        ref = ctx.mlmc_level_trace(m, sig, g, p, n, seed=40 + i, job=i, lanes=1, **kw)
+        ctx.close()
+        assert res[i]["status"] == 0 and np.array_equal(res[i]["trace"], ref["trace"]), i
+
+
 def test_clover_16x32_dslash_and_solves_at_the_bench_precision():
     """The bench lattice, links and precision with the clover term: the FP16 dslash (12-real links,
     16-system tile, the paired clover pass) against the oracle's D_sw on sampled vectors, and solves
