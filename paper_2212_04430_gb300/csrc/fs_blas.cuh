@@ -580,6 +580,7 @@ __global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
   fin_sources(op, a, src, kk);
   const int g0 = (int)((long long)a.ngroups * y / FIN_SPLIT), g1 = (int)((long long)a.ngroups * (y + 1) / FIN_SPLIT);
   double acc[NV];
+  const double* base[NV];
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     // value v: entry kidx of source q (sources in order, kk[q] entries each)
@@ -587,10 +588,14 @@ __global__ void __launch_bounds__(256) fin_kernel(FinArgs a, int op) {
     if (kidx >= kk[0]) { kidx -= kk[0]; q = 1; if (kidx >= kk[1]) { kidx -= kk[1]; q = 2; } }
     const double* sp = q == 0 ? src[0] : (q == 1 ? src[1] : src[2]);
     const int kq = q == 0 ? kk[0] : (q == 1 ? kk[1] : kk[2]);
-    const double* base = sp + ((size_t)sys * kq + kidx) * a.ngroups;
-    double t = 0.0;
-    for (int g = g0 + (int)threadIdx.x; g < g1; g += blockDim.x) t += base[g];
-    acc[v] = t;
+    base[v] = sp + ((size_t)sys * kq + kidx) * a.ngroups;
+    acc[v] = 0.0;
+  }
+  // each value summed over this thread's groups in ascending order, the NV loads of a group
+  // issued together
+  for (int g = g0 + (int)threadIdx.x; g < g1; g += blockDim.x) {
+#pragma unroll
+    for (int v = 0; v < NV; v++) acc[v] += base[v][g];
   }
 #pragma unroll
   for (int v = 0; v < NV; v++) sm[threadIdx.x * NV + v] = acc[v];
