@@ -76,11 +76,12 @@ def hop_traffic_ratio(workload):
 
 
 class ClockSampler:
-    """nvidia-smi samples every 200 ms while the timed region runs."""
+    """nvidia-smi samples every 200 ms while the timed region runs (clocks, throttle reasons, and the
+    share of time a kernel of this GPU was running: the gaps the host's solve loops leave)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, index):
         self.index = index
@@ -109,7 +110,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
+        sm, smax, busy, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
@@ -123,8 +124,14 @@ class ClockSampler:
             for name, val in zip(names, parts[5:9]):
                 if val.lower() == "active":
                     reasons.add(name)
+            if len(parts) > 9:
+                try:
+                    busy.append(float(parts[9]))
+                except ValueError:
+                    pass
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "gpu_busy_pct": statistics.mean(busy) if busy else None}
 
 
 def measure_arith_peaks(pkg, index, seconds):
@@ -790,6 +797,25 @@ def main():
         e2e = {"value": total_solves / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    # ---- one lane, no profiling: how much of the time a kernel runs while the host's solve loop
+    # checks the tiles every few iterations (the headline's three lanes hide these gaps)
+    single = None
+    if rank == 0:
+        s_clk = ClockSampler(torch.cuda.current_device())
+        s_clk.start()
+        torch.cuda.synchronize()
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        step(job0 + 5000, lanes=1)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        sc = s_clk.stop()
+        single = {"solves_per_s": solves_per_step / (h0.elapsed_time(h1) / 1e3), "gpu_busy_pct": sc.get("gpu_busy_pct"),
+                  "samples": sc.get("samples"),
+                  "note": "one step on one lane; gpu_busy_pct = nvidia-smi utilization.gpu, the share of time a "
+                          "kernel was running, averaged over the samples"}
+
     # ---- roofline pass: the same step on one lane, every hop launch timed with CUDA events on
     # its stream (with several lanes a launch shares the GPU with the other lanes' kernels, and its
     # duration would measure that sharing rather than the kernel)
@@ -930,6 +956,7 @@ def main():
                 "config": config_of(args, w), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "arith_peaks": arith, "serving": serving,
                 "serving_stable": serving_stable, "estimators": estimators, "wilson_clover": clover,
+                "single_lane": single,
                 "pipeline": pipeline,
                 "fp64_single_rhs": fp64, "probing": probing, "variance_sampling_24x64": large,
                 "solver": {"mean_iters": float(np.mean(iters)) if iters else None,
