@@ -319,6 +319,50 @@ def test_server_runs_clover_and_wilson_jobs_as_a_context_does():
         assert res[i]["status"] == 0 and np.array_equal(res[i]["trace"], ref["trace"]), i
 
 
+def test_clover_with_the_papers_noise_lanes_and_displacements():
+    """The clover term composes with every other part of the path: probed, fully diluted noise and
+    the generalised expansion (the paper's set-up) give bit-identical samples on one and two lanes,
+    equal to the oracle's; several displacements from one set of solves equal single-displacement
+    calls exactly."""
+    from oracle import hpe as ohpe
+    from oracle import probing as opr
+    dims = (4, 4, 4, 4)
+    v = int(np.prod(dims))
+    u = inputs.gauge_field(dims, "smooth", seed=1215, eps=0.4)
+    c_sw, m, sig, p, K = 1.0, -0.1, [0.1, 0.5], 1, 3
+    ct = cterm_of(u, dims, c_sw)
+    n = [2, 2]
+    g = pkg.gamma_matrix("g3")
+    col, nc = opr.greedy_coloring(dims, 1, 1)
+    ctx = make_ctx(dims, u, c_sw)
+    kw = dict(colors=col, ncolors=nc, dilute=True, hpe_order=K, prec="f64", tol=1e-12, rhs_tile=32, estimator="diff")
+    one = ctx.mlmc_level_trace(m, sig, g, p, n, seed=9, job=3, lanes=1, **kw)
+    two = ctx.mlmc_level_trace(m, sig, g, p, n, seed=9, job=3, lanes=2, **kw)
+    assert one["rc"] == 0 and two["rc"] == 0
+    for lev in range(2):
+        assert np.array_equal(one["samples"][lev], two["samples"][lev]), lev
+    go = odirac.gamma_product(["g3"])
+    solver = oest.make_dense_solver(u, m, dims, -1, ct)
+    ecol, enc = opr.greedy_coloring(dims, K - 1, p)
+    t_exact = ohpe.exact_part_probed(u, m, sig[1], go, p, K, dims, ecol, enc, cterm=ct)
+    ref = []
+    for s in range(n[1]):
+        tot = t_exact
+        for (j, a) in opr.pieces(nc, True):
+            z = opr.probed_noise(v, 9, 3, 1, s, col, j, a)
+            tot += ohpe.stochastic_part(u, solver, z, m, sig[1], go, p, K, dims, cterm=ct)
+        ref.append(tot)
+    assert sample_err(one["samples"][1], np.array(ref)) < 1e-9
+    # several displacements from one set of solves (plain noise, mixed precision)
+    kw2 = dict(seed=12, job=1, estimator="split_even", prec="f32", tol=1e-9, rhs_tile=8)
+    many = ctx.mlmc_level_trace(m, sig, g, [2, 0, 1], [3, 3], **kw2)
+    for r in many:
+        single = ctx.mlmc_level_trace(m, sig, g, r["p"], [3, 3], **kw2)
+        for lev in range(2):
+            assert np.array_equal(r["samples"][lev], single["samples"][lev]), (r["p"], lev)
+    ctx.close()
+
+
 def test_clover_16x32_dslash_and_solves_at_the_bench_precision():
     """The bench lattice, links and precision with the clover term: the FP16 dslash (12-real links,
     16-system tile, the paired clover pass) against the oracle's D_sw on sampled vectors, and solves
