@@ -57,6 +57,7 @@ void release(Ctx& c) {
     for (auto& kv : c.gauge_lo) cudaFree(kv.second);
     if (c.clover64) cudaFree(c.clover64);
     if (c.clover32) cudaFree(c.clover32);
+    fs::clover_inverses_free(&c);
   }
   if (c.colors_own && c.colors_d) cudaFree(c.colors_d);
   if (c.canon_d) cudaFree(c.canon_d);
@@ -414,6 +415,7 @@ int fs_set_clover(fs_ctx* ctx, double c_sw) {
   for (auto& l : c.lanes)
     if (cudaError_t e = cudaStreamSynchronize(l->stream)) return c.cuda_fail(e, "fs_set_clover");
   if (c_sw == 0.0) {
+    fs::clover_inverses_free(&c);
     if (c.clover64) {
       cudaFree(c.clover64);
       cudaFree(c.clover32);
@@ -499,6 +501,7 @@ int shifted_solve(fs_ctx* ctx, double m, const double* sigma, int nshift, const 
   const int S = nshift * nrhs;
   if (int rc = resolve_params(c, params, S, m, o)) return rc;
   if (int rc = set_device(c)) return rc;
+  if (int rc = fs::clover_inverses(&c, m, sigma, nshift, o.so)) return rc;
   std::vector<fs::QJob> jobs(S);
   for (int i = 0; i < S; i++) {
     const int j = i / nrhs, k = i % nrhs;
@@ -552,6 +555,8 @@ int shifted_solve_dev(fs_ctx* ctx, double m, const double* sigma, int nshift, co
   const int S = nshift * nrhs;
   if ((long long)nshift * nrhs > 0x7FFFFFFF) return c.fail(FS_ERR_ARG, "too many systems");
   if (int rc = resolve_params(c, params, S, m, o)) return rc;
+  if (int rc = set_device(c)) return rc;
+  if (int rc = fs::clover_inverses(&c, m, sigma, nshift, o.so)) return rc;
   std::vector<fs::QJob> jobs(S);
   for (int i = 0; i < S; i++) {
     const int j = i / nrhs, k = i % nrhs;
@@ -587,6 +592,8 @@ int fs_hpe_exact_trace(fs_ctx* ctx, double m, double sigma, const double* gamma,
   if (std::fabs(4.0 + m + sigma) < 1e-12) return c.fail(FS_ERR_ARG, "4 + m + sigma must be nonzero");
   Opts o;
   if (int rc = resolve_params(c, params, 12, m, o)) return rc;  // 12 < 16: no tile autotuning
+  if (int rc = set_device(c)) return rc;
+  if (int rc = fs::clover_inverses(&c, m, &sigma, 1, o.so)) return rc;
   if (!params || params->rhs_tile == 0) o.tile = fs::MAX_TILE;  // the probing pieces fill whole tiles
   if (int rc = set_device(c)) return rc;
   fs::TileBase* T = c.tile(o.so.prec, o.tile, o.so.nr);
@@ -681,6 +688,7 @@ int mlmc_impl(Ctx& c, const fs_mlmc_params* P, const int* p_in, int np, double* 
   Opts o;
   if (int rc = resolve_params(c, &P->solve, nsolve, P->m, o)) return rc;
   if (int rc = set_device(c)) return rc;
+  if (int rc = fs::clover_inverses(&c, P->m, P->sigma, P->nlev, o.so)) return rc;
   std::vector<double> csum((size_t)np * total * 2, 0.0);  // per-sample values [np][level-major][2]
   std::vector<long long> off(L + 2, 0);
   for (int l = 0; l <= L; l++) off[l + 1] = off[l] + P->n_samples[l];
@@ -888,6 +896,7 @@ int variance_sample_impl(Ctx& c, double m, const double* s_hat, int ms, const do
   Opts o;
   if (int rc = resolve_params(c, params, nsys, m, o)) return rc;
   if (int rc = set_device(c)) return rc;
+  if (int rc = fs::clover_inverses(&c, m, s_hat, ms, o.so)) return rc;
   if (colors)
     if (int rc = fs::upload_colors(&c, colors)) return rc;
   // keep the requested tile even where whole groups leave a few slots idle: a multiple of 32

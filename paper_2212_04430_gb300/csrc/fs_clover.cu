@@ -1,6 +1,8 @@
 // Clover table of a gauge field: the field strength from the clover leaves, the two chiral 6x6
 // blocks of C(x), and their eigen-decomposition (fs_clover.cuh describes the operator and layout).
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "fs_engine.h"
 
@@ -246,9 +248,112 @@ void mul2(const double (&ar)[4], const double (&ai)[4], bool adjA, const double 
     }
 }
 
+// The packed (A + C_b)^-1 of one shift, from the eigen-decomposition: P_ij = sum_k V_ik conj(V_jk) /
+// (A + lambda_k), i <= j; one thread per (parity, site), FP64, stored in FP64 and FP32.
+__global__ void __launch_bounds__(128) clover_inverse_kernel(const double* __restrict__ eig, double* o64, float* o32,
+                                                             int n2, double A) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= n2) return;
+  for (int b = 0; b < 2; b++) {
+    const double* t = eig + ((size_t)id * 2 + b) * CLV_REALS;
+    double f[6];
+    for (int k = 0; k < 6; k++) f[k] = 1.0 / (A + t[72 + k]);
+    double* d64 = o64 + ((size_t)id * 2 + b) * CLV_PACKED;
+    float* d32 = o32 + ((size_t)id * 2 + b) * CLV_PACKED;
+    for (int i = 0; i < 6; i++)
+      for (int j = i; j < 6; j++) {
+        double re = 0.0, im = 0.0;
+        for (int k = 0; k < 6; k++) {
+          // V_ik conj(V_jk) f_k
+          const double ar = t[2 * (i * 6 + k)], ai = t[2 * (i * 6 + k) + 1];
+          const double br = t[2 * (j * 6 + k)], bi = t[2 * (j * 6 + k) + 1];
+          re += (ar * br + ai * bi) * f[k];
+          im += (ai * br - ar * bi) * f[k];
+        }
+        if (i == j) {
+          d64[i] = re;
+          d32[i] = (float)re;
+        } else {
+          const int u = 6 + 2 * clv_upper(i, j);
+          d64[u] = re;
+          d64[u + 1] = im;
+          d32[u] = (float)re;
+          d32[u + 1] = (float)im;
+        }
+      }
+  }
+}
+
 }  // namespace
 
+void clover_inverses_free(Ctx* c) {
+  const size_t n = (size_t)2 * c->g.Vh * 2 * CLV_PACKED;
+  for (auto& kv : c->clv_inv) {
+    cudaFree(kv.second.t64);
+    cudaFree(kv.second.t32);
+    c->extra_bytes -= n * (sizeof(double) + sizeof(float));
+  }
+  c->clv_inv.clear();
+}
+
+int clover_inverses(Ctx* c, double m, const double* sigma, int n, SolveOpts& o) {
+  o.clv_inv = nullptr;
+  if (c->c_sw == 0.0 || c->clover64 == nullptr) return 0;
+  if (c->shared) return c->fail(1, "a lane takes its owner's clover inverses");
+  std::vector<double> want;
+  for (int k = 0; k < n; k++) want.push_back(4.0 + m + sigma[k]);  // the A of init_state, bit for bit
+  constexpr size_t MAX_SHIFTS = 32;
+  if (c->clv_inv.size() + want.size() > MAX_SHIFTS) {
+    // drop the entries this call does not name (no kernel reads them between calls)
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e) return c->cuda_fail(e, "clover inverses");
+    const size_t bytes = (size_t)2 * c->g.Vh * 2 * CLV_PACKED * (sizeof(double) + sizeof(float));
+    for (auto it = c->clv_inv.begin(); it != c->clv_inv.end();) {
+      if (std::find(want.begin(), want.end(), it->first) == want.end()) {
+        cudaFree(it->second.t64);
+        cudaFree(it->second.t32);
+        c->extra_bytes -= bytes;
+        it = c->clv_inv.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+  const size_t cnt = (size_t)2 * c->g.Vh * 2 * CLV_PACKED;
+  const int n2 = 2 * c->g.Vh;
+  for (double A : want) {
+    if (c->clv_inv.count(A)) continue;
+    if (c->clv_inv.size() >= MAX_SHIFTS) break;  // the rest take the eigen-decomposed form
+    ClvInv t;
+    if (cudaMalloc(&t.t64, cnt * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return c->fail(3, "device allocation of a clover inverse failed");
+    }
+    if (cudaMalloc(&t.t32, cnt * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(t.t64);
+      return c->fail(3, "device allocation of a clover inverse failed");
+    }
+    c->extra_bytes += cnt * (sizeof(double) + sizeof(float));
+    clover_inverse_kernel<<<(n2 + 127) / 128, 128, 0, c->stream>>>(c->clover64, t.t64, t.t32, n2, A);
+    note_launch();
+    if (cudaError_t e = cudaGetLastError()) {
+      cudaFree(t.t64);
+      cudaFree(t.t32);
+      c->extra_bytes -= cnt * (sizeof(double) + sizeof(float));
+      return c->cuda_fail(e, "clover inverse");
+    }
+    c->clv_inv[A] = t;
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);  // the lanes read them on their own streams
+  if (e) return c->cuda_fail(e, "clover inverses");
+  o.clv_inv = &c->clv_inv;
+  return 0;
+}
+
 int clover_build(Ctx* c, double c_sw) {
+  if (cudaError_t e = cudaStreamSynchronize(c->stream)) return c->cuda_fail(e, "clover table");
+  clover_inverses_free(c);  // they belong to the old table
   const size_t n = (size_t)2 * c->g.Vh * 2 * CLV_REALS;
   if (!c->clover64) {
     if (cudaMalloc(&c->clover64, n * sizeof(double)) != cudaSuccess) {

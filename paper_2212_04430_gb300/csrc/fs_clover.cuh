@@ -23,6 +23,7 @@ namespace fs {
 
 constexpr int CLV_REALS = 114;  // 72 (V) + 6 (lambda) + 36 (C packed) per chirality block
 constexpr int CLV_C = 78;       // offset of the packed C in a block
+constexpr int CLV_PACKED = 36;  // a packed Hermitian 6x6 block (the per-shift inverses)
 
 // index of the upper-triangle entry (i < j) in the packed C (complex entries after the diagonal)
 __host__ __device__ constexpr int clv_upper(int i, int j) { return i * 5 - i * (i - 1) / 2 + (j - i - 1); }
@@ -52,33 +53,45 @@ struct ClovArgs {
 __device__ __forceinline__ float mulrn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mulrn(double a, double b) { return __dmul_rn(a, b); }
 
+// o = P v for one chirality block (12 reals of v and o), P Hermitian and packed (its 6 real
+// diagonal entries, then the 15 above the diagonal): row i is d_i v_i + sum_{j != i} P_ij v_j with
+// P_ji = conj(P_ij). C itself, or the packed inverse of one shift.
+template <typename Tc, typename Tm>
+__device__ __forceinline__ void herm6(const Tc* __restrict__ t, const Tm* v, Tm* o) {
+#pragma unroll
+  for (int i = 0; i < 6; i++) {
+    const Tm d = (Tm)t[i];
+    Tm re = mulrn(d, v[2 * i]), im = mulrn(d, v[2 * i + 1]);
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+      if (j == i) continue;
+      const int u = 6 + 2 * (i < j ? clv_upper(i, j) : clv_upper(j, i));
+      const Tm cr = (Tm)t[u], ci = i < j ? (Tm)t[u + 1] : -(Tm)t[u + 1];
+      const Tm pr = v[2 * j], pi = v[2 * j + 1];
+      re = fmadd(cr, pr, re);
+      re = fmadd(-ci, pi, re);
+      im = fmadd(cr, pi, im);
+      im = fmadd(ci, pr, im);
+    }
+    o[2 * i] = re;
+    o[2 * i + 1] = im;
+  }
+}
+
+// (A + C(x))^-1 v from the packed inverse of the system's shift (the site's two blocks)
+template <typename Tc, typename Tm>
+__device__ __forceinline__ void clover_site_packed(const Tc* __restrict__ inv, const Tm (&v)[24], Tm (&o)[24]) {
+  herm6<Tc, Tm>(inv, v, o);
+  herm6<Tc, Tm>(inv + CLV_PACKED, v + 12, o + 12);
+}
+
 // One site of one system: the two chirality blocks of the spinor v (index 6 spin + 2 colour + re/im).
 template <int MODE, typename Tc, typename Tm>
 __device__ __forceinline__ void clover_site(const Tc* __restrict__ tab, Tm a, const Tm (&v)[24], Tm (&o)[24]) {
   if constexpr (MODE != CLV_INV) {
-    // o = C v from the packed blocks: row i, d_i v_i + sum_{j != i} C_ij v_j, C_ji = conj(C_ij)
-#pragma unroll
-    for (int b = 0; b < 2; b++) {
-      const Tc* t = tab + b * CLV_REALS + CLV_C;
-#pragma unroll
-      for (int i = 0; i < 6; i++) {
-        const Tm d = (Tm)t[i];
-        Tm re = mulrn(d, v[12 * b + 2 * i]), im = mulrn(d, v[12 * b + 2 * i + 1]);
-#pragma unroll
-        for (int j = 0; j < 6; j++) {
-          if (j == i) continue;
-          const int u = 6 + 2 * (i < j ? clv_upper(i, j) : clv_upper(j, i));
-          const Tm cr = (Tm)t[u], ci = i < j ? (Tm)t[u + 1] : -(Tm)t[u + 1];
-          const Tm pr = v[12 * b + 2 * j], pi = v[12 * b + 2 * j + 1];
-          re = fmadd(cr, pr, re);
-          re = fmadd(-ci, pi, re);
-          im = fmadd(cr, pi, im);
-          im = fmadd(ci, pr, im);
-        }
-        o[12 * b + 2 * i] = re;
-        o[12 * b + 2 * i + 1] = im;
-      }
-    }
+    // o = C v from the packed blocks
+    herm6<Tc, Tm>(tab + CLV_C, v, o);
+    herm6<Tc, Tm>(tab + CLV_REALS + CLV_C, v + 12, o + 12);
     return;
   }
   // (a + C)^-1 v = V diag(1 / (a + lambda)) V^dag v, one eigenvector (column j of V) at a time:
@@ -122,6 +135,31 @@ __device__ __forceinline__ void clover_site(const Tc* __restrict__ tab, Tm a, co
       o[12 * b + 2 * i] = orr[i];
       o[12 * b + 2 * i + 1] = oi[i];
     }
+  }
+}
+
+// herm6 for two systems at once, each lane with its own packed block (t0, t1; the per-shift
+// inverses of two shifts): per lane the same operations in the same order as herm6.
+__device__ __forceinline__ void herm6_pk2(const float* __restrict__ t0, const float* __restrict__ t1, const float2* v,
+                                          float2* o) {
+  using namespace pk;
+#pragma unroll
+  for (int i = 0; i < 6; i++) {
+    const float2 d = make_float2(t0[i], t1[i]);
+    float2 re = mul2(d, v[2 * i]), im = mul2(d, v[2 * i + 1]);
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+      if (j == i) continue;
+      const int u = 6 + 2 * (i < j ? clv_upper(i, j) : clv_upper(j, i));
+      const float2 c2 = make_float2(t0[u], t1[u]);
+      const float2 i2 = i < j ? make_float2(t0[u + 1], t1[u + 1]) : make_float2(-t0[u + 1], -t1[u + 1]);
+      re = fma2(c2, v[2 * j], re);
+      re = fma2(neg2(i2), v[2 * j + 1], re);
+      im = fma2(c2, v[2 * j + 1], im);
+      im = fma2(i2, v[2 * j], im);
+    }
+    o[2 * i] = re;
+    o[2 * i + 1] = im;
   }
 }
 
@@ -218,6 +256,13 @@ __global__ void __launch_bounds__(256, 2) clover_kernel_pk(ClovArgs a) {
   const Field<Ts> out = make_field<Ts>(a.out, g.Vh, sh.N, false);
   const Field<Ts> Y = make_field<Ts>(const_cast<void*>(a.Y), g.Vh, sh.N, false);
   const float* table = (const float*)a.table;
+  // the packed inverses of the two systems' shifts: the systems of one call all have theirs (the
+  // autotuner's trial systems none), so where only one is set its partner sits idle and takes
+  // the same table, its result discarded
+  const float* inv0 = MODE == CLV_INV ? a.st[s0].clv_inv32 : nullptr;
+  const float* inv1 = MODE == CLV_INV ? a.st[s1].clv_inv32 : nullptr;
+  if (inv0 == nullptr) inv0 = inv1;
+  if (inv1 == nullptr) inv1 = inv0;
   const int nchunk2 = (g.Vh + S2 - 1) / S2;
   for (int chunk = blockIdx.x; chunk < nchunk2; chunk += gridDim.x) {
     const int site = chunk * S2 + ls;
@@ -228,7 +273,13 @@ __global__ void __launch_bounds__(256, 2) clover_kernel_pk(ClovArgs a) {
     float2 v[24], o[24];
 #pragma unroll
     for (int k = 0; k < 24; k++) v[k] = make_float2(v0[k], v1[k]);
-    clover_site_pk<MODE>(table + ((size_t)a.parity * g.Vh + site) * 2 * CLV_REALS, A, v, o);
+    if (inv0 != nullptr) {
+      const size_t off = ((size_t)a.parity * g.Vh + site) * 2 * CLV_PACKED;
+      herm6_pk2(inv0 + off, inv1 + off, v, o);
+      herm6_pk2(inv0 + off + CLV_PACKED, inv1 + off + CLV_PACKED, v + 12, o + 12);
+    } else {
+      clover_site_pk<MODE>(table + ((size_t)a.parity * g.Vh + site) * 2 * CLV_REALS, A, v, o);
+    }
     if constexpr (MODE == CLV_SUB) {
       Y.load(site, s0, v0);
       Y.load(site, s1, v1);
@@ -261,7 +312,13 @@ __global__ void __launch_bounds__(WL ? 128 : 256) clover_kernel(ClovArgs a) {
     Tm v[24], o[24];
     in.load(site, sys, v);
     const Tm A = coef<Tm>(a.st[sys], C_A);
-    clover_site<MODE, Tc, Tm>(table + ((size_t)a.parity * g.Vh + site) * 2 * CLV_REALS, A, v, o);
+    const Tc* inv = nullptr;  // the packed inverse of the system's shift, where the call built one
+    if constexpr (MODE == CLV_INV) {
+      if constexpr (std::is_same<Tc, double>::value) inv = a.st[sys].clv_inv64;
+      else inv = a.st[sys].clv_inv32;
+    }
+    if (inv != nullptr) clover_site_packed<Tc, Tm>(inv + ((size_t)a.parity * g.Vh + site) * 2 * CLV_PACKED, v, o);
+    else clover_site<MODE, Tc, Tm>(table + ((size_t)a.parity * g.Vh + site) * 2 * CLV_REALS, A, v, o);
     if constexpr (MODE == CLV_SUB) {
       Tm y[24];
       Y.load(site, sys, y);

@@ -256,6 +256,10 @@ struct SysState {
   int max_iter;
   int cg_iters;               // CGNR fallback iterations
   int cg_max_iter;
+  // Wilson-clover: the packed (A + C(x))^-1 of this system's shift, [2][Vh][2][36] in FP64 and
+  // FP32 (nullptr: the clover passes take the shift-independent eigen-decomposed table)
+  const double* clv_inv64;
+  const float* clv_inv32;
 };
 
 template <typename Tm>

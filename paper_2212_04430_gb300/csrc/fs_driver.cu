@@ -45,6 +45,13 @@ void init_state(SysState& s, double sigma, const SolveOpts& o) {
   s.max_iter = o.max_iter;
   s.status = SYS_IDLE;
   s.flags = FLAG_INIT;
+  if (o.clv_inv != nullptr) {  // Wilson-clover: the packed inverse of this shift, where the call built one
+    auto it = o.clv_inv->find(A);
+    if (it != o.clv_inv->end()) {
+      s.clv_inv64 = it->second.t64;
+      s.clv_inv32 = it->second.t32;
+    }
+  }
 }
 
 cudaError_t upload_slots(Ctx* c, TileBase* T, const std::vector<int>& slots) {

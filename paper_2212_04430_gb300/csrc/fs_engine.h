@@ -139,6 +139,12 @@ class TileBase {
   virtual cudaError_t enqueue_cg_iter() = 0;
 };
 
+// The packed (A + C(x))^-1 of one shift (Wilson-clover), [2][Vh][2][CLV_PACKED] reals.
+struct ClvInv {
+  double* t64 = nullptr;
+  float* t32 = nullptr;
+};
+
 struct Ctx {
   int device = 0;
   int nsm = 0;
@@ -187,10 +193,13 @@ struct Ctx {
   double c_sw = 0.0;
   double* clover64 = nullptr;     // [2][Vh][2][CLV_REALS]
   float* clover32 = nullptr;
+  std::map<double, ClvInv> clv_inv;  // packed inverses per A = 4 + m + sigma, built per call (owner only)
 };
 
 // Builds c's clover tables from its FP64 gauge copy (fs_clover.cu); 0 or an error code.
 int clover_build(Ctx* c, double c_sw);
+// Frees every packed inverse (their table changed).
+void clover_inverses_free(Ctx* c);
 
 // The contraction's straight z-paths W(x, x + q z) for the displacements q > 0 in pmask,
 // built once per gauge field (fs_engine.cu); 0 or an error code (message in c->err).
@@ -212,6 +221,7 @@ struct SysSpec {
 };
 
 struct SolveOpts {
+  const std::map<double, ClvInv>* clv_inv = nullptr;  // per A = 4 + m + sigma; read-only during a call
   double m;
   double tol;
   int max_iter;
@@ -222,6 +232,12 @@ struct SolveOpts {
   int check_every;
   int cg_max_iter;  // CGNR fallback iterations; 0: no fallback
 };
+
+// The packed (A + C(x))^-1 for the shifts sigma[0..n) of a call (A = 4 + m + sigma), built from the
+// eigen-decomposed table where missing and kept for later calls (at most 32 shifts; entries the
+// call does not name are dropped first); o.clv_inv then points at them. A no-op without the
+// clover term. 0 or an error code (fs_clover.cu).
+int clover_inverses(Ctx* c, double m, const double* sigma, int n, SolveOpts& o);
 
 // A group of systems whose solutions are contracted together (they share the tile
 // until all of them have converged).
