@@ -29,9 +29,11 @@ constexpr int CLV_PACKED = 36;  // a packed Hermitian 6x6 block (the per-shift i
 __host__ __device__ constexpr int clv_upper(int i, int j) { return i * 5 - i * (i - 1) / 2 + (j - i - 1); }
 
 enum ClovMode {
-  CLV_MUL = 0,  // out = C in
-  CLV_SUB = 1,  // out = Y - C in
-  CLV_INV = 2,  // out = (a + C)^-1 in, a = the system's A = 4 + m + sigma
+  CLV_MUL = 0,      // out = C in
+  CLV_SUB = 1,      // out = Y - C in
+  CLV_INV = 2,      // out = (a + C)^-1 in, a = the system's A = 4 + m + sigma
+  CLV_INV_MUL = 3,  // both site factors of one M-hat in one launch: out = (a + C)^-1 in on `parity`,
+                    // out2 = C in2 on the other parity (tile layout)
 };
 
 struct ClovArgs {
@@ -46,6 +48,8 @@ struct ClovArgs {
   int parity;          // of the sites the fields hold
   int mask;
   int sysmajor;
+  void* out2;          // CLV_INV_MUL: the C pass's output and input, on the other parity
+  const void* in2;
 };
 
 // products rounded on their own (never contracted into a neighbouring add), so that the paired
@@ -240,6 +244,37 @@ __device__ __forceinline__ void clover_site_pk(const float* __restrict__ tab, fl
 
 // The paired pass over a tile of an even number of systems per block row (NB): NB / 2 threads per
 // site, each holding systems (2k, 2k + 1) of its row; blockDim.x / (NB / 2) sites per block.
+// One site of the paired pass: systems s0, s0 + 1 of fields in / out (MODE != CLV_INV_MUL).
+template <typename Ts, int MODE>
+__device__ __forceinline__ void clover_pair_site(const ClovArgs& a, const Field<Ts>& in, const Field<Ts>& out,
+                                                 const Field<Ts>& Y, int parity, int site, int s0, bool sel0,
+                                                 bool sel1, float2 A, const float* inv0, const float* inv1) {
+  const Geom& g = a.g;
+  float v0[24], v1[24];
+  in.load(site, s0, v0);
+  in.load(site, s0 + 1, v1);
+  float2 v[24], o[24];
+#pragma unroll
+  for (int k = 0; k < 24; k++) v[k] = make_float2(v0[k], v1[k]);
+  if (MODE == CLV_INV && inv0 != nullptr) {
+    const size_t off = ((size_t)parity * g.Vh + site) * 2 * CLV_PACKED;
+    herm6_pk2(inv0 + off, inv1 + off, v, o);
+    herm6_pk2(inv0 + off + CLV_PACKED, inv1 + off + CLV_PACKED, v + 12, o + 12);
+  } else {
+    clover_site_pk<MODE>((const float*)a.table + ((size_t)parity * g.Vh + site) * 2 * CLV_REALS, A, v, o);
+  }
+  if constexpr (MODE == CLV_SUB) {
+    Y.load(site, s0, v0);
+    Y.load(site, s0 + 1, v1);
+#pragma unroll
+    for (int k = 0; k < 24; k++) o[k] = make_float2(v0[k] - o[k].x, v1[k] - o[k].y);
+  }
+#pragma unroll
+  for (int k = 0; k < 24; k++) { v0[k] = o[k].x; v1[k] = o[k].y; }
+  if (sel0) out.store(site, s0, v0);
+  if (sel1) out.store(site, s0 + 1, v1);
+}
+
 template <typename Ts, int MODE>
 __global__ void __launch_bounds__(256, 2) clover_kernel_pk(ClovArgs a) {
   if (a.gate != nullptr && *a.gate == 0) return;
@@ -255,41 +290,26 @@ __global__ void __launch_bounds__(256, 2) clover_kernel_pk(ClovArgs a) {
   const Field<Ts> in = make_field<Ts>(const_cast<void*>(a.in), g.Vh, sh.N, false);
   const Field<Ts> out = make_field<Ts>(a.out, g.Vh, sh.N, false);
   const Field<Ts> Y = make_field<Ts>(const_cast<void*>(a.Y), g.Vh, sh.N, false);
-  const float* table = (const float*)a.table;
+  const Field<Ts> in2 = make_field<Ts>(const_cast<void*>(a.in2), g.Vh, sh.N, false);
+  const Field<Ts> out2 = make_field<Ts>(a.out2, g.Vh, sh.N, false);
   // the packed inverses of the two systems' shifts: the systems of one call all have theirs (the
   // autotuner's trial systems none), so where only one is set its partner sits idle and takes
   // the same table, its result discarded
-  const float* inv0 = MODE == CLV_INV ? a.st[s0].clv_inv32 : nullptr;
-  const float* inv1 = MODE == CLV_INV ? a.st[s1].clv_inv32 : nullptr;
+  constexpr bool INV = MODE == CLV_INV || MODE == CLV_INV_MUL;
+  const float* inv0 = INV ? a.st[s0].clv_inv32 : nullptr;
+  const float* inv1 = INV ? a.st[s1].clv_inv32 : nullptr;
   if (inv0 == nullptr) inv0 = inv1;
   if (inv1 == nullptr) inv1 = inv0;
   const int nchunk2 = (g.Vh + S2 - 1) / S2;
   for (int chunk = blockIdx.x; chunk < nchunk2; chunk += gridDim.x) {
     const int site = chunk * S2 + ls;
     if (site >= g.Vh) continue;
-    float v0[24], v1[24];
-    in.load(site, s0, v0);
-    in.load(site, s1, v1);
-    float2 v[24], o[24];
-#pragma unroll
-    for (int k = 0; k < 24; k++) v[k] = make_float2(v0[k], v1[k]);
-    if (inv0 != nullptr) {
-      const size_t off = ((size_t)a.parity * g.Vh + site) * 2 * CLV_PACKED;
-      herm6_pk2(inv0 + off, inv1 + off, v, o);
-      herm6_pk2(inv0 + off + CLV_PACKED, inv1 + off + CLV_PACKED, v + 12, o + 12);
+    if constexpr (MODE == CLV_INV_MUL) {
+      clover_pair_site<Ts, CLV_INV>(a, in, out, Y, a.parity, site, s0, sel0, sel1, A, inv0, inv1);
+      clover_pair_site<Ts, CLV_MUL>(a, in2, out2, Y, 1 - a.parity, site, s0, sel0, sel1, A, nullptr, nullptr);
     } else {
-      clover_site_pk<MODE>(table + ((size_t)a.parity * g.Vh + site) * 2 * CLV_REALS, A, v, o);
+      clover_pair_site<Ts, MODE>(a, in, out, Y, a.parity, site, s0, sel0, sel1, A, inv0, inv1);
     }
-    if constexpr (MODE == CLV_SUB) {
-      Y.load(site, s0, v0);
-      Y.load(site, s1, v1);
-#pragma unroll
-      for (int k = 0; k < 24; k++) o[k] = make_float2(v0[k] - o[k].x, v1[k] - o[k].y);
-    }
-#pragma unroll
-    for (int k = 0; k < 24; k++) { v0[k] = o[k].x; v1[k] = o[k].y; }
-    if (sel0) out.store(site, s0, v0);
-    if (sel1) out.store(site, s1, v1);
   }
 }
 
@@ -305,27 +325,39 @@ __global__ void __launch_bounds__(WL ? 128 : 256) clover_kernel(ClovArgs a) {
   const Field<Ts> in = make_field<Ts>(const_cast<void*>(a.in), g.Vh, sh.N, WL);
   const Field<Ts> out = make_field<Ts>(a.out, g.Vh, sh.N, WL);
   const Field<Ts> Y = make_field<Ts>(const_cast<void*>(a.Y), g.Vh, sh.N, WL);
+  const Field<Ts> in2 = make_field<Ts>(const_cast<void*>(a.in2), g.Vh, sh.N, WL);
+  const Field<Ts> out2 = make_field<Ts>(a.out2, g.Vh, sh.N, WL);
   const Tc* table = (const Tc*)a.table;
-  auto body = [&](int sys, int chunk) {
-    const int site = chunk * sh.SB + lsite;
-    if (site >= g.Vh) return;
+  // one site of one system in mode M (a single-pass mode) on fields fi -> fo of parity par
+  auto pass = [&](auto Mc, int sys, int site, const Field<Ts>& fi, const Field<Ts>& fo, int par) {
+    constexpr int M = decltype(Mc)::value;
     Tm v[24], o[24];
-    in.load(site, sys, v);
+    fi.load(site, sys, v);
     const Tm A = coef<Tm>(a.st[sys], C_A);
     const Tc* inv = nullptr;  // the packed inverse of the system's shift, where the call built one
-    if constexpr (MODE == CLV_INV) {
+    if constexpr (M == CLV_INV) {
       if constexpr (std::is_same<Tc, double>::value) inv = a.st[sys].clv_inv64;
       else inv = a.st[sys].clv_inv32;
     }
-    if (inv != nullptr) clover_site_packed<Tc, Tm>(inv + ((size_t)a.parity * g.Vh + site) * 2 * CLV_PACKED, v, o);
-    else clover_site<MODE, Tc, Tm>(table + ((size_t)a.parity * g.Vh + site) * 2 * CLV_REALS, A, v, o);
-    if constexpr (MODE == CLV_SUB) {
+    if (inv != nullptr) clover_site_packed<Tc, Tm>(inv + ((size_t)par * g.Vh + site) * 2 * CLV_PACKED, v, o);
+    else clover_site<M, Tc, Tm>(table + ((size_t)par * g.Vh + site) * 2 * CLV_REALS, A, v, o);
+    if constexpr (M == CLV_SUB) {
       Tm y[24];
       Y.load(site, sys, y);
 #pragma unroll
       for (int k = 0; k < 24; k++) o[k] = y[k] - o[k];
     }
-    out.store(site, sys, o);
+    fo.store(site, sys, o);
+  };
+  auto body = [&](int sys, int chunk) {
+    const int site = chunk * sh.SB + lsite;
+    if (site >= g.Vh) return;
+    if constexpr (MODE == CLV_INV_MUL) {
+      pass(IntC<CLV_INV>{}, sys, site, in, out, a.parity);
+      pass(IntC<CLV_MUL>{}, sys, site, in2, out2, 1 - a.parity);
+    } else {
+      pass(IntC<MODE>{}, sys, site, in, out, a.parity);
+    }
   };
   if constexpr (!WL) {
     const int sys = blockIdx.y * sh.NB + lsys;

@@ -253,6 +253,17 @@ class Tile : public TileBase {
     return launch_clover<Ts>(mode, a, L);
   }
 
+  // Both site factors of a Wilson-clover M-hat in one tile-layout launch over the active systems:
+  // out = (A + C_oo)^-1 in (odd sites), out2 = C_ee in2 (even sites).
+  cudaError_t clover_pass2(void* out, const void* in, void* out2, const void* in2) {
+    ClovArgs a{};
+    a.out = out; a.in = in; a.out2 = out2; a.in2 = in2;
+    a.table = std::is_same<Ts, double>::value ? (const void*)c->clover64 : (const void*)c->clover32;
+    a.st = st_d; a.gate = nullptr;
+    a.g = c->g; a.sh = sh; a.parity = 1; a.mask = MASK_ACTIVE;
+    return launch_clover<Ts>(CLV_INV_MUL, a, L);
+  }
+
   HopArgs hop(void* out, const void* in, const void* X, const void* Y, const void* R, double* part, int p_out,
               int mask, bool gated, bool hi, bool sysmajor = false) {
     HopArgs a{};
@@ -396,18 +407,14 @@ class Tile : public TileBase {
     if ((e = hop_lo(COEF_PLAIN, DOT_NONE, hop(tmp, p, nullptr, nullptr, nullptr, nullptr, 1, MASK_ACTIVE, false,
                                               false), 0))) return e;
     // Wilson-clover: M-hat p = (A + C_ee) p - H_eo (A + C_oo)^-1 H_oe p / 4, the site factors by passes
-    if (cl && ((e = clover_pass(CLV_INV, tmp, tmp, nullptr, 1, MASK_ACTIVE, false, false)) ||
-               (e = clover_pass(CLV_MUL, cw, p, nullptr, 0, MASK_ACTIVE, false, false))))
-      return e;
+    if (cl && (e = clover_pass2(tmp, tmp, cw, p))) return e;
     if ((e = hop_lo(COEF_MHAT, DOT_R, hop(v, tmp, p, cl ? cw : nullptr, rhat, pa, 0, MASK_ACTIVE, false, false), 2)))
       return e;
     if ((e = fin(FIN_ALPHA, MASK_ACTIVE, pa))) return e;
     if ((e = launch_blas<Ts>(OP_S, blas(MASK_ACTIVE, nullptr, nullptr, false), L))) return e;
     if ((e = hop_lo(COEF_PLAIN, DOT_NONE, hop(tmp, s, nullptr, nullptr, nullptr, nullptr, 1, MASK_ACTIVE, false,
                                               false), 0))) return e;
-    if (cl && ((e = clover_pass(CLV_INV, tmp, tmp, nullptr, 1, MASK_ACTIVE, false, false)) ||
-               (e = clover_pass(CLV_MUL, cw, s, nullptr, 0, MASK_ACTIVE, false, false))))
-      return e;
+    if (cl && (e = clover_pass2(tmp, tmp, cw, s))) return e;
     if ((e = hop_lo(COEF_MHAT, DOT_TS, hop(t, tmp, s, cl ? cw : nullptr, rhat, pa, 0, MASK_ACTIVE, false, false), 2)))
       return e;
     if ((e = fin(FIN_OMEGA, MASK_ACTIVE, pa))) return e;

@@ -206,6 +206,18 @@ cudaError_t launch_clover(int mode, const ClovArgs& a, const Launch& l) {
   FS_CLV(CLV_MUL)
   FS_CLV(CLV_SUB)
   FS_CLV(CLV_INV)
+  if (mode == CLV_INV_MUL) {  // tile layout only
+    if (a.sysmajor) return cudaErrorInvalidValue;
+    if constexpr (!std::is_same<Ts, double>::value)
+      if (paired) {
+        clover_kernel_pk<Ts, CLV_INV_MUL><<<grid, 256, 0, l.stream>>>(a);
+        note_launch();
+        return cudaGetLastError();
+      }
+    clover_kernel<Ts, Tc, Tm, CLV_INV_MUL, false><<<grid, block, 0, l.stream>>>(a);
+    note_launch();
+    return cudaGetLastError();
+  }
 #undef FS_CLV
   return cudaErrorInvalidValue;
 }
