@@ -388,3 +388,26 @@ def test_clover_16x32_dslash_and_solves_at_the_bench_precision():
             assert r <= 1.05e-8, (s, k, r)
             assert st[j * 2 + k]["status"] == 2
     ctx.close()
+
+
+def test_clover_16x32_last_level_sample_against_an_oracle_solve():
+    """One last-level sample of the 16^3x32 job with the clover term (sigma_L = 0.6, the cheapest level
+    for the oracle) against the contraction of the oracle's own D_sw BiCGStab solution on the same
+    noise, at the mixed-precision tolerance of the level traces."""
+    from oracle import philox as ophilox
+    dims = (16, 16, 16, 32)
+    v = int(np.prod(dims))
+    u = inputs.gauge_field(dims, "smooth", seed=1003, eps=0.4)
+    c_sw = 1.0
+    ctx = make_ctx(dims, u, c_sw)
+    sig = [0.005, 0.03, 0.15, 0.6]
+    m, p, seed, job = -0.35, 4, 2003, 79
+    out = ctx.mlmc_level_trace(m, sig, pkg.gamma_matrix("g3"), p, [1, 1, 1, 1], seed=seed, job=job, prec="f16",
+                               tol=1e-8, rhs_tile=32, link_compress=12, estimator="diff")
+    ctx.close()
+    assert out["rc"] == 0
+    z = ophilox.z4_noise(v, seed, job, 3, 0)
+    solver = oest.make_solver(u, m, dims, -1, tol=1e-10, cterm=cterm_of(u, dims, c_sw))
+    ref = oest.contract(u, z, solver(z, 0.6), odirac.GAMMA[2], p, dims)
+    got = out["samples"][3][0]
+    assert abs(got - ref) <= 1e-6 * abs(ref), (got, ref)
