@@ -202,8 +202,9 @@ FS_API int fs_set_clover(fs_ctx* ctx, double c_sw);
 /* ---- the operations of the paper -------------------------------------------------- */
 
 /* out_k = (D + sigma I) in_k for k < nrhs, full lattice (the operator of
- * Eq. (shifted_linear_systems)). in/out: host [nrhs][V][4][3][2]. prec selects the
- * storage precision of the device vectors (F64 computes in FP64, others in FP32). */
+ * Eq. (shifted_linear_systems); D_sw + sigma I with the clover term, fs_set_clover). in/out: host
+ * [nrhs][V][4][3][2]. prec selects the storage precision of the device vectors (F64 computes in
+ * FP64, others in FP32). */
 FS_API int wilson_dslash(fs_ctx* ctx, double m, double sigma, const double* in, double* out, int nrhs,
                   int prec, int link_compress);
 
