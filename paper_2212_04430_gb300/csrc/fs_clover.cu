@@ -321,9 +321,10 @@ int clover_inverses(Ctx* c, double m, const double* sigma, int n, SolveOpts& o) 
   }
   const size_t cnt = (size_t)2 * c->g.Vh * 2 * CLV_PACKED;
   const int n2 = 2 * c->g.Vh;
+  // every shift the call names gets its table (the paired pass relies on it: a system without
+  // one would take its partner's), however many; only the kept tables of other calls are capped
   for (double A : want) {
     if (c->clv_inv.count(A)) continue;
-    if (c->clv_inv.size() >= MAX_SHIFTS) break;  // the rest take the eigen-decomposed form
     ClvInv t;
     if (cudaMalloc(&t.t64, cnt * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();

@@ -233,10 +233,10 @@ struct SolveOpts {
   int cg_max_iter;  // CGNR fallback iterations; 0: no fallback
 };
 
-// The packed (A + C(x))^-1 for the shifts sigma[0..n) of a call (A = 4 + m + sigma), built from the
-// eigen-decomposed table where missing and kept for later calls (at most 32 shifts; entries the
-// call does not name are dropped first); o.clv_inv then points at them. A no-op without the
-// clover term. 0 or an error code (fs_clover.cu).
+// The packed (A + C(x))^-1 for every shift sigma[0..n) of a call (A = 4 + m + sigma), built from
+// the eigen-decomposed table where missing and kept for later calls (beyond 32 in all, the kept
+// tables of shifts the call does not name are dropped first); o.clv_inv then points at them. A
+// no-op without the clover term. 0 or an error code (3: no device memory for them) (fs_clover.cu).
 int clover_inverses(Ctx* c, double m, const double* sigma, int n, SolveOpts& o);
 
 // A group of systems whose solutions are contracted together (they share the tile

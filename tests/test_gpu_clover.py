@@ -363,6 +363,22 @@ def test_clover_with_the_papers_noise_lanes_and_displacements():
     ctx.close()
 
 
+def test_clover_call_with_more_shifts_than_the_kept_inverses():
+    """34 shifts in one call on 32-system tiles (the paired passes): every shift gets its packed
+    inverse, so every solution meets tol by the oracle's D_sw residual."""
+    dims = (4, 4, 2, 4)
+    u = inputs.gauge_field(dims, "smooth", seed=1216, eps=0.4)
+    b = inputs.random_spinor(dims, 26, nvec=1)
+    sig = list(np.linspace(0.0, 0.99, 34))
+    ct = cterm_of(u, dims, 1.0)
+    ctx = make_ctx(dims, u, 1.0)
+    x, st, rc = ctx.shifted_solve(-0.2, sig, b, prec="f16", tol=1e-8, rhs_tile=32, link_compress=12)
+    ctx.close()
+    assert rc == 0
+    for j, s in enumerate(sig):
+        assert rel_resid_sw(u, x[j, 0], b[0], -0.2, s, dims, ct) <= 1.05e-8, (j, s)
+
+
 def test_clover_16x32_dslash_and_solves_at_the_bench_precision():
     """The bench lattice, links and precision with the clover term: the FP16 dslash (12-real links,
     16-system tile, the paired clover pass) against the oracle's D_sw on sampled vectors, and solves
